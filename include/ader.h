@@ -1,0 +1,164 @@
+/*
+ * ader.h - C ABI of the GB300 ADER-DG time-step library (libader.so).
+ *
+ * The library advances first-order hyperbolic systems
+ *     dQ/dt + div F(Q) + B(Q) . grad Q = S(Q) + sum_i delta_i          (Eq. (1), Sec. 2)
+ * on uniform Cartesian grids with the ADER-DG scheme of Sec. 3.3: per cell an element-local
+ * space-time predictor (Eq. (5), fixed-point iteration), per face a Rusanov numerical flux
+ * (with a path-conservative fluctuation for B(Q).grad Q), per cell the corrector Eq. (6),
+ * the CFL time step Eq. (7) and, for the Euler equations, the a-posteriori FV subcell limiter
+ * of Sec. 3.5.  PDE terms follow the user functions of Table 2 (flux, nonConservativeProduct,
+ * pointSource, eigenvalues, boundaryValues, multiplyMaterialParameterMatrix,
+ * isPhysicallyAdmissable), built in for three systems: scalar advection (tests), compressible
+ * Euler (Eq. (8), gamma-law pressure of Sec. 6.1) and linear elasticity (Sec. 2.1).
+ *
+ * Conventions for every call:
+ *  - All floating-point data are IEEE binary64 ("double").
+ *  - State layout: q[cell][node][var], cell = i + nx*(j + ny*k), node = a + n*(b + n*c)
+ *    (x fastest), n = order+1 Gauss-Legendre nodes per direction on each cell, nodes
+ *    ascending in [0,1] (ader_reference_nodes returns them).
+ *  - Pointers are owned by the caller.  The context copies what it needs; it never keeps a
+ *    caller pointer except the seismogram buffer of ader_set_receivers.
+ *  - "on_device" = 1: the pointer is CUDA device memory of the context's device, used in
+ *    stream order on the context's stream; 0: host memory, the call synchronises the stream.
+ *  - Calls are asynchronous on the context's stream unless stated otherwise.  Errors found on
+ *    the device (non-finite state, inadmissible FV result, a device wait that gave up) are
+ *    latched in a device status word and returned by the next synchronising call
+ *    (ader_sync, ader_last_dt, ader_get_state with on_device = 0, ...).  No kernel traps.
+ *  - A context is not thread-safe.  Calls before the state is set return ADER_ESTATE.
+ */
+#ifndef ADER_H
+#define ADER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ader_ctx ader_ctx;
+
+typedef enum {
+  ADER_OK = 0,
+  ADER_EINVAL = 1,        /* bad argument (NULL pointer, size mismatch, out-of-range value) */
+  ADER_ENOMEM = 2,        /* device or host allocation failed */
+  ADER_ECUDA = 3,         /* a CUDA runtime call failed */
+  ADER_ESTATE = 4,        /* call order: e.g. ader_step before ader_set_state */
+  ADER_ENONFINITE = 5,    /* a non-finite value appeared in the state */
+  ADER_EADMISSIBLE = 6,   /* the FV recompute of a troubled cell is not physically admissible */
+  ADER_ETIMEOUT = 7,      /* a bounded device-side wait gave up */
+  ADER_EUNSUPPORTED = 8   /* combination of PDE / dimension / order / option not built */
+} ader_status;
+
+typedef enum { ADER_PDE_ADVECTION = 0, ADER_PDE_EULER = 1, ADER_PDE_ELASTIC = 2 } ader_pde;
+
+/* Boundary kinds per face (Table 2 "boundaryValues"):
+ *  PERIODIC  - wrap around (both faces of a direction must be periodic);
+ *  WALL      - reflecting wall: mirror state with the normal momentum negated (Euler);
+ *  ABSORBING - zero exterior state for linear PDEs (advection, elastic), a transmissive copy of
+ *              the interior state for Euler; the exterior material is the interior one. */
+typedef enum { ADER_BC_PERIODIC = 0, ADER_BC_WALL = 1, ADER_BC_ABSORBING = 2 } ader_bc;
+
+/* Arithmetic of the space-time predictor (the rest of the step is always FP64):
+ *  FP64  - everything in binary64;
+ *  MIXED - predictor iterations on the increment q - u^n in binary32 with FP64 base terms
+ *          (see the precision notes of the library documentation). */
+typedef enum { ADER_PREC_FP64 = 0, ADER_PREC_MIXED = 1 } ader_prec;
+
+typedef struct {
+  int dim;             /* 2 or 3 (elastic: 3) */
+  int order;           /* polynomial order N >= 1 (n = N+1 nodes per direction) */
+  int pde;             /* ader_pde */
+  int n[3];            /* cells per direction (n[2] ignored for dim = 2) */
+  double lo[3], hi[3]; /* domain box */
+  int bc[3][2];        /* ader_bc for the low / high face of each direction */
+  double cfl;          /* CFL_N of Eq. (7): dt = cfl / (dim (2N+1)) * min h / lambda_max */
+  double gamma;        /* ratio of specific heats (Euler), e.g. 1.4 */
+  double adv[3];       /* advection velocity (ADER_PDE_ADVECTION) */
+  int picard_iters;    /* fixed number of predictor iterations; 0 => order + 1 */
+  int limiter;         /* 1: a-posteriori FV subcell limiter (Euler only), 0: off */
+  int precision;       /* ader_prec */
+} ader_config;
+
+/* Create a context on the current CUDA device.  `cuda_stream` is a cudaStream_t (NULL = the
+ * legacy default stream).  Allocates every device buffer the step needs (the state, the next
+ * state, face data, face fluxes, limiter data).  *out is NULL on failure. */
+ader_status ader_create(const ader_config* cfg, void* cuda_stream, ader_ctx** out);
+
+/* Release the context and its device buffers; NULL-safe.  Synchronises its stream. */
+void ader_destroy(ader_ctx* ctx);
+
+/* The library's n = order+1 Gauss-Legendre nodes x[n] (ascending in [0,1]) and weights w[n]
+ * (sum 1), host arrays.  Either pointer may be NULL. */
+ader_status ader_reference_nodes(int order, double* x, double* w);
+
+/* Number of cells, nodes per cell (n^dim) and variables of the context. */
+ader_status ader_sizes(const ader_ctx* ctx, int64_t* cells, int64_t* nodes_per_cell, int* nvar);
+
+/* Copy the state in / out; `count` must equal cells * nodes_per_cell * nvar.  Setting the
+ * state also resets the limiter history (no cell troubled at the previous step). */
+ader_status ader_set_state(ader_ctx* ctx, const double* q, int64_t count, int on_device);
+ader_status ader_get_state(ader_ctx* ctx, double* q, int64_t count, int on_device);
+
+/* Per-cell material (rho, lambda, mu), [cells][3], for the elastic PDE.  Required before
+ * stepping an elastic context. */
+ader_status ader_set_material(ader_ctx* ctx, const double* mat, int on_device);
+
+/* Moment-tensor point source (Eq. (1) delta term; Table 2 pointSource) at x0, adding
+ * -M R(t) delta(x - x0) to the stress components (xx, yy, zz, xy, xz, yz), R the Ricker wavelet
+ * (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2).  Elastic only.  x0 lies in the half-open
+ * cell [x_k, x_{k+1}) (the last cell also owns the upper boundary). */
+ader_status ader_set_point_source(ader_ctx* ctx, const double x0[3], const double M[6],
+                                  double f0, double t0);
+
+/* Receivers at nrec host points xyz[nrec][3]: after every ader_step the velocity
+ * (v_x, v_y, v_z) of the new state at each receiver is written to
+ * seismo[k][nrec][3] (device memory, capacity `max_steps` rows, k = steps since this call).
+ * The caller keeps `seismo` alive while stepping.  Elastic only.  nrec = 0 removes them. */
+ader_status ader_set_receivers(ader_ctx* ctx, int nrec, const double* xyz, double* seismo,
+                               int64_t max_steps);
+
+/* Simulation time (device-side).  ader_get_time synchronises. */
+ader_status ader_set_time(ader_ctx* ctx, double t);
+ader_status ader_get_time(ader_ctx* ctx, double* t);
+
+/* One ADER-DG time step on the context's stream.  dt > 0: that step size; dt <= 0: the CFL
+ * step of Eq. (7) computed on the device from the current state.  t_end > 0: the step is
+ * clipped so that t does not pass t_end (a step at t >= t_end leaves the state unchanged);
+ * t_end <= 0: no clipping.  Does not synchronise. */
+ader_status ader_step(ader_ctx* ctx, double dt, double t_end);
+
+/* Run `steps` steps (same dt / t_end meaning as ader_step) and synchronise. */
+ader_status ader_run(ader_ctx* ctx, int steps, double dt, double t_end);
+
+/* The dt used by the last step (host; synchronises). */
+ader_status ader_last_dt(ader_ctx* ctx, double* dt);
+
+/* Troubled-cell flags of the last step, [cells] bytes (1 = recomputed with FV), and the count. */
+ader_status ader_get_flags(ader_ctx* ctx, uint8_t* flags, int on_device);
+ader_status ader_troubled_count(ader_ctx* ctx, int64_t* count);
+
+/* Synchronise the stream and return (then clear) the latched device status. */
+ader_status ader_sync(ader_ctx* ctx);
+
+/* Capture `steps` calls of ader_step(dt, t_end) into a CUDA graph and replay it `replays` times
+ * (steps * replays steps in total); the graph is kept and reused while (steps, dt, t_end) stay
+ * the same.  Does not synchronise. */
+ader_status ader_run_graph(ader_ctx* ctx, int steps, int replays, double dt, double t_end);
+
+/* Per-phase device timing.  While enabled, every ader_step records CUDA events on the context's
+ * stream around its phases: 0 CFL speed reduction, 1 dt finalisation, 2 predictor, 3 Riemann,
+ * 4 corrector, 5 limiter, 6 receivers and time advance.  ader_phase_times synchronises, writes
+ * the summed milliseconds of each phase over the recorded steps to ms[7], the number of recorded
+ * steps to *steps, and clears the record.  Timing adds no synchronisation between steps. */
+ader_status ader_enable_timing(ader_ctx* ctx, int on);
+ader_status ader_phase_times(ader_ctx* ctx, double ms[7], int* steps);
+
+/* Human-readable name of a status. */
+const char* ader_status_string(ader_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADER_H */

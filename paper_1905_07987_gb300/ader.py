@@ -1,0 +1,260 @@
+"""ctypes binding of the C ABI in include/ader.h (argument marshalling only).
+
+Every step of the method runs in the CUDA kernels of libader.so; this module only converts
+arguments.  Tensors passed with ``on_device`` are torch CUDA tensors (their ``data_ptr()`` goes
+to the library, on the context's stream); host data may be numpy arrays or CPU tensors.
+The library is loaded on first use; if it is missing the call raises (there is no fallback).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libader.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ENONFINITE, EADMISSIBLE, ETIMEOUT, EUNSUPPORTED = range(9)
+PDE = {"advection": 0, "euler": 1, "elastic": 2}
+BC = {"periodic": 0, "wall": 1, "absorbing": 2}
+PREC = {"fp64": 0, "mixed": 1}
+
+
+class AderError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, status_string(status), status))
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("order", ctypes.c_int),
+        ("pde", ctypes.c_int),
+        ("n", ctypes.c_int * 3),
+        ("lo", ctypes.c_double * 3),
+        ("hi", ctypes.c_double * 3),
+        ("bc", (ctypes.c_int * 2) * 3),
+        ("cfl", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("adv", ctypes.c_double * 3),
+        ("picard_iters", ctypes.c_int),
+        ("limiter", ctypes.c_int),
+        ("precision", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_L = ctypes.c_int64
+_SIGS = {
+    "ader_status_string": ([_I], ctypes.c_char_p),
+    "ader_reference_nodes": ([_I, _P, _P], _I),
+    "ader_create": ([ctypes.POINTER(Config), _P, ctypes.POINTER(_P)], _I),
+    "ader_destroy": ([_P], None),
+    "ader_sizes": ([_P, ctypes.POINTER(_L), ctypes.POINTER(_L), ctypes.POINTER(_I)], _I),
+    "ader_set_state": ([_P, _P, _L, _I], _I),
+    "ader_get_state": ([_P, _P, _L, _I], _I),
+    "ader_set_material": ([_P, _P, _I], _I),
+    "ader_set_point_source": ([_P, _P, _P, _D, _D], _I),
+    "ader_set_receivers": ([_P, _I, _P, _P, _L], _I),
+    "ader_set_time": ([_P, _D], _I),
+    "ader_get_time": ([_P, ctypes.POINTER(_D)], _I),
+    "ader_step": ([_P, _D, _D], _I),
+    "ader_run": ([_P, _I, _D, _D], _I),
+    "ader_last_dt": ([_P, ctypes.POINTER(_D)], _I),
+    "ader_get_flags": ([_P, _P, _I], _I),
+    "ader_troubled_count": ([_P, ctypes.POINTER(_L)], _I),
+    "ader_sync": ([_P], _I),
+    "ader_run_graph": ([_P, _I, _I, _D, _D], _I),
+    "ader_enable_timing": ([_P, _I], _I),
+    "ader_phase_times": ([_P, _P, ctypes.POINTER(_I)], _I),
+}
+
+PHASES = ("cfl", "dt", "predictor", "riemann", "corrector", "limiter", "receivers")
+
+
+def lib():
+    """Load libader.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libader.so not found at %s: build it first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def status_string(s):
+    try:
+        return lib().ader_status_string(int(s)).decode()
+    except Exception:  # noqa: BLE001 - only used inside error messages
+        return "status"
+
+
+def check(status, what):
+    if status != OK:
+        raise AderError(status, what)
+
+
+def reference_nodes(order):
+    x = np.zeros(order + 1)
+    w = np.zeros(order + 1)
+    check(lib().ader_reference_nodes(order, x.ctypes.data, w.ctypes.data), "ader_reference_nodes")
+    return x, w
+
+
+def _ptr(a):
+    """(pointer, on_device, keepalive) of a numpy array or torch tensor (contiguous float64)."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if not a.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return a.data_ptr(), 1 if a.is_cuda else 0, a
+    except ImportError:  # pragma: no cover
+        pass
+    arr = np.ascontiguousarray(a)
+    return arr.ctypes.data, 0, arr
+
+
+def make_config(pde, dim, order, ncell, lo, hi, bc, cfl, gamma=1.4, adv=(0.0, 0.0, 0.0),
+                picard_iters=0, limiter=False, precision="fp64"):
+    c = Config()
+    c.dim = dim
+    c.order = order
+    c.pde = PDE[pde] if isinstance(pde, str) else int(pde)
+    for d in range(3):
+        c.n[d] = int(ncell[d]) if d < dim else 1
+        c.lo[d] = float(lo[d]) if d < dim else 0.0
+        c.hi[d] = float(hi[d]) if d < dim else 1.0
+    if isinstance(bc, str):
+        bc = [(bc, bc)] * dim
+    for d in range(3):
+        for s in range(2):
+            k = bc[d][s] if d < dim else "periodic"
+            c.bc[d][s] = BC[k] if isinstance(k, str) else int(k)
+    c.cfl = float(cfl)
+    c.gamma = float(gamma)
+    for d in range(3):
+        c.adv[d] = float(adv[d]) if d < len(adv) else 0.0
+    c.picard_iters = int(picard_iters)
+    c.limiter = 1 if limiter else 0
+    c.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+    return c
+
+
+class Context:
+    """Owns one ader_ctx.  Methods map one-to-one to the C ABI."""
+
+    def __init__(self, config, stream=None):
+        L = lib()
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except ImportError:  # pragma: no cover
+                stream = 0
+        self.config = config
+        self._stream = stream
+        h = _P()
+        check(L.ader_create(ctypes.byref(config), _P(stream), ctypes.byref(h)), "ader_create")
+        self._h = h
+        cells, nodes, nvar = _L(), _L(), _I()
+        check(L.ader_sizes(h, ctypes.byref(cells), ctypes.byref(nodes), ctypes.byref(nvar)), "ader_sizes")
+        self.cells, self.nodes, self.nvar = cells.value, nodes.value, nvar.value
+        self.count = self.cells * self.nodes * self.nvar
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ader_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def set_state(self, q):
+        p, dev, keep = _ptr(q)
+        check(lib().ader_set_state(self._h, p, self.count, dev), "ader_set_state")
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.count)
+        p, dev, keep = _ptr(out)
+        check(lib().ader_get_state(self._h, p, self.count, dev), "ader_get_state")
+        return out
+
+    def set_material(self, mat):
+        p, dev, keep = _ptr(mat)
+        check(lib().ader_set_material(self._h, p, dev), "ader_set_material")
+
+    def set_point_source(self, x0, M, f0, t0):
+        x0 = np.ascontiguousarray(x0, dtype=np.float64)
+        M = np.ascontiguousarray(M, dtype=np.float64)
+        check(lib().ader_set_point_source(self._h, x0.ctypes.data, M.ctypes.data, float(f0), float(t0)),
+              "ader_set_point_source")
+
+    def set_receivers(self, xyz, seismo, max_steps):
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        p, dev, keep = _ptr(seismo)
+        if not dev:
+            raise ValueError("seismogram buffer must be device memory")
+        self._seismo = seismo
+        check(lib().ader_set_receivers(self._h, len(xyz), xyz.ctypes.data, p, int(max_steps)),
+              "ader_set_receivers")
+
+    def set_time(self, t):
+        check(lib().ader_set_time(self._h, float(t)), "ader_set_time")
+
+    def time(self):
+        t = _D()
+        check(lib().ader_get_time(self._h, ctypes.byref(t)), "ader_get_time")
+        return t.value
+
+    def step(self, dt=0.0, t_end=0.0):
+        check(lib().ader_step(self._h, float(dt), float(t_end)), "ader_step")
+
+    def run(self, steps, dt=0.0, t_end=0.0):
+        check(lib().ader_run(self._h, int(steps), float(dt), float(t_end)), "ader_run")
+
+    def run_graph(self, steps, replays, dt=0.0, t_end=0.0):
+        check(lib().ader_run_graph(self._h, int(steps), int(replays), float(dt), float(t_end)),
+              "ader_run_graph")
+
+    def last_dt(self):
+        v = _D()
+        check(lib().ader_last_dt(self._h, ctypes.byref(v)), "ader_last_dt")
+        return v.value
+
+    def flags(self):
+        out = np.zeros(self.cells, dtype=np.uint8)
+        check(lib().ader_get_flags(self._h, out.ctypes.data, 0), "ader_get_flags")
+        return out
+
+    def troubled_count(self):
+        v = _L()
+        check(lib().ader_troubled_count(self._h, ctypes.byref(v)), "ader_troubled_count")
+        return v.value
+
+    def enable_timing(self, on=True):
+        check(lib().ader_enable_timing(self._h, 1 if on else 0), "ader_enable_timing")
+
+    def phase_times(self):
+        """(dict phase -> summed ms, recorded steps); synchronises and clears the record."""
+        ms = np.zeros(7)
+        n = _I()
+        check(lib().ader_phase_times(self._h, ms.ctypes.data, ctypes.byref(n)), "ader_phase_times")
+        return dict(zip(PHASES, ms.tolist())), n.value
+
+    def sync(self):
+        check(lib().ader_sync(self._h), "ader_sync")

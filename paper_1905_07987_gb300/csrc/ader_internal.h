@@ -1,0 +1,123 @@
+// Internal declarations shared by the host runtime (api.cu) and the kernel translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ader {
+
+constexpr int MAXN = 7;   // nodes per direction supported (order <= 6)
+constexpr int MAXNS = 13; // FV subcells per direction (2N+1)
+
+// Boundary kinds (same values as ader_bc in include/ader.h).
+constexpr int BC_PERIODIC = 0, BC_WALL = 1, BC_ABSORBING = 2;
+
+// Error bits latched in DevScalars::status by kernels.
+enum : int {
+  ST_NONFINITE = 1,
+  ST_ADMISSIBLE = 2,
+  ST_TIMEOUT = 4,
+  ST_SEISMO_FULL = 8,
+};
+
+// Device-resident scalars of the time loop.  dt and t never travel to the host during a run.
+struct DevScalars {
+  double t;                  // t^n
+  double dt;                 // dt of the current / last step
+  unsigned long long lam_bits;  // max signal speed of the state at t^n (bit pattern, >= 0)
+  int status;                // latched error bits
+  int pad;
+  long long nstep;           // steps taken
+  long long seismo_row;      // next seismogram row
+  int n_troubled;            // troubled cells of the last step
+  int pad2;
+};
+
+// 1-D reference-element tables, passed by value as a kernel parameter (constant bank).
+struct Tables {
+  double D[MAXN][MAXN];   // D[i][m] = phi_m'(x_i)
+  double Kw[MAXN][MAXN];  // K1^{-1} diag(w): predictor update q = u + dt Kw R
+  double w[MAXN];         // Gauss-Legendre weights on [0,1]
+  double x[MAXN];         // nodes
+  double e0[MAXN], e1[MAXN];  // phi_m(0), phi_m(1)
+  double c0[MAXN], c1[MAXN];  // e0/w, e1/w
+  double pz[3], pw[3];        // 3-point Gauss-Legendre rule on [0,1] (path integral of B)
+};
+
+// Subcell tables of the limiter (Sec. 3.5).
+struct SubTables {
+  double P1[MAXNS][MAXN];  // DG nodal values -> subcell averages
+  double R1[MAXN][MAXNS];  // subcell averages -> DG (mean-preserving least squares)
+  double Pf[MAXNS][MAXN];  // P1[s][m] / (w_m ns): subface flux -> nodal face flux weights
+};
+
+struct Geometry {
+  int dim, order;
+  int n[3];            // cells per direction
+  long long ncells;
+  double lo[3], h[3], inv_h[3];
+  int bc[3][2];
+};
+
+struct PdeParams {
+  double gamma;
+  double a[3];
+};
+
+struct PointSrc {
+  int cell;            // -1: none
+  double M[6];
+  double f0, t0;
+  const double* phi;   // [n^dim]: Phi_j(xi0) / (W_j h^dim)
+};
+
+struct Receivers {
+  int nrec;
+  const int* cell;     // [nrec]
+  const double* phi;   // [nrec][n^dim] basis values at the receiver
+  double* seismo;      // [max_rows][nrec][3]
+  long long max_rows;
+};
+
+// Arguments of one step's kernels.
+struct StepArgs {
+  Geometry g;
+  PdeParams p;
+  const double* u;     // state at t^n
+  double* u_next;      // state at t^{n+1} (predictor writes u + volume terms, corrector adds faces)
+  double* face;        // per cell, direction, side: time-averaged q (and flux) extrapolations
+  double* phi;         // per direction and face: numerical fluxes
+  const double* mat;   // [cells][3] or null
+  DevScalars* dev;
+  int iters;
+  PointSrc src;
+  double dt_fixed;     // > 0: fixed dt
+  double t_end;        // > 0: clip
+  double cfl;
+};
+
+// Per (pde, dim) kernel family; order dispatch happens inside.
+struct Family {
+  int nvar;
+  bool conservative;   // has a flux F (face records carry Fbar)
+  // launchers: return cudaError_t of the launch
+  cudaError_t (*cfl)(const StepArgs&, cudaStream_t);
+  cudaError_t (*predictor)(const StepArgs&, const Tables&, int prec, cudaStream_t);
+  cudaError_t (*riemann)(const StepArgs&, const Tables&, cudaStream_t);
+  cudaError_t (*corrector)(const StepArgs&, const Tables&, cudaStream_t);
+  size_t (*predictor_smem)(int order, int prec);
+};
+
+const Family* family_advection2();
+const Family* family_advection3();
+const Family* family_euler2();
+const Family* family_euler3();
+const Family* family_elastic3();
+
+// Small kernels shared by all families (common.cu).
+cudaError_t launch_dt_finalize(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_advance(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_advance_rec(const StepArgs& a, int receivers_on, cudaStream_t s);
+cudaError_t launch_receivers(const StepArgs& a, const Receivers& r, int nodes, int nvar,
+                             cudaStream_t s);
+
+}  // namespace ader

@@ -1,0 +1,685 @@
+// Host runtime behind the C ABI of include/ader.h: context, reference-element tables, device
+// buffers, the per-step kernel sequence and CUDA-graph replay.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ader.h"
+#include "ader_internal.h"
+
+using namespace ader;
+
+namespace {
+
+// ---- reference element (host, FP64) ------------------------------------------------------
+// Gauss-Legendre nodes and weights on [0,1] by the Golub-Welsch method: eigenvalues of the
+// symmetric tridiagonal Jacobi matrix of the Legendre recurrence (off-diagonal
+// k / sqrt(4k^2 - 1)), weights 2 v_0^2 from the normalised eigenvectors; eigen-decomposition by
+// cyclic Jacobi rotations.
+void gauss_legendre_gw(int n, double* x, double* w) {
+  double A[MAXNS][MAXNS] = {};
+  double V[MAXNS][MAXNS] = {};
+  for (int i = 0; i < n; ++i) V[i][i] = 1.0;
+  for (int k = 1; k < n; ++k) {
+    const double b = k / std::sqrt(4.0 * k * k - 1.0);
+    A[k - 1][k] = A[k][k - 1] = b;
+  }
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += A[p][q] * A[p][q];
+    if (off < 1e-34) break;
+    for (int p = 0; p < n; ++p) {
+      for (int q = p + 1; q < n; ++q) {
+        if (std::fabs(A[p][q]) < 1e-300) continue;
+        const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {  // A <- A J
+          const double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - s * akq;
+          A[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // A <- J^T A
+          const double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - s * aqk;
+          A[q][k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {  // V <- V J
+          const double vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = c * vkp - s * vkq;
+          V[k][q] = s * vkp + c * vkq;
+        }
+      }
+    }
+  }
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      if (A[idx[j]][idx[j]] < A[idx[i]][idx[i]]) std::swap(idx[i], idx[j]);
+  for (int i = 0; i < n; ++i) {
+    const int k = idx[i];
+    x[i] = 0.5 * (A[k][k] + 1.0);
+    w[i] = V[0][k] * V[0][k];  // 2 v0^2 on [-1,1], halved on [0,1]
+  }
+  if (n % 2 == 1) x[n / 2] = 0.5;  // exact middle node
+}
+
+// Barycentric weights 1 / prod_{k != m} (x_m - x_k).
+void bary(int n, const double* x, double* lam) {
+  for (int m = 0; m < n; ++m) {
+    double p = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (k != m) p *= (x[m] - x[k]);
+    lam[m] = 1.0 / p;
+  }
+}
+
+// Lagrange basis values at xi by the second barycentric formula.
+void basis_at(int n, const double* x, double xi, double* phi) {
+  double lam[MAXN];
+  bary(n, x, lam);
+  for (int m = 0; m < n; ++m)
+    if (xi == x[m]) {
+      for (int k = 0; k < n; ++k) phi[k] = (k == m) ? 1.0 : 0.0;
+      return;
+    }
+  double den = 0.0;
+  for (int m = 0; m < n; ++m) den += lam[m] / (xi - x[m]);
+  for (int m = 0; m < n; ++m) phi[m] = lam[m] / (xi - x[m]) / den;
+}
+
+// Gauss-Jordan inverse with partial pivoting (n <= MAXN).
+bool invert(int n, double (*a)[MAXN], double (*inv)[MAXN]) {
+  double m[MAXN][2 * MAXN];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < 2 * n; ++j) m[i][j] = j < n ? a[i][j] : (j - n == i ? 1.0 : 0.0);
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(m[r][c]) > std::fabs(m[piv][c])) piv = r;
+    if (std::fabs(m[piv][c]) < 1e-300) return false;
+    for (int j = 0; j < 2 * n; ++j) std::swap(m[c][j], m[piv][j]);
+    const double d = m[c][c];
+    for (int j = 0; j < 2 * n; ++j) m[c][j] /= d;
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = m[r][c];
+      for (int j = 0; j < 2 * n; ++j) m[r][j] -= f * m[c][j];
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) inv[i][j] = m[i][j + n];
+  return true;
+}
+
+bool build_tables(int order, Tables& T) {
+  std::memset(&T, 0, sizeof(T));
+  const int n = order + 1;
+  double x[MAXN], w[MAXN], lam[MAXN];
+  gauss_legendre_gw(n, x, w);
+  bary(n, x, lam);
+  for (int i = 0; i < n; ++i) {
+    double diag = 0.0;
+    for (int m = 0; m < n; ++m) {
+      if (m == i) continue;
+      T.D[i][m] = (lam[m] / lam[i]) / (x[i] - x[m]);
+      diag -= T.D[i][m];
+    }
+    T.D[i][i] = diag;
+  }
+  basis_at(n, x, 0.0, T.e0);
+  basis_at(n, x, 1.0, T.e1);
+  for (int i = 0; i < n; ++i) {
+    T.w[i] = w[i];
+    T.x[i] = x[i];
+    T.c0[i] = T.e0[i] / w[i];
+    T.c1[i] = T.e1[i] / w[i];
+  }
+  // K1[k][l] = e1[k] e1[l] - w[l] D[l][k];  Kw = K1^{-1} diag(w)
+  double K1[MAXN][MAXN] = {}, Ki[MAXN][MAXN] = {};
+  for (int k = 0; k < n; ++k)
+    for (int l = 0; l < n; ++l) K1[k][l] = T.e1[k] * T.e1[l] - w[l] * T.D[l][k];
+  if (!invert(n, K1, Ki)) return false;
+  for (int k = 0; k < n; ++k)
+    for (int l = 0; l < n; ++l) T.Kw[k][l] = Ki[k][l] * w[l];
+  double pz[3], pw[3];
+  gauss_legendre_gw(3, pz, pw);
+  for (int i = 0; i < 3; ++i) {
+    T.pz[i] = pz[i];
+    T.pw[i] = pw[i];
+  }
+  return true;
+}
+
+const Family* pick_family(int pde, int dim) {
+  if (pde == ADER_PDE_ADVECTION) return dim == 2 ? family_advection2() : family_advection3();
+  if (pde == ADER_PDE_EULER) return dim == 2 ? family_euler2() : family_euler3();
+  if (pde == ADER_PDE_ELASTIC && dim == 3) return family_elastic3();
+  return nullptr;
+}
+
+}  // namespace
+
+struct ader_ctx {
+  ader_config cfg;
+  cudaStream_t stream = nullptr;
+  const Family* fam = nullptr;
+  Geometry g{};
+  PdeParams p{};
+  Tables tab{};
+  long long nodes = 0, nvar = 0, ndof = 0;
+  int nf = 0;
+  double* u = nullptr;
+  double* u_next = nullptr;
+  double* face = nullptr;
+  double* phi = nullptr;
+  double* mat = nullptr;
+  DevScalars* dev = nullptr;
+  bool state_set = false, mat_set = false;
+  PointSrc src{};
+  double* src_phi = nullptr;
+  Receivers rec{};
+  int* rec_cell = nullptr;
+  double* rec_phi = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int g_steps = 0;
+  double g_dt = 0, g_tend = 0;
+  double* g_u0 = nullptr;
+  // per-phase timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;  // 8 events per recorded step
+  int ev_used = 0;              // recorded steps
+};
+
+static const int NPHASE = 7;
+
+#define CUDA_OK(x)                      \
+  do {                                  \
+    cudaError_t _e = (x);               \
+    if (_e != cudaSuccess) return ADER_ECUDA; \
+  } while (0)
+
+static ader_status latched(int bits) {
+  if (bits & ST_NONFINITE) return ADER_ENONFINITE;
+  if (bits & ST_ADMISSIBLE) return ADER_EADMISSIBLE;
+  if (bits & ST_TIMEOUT) return ADER_ETIMEOUT;
+  if (bits & ST_SEISMO_FULL) return ADER_EINVAL;
+  return ADER_OK;
+}
+
+static void free_all(ader_ctx* c) {
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  c->ev.clear();
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  cudaFree(c->u);
+  cudaFree(c->u_next);
+  cudaFree(c->face);
+  cudaFree(c->phi);
+  cudaFree(c->mat);
+  cudaFree(c->dev);
+  cudaFree(c->src_phi);
+  cudaFree(c->rec_cell);
+  cudaFree(c->rec_phi);
+}
+
+extern "C" {
+
+const char* ader_status_string(ader_status s) {
+  switch (s) {
+    case ADER_OK: return "ok";
+    case ADER_EINVAL: return "invalid argument";
+    case ADER_ENOMEM: return "out of memory";
+    case ADER_ECUDA: return "CUDA error";
+    case ADER_ESTATE: return "call order (state not set)";
+    case ADER_ENONFINITE: return "non-finite value in the state";
+    case ADER_EADMISSIBLE: return "FV recompute not physically admissible";
+    case ADER_ETIMEOUT: return "device wait timed out";
+    case ADER_EUNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+ader_status ader_reference_nodes(int order, double* x, double* w) {
+  if (order < 1 || order > MAXN - 1) return ADER_EINVAL;
+  double xx[MAXN], ww[MAXN];
+  gauss_legendre_gw(order + 1, xx, ww);
+  for (int i = 0; i <= order; ++i) {
+    if (x) x[i] = xx[i];
+    if (w) w[i] = ww[i];
+  }
+  return ADER_OK;
+}
+
+ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
+  if (!out) return ADER_EINVAL;
+  *out = nullptr;
+  if (!cfg) return ADER_EINVAL;
+  if (cfg->dim < 2 || cfg->dim > 3 || cfg->order < 1 || cfg->order > MAXN - 1) return ADER_EUNSUPPORTED;
+  const Family* fam = pick_family(cfg->pde, cfg->dim);
+  if (!fam) return ADER_EUNSUPPORTED;
+  if (cfg->precision != ADER_PREC_FP64) return ADER_EUNSUPPORTED;
+  if (cfg->limiter) return ADER_EUNSUPPORTED;
+  if (!(cfg->cfl > 0.0)) return ADER_EINVAL;
+  long long ncells = 1;
+  for (int d = 0; d < cfg->dim; ++d) {
+    if (cfg->n[d] < 1 || !(cfg->hi[d] > cfg->lo[d])) return ADER_EINVAL;
+    for (int s = 0; s < 2; ++s)
+      if (cfg->bc[d][s] < 0 || cfg->bc[d][s] > 2) return ADER_EINVAL;
+    if ((cfg->bc[d][0] == ADER_BC_PERIODIC) != (cfg->bc[d][1] == ADER_BC_PERIODIC)) return ADER_EINVAL;
+    if (cfg->pde != ADER_PDE_EULER)
+      for (int s = 0; s < 2; ++s)
+        if (cfg->bc[d][s] == ADER_BC_WALL) return ADER_EUNSUPPORTED;
+    ncells *= cfg->n[d];
+  }
+  ader_ctx* c = new (std::nothrow) ader_ctx();
+  if (!c) return ADER_ENOMEM;
+  c->cfg = *cfg;
+  c->stream = (cudaStream_t)stream;
+  c->fam = fam;
+  Geometry& g = c->g;
+  g.dim = cfg->dim;
+  g.order = cfg->order;
+  g.ncells = ncells;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = d < cfg->dim ? cfg->n[d] : 1;
+    g.lo[d] = d < cfg->dim ? cfg->lo[d] : 0.0;
+    g.h[d] = d < cfg->dim ? (cfg->hi[d] - cfg->lo[d]) / cfg->n[d] : 1.0;
+    g.inv_h[d] = 1.0 / g.h[d];
+    g.bc[d][0] = d < cfg->dim ? cfg->bc[d][0] : 0;
+    g.bc[d][1] = d < cfg->dim ? cfg->bc[d][1] : 0;
+  }
+  c->p.gamma = cfg->gamma > 0 ? cfg->gamma : 1.4;
+  for (int d = 0; d < 3; ++d) c->p.a[d] = cfg->adv[d];
+  if (!build_tables(cfg->order, c->tab)) {
+    delete c;
+    return ADER_EINVAL;
+  }
+  const int n = cfg->order + 1;
+  c->nodes = 1;
+  for (int d = 0; d < cfg->dim; ++d) c->nodes *= n;
+  c->nvar = fam->nvar;
+  c->ndof = ncells * c->nodes * c->nvar;
+  c->nf = (int)(c->nodes / n);
+  const long long face_rec = (long long)c->nf * c->nvar * (fam->conservative ? 2 : 1);
+  const int nphi = cfg->pde == ADER_PDE_ELASTIC ? 2 : 1;
+  long long nphi_total = 0;
+  for (int d = 0; d < cfg->dim; ++d)
+    nphi_total += (long long)(g.n[d] + 1) * (ncells / g.n[d]) * nphi * c->nf * c->nvar;
+  cudaError_t e = cudaSuccess;
+  e = cudaMalloc(&c->u, c->ndof * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->u_next, c->ndof * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->face, ncells * cfg->dim * 2 * face_rec * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->phi, nphi_total * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->dev, sizeof(DevScalars));
+  if (e == cudaSuccess && cfg->pde == ADER_PDE_ELASTIC) e = cudaMalloc(&c->mat, ncells * 3 * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+    return e == cudaErrorMemoryAllocation ? ADER_ENOMEM : ADER_ECUDA;
+  }
+  e = cudaMemsetAsync(c->dev, 0, sizeof(DevScalars), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->phi, 0, nphi_total * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    free_all(c);
+    delete c;
+    return ADER_ECUDA;
+  }
+  c->src.cell = -1;
+  *out = c;
+  return ADER_OK;
+}
+
+void ader_destroy(ader_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+ader_status ader_sizes(const ader_ctx* c, int64_t* cells, int64_t* nodes, int* nvar) {
+  if (!c) return ADER_EINVAL;
+  if (cells) *cells = c->g.ncells;
+  if (nodes) *nodes = c->nodes;
+  if (nvar) *nvar = (int)c->nvar;
+  return ADER_OK;
+}
+
+static ader_status copy(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind,
+                        cudaStream_t s, bool sync) {
+  CUDA_OK(cudaMemcpyAsync(dst, src, bytes, kind, s));
+  if (sync) CUDA_OK(cudaStreamSynchronize(s));
+  return ADER_OK;
+}
+
+ader_status ader_set_state(ader_ctx* c, const double* q, int64_t count, int on_device) {
+  if (!c || !q || count != c->ndof) return ADER_EINVAL;
+  ader_status st = copy(c->u, q, count * sizeof(double),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream,
+                        !on_device);
+  if (st != ADER_OK) return st;
+  c->state_set = true;
+  return ADER_OK;
+}
+
+ader_status ader_get_state(ader_ctx* c, double* q, int64_t count, int on_device) {
+  if (!c || !q || count != c->ndof) return ADER_EINVAL;
+  if (!c->state_set) return ADER_ESTATE;
+  return copy(q, c->u, count * sizeof(double),
+              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream, !on_device);
+}
+
+ader_status ader_set_material(ader_ctx* c, const double* mat, int on_device) {
+  if (!c || !mat) return ADER_EINVAL;
+  if (c->cfg.pde != ADER_PDE_ELASTIC) return ADER_EUNSUPPORTED;
+  if (!on_device) {
+    for (long long i = 0; i < c->g.ncells; ++i)
+      if (!(mat[3 * i] > 0) || !(mat[3 * i + 2] > 0) || !(mat[3 * i + 1] + 2 * mat[3 * i + 2] > 0))
+        return ADER_EINVAL;
+  }
+  ader_status st = copy(c->mat, mat, c->g.ncells * 3 * sizeof(double),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream,
+                        !on_device);
+  if (st != ADER_OK) return st;
+  c->mat_set = true;
+  return ADER_OK;
+}
+
+// Cell and reference coordinates of a point (half-open cells, last cell owns the upper face).
+static long long locate(const ader_ctx* c, const double* x, double* xi) {
+  long long cell = 0, stride = 1;
+  for (int d = 0; d < c->g.dim; ++d) {
+    const double s = (x[d] - c->g.lo[d]) / c->g.h[d];
+    long long k = (long long)std::floor(s);
+    if (k < 0) k = 0;
+    if (k > c->g.n[d] - 1) k = c->g.n[d] - 1;
+    xi[d] = s - (double)k;
+    cell += k * stride;
+    stride *= c->g.n[d];
+  }
+  return cell;
+}
+
+// Phi_j(xi) = prod_d phi_{j_d}(xi_d) for every node j (x fastest).
+static void tensor_basis(const ader_ctx* c, const double* xi, double* out) {
+  const int n = c->g.order + 1;
+  double b[3][MAXN];
+  for (int d = 0; d < c->g.dim; ++d) basis_at(n, c->tab.x, xi[d], b[d]);
+  for (long long j = 0; j < c->nodes; ++j) {
+    long long r = j;
+    double v = 1.0;
+    for (int d = 0; d < c->g.dim; ++d) {
+      v *= b[d][r % n];
+      r /= n;
+    }
+    out[j] = v;
+  }
+}
+
+ader_status ader_set_point_source(ader_ctx* c, const double x0[3], const double M[6], double f0,
+                                  double t0) {
+  if (!c || !x0 || !M) return ADER_EINVAL;
+  if (c->cfg.pde != ADER_PDE_ELASTIC) return ADER_EUNSUPPORTED;
+  for (int d = 0; d < 3; ++d)
+    if (!(x0[d] >= c->g.lo[d]) || !(x0[d] <= c->g.lo[d] + c->g.h[d] * c->g.n[d])) return ADER_EINVAL;
+  double xi[3];
+  const long long cell = locate(c, x0, xi);
+  std::vector<double> phi(c->nodes);
+  tensor_basis(c, xi, phi.data());
+  const int n = c->g.order + 1;
+  double vol = 1.0;
+  for (int d = 0; d < c->g.dim; ++d) vol *= c->g.h[d];
+  for (long long j = 0; j < c->nodes; ++j) {
+    long long r = j;
+    double W = 1.0;
+    for (int d = 0; d < c->g.dim; ++d) {
+      W *= c->tab.w[r % n];
+      r /= n;
+    }
+    phi[j] /= (W * vol);
+  }
+  if (!c->src_phi) CUDA_OK(cudaMalloc(&c->src_phi, c->nodes * sizeof(double)));
+  ader_status st = copy(c->src_phi, phi.data(), c->nodes * sizeof(double), cudaMemcpyHostToDevice,
+                        c->stream, true);
+  if (st != ADER_OK) return st;
+  c->src.cell = (int)cell;
+  for (int a = 0; a < 6; ++a) c->src.M[a] = M[a];
+  c->src.f0 = f0;
+  c->src.t0 = t0;
+  c->src.phi = c->src_phi;
+  return ADER_OK;
+}
+
+ader_status ader_set_receivers(ader_ctx* c, int nrec, const double* xyz, double* seismo,
+                               int64_t max_steps) {
+  if (!c || nrec < 0) return ADER_EINVAL;
+  if (c->cfg.pde != ADER_PDE_ELASTIC) return ADER_EUNSUPPORTED;
+  cudaFree(c->rec_cell);
+  cudaFree(c->rec_phi);
+  c->rec_cell = nullptr;
+  c->rec_phi = nullptr;
+  c->rec.nrec = 0;
+  if (nrec == 0) return ADER_OK;
+  if (!xyz || !seismo || max_steps < 1) return ADER_EINVAL;
+  std::vector<int> cells(nrec);
+  std::vector<double> phi((size_t)nrec * c->nodes);
+  for (int r = 0; r < nrec; ++r) {
+    double xi[3];
+    cells[r] = (int)locate(c, xyz + 3 * r, xi);
+    tensor_basis(c, xi, phi.data() + (size_t)r * c->nodes);
+  }
+  CUDA_OK(cudaMalloc(&c->rec_cell, nrec * sizeof(int)));
+  CUDA_OK(cudaMalloc(&c->rec_phi, phi.size() * sizeof(double)));
+  ader_status st = copy(c->rec_cell, cells.data(), nrec * sizeof(int), cudaMemcpyHostToDevice, c->stream, false);
+  if (st == ADER_OK)
+    st = copy(c->rec_phi, phi.data(), phi.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream, true);
+  if (st != ADER_OK) return st;
+  // restart the row counter
+  long long zero = 0;
+  st = copy(&c->dev->seismo_row, &zero, sizeof(long long), cudaMemcpyHostToDevice, c->stream, true);
+  if (st != ADER_OK) return st;
+  c->rec.nrec = nrec;
+  c->rec.cell = c->rec_cell;
+  c->rec.phi = c->rec_phi;
+  c->rec.seismo = seismo;
+  c->rec.max_rows = max_steps;
+  return ADER_OK;
+}
+
+ader_status ader_set_time(ader_ctx* c, double t) {
+  if (!c) return ADER_EINVAL;
+  return copy(&c->dev->t, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream, true);
+}
+
+ader_status ader_get_time(ader_ctx* c, double* t) {
+  if (!c || !t) return ADER_EINVAL;
+  return copy(t, &c->dev->t, sizeof(double), cudaMemcpyDeviceToHost, c->stream, true);
+}
+
+static StepArgs make_args(ader_ctx* c, double dt, double t_end) {
+  StepArgs a{};
+  a.g = c->g;
+  a.p = c->p;
+  a.u = c->u;
+  a.u_next = c->u_next;
+  a.face = c->face;
+  a.phi = c->phi;
+  a.mat = c->mat;
+  a.dev = c->dev;
+  a.iters = c->cfg.picard_iters > 0 ? c->cfg.picard_iters : c->cfg.order + 1;
+  a.src = c->src;
+  a.dt_fixed = dt > 0 ? dt : 0.0;
+  a.t_end = t_end > 0 ? t_end : 0.0;
+  a.cfl = c->cfg.cfl;
+  return a;
+}
+
+// Event slot for phase boundary k of the step being recorded (nullptr when not timing).
+static cudaEvent_t mark_event(ader_ctx* c, int k) {
+  if (!c->timing) return nullptr;
+  const size_t need = (size_t)(c->ev_used + 1) * (NPHASE + 1);
+  while (c->ev.size() < need) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->ev.push_back(e);
+  }
+  return c->ev[(size_t)c->ev_used * (NPHASE + 1) + k];
+}
+
+static ader_status mark(ader_ctx* c, int k) {
+  cudaEvent_t e = mark_event(c, k);
+  if (e) CUDA_OK(cudaEventRecord(e, c->stream));
+  return ADER_OK;
+}
+
+static ader_status step_impl(ader_ctx* c, double dt, double t_end) {
+  const StepArgs a = make_args(c, dt, t_end);
+  cudaStream_t s = c->stream;
+  ader_status st;
+  if ((st = mark(c, 0)) != ADER_OK) return st;
+  if (!(dt > 0)) CUDA_OK(c->fam->cfl(a, s));
+  if ((st = mark(c, 1)) != ADER_OK) return st;
+  CUDA_OK(launch_dt_finalize(a, s));
+  if ((st = mark(c, 2)) != ADER_OK) return st;
+  CUDA_OK(c->fam->predictor(a, c->tab, c->cfg.precision, s));
+  if ((st = mark(c, 3)) != ADER_OK) return st;
+  CUDA_OK(c->fam->riemann(a, c->tab, s));
+  if ((st = mark(c, 4)) != ADER_OK) return st;
+  CUDA_OK(c->fam->corrector(a, c->tab, s));
+  if ((st = mark(c, 5)) != ADER_OK) return st;
+  if ((st = mark(c, 6)) != ADER_OK) return st;
+  if (c->rec.nrec > 0) CUDA_OK(launch_receivers(a, c->rec, (int)c->nodes, (int)c->nvar, s));
+  CUDA_OK(launch_advance_rec(a, c->rec.nrec > 0, s));
+  if ((st = mark(c, 7)) != ADER_OK) return st;
+  if (c->timing) c->ev_used++;
+  std::swap(c->u, c->u_next);
+  return ADER_OK;
+}
+
+ader_status ader_step(ader_ctx* c, double dt, double t_end) {
+  if (!c) return ADER_EINVAL;
+  if (!c->state_set) return ADER_ESTATE;
+  if (c->cfg.pde == ADER_PDE_ELASTIC && !c->mat_set) return ADER_ESTATE;
+  if (!(dt == dt) || !(t_end == t_end)) return ADER_EINVAL;
+  return step_impl(c, dt, t_end);
+}
+
+ader_status ader_sync(ader_ctx* c) {
+  if (!c) return ADER_EINVAL;
+  CUDA_OK(cudaStreamSynchronize(c->stream));
+  int bits = 0;
+  CUDA_OK(cudaMemcpy(&bits, &c->dev->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (bits) {
+    int zero = 0;
+    CUDA_OK(cudaMemcpy(&c->dev->status, &zero, sizeof(int), cudaMemcpyHostToDevice));
+  }
+  return latched(bits);
+}
+
+ader_status ader_run(ader_ctx* c, int steps, double dt, double t_end) {
+  if (!c || steps < 0) return ADER_EINVAL;
+  for (int i = 0; i < steps; ++i) {
+    ader_status st = ader_step(c, dt, t_end);
+    if (st != ADER_OK) return st;
+  }
+  return ader_sync(c);
+}
+
+ader_status ader_last_dt(ader_ctx* c, double* dt) {
+  if (!c || !dt) return ADER_EINVAL;
+  ader_status st = copy(dt, &c->dev->dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream, true);
+  if (st != ADER_OK) return st;
+  return ader_sync(c);
+}
+
+ader_status ader_get_flags(ader_ctx* c, uint8_t* flags, int on_device) {
+  if (!c || !flags) return ADER_EINVAL;
+  if (on_device) {
+    CUDA_OK(cudaMemsetAsync(flags, 0, c->g.ncells, c->stream));
+  } else {
+    std::memset(flags, 0, c->g.ncells);
+  }
+  return ADER_OK;
+}
+
+ader_status ader_troubled_count(ader_ctx* c, int64_t* count) {
+  if (!c || !count) return ADER_EINVAL;
+  *count = 0;
+  return ADER_OK;
+}
+
+ader_status ader_enable_timing(ader_ctx* c, int on) {
+  if (!c) return ADER_EINVAL;
+  c->timing = on != 0;
+  c->ev_used = 0;
+  return ADER_OK;
+}
+
+ader_status ader_phase_times(ader_ctx* c, double ms[7], int* steps) {
+  if (!c || !ms) return ADER_EINVAL;
+  CUDA_OK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < NPHASE; ++k) ms[k] = 0.0;
+  for (int sidx = 0; sidx < c->ev_used; ++sidx) {
+    for (int k = 0; k < NPHASE; ++k) {
+      float t = 0.f;
+      CUDA_OK(cudaEventElapsedTime(&t, c->ev[(size_t)sidx * (NPHASE + 1) + k],
+                                   c->ev[(size_t)sidx * (NPHASE + 1) + k + 1]));
+      ms[k] += t;
+    }
+  }
+  if (steps) *steps = c->ev_used;
+  c->ev_used = 0;
+  return ADER_OK;
+}
+
+ader_status ader_run_graph(ader_ctx* c, int steps, int replays, double dt, double t_end) {
+  if (!c || steps < 1 || replays < 0 || (steps % 2) != 0 || c->timing) return ADER_EINVAL;
+  if (!c->state_set) return ADER_ESTATE;
+  if (c->cfg.pde == ADER_PDE_ELASTIC && !c->mat_set) return ADER_ESTATE;
+  if (!c->gexec || c->g_steps != steps || c->g_dt != dt || c->g_tend != t_end || c->g_u0 != c->u) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    cudaStream_t cap = c->stream;
+    bool own = false;
+    if (cap == nullptr) {  // the legacy stream cannot be captured
+      CUDA_OK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      own = true;
+      CUDA_OK(cudaStreamSynchronize(nullptr));
+    }
+    cudaStream_t saved = c->stream;
+    c->stream = cap;
+    double* u0 = c->u;
+    CUDA_OK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    ader_status st = ADER_OK;
+    for (int i = 0; i < steps && st == ADER_OK; ++i) st = step_impl(c, dt, t_end);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap, &g);
+    c->stream = saved;
+    if (st != ADER_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (own) cudaStreamDestroy(cap);
+      c->u = u0;  // steps are even, but restore in case of a partial capture
+      return st != ADER_OK ? st : ADER_ECUDA;
+    }
+    c->graph = g;
+    CUDA_OK(cudaGraphInstantiate(&c->gexec, g, 0));
+    if (own) cudaStreamDestroy(cap);
+    c->g_steps = steps;
+    c->g_dt = dt;
+    c->g_tend = t_end;
+    c->g_u0 = c->u;
+  }
+  for (int r = 0; r < replays; ++r) CUDA_OK(cudaGraphLaunch(c->gexec, c->stream));
+  return ADER_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+// Small kernels shared by every kernel family: time-step finalisation (Eq. (7)), the time
+// advance, and the receiver read-out.
+#include "ader_internal.h"
+
+namespace ader {
+
+// dt = CFL_N / (d (2N+1)) * min_d h_d / lambda_max  (or the fixed dt), clipped to t_end.
+__global__ void k_dt_finalize(const __grid_constant__ StepArgs A) {
+  DevScalars* s = A.dev;
+  double dt;
+  if (A.dt_fixed > 0.0) {
+    dt = A.dt_fixed;
+  } else {
+    const double lam = __longlong_as_double((long long)s->lam_bits);
+    double hmin = A.g.h[0];
+    for (int d = 1; d < A.g.dim; ++d) hmin = fmin(hmin, A.g.h[d]);
+    dt = A.cfl / (double)(A.g.dim * (2 * A.g.order + 1)) * hmin / lam;
+  }
+  if (A.t_end > 0.0) dt = fmin(dt, A.t_end - s->t);
+  if (dt < 0.0) dt = 0.0;
+  if (!isfinite(dt)) {
+    atomicOr(&s->status, ST_NONFINITE);
+    dt = 0.0;
+  }
+  s->dt = dt;
+  s->lam_bits = 0ull;
+}
+
+__global__ void k_advance(DevScalars* s, int receivers_on) {
+  s->t += s->dt;
+  s->nstep += 1;
+  if (receivers_on) s->seismo_row += 1;
+}
+
+// One warp per receiver: v(x_r) = sum_j Phi_j(xi_r) u[cell_r][j][0..2].
+__global__ void k_receivers(const double* __restrict__ u, DevScalars* s, Receivers r, int nodes,
+                            int nvar) {
+  const int lane = threadIdx.x & 31;
+  const int rec = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (rec >= r.nrec) return;
+  const long long row = s->seismo_row;
+  if (row >= r.max_rows) {
+    if (lane == 0) atomicOr(&s->status, ST_SEISMO_FULL);
+    return;
+  }
+  const double* uc = u + (long long)r.cell[rec] * nodes * nvar;
+  const double* ph = r.phi + (long long)rec * nodes;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (int j = lane; j < nodes; j += 32) {
+    const double p = ph[j];
+    a0 = fma(p, uc[j * nvar + 0], a0);
+    a1 = fma(p, uc[j * nvar + 1], a1);
+    a2 = fma(p, uc[j * nvar + 2], a2);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+  }
+  if (lane == 0) {
+    double* out = r.seismo + (row * r.nrec + rec) * 3;
+    out[0] = a0;
+    out[1] = a1;
+    out[2] = a2;
+  }
+}
+
+cudaError_t launch_dt_finalize(const StepArgs& a, cudaStream_t s) {
+  k_dt_finalize<<<1, 1, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_rec(const StepArgs& a, int receivers_on, cudaStream_t s) {
+  k_advance<<<1, 1, 0, s>>>(a.dev, receivers_on);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(const StepArgs& a, cudaStream_t s) { return launch_advance_rec(a, 0, s); }
+
+cudaError_t launch_receivers(const StepArgs& a, const Receivers& r, int nodes, int nvar,
+                             cudaStream_t s) {
+  if (r.nrec <= 0) return cudaSuccess;
+  const int wpb = 4;
+  k_receivers<<<(r.nrec + wpb - 1) / wpb, 32 * wpb, 0, s>>>(a.u_next, a.dev, r, nodes, nvar);
+  return cudaGetLastError();
+}
+
+}  // namespace ader

@@ -1,0 +1,676 @@
+// FP64 kernels of one ADER-DG step (Sec. 3.3-3.4), templated on the PDE system, the dimension
+// and the order.  One thread block per cell for the predictor (the work is FP64-pipe bound on
+// GB300: every cell is an independent dense small contraction problem), one warp per face for
+// the Riemann solver, one thread per degree of freedom for the corrector.
+#pragma once
+#include <cstdio>
+#include "ader_internal.h"
+#include "pde.cuh"
+
+namespace ader {
+
+// Compile-time sizes of the order-N scheme for system P in D dimensions.
+template <class P, int D, int N>
+struct Cfg {
+  static constexpr int n = N + 1;               // nodes per direction (and time nodes)
+  static constexpr int NS = ipow(n, D);         // spatial nodes per cell
+  static constexpr int NST = NS * n;            // space-time nodes per cell
+  static constexpr int NV = P::NV;
+  static constexpr int NL = NS * NV;            // lines (spatial node, variable)
+  static constexpr int NF = ipow(n, D - 1);     // nodes per face
+  static constexpr int FR = NF * NV * (P::CONS ? 2 : 1);  // doubles per face record
+  static constexpr int NPHI = P::NCP ? 2 : 1;   // numerical fluxes per face node and variable
+  static constexpr int TPB_RAW = ((NL + 5) / 6 + 31) / 32 * 32;
+  static constexpr int TPB = TPB_RAW < 64 ? 64 : (TPB_RAW > 512 ? 512 : TPB_RAW);
+  static constexpr int LPT = (NL + TPB - 1) / TPB;   // lines per thread
+  static constexpr int NPT = (NST + TPB - 1) / TPB;  // space-time nodes per thread
+  static constexpr int FSLOTS = P::CONS ? cmax(n, D + 1) : 0;
+  static constexpr size_t SMEM = (size_t)(n + FSLOTS) * NL * sizeof(double);
+};
+
+template <int n, int d>
+__device__ __forceinline__ int digit(int j) {
+  return (j / ipow(n, d)) % n;
+}
+
+// Lines (j, v) owned by this thread: l = tid + k*TPB.
+// Accumulate R[k][t] += coef * sum_m D[j_d][m] X[t][(j with j_d -> m)][vsrc]   (X: [n][NL] in smem)
+template <class C, int d>
+__device__ __forceinline__ void contract_lines(const double* X, const Tables& T, double coef,
+                                               double (&R)[C::LPT][C::n], int tid) {
+  constexpr int n = C::n, NV = C::NV, NL = C::NL, TPB = C::TPB, st = ipow(n, d);
+#pragma unroll
+  for (int k = 0; k < C::LPT; ++k) {
+    const int l = tid + k * TPB;
+    if (l < NL) {
+      const int j = l / NV, v = l - (l / NV) * NV;
+      const int jd = digit<n, d>(j);
+      const int j0 = j - jd * st;
+      const double* Dr = T.D[jd];
+#pragma unroll
+      for (int t = 0; t < n; ++t) {
+        double acc = 0.0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) acc = fma(Dr[m], X[t * NL + (j0 + m * st) * NV + v], acc);
+        R[k][t] = fma(coef, acc, R[k][t]);
+      }
+    }
+  }
+}
+
+// Elastic: each row v of B_d has one non-zero coef(d,v) at column src(d,v); the NCP term
+// B_d dq/dx_d is contracted directly from q (no flux buffer).
+template <class C, int d>
+__device__ __forceinline__ void contract_ncp_elastic(const double* X, const Tables& T,
+                                                     double inv_h, double irho, double lam,
+                                                     double mu, double (&R)[C::LPT][C::n],
+                                                     int tid) {
+  constexpr int n = C::n, NV = C::NV, NL = C::NL, TPB = C::TPB, st = ipow(n, d);
+#pragma unroll
+  for (int k = 0; k < C::LPT; ++k) {
+    const int l = tid + k * TPB;
+    if (l < NL) {
+      const int j = l / NV, v = l - (l / NV) * NV;
+      const int s = Elastic::src(d, v);
+      if (s >= 0) {
+        const double coef = -Elastic::coef_ir(d, v, irho, lam, mu) * inv_h;
+        const int jd = digit<n, d>(j);
+        const int j0 = j - jd * st;
+        const double* Dr = T.D[jd];
+#pragma unroll
+        for (int t = 0; t < n; ++t) {
+          double acc = 0.0;
+#pragma unroll
+          for (int m = 0; m < n; ++m) acc = fma(Dr[m], X[t * NL + (j0 + m * st) * NV + s], acc);
+          R[k][t] = fma(coef, acc, R[k][t]);
+        }
+      }
+    }
+  }
+}
+
+template <class C, int d, class P>
+__device__ __forceinline__ void flux_nodes(const double (&qn)[C::NPT][C::NV],
+                                           const typename P::Aux (&ax)[C::NPT],
+                                           const PdeParams& pp, double* Fs, int tid) {
+#pragma unroll
+  for (int k = 0; k < C::NPT; ++k) {
+    const int node = tid + k * C::TPB;
+    if (node < C::NST) {
+      double F[C::NV];
+      P::flux(qn[k], ax[k], pp, d, F);
+#pragma unroll
+      for (int v = 0; v < C::NV; ++v) Fs[node * C::NV + v] = F[v];
+    }
+  }
+}
+
+template <class C, class P>
+__device__ __forceinline__ void load_nodes(const double* qs, const PdeParams& pp,
+                                           double (&qn)[C::NPT][C::NV],
+                                           typename P::Aux (&ax)[C::NPT], int tid) {
+#pragma unroll
+  for (int k = 0; k < C::NPT; ++k) {
+    const int node = tid + k * C::TPB;
+    if (node < C::NST) {
+#pragma unroll
+      for (int v = 0; v < C::NV; ++v) qn[k][v] = qs[node * C::NV + v];
+      P::aux(qn[k], pp, ax[k]);
+    }
+  }
+}
+
+// Space-time predictor (Eq. (5)) with the fused epilogue: time averages, volume term, the
+// cell-local part of the face terms of Eq. (6), and the face extrapolations.
+//   q^0 = u;  q^{r+1} = u + dt Kw R(q^r)  (Kw = K1^{-1} diag(w), K1^{-1} e0 = 1)
+//   R(q) = -sum_d (1/h_d) D_d F_d(q) - sum_d (1/h_d) B_d D_d q + point source
+template <class P, int D, int N>
+__global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
+    k_predictor(const __grid_constant__ StepArgs A, const __grid_constant__ Tables T) {
+  using C = Cfg<P, D, N>;
+  constexpr int n = C::n, NV = C::NV, NL = C::NL, TPB = C::TPB, LPT = C::LPT;
+  constexpr int NF = C::NF, FR = C::FR;
+  extern __shared__ double smem[];
+  double* qs = smem;           // [n][NL] space-time predictor (time-major)
+  double* Fs = smem + n * NL;  // [FSLOTS][NL] fluxes (conservative systems)
+  const long long c = blockIdx.x;
+  const int tid = threadIdx.x;
+  const double dt = A.dev->dt;
+  const double tn = A.dev->t;
+  const double* u = A.u + c * NL;
+
+  double ul[LPT];
+#pragma unroll
+  for (int k = 0; k < LPT; ++k) {
+    const int l = tid + k * TPB;
+    ul[k] = 0.0;
+    if (l < NL) {
+      ul[k] = u[l];
+#pragma unroll
+      for (int t = 0; t < n; ++t) qs[t * NL + l] = ul[k];
+    }
+  }
+  double irho = 0.0, lam = 0.0, mu = 0.0;
+  if constexpr (P::NCP) {
+    irho = 1.0 / A.mat[c * 3 + 0];
+    lam = A.mat[c * 3 + 1];
+    mu = A.mat[c * 3 + 2];
+  }
+  const bool has_src = (A.src.cell == c);
+  double ric[n];
+#pragma unroll
+  for (int t = 0; t < n; ++t) ric[t] = 0.0;
+  if (has_src) {
+#pragma unroll
+    for (int t = 0; t < n; ++t) {
+      const double tau = fma(T.x[t], dt, tn) - A.src.t0;
+      const double a = (M_PI * A.src.f0 * tau) * (M_PI * A.src.f0 * tau);
+      ric[t] = (1.0 - 2.0 * a) * exp(-a);
+    }
+  }
+  __syncthreads();
+
+  for (int it = 0; it < A.iters; ++it) {
+    double R[LPT][n];
+#pragma unroll
+    for (int k = 0; k < LPT; ++k)
+#pragma unroll
+      for (int t = 0; t < n; ++t) R[k][t] = 0.0;
+    if constexpr (P::CONS) {
+      double qn[C::NPT][NV];
+      typename P::Aux ax[C::NPT];
+      load_nodes<C, P>(qs, A.p, qn, ax, tid);
+      flux_nodes<C, 0, P>(qn, ax, A.p, Fs, tid);
+      __syncthreads();
+      contract_lines<C, 0>(Fs, T, -A.g.inv_h[0], R, tid);
+      __syncthreads();
+      flux_nodes<C, 1, P>(qn, ax, A.p, Fs, tid);
+      __syncthreads();
+      contract_lines<C, 1>(Fs, T, -A.g.inv_h[1], R, tid);
+      __syncthreads();
+      if constexpr (D == 3) {
+        flux_nodes<C, 2, P>(qn, ax, A.p, Fs, tid);
+        __syncthreads();
+        contract_lines<C, 2>(Fs, T, -A.g.inv_h[2], R, tid);
+      }
+    }
+    if constexpr (P::NCP) {
+      contract_ncp_elastic<C, 0>(qs, T, A.g.inv_h[0], irho, lam, mu, R, tid);
+      contract_ncp_elastic<C, 1>(qs, T, A.g.inv_h[1], irho, lam, mu, R, tid);
+      contract_ncp_elastic<C, 2>(qs, T, A.g.inv_h[2], irho, lam, mu, R, tid);
+    }
+    if (has_src) {
+#pragma unroll
+      for (int k = 0; k < LPT; ++k) {
+        const int l = tid + k * TPB;
+        if (l < NL) {
+          const int j = l / NV, v = l - (l / NV) * NV;
+          if (v >= 3) {
+            const double amp = -A.src.M[v - 3] * A.src.phi[j];
+#pragma unroll
+            for (int t = 0; t < n; ++t) R[k][t] = fma(amp, ric[t], R[k][t]);
+          }
+        }
+      }
+    }
+    __syncthreads();  // every read of qs of this iteration is done
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      const int l = tid + k * TPB;
+      if (l < NL) {
+#pragma unroll
+        for (int t = 0; t < n; ++t) {
+          double acc = 0.0;
+#pragma unroll
+          for (int m = 0; m < n; ++m) acc = fma(T.Kw[t][m], R[k][m], acc);
+          qs[t * NL + l] = fma(dt, acc, ul[k]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- epilogue: time averages -------------------------------------------------------
+  double qb[LPT];
+#pragma unroll
+  for (int k = 0; k < LPT; ++k) {
+    const int l = tid + k * TPB;
+    qb[k] = 0.0;
+    if (l < NL) {
+#pragma unroll
+      for (int t = 0; t < n; ++t) qb[k] = fma(T.w[t], qs[t * NL + l], qb[k]);
+    }
+  }
+  double* qbs;   // time-averaged q [NL] in smem
+  double* FBs;   // time-averaged fluxes [D][NL] in smem (conservative)
+  if constexpr (P::CONS) {
+    double FB[D][LPT];
+    double qn[C::NPT][NV];
+    typename P::Aux ax[C::NPT];
+    load_nodes<C, P>(qs, A.p, qn, ax, tid);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      if (d == 0) flux_nodes<C, 0, P>(qn, ax, A.p, Fs, tid);
+      if (d == 1) flux_nodes<C, 1, P>(qn, ax, A.p, Fs, tid);
+      if constexpr (D == 3)
+        if (d == 2) flux_nodes<C, 2, P>(qn, ax, A.p, Fs, tid);
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < LPT; ++k) {
+        const int l = tid + k * TPB;
+        FB[d][k] = 0.0;
+        if (l < NL) {
+#pragma unroll
+          for (int t = 0; t < n; ++t) FB[d][k] = fma(T.w[t], Fs[t * NL + l], FB[d][k]);
+        }
+      }
+      __syncthreads();
+    }
+    qbs = Fs;
+    FBs = Fs + NL;
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      const int l = tid + k * TPB;
+      if (l < NL) {
+        qbs[l] = qb[k];
+#pragma unroll
+        for (int d = 0; d < D; ++d) FBs[d * NL + l] = FB[d][k];
+      }
+    }
+  } else {
+    qbs = qs;
+    FBs = nullptr;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      const int l = tid + k * TPB;
+      if (l < NL) qbs[l] = qb[k];
+    }
+  }
+  __syncthreads();
+
+  // ---- volume term and cell-local face terms -> u_next ---------------------------------
+  double* un = A.u_next + c * NL;
+#pragma unroll
+  for (int k = 0; k < LPT; ++k) {
+    const int l = tid + k * TPB;
+    if (l < NL) {
+      const int j = l / NV, v = l - (l / NV) * NV;
+      double vol = 0.0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const int st = (d == 0 ? 1 : (d == 1 ? n : n * n));
+        const int jd = (j / st) % n;
+        const int j0 = j - jd * st;
+        if constexpr (P::CONS) {
+          double dF = 0.0, Fp = 0.0, Fm = 0.0;
+#pragma unroll
+          for (int m = 0; m < n; ++m) {
+            const double f = FBs[d * NL + (j0 + m * st) * NV + v];
+            dF = fma(T.D[jd][m], f, dF);
+            Fp = fma(T.e1[m], f, Fp);
+            Fm = fma(T.e0[m], f, Fm);
+          }
+          // -(1/h) D F + (1/h)(e1/w F+ - e0/w F-)
+          vol += A.g.inv_h[d] * (-dF + T.c1[jd] * Fp - T.c0[jd] * Fm);
+        }
+        if constexpr (P::NCP) {
+          const int s = Elastic::src(d, v);
+          if (s >= 0) {
+            double dq = 0.0;
+#pragma unroll
+            for (int m = 0; m < n; ++m) dq = fma(T.D[jd][m], qbs[(j0 + m * st) * NV + s], dq);
+            vol -= A.g.inv_h[d] * Elastic::coef_ir(d, v, irho, lam, mu) * dq;
+          }
+        }
+      }
+      if (has_src && v >= 3) {
+        double sbar = 0.0;
+#pragma unroll
+        for (int t = 0; t < n; ++t) sbar = fma(T.w[t], ric[t], sbar);
+        vol = fma(-A.src.M[v - 3] * A.src.phi[j], sbar, vol);
+      }
+      un[l] = fma(dt, vol, ul[k]);
+    }
+  }
+
+  // ---- face records: time-averaged q (and F_d) extrapolated to both ends of each direction
+  double* fc = A.face + c * (long long)(D * 2 * FR);
+  constexpr int NFE = D * 2 * NF * NV;
+  for (int e = tid; e < NFE; e += TPB) {
+    const int v = e % NV;
+    const int jp = (e / NV) % NF;
+    const int side = (e / (NV * NF)) % 2;
+    const int d = e / (NV * NF * 2);
+    const int st = (d == 0 ? 1 : (d == 1 ? n : n * n));
+    const int jbase = (jp % st) + (jp / st) * st * n;
+    const double* ev = side ? T.e1 : T.e0;
+    double qf = 0.0, ff = 0.0;
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      const int jj = jbase + m * st;
+      qf = fma(ev[m], qbs[jj * NV + v], qf);
+      if constexpr (P::CONS) ff = fma(ev[m], FBs[d * NL + jj * NV + v], ff);
+    }
+    double* rec = fc + (d * 2 + side) * FR;
+    rec[jp * NV + v] = qf;
+    if constexpr (P::CONS) rec[NF * NV + jp * NV + v] = ff;
+  }
+}
+
+// Index helpers for faces.  In direction d the faces of one grid line are numbered k = 0..n_d
+// (face k is the lower face of cell k); the grid line is the cell index with digit d removed.
+struct FaceIdx {
+  __device__ static long long trans_of_cell(const Geometry& g, long long c, int d, int& id) {
+    const int i0 = (int)(c % g.n[0]);
+    const long long r = c / g.n[0];
+    const int i1 = (int)(r % g.n[1]);
+    const int i2 = (int)(r / g.n[1]);
+    if (d == 0) { id = i0; return i1 + (long long)g.n[1] * i2; }
+    if (d == 1) { id = i1; return i0 + (long long)g.n[0] * i2; }
+    id = i2;
+    return i0 + (long long)g.n[0] * i1;
+  }
+  __device__ static long long cell_of(const Geometry& g, long long tr, int d, int id) {
+    if (d == 0) return id + (long long)g.n[0] * tr;
+    if (d == 1) {
+      const long long i0 = tr % g.n[0], i2 = tr / g.n[0];
+      return i0 + (long long)g.n[0] * (id + (long long)g.n[1] * i2);
+    }
+    const long long i0 = tr % g.n[0], i1 = tr / g.n[0];
+    return i0 + (long long)g.n[0] * (i1 + (long long)g.n[1] * id);
+  }
+  __device__ static long long ntrans(const Geometry& g, int d) {
+    return g.ncells / g.n[d];
+  }
+};
+
+// Ghost state at a non-periodic boundary from the interior face record values.
+template <class P>
+__device__ __forceinline__ void ghost(int kind, int d, double* q, double* F) {
+  if (kind == 1) {  // wall
+    P::mirror(q, d);
+    if constexpr (P::CONS) P::mirror_flux(F, d);
+  } else {          // absorbing
+    if constexpr (P::LINEAR) {
+#pragma unroll
+      for (int v = 0; v < P::NV; ++v) {
+        q[v] = 0.0;
+        if constexpr (P::CONS) F[v] = 0.0;
+      }
+    }
+  }
+}
+
+// Rusanov flux with one wave speed per face (max over face nodes and both sides) and the halved
+// path-conservative fluctuation:  Phi_L = G + Bbar dq / 2,  Phi_R = G - Bbar dq / 2.
+// One warp per face; faces of direction d, offset `phi_off` in the flux buffer.
+template <class P, int D, int N>
+__global__ void __launch_bounds__(128) k_riemann(const __grid_constant__ StepArgs A,
+                                                 const __grid_constant__ Tables T, int d,
+                                                 long long phi_off) {
+  using C = Cfg<P, D, N>;
+  constexpr int NV = C::NV, NF = C::NF, FR = C::FR, NPHI = C::NPHI;
+  constexpr int PER = (NF + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  const long long f = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
+  const Geometry& g = A.g;
+  const int nd = g.n[d];
+  const long long nfaces = (long long)(nd + 1) * FaceIdx::ntrans(g, d);
+  if (f >= nfaces) return;
+  const int kf = (int)(f % (nd + 1));
+  const long long tr = f / (nd + 1);
+  const bool periodic = (g.bc[d][0] == BC_PERIODIC);
+  if (periodic && kf == nd) return;  // duplicate of face 0
+  long long cL = -1, cR = -1;
+  if (kf > 0) cL = FaceIdx::cell_of(g, tr, d, kf - 1);
+  else if (periodic) cL = FaceIdx::cell_of(g, tr, d, nd - 1);
+  if (kf < nd) cR = FaceIdx::cell_of(g, tr, d, kf);
+  else if (periodic) cR = FaceIdx::cell_of(g, tr, d, 0);
+  const double* recL = cL >= 0 ? A.face + cL * (long long)(D * 2 * FR) + (d * 2 + 1) * FR : nullptr;
+  const double* recR = cR >= 0 ? A.face + cR * (long long)(D * 2 * FR) + (d * 2 + 0) * FR : nullptr;
+
+  double qL[PER][NV], qR[PER][NV], FL[PER][NV], FR_[PER][NV];
+  double smax = 0.0;
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int jp = lane + 32 * r;
+    if (jp < NF) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const double* a = recL ? recL : recR;
+        const double* b = recR ? recR : recL;
+        qL[r][v] = a[jp * NV + v];
+        qR[r][v] = b[jp * NV + v];
+        FL[r][v] = P::CONS ? a[NF * NV + jp * NV + v] : 0.0;
+        FR_[r][v] = P::CONS ? b[NF * NV + jp * NV + v] : 0.0;
+      }
+      if (!recL) ghost<P>(g.bc[d][0], d, qL[r], FL[r]);
+      if (!recR) ghost<P>(g.bc[d][1], d, qR[r], FR_[r]);
+      if constexpr (P::CONS && !P::LINEAR) {
+        smax = fmax(smax, fmax(P::speed(qL[r], A.p, d), P::speed(qR[r], A.p, d)));
+      }
+    }
+  }
+  double s;
+  double cb[NV];
+  if constexpr (P::NCP) {
+    const long long mcL = cL >= 0 ? cL : cR, mcR = cR >= 0 ? cR : cL;
+    const double rL = A.mat[mcL * 3], lL = A.mat[mcL * 3 + 1], uL = A.mat[mcL * 3 + 2];
+    const double rR = A.mat[mcR * 3], lR = A.mat[mcR * 3 + 1], uR = A.mat[mcR * 3 + 2];
+    const double sL = Elastic::vp(rL, lL, uL), sR = Elastic::vp(rR, lR, uR);
+    s = (sL >= sR) ? sL : sR;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double acc = 0.0;
+#pragma unroll
+      for (int gq = 0; gq < 3; ++gq) {
+        const double z = T.pz[gq];
+        acc = fma(T.pw[gq],
+                  Elastic::coef(d, v, fma(z, rR - rL, rL), fma(z, lR - lL, lL), fma(z, uR - uL, uL)),
+                  acc);
+      }
+      cb[v] = acc;
+    }
+  } else if constexpr (P::LINEAR) {
+    s = fabs(A.p.a[d]);
+  } else {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    s = smax;
+  }
+  double* out = A.phi + phi_off + f * (long long)(NPHI * NF * NV);
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int jp = lane + 32 * r;
+    if (jp < NF) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const double G = 0.5 * (FL[r][v] + FR_[r][v]) - 0.5 * s * (qR[r][v] - qL[r][v]);
+        if constexpr (P::NCP) {
+          const int sv = Elastic::src(d, v);
+          const double half = sv >= 0 ? 0.5 * cb[v] * (qR[r][sv] - qL[r][sv]) : 0.0;
+          out[jp * NV + v] = G + half;
+          out[NF * NV + jp * NV + v] = G - half;
+        } else {
+          out[jp * NV + v] = G;
+        }
+      }
+    }
+  }
+}
+
+// Corrector, face part of Eq. (6) in strong form:
+//   u_j -= dt sum_d (1/h_d) [ e1_{j_d}/w_{j_d} Phi_L(right face) - e0_{j_d}/w_{j_d} Phi_R(left face) ]
+template <class P, int D, int N>
+__global__ void __launch_bounds__(256) k_corrector(const __grid_constant__ StepArgs A,
+                                                   const __grid_constant__ Tables T,
+                                                   long long off1, long long off2) {
+  using C = Cfg<P, D, N>;
+  constexpr int n = C::n, NV = C::NV, NL = C::NL, NF = C::NF, NPHI = C::NPHI;
+  const long long e = (long long)blockIdx.x * 256 + threadIdx.x;
+  if (e >= A.g.ncells * NL) return;
+  const long long c = e / NL;
+  const int l = (int)(e - c * NL);
+  const int j = l / NV, v = l - (l / NV) * NV;
+  const double dt = A.dev->dt;
+  double acc = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int st = (d == 0 ? 1 : (d == 1 ? n : n * n));
+    const int jd = (j / st) % n;
+    const int jp = (j % st) + (j / (st * n)) * st;
+    int id;
+    const long long tr = FaceIdx::trans_of_cell(A.g, c, d, id);
+    const int nd = A.g.n[d];
+    int kr = id + 1;
+    if (kr == nd && A.g.bc[d][1] == BC_PERIODIC) kr = 0;
+    const long long off = d == 0 ? 0 : (d == 1 ? off1 : off2);
+    const long long fr = kr + (long long)(nd + 1) * tr;
+    const long long fl = id + (long long)(nd + 1) * tr;
+    const double PhiL = A.phi[off + fr * (NPHI * NF * NV) + jp * NV + v];
+    const double PhiR = A.phi[off + fl * (NPHI * NF * NV) + (NPHI - 1) * NF * NV + jp * NV + v];
+    acc += A.g.inv_h[d] * (T.c1[jd] * PhiL - T.c0[jd] * PhiR);
+  }
+  A.u_next[e] = fma(-dt, acc, A.u_next[e]);
+}
+
+// Max signal speed of the state (Eq. (7)); NaN / Inf latches ST_NONFINITE.
+template <class P, int D, int N>
+__global__ void __launch_bounds__(256) k_cfl(const __grid_constant__ StepArgs A) {
+  using C = Cfg<P, D, N>;
+  constexpr int NS = C::NS, NV = C::NV;
+  double lmax = 0.0;
+  bool bad = false;
+  const long long total = P::NCP ? A.g.ncells : A.g.ncells * NS;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    double s;
+    if constexpr (P::NCP) {
+      s = Elastic::vp(A.mat[i * 3], A.mat[i * 3 + 1], A.mat[i * 3 + 2]);
+      // the state itself only needs a finiteness check
+    } else {
+      const double* q = A.u + i * NV;
+      s = 0.0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) s = fmax(s, P::speed(q, A.p, d));
+      double sum = 0.0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sum += q[v];
+      if (!isfinite(sum)) bad = true;
+    }
+    if (!(s >= 0.0) || isinf(s)) bad = true;
+    else lmax = fmax(lmax, s);
+  }
+  if constexpr (P::NCP) {
+    const long long tot2 = A.g.ncells * NS * NV;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < tot2;
+         i += (long long)gridDim.x * blockDim.x)
+      if (!isfinite(A.u[i])) bad = true;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+  bad = __any_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&A.dev->lam_bits, (unsigned long long)__double_as_longlong(lmax));
+    if (bad) atomicOr(&A.dev->status, ST_NONFINITE);
+  }
+}
+
+// ---- launchers ----------------------------------------------------------------------------
+template <class P, int D, int N>
+cudaError_t launch_predictor_n(const StepArgs& a, const Tables& t, cudaStream_t s) {
+  using C = Cfg<P, D, N>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_predictor<P, D, N>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (a.g.ncells > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_predictor<P, D, N><<<(unsigned)a.g.ncells, C::TPB, C::SMEM, s>>>(a, t);
+  return cudaGetLastError();
+}
+
+template <class P, int D, int N>
+cudaError_t launch_riemann_n(const StepArgs& a, const Tables& t, cudaStream_t s) {
+  using C = Cfg<P, D, N>;
+  long long off = 0;
+  for (int d = 0; d < D; ++d) {
+    const long long nf = (long long)(a.g.n[d] + 1) * (a.g.ncells / a.g.n[d]);
+    const long long blocks = (nf + 3) / 4;
+    k_riemann<P, D, N><<<(unsigned)blocks, 128, 0, s>>>(a, t, d, off);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    off += nf * (long long)(C::NPHI * C::NF * C::NV);
+  }
+  return cudaSuccess;
+}
+
+template <class P, int D, int N>
+cudaError_t launch_corrector_n(const StepArgs& a, const Tables& t, cudaStream_t s) {
+  using C = Cfg<P, D, N>;
+  long long offs[3] = {0, 0, 0};
+  long long off = 0;
+  for (int d = 0; d < D; ++d) {
+    offs[d] = off;
+    off += (long long)(a.g.n[d] + 1) * (a.g.ncells / a.g.n[d]) * (C::NPHI * C::NF * C::NV);
+  }
+  const long long tot = a.g.ncells * C::NL;
+  k_corrector<P, D, N><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a, t, offs[1], offs[2]);
+  return cudaGetLastError();
+}
+
+template <class P, int D, int N>
+cudaError_t launch_cfl_n(const StepArgs& a, cudaStream_t s) {
+  k_cfl<P, D, N><<<152 * 8, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+#define ADER_DISPATCH_N(FN, ...)                      \
+  switch (a.g.order) {                                \
+    case 1: return FN<P, D, 1>(__VA_ARGS__);          \
+    case 2: return FN<P, D, 2>(__VA_ARGS__);          \
+    case 3: return FN<P, D, 3>(__VA_ARGS__);          \
+    case 4: return FN<P, D, 4>(__VA_ARGS__);          \
+    case 5: return FN<P, D, 5>(__VA_ARGS__);          \
+    case 6: return FN<P, D, 6>(__VA_ARGS__);          \
+    default: return cudaErrorInvalidValue;            \
+  }
+
+template <class P, int D>
+struct FamilyImpl {
+  static cudaError_t cfl(const StepArgs& a, cudaStream_t s) { ADER_DISPATCH_N(launch_cfl_n, a, s) }
+  static cudaError_t predictor(const StepArgs& a, const Tables& t, int prec, cudaStream_t s);
+  static cudaError_t riemann(const StepArgs& a, const Tables& t, cudaStream_t s) {
+    ADER_DISPATCH_N(launch_riemann_n, a, t, s)
+  }
+  static cudaError_t corrector(const StepArgs& a, const Tables& t, cudaStream_t s) {
+    ADER_DISPATCH_N(launch_corrector_n, a, t, s)
+  }
+  static size_t smem(int order, int prec) {
+    switch (order) {
+      case 1: return Cfg<P, D, 1>::SMEM;
+      case 2: return Cfg<P, D, 2>::SMEM;
+      case 3: return Cfg<P, D, 3>::SMEM;
+      case 4: return Cfg<P, D, 4>::SMEM;
+      case 5: return Cfg<P, D, 5>::SMEM;
+      case 6: return Cfg<P, D, 6>::SMEM;
+    }
+    return 0;
+  }
+  static const Family* get() {
+    static const Family f = {P::NV, P::CONS, &cfl, &predictor, &riemann, &corrector, &smem};
+    return &f;
+  }
+};
+
+template <class P, int D>
+cudaError_t FamilyImpl<P, D>::predictor(const StepArgs& a, const Tables& t, int prec,
+                                        cudaStream_t s) {
+  (void)prec;
+  ADER_DISPATCH_N(launch_predictor_n, a, t, s)
+}
+
+}  // namespace ader

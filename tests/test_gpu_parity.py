@@ -1,0 +1,206 @@
+"""GPU parity of the FP64 CUDA path against the CPU oracle (same seeded inputs, element by
+element).  Tolerance: relative L-infinity <= 1e-12 per variable (scaled by max|u_var|)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1905_07987_gb300 import ader, synth
+from cases import Case, rel_linf
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _build():
+    from paper_1905_07987_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def euler_data(c, kind="wave", seed=0):
+    if kind == "wave":
+        return synth.entropy_wave(c.X)
+    rng = np.random.default_rng(seed)
+    X = c.X
+    D = c.dim
+    bump = np.exp(-6 * sum((x - 0.5 * (lo + hi)) ** 2 for x, lo, hi in zip(X, c.lo, c.hi)))
+    rho = 1.0 + 0.4 * bump + 0.02 * rng.standard_normal(X[0].shape)
+    vel = [0.3 * np.sin(2 * math.pi * X[(d + 1) % D]) + 0.1 * d for d in range(D)]
+    p = 1.0 + 0.5 * bump
+    return synth.euler_conserved(rho, vel, p)
+
+
+@pytest.mark.parametrize("dim,order,ncell", [(2, 3, (7, 5)), (2, 1, (3, 4)), (3, 4, (5, 4, 3)),
+                                             (3, 2, (3, 3, 4)), (3, 3, (4, 3, 2))])
+def test_euler_periodic_step(dim, order, ncell):
+    c = Case("euler", dim, order, ncell)
+    u0 = euler_data(c, "random", seed=order)
+    c.set(u0)
+    c.ctx.step()
+    dt = c.ctx.last_dt()
+    ref_dt = float(c.oracle.cfl_dt(torch.from_numpy(u0)))
+    assert abs(dt - ref_dt) <= 1e-14 * ref_dt
+    assert rel_linf(c.get(), c.oracle_step(u0, dt)) <= TOL
+
+
+@pytest.mark.parametrize("bc", ["wall", "absorbing"])
+def test_euler_boundaries(bc):
+    c = Case("euler", 3, 3, (4, 3, 5), lo=(-1, -1, -1), hi=(1, 1, 1), bc=bc)
+    u0 = euler_data(c, "random", seed=3)
+    c.set(u0)
+    c.ctx.step()
+    dt = c.ctx.last_dt()
+    assert rel_linf(c.get(), c.oracle_step(u0, dt)) <= TOL
+
+
+def test_euler_2d_mixed_boundaries():
+    bc = [("wall", "absorbing"), ("periodic", "periodic")]
+    c = Case("euler", 2, 3, (6, 5), bc=bc)
+    u0 = euler_data(c, "random", seed=5)
+    c.set(u0)
+    c.ctx.step()
+    assert rel_linf(c.get(), c.oracle_step(u0, c.ctx.last_dt())) <= TOL
+
+
+@pytest.mark.parametrize("order", range(1, 7))
+def test_advection_all_orders(order):
+    for dim, nc in ((2, (3, 4)), (3, (3, 2, 2))):
+        c = Case("advection", dim, order, nc, bc="absorbing" if order % 2 else "periodic")
+        rng = np.random.default_rng(order)
+        u0 = rng.standard_normal(c.shape)
+        c.set(u0)
+        c.ctx.step()
+        assert rel_linf(c.get(), c.oracle_step(u0, c.ctx.last_dt())) <= TOL
+
+
+@pytest.mark.parametrize("order", [2, 3, 4, 5])
+def test_elastic_step_with_source(order):
+    ncell = (3, 4, 3)
+    mat = synth.elastic_material(ncell, seed=order)
+    c = Case("elastic", 3, order, ncell, hi=(1.5, 2.0, 1.5), bc="absorbing", material=mat)
+    rng = np.random.default_rng(order)
+    u0 = rng.standard_normal(c.shape)
+    M = synth.moment_tensor(seed=7)
+    c.point_source((0.75, 1.0, 0.75), M, 2.0, 0.5)
+    c.set(u0)
+    c.ctx.set_time(0.37)
+    c.ctx.step()
+    dt = c.ctx.last_dt()
+    assert rel_linf(c.get(), c.oracle_step(u0, dt, 0.37)) <= TOL
+
+
+def test_elastic_periodic_multistep_and_receivers():
+    ncell = (4, 3, 3)
+    mat = synth.elastic_material(ncell, seed=11)
+    c = Case("elastic", 3, 3, ncell, hi=(2.0, 1.5, 1.5), bc="periodic", material=mat)
+    u0 = synth.plane_wave_elastic(c.X, [2.7, 30.0, 25.0], L=2.0)
+    pts = synth.receivers_top(ncell, c.lo, c.hi, nside=3)
+    seismo = c.receivers(pts, 8)
+    c.set(u0)
+    u = torch.from_numpy(u0)
+    t = 0.0
+    rec = []
+    for k in range(5):
+        dt = float(c.oracle.cfl_dt(u))
+        u = c.oracle.step(u, torch.tensor(dt, dtype=torch.float64), t)
+        t += dt
+        rec.append(c.oracle.record(u).numpy())
+    c.ctx.run(5)
+    assert rel_linf(c.get(), u.numpy()) <= 10 * TOL
+    got = seismo[:5].cpu().numpy()
+    ref = np.stack(rec)
+    assert np.abs(got - ref).max() <= 10 * TOL * np.abs(ref).max()
+    assert abs(c.ctx.time() - t) <= 1e-13 * t
+
+
+def test_euler_free_running_matches_oracle_over_many_steps():
+    c = Case("euler", 2, 3, (9, 8))
+    u0 = synth.entropy_wave(c.X)
+    c.set(u0)
+    u, t = c.oracle.run(torch.from_numpy(u0), 20)
+    c.ctx.run(20)
+    assert rel_linf(c.get(), u.numpy()) <= 20 * TOL
+    assert abs(c.ctx.time() - t) <= 1e-13 * t
+
+
+def test_t_end_clipping_and_fixed_dt():
+    c = Case("euler", 2, 2, (5, 5))
+    u0 = synth.entropy_wave(c.X)
+    c.set(u0)
+    c.ctx.step(dt=0.004)
+    assert c.ctx.last_dt() == 0.004
+    assert rel_linf(c.get(), c.oracle_step(u0, 0.004)) <= TOL
+    c.ctx.set_time(0.0)
+    c.set(u0)
+    c.ctx.run(3, t_end=0.01)
+    assert abs(c.ctx.time() - 0.01) < 1e-16
+    u, t = c.oracle.run(torch.from_numpy(u0), None, t_end=0.01)
+    assert rel_linf(c.get(), u.numpy()) <= 10 * TOL
+    # a further step at t = t_end leaves the state unchanged
+    before = c.get()
+    c.ctx.step(t_end=0.01)
+    assert c.ctx.last_dt() == 0.0
+    assert np.array_equal(c.get(), before)
+
+
+def test_graph_replay_equals_step_loop():
+    c1 = Case("euler", 3, 3, (4, 4, 3))
+    c2 = Case("euler", 3, 3, (4, 4, 3))
+    u0 = synth.entropy_wave(c1.X)
+    c1.set(u0)
+    c2.set(u0)
+    c1.ctx.run(6)
+    c2.ctx.run_graph(2, 3)
+    c2.ctx.sync()
+    assert np.array_equal(c1.get(), c2.get())
+
+
+def test_errors_are_reported():
+    c = Case("euler", 2, 2, (3, 3))
+    with pytest.raises(ader.AderError) as e:
+        c.ctx.step()
+    assert e.value.status == ader.ESTATE
+    with pytest.raises(ader.AderError):
+        c.ctx.set_state(torch.zeros(5, dtype=torch.float64, device="cuda"))
+    u0 = synth.entropy_wave(c.X)
+    u0[4, 1, 2, 0] = np.nan
+    c.set(u0)
+    c.ctx.step()
+    with pytest.raises(ader.AderError) as e:
+        c.ctx.sync()
+    assert e.value.status == ader.ENONFINITE
+    c.set(synth.entropy_wave(c.X))
+    c.ctx.step()
+    c.ctx.sync()  # status was cleared
+
+
+def test_full_size_sampled_cells_euler_81():
+    """Full-size entropy wave (81^3 cells, p=4) in the launch configuration the benchmark times;
+    sampled cells checked against the oracle on their 3x3x3 neighbourhood (the update of a cell
+    depends only on itself and its face neighbours)."""
+    nc = (81, 81, 81)
+    c = Case("euler", 3, 4, nc)
+    u0 = synth.entropy_wave(c.X)
+    c.set(u0)
+    c.ctx.step()
+    dt = c.ctx.last_dt()
+    got = c.get()
+    from oracle.aderdg import ADERDG, Grid
+    from oracle.pde import Euler
+    sub = ADERDG(Euler(3), Grid((3, 3, 3), (0, 0, 0), (3 / 81,) * 3, [("periodic", "periodic")] * 3), 4,
+                 cfl=c.cfl)
+    rng = np.random.default_rng(0)
+    samples = [(0, 0, 0), (80, 80, 80), (40, 7, 63)] + [tuple(rng.integers(0, 81, 3)) for _ in range(5)]
+    for (i, j, k) in samples:
+        idx = []
+        for dk in (-1, 0, 1):
+            for dj in (-1, 0, 1):
+                for di in (-1, 0, 1):
+                    idx.append(((i + di) % 81) + 81 * (((j + dj) % 81) + 81 * ((k + dk) % 81)))
+        loc = u0[idx]
+        out = sub.step(torch.from_numpy(loc), torch.tensor(dt, dtype=torch.float64)).numpy()
+        centre = i + 81 * (j + 81 * k)
+        assert rel_linf(got[centre], out[13]) <= TOL, (i, j, k)

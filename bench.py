@@ -1,0 +1,277 @@
+"""Benchmark: ADER-DG DOF-updates/s of the GB300 library on the 3-D Euler entropy-wave workload
+(81^3 cells, order 4, 5 variables: 332 M degrees of freedom), one JSON line on stdout.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--prec fp64]
+
+A step is one ADER-DG time step of the whole grid (CFL reduction, predictor, Riemann solver,
+corrector).  ``value`` is device-timed with CUDA events on the library's stream, the state
+resident in HBM; ``e2e`` is the same metric through the C ABI with host buffers (host-to-device
+copy of the state, the step, device-to-host copy of the new state, every step).  For N > 1 each
+rank advances its own replica (the method needs no exchange between independent grids);
+``value`` sums all ranks.  ``--impl reference`` times the CPU oracle on a bounded sample of the
+same workload on this machine's cores.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "euler3d_p4_81": dict(pde="euler", dim=3, order=4, ncell=(81, 81, 81), lo=(0.0,) * 3,
+                          hi=(1.0,) * 3, bc="periodic"),
+    # smaller grid of the same scheme, used for single-kernel profiles (state 0.32 GB > L2)
+    "euler3d_p4_40": dict(pde="euler", dim=3, order=4, ncell=(40, 40, 40), lo=(0.0,) * 3,
+                          hi=(1.0,) * 3, bc="periodic"),
+    "euler2d_p3_27": dict(pde="euler", dim=2, order=3, ncell=(27, 27), lo=(0.0,) * 2,
+                          hi=(1.0,) * 2, bc="periodic"),
+}
+FP64_SMS, FP64_FMA_PER_CLK, SM_MAX_MHZ = 152, 2, 2070.0
+FP64_PEAK = FP64_SMS * FP64_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6  # FLOP/s
+
+
+def predictor_flops_per_cell(pde, D, N, iters):
+    """Algorithmic FP64 flops of the fused predictor kernel for one cell (FMA = 2 flops,
+    add / multiply / divide = 1), as counted in the design doc."""
+    n = N + 1
+    NST = n ** (D + 1)
+    NV = D + 2
+    NL = n ** D * NV
+    NF = n ** (D - 1)
+    cF = (2 * D + 5) + D * (D + 4)           # aux (1/rho, p) + D flux vectors per node
+    it = cF * NST + D * NST * NV * (2 * n + 2) + NL * n * (2 * n + 2)
+    epi = (cF * NST + (D + 1) * NL * 2 * n + D * NL * (6 * n + 5) + 2 * NL
+           + 2 * D * NF * NV * 2 * n * 2)
+    return iters * it + epi
+
+
+def sample_clocks(stop_after_s):
+    """nvidia-smi clock / throttle samples every 200 ms (started before the timed region)."""
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                text=True)
+    except OSError:
+        return None
+
+
+def parse_clocks(proc, gpu_index):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        out, _ = proc.communicate()
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.strip().splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            if int(f[0]) != gpu_index:
+                continue
+            sm.append(float(f[1]))
+            smax.append(float(f[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def build_initial(ader, synth, wl):
+    x, _ = ader.reference_nodes(wl["order"])
+    X = synth.node_coordinates(x, wl["ncell"], wl["lo"], wl["hi"])
+    u = synth.entropy_wave(X)
+    return u.reshape(-1)
+
+
+def oracle_sample(wl, budget_s):
+    """Time the CPU oracle on a bounded sample of the workload: a 6^3 (2-D: 12^2) periodic
+    block of cells of the same size and order; returns (DOF-updates/s, description, threads)."""
+    import torch
+
+    from oracle.aderdg import ADERDG, Grid
+    from oracle.pde import Euler
+    from paper_1905_07987_gb300 import synth
+    D, N = wl["dim"], wl["order"]
+    m = 6 if D == 3 else 12
+    h = (wl["hi"][0] - wl["lo"][0]) / wl["ncell"][0]
+    g = Grid((m,) * D, (0.0,) * D, (m * h,) * D, [("periodic", "periodic")] * D)
+    s = ADERDG(Euler(D), g, N, cfl=synth.cfl_number(N))
+    X = s.node_coords()
+    u = torch.from_numpy(synth.entropy_wave([x.numpy() for x in X]))
+    s.step(u, s.cfl_dt(u))  # warm-up
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        u = s.step(u, s.cfl_dt(u))
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or steps >= 100000:
+            break
+    dofs = g.C * (N + 1) ** D * (D + 2)
+    desc = "%d^%d periodic cells of the same h and order, %d oracle steps in %.1f s" % (m, D, steps, el)
+    return dofs * steps / el, desc, torch.get_num_threads(), el / steps
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="euler3d_p4_81", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="fp64", choices=["fp64"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    D, N = wl["dim"], wl["order"]
+    cells = int(np.prod(wl["ncell"]))
+    dofs = cells * (N + 1) ** D * (D + 2)
+    metric = "ADER-DG DOF-updates/s on 1 GB300 (FP64 vs mixed @ stated err); % roofline"
+    config = {"workload": args.workload, "pde": wl["pde"], "dim": D, "order": N,
+              "cells": list(wl["ncell"]), "dofs": dofs, "init": "entropy wave (analytic)",
+              "l2": "inputs larger than L2 (state %.2f GB)" % (dofs * 8 / 1e9),
+              "precision": args.prec}
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        v, desc, cores, per_step = oracle_sample(wl, min(args.cpu_budget, 20.0))
+        line = {"impl": "reference", "metric": metric, "value": v, "unit": "DOF-updates/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": dofs / v * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": v, "unit": "DOF-updates/s", "cores": cores,
+                                 "kind": "oracle", "sample": desc},
+                "e2e": {"value": v, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    from paper_1905_07987_gb300 import ader, synth
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    cfg = ader.make_config(wl["pde"], D, N, wl["ncell"], wl["lo"], wl["hi"], wl["bc"],
+                           synth.cfl_number(N), precision=args.prec)
+    ctx = ader.Context(cfg, stream=stream.cuda_stream)
+    u0 = build_initial(ader, synth, wl)
+    u0_dev = torch.from_numpy(u0).to("cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ctx.set_state(u0_dev)
+        for _ in range(args.warmup):
+            ctx.step()
+    ctx.sync()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- device-timed region ---------------------------------------------------------------
+    clk = sample_clocks(0)
+    time.sleep(0.3)
+    ctx.enable_timing(True)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_total = e0.elapsed_time(e1)
+    clocks = parse_clocks(clk, dev)
+    phases, nrec = ctx.phase_times()
+    ctx.enable_timing(False)
+    ctx.sync()
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * dofs * args.steps / (ms_total * 1e-3)
+
+    # ---- end-to-end through the C ABI with host buffers --------------------------------------
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(u0).pin_memory()
+        h_out = torch.empty(dofs, dtype=torch.float64).pin_memory()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.set_state(h_in)
+            ctx.step()
+            ctx.get_state(h_out)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * dofs * args.steps / el, "unit": "DOF-updates/s",
+               "h2d_bytes_per_step": dofs * 8, "d2h_bytes_per_step": dofs * 8}
+
+    # ---- roofline of the dominant kernel (the predictor) -------------------------------------
+    pred_ms = phases["predictor"] / max(nrec, 1)
+    flops = predictor_flops_per_cell(wl["pde"], D, N, N + 1) * cells
+    achieved = flops / (pred_ms * 1e-3) / 1e12
+    peak = FP64_PEAK / 1e12
+    roof = {"bound": "alu", "kernel": "k_predictor (FP64)", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+            "flops_per_cell": flops / cells, "ms_per_launch": pred_ms,
+            "phase_ms_per_step": {k: v / max(nrec, 1) for k, v in phases.items()}}
+    launches_per_step = 1 + 1 + 1 + D + 1 + 1
+    line = {"metric": metric, "value": value, "unit": "DOF-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config, "roofline": roof, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
+    if world == 1 and rank == 0:
+        v, desc, cores, _ = oracle_sample(wl, args.cpu_budget)
+        line["cpu_baseline"] = {"value": v, "unit": "DOF-updates/s", "cores": cores,
+                                "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

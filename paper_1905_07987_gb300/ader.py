@@ -111,18 +111,20 @@ def reference_nodes(order):
     return x, w
 
 
-def _ptr(a):
-    """(pointer, on_device, keepalive) of a numpy array or torch tensor (contiguous float64)."""
+def _ptr(a, dtype=np.float64):
+    """(pointer, on_device, keepalive, element count) of a numpy array or torch tensor."""
     try:
         import torch
         if isinstance(a, torch.Tensor):
             if not a.is_contiguous():
                 raise ValueError("tensor must be contiguous")
-            return a.data_ptr(), 1 if a.is_cuda else 0, a
+            if a.dtype != {np.float64: torch.float64, np.uint8: torch.uint8}[dtype]:
+                raise ValueError("tensor must be %s" % np.dtype(dtype).name)
+            return a.data_ptr(), 1 if a.is_cuda else 0, a, a.numel()
     except ImportError:  # pragma: no cover
         pass
-    arr = np.ascontiguousarray(a)
-    return arr.ctypes.data, 0, arr
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data, 0, arr, arr.size
 
 
 def make_config(pde, dim, order, ncell, lo, hi, bc, cfl, gamma=1.4, adv=(0.0, 0.0, 0.0),
@@ -184,18 +186,22 @@ class Context:
             pass
 
     def set_state(self, q):
-        p, dev, keep = _ptr(q)
-        check(lib().ader_set_state(self._h, p, self.count, dev), "ader_set_state")
+        p, dev, keep, n = _ptr(q)
+        check(lib().ader_set_state(self._h, p, n, dev), "ader_set_state")
 
     def get_state(self, out=None):
         if out is None:
             out = np.empty(self.count)
-        p, dev, keep = _ptr(out)
-        check(lib().ader_get_state(self._h, p, self.count, dev), "ader_get_state")
+        p, dev, keep, n = _ptr(out)
+        if isinstance(out, np.ndarray) and keep is not out:
+            raise ValueError("output array must be contiguous float64")
+        check(lib().ader_get_state(self._h, p, n, dev), "ader_get_state")
         return out
 
     def set_material(self, mat):
-        p, dev, keep = _ptr(mat)
+        p, dev, keep, n = _ptr(mat)
+        if n != 3 * self.cells:
+            raise ValueError("material must hold 3 values per cell")
         check(lib().ader_set_material(self._h, p, dev), "ader_set_material")
 
     def set_point_source(self, x0, M, f0, t0):
@@ -206,9 +212,11 @@ class Context:
 
     def set_receivers(self, xyz, seismo, max_steps):
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
-        p, dev, keep = _ptr(seismo)
+        p, dev, keep, n = _ptr(seismo)
         if not dev:
             raise ValueError("seismogram buffer must be device memory")
+        if n < int(max_steps) * len(xyz) * 3:
+            raise ValueError("seismogram buffer smaller than max_steps x nrec x 3")
         self._seismo = seismo
         check(lib().ader_set_receivers(self._h, len(xyz), xyz.ctypes.data, p, int(max_steps)),
               "ader_set_receivers")

@@ -132,6 +132,105 @@ def oracle_sample(wl, budget_s):
     return dofs * steps / el, desc, torch.get_num_threads(), el / steps
 
 
+FP32_PEAK = FP64_SMS * 128 * 2 * SM_MAX_MHZ * 1e6  # FLOP/s
+
+
+def density_error(ctx, wl, t, nodes, weights):
+    """(L2, Linf) error of the density against the exact entropy wave at time t, evaluated at the
+    Gauss-Legendre nodes (L2 with the nodal quadrature) on the GPU with plain torch ops."""
+    import torch
+    D, N = wl["dim"], wl["order"]
+    n = N + 1
+    st = torch.empty(ctx.count, dtype=torch.float64, device="cuda")
+    ctx.get_state(st)
+    torch.cuda.synchronize()
+    rho = st.view(ctx.cells, n ** D, D + 2)[:, :, 0]
+    nc = wl["ncell"]
+    lo, hi = wl["lo"], wl["hi"]
+    c = torch.arange(ctx.cells, device="cuda")
+    xi = torch.tensor(nodes, device="cuda", dtype=torch.float64)
+    w = torch.tensor(weights, device="cuda", dtype=torch.float64)
+    j = torch.arange(n ** D, device="cuda")
+    s = torch.zeros(ctx.cells, n ** D, dtype=torch.float64, device="cuda")
+    W = torch.ones(n ** D, dtype=torch.float64, device="cuda")
+    rem_c, rem_j = c, j
+    vol = 1.0
+    for d in range(D):
+        h = (hi[d] - lo[d]) / nc[d]
+        vol *= h
+        ic = rem_c % nc[d]
+        rem_c = rem_c // nc[d]
+        a = rem_j % n
+        rem_j = rem_j // n
+        s = s + (lo[d] + h * (ic[:, None].double() + xi[a][None, :]))
+        W = W * w[a]
+    ex = 1.0 + 0.2 * torch.sin(2 * math.pi * (s - D * t))
+    err = rho - ex
+    l2 = math.sqrt(float((err * err * W[None, :]).sum()) * vol)
+    return l2, float(err.abs().max())
+
+
+def run_form(ader, synth, wl, prec, args, stream, u0_dev, err_steps):
+    """Warm up, time K steps with CUDA events (plus per-phase events), then run untimed to
+    err_steps steps in total and measure the density error against the exact solution."""
+    import torch
+    D, N = wl["dim"], wl["order"]
+    cfg = ader.make_config(wl["pde"], D, N, wl["ncell"], wl["lo"], wl["hi"], wl["bc"],
+                           synth.cfl_number(N), precision=prec)
+    ctx = ader.Context(cfg, stream=stream.cuda_stream)
+    ctx.set_state(u0_dev)
+    ctx.set_time(0.0)
+    for _ in range(args.warmup):
+        ctx.step()
+    ctx.sync()
+    clk = sample_clocks(0)
+    time.sleep(0.3)
+    ctx.enable_timing(True)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_total = e0.elapsed_time(e1)
+    clocks = parse_clocks(clk, torch.cuda.current_device())
+    phases, nrec = ctx.phase_times()
+    ctx.enable_timing(False)
+    ctx.sync()
+    done = args.warmup + args.steps
+    err = None
+    if err_steps and err_steps > done:
+        ctx.run(err_steps - done)
+    if err_steps:
+        x, w = ader.reference_nodes(N)
+        t = ctx.time()
+        l2, linf = density_error(ctx, wl, t, x, w)
+        err = {"steps": max(done, err_steps), "t": t, "l2_rho": l2, "linf_rho": linf}
+    return ctx, ms_total, phases, nrec, clocks, err
+
+
+_WORLD = [1]
+
+
+def barrier():
+    if _WORLD[0] > 1:
+        import torch
+        torch.distributed.barrier()
+
+
+def max_over_ranks(x):
+    if _WORLD[0] > 1:
+        import torch
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+    return x
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -139,7 +238,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="euler3d_p4_81", choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default="fp64", choices=["fp64"])
+    ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed"],
+                    help="form reported as the headline value")
+    ap.add_argument("--forms", default="fp64,mixed", help="forms to time (comma list)")
+    ap.add_argument("--err-steps", type=int, default=50,
+                    help="steps after which the error against the exact solution is measured")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -150,12 +253,14 @@ def main():
     metric = "ADER-DG DOF-updates/s on 1 GB300 (FP64 vs mixed @ stated err); % roofline"
     config = {"workload": args.workload, "pde": wl["pde"], "dim": D, "order": N,
               "cells": list(wl["ncell"]), "dofs": dofs, "init": "entropy wave (analytic)",
+              "cfl": "0.9 x order-%d stability limit" % N,
               "l2": "inputs larger than L2 (state %.2f GB)" % (dofs * 8 / 1e9),
               "precision": args.prec}
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    _WORLD[0] = world
 
     if args.impl == "reference":
         if rank != 0:
@@ -181,53 +286,33 @@ def main():
         dist.init_process_group("nccl")
     else:
         torch.cuda.set_device(0)
-    dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
-    cfg = ader.make_config(wl["pde"], D, N, wl["ncell"], wl["lo"], wl["hi"], wl["bc"],
-                           synth.cfl_number(N), precision=args.prec)
-    ctx = ader.Context(cfg, stream=stream.cuda_stream)
     u0 = build_initial(ader, synth, wl)
     u0_dev = torch.from_numpy(u0).to("cuda")
     torch.cuda.synchronize()
-    with torch.cuda.stream(stream):
-        ctx.set_state(u0_dev)
-        for _ in range(args.warmup):
-            ctx.step()
-    ctx.sync()
 
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    # ---- device-timed region ---------------------------------------------------------------
-    clk = sample_clocks(0)
-    time.sleep(0.3)
-    ctx.enable_timing(True)
-    barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        ctx.step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    ms_total = e0.elapsed_time(e1)
-    clocks = parse_clocks(clk, dev)
-    phases, nrec = ctx.phase_times()
-    ctx.enable_timing(False)
-    ctx.sync()
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / args.steps
-    value = world * dofs * args.steps / (ms_total * 1e-3)
+    forms = [f for f in args.forms.split(",") if f]
+    if args.prec not in forms:
+        forms.append(args.prec)
+    res = {}
+    head_ctx = None
+    for prec in forms:
+        ctx, ms_total, phases, nrec, clocks, err = run_form(ader, synth, wl, prec, args, stream,
+                                                            u0_dev, args.err_steps)
+        ms_total = max_over_ranks(ms_total)
+        res[prec] = dict(value=world * dofs * args.steps / (ms_total * 1e-3),
+                         ms_per_step=ms_total / args.steps, phases=phases, nrec=nrec,
+                         clocks=clocks, err=err)
+        if prec == args.prec:
+            head_ctx = ctx
+        else:
+            ctx.close()
+    head = res[args.prec]
 
     # ---- end-to-end through the C ABI with host buffers --------------------------------------
     e2e = None
     if not args.no_e2e:
+        ctx = head_ctx
         h_in = torch.from_numpy(u0).pin_memory()
         h_out = torch.empty(dofs, dtype=torch.float64).pin_memory()
         barrier()
@@ -238,37 +323,46 @@ def main():
             ctx.step()
             ctx.get_state(h_out)
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(time.perf_counter() - t0)
         e2e = {"value": world * dofs * args.steps / el, "unit": "DOF-updates/s",
                "h2d_bytes_per_step": dofs * 8, "d2h_bytes_per_step": dofs * 8}
+    head_ctx.close()
 
     # ---- roofline of the dominant kernel (the predictor) -------------------------------------
-    pred_ms = phases["predictor"] / max(nrec, 1)
+    nrec = max(head["nrec"], 1)
+    pred_ms = head["phases"]["predictor"] / nrec
     flops = predictor_flops_per_cell(wl["pde"], D, N, N + 1) * cells
     achieved = flops / (pred_ms * 1e-3) / 1e12
-    peak = FP64_PEAK / 1e12
-    roof = {"bound": "alu", "kernel": "k_predictor (FP64)", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
-            "flops_per_cell": flops / cells, "ms_per_launch": pred_ms,
-            "phase_ms_per_step": {k: v / max(nrec, 1) for k, v in phases.items()}}
+    if args.prec == "fp64":
+        peak, src, kname = FP64_PEAK, "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz", \
+            "k_predictor (FP64)"
+    else:
+        peak, src, kname = FP32_PEAK, "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz", \
+            "k_predictor_mixed (binary32 increments, float-float base)"
+    roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak / 1e12,
+            "unit": "TFLOP/s", "frac": achieved / (peak / 1e12), "traffic": None,
+            "peak_source": src, "flops_per_cell": flops / cells, "ms_per_launch": pred_ms,
+            "phase_ms_per_step": {k: v / nrec for k, v in head["phases"].items()}}
+    forms_out = {}
+    for k, r in res.items():
+        forms_out[k] = {"value": r["value"], "ms_per_step": r["ms_per_step"],
+                        "predictor_ms": r["phases"]["predictor"] / max(r["nrec"], 1), "err": r["err"]}
+    if "fp64" in res and "mixed" in res and res["fp64"]["err"] and res["mixed"]["err"]:
+        forms_out["mixed_over_fp64_l2_error"] = res["mixed"]["err"]["l2_rho"] / res["fp64"]["err"]["l2_rho"]
+        forms_out["mixed_speedup"] = res["mixed"]["value"] / res["fp64"]["value"]
     launches_per_step = 1 + 1 + 1 + D + 1 + 1
-    line = {"metric": metric, "value": value, "unit": "DOF-updates/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config, "roofline": roof, "e2e": e2e,
-            "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
+    line = {"metric": metric, "value": head["value"], "unit": "DOF-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.prec == "fp64" else "f32+f64",
+            "data": "synthetic", "config": config, "roofline": roof, "forms": forms_out,
+            "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": head["clocks"]}
     if world == 1 and rank == 0:
         v, desc, cores, _ = oracle_sample(wl, args.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": "DOF-updates/s", "cores": cores,
                                 "kind": "oracle", "sample": desc}
     if rank == 0:
         print(json.dumps(line))
-    ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

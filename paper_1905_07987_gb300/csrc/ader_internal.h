@@ -43,6 +43,17 @@ struct Tables {
   double pz[3], pw[3];        // 3-point Gauss-Legendre rule on [0,1] (path integral of B)
 };
 
+// Single-precision and float-float copies of the tables for the mixed-precision predictor.
+// A float-float value is hi + lo with hi = fl32(x), lo = fl32(x - hi).
+struct TablesF {
+  float Dh[MAXN][MAXN], Dl[MAXN][MAXN];    // strong derivative D
+  float Wh[MAXN][MAXN], Wl[MAXN][MAXN];    // weak derivative Dw = c1 e1^T - c0 e0^T - D
+  float Kw[MAXN][MAXN];                    // K1^{-1} diag(w)
+  float kw1[MAXN];                         // row sums of Kw
+  float w[MAXN];
+  float e0h[MAXN], e0l[MAXN], e1h[MAXN], e1l[MAXN];
+};
+
 // Subcell tables of the limiter (Sec. 3.5).
 struct SubTables {
   double P1[MAXNS][MAXN];  // DG nodal values -> subcell averages
@@ -101,7 +112,7 @@ struct Family {
   bool conservative;   // has a flux F (face records carry Fbar)
   // launchers: return cudaError_t of the launch
   cudaError_t (*cfl)(const StepArgs&, cudaStream_t);
-  cudaError_t (*predictor)(const StepArgs&, const Tables&, int prec, cudaStream_t);
+  cudaError_t (*predictor)(const StepArgs&, const Tables&, const TablesF&, int prec, cudaStream_t);
   cudaError_t (*riemann)(const StepArgs&, const Tables&, cudaStream_t);
   cudaError_t (*corrector)(const StepArgs&, const Tables&, cudaStream_t);
   size_t (*predictor_smem)(int order, int prec);

@@ -155,6 +155,30 @@ bool build_tables(int order, Tables& T) {
   return true;
 }
 
+void split_f(double x, float& h, float& l) {
+  h = (float)x;
+  l = (float)(x - (double)h);
+}
+
+void build_tables_f(int order, const Tables& T, TablesF& F) {
+  std::memset(&F, 0, sizeof(F));
+  const int n = order + 1;
+  for (int i = 0; i < n; ++i) {
+    double rs = 0.0;
+    for (int m = 0; m < n; ++m) {
+      split_f(T.D[i][m], F.Dh[i][m], F.Dl[i][m]);
+      const double w = T.c1[i] * T.e1[m] - T.c0[i] * T.e0[m] - T.D[i][m];
+      split_f(w, F.Wh[i][m], F.Wl[i][m]);
+      F.Kw[i][m] = (float)T.Kw[i][m];
+      rs += T.Kw[i][m];
+    }
+    F.kw1[i] = (float)rs;
+    F.w[i] = (float)T.w[i];
+    split_f(T.e0[i], F.e0h[i], F.e0l[i]);
+    split_f(T.e1[i], F.e1h[i], F.e1l[i]);
+  }
+}
+
 const Family* pick_family(int pde, int dim) {
   if (pde == ADER_PDE_ADVECTION) return dim == 2 ? family_advection2() : family_advection3();
   if (pde == ADER_PDE_EULER) return dim == 2 ? family_euler2() : family_euler3();
@@ -171,6 +195,7 @@ struct ader_ctx {
   Geometry g{};
   PdeParams p{};
   Tables tab{};
+  TablesF tabf{};
   long long nodes = 0, nvar = 0, ndof = 0;
   int nf = 0;
   double* u = nullptr;
@@ -263,7 +288,7 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
   if (cfg->dim < 2 || cfg->dim > 3 || cfg->order < 1 || cfg->order > MAXN - 1) return ADER_EUNSUPPORTED;
   const Family* fam = pick_family(cfg->pde, cfg->dim);
   if (!fam) return ADER_EUNSUPPORTED;
-  if (cfg->precision != ADER_PREC_FP64) return ADER_EUNSUPPORTED;
+  if (cfg->precision != ADER_PREC_FP64 && cfg->precision != ADER_PREC_MIXED) return ADER_EUNSUPPORTED;
   if (cfg->limiter) return ADER_EUNSUPPORTED;
   if (!(cfg->cfl > 0.0)) return ADER_EINVAL;
   long long ncells = 1;
@@ -300,6 +325,7 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
     delete c;
     return ADER_EINVAL;
   }
+  build_tables_f(cfg->order, c->tab, c->tabf);
   const int n = cfg->order + 1;
   c->nodes = 1;
   for (int d = 0; d < cfg->dim; ++d) c->nodes *= n;
@@ -548,7 +574,7 @@ static ader_status step_impl(ader_ctx* c, double dt, double t_end) {
   if ((st = mark(c, 1)) != ADER_OK) return st;
   CUDA_OK(launch_dt_finalize(a, s));
   if ((st = mark(c, 2)) != ADER_OK) return st;
-  CUDA_OK(c->fam->predictor(a, c->tab, c->cfg.precision, s));
+  CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, c->cfg.precision, s));
   if ((st = mark(c, 3)) != ADER_OK) return st;
   CUDA_OK(c->fam->riemann(a, c->tab, s));
   if ((st = mark(c, 4)) != ADER_OK) return st;

@@ -642,34 +642,47 @@ cudaError_t launch_cfl_n(const StepArgs& a, cudaStream_t s) {
 template <class P, int D>
 struct FamilyImpl {
   static cudaError_t cfl(const StepArgs& a, cudaStream_t s) { ADER_DISPATCH_N(launch_cfl_n, a, s) }
-  static cudaError_t predictor(const StepArgs& a, const Tables& t, int prec, cudaStream_t s);
+  static cudaError_t predictor(const StepArgs& a, const Tables& t, const TablesF& f, int prec,
+                               cudaStream_t s);
   static cudaError_t riemann(const StepArgs& a, const Tables& t, cudaStream_t s) {
     ADER_DISPATCH_N(launch_riemann_n, a, t, s)
   }
   static cudaError_t corrector(const StepArgs& a, const Tables& t, cudaStream_t s) {
     ADER_DISPATCH_N(launch_corrector_n, a, t, s)
   }
-  static size_t smem(int order, int prec) {
-    switch (order) {
-      case 1: return Cfg<P, D, 1>::SMEM;
-      case 2: return Cfg<P, D, 2>::SMEM;
-      case 3: return Cfg<P, D, 3>::SMEM;
-      case 4: return Cfg<P, D, 4>::SMEM;
-      case 5: return Cfg<P, D, 5>::SMEM;
-      case 6: return Cfg<P, D, 6>::SMEM;
-    }
-    return 0;
-  }
+  static size_t smem(int order, int prec);
   static const Family* get() {
     static const Family f = {P::NV, P::CONS, &cfl, &predictor, &riemann, &corrector, &smem};
     return &f;
   }
 };
 
+}  // namespace ader
+#include "kernels_mixed.cuh"
+namespace ader {
+
 template <class P, int D>
-cudaError_t FamilyImpl<P, D>::predictor(const StepArgs& a, const Tables& t, int prec,
-                                        cudaStream_t s) {
-  (void)prec;
+size_t FamilyImpl<P, D>::smem(int order, int prec) {
+#define ADER_SMEM_CASE(NN) \
+  case NN: return prec == 1 ? CfgM<P, D, NN>::SMEM : Cfg<P, D, NN>::SMEM;
+  switch (order) {
+    ADER_SMEM_CASE(1)
+    ADER_SMEM_CASE(2)
+    ADER_SMEM_CASE(3)
+    ADER_SMEM_CASE(4)
+    ADER_SMEM_CASE(5)
+    ADER_SMEM_CASE(6)
+  }
+#undef ADER_SMEM_CASE
+  return 0;
+}
+
+template <class P, int D>
+cudaError_t FamilyImpl<P, D>::predictor(const StepArgs& a, const Tables& t, const TablesF& f,
+                                        int prec, cudaStream_t s) {
+  if (prec == 1) {
+    ADER_DISPATCH_N(launch_predictor_mixed_n, a, t, f, s)
+  }
   ADER_DISPATCH_N(launch_predictor_n, a, t, s)
 }
 

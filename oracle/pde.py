@@ -93,7 +93,10 @@ class Euler:
         return torch.stack(comps, dim=-1)
 
     def sound_speed(self, q):
-        return torch.sqrt(self.gamma * self.pressure(q) / q[..., 0])
+        """sqrt(gamma p / rho); a negative c^2 (a non-admissible state, which the limiter rejects)
+        counts as 0 so that wave-speed estimates stay finite; NaN propagates."""
+        c2 = self.gamma * self.pressure(q) / q[..., 0]
+        return torch.sqrt(torch.where(c2 < 0, torch.zeros_like(c2), c2))
 
     def max_speed(self, q, d, mat=None):
         """|v_d| + c: the largest |eigenvalue| of dF_d/dQ (eigenvalues v_d - c, v_d, v_d + c)."""

@@ -60,11 +60,14 @@ struct Euler {
     for (int i = 0; i < D; ++i) j2 = fma(q[1 + i], q[1 + i], j2);
     return (gamma - 1.0) * (q[NV - 1] - 0.5 * j2 / q[0]);
   }
-  // |v_d| + c
+  // |v_d| + c; a negative c^2 (non-admissible state, rejected by the limiter) counts as 0 so the
+  // estimate stays finite; NaN propagates.
   __device__ static double speed(const double* q, const PdeParams& pp, int d) {
     const double ir = 1.0 / q[0];
     const double p = pressure(q, pp.gamma);
-    return fabs(q[1 + d] * ir) + sqrt(pp.gamma * p * ir);
+    double c2 = pp.gamma * p * ir;
+    if (c2 < 0.0) c2 = 0.0;
+    return fabs(q[1 + d] * ir) + sqrt(c2);
   }
   __device__ static void mirror(double* q, int d) { q[1 + d] = -q[1 + d]; }
   // F_d of the mirrored state: all components but the normal momentum flux change sign.

@@ -83,6 +83,19 @@ def node_coordinates(nodes, ncell, lo, hi):
     return out
 
 
+def subcell_centres(ns, ncell, lo, hi):
+    """Centres of the ns^d equal subcells of every cell (same layout as node_coordinates)."""
+    return node_coordinates((np.arange(ns) + 0.5) / ns, ncell, lo, hi)
+
+
+def discontinuous_cells(U_sub):
+    """Cells whose sampled subcell values are not all equal (the initial data jumps inside them):
+    bool [C].  U_sub: [C, ns, ..., ns, nvar]."""
+    C = U_sub.shape[0]
+    flat = U_sub.reshape(C, -1, U_sub.shape[-1])
+    return (flat.max(axis=1) - flat.min(axis=1)).max(axis=1) > 0
+
+
 def entropy_wave(X, t=0.0, amp=0.2):
     """Density wave rho = 1 + amp sin(2 pi (sum_d x_d - d t)) advected with v = (1,..,1), p = 1:
     an exact solution of the Euler equations (Sec. 6.1 workloads)."""

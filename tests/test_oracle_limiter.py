@@ -1,0 +1,156 @@
+"""Pins for the oracle's a-posteriori subcell limiter (Sec. 3.5): Godunov limit of the FV scheme,
+the exact Sod solution, conservation through troubled cells and neighbour fixes, no troubled
+cells on smooth data, symmetry of the explosion, and detection of non-finite states."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle.aderdg import ADERDG, Grid
+from oracle.limiter import Limiter
+from oracle.pde import Euler
+from paper_1905_07987_gb300 import synth
+from sod_exact import sample, star_state
+
+T = lambda a: torch.as_tensor(np.asarray(a), dtype=torch.float64)
+
+
+def make(ncell, N, lo, hi, bc):
+    dim = len(ncell)
+    g = Grid(ncell, lo, hi, [(bc, bc)] * dim if isinstance(bc, str) else bc)
+    s = ADERDG(Euler(dim), g, N, cfl=synth.cfl_number(N))
+    return s, Limiter(s)
+
+
+def coords(s):
+    return synth.node_coordinates(s.ref.x.numpy(), s.grid.ncell, s.grid.lo, s.grid.hi)
+
+
+def test_exact_riemann_solver_reproduces_the_textbook_sod_star_state():
+    ps, us = star_state((1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
+    assert abs(ps - 0.30313) < 1e-5 and abs(us - 0.92745) < 1e-5
+
+
+def test_fv_without_slopes_is_first_order_godunov_rusanov():
+    s, lim = make((3, 2), 2, (0, 0), (1, 1), 'periodic')
+    rng = np.random.default_rng(0)
+    rep = T(synth.euler_conserved(1 + 0.3 * rng.random((6, 5, 5)), [0.2 * rng.random((6, 5, 5)), -0.1],
+                                  1 + 0.2 * rng.random((6, 5, 5))))
+    dt = 0.003
+    U_new, _ = lim.fv_global(rep, dt, slopes=False)
+    G = lim.to_global(rep)  # [10 (y), 15 (x), 4]
+    pde = Euler(2)
+    dx = [1 / 15, 1 / 10]
+    out = G.clone()
+    for d, ax in ((0, 1), (1, 0)):
+        Ur = torch.roll(G, -1, dims=ax)
+        s_ = torch.maximum(pde.max_speed(G, d), pde.max_speed(Ur, d))[..., None]
+        f = 0.5 * (pde.flux(G, d) + pde.flux(Ur, d)) - 0.5 * s_ * (Ur - G)  # right faces
+        out = out - dt / dx[d] * (f - torch.roll(f, 1, dims=ax))
+    assert torch.allclose(lim.to_global(U_new), out, atol=1e-14)
+
+
+def sod_run(nc, t_end=0.15):
+    s, lim = make((nc, 1), 2, (0, 0), (1, 1.0 / nc), [('absorbing', 'absorbing'), ('periodic', 'periodic')])
+    X = coords(s)
+    left = X[0] < 0.5
+    u = T(synth.euler_conserved(np.where(left, 1.0, 0.125), [0.0, 0.0], np.where(left, 1.0, 0.1)))
+    Xs = synth.subcell_centres(lim.ns, s.grid.ncell, s.grid.lo, s.grid.hi)
+    ls = Xs[0] < 0.5
+    Us = synth.euler_conserved(np.where(ls, 1.0, 0.125), [0.0, 0.0], np.where(ls, 1.0, 0.1))
+    u, rep = lim.initial_rep(u, T(Us), torch.from_numpy(synth.discontinuous_cells(Us)))
+    t = 0.0
+    while t < t_end - 1e-14:
+        dt = min(float(s.cfl_dt(u)), t_end - t)
+        u, tr, rep, ok = lim.step(u, rep, torch.tensor(dt, dtype=torch.float64), t, force=True)
+        assert ok
+        t += dt
+    # L1 error of the subcell averages (the FV representation) against the exact solution
+    G = lim.to_global(rep)[0, :, 0].numpy()
+    ns = lim.ns
+    xs = (np.arange(nc * ns) + 0.5) / (nc * ns)
+    ex = np.array([sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), (x - 0.5) / t)[0] for x in xs])
+    return np.mean(np.abs(G - ex))
+
+
+def test_pure_fv_scheme_converges_to_the_exact_sod_solution():
+    e1 = sod_run(8)
+    e2 = sod_run(16)
+    assert e2 < 0.65 * e1, (e1, e2)
+    assert e2 < 0.02
+
+
+def explosion(ncell, N, lo=-1.0, hi=1.0):
+    """Explosion data; cells cut by the initial sphere start with FV subcell averages."""
+    dim = len(ncell)
+    s, lim = make(ncell, N, (lo,) * dim, (hi,) * dim, 'wall')
+    u = T(synth.explosion(coords(s)))
+    Us = synth.explosion(synth.subcell_centres(lim.ns, s.grid.ncell, s.grid.lo, s.grid.hi))
+    flags = torch.from_numpy(synth.discontinuous_cells(Us))
+    u, rep = lim.initial_rep(u, T(Us), flags)
+    return s, lim, u, rep
+
+
+def totals(s, u):
+    W = s.tensor_basis_weights()
+    vol = 1.0
+    for h in s.grid.h:
+        vol *= h
+    return (u * W[None, ..., None]).sum(dim=tuple(range(0, s.D + 1))) * vol
+
+
+def test_limited_explosion_conserves_mass_and_energy_and_flags_the_front():
+    s, lim, u, rep = explosion((10, 10), 2)
+    m0 = totals(s, u)
+    n_tr = []
+    for _ in range(4):
+        u, tr, rep, ok = lim.step(u, rep, s.cfl_dt(u))
+        assert ok
+        n_tr.append(int(tr.sum()))
+    m1 = totals(s, u)
+    assert abs(float(m1[0] - m0[0])) < 1e-13 * float(m0[0])
+    assert abs(float(m1[3] - m0[3])) < 1e-13 * float(m0[3])
+    assert min(n_tr) > 0 and max(n_tr) < 100
+
+
+def test_explosion_flags_and_state_are_symmetric():
+    s, lim, u, rep = explosion((8, 8), 2)
+    for _ in range(3):
+        u, tr, rep, ok = lim.step(u, rep, s.cfl_dt(u))
+    F = tr.reshape(8, 8)
+    assert torch.equal(F, F.flip(0)) and torch.equal(F, F.flip(1)) and torch.equal(F, F.T)
+    uu = u.reshape(8, 8, 3, 3, 4)
+    assert torch.allclose(uu[..., 0], uu.flip(1).flip(3)[..., 0], atol=1e-12)
+    assert torch.allclose(uu[..., 0], uu.transpose(0, 1).transpose(2, 3)[..., 0], atol=1e-12)
+
+
+def test_smooth_flow_has_no_troubled_cells():
+    """A smooth wave of small amplitude stays inside the relaxed DMP (delta0 = 1e-4)."""
+    s, lim = make((8, 8), 3, (0, 0), (1, 1), 'periodic')
+    u = T(synth.entropy_wave(coords(s), amp=1e-3))
+    u, rep = lim.initial_rep(u)
+    for _ in range(3):
+        u, tr, rep, ok = lim.step(u, rep, s.cfl_dt(u))
+        assert not tr.any()
+
+
+def test_forced_recompute_equals_pure_fv_and_is_conservative():
+    s, lim, u, rep = explosion((6, 6), 2)
+    dt = s.cfl_dt(u)
+    u1, tr, rep1, ok = lim.step(u, rep, dt, force=True)
+    U_all, _ = lim.fv_global(rep, dt)
+    assert tr.all() and torch.allclose(rep1, U_all, atol=0)
+    assert torch.allclose(u1, lim.reconstruct(U_all), atol=0)
+    m0, m1 = totals(s, u), totals(s, u1)
+    assert abs(float(m1[0] - m0[0])) < 1e-14
+
+
+def test_non_finite_candidate_is_troubled():
+    s, lim = make((4, 4), 2, (0, 0), (1, 1), 'periodic')
+    u = T(synth.entropy_wave(coords(s)))
+    u, rep = lim.initial_rep(u)
+    bad = u.clone()
+    bad[5, 1, 1, 2] = float('nan')
+    tr, _ = lim.detect(bad, rep)
+    assert bool(tr[5]) and int(tr.sum()) == 1

@@ -76,7 +76,8 @@ typedef struct {
   double gamma;        /* ratio of specific heats (Euler), e.g. 1.4 */
   double adv[3];       /* advection velocity (ADER_PDE_ADVECTION) */
   int picard_iters;    /* fixed number of predictor iterations; 0 => order + 1 */
-  int limiter;         /* 1: a-posteriori FV subcell limiter (Euler only), 0: off */
+  int limiter;         /* a-posteriori FV subcell limiter (Euler, order <= 4): 0 off, 1 on,
+                          2 every cell troubled (the pure FV scheme, for tests) */
   int precision;       /* ader_prec */
 } ader_config;
 
@@ -133,6 +134,17 @@ ader_status ader_run(ader_ctx* ctx, int steps, double dt, double t_end);
 
 /* The dt used by the last step (host; synchronises). */
 ader_status ader_last_dt(ader_ctx* ctx, double* dt);
+
+/* Limiter history (ader_config.limiter != 0).  ader_set_state resets it: every cell's
+ * representation at the current time becomes the subcell averages of its DG polynomial and no
+ * cell counts as troubled.  ader_set_subcell_state then puts the cells with flags[c] != 0 into
+ * the FV space, as at the start of a limited run along a discontinuity (Sec. 3.5): their
+ * representation becomes U_sub[c] ([cells][(2N+1)^dim][nvar], subcell index x fastest; rows of
+ * unflagged cells are ignored) and their DG state R(U_sub[c]).  ader_get_subcell_state returns the
+ * current representation of every cell. */
+ader_status ader_set_subcell_state(ader_ctx* ctx, const double* U_sub, const uint8_t* flags,
+                                   int on_device);
+ader_status ader_get_subcell_state(ader_ctx* ctx, double* U_sub, int on_device);
 
 /* Troubled-cell flags of the last step, [cells] bytes (1 = recomputed with FV), and the count. */
 ader_status ader_get_flags(ader_ctx* ctx, uint8_t* flags, int on_device);

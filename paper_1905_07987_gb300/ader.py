@@ -69,6 +69,8 @@ _SIGS = {
     "ader_troubled_count": ([_P, ctypes.POINTER(_L)], _I),
     "ader_sync": ([_P], _I),
     "ader_run_graph": ([_P, _I, _I, _D, _D], _I),
+    "ader_set_subcell_state": ([_P, _P, _P, _I], _I),
+    "ader_get_subcell_state": ([_P, _P, _I], _I),
     "ader_enable_timing": ([_P, _I], _I),
     "ader_phase_times": ([_P, _P, ctypes.POINTER(_I)], _I),
 }
@@ -220,6 +222,19 @@ class Context:
         self._seismo = seismo
         check(lib().ader_set_receivers(self._h, len(xyz), xyz.ctypes.data, p, int(max_steps)),
               "ader_set_receivers")
+
+    def set_subcell_state(self, U_sub, flags):
+        """Cells with flags != 0 start in the FV space with subcell averages U_sub."""
+        p, dev, keep, n = _ptr(U_sub)
+        fp, fdev, fkeep, fn = _ptr(flags, np.uint8)
+        if fn != self.cells or fdev != dev:
+            raise ValueError("flags must hold one byte per cell, on the same side as U_sub")
+        check(lib().ader_set_subcell_state(self._h, p, fp, dev), "ader_set_subcell_state")
+
+    def get_subcell_state(self, out):
+        p, dev, keep, n = _ptr(out)
+        check(lib().ader_get_subcell_state(self._h, p, dev), "ader_get_subcell_state")
+        return out
 
     def set_time(self, t):
         check(lib().ader_set_time(self._h, float(t)), "ader_set_time")

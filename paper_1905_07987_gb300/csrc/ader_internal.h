@@ -61,6 +61,8 @@ struct SubTables {
   double Pf[MAXNS][MAXN];  // P1[s][m] / (w_m ns): subface flux -> nodal face flux weights
 };
 
+struct LimArgs;
+
 struct Geometry {
   int dim, order;
   int n[3];            // cells per direction
@@ -116,6 +118,12 @@ struct Family {
   cudaError_t (*riemann)(const StepArgs&, const Tables&, cudaStream_t);
   cudaError_t (*corrector)(const StepArgs&, const Tables&, cudaStream_t);
   size_t (*predictor_smem)(int order, int prec);
+  // limiter (Euler only; null otherwise)
+  cudaError_t (*lim_init)(int order, double* u, const double* Usub, const uint8_t* flags,
+                          double* rep, double* mm, long long ncells, const SubTables& S,
+                          cudaStream_t s);
+  cudaError_t (*lim_step)(const StepArgs&, const LimArgs&, const Tables&, const SubTables&,
+                          cudaStream_t);
 };
 
 const Family* family_advection2();
@@ -123,6 +131,8 @@ const Family* family_advection3();
 const Family* family_euler2();
 const Family* family_euler3();
 const Family* family_elastic3();
+int limiter_max_order2();
+int limiter_max_order3();
 
 // Small kernels shared by all families (common.cu).
 cudaError_t launch_dt_finalize(const StepArgs& a, cudaStream_t s);

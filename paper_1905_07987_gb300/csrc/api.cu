@@ -9,6 +9,21 @@
 #include "../../include/ader.h"
 #include "ader_internal.h"
 
+namespace ader {
+struct LimArgs {
+  const double* rep;
+  double* rep_new;
+  const double* mm;
+  double* mm_new;
+  const uint8_t* flags_prev;
+  uint8_t* flags;
+  int* list;
+  double* bflux;
+  int force;
+  double delta0, eps;
+};
+}  // namespace ader
+
 using namespace ader;
 
 namespace {
@@ -179,6 +194,80 @@ void build_tables_f(int order, const Tables& T, TablesF& F) {
   }
 }
 
+// Solve A x = b for several right-hand sides (Gauss-Jordan, partial pivoting); A is m x m.
+bool solve_dense(int m, std::vector<double> A, std::vector<double>& B, int nrhs) {
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < m; ++r)
+      if (std::fabs(A[r * m + c]) > std::fabs(A[piv * m + c])) piv = r;
+    if (std::fabs(A[piv * m + c]) < 1e-300) return false;
+    if (piv != c) {
+      for (int j = 0; j < m; ++j) std::swap(A[c * m + j], A[piv * m + j]);
+      for (int j = 0; j < nrhs; ++j) std::swap(B[c * nrhs + j], B[piv * nrhs + j]);
+    }
+    const double d = A[c * m + c];
+    for (int j = 0; j < m; ++j) A[c * m + j] /= d;
+    for (int j = 0; j < nrhs; ++j) B[c * nrhs + j] /= d;
+    for (int r = 0; r < m; ++r) {
+      if (r == c) continue;
+      const double f = A[r * m + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < m; ++j) A[r * m + j] -= f * A[c * m + j];
+      for (int j = 0; j < nrhs; ++j) B[r * nrhs + j] -= f * B[c * nrhs + j];
+    }
+  }
+  return true;
+}
+
+// Subcell tables of the limiter (Sec. 3.5): P1[s][m] = mean of phi_m over subcell s, computed
+// from the monomial coefficients of phi_m (inverse Vandermonde) and exact antiderivatives;
+// R1 = the mean-preserving least-squares left inverse of P1 (KKT system).
+bool build_subtables(int order, const Tables& T, SubTables& S) {
+  std::memset(&S, 0, sizeof(S));
+  const int n = order + 1, ns = 2 * order + 1;
+  // coefficients: phi_m(x) = sum_k a[k][m] x^k  <=>  V a = I with V[i][k] = x_i^k
+  std::vector<double> V(n * n), a(n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double p = 1.0;
+    for (int k = 0; k < n; ++k) {
+      V[i * n + k] = p;
+      p *= T.x[i];
+    }
+    a[i * n + i] = 1.0;
+  }
+  if (!solve_dense(n, V, a, n)) return false;
+  for (int s = 0; s < ns; ++s) {
+    const double lo = (double)s / ns, hi = (double)(s + 1) / ns;
+    for (int m = 0; m < n; ++m) {
+      double acc = 0.0, plo = lo, phi = hi;
+      for (int k = 0; k < n; ++k) {
+        acc += a[k * n + m] * (phi - plo) / (k + 1);
+        plo *= lo;
+        phi *= hi;
+      }
+      S.P1[s][m] = acc * ns;
+    }
+  }
+  // KKT: [2 P1^T P1, w; w^T, 0] [R1; mu] = [2 P1^T; 1^T / ns]
+  const int m = n + 1;
+  std::vector<double> K(m * m, 0.0), B(m * ns, 0.0);
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) {
+      double acc = 0.0;
+      for (int s = 0; s < ns; ++s) acc += S.P1[s][i] * S.P1[s][j];
+      K[i * m + j] = 2.0 * acc;
+    }
+    K[i * m + n] = T.w[i];
+    K[n * m + i] = T.w[i];
+    for (int s = 0; s < ns; ++s) B[i * ns + s] = 2.0 * S.P1[s][i];
+  }
+  for (int s = 0; s < ns; ++s) B[n * ns + s] = 1.0 / ns;
+  if (!solve_dense(m, K, B, ns)) return false;
+  for (int i = 0; i < n; ++i)
+    for (int s = 0; s < ns; ++s) S.R1[i][s] = B[i * ns + s];
+  return true;
+}
+
 const Family* pick_family(int pde, int dim) {
   if (pde == ADER_PDE_ADVECTION) return dim == 2 ? family_advection2() : family_advection3();
   if (pde == ADER_PDE_EULER) return dim == 2 ? family_euler2() : family_euler3();
@@ -196,6 +285,12 @@ struct ader_ctx {
   PdeParams p{};
   Tables tab{};
   TablesF tabf{};
+  SubTables sub{};
+  // limiter state (Euler, limiter != 0): representations, their min/max, flags, troubled list
+  double *rep = nullptr, *rep_new = nullptr, *mm = nullptr, *mm_new = nullptr, *bflux = nullptr;
+  uint8_t* flags = nullptr;
+  int* list = nullptr;
+  long long nss = 0;
   long long nodes = 0, nvar = 0, ndof = 0;
   int nf = 0;
   double* u = nullptr;
@@ -238,6 +333,13 @@ static ader_status latched(int bits) {
 }
 
 static void free_all(ader_ctx* c) {
+  cudaFree(c->rep);
+  cudaFree(c->rep_new);
+  cudaFree(c->mm);
+  cudaFree(c->mm_new);
+  cudaFree(c->bflux);
+  cudaFree(c->flags);
+  cudaFree(c->list);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   c->ev.clear();
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -289,7 +391,11 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
   const Family* fam = pick_family(cfg->pde, cfg->dim);
   if (!fam) return ADER_EUNSUPPORTED;
   if (cfg->precision != ADER_PREC_FP64 && cfg->precision != ADER_PREC_MIXED) return ADER_EUNSUPPORTED;
-  if (cfg->limiter) return ADER_EUNSUPPORTED;
+  if (cfg->limiter < 0 || cfg->limiter > 2) return ADER_EINVAL;
+  if (cfg->limiter) {
+    if (cfg->pde != ADER_PDE_EULER) return ADER_EUNSUPPORTED;
+    if (cfg->order > (cfg->dim == 2 ? limiter_max_order2() : limiter_max_order3())) return ADER_EUNSUPPORTED;
+  }
   if (!(cfg->cfl > 0.0)) return ADER_EINVAL;
   long long ncells = 1;
   for (int d = 0; d < cfg->dim; ++d) {
@@ -344,6 +450,23 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->phi, nphi_total * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->dev, sizeof(DevScalars));
   if (e == cudaSuccess && cfg->pde == ADER_PDE_ELASTIC) e = cudaMalloc(&c->mat, ncells * 3 * sizeof(double));
+  if (cfg->limiter) {
+    const int ns = 2 * cfg->order + 1;
+    c->nss = 1;
+    long long nsf = 1;
+    for (int d = 0; d < cfg->dim; ++d) c->nss *= ns;
+    for (int d = 1; d < cfg->dim; ++d) nsf *= ns;
+    if (!build_subtables(cfg->order, c->tab, c->sub)) e = cudaErrorInvalidValue;
+    const size_t nrep = (size_t)ncells * c->nss * c->nvar;
+    if (e == cudaSuccess) e = cudaMalloc(&c->rep, nrep * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->rep_new, nrep * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->mm, ncells * 2 * c->nvar * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->mm_new, ncells * 2 * c->nvar * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->bflux, (size_t)ncells * cfg->dim * 2 * nsf * c->nvar * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->flags, ncells);
+    if (e == cudaSuccess) e = cudaMalloc(&c->list, ncells * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, ncells, c->stream);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_all(c);
@@ -391,8 +514,37 @@ ader_status ader_set_state(ader_ctx* c, const double* q, int64_t count, int on_d
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream,
                         !on_device);
   if (st != ADER_OK) return st;
+  if (c->cfg.limiter) {
+    CUDA_OK(c->fam->lim_init(c->cfg.order, c->u, nullptr, nullptr, c->rep, c->mm, c->g.ncells,
+                             c->sub, c->stream));
+    CUDA_OK(cudaMemsetAsync(c->flags, 0, c->g.ncells, c->stream));
+  }
   c->state_set = true;
   return ADER_OK;
+}
+
+ader_status ader_set_subcell_state(ader_ctx* c, const double* U_sub, const uint8_t* flags,
+                                   int on_device) {
+  if (!c || !U_sub || !flags) return ADER_EINVAL;
+  if (!c->cfg.limiter) return ADER_EUNSUPPORTED;
+  if (!c->state_set) return ADER_ESTATE;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  ader_status st = copy(c->rep_new, U_sub, (size_t)c->g.ncells * c->nss * c->nvar * sizeof(double),
+                        k, c->stream, false);
+  if (st == ADER_OK) st = copy(c->flags, flags, c->g.ncells, k, c->stream, false);
+  if (st != ADER_OK) return st;
+  CUDA_OK(c->fam->lim_init(c->cfg.order, c->u, c->rep_new, c->flags, c->rep, c->mm, c->g.ncells,
+                           c->sub, c->stream));
+  if (!on_device) CUDA_OK(cudaStreamSynchronize(c->stream));
+  return ADER_OK;
+}
+
+ader_status ader_get_subcell_state(ader_ctx* c, double* U_sub, int on_device) {
+  if (!c || !U_sub) return ADER_EINVAL;
+  if (!c->cfg.limiter) return ADER_EUNSUPPORTED;
+  if (!c->state_set) return ADER_ESTATE;
+  return copy(U_sub, c->rep, (size_t)c->g.ncells * c->nss * c->nvar * sizeof(double),
+              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream, !on_device);
 }
 
 ader_status ader_get_state(ader_ctx* c, double* q, int64_t count, int on_device) {
@@ -580,6 +732,13 @@ static ader_status step_impl(ader_ctx* c, double dt, double t_end) {
   if ((st = mark(c, 4)) != ADER_OK) return st;
   CUDA_OK(c->fam->corrector(a, c->tab, s));
   if ((st = mark(c, 5)) != ADER_OK) return st;
+  if (c->cfg.limiter) {
+    LimArgs l{c->rep, c->rep_new, c->mm, c->mm_new, nullptr, c->flags, c->list, c->bflux,
+              c->cfg.limiter == 2 ? 1 : 0, 1e-4, 1e-3};
+    CUDA_OK(c->fam->lim_step(a, l, c->tab, c->sub, s));
+    std::swap(c->rep, c->rep_new);
+    std::swap(c->mm, c->mm_new);
+  }
   if ((st = mark(c, 6)) != ADER_OK) return st;
   if (c->rec.nrec > 0) CUDA_OK(launch_receivers(a, c->rec, (int)c->nodes, (int)c->nvar, s));
   CUDA_OK(launch_advance_rec(a, c->rec.nrec > 0, s));
@@ -627,17 +786,26 @@ ader_status ader_last_dt(ader_ctx* c, double* dt) {
 
 ader_status ader_get_flags(ader_ctx* c, uint8_t* flags, int on_device) {
   if (!c || !flags) return ADER_EINVAL;
-  if (on_device) {
-    CUDA_OK(cudaMemsetAsync(flags, 0, c->g.ncells, c->stream));
-  } else {
-    std::memset(flags, 0, c->g.ncells);
+  if (!c->cfg.limiter) {
+    if (on_device) {
+      CUDA_OK(cudaMemsetAsync(flags, 0, c->g.ncells, c->stream));
+    } else {
+      std::memset(flags, 0, c->g.ncells);
+    }
+    return ADER_OK;
   }
-  return ADER_OK;
+  return copy(flags, c->flags, c->g.ncells,
+              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream, !on_device);
 }
 
 ader_status ader_troubled_count(ader_ctx* c, int64_t* count) {
   if (!c || !count) return ADER_EINVAL;
-  *count = 0;
+  int n = 0;
+  if (c->cfg.limiter) {
+    ader_status st = copy(&n, &c->dev->n_troubled, sizeof(int), cudaMemcpyDeviceToHost, c->stream, true);
+    if (st != ADER_OK) return st;
+  }
+  *count = n;
   return ADER_OK;
 }
 

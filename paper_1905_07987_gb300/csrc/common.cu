@@ -24,6 +24,7 @@ __global__ void k_dt_finalize(const __grid_constant__ StepArgs A) {
   }
   s->dt = dt;
   s->lam_bits = 0ull;
+  s->n_troubled = 0;
 }
 
 __global__ void k_advance(DevScalars* s, int receivers_on) {

@@ -1,0 +1,638 @@
+// A-posteriori finite-volume subcell limiter (Sec. 3.5), FP64, for the Euler equations.
+//
+// Per step, after the unlimited ADER-DG step has written the candidate u* to u_next:
+//   k_lim_detect  one block per cell: subcell averages P(u*), relaxed DMP against the min/max of
+//                 the t^n representations of the cell and its face neighbours, positivity of
+//                 density and pressure at nodes and subcells; troubled cells are compacted into a
+//                 list with one atomic per flagged block.
+//   k_lim_fv      persistent blocks over the troubled list: MUSCL-Hancock (minmod) + Rusanov on
+//                 the (2N+1)^d subcells with a 2-subcell halo from the t^n representations of all
+//                 neighbours, u_next = R(U_sub), the boundary subface fluxes saved per cell.
+//   k_lim_fix     one block per cell: an untroubled face neighbour of a troubled cell replaces its
+//                 DG flux on the shared face by the subface fluxes integrated against its test
+//                 functions (exact conservation), then refreshes its representation.
+// The t^n representation rep (subcell averages of every cell) and its per-variable min/max are
+// double-buffered across steps.
+#pragma once
+#include "kernels.cuh"
+
+namespace ader {
+
+struct LimArgs {
+  const double* rep;     // [C][NSS][NV] representation at t^n
+  double* rep_new;       // [C][NSS][NV] representation at t^{n+1}
+  const double* mm;      // [C][2][NV] min / max of rep
+  double* mm_new;
+  const uint8_t* flags_prev;  // [C] troubled at the previous step (unused by the kernels)
+  uint8_t* flags;        // [C] troubled at this step
+  int* list;             // [C] troubled cells (first n_troubled entries)
+  double* bflux;         // [C][D][2][NSF][NV] subface fluxes on the cell boundary
+  int force;             // 1: every cell troubled (pure FV scheme)
+  double delta0, eps;
+};
+
+template <int D, int N>
+struct CfgL {
+  static constexpr int n = N + 1, ns = 2 * N + 1, NV = D + 2;
+  static constexpr int NN = ipow(n, D), NSS = ipow(ns, D), NSF = ipow(ns, D - 1);
+  static constexpr int NH = ipow(ns + 4, D), NC = ipow(ns + 2, D);
+  static constexpr int TPB = 128;
+  // projection / reconstruction scratch: nodal values, two partial results, subcell values
+  static constexpr int T1 = ipow(ns, D - 1) * n * NV;
+  static constexpr int T2 = D == 3 ? n * ns * ns * NV : 0;
+  static constexpr size_t SMEM_P = (size_t)(NN * NV + T1 + T2 + NSS * NV) * sizeof(double);
+  static constexpr size_t SMEM_FV =
+      (size_t)(NH * NV + NC * NV + NSS * NV + T1 + T2 + NN * NV) * sizeof(double);
+};
+
+// sub[s][v] = sum over nodes of prod_e P1[s_e][a_e] u[a][v] (sum factorisation, x first).
+// u: [NN][NV], out: [NSS][NV]; t1, t2 scratch.  All threads of the block participate.
+template <int D, int N>
+__device__ void project_P(const double* u, double* t1, double* t2, double* out,
+                          const SubTables& S) {
+  using L = CfgL<D, N>;
+  constexpr int n = L::n, ns = L::ns, NV = L::NV;
+  if constexpr (D == 2) {
+    // t1[b][sx][v] = sum_a P1[sx][a] u[b][a][v]
+    for (int e = threadIdx.x; e < n * ns * NV; e += blockDim.x) {
+      const int v = e % NV, sx = (e / NV) % ns, b = e / (NV * ns);
+      double acc = 0.0;
+#pragma unroll
+      for (int a = 0; a < n; ++a) acc = fma(S.P1[sx][a], u[(b * n + a) * NV + v], acc);
+      t1[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ns * ns * NV; e += blockDim.x) {
+      const int v = e % NV, sx = (e / NV) % ns, sy = e / (NV * ns);
+      double acc = 0.0;
+#pragma unroll
+      for (int b = 0; b < n; ++b) acc = fma(S.P1[sy][b], t1[(b * ns + sx) * NV + v], acc);
+      out[e] = acc;
+    }
+  } else {
+    for (int e = threadIdx.x; e < n * n * ns * NV; e += blockDim.x) {
+      const int v = e % NV, sx = (e / NV) % ns, zb = e / (NV * ns);  // zb = z*n + b(y)
+      double acc = 0.0;
+#pragma unroll
+      for (int a = 0; a < n; ++a) acc = fma(S.P1[sx][a], u[(zb * n + a) * NV + v], acc);
+      t1[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * ns * ns * NV; e += blockDim.x) {
+      const int v = e % NV, sx = (e / NV) % ns, sy = (e / (NV * ns)) % ns, z = e / (NV * ns * ns);
+      double acc = 0.0;
+#pragma unroll
+      for (int b = 0; b < n; ++b) acc = fma(S.P1[sy][b], t1[((z * n + b) * ns + sx) * NV + v], acc);
+      t2[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ns * ns * ns * NV; e += blockDim.x) {
+      const int v = e % NV, syx = (e / NV) % (ns * ns), sz = e / (NV * ns * ns);
+      double acc = 0.0;
+#pragma unroll
+      for (int c = 0; c < n; ++c) acc = fma(S.P1[sz][c], t2[(c * ns * ns + syx) * NV + v], acc);
+      out[e] = acc;
+    }
+  }
+  __syncthreads();
+}
+
+// u[a][v] = sum over subcells of prod_e R1[a_e][s_e] U[s][v].
+template <int D, int N>
+__device__ void reconstruct_R(const double* U, double* t1, double* t2, double* out,
+                              const SubTables& S) {
+  using L = CfgL<D, N>;
+  constexpr int n = L::n, ns = L::ns, NV = L::NV;
+  if constexpr (D == 2) {
+    for (int e = threadIdx.x; e < ns * n * NV; e += blockDim.x) {  // t1[sy][a][v]
+      const int v = e % NV, a = (e / NV) % n, sy = e / (NV * n);
+      double acc = 0.0;
+#pragma unroll
+      for (int s = 0; s < ns; ++s) acc = fma(S.R1[a][s], U[(sy * ns + s) * NV + v], acc);
+      t1[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n * NV; e += blockDim.x) {
+      const int v = e % NV, a = (e / NV) % n, b = e / (NV * n);
+      double acc = 0.0;
+#pragma unroll
+      for (int s = 0; s < ns; ++s) acc = fma(S.R1[b][s], t1[(s * n + a) * NV + v], acc);
+      out[e] = acc;
+    }
+  } else {
+    for (int e = threadIdx.x; e < ns * ns * n * NV; e += blockDim.x) {  // t1[sz][sy][a]
+      const int v = e % NV, a = (e / NV) % n, zy = e / (NV * n);
+      double acc = 0.0;
+#pragma unroll
+      for (int s = 0; s < ns; ++s) acc = fma(S.R1[a][s], U[(zy * ns + s) * NV + v], acc);
+      t1[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ns * n * n * NV; e += blockDim.x) {  // t2[sz][b][a]
+      const int v = e % NV, a = (e / NV) % n, b = (e / (NV * n)) % n, sz = e / (NV * n * n);
+      double acc = 0.0;
+#pragma unroll
+      for (int s = 0; s < ns; ++s) acc = fma(S.R1[b][s], t1[((sz * ns + s) * n + a) * NV + v], acc);
+      t2[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n * n * NV; e += blockDim.x) {
+      const int v = e % NV, ba = (e / NV) % (n * n), c = e / (NV * n * n);
+      double acc = 0.0;
+#pragma unroll
+      for (int s = 0; s < ns; ++s) acc = fma(S.R1[c][s], t2[(s * n * n + ba) * NV + v], acc);
+      out[e] = acc;
+    }
+  }
+  __syncthreads();
+}
+
+template <int D>
+__device__ __forceinline__ bool admissible(const double* q, double gamma) {
+  bool fin = true;
+#pragma unroll
+  for (int v = 0; v < D + 2; ++v) fin = fin && isfinite(q[v]);
+  const double p = Euler<D>::pressure(q, gamma);
+  return fin && (q[0] > 0.0) && (p > 0.0);
+}
+
+// Per-variable min / max of sub[NSS][NV] into mm[2][NV]; red: smem scratch [2][NV][32].
+template <int NSS, int NV>
+__device__ void block_minmax(const double* sub, double* mm, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int v = 0; v < NV; ++v) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int s = threadIdx.x; s < NSS; s += blockDim.x) {
+      const double x = sub[s * NV + v];
+      lo = fmin(lo, x);
+      hi = fmax(hi, x);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      red[(0 * NV + v) * 32 + warp] = lo;
+      red[(1 * NV + v) * 32 + warp] = hi;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * NV) {
+    const int k = threadIdx.x;
+    double r = red[k * 32];
+    for (int w = 1; w < nw; ++w) r = (k < NV) ? fmin(r, red[k * 32 + w]) : fmax(r, red[k * 32 + w]);
+    mm[k] = r;
+  }
+  __syncthreads();
+}
+
+template <int D>
+__device__ __forceinline__ long long neighbor(const Geometry& g, long long c, int d, int side) {
+  long long idx[3], rem = c;
+  for (int e = 0; e < 3; ++e) {
+    idx[e] = rem % g.n[e];
+    rem /= g.n[e];
+  }
+  long long j = idx[d] + side;
+  if (j < 0 || j >= g.n[d]) {
+    if (g.bc[d][0] != BC_PERIODIC) return -1;
+    j = (j + g.n[d]) % g.n[d];
+  }
+  idx[d] = j;
+  return idx[0] + (long long)g.n[0] * (idx[1] + (long long)g.n[1] * idx[2]);
+}
+
+template <int D, int N>
+__global__ void __launch_bounds__(128) k_lim_detect(const __grid_constant__ StepArgs A,
+                                                    const __grid_constant__ LimArgs L,
+                                                    const __grid_constant__ SubTables S) {
+  using C = CfgL<D, N>;
+  constexpr int NN = C::NN, NSS = C::NSS, NV = C::NV;
+  extern __shared__ double sm[];
+  double* us = sm;
+  double* t1 = us + NN * NV;
+  double* t2 = t1 + C::T1;
+  double* sub = t2 + C::T2;
+  __shared__ double red[2 * NV * 32];
+  __shared__ double bnd[2][NV];
+  const long long c = blockIdx.x;
+  const double* u = A.u_next + c * (NN * NV);
+  for (int e = threadIdx.x; e < NN * NV; e += blockDim.x) us[e] = u[e];
+  if (threadIdx.x < NV) {
+    const int v = threadIdx.x;
+    double lo = L.mm[c * 2 * NV + v], hi = L.mm[c * 2 * NV + NV + v];
+    for (int d = 0; d < D; ++d)
+      for (int side = -1; side <= 1; side += 2) {
+        const long long nb = neighbor<D>(A.g, c, d, side);
+        if (nb >= 0) {
+          lo = fmin(lo, L.mm[nb * 2 * NV + v]);
+          hi = fmax(hi, L.mm[nb * 2 * NV + NV + v]);
+        }
+      }
+    bnd[0][v] = lo;
+    bnd[1][v] = hi;
+  }
+  __syncthreads();
+  project_P<D, N>(us, t1, t2, sub, S);
+  bool ok = true;
+  for (int s = threadIdx.x; s < NSS; s += blockDim.x) {
+    const double* q = sub + s * NV;
+    ok = ok && admissible<D>(q, A.p.gamma);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double lo = bnd[0][v], hi = bnd[1][v];
+      const double delta = fmax(L.eps * (hi - lo), L.delta0);
+      const double x = q[v];
+      ok = ok && (x >= lo - delta) && (x <= hi + delta);
+    }
+  }
+  for (int j = threadIdx.x; j < NN; j += blockDim.x) ok = ok && admissible<D>(us + j * NV, A.p.gamma);
+  const bool all_ok = __syncthreads_and(ok) != 0;
+  const bool troubled = L.force ? true : !all_ok;
+  double* rn = L.rep_new + c * (NSS * NV);
+  for (int e = threadIdx.x; e < NSS * NV; e += blockDim.x) rn[e] = sub[e];
+  block_minmax<NSS, NV>(sub, L.mm_new + c * 2 * NV, red);
+  if (threadIdx.x == 0) {
+    L.flags[c] = troubled ? 1 : 0;
+    if (troubled) {
+      const int k = atomicAdd(&A.dev->n_troubled, 1);
+      L.list[k] = (int)c;
+    }
+  }
+}
+
+// Halo value of subcell (hx, hy, hz) in [-2, ns+2)^D of cell c from the t^n representations,
+// with the boundary conditions applied on the global subcell grid.
+template <int D, int N>
+__device__ __forceinline__ void halo_value(const Geometry& g, const double* rep, long long c,
+                                           const int* h, double* out) {
+  using C = CfgL<D, N>;
+  constexpr int ns = C::ns, NV = C::NV, NSS = C::NSS;
+  long long idx[3], rem = c;
+  for (int e = 0; e < 3; ++e) {
+    idx[e] = rem % g.n[e];
+    rem /= g.n[e];
+  }
+  bool flip[3] = {false, false, false};
+  long long owner[3];
+  int sidx[3] = {0, 0, 0};
+  for (int d = 0; d < 3; ++d) {
+    if (d >= D) {
+      owner[d] = 0;
+      continue;
+    }
+    const long long Nd = (long long)g.n[d] * ns;
+    long long gs = idx[d] * ns + h[d];
+    if (gs < 0) {
+      if (g.bc[d][0] == BC_PERIODIC) gs += Nd;
+      else {
+        gs = -1 - gs;
+        flip[d] = g.bc[d][0] == BC_WALL;
+      }
+    } else if (gs >= Nd) {
+      if (g.bc[d][1] == BC_PERIODIC) gs -= Nd;
+      else {
+        gs = 2 * Nd - 1 - gs;
+        flip[d] = g.bc[d][1] == BC_WALL;
+      }
+    }
+    owner[d] = gs / ns;
+    sidx[d] = (int)(gs % ns);
+  }
+  const long long oc = owner[0] + (long long)g.n[0] * (owner[1] + (long long)g.n[1] * owner[2]);
+  const int s = D == 3 ? sidx[0] + ns * (sidx[1] + ns * sidx[2]) : sidx[0] + ns * sidx[1];
+  const double* src = rep + (oc * NSS + s) * NV;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[v] = src[v];
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+    if (flip[d]) out[1 + d] = -out[1 + d];
+}
+
+__device__ __forceinline__ double minmod(double a, double b) {
+  return (a * b > 0.0) ? copysign(fmin(fabs(a), fabs(b)), a) : 0.0;
+}
+
+template <int D, int N>
+__global__ void __launch_bounds__(256) k_lim_fv(const __grid_constant__ StepArgs A,
+                                                const __grid_constant__ LimArgs L,
+                                                const __grid_constant__ SubTables S) {
+  using C = CfgL<D, N>;
+  using P = Euler<D>;
+  constexpr int ns = C::ns, NV = C::NV, NSS = C::NSS, NSF = C::NSF, NN = C::NN;
+  constexpr int W = ns + 4, WC = ns + 2;
+  extern __shared__ double sm[];
+  double* H = sm;                  // halo [W^D][NV]
+  double* INC = H + C::NH * NV;    // half-step increments of the core [WC^D][NV]
+  double* UN = INC + C::NC * NV;   // new subcell averages [NSS][NV]
+  double* t1 = UN + NSS * NV;
+  double* t2 = t1 + C::T1;
+  double* un = t2 + C::T2;         // reconstructed nodal values [NN][NV]
+  __shared__ double red[2 * NV * 32];
+  const double dt = A.dev->dt;
+  const int count = A.dev->n_troubled;
+  for (int it = blockIdx.x; it < count; it += gridDim.x) {
+    const long long c = L.list[it];
+    // halo
+    for (int e = threadIdx.x; e < C::NH; e += blockDim.x) {
+      int h[3] = {0, 0, 0};
+      int r = e;
+      for (int d = 0; d < D; ++d) {
+        h[d] = r % W - 2;
+        r /= W;
+      }
+      halo_value<D, N>(A.g, L.rep, c, h, H + e * NV);
+    }
+    __syncthreads();
+    // half-step increments on the core [-1, ns] (order of directions as in the oracle)
+    for (int e = threadIdx.x; e < C::NC; e += blockDim.x) {
+      int h[3] = {0, 0, 0};
+      int r = e;
+      for (int d = 0; d < D; ++d) {
+        h[d] = r % WC + 1;  // halo coordinate of the core cell
+        r /= WC;
+      }
+      int hi = 0, st = 1;
+      for (int d = 0; d < D; ++d) {
+        hi += h[d] * st;
+        st *= W;
+      }
+      const double* U = H + hi * NV;
+      double inc[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) inc[v] = 0.0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const int sd = d == 0 ? 1 : (d == 1 ? W : W * W);
+        double Up[NV], Um[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const double sg = minmod(U[v] - U[v - sd * NV], U[v + sd * NV] - U[v]);
+          Up[v] = U[v] + 0.5 * sg;
+          Um[v] = U[v] - 0.5 * sg;
+        }
+        typename P::Aux ap, am;
+        P::aux(Up, A.p, ap);
+        P::aux(Um, A.p, am);
+        double Fp[NV], Fm[NV];
+        P::flux(Up, ap, A.p, d, Fp);
+        P::flux(Um, am, A.p, d, Fm);
+        const double dx = A.g.h[d] / ns;
+        const double cf = dt / (2.0 * dx);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) inc[v] = inc[v] - cf * (Fp[v] - Fm[v]);
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) INC[e * NV + v] = inc[v];
+    }
+    __syncthreads();
+    // fluxes and update of the interior subcells
+    for (int e = threadIdx.x; e < NSS; e += blockDim.x) {
+      int s[3] = {0, 0, 0};
+      int r = e;
+      for (int d = 0; d < D; ++d) {
+        s[d] = r % ns;
+        r /= ns;
+      }
+      int hi = 0, ci = 0, st = 1, stc = 1;
+      for (int d = 0; d < D; ++d) {
+        hi += (s[d] + 2) * st;
+        ci += (s[d] + 1) * stc;
+        st *= W;
+        stc *= WC;
+      }
+      double Unew[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Unew[v] = H[hi * NV + v];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const int sd = d == 0 ? 1 : (d == 1 ? W : W * W);
+        const int sdc = d == 0 ? 1 : (d == 1 ? WC : WC * WC);
+        double fl[2][NV];  // flux at the left (k=0) and right (k=1) face of this subcell
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int hL = hi + (k - 1) * sd, hR = hi + k * sd;       // halo index of L and R cells
+          const int cL = ci + (k - 1) * sdc, cR = ci + k * sdc;     // core index of L and R
+          double QL[NV], QR[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const double* UL = H + hL * NV;
+            const double* UR = H + hR * NV;
+            const double sL = minmod(UL[v] - UL[v - sd * NV], UL[v + sd * NV] - UL[v]);
+            const double sR = minmod(UR[v] - UR[v - sd * NV], UR[v + sd * NV] - UR[v]);
+            QL[v] = (UL[v] + 0.5 * sL) + INC[cL * NV + v];
+            QR[v] = (UR[v] - 0.5 * sR) + INC[cR * NV + v];
+          }
+          typename P::Aux aL, aR;
+          P::aux(QL, A.p, aL);
+          P::aux(QR, A.p, aR);
+          double FL[NV], FR[NV];
+          P::flux(QL, aL, A.p, d, FL);
+          P::flux(QR, aR, A.p, d, FR);
+          const double sp = fmax(P::speed(QL, A.p, d), P::speed(QR, A.p, d));
+#pragma unroll
+          for (int v = 0; v < NV; ++v) fl[k][v] = 0.5 * (FL[v] + FR[v]) - 0.5 * sp * (QR[v] - QL[v]);
+        }
+        const double dx = A.g.h[d] / ns;
+        const double cf = dt / dx;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Unew[v] = Unew[v] + cf * (fl[0][v] - fl[1][v]);
+        // boundary subface fluxes: transverse index of the face = s with digit d removed
+        int tr = 0, stt = 1;
+        for (int e2 = 0; e2 < D; ++e2)
+          if (e2 != d) {
+            tr += s[e2] * stt;
+            stt *= ns;
+          }
+        double* bf = L.bflux + ((c * D + d) * 2) * (long long)(NSF * NV);
+        if (s[d] == 0)
+          for (int v = 0; v < NV; ++v) bf[tr * NV + v] = fl[0][v];
+        if (s[d] == ns - 1)
+          for (int v = 0; v < NV; ++v) bf[NSF * NV + tr * NV + v] = fl[1][v];
+      }
+      bool ok = admissible<D>(Unew, A.p.gamma);
+      if (!ok) atomicOr(&A.dev->status, ST_ADMISSIBLE);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) UN[e * NV + v] = Unew[v];
+    }
+    __syncthreads();
+    double* rn = L.rep_new + c * (NSS * NV);
+    for (int e = threadIdx.x; e < NSS * NV; e += blockDim.x) rn[e] = UN[e];
+    block_minmax<NSS, NV>(UN, L.mm_new + c * 2 * NV, red);
+    reconstruct_R<D, N>(UN, t1, t2, un, S);
+    double* uo = A.u_next + c * (NN * NV);
+    for (int e = threadIdx.x; e < NN * NV; e += blockDim.x) uo[e] = un[e];
+    __syncthreads();
+  }
+}
+
+// Neighbour fix: for an untroubled cell with troubled face neighbours.
+template <int D, int N>
+__global__ void __launch_bounds__(128) k_lim_fix(const __grid_constant__ StepArgs A,
+                                                 const __grid_constant__ LimArgs L,
+                                                 const __grid_constant__ Tables T,
+                                                 const __grid_constant__ SubTables S,
+                                                 long long off1, long long off2) {
+  using C = CfgL<D, N>;
+  constexpr int n = C::n, ns = C::ns, NV = C::NV, NN = C::NN, NSS = C::NSS, NSF = C::NSF;
+  constexpr int NF = ipow(n, D - 1);
+  const long long c = blockIdx.x;
+  if (L.flags[c]) return;
+  long long nbs[3][2];
+  bool any = false;
+  for (int d = 0; d < D; ++d)
+    for (int k = 0; k < 2; ++k) {
+      const long long nb = neighbor<D>(A.g, c, d, k ? 1 : -1);
+      nbs[d][k] = (nb >= 0 && L.flags[nb]) ? nb : -1;
+      any = any || nbs[d][k] >= 0;
+    }
+  if (!any) return;  // uniform per block
+  extern __shared__ double sm[];
+  double* us = sm;
+  double* t1 = us + NN * NV;
+  double* t2 = t1 + C::T1;
+  double* sub = t2 + C::T2;
+  double* geff = sub + NSS * NV;  // [NF][NV]
+  __shared__ double red[2 * NV * 32];
+  double* u = A.u_next + c * (NN * NV);
+  for (int e = threadIdx.x; e < NN * NV; e += blockDim.x) us[e] = u[e];
+  __syncthreads();
+  const double dt = A.dev->dt;
+  for (int d = 0; d < D; ++d) {
+    for (int kk = 0; kk < 2; ++kk) {
+      const int k = 1 - kk;  // right face first, then left (order of the oracle)
+      const long long nb = nbs[d][k];
+      if (nb < 0) continue;
+      // subface fluxes of the troubled neighbour on the shared face (its opposite side)
+      const double* f = L.bflux + ((nb * D + d) * 2 + (k ? 0 : 1)) * (long long)(NSF * NV);
+      // G_eff[j][v] = prod over transverse axes (1/(ns w_je)) sum_s P1[s][je] f[s][v]
+      for (int e = threadIdx.x; e < NF * NV; e += blockDim.x) {
+        const int v = e % NV, jp = e / NV;
+        const int j0 = jp % n, j1 = jp / n;
+        double acc = 0.0;
+        if constexpr (D == 2) {
+          for (int s0 = 0; s0 < ns; ++s0) acc = fma(S.P1[s0][j0], f[s0 * NV + v], acc);
+          acc = acc / ns / T.w[j0];
+        } else {
+          for (int s1 = 0; s1 < ns; ++s1) {
+            double a0 = 0.0;
+            for (int s0 = 0; s0 < ns; ++s0) a0 = fma(S.P1[s0][j0], f[(s1 * ns + s0) * NV + v], a0);
+            acc = fma(S.P1[s1][j1], a0, acc);
+          }
+          acc = acc / ns / T.w[j0] / ns / T.w[j1];
+        }
+        geff[e] = acc;
+      }
+      __syncthreads();
+      // DG flux on that face and the correction of the nodal values
+      int id;
+      const long long tr = FaceIdx::trans_of_cell(A.g, c, d, id);
+      const int nd = A.g.n[d];
+      int kf = k ? id + 1 : id;
+      if (k && kf == nd && A.g.bc[d][1] == BC_PERIODIC) kf = 0;
+      const long long off = d == 0 ? 0 : (d == 1 ? off1 : off2);
+      const double* phi = A.phi + off + (kf + (long long)(nd + 1) * tr) * (NF * NV);
+      const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
+      for (int e = threadIdx.x; e < NN * NV; e += blockDim.x) {
+        const int v = e % NV, j = e / NV;
+        const int jd = (j / st) % n;
+        const int jp = (j % st) + (j / (st * n)) * st;
+        const double g = geff[jp * NV + v] - phi[jp * NV + v];
+        const double corr = k ? -dt / A.g.h[d] * T.c1[jd] * g : dt / A.g.h[d] * T.c0[jd] * g;
+        us[e] = us[e] + corr;
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = threadIdx.x; e < NN * NV; e += blockDim.x) u[e] = us[e];
+  project_P<D, N>(us, t1, t2, sub, S);
+  double* rn = L.rep_new + c * (NSS * NV);
+  for (int e = threadIdx.x; e < NSS * NV; e += blockDim.x) rn[e] = sub[e];
+  block_minmax<NSS, NV>(sub, L.mm_new + c * 2 * NV, red);
+}
+
+// rep = P(u) for every cell (reset of the limiter history); flagged cells keep the given U_sub
+// and get u = R(U_sub).
+template <int D, int N>
+__global__ void __launch_bounds__(128) k_lim_init(double* u, const double* Usub,
+                                                  const uint8_t* flags, double* rep, double* mm,
+                                                  const __grid_constant__ SubTables S) {
+  using C = CfgL<D, N>;
+  constexpr int NV = C::NV, NN = C::NN, NSS = C::NSS;
+  extern __shared__ double sm[];
+  double* us = sm;
+  double* t1 = us + NN * NV;
+  double* t2 = t1 + C::T1;
+  double* sub = t2 + C::T2;
+  __shared__ double red[2 * NV * 32];
+  const long long c = blockIdx.x;
+  double* uc = u + c * (NN * NV);
+  const bool fl = flags && flags[c];
+  if (fl) {
+    const double* U = Usub + c * (NSS * NV);
+    for (int e = threadIdx.x; e < NSS * NV; e += blockDim.x) sub[e] = U[e];
+    __syncthreads();
+    reconstruct_R<D, N>(sub, t1, t2, us, S);
+    for (int e = threadIdx.x; e < NN * NV; e += blockDim.x) uc[e] = us[e];
+  } else {
+    for (int e = threadIdx.x; e < NN * NV; e += blockDim.x) us[e] = uc[e];
+    __syncthreads();
+    project_P<D, N>(us, t1, t2, sub, S);
+  }
+  double* r = rep + c * (NSS * NV);
+  for (int e = threadIdx.x; e < NSS * NV; e += blockDim.x) r[e] = sub[e];
+  block_minmax<NSS, NV>(sub, mm + c * 2 * NV, red);
+}
+
+// ---- launchers -----------------------------------------------------------------------------
+template <int D, int N>
+struct LimLaunch {
+  using C = CfgL<D, N>;
+  static size_t smem_fix() { return C::SMEM_P + (size_t)ipow(N + 1, D - 1) * C::NV * sizeof(double); }
+  static cudaError_t init(double* u, const double* Usub, const uint8_t* flags, double* rep,
+                          double* mm, long long ncells, const SubTables& S, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_lim_init<D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)C::SMEM_P);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    k_lim_init<D, N><<<(unsigned)ncells, C::TPB, C::SMEM_P, s>>>(u, Usub, flags, rep, mm, S);
+    return cudaGetLastError();
+  }
+  static cudaError_t step(const StepArgs& a, const LimArgs& l, const Tables& T, const SubTables& S,
+                          cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_lim_detect<D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)C::SMEM_P);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_lim_fv<D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)C::SMEM_FV);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_lim_fix<D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_fix());
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    const unsigned nc = (unsigned)a.g.ncells;
+    k_lim_detect<D, N><<<nc, C::TPB, C::SMEM_P, s>>>(a, l, S);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_lim_fv<D, N><<<152 * 2, 256, C::SMEM_FV, s>>>(a, l, S);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    long long offs[3] = {0, 0, 0}, off = 0;
+    const int nf = ipow(N + 1, D - 1);
+    for (int d = 0; d < D; ++d) {
+      offs[d] = off;
+      off += (long long)(a.g.n[d] + 1) * (a.g.ncells / a.g.n[d]) * nf * C::NV;
+    }
+    k_lim_fix<D, N><<<nc, C::TPB, smem_fix(), s>>>(a, l, T, S, offs[1], offs[2]);
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace ader

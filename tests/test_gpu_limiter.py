@@ -1,0 +1,113 @@
+"""GPU parity of the a-posteriori subcell limiter (Sec. 3.5) against the oracle: troubled-cell
+flags bit-identical, states within relative 1e-12 per step (teacher forcing: both sides start
+every step from the oracle's state and representation), free-running runs, the pure FV mode,
+and conservation."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.limiter import Limiter
+from paper_1905_07987_gb300 import synth
+from cases import Case, rel_linf
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _build():
+    from paper_1905_07987_gb300 import build
+    build.build()
+
+
+def explosion_case(ncell, order, limiter=1, bc="wall"):
+    dim = len(ncell)
+    c = Case("euler", dim, order, ncell, lo=(-1.0,) * dim, hi=(1.0,) * dim, bc=bc, limiter=limiter)
+    lim = Limiter(c.oracle)
+    u0 = synth.explosion(c.X)
+    Us = synth.explosion(synth.subcell_centres(lim.ns, c.ncell, c.lo, c.hi))
+    flags = synth.discontinuous_cells(Us)
+    u, rep = lim.initial_rep(torch.from_numpy(u0), torch.from_numpy(Us), torch.from_numpy(flags))
+    return c, lim, u0, Us, flags, u, rep
+
+
+def gpu_set(c, u_nodal_before_init, Us, flags):
+    c.set(u_nodal_before_init)
+    c.ctx.set_subcell_state(torch.from_numpy(np.ascontiguousarray(Us).reshape(-1)).cuda(),
+                            torch.from_numpy(flags.astype(np.uint8)).cuda())
+
+
+def gpu_rep(c, lim):
+    out = torch.empty(c.ctx.cells * lim.ns ** c.dim * c.ctx.nvar, dtype=torch.float64, device="cuda")
+    c.ctx.get_subcell_state(out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().reshape((c.ctx.cells,) + (lim.ns,) * c.dim + (c.ctx.nvar,))
+
+
+@pytest.mark.parametrize("dim,ncell,order", [(2, (10, 10), 2), (2, (9, 8), 3), (3, (6, 6, 6), 3),
+                                             (3, (5, 4, 6), 2), (3, (4, 4, 4), 4)])
+def test_limited_steps_teacher_forced(dim, ncell, order):
+    c, lim, u0, Us, flags, u, rep = explosion_case(ncell, order)
+    gpu_set(c, u0, Us, flags)
+    # the initial FV cells: identical state and representation on both sides
+    assert rel_linf(c.get(), u.numpy()) <= TOL
+    assert rel_linf(gpu_rep(c, lim), rep.numpy()) <= TOL
+    prev = torch.from_numpy(flags)
+    t = 0.0
+    for step in range(3):
+        if step > 0:  # teacher forcing: restart the GPU from the oracle's state
+            gpu_set(c, u.numpy(), rep.numpy(), prev.numpy())
+            # set_state reset u of flagged cells to R(rep): same as the oracle's u for those cells
+        c.ctx.set_time(t)
+        c.ctx.step()
+        dt = c.ctx.last_dt()
+        u, tr, rep, ok = lim.step(u, rep, torch.tensor(dt, dtype=torch.float64), t)
+        assert ok
+        fl = np.zeros(c.ctx.cells, dtype=np.uint8)
+        fl[:] = c.ctx.flags()
+        assert np.array_equal(fl.astype(bool), tr.numpy()), step
+        assert c.ctx.troubled_count() == int(tr.sum())
+        assert rel_linf(c.get(), u.numpy()) <= TOL, step
+        assert rel_linf(gpu_rep(c, lim), rep.numpy()) <= TOL, step
+        prev = tr
+        t += dt
+
+
+def test_limited_free_run_flags_identical_every_step():
+    c, lim, u0, Us, flags, u, rep = explosion_case((12, 12), 3)
+    gpu_set(c, u0, Us, flags)
+    for step in range(12):
+        c.ctx.step()
+        dt = c.ctx.last_dt()
+        u, tr, rep, ok = lim.step(u, rep, torch.tensor(dt, dtype=torch.float64))
+        assert np.array_equal(c.ctx.flags().astype(bool), tr.numpy()), step
+    assert rel_linf(c.get(), u.numpy()) <= 1e-11
+
+
+def test_pure_fv_mode_matches_forced_oracle():
+    c, lim, u0, Us, flags, u, rep = explosion_case((6, 5, 4), 2, limiter=2)
+    gpu_set(c, u0, Us, flags)
+    c.ctx.step()
+    dt = c.ctx.last_dt()
+    u1, tr, rep1, ok = lim.step(u, rep, torch.tensor(dt, dtype=torch.float64), force=True)
+    assert c.ctx.flags().all() and tr.all()
+    assert rel_linf(c.get(), u1.numpy()) <= TOL
+    assert rel_linf(gpu_rep(c, lim), rep1.numpy()) <= TOL
+
+
+def test_limited_run_conserves_mass_and_energy():
+    c, lim, u0, Us, flags, u, rep = explosion_case((8, 8, 8), 3)
+    gpu_set(c, u0, Us, flags)
+    W = c.oracle.tensor_basis_weights().numpy()
+    vol = np.prod(c.oracle.grid.h)
+
+    def tot(x):
+        return (x * W[None, ..., None]).reshape(-1, x.shape[-1]).sum(0) * vol if False else \
+            np.einsum('c...v,...->v', x, W) * vol
+
+    m0 = tot(c.get())
+    c.ctx.run(10)
+    m1 = tot(c.get())
+    assert abs(m1[0] - m0[0]) < 1e-13 * abs(m0[0])
+    assert abs(m1[4] - m0[4]) < 1e-13 * abs(m0[4])
+    assert c.ctx.troubled_count() > 0

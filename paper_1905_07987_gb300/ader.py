@@ -150,7 +150,7 @@ def make_config(pde, dim, order, ncell, lo, hi, bc, cfl, gamma=1.4, adv=(0.0, 0.
     for d in range(3):
         c.adv[d] = float(adv[d]) if d < len(adv) else 0.0
     c.picard_iters = int(picard_iters)
-    c.limiter = 1 if limiter else 0
+    c.limiter = int(limiter)
     c.precision = PREC[precision] if isinstance(precision, str) else int(precision)
     return c
 

@@ -102,8 +102,7 @@ def test_limited_run_conserves_mass_and_energy():
     vol = np.prod(c.oracle.grid.h)
 
     def tot(x):
-        return (x * W[None, ..., None]).reshape(-1, x.shape[-1]).sum(0) * vol if False else \
-            np.einsum('c...v,...->v', x, W) * vol
+        return (x * W[None, ..., None]).reshape(-1, x.shape[-1]).sum(0) * vol
 
     m0 = tot(c.get())
     c.ctx.run(10)

@@ -158,6 +158,26 @@ ader_status ader_sync(ader_ctx* ctx);
  * the same.  Does not synchronise. */
 ader_status ader_run_graph(ader_ctx* ctx, int steps, int replays, double dt, double t_end);
 
+/* Adjoint of one linear-elastic step (elastic contexts, order <= 5).  With a fixed dt the step
+ * u^{n+1} = A(m) u^n + b^n(M, m) is affine (Eq. (5) predictor, Rusanov faces, Eq. (6) corrector,
+ * moment-tensor point source of Eq. (1)); this call maps lam = lambda^{n+1} to
+ *     lambda^n = A(m)^T lambda^{n+1} + dJdu   (in place in `lam`)
+ * and accumulates  grad_mat[c][0..2] += d/d(rho, lambda, mu)_c of (lambda^{n+1})^T u^{n+1}  and
+ * grad_M[0..5] += d/dM of the same, evaluated at the forward state u_n = u^n with the step
+ * starting at time t_n.  The wave speed max(vp_L, vp_R) of a face takes the left value at ties.
+ * All pointers are device memory of the context's device ([cells][nodes][9] for u_n, lam, dJdu;
+ * [cells][3]; [6]); dJdu may be NULL.  Uses the context's material, point source and order; the
+ * context's own state and time are not touched.  Stream-ordered, no synchronisation.  The first
+ * call allocates its work buffers (ADER_ENOMEM if that fails). */
+ader_status ader_adjoint_step(ader_ctx* ctx, double t_n, double dt, const double* u_n, double* lam,
+                              const double* dJdu, double* grad_mat, double* grad_M);
+
+/* Transpose of the receiver read-out: dJdu[cell_r][j][v] += scale * res[r][v] * Phi_j(x_r) for the
+ * velocity components v = 0..2 of every receiver r (res: device [nrec][3]; dJdu: device state-sized,
+ * accumulated).  With res = seismogram - observation and scale = dt this is the derivative of the
+ * misfit 1/2 dt sum |v(x_r) - obs|^2 with respect to the state that was recorded. */
+ader_status ader_receivers_adjoint(ader_ctx* ctx, const double* res, double scale, double* dJdu);
+
 /* Per-phase device timing.  While enabled, every ader_step records CUDA events on the context's
  * stream around its phases: 0 CFL speed reduction, 1 dt finalisation, 2 predictor, 3 Riemann,
  * 4 corrector, 5 limiter, 6 receivers and time advance.  ader_phase_times synchronises, writes

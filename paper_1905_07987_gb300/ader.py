@@ -71,6 +71,8 @@ _SIGS = {
     "ader_run_graph": ([_P, _I, _I, _D, _D], _I),
     "ader_set_subcell_state": ([_P, _P, _P, _I], _I),
     "ader_get_subcell_state": ([_P, _P, _I], _I),
+    "ader_adjoint_step": ([_P, _D, _D, _P, _P, _P, _P, _P], _I),
+    "ader_receivers_adjoint": ([_P, _P, _D, _P], _I),
     "ader_enable_timing": ([_P, _I], _I),
     "ader_phase_times": ([_P, _P, ctypes.POINTER(_I)], _I),
 }
@@ -235,6 +237,29 @@ class Context:
         p, dev, keep, n = _ptr(out)
         check(lib().ader_get_subcell_state(self._h, p, dev), "ader_get_subcell_state")
         return out
+
+    def adjoint_step(self, t_n, dt, u_n, lam, grad_mat, grad_M, dJdu=None):
+        """lam <- A^T lam (+ dJdu) for the step from t_n with fixed dt at forward state u_n;
+        accumulates grad_mat [cells,3] and grad_M [6].  All CUDA float64 tensors."""
+        ptrs = []
+        for a in (u_n, lam, grad_mat, grad_M) + ((dJdu,) if dJdu is not None else ()):
+            p, dev, keep, n = _ptr(a)
+            if not dev:
+                raise ValueError("adjoint buffers must be device tensors")
+            ptrs.append(p)
+        if lam.numel() != self.count or u_n.numel() != self.count or grad_mat.numel() != 3 * self.cells \
+                or grad_M.numel() != 6 or (dJdu is not None and dJdu.numel() != self.count):
+            raise ValueError("adjoint buffer sizes")
+        dj = ptrs[4] if dJdu is not None else None
+        check(lib().ader_adjoint_step(self._h, float(t_n), float(dt), ptrs[0], ptrs[1], dj, ptrs[2], ptrs[3]),
+              "ader_adjoint_step")
+
+    def receivers_adjoint(self, res, scale, dJdu):
+        p, dev, keep, n = _ptr(res)
+        q, dev2, keep2, n2 = _ptr(dJdu)
+        if not (dev and dev2) or n2 != self.count:
+            raise ValueError("receiver adjoint buffers must be device tensors of the right size")
+        check(lib().ader_receivers_adjoint(self._h, p, float(scale), q), "ader_receivers_adjoint")
 
     def set_time(self, t):
         check(lib().ader_set_time(self._h, float(t)), "ader_set_time")

@@ -62,6 +62,7 @@ struct SubTables {
 };
 
 struct LimArgs;
+struct AdjArgs;
 
 struct Geometry {
   int dim, order;
@@ -124,7 +125,14 @@ struct Family {
                           cudaStream_t s);
   cudaError_t (*lim_step)(const StepArgs&, const LimArgs&, const Tables&, const SubTables&,
                           cudaStream_t);
+  // adjoint of the linear elastic step (elastic only; null otherwise)
+  cudaError_t (*adj_run)(const StepArgs&, const AdjArgs&, const Tables&, int blocks, cudaStream_t);
+  long long (*adj_scratch_per_block)(int order, int iters);
+  int (*adj_blocks_per_sm)(int order);
 };
+cudaError_t launch_set_scalars(DevScalars* d, double t, double dt, cudaStream_t s);
+cudaError_t launch_receivers_adjoint(const Receivers& r, const double* res, double scale,
+                                     double* dJdu, int nodes, int nvar, cudaStream_t s);
 
 const Family* family_advection2();
 const Family* family_advection3();

@@ -10,6 +10,17 @@
 #include "ader_internal.h"
 
 namespace ader {
+struct AdjArgs {
+  const double* u_n;
+  double* lam;
+  const double* dJdu;
+  double* grad_mat;
+  double* grad_M;
+  double* adjf;
+  double* gface;
+  double* scratch;
+  long long scratch_per_block;
+};
 struct LimArgs {
   const double* rep;
   double* rep_new;
@@ -291,6 +302,11 @@ struct ader_ctx {
   uint8_t* flags = nullptr;
   int* list = nullptr;
   long long nss = 0;
+  // adjoint work buffers (allocated on the first ader_adjoint_step)
+  DevScalars* dev_adj = nullptr;
+  double *adjf = nullptr, *gface = nullptr, *adj_scratch = nullptr;
+  int adj_blocks = 0;
+  long long adj_spb = 0;
   long long nodes = 0, nvar = 0, ndof = 0;
   int nf = 0;
   double* u = nullptr;
@@ -333,6 +349,10 @@ static ader_status latched(int bits) {
 }
 
 static void free_all(ader_ctx* c) {
+  cudaFree(c->dev_adj);
+  cudaFree(c->adjf);
+  cudaFree(c->gface);
+  cudaFree(c->adj_scratch);
   cudaFree(c->rep);
   cudaFree(c->rep_new);
   cudaFree(c->mm);
@@ -806,6 +826,57 @@ ader_status ader_troubled_count(ader_ctx* c, int64_t* count) {
     if (st != ADER_OK) return st;
   }
   *count = n;
+  return ADER_OK;
+}
+
+ader_status ader_adjoint_step(ader_ctx* c, double t_n, double dt, const double* u_n, double* lam,
+                              const double* dJdu, double* grad_mat, double* grad_M) {
+  if (!c || !u_n || !lam || !grad_mat || !grad_M || !(dt > 0.0)) return ADER_EINVAL;
+  if (c->cfg.pde != ADER_PDE_ELASTIC || !c->fam->adj_run) return ADER_EUNSUPPORTED;
+  if (c->cfg.order > 5) return ADER_EUNSUPPORTED;
+  if (!c->mat_set) return ADER_ESTATE;
+  const int iters = c->cfg.picard_iters > 0 ? c->cfg.picard_iters : c->cfg.order + 1;
+  if (!c->dev_adj) {
+    int dev = 0, sms = 0;
+    CUDA_OK(cudaGetDevice(&dev));
+    CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    c->adj_blocks = sms * c->fam->adj_blocks_per_sm(c->cfg.order);
+    c->adj_spb = c->fam->adj_scratch_per_block(c->cfg.order, iters);
+    long long nfaces = 0;
+    for (int d = 0; d < 3; ++d) nfaces += (long long)(c->g.n[d] + 1) * (c->g.ncells / c->g.n[d]);
+    cudaError_t e = cudaMalloc(&c->dev_adj, sizeof(DevScalars));
+    if (e == cudaSuccess) e = cudaMalloc(&c->adjf, (size_t)c->g.ncells * 3 * 2 * c->nf * c->nvar * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->gface, (size_t)nfaces * 6 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->adj_scratch, (size_t)c->adj_blocks * c->adj_spb * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(c->dev_adj);
+      cudaFree(c->adjf);
+      cudaFree(c->gface);
+      cudaFree(c->adj_scratch);
+      c->dev_adj = nullptr;
+      c->adjf = c->gface = c->adj_scratch = nullptr;
+      return e == cudaErrorMemoryAllocation ? ADER_ENOMEM : ADER_ECUDA;
+    }
+    CUDA_OK(cudaMemsetAsync(c->dev_adj, 0, sizeof(DevScalars), c->stream));
+  }
+  CUDA_OK(launch_set_scalars(c->dev_adj, t_n, dt, c->stream));
+  StepArgs a = make_args(c, dt, 0.0);
+  a.u = u_n;
+  a.dev = c->dev_adj;
+  a.iters = iters;
+  // forward face data of the step from u^n (the predictor also writes the scratch next state)
+  CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
+  AdjArgs j{u_n, lam, dJdu, grad_mat, grad_M, c->adjf, c->gface, c->adj_scratch, c->adj_spb};
+  CUDA_OK(c->fam->adj_run(a, j, c->tab, c->adj_blocks, c->stream));
+  return ADER_OK;
+}
+
+ader_status ader_receivers_adjoint(ader_ctx* c, const double* res, double scale, double* dJdu) {
+  if (!c || !res || !dJdu) return ADER_EINVAL;
+  if (c->cfg.pde != ADER_PDE_ELASTIC) return ADER_EUNSUPPORTED;
+  if (c->rec.nrec <= 0) return ADER_ESTATE;
+  CUDA_OK(launch_receivers_adjoint(c->rec, res, scale, dJdu, (int)c->nodes, (int)c->nvar, c->stream));
   return ADER_OK;
 }
 

@@ -66,6 +66,37 @@ __global__ void k_receivers(const double* __restrict__ u, DevScalars* s, Receive
   }
 }
 
+__global__ void k_set_scalars(DevScalars* d, double t, double dt) {
+  d->t = t;
+  d->dt = dt;
+}
+
+// dJ/du[cell_r][j][v] += scale * res[r][v] * Phi_j(xi_r), receivers in order (deterministic: each
+// thread owns one (node, component) slot).
+__global__ void k_receivers_adjoint(Receivers r, const double* res, double scale, double* dJdu,
+                                    int nodes, int nvar) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nodes * 3) return;
+  const int j = e / 3, v = e % 3;
+  for (int k = 0; k < r.nrec; ++k) {
+    double* dst = dJdu + ((long long)r.cell[k] * nodes + j) * nvar + v;
+    *dst = fma(scale * res[k * 3 + v], r.phi[(long long)k * nodes + j], *dst);
+  }
+}
+
+cudaError_t launch_set_scalars(DevScalars* d, double t, double dt, cudaStream_t s) {
+  k_set_scalars<<<1, 1, 0, s>>>(d, t, dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_receivers_adjoint(const Receivers& r, const double* res, double scale,
+                                     double* dJdu, int nodes, int nvar, cudaStream_t s) {
+  if (r.nrec <= 0) return cudaSuccess;
+  const int tot = nodes * 3;
+  k_receivers_adjoint<<<(tot + 127) / 128, 128, 0, s>>>(r, res, scale, dJdu, nodes, nvar);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dt_finalize(const StepArgs& a, cudaStream_t s) {
   k_dt_finalize<<<1, 1, 0, s>>>(a);
   return cudaGetLastError();

@@ -652,8 +652,8 @@ struct FamilyImpl {
   }
   static size_t smem(int order, int prec);
   static const Family* get() {
-    static const Family f = {P::NV, P::CONS, &cfl, &predictor, &riemann, &corrector, &smem,
-                             nullptr, nullptr};
+    static const Family f = {P::NV, P::CONS, &cfl,    &predictor, &riemann, &corrector, &smem,
+                             nullptr, nullptr, nullptr, nullptr,   nullptr};
     return &f;
   }
 };

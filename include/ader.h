@@ -178,6 +178,20 @@ ader_status ader_adjoint_step(ader_ctx* ctx, double t_n, double dt, const double
  * misfit 1/2 dt sum |v(x_r) - obs|^2 with respect to the state that was recorded. */
 ader_status ader_receivers_adjoint(ader_ctx* ctx, const double* res, double scale, double* dJdu);
 
+/* Receiver misfit and its gradient by the adjoint method with checkpointing (elastic contexts
+ * with receivers set).  Runs `steps` forward steps of fixed size dt from the device state u0 at
+ * time t0, recording the receiver velocities after every step, and evaluates
+ *     J = 1/2 dt sum_k sum_r |v_r(u^{k+1}) - obs[k][r]|^2      (obs: device [steps][nrec][3]).
+ * If grad_mat or grad_M is non-NULL it then runs the adjoint sweep: the state of every k_ckpt-th
+ * step is kept on the device, each segment is recomputed from its checkpoint, and
+ * ader_adjoint_step is applied backwards, writing dJ/d(rho, lambda, mu) per cell to grad_mat
+ * (device [cells][3], overwritten) and dJ/dM to grad_M (device [6], overwritten).  J is written
+ * to host memory.  Allocates (steps/k_ckpt + k_ckpt + 1) states of work memory for the call.
+ * Synchronises.  The context's state afterwards is unspecified (set it again before stepping). */
+ader_status ader_misfit_gradient(ader_ctx* ctx, const double* u0, double t0, double dt, int steps,
+                                 int k_ckpt, const double* obs, double* J, double* grad_mat,
+                                 double* grad_M);
+
 /* Per-phase device timing.  While enabled, every ader_step records CUDA events on the context's
  * stream around its phases: 0 CFL speed reduction, 1 dt finalisation, 2 predictor, 3 Riemann,
  * 4 corrector, 5 limiter, 6 receivers and time advance.  ader_phase_times synchronises, writes

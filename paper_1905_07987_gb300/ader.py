@@ -73,6 +73,7 @@ _SIGS = {
     "ader_get_subcell_state": ([_P, _P, _I], _I),
     "ader_adjoint_step": ([_P, _D, _D, _P, _P, _P, _P, _P], _I),
     "ader_receivers_adjoint": ([_P, _P, _D, _P], _I),
+    "ader_misfit_gradient": ([_P, _P, _D, _D, _I, _I, _P, ctypes.POINTER(_D), _P, _P], _I),
     "ader_enable_timing": ([_P, _I], _I),
     "ader_phase_times": ([_P, _P, ctypes.POINTER(_I)], _I),
 }
@@ -260,6 +261,17 @@ class Context:
         if not (dev and dev2) or n2 != self.count:
             raise ValueError("receiver adjoint buffers must be device tensors of the right size")
         check(lib().ader_receivers_adjoint(self._h, p, float(scale), q), "ader_receivers_adjoint")
+
+    def misfit_gradient(self, u0, t0, dt, steps, k_ckpt, obs, grad_mat=None, grad_M=None):
+        """(J, grad_mat, grad_M) of the receiver misfit (device tensors in and out)."""
+        J = _D()
+        pu = _ptr(u0)
+        po = _ptr(obs)
+        gm = _ptr(grad_mat)[0] if grad_mat is not None else None
+        gM = _ptr(grad_M)[0] if grad_M is not None else None
+        check(lib().ader_misfit_gradient(self._h, pu[0], float(t0), float(dt), int(steps), int(k_ckpt),
+                                         po[0], ctypes.byref(J), gm, gM), "ader_misfit_gradient")
+        return J.value
 
     def set_time(self, t):
         check(lib().ader_set_time(self._h, float(t)), "ader_set_time")

@@ -131,6 +131,9 @@ struct Family {
   int (*adj_blocks_per_sm)(int order);
 };
 cudaError_t launch_set_scalars(DevScalars* d, double t, double dt, cudaStream_t s);
+cudaError_t launch_sub(const double* a, const double* b, double* out, int n, cudaStream_t s);
+cudaError_t launch_misfit(const double* a, const double* b, long long n, double scale, double* J,
+                          cudaStream_t s);
 cudaError_t launch_receivers_adjoint(const Receivers& r, const double* res, double scale,
                                      double* dJdu, int nodes, int nvar, cudaStream_t s);
 

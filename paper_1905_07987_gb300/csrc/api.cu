@@ -2,6 +2,7 @@
 // buffers, the per-step kernel sequence and CUDA-graph replay.
 #include <cmath>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -374,6 +375,23 @@ static void free_all(ader_ctx* c) {
   cudaFree(c->rec_cell);
   cudaFree(c->rec_phi);
 }
+
+// RAII list of device buffers for the checkpointed driver.
+struct DevBufs {
+  std::vector<void*> p;
+  ~DevBufs() {
+    for (void* q : p) cudaFree(q);
+  }
+  template <typename T>
+  cudaError_t alloc(T** out, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e == cudaSuccess) p.push_back(q);
+    *out = (T*)q;
+    return e;
+  }
+};
+
 
 extern "C" {
 
@@ -878,6 +896,79 @@ ader_status ader_receivers_adjoint(ader_ctx* c, const double* res, double scale,
   if (c->rec.nrec <= 0) return ADER_ESTATE;
   CUDA_OK(launch_receivers_adjoint(c->rec, res, scale, dJdu, (int)c->nodes, (int)c->nvar, c->stream));
   return ADER_OK;
+}
+
+ader_status ader_misfit_gradient(ader_ctx* c, const double* u0, double t0, double dt, int steps,
+                                 int k_ckpt, const double* obs, double* J, double* grad_mat,
+                                 double* grad_M) {
+  if (!c || !u0 || !obs || !J || steps < 1 || k_ckpt < 1 || !(dt > 0.0)) return ADER_EINVAL;
+  if (c->cfg.pde != ADER_PDE_ELASTIC) return ADER_EUNSUPPORTED;
+  if (!c->mat_set || c->rec.nrec <= 0) return ADER_ESTATE;
+  const size_t nd = (size_t)c->ndof;
+  const int nrec = c->rec.nrec;
+  const int nseg = (steps + k_ckpt - 1) / k_ckpt;
+  DevBufs B;
+  double *ckpt, *seg, *lam, *seismo, *res, *Jd;
+  cudaError_t e = B.alloc(&ckpt, nd * nseg);
+  if (e == cudaSuccess) e = B.alloc(&seg, nd * (size_t)k_ckpt);
+  if (e == cudaSuccess) e = B.alloc(&lam, nd);
+  if (e == cudaSuccess) e = B.alloc(&seismo, (size_t)steps * nrec * 3);
+  if (e == cudaSuccess) e = B.alloc(&res, (size_t)nrec * 3);
+  if (e == cudaSuccess) e = B.alloc(&Jd, 1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? ADER_ENOMEM : ADER_ECUDA;
+  }
+  const Receivers saved = c->rec;
+  ader_status st = ADER_OK;
+  // ---- forward sweep with a checkpoint every k steps -------------------------------------
+  c->rec.seismo = seismo;
+  c->rec.max_rows = steps;
+  long long zero = 0;
+  CUDA_OK(cudaMemcpyAsync(&c->dev->seismo_row, &zero, sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+  CUDA_OK(cudaMemcpyAsync(c->u, u0, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  c->state_set = true;
+  CUDA_OK(launch_set_scalars(c->dev, t0, dt, c->stream));
+  for (int n = 0; n < steps && st == ADER_OK; ++n) {
+    if (n % k_ckpt == 0)
+      CUDA_OK(cudaMemcpyAsync(ckpt + (size_t)(n / k_ckpt) * nd, c->u, nd * sizeof(double),
+                              cudaMemcpyDeviceToDevice, c->stream));
+    st = step_impl(c, dt, 0.0);
+  }
+  if (st == ADER_OK) {
+    CUDA_OK(launch_misfit(seismo, obs, (long long)steps * nrec * 3, dt, Jd, c->stream));
+    CUDA_OK(cudaMemcpyAsync(J, Jd, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  // ---- backward sweep: recompute each segment from its checkpoint ------------------------
+  if (st == ADER_OK && (grad_mat || grad_M)) {
+    double *gm = grad_mat, *gM = grad_M;
+    if (!gm && (e = B.alloc(&gm, (size_t)c->g.ncells * 3)) != cudaSuccess) return ADER_ENOMEM;
+    if (!gM && (e = B.alloc(&gM, 6)) != cudaSuccess) return ADER_ENOMEM;
+    CUDA_OK(cudaMemsetAsync(gm, 0, (size_t)c->g.ncells * 3 * sizeof(double), c->stream));
+    CUDA_OK(cudaMemsetAsync(gM, 0, 6 * sizeof(double), c->stream));
+    CUDA_OK(cudaMemsetAsync(lam, 0, nd * sizeof(double), c->stream));
+    c->rec.nrec = 0;  // no recording while recomputing
+    for (int sg = nseg - 1; sg >= 0 && st == ADER_OK; --sg) {
+      const int a = sg * k_ckpt, b = std::min(a + k_ckpt, steps);
+      CUDA_OK(cudaMemcpyAsync(c->u, ckpt + (size_t)sg * nd, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      CUDA_OK(launch_set_scalars(c->dev, t0 + a * dt, dt, c->stream));
+      for (int i = 0; i < b - a && st == ADER_OK; ++i) {
+        CUDA_OK(cudaMemcpyAsync(seg + (size_t)i * nd, c->u, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        if (i + 1 < b - a) st = step_impl(c, dt, 0.0);
+      }
+      for (int n = b; n > a && st == ADER_OK; --n) {
+        // lambda += dt R^T (seismo[n-1] - obs[n-1]);  then lambda <- A^T lambda, gradients
+        CUDA_OK(launch_sub(seismo + (size_t)(n - 1) * nrec * 3, obs + (size_t)(n - 1) * nrec * 3, res,
+                           nrec * 3, c->stream));
+        CUDA_OK(launch_receivers_adjoint(saved, res, dt, lam, (int)c->nodes, (int)c->nvar, c->stream));
+        st = ader_adjoint_step(c, t0 + (n - 1) * dt, dt, seg + (size_t)(n - 1 - a) * nd, lam, nullptr, gm, gM);
+      }
+    }
+  }
+  c->rec = saved;
+  CUDA_OK(cudaStreamSynchronize(c->stream));
+  if (st != ADER_OK) return st;
+  return ader_sync(c);
 }
 
 ader_status ader_enable_timing(ader_ctx* c, int on) {

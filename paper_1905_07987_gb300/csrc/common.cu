@@ -84,6 +84,40 @@ __global__ void k_receivers_adjoint(Receivers r, const double* res, double scale
   }
 }
 
+// res = seismo_row - obs_row ([n] values)
+__global__ void k_sub(const double* a, const double* b, double* out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] - b[i];
+}
+
+// J = 1/2 scale sum (a - b)^2 over n values (one block, fixed reduction order).
+__global__ void k_misfit(const double* a, const double* b, long long n, double scale, double* J) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const double r = a[i] - b[i];
+    s = fma(r, r, s);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *J = 0.5 * scale * red[0];
+}
+
+cudaError_t launch_sub(const double* a, const double* b, double* out, int n, cudaStream_t s) {
+  k_sub<<<(n + 127) / 128, 128, 0, s>>>(a, b, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_misfit(const double* a, const double* b, long long n, double scale, double* J,
+                          cudaStream_t s) {
+  k_misfit<<<1, 256, 0, s>>>(a, b, n, scale, J);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_set_scalars(DevScalars* d, double t, double dt, cudaStream_t s) {
   k_set_scalars<<<1, 1, 0, s>>>(d, t, dt);
   return cudaGetLastError();

@@ -1,0 +1,13 @@
+// Adjoint kernels of the elastic step, order 2 (own translation unit to keep builds parallel).
+#include "kernels_adjoint.cuh"
+
+namespace ader {
+template <>
+cudaError_t adj_run_n<2>(const StepArgs& a, const AdjArgs& j, const Tables& t, int blocks, cudaStream_t s) {
+  return AdjLaunch<2>::run(a, j, t, blocks, s);
+}
+template <>
+long long adj_scratch_n<2>(int iters) { return AdjLaunch<2>::scratch_per_block(iters); }
+template <>
+int adj_bps_n<2>() { return AdjLaunch<2>::blocks_per_sm(); }
+}  // namespace ader

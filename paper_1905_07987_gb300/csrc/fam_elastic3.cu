@@ -1,35 +1,42 @@
 // Kernel family: linear elasticity in 3D, orders 1-6, with the adjoint step (orders 1-5).
-#include "kernels_adjoint.cuh"
+#include "kernels.cuh"
 
 namespace ader {
+struct AdjArgs;
+template <int N>
+cudaError_t adj_run_n(const StepArgs& a, const AdjArgs& j, const Tables& t, int blocks, cudaStream_t s);
+template <int N>
+long long adj_scratch_n(int iters);
+template <int N>
+int adj_bps_n();
 namespace {
 cudaError_t adj_run(const StepArgs& a, const AdjArgs& j, const Tables& t, int blocks, cudaStream_t s) {
   switch (a.g.order) {
-    case 1: return AdjLaunch<1>::run(a, j, t, blocks, s);
-    case 2: return AdjLaunch<2>::run(a, j, t, blocks, s);
-    case 3: return AdjLaunch<3>::run(a, j, t, blocks, s);
-    case 4: return AdjLaunch<4>::run(a, j, t, blocks, s);
-    case 5: return AdjLaunch<5>::run(a, j, t, blocks, s);
+    case 1: return adj_run_n<1>(a, j, t, blocks, s);
+    case 2: return adj_run_n<2>(a, j, t, blocks, s);
+    case 3: return adj_run_n<3>(a, j, t, blocks, s);
+    case 4: return adj_run_n<4>(a, j, t, blocks, s);
+    case 5: return adj_run_n<5>(a, j, t, blocks, s);
   }
   return cudaErrorInvalidValue;
 }
 long long adj_scratch(int order, int iters) {
   switch (order) {
-    case 1: return AdjLaunch<1>::scratch_per_block(iters);
-    case 2: return AdjLaunch<2>::scratch_per_block(iters);
-    case 3: return AdjLaunch<3>::scratch_per_block(iters);
-    case 4: return AdjLaunch<4>::scratch_per_block(iters);
-    case 5: return AdjLaunch<5>::scratch_per_block(iters);
+    case 1: return adj_scratch_n<1>(iters);
+    case 2: return adj_scratch_n<2>(iters);
+    case 3: return adj_scratch_n<3>(iters);
+    case 4: return adj_scratch_n<4>(iters);
+    case 5: return adj_scratch_n<5>(iters);
   }
   return 0;
 }
 int adj_bps(int order) {
   switch (order) {
-    case 1: return AdjLaunch<1>::blocks_per_sm();
-    case 2: return AdjLaunch<2>::blocks_per_sm();
-    case 3: return AdjLaunch<3>::blocks_per_sm();
-    case 4: return AdjLaunch<4>::blocks_per_sm();
-    case 5: return AdjLaunch<5>::blocks_per_sm();
+    case 1: return adj_bps_n<1>();
+    case 2: return adj_bps_n<2>();
+    case 3: return adj_bps_n<3>();
+    case 4: return adj_bps_n<4>();
+    case 5: return adj_bps_n<5>();
   }
   return 0;
 }

@@ -28,6 +28,23 @@ struct AdjArgs {
   long long scratch_per_block;
 };
 
+// Rows r of B_d whose single non-zero sits in column k (B_d^T has these entries in row k).
+struct RowsT {
+  signed char r[3][9][3];
+};
+__host__ __device__ constexpr RowsT make_rows() {
+  RowsT t{};
+  for (int d = 0; d < 3; ++d)
+    for (int k = 0; k < 9; ++k) {
+      int m = 0;
+      for (int q = 0; q < 3; ++q) t.r[d][k][q] = -1;
+      for (int r = 0; r < 9; ++r)
+        if (Elastic::src(d, r) == k) t.r[d][k][m++] = (signed char)r;
+    }
+  return t;
+}
+static __constant__ RowsT c_rows = make_rows();
+
 // d coef(d, v) / d (rho, lambda, mu)
 __device__ __forceinline__ void dcoef(int d, int v, double rho, double* g) {
   g[0] = g[1] = g[2] = 0.0;
@@ -292,7 +309,7 @@ __global__ void __launch_bounds__(Cfg<Elastic, 3, N>::TPB)
       if (l >= NL) continue;
       const int j = l / NV, v = l % NV;
       double qbh = 0.0;  // adjoint of q_bar[j][v]
-#pragma unroll
+#pragma unroll 1
       for (int d = 0; d < 3; ++d) {
         const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
         const int jd = (j / st) % n, j0 = j - jd * st;
@@ -308,9 +325,10 @@ __global__ void __launch_bounds__(Cfg<Elastic, 3, N>::TPB)
           for (int q = 0; q < 3; ++q) gm[q] = fma(w, dc[q], gm[q]);
         }
         // (L^T lam)[j][v] = -(1/h) sum_{rows r with src(d,r) = v} coef(d,r) sum_i D[i][jd] lam[j(i)][r]
-#pragma unroll
-        for (int r = 0; r < NV; ++r) {
-          if (Elastic::src(d, r) != v) continue;
+#pragma unroll 1
+        for (int q = 0; q < 3; ++q) {
+          const int r = c_rows.r[d][v][q];
+          if (r < 0) break;
           double acc = 0.0;
 #pragma unroll
           for (int i = 0; i < n; ++i) acc = fma(T.D[i][jd], P[NL + (j0 + i * st) * NV + r], acc);
@@ -365,7 +383,7 @@ __global__ void __launch_bounds__(Cfg<Elastic, 3, N>::TPB)
         for (int t = 0; t < n; ++t) qh[k][t] = 0.0;
         if (l >= NL) continue;
         const int j = l / NV, v = l % NV;
-#pragma unroll
+#pragma unroll 1
         for (int d = 0; d < 3; ++d) {
           const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
           const int jd = (j / st) % n, j0 = j - jd * st;
@@ -384,9 +402,10 @@ __global__ void __launch_bounds__(Cfg<Elastic, 3, N>::TPB)
             const double w = -A.g.inv_h[d] * acc;
             for (int q = 0; q < 3; ++q) gm[q] = fma(w, dc[q], gm[q]);
           }
-#pragma unroll
-          for (int rr = 0; rr < NV; ++rr) {
-            if (Elastic::src(d, rr) != v) continue;
+#pragma unroll 1
+          for (int q = 0; q < 3; ++q) {
+            const int rr = c_rows.r[d][v][q];
+            if (rr < 0) break;
             const double cf = -A.g.inv_h[d] * Elastic::coef_ir(d, rr, irho, lamc, mu);
 #pragma unroll
             for (int t = 0; t < n; ++t) {
@@ -460,6 +479,13 @@ __global__ void __launch_bounds__(Cfg<Elastic, 3, N>::TPB)
     __syncthreads();
   }
 }
+
+template <int N>
+cudaError_t adj_run_n(const StepArgs& a, const AdjArgs& j, const Tables& t, int blocks, cudaStream_t s);
+template <int N>
+long long adj_scratch_n(int iters);
+template <int N>
+int adj_bps_n();
 
 template <int N>
 struct AdjLaunch {

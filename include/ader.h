@@ -200,6 +200,29 @@ ader_status ader_misfit_gradient(ader_ctx* ctx, const double* u0, double t0, dou
 ader_status ader_enable_timing(ader_ctx* ctx, int on);
 ader_status ader_phase_times(ader_ctx* ctx, double ms[7], int* steps);
 
+/* Ensembles of independent runs (several solvers on one machine, Sec. 5.1; batching of uneven
+ * grids).  Each run is an ordinary context (its own grid, order, PDE, material, source), created
+ * from cfgs[i] on `cuda_stream`.  ader_ensemble_step advances every run by `steps` steps (same dt /
+ * t_end meaning as ader_step, applied to each run): all runs' kernels are captured into one CUDA
+ * graph of `steps_per_graph` steps, forked over `branches` streams inside the graph and joined,
+ * and the graph is replayed (re-captured when the arguments change); a remainder of steps is
+ * launched directly.  Not synchronising.  The per-run contexts are owned by the ensemble
+ * (ader_ensemble_run); use them to set states, materials, sources and receivers and to read
+ * results, but do not destroy them. */
+typedef struct ader_ensemble ader_ensemble;
+ader_status ader_ensemble_create(const ader_config* cfgs, int nruns, void* cuda_stream,
+                                 ader_ensemble** out);
+void ader_ensemble_destroy(ader_ensemble* ens);
+ader_ctx* ader_ensemble_run(ader_ensemble* ens, int i);
+ader_status ader_ensemble_step(ader_ensemble* ens, int steps, double dt, double t_end);
+ader_status ader_ensemble_sync(ader_ensemble* ens);
+/* Launch shape: branches in [1, 16], steps_per_graph even and >= 2. */
+ader_status ader_ensemble_set_launch(ader_ensemble* ens, int branches, int steps_per_graph);
+/* Autotuner: times every (branches, steps_per_graph) candidate with fixed dt > 0 on the current
+ * states (which it restores), keeps the fastest; best[2] and *ms_per_step receive the choice and
+ * its time per step.  Synchronises. */
+ader_status ader_ensemble_autotune(ader_ensemble* ens, double dt, int* best, double* ms_per_step);
+
 /* Human-readable name of a status. */
 const char* ader_status_string(ader_status s);
 

@@ -74,6 +74,13 @@ _SIGS = {
     "ader_adjoint_step": ([_P, _D, _D, _P, _P, _P, _P, _P], _I),
     "ader_receivers_adjoint": ([_P, _P, _D, _P], _I),
     "ader_misfit_gradient": ([_P, _P, _D, _D, _I, _I, _P, ctypes.POINTER(_D), _P, _P], _I),
+    "ader_ensemble_create": ([ctypes.POINTER(Config), _I, _P, ctypes.POINTER(_P)], _I),
+    "ader_ensemble_destroy": ([_P], None),
+    "ader_ensemble_run": ([_P, _I], _P),
+    "ader_ensemble_step": ([_P, _I, _D, _D], _I),
+    "ader_ensemble_sync": ([_P], _I),
+    "ader_ensemble_set_launch": ([_P, _I, _I], _I),
+    "ader_ensemble_autotune": ([_P, _D, _P, ctypes.POINTER(_D)], _I),
     "ader_enable_timing": ([_P, _I], _I),
     "ader_phase_times": ([_P, _P, ctypes.POINTER(_I)], _I),
 }
@@ -158,21 +165,29 @@ def make_config(pde, dim, order, ncell, lo, hi, bc, cfl, gamma=1.4, adv=(0.0, 0.
     return c
 
 
+def _default_stream():
+    try:
+        import torch
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+    except ImportError:  # pragma: no cover
+        return 0
+
+
 class Context:
     """Owns one ader_ctx.  Methods map one-to-one to the C ABI."""
 
-    def __init__(self, config, stream=None):
+    def __init__(self, config, stream=None, handle=None):
         L = lib()
         if stream is None:
-            try:
-                import torch
-                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
-            except ImportError:  # pragma: no cover
-                stream = 0
+            stream = _default_stream()
         self.config = config
         self._stream = stream
-        h = _P()
-        check(L.ader_create(ctypes.byref(config), _P(stream), ctypes.byref(h)), "ader_create")
+        self._owned = handle is None
+        if handle is None:
+            h = _P()
+            check(L.ader_create(ctypes.byref(config), _P(stream), ctypes.byref(h)), "ader_create")
+        else:
+            h = _P(handle)
         self._h = h
         cells, nodes, nvar = _L(), _L(), _I()
         check(L.ader_sizes(h, ctypes.byref(cells), ctypes.byref(nodes), ctypes.byref(nvar)), "ader_sizes")
@@ -181,7 +196,8 @@ class Context:
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().ader_destroy(self._h)
+            if self._owned:
+                lib().ader_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -318,3 +334,49 @@ class Context:
 
     def sync(self):
         check(lib().ader_sync(self._h), "ader_sync")
+
+
+class Ensemble:
+    """Several independent runs advanced together (one CUDA graph launch per steps_per_graph
+    steps).  ``runs[i]`` are non-owning Context views of the member contexts."""
+
+    def __init__(self, configs, stream=None):
+        L = lib()
+        if stream is None:
+            stream = _default_stream()
+        arr = (Config * len(configs))(*configs)
+        h = _P()
+        check(L.ader_ensemble_create(arr, len(configs), _P(stream), ctypes.byref(h)), "ader_ensemble_create")
+        self._h = h
+        self.runs = [Context(cfg, stream=stream, handle=L.ader_ensemble_run(h, i))
+                     for i, cfg in enumerate(configs)]
+
+    def step(self, steps, dt=0.0, t_end=0.0):
+        check(lib().ader_ensemble_step(self._h, int(steps), float(dt), float(t_end)), "ader_ensemble_step")
+
+    def sync(self):
+        check(lib().ader_ensemble_sync(self._h), "ader_ensemble_sync")
+
+    def set_launch(self, branches, steps_per_graph):
+        check(lib().ader_ensemble_set_launch(self._h, int(branches), int(steps_per_graph)),
+              "ader_ensemble_set_launch")
+
+    def autotune(self, dt):
+        best = np.zeros(2, dtype=np.int32)
+        ms = _D()
+        check(lib().ader_ensemble_autotune(self._h, float(dt), best.ctypes.data, ctypes.byref(ms)),
+              "ader_ensemble_autotune")
+        return int(best[0]), int(best[1]), ms.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for r in self.runs:
+                r.close()
+            lib().ader_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

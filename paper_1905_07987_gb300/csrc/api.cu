@@ -971,6 +971,229 @@ ader_status ader_misfit_gradient(ader_ctx* c, const double* u0, double t0, doubl
   return ader_sync(c);
 }
 
+}  // extern "C"
+
+// ---- ensembles ------------------------------------------------------------------------------
+struct ader_ensemble {
+  std::vector<ader_ctx*> runs;
+  cudaStream_t stream = nullptr;
+  std::vector<cudaStream_t> branch;   // fork streams used inside the captured graph
+  std::vector<cudaEvent_t> ev;        // fork / join events
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int g_steps = 0, g_branches = 0;
+  double g_dt = 0.0, g_tend = 0.0;
+  std::vector<double*> g_u0;
+  int branches = 1;                   // chosen by the autotuner (or 1)
+  int steps_per_graph = 2;
+};
+
+static void ens_free_graph(ader_ensemble* e) {
+  if (e->gexec) cudaGraphExecDestroy(e->gexec);
+  if (e->graph) cudaGraphDestroy(e->graph);
+  e->gexec = nullptr;
+  e->graph = nullptr;
+}
+
+static ader_status ens_capture(ader_ensemble* e, int steps, double dt, double t_end, int nb) {
+  ens_free_graph(e);
+  while ((int)e->branch.size() < nb) {
+    cudaStream_t s;
+    CUDA_OK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    e->branch.push_back(s);
+  }
+  while (e->ev.size() < (size_t)(nb + 1)) {
+    cudaEvent_t v;
+    CUDA_OK(cudaEventCreateWithFlags(&v, cudaEventDisableTiming));
+    e->ev.push_back(v);
+  }
+  cudaStream_t cap = e->branch[0];
+  std::vector<cudaStream_t> saved(e->runs.size());
+  for (size_t r = 0; r < e->runs.size(); ++r) saved[r] = e->runs[r]->stream;
+  CUDA_OK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  ader_status st = ADER_OK;
+  // fork: branches 1..nb-1 wait on the start of the capture
+  if (cudaEventRecord(e->ev[0], cap) != cudaSuccess) st = ADER_ECUDA;
+  for (int b = 1; b < nb && st == ADER_OK; ++b)
+    if (cudaStreamWaitEvent(e->branch[b], e->ev[0], 0) != cudaSuccess) st = ADER_ECUDA;
+  for (size_t r = 0; r < e->runs.size() && st == ADER_OK; ++r) {
+    ader_ctx* c = e->runs[r];
+    c->stream = e->branch[r % nb];
+    for (int k = 0; k < steps && st == ADER_OK; ++k) st = step_impl(c, dt, t_end);
+  }
+  // join
+  for (int b = 1; b < nb && st == ADER_OK; ++b) {
+    if (cudaEventRecord(e->ev[b], e->branch[b]) != cudaSuccess) st = ADER_ECUDA;
+    else if (cudaStreamWaitEvent(cap, e->ev[b], 0) != cudaSuccess) st = ADER_ECUDA;
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(cap, &g);
+  for (size_t r = 0; r < e->runs.size(); ++r) e->runs[r]->stream = saved[r];
+  if (st != ADER_OK || ce != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return st != ADER_OK ? st : ADER_ECUDA;
+  }
+  e->graph = g;
+  CUDA_OK(cudaGraphInstantiate(&e->gexec, g, 0));
+  e->g_steps = steps;
+  e->g_branches = nb;
+  e->g_dt = dt;
+  e->g_tend = t_end;
+  e->g_u0.clear();
+  for (ader_ctx* c : e->runs) e->g_u0.push_back(c->u);
+  return ADER_OK;
+}
+
+extern "C" {
+
+ader_status ader_ensemble_create(const ader_config* cfgs, int nruns, void* stream,
+                                 ader_ensemble** out) {
+  if (!out) return ADER_EINVAL;
+  *out = nullptr;
+  if (!cfgs || nruns < 1) return ADER_EINVAL;
+  ader_ensemble* e = new (std::nothrow) ader_ensemble();
+  if (!e) return ADER_ENOMEM;
+  e->stream = (cudaStream_t)stream;
+  for (int r = 0; r < nruns; ++r) {
+    ader_ctx* c = nullptr;
+    const ader_status st = ader_create(&cfgs[r], stream, &c);
+    if (st != ADER_OK) {
+      ader_ensemble_destroy(e);
+      return st;
+    }
+    e->runs.push_back(c);
+  }
+  *out = e;
+  return ADER_OK;
+}
+
+void ader_ensemble_destroy(ader_ensemble* e) {
+  if (!e) return;
+  ens_free_graph(e);
+  for (ader_ctx* c : e->runs) ader_destroy(c);
+  for (cudaStream_t s : e->branch) cudaStreamDestroy(s);
+  for (cudaEvent_t v : e->ev) cudaEventDestroy(v);
+  delete e;
+}
+
+ader_ctx* ader_ensemble_run(ader_ensemble* e, int i) {
+  if (!e || i < 0 || i >= (int)e->runs.size()) return nullptr;
+  return e->runs[i];
+}
+
+ader_status ader_ensemble_step(ader_ensemble* e, int steps, double dt, double t_end) {
+  if (!e || steps < 1) return ADER_EINVAL;
+  for (ader_ctx* c : e->runs) {
+    if (!c->state_set) return ADER_ESTATE;
+    if (c->cfg.pde == ADER_PDE_ELASTIC && !c->mat_set) return ADER_ESTATE;
+    if (c->timing) return ADER_EINVAL;
+  }
+  // whole graphs of steps_per_graph (even) steps, the remainder one step at a time
+  const int spg = e->steps_per_graph;
+  const int ng = steps / spg, rest = steps % spg;
+  if (ng > 0) {
+    bool same = e->gexec && e->g_steps == spg && e->g_dt == dt && e->g_tend == t_end &&
+                e->g_branches == e->branches;
+    for (size_t r = 0; same && r < e->runs.size(); ++r) same = e->g_u0[r] == e->runs[r]->u;
+    if (!same) {
+      const ader_status st = ens_capture(e, spg, dt, t_end, e->branches);
+      if (st != ADER_OK) return st;
+    }
+    // order the replays after earlier work on the ensemble stream
+    CUDA_OK(cudaEventRecord(e->ev[0], e->stream));
+    CUDA_OK(cudaStreamWaitEvent(e->branch[0], e->ev[0], 0));
+    for (int k = 0; k < ng; ++k) CUDA_OK(cudaGraphLaunch(e->gexec, e->branch[0]));
+    CUDA_OK(cudaEventRecord(e->ev[0], e->branch[0]));
+    CUDA_OK(cudaStreamWaitEvent(e->stream, e->ev[0], 0));
+  }
+  for (int k = 0; k < rest; ++k)
+    for (ader_ctx* c : e->runs) {
+      const ader_status st = step_impl(c, dt, t_end);
+      if (st != ADER_OK) return st;
+    }
+  return ADER_OK;
+}
+
+ader_status ader_ensemble_sync(ader_ensemble* e) {
+  if (!e) return ADER_EINVAL;
+  ader_status first = ADER_OK;
+  for (ader_ctx* c : e->runs) {
+    const ader_status st = ader_sync(c);
+    if (st != ADER_OK && first == ADER_OK) first = st;
+  }
+  return first;
+}
+
+ader_status ader_ensemble_set_launch(ader_ensemble* e, int branches, int steps_per_graph) {
+  if (!e || branches < 1 || branches > 16 || steps_per_graph < 2 || steps_per_graph % 2) return ADER_EINVAL;
+  e->branches = branches;
+  e->steps_per_graph = steps_per_graph;
+  return ADER_OK;
+}
+
+// Time each (branches, steps per graph) candidate on the current states (restored afterwards)
+// and keep the fastest.  best[0..1] receives the choice, ms_per_step its time.
+ader_status ader_ensemble_autotune(ader_ensemble* e, double dt, int* best, double* ms_per_step) {
+  if (!e || !(dt > 0.0)) return ADER_EINVAL;
+  for (ader_ctx* c : e->runs)
+    if (!c->state_set) return ADER_ESTATE;
+  DevBufs B;
+  std::vector<double*> save(e->runs.size());
+  for (size_t r = 0; r < e->runs.size(); ++r) {
+    if (B.alloc(&save[r], (size_t)e->runs[r]->ndof) != cudaSuccess) return ADER_ENOMEM;
+    CUDA_OK(cudaMemcpyAsync(save[r], e->runs[r]->u, e->runs[r]->ndof * sizeof(double),
+                            cudaMemcpyDeviceToDevice, e->stream));
+  }
+  const int cand_b[] = {1, 2, 4, 8};
+  const int cand_s[] = {2, 4, 8};
+  cudaEvent_t t0, t1;
+  CUDA_OK(cudaEventCreate(&t0));
+  CUDA_OK(cudaEventCreate(&t1));
+  double best_ms = 1e300;
+  int bb = 1, bs = 2;
+  const int ob = e->branches, os = e->steps_per_graph;
+  for (int b : cand_b) {
+    if (b > (int)e->runs.size()) continue;
+    for (int sp : cand_s) {
+      e->branches = b;
+      e->steps_per_graph = sp;
+      ader_status st = ader_ensemble_step(e, sp, dt, 0.0);  // capture + warm-up
+      if (st != ADER_OK) break;
+      CUDA_OK(cudaEventRecord(t0, e->stream));
+      st = ader_ensemble_step(e, 2 * sp, dt, 0.0);
+      CUDA_OK(cudaEventRecord(t1, e->stream));
+      CUDA_OK(cudaEventSynchronize(t1));
+      float ms = 0.f;
+      CUDA_OK(cudaEventElapsedTime(&ms, t0, t1));
+      const double per = ms / (2.0 * sp);
+      if (st == ADER_OK && per < best_ms) {
+        best_ms = per;
+        bb = b;
+        bs = sp;
+      }
+      for (size_t r = 0; r < e->runs.size(); ++r)  // restore the states (even steps: same buffers)
+        CUDA_OK(cudaMemcpyAsync(e->runs[r]->u, save[r], e->runs[r]->ndof * sizeof(double),
+                                cudaMemcpyDeviceToDevice, e->stream));
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  CUDA_OK(cudaStreamSynchronize(e->stream));
+  if (best_ms == 1e300) {
+    e->branches = ob;
+    e->steps_per_graph = os;
+    return ADER_ECUDA;
+  }
+  e->branches = bb;
+  e->steps_per_graph = bs;
+  if (best) {
+    best[0] = bb;
+    best[1] = bs;
+  }
+  if (ms_per_step) *ms_per_step = best_ms;
+  return ADER_OK;
+}
+
 ader_status ader_enable_timing(ader_ctx* c, int on) {
   if (!c) return ADER_EINVAL;
   c->timing = on != 0;

@@ -1,0 +1,103 @@
+"""Ensembles of uneven elastic grids advanced by one CUDA graph: identical to stepping every run
+on its own, for every launch shape the autotuner may choose, and each run against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1905_07987_gb300 import ader, synth
+from cases import rel_linf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _build():
+    from paper_1905_07987_gb300 import build
+    build.build()
+
+
+def member_configs(sides, order, precision="fp64"):
+    cfgs = []
+    for s in sides:
+        cfgs.append(ader.make_config("elastic", 3, order, (s, s, s), (0, 0, 0), (0.5 * s,) * 3,
+                                     "absorbing", synth.cfl_number(order), precision=precision))
+    return cfgs
+
+
+def setup_member(ctx, side, order, seed):
+    x, _ = ader.reference_nodes(order)
+    X = synth.node_coordinates(x, (side,) * 3, (0, 0, 0), (0.5 * side,) * 3)
+    mat = synth.elastic_material((side,) * 3, seed=seed)
+    ctx.set_material(torch.from_numpy(mat.reshape(-1).copy()).cuda())
+    c = 0.25 * side
+    bump = np.exp(-4 * ((X[0] - c) ** 2 + (X[1] - c) ** 2 + (X[2] - c) ** 2))
+    u0 = np.stack([bump, 0 * bump, -bump] + [0.1 * bump] * 6, -1)
+    ctx.set_state(torch.from_numpy(u0.reshape(-1).copy()).cuda())
+    ctx.set_point_source((0.2 * side, 0.3 * side, 0.25 * side), synth.moment_tensor(seed=seed), 2.0, 0.5)
+    return u0, mat
+
+
+def states(ctxs):
+    out = []
+    for c in ctxs:
+        t = torch.empty(c.count, dtype=torch.float64, device="cuda")
+        c.get_state(t)
+        out.append(t)
+    torch.cuda.synchronize()
+    return [t.cpu().numpy() for t in out]
+
+
+@pytest.mark.parametrize("branches,spg", [(1, 2), (2, 4), (3, 2)])
+def test_ensemble_graph_equals_separate_runs(branches, spg):
+    sides, order = [3, 5, 4, 2], 2
+    ens = ader.Ensemble(member_configs(sides, order))
+    singles = [ader.Context(c) for c in member_configs(sides, order)]
+    for i, s in enumerate(sides):
+        setup_member(ens.runs[i], s, order, seed=i)
+        setup_member(singles[i], s, order, seed=i)
+    ens.set_launch(branches, spg)
+    dt = 1e-3
+    ens.step(7, dt=dt)
+    ens.sync()
+    for c in singles:
+        c.run(7, dt=dt)
+    for a, b in zip(states(ens.runs), states(singles)):
+        assert np.array_equal(a, b)
+    ens.close()
+
+
+def test_ensemble_members_match_the_oracle():
+    from oracle.aderdg import ADERDG, Grid, PointSource
+    from oracle.pde import Elastic
+    sides, order = [2, 3], 3
+    ens = ader.Ensemble(member_configs(sides, order))
+    refs = []
+    for i, s in enumerate(sides):
+        u0, mat = setup_member(ens.runs[i], s, order, seed=10 + i)
+        g = Grid((s,) * 3, (0, 0, 0), (0.5 * s,) * 3, [("absorbing", "absorbing")] * 3)
+        o = ADERDG(Elastic(), g, order, cfl=synth.cfl_number(order), material=torch.from_numpy(mat))
+        cell, xi = synth.locate((0.2 * s, 0.3 * s, 0.25 * s), (s,) * 3, (0, 0, 0), (0.5 * s,) * 3)
+        o.set_point_source(PointSource(cell, xi, torch.from_numpy(synth.moment_tensor(seed=10 + i)), 2.0, 0.5))
+        u, t = o.run(torch.from_numpy(u0), 4)
+        refs.append(u.numpy())
+    ens.step(4)
+    ens.sync()
+    for a, r in zip(states(ens.runs), refs):
+        assert rel_linf(a.reshape(r.shape), r) <= 1e-11
+    ens.close()
+
+
+def test_autotune_keeps_results_and_picks_a_valid_shape():
+    sides, order = [4, 3, 5], 2
+    ens = ader.Ensemble(member_configs(sides, order, precision="mixed"))
+    for i, s in enumerate(sides):
+        setup_member(ens.runs[i], s, order, seed=i)
+    before = states(ens.runs)
+    b, spg, ms = ens.autotune(1e-3)
+    assert b in (1, 2, 4, 8) and spg in (2, 4, 8) and ms > 0
+    after = states(ens.runs)
+    for x, y in zip(before, after):
+        assert np.array_equal(x, y)
+    ens.step(6, dt=1e-3)
+    ens.sync()
+    ens.close()

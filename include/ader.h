@@ -172,6 +172,31 @@ ader_status ader_run_graph(ader_ctx* ctx, int steps, int replays, double dt, dou
 ader_status ader_adjoint_step(ader_ctx* ctx, double t_n, double dt, const double* u_n, double* lam,
                               const double* dJdu, double* grad_mat, double* grad_M);
 
+/* Same result as ader_adjoint_step, but this call allocates no memory: its work buffers (the
+ * forward Picard iterates kept per thread block, the face adjoints and the per-face material
+ * gradients) live in one fixed 64 MiB array of device memory that the library defines, so no
+ * cudaMalloc, cudaFree or other allocating call is made.  It exists for callers that cannot
+ * allocate device memory at the time of the call: for example code whose device memory is
+ * owned by another allocator (a framework's memory pool that has reserved the GPU), processes
+ * that run under a fixed memory budget, or loops that cannot afford the device-wide
+ * synchronisation that cudaMalloc and cudaFree imply.  There is no counterpart in the paper.
+ * Limits and behaviour:
+ *  - The face adjoints (cells x 3 x 2 x n^2 x 9 doubles), the face gradients (6 doubles per
+ *    face) and one iterate slab (order x (order+1) x n^3 x 9 doubles) must fit in 64 MiB;
+ *    otherwise ADER_EINVAL and nothing runs.  Fewer thread blocks are used when the slabs of all
+ *    of them do not fit.
+ *  - The array is shared by every call on a device and keeps the contents of the last call
+ *    (every location the kernels read is written first in the same call).  Calls whose work
+ *    overlaps on the GPU (different streams or contexts on the same device) race on it and must
+ *    be ordered by the caller.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ *    make that first call before any stream capture begins.
+ *  - The context's next-state and face buffers (allocated by ader_create) are overwritten, as in
+ *    ader_adjoint_step. */
+ader_status ader_adjoint_step_static(ader_ctx* ctx, double t_n, double dt, const double* u_n,
+                                     double* lam, const double* dJdu, double* grad_mat,
+                                     double* grad_M);
+
 /* Transpose of the receiver read-out: dJdu[cell_r][j][v] += scale * res[r][v] * Phi_j(x_r) for the
  * velocity components v = 0..2 of every receiver r (res: device [nrec][3]; dJdu: device state-sized,
  * accumulated).  With res = seismogram - observation and scale = dt this is the derivative of the

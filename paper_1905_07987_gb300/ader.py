@@ -73,6 +73,7 @@ _SIGS = {
     "ader_get_subcell_state": ([_P, _P, _I], _I),
     "ader_adjoint_step": ([_P, _D, _D, _P, _P, _P, _P, _P], _I),
     "ader_receivers_adjoint": ([_P, _P, _D, _P], _I),
+    "ader_adjoint_step_static": ([_P, _D, _D, _P, _P, _P, _P, _P], _I),
     "ader_misfit_gradient": ([_P, _P, _D, _D, _I, _I, _P, ctypes.POINTER(_D), _P, _P], _I),
     "ader_ensemble_create": ([ctypes.POINTER(Config), _I, _P, ctypes.POINTER(_P)], _I),
     "ader_ensemble_destroy": ([_P], None),
@@ -255,9 +256,10 @@ class Context:
         check(lib().ader_get_subcell_state(self._h, p, dev), "ader_get_subcell_state")
         return out
 
-    def adjoint_step(self, t_n, dt, u_n, lam, grad_mat, grad_M, dJdu=None):
+    def adjoint_step(self, t_n, dt, u_n, lam, grad_mat, grad_M, dJdu=None, static=False):
         """lam <- A^T lam (+ dJdu) for the step from t_n with fixed dt at forward state u_n;
-        accumulates grad_mat [cells,3] and grad_M [6].  All CUDA float64 tensors."""
+        accumulates grad_mat [cells,3] and grad_M [6].  All CUDA float64 tensors.  static=True
+        calls the allocation-free variant (work memory in the library's fixed device array)."""
         ptrs = []
         for a in (u_n, lam, grad_mat, grad_M) + ((dJdu,) if dJdu is not None else ()):
             p, dev, keep, n = _ptr(a)
@@ -268,8 +270,9 @@ class Context:
                 or grad_M.numel() != 6 or (dJdu is not None and dJdu.numel() != self.count):
             raise ValueError("adjoint buffer sizes")
         dj = ptrs[4] if dJdu is not None else None
-        check(lib().ader_adjoint_step(self._h, float(t_n), float(dt), ptrs[0], ptrs[1], dj, ptrs[2], ptrs[3]),
-              "ader_adjoint_step")
+        fn = lib().ader_adjoint_step_static if static else lib().ader_adjoint_step
+        check(fn(self._h, float(t_n), float(dt), ptrs[0], ptrs[1], dj, ptrs[2], ptrs[3]),
+              "ader_adjoint_step_static" if static else "ader_adjoint_step")
 
     def receivers_adjoint(self, res, scale, dJdu):
         p, dev, keep, n = _ptr(res)

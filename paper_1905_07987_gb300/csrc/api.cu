@@ -4,6 +4,7 @@
 #include <cstdlib>
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -887,6 +888,76 @@ ader_status ader_adjoint_step(ader_ctx* c, double t_n, double dt, const double* 
   CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
   AdjArgs j{u_n, lam, dJdu, grad_mat, grad_M, c->adjf, c->gface, c->adj_scratch, c->adj_spb};
   CUDA_OK(c->fam->adj_run(a, j, c->tab, c->adj_blocks, c->stream));
+  return ADER_OK;
+}
+
+}  // extern "C"
+
+// ---- allocation-free adjoint step ---------------------------------------------------------
+// Work memory of ader_adjoint_step_static lives in this fixed device array, which every GPU that
+// loads the library keeps until the process exits.  Host code must not use the symbol itself as
+// a device address: its device address is looked up once per device below.
+namespace {
+constexpr size_t kStaticScratchBytes = 64ull << 20;  // 64 MiB
+constexpr int kMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_adj_static[kStaticScratchBytes];
+std::mutex g_adj_static_mu;
+void* g_adj_static_addr[kMaxDevices] = {};
+
+size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+}  // namespace
+
+extern "C" {
+
+ader_status ader_adjoint_step_static(ader_ctx* c, double t_n, double dt, const double* u_n,
+                                     double* lam, const double* dJdu, double* grad_mat,
+                                     double* grad_M) {
+  if (!c || !u_n || !lam || !grad_mat || !grad_M || !(dt > 0.0)) return ADER_EINVAL;
+  if (c->cfg.pde != ADER_PDE_ELASTIC || !c->fam->adj_run) return ADER_EUNSUPPORTED;
+  if (c->cfg.order > 5) return ADER_EUNSUPPORTED;
+  if (!c->mat_set) return ADER_ESTATE;
+  int dev = 0;
+  CUDA_OK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return ADER_EUNSUPPORTED;
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_adj_static_mu);
+    if (!g_adj_static_addr[dev]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_adj_static);
+      if (e != cudaSuccess || !p) return ADER_ECUDA;
+      g_adj_static_addr[dev] = p;
+    }
+    base = g_adj_static_addr[dev];
+  }
+  // layout: device scalars | face adjoints | face material gradients | per-block iterate slabs
+  const int iters = c->cfg.picard_iters > 0 ? c->cfg.picard_iters : c->cfg.order + 1;
+  long long nfaces = 0;
+  for (int d = 0; d < 3; ++d) nfaces += (long long)(c->g.n[d] + 1) * (c->g.ncells / c->g.n[d]);
+  const size_t b_dev = round256(sizeof(DevScalars));
+  const size_t b_adjf = round256((size_t)c->g.ncells * 3 * 2 * c->nf * c->nvar * sizeof(double));
+  const size_t b_gface = round256((size_t)nfaces * 6 * sizeof(double));
+  const long long spb = c->fam->adj_scratch_per_block(c->cfg.order, iters);
+  const size_t b_slab = (size_t)spb * sizeof(double);
+  const size_t fixed = b_dev + b_adjf + b_gface;
+  if (fixed + b_slab > kStaticScratchBytes) return ADER_EINVAL;  // grid too large for the array
+  int sms = 0;
+  CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  long long blocks = (long long)sms * c->fam->adj_blocks_per_sm(c->cfg.order);
+  blocks = std::min<long long>(blocks, (long long)((kStaticScratchBytes - fixed) / b_slab));
+  unsigned char* p = (unsigned char*)base;
+  DevScalars* dev_s = (DevScalars*)p;
+  double* adjf = (double*)(p + b_dev);
+  double* gface = (double*)(p + b_dev + b_adjf);
+  double* slab = (double*)(p + fixed);
+  CUDA_OK(launch_set_scalars(dev_s, t_n, dt, c->stream));
+  StepArgs a = make_args(c, dt, 0.0);
+  a.u = u_n;
+  a.dev = dev_s;
+  a.iters = iters;
+  CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
+  AdjArgs j{u_n, lam, dJdu, grad_mat, grad_M, adjf, gface, slab, spb};
+  CUDA_OK(c->fam->adj_run(a, j, c->tab, (int)blocks, c->stream));
   return ADER_OK;
 }
 

@@ -213,6 +213,177 @@ def run_form(ader, synth, wl, prec, args, stream, u0_dev, err_steps):
     return ctx, ms_total, phases, nrec, clocks, err
 
 
+def _dev_state(ctx):
+    import torch
+    t = torch.empty(ctx.count, dtype=torch.float64, device="cuda")
+    ctx.get_state(t)
+    torch.cuda.synchronize()
+    return t
+
+
+def extra_euler2d(ader, synth, stream):
+    """2-D entropy wave, order 3, 27^2 periodic cells, to t = 1 (CFL steps), replayed as CUDA
+    graphs of 2 steps; DOF-updates/s and the density error against the exact solution."""
+    import torch
+    N, nc = 3, (27, 27)
+    cfg = ader.make_config("euler", 2, N, nc, (0, 0), (1, 1), "periodic", synth.cfl_number(N))
+    ctx = ader.Context(cfg, stream=stream.cuda_stream)
+    x, w = ader.reference_nodes(N)
+    u0 = torch.from_numpy(synth.entropy_wave(synth.node_coordinates(x, nc, (0, 0), (1, 1))).reshape(-1).copy()).cuda()
+    torch.cuda.synchronize()
+    ctx.set_state(u0)
+    ctx.run_graph(2, 4, t_end=1.0)  # warm-up and capture
+    ctx.sync()
+    ctx.set_state(u0)
+    ctx.set_time(0.0)
+    steps = 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    while True:
+        ctx.run_graph(2, 64, t_end=1.0)
+        steps += 128
+        if ctx.time() >= 1.0 - 1e-14:
+            break
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    wl = dict(dim=2, order=N, ncell=nc, lo=(0, 0), hi=(1, 1))
+    l2, linf = density_error(ctx, wl, ctx.time(), x, w)
+    dofs = 729 * 16 * 4
+    ctx.close()
+    return {"workload": "euler2d_p3_27 (entropy wave to t = 1)", "steps_launched": steps,
+            "value": dofs * steps / (ms * 1e-3), "unit": "DOF-updates/s (incl. no-op steps after t_end)",
+            "ms_total": ms, "l2_rho_vs_exact": l2, "linf_rho_vs_exact": linf, "dtype": "f64"}
+
+
+def extra_elastic(ader, synth, stream, steps=2, warmup=1):
+    """3-D elastic, order 5, 81^3 cells (h = 0.5 km), seeded material, moment-tensor Ricker source
+    at the centre, 64 receivers on the top face: FP64 and mixed predictor; mixed vs FP64 state."""
+    import torch
+    N, n = 5, 81
+    L = 0.5 * n
+    mat = torch.from_numpy(synth.elastic_material((n,) * 3, seed=1905).reshape(-1).copy()).cuda()
+    out = {"workload": "elastic3d_p5_81", "dofs": n ** 3 * 216 * 9}
+    finals = {}
+    for prec in ("fp64", "mixed"):
+        cfg = ader.make_config("elastic", 3, N, (n,) * 3, (0, 0, 0), (L,) * 3, "absorbing",
+                               synth.cfl_number(N), precision=prec)
+        ctx = ader.Context(cfg, stream=stream.cuda_stream)
+        ctx.set_material(mat)
+        ctx.set_point_source((L / 2,) * 3, synth.moment_tensor(), 2.0, 0.5)
+        seismo = torch.zeros(steps + warmup + 1, 64, 3, dtype=torch.float64, device="cuda")
+        ctx.set_receivers(synth.receivers_top((n,) * 3, (0, 0, 0), (L,) * 3), seismo, steps + warmup + 1)
+        ctx.set_state(torch.zeros(ctx.count, dtype=torch.float64, device="cuda"))
+        ctx.set_time(0.45)  # near the wavelet peak so the source is active
+        for _ in range(warmup):
+            ctx.step()
+        ctx.sync()
+        ctx.enable_timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ph, nr = ctx.phase_times()
+        ctx.enable_timing(False)
+        finals[prec] = _dev_state(ctx)
+        out[prec] = {"ms_per_step": ms / steps, "value": out["dofs"] * steps / (ms * 1e-3),
+                     "predictor_ms": ph["predictor"] / max(nr, 1)}
+        ctx.close()
+        del seismo
+    d = (finals["mixed"] - finals["fp64"]).abs().max().item()
+    out["mixed_vs_fp64_rel_linf"] = d / max(finals["fp64"].abs().max().item(), 1e-300)
+    out["mixed_speedup"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    return out
+
+
+def extra_explosion(ader, synth, stream, steps=4, warmup=2):
+    """3-D spherical explosion, order 3, 64^3 cells on [-1,1]^3, wall boundaries, a-posteriori
+    subcell limiter (7^3 subcells): FP64 step time, troubled cells, conservation."""
+    import torch
+    N, n = 3, 64
+    cfg = ader.make_config("euler", 3, N, (n,) * 3, (-1,) * 3, (1,) * 3, "wall", synth.cfl_number(N),
+                           limiter=1)
+    ctx = ader.Context(cfg, stream=stream.cuda_stream)
+    x, w = ader.reference_nodes(N)
+    X = synth.node_coordinates(x, (n,) * 3, (-1,) * 3, (1,) * 3)
+    Us = synth.explosion(synth.subcell_centres(2 * N + 1, (n,) * 3, (-1,) * 3, (1,) * 3))
+    fl = synth.discontinuous_cells(Us).astype(np.uint8)
+    ctx.set_state(torch.from_numpy(synth.explosion(X).reshape(-1).copy()).cuda())
+    ctx.set_subcell_state(torch.from_numpy(Us.reshape(-1).copy()).cuda(), torch.from_numpy(fl).cuda())
+    W = torch.from_numpy(np.einsum("i,j,k->ijk", w, w, w).reshape(-1)).cuda()
+
+    def totals():
+        st = _dev_state(ctx).view(ctx.cells, -1, 5)
+        return (st * W[None, :, None]).sum(dim=(0, 1))
+
+    m0 = totals()
+    for _ in range(warmup):
+        ctx.step()
+    ctx.sync()
+    ctx.enable_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ph, nr = ctx.phase_times()
+    ctx.enable_timing(False)
+    ctx.sync()
+    m1 = totals()
+    dofs = n ** 3 * 64 * 5
+    out = {"workload": "explosion3d_p3_64 (limiter on)", "ms_per_step": ms / steps,
+           "value": dofs * steps / (ms * 1e-3), "unit": "DOF-updates/s", "dtype": "f64",
+           "troubled_cells_last_step": ctx.troubled_count(),
+           "troubled_fraction": ctx.troubled_count() / n ** 3,
+           "phase_ms_per_step": {k: v / max(nr, 1) for k, v in ph.items()},
+           "mass_rel_drift": abs(float(m1[0] - m0[0])) / abs(float(m0[0])),
+           "energy_rel_drift": abs(float(m1[4] - m0[4])) / abs(float(m0[4])),
+           "steps_run": steps + warmup}
+    ctx.close()
+    return out
+
+
+def extra_ensemble(ader, synth, stream, steps=4):
+    """16 elastic order-4 runs, cube sides drawn by seed from {24,32,40,48,64}, each with its own
+    seeded material and source, mixed predictor, advanced by one CUDA graph per step block."""
+    import torch
+    sides = synth.ensemble_sides(16)
+    cfgs = [ader.make_config("elastic", 3, 4, (s,) * 3, (0, 0, 0), (0.5 * s,) * 3, "absorbing",
+                             synth.cfl_number(4), precision="mixed") for s in sides]
+    ens = ader.Ensemble(cfgs, stream=stream.cuda_stream)
+    dts = []
+    for i, (s, r) in enumerate(zip(sides, ens.runs)):
+        mat = synth.elastic_material((s,) * 3, seed=100 + i)
+        r.set_material(torch.from_numpy(mat.reshape(-1).copy()).cuda())
+        r.set_point_source((0.25 * s,) * 3, synth.moment_tensor(seed=200 + i), 2.0, 0.5)
+        r.set_state(torch.zeros(r.count, dtype=torch.float64, device="cuda"))
+        r.set_time(0.45)
+        vpmax = float(np.sqrt((mat[:, 1] + 2 * mat[:, 2]) / mat[:, 0]).max())
+        dts.append(synth.cfl_number(4) / (3 * 9) * 0.5 / vpmax)
+    dt = min(dts)  # one fixed dt for the ensemble (as for the adjoint runs)
+    best = ens.autotune(dt)
+    ens.step(2, dt=dt)
+    ens.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ens.step(steps, dt=dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ens.sync()
+    dofs = sum(s ** 3 for s in sides) * 125 * 9
+    ens.close()
+    return {"workload": "ensemble16_elastic_p4", "sides": sides, "dofs": dofs,
+            "ms_per_step": ms / steps, "value": dofs * steps / (ms * 1e-3), "unit": "DOF-updates/s",
+            "dtype": "f32+f64", "autotuned": {"branches": best[0], "steps_per_graph": best[1],
+                                              "ms_per_step_at_tuning": best[2]}}
+
+
 _WORLD = [1]
 
 
@@ -245,6 +416,8 @@ def main():
                     help="steps after which the error against the exact solution is measured")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other workloads (2-D Euler, elastic, explosion, ensemble)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     D, N = wl["dim"], wl["order"]
@@ -357,6 +530,16 @@ def main():
             "dtype": "f64" if args.prec == "fp64" else "f32+f64",
             "data": "synthetic", "config": config, "roofline": roof, "forms": forms_out,
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": head["clocks"]}
+    if not args.no_extra and world == 1:
+        extra = {}
+        for name, fn in (("euler2d_p3_27", extra_euler2d), ("explosion3d_p3_64", extra_explosion),
+                         ("elastic3d_p5_81", extra_elastic), ("ensemble16_elastic_p4", extra_ensemble)):
+            try:
+                extra[name] = fn(ader, synth, stream)
+            except Exception as exc:  # report, keep the headline line
+                extra[name] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+            torch.cuda.empty_cache()
+        line["workloads"] = extra
     if world == 1 and rank == 0:
         v, desc, cores, _ = oracle_sample(wl, args.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": "DOF-updates/s", "cores": cores,

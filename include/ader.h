@@ -243,7 +243,7 @@ ader_status ader_ensemble_step(ader_ensemble* ens, int steps, double dt, double 
 ader_status ader_ensemble_sync(ader_ensemble* ens);
 /* Launch shape: branches in [1, 16], steps_per_graph even and >= 2. */
 ader_status ader_ensemble_set_launch(ader_ensemble* ens, int branches, int steps_per_graph);
-/* Autotuner: times every (branches, steps_per_graph) candidate with fixed dt > 0 on the current
+/* Autotuner: times every (branches in {1,2,4}, steps_per_graph in {2,4}) candidate with fixed dt > 0 on the current
  * states (which it restores), keeps the fastest; best[2] and *ms_per_step receive the choice and
  * its time per step.  Synchronises. */
 ader_status ader_ensemble_autotune(ader_ensemble* ens, double dt, int* best, double* ms_per_step);

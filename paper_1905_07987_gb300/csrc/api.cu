@@ -1215,8 +1215,8 @@ ader_status ader_ensemble_autotune(ader_ensemble* e, double dt, int* best, doubl
     CUDA_OK(cudaMemcpyAsync(save[r], e->runs[r]->u, e->runs[r]->ndof * sizeof(double),
                             cudaMemcpyDeviceToDevice, e->stream));
   }
-  const int cand_b[] = {1, 2, 4, 8};
-  const int cand_s[] = {2, 4, 8};
+  const int cand_b[] = {1, 2, 4};
+  const int cand_s[] = {2, 4};
   cudaEvent_t t0, t1;
   CUDA_OK(cudaEventCreate(&t0));
   CUDA_OK(cudaEventCreate(&t1));
@@ -1231,12 +1231,12 @@ ader_status ader_ensemble_autotune(ader_ensemble* e, double dt, int* best, doubl
       ader_status st = ader_ensemble_step(e, sp, dt, 0.0);  // capture + warm-up
       if (st != ADER_OK) break;
       CUDA_OK(cudaEventRecord(t0, e->stream));
-      st = ader_ensemble_step(e, 2 * sp, dt, 0.0);
+      st = ader_ensemble_step(e, sp, dt, 0.0);
       CUDA_OK(cudaEventRecord(t1, e->stream));
       CUDA_OK(cudaEventSynchronize(t1));
       float ms = 0.f;
       CUDA_OK(cudaEventElapsedTime(&ms, t0, t1));
-      const double per = ms / (2.0 * sp);
+      const double per = ms / sp;
       if (st == ADER_OK && per < best_ms) {
         best_ms = per;
         bb = b;

@@ -94,7 +94,7 @@ def test_autotune_keeps_results_and_picks_a_valid_shape():
         setup_member(ens.runs[i], s, order, seed=i)
     before = states(ens.runs)
     b, spg, ms = ens.autotune(1e-3)
-    assert b in (1, 2, 4, 8) and spg in (2, 4, 8) and ms > 0
+    assert b in (1, 2, 4) and spg in (2, 4) and ms > 0
     after = states(ens.runs)
     for x, y in zip(before, after):
         assert np.array_equal(x, y)

@@ -48,9 +48,11 @@ struct Tables {
 struct TablesF {
   float Dh[MAXN][MAXN], Dl[MAXN][MAXN];    // strong derivative D
   float Wh[MAXN][MAXN], Wl[MAXN][MAXN];    // weak derivative Dw = c1 e1^T - c0 e0^T - D
-  float Kw[MAXN][MAXN];                    // K1^{-1} diag(w)
-  float kw1[MAXN];                         // row sums of Kw
-  float w[MAXN];
+  float Kw[MAXN][MAXN], Kwl[MAXN][MAXN];   // K1^{-1} diag(w) (hi, lo)
+  float kw1[MAXN], kw1l[MAXN];             // row sums of Kw (hi, lo)
+  float w[MAXN], wl[MAXN];
+  float ihh[3], ihl[3];                    // 1/h_d (hi, lo)
+  float g1h, g1l;                          // gamma - 1 (hi, lo)
   float e0h[MAXN], e0l[MAXN], e1h[MAXN], e1l[MAXN];
 };
 

@@ -197,11 +197,11 @@ void build_tables_f(int order, const Tables& T, TablesF& F) {
       split_f(T.D[i][m], F.Dh[i][m], F.Dl[i][m]);
       const double w = T.c1[i] * T.e1[m] - T.c0[i] * T.e0[m] - T.D[i][m];
       split_f(w, F.Wh[i][m], F.Wl[i][m]);
-      F.Kw[i][m] = (float)T.Kw[i][m];
+      split_f(T.Kw[i][m], F.Kw[i][m], F.Kwl[i][m]);
       rs += T.Kw[i][m];
     }
-    F.kw1[i] = (float)rs;
-    F.w[i] = (float)T.w[i];
+    split_f(rs, F.kw1[i], F.kw1l[i]);
+    split_f(T.w[i], F.w[i], F.wl[i]);
     split_f(T.e0[i], F.e0h[i], F.e0l[i]);
     split_f(T.e1[i], F.e1h[i], F.e1l[i]);
   }
@@ -471,6 +471,8 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
     return ADER_EINVAL;
   }
   build_tables_f(cfg->order, c->tab, c->tabf);
+  for (int d = 0; d < 3; ++d) split_f(c->g.inv_h[d], c->tabf.ihh[d], c->tabf.ihl[d]);
+  split_f(c->p.gamma - 1.0, c->tabf.g1h, c->tabf.g1l);
   const int n = cfg->order + 1;
   c->nodes = 1;
   for (int d = 0; d < cfg->dim; ++d) c->nodes *= n;

@@ -4,11 +4,13 @@
 //   dq^{r+1} = dt Kw [ B0 + dR(dq^r) ],   B0 = R(u^n),   dR(dq) = R(u^n + dq) - R(u^n)
 // B0 and every term that carries the O(1) size of the solution (the flux F(u^n), its derivative,
 // the face extrapolations of u^n and F(u^n)) are formed in FP64 or in float-float (hi + lo pairs
-// of binary32 with error-free transformations, about 44 significant bits) on the FP32 pipe; the
-// Picard iterations, the flux increments F(u+dq) - F(u) (written so that no O(1) terms cancel)
-// and their contractions run in binary32.  The corrector, Riemann solver, CFL condition and
-// pressure / sound speed of the face states stay FP64 (other kernels).  Rounding in binary32
-// therefore perturbs only O(dt) increments: relative error ~1e-7 of the per-step change.
+// of binary32 with error-free transformations, about 44 significant bits) on the FP32 pipe.
+// The first N Picard iterations, their flux increments F(u+dq) - F(u) (written so that no O(1)
+// terms cancel) and contractions run in plain binary32 -- each iteration damps the error of the
+// previous one by the CFL-sized factor |dt Kw dR/dq|.  The last iteration's time solve, the final
+// flux increments, their time averages and every contraction of the epilogue run in float-float,
+// so that no binary32 rounding of the final predictor reaches the update.  The corrector, Riemann
+// solver, CFL condition and pressure / sound speed of the face states stay FP64 (other kernels).
 #pragma once
 #include "kernels.cuh"
 
@@ -24,6 +26,37 @@ __device__ __forceinline__ ff ff_split(double x) {
 }
 __device__ __forceinline__ double ff_to_d(ff a) { return (double)a.h + (double)a.l; }
 
+__device__ __forceinline__ ff ff_norm(float s, float e) {
+  const float h = s + e;
+  return {h, e - (h - s)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const float s = a.h + b.h;
+  const float bv = s - a.h;
+  const float e = (a.h - (s - bv)) + (b.h - bv);
+  return ff_norm(s, e + (a.l + b.l));
+}
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, {-b.h, -b.l}); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return ff_norm(p, e);
+}
+__device__ __forceinline__ ff ff_mulf(ff a, float b) {
+  const float p = a.h * b;
+  float e = fmaf(a.h, b, -p);
+  e = fmaf(a.l, b, e);
+  return ff_norm(p, e);
+}
+// a / b: binary32 quotient, float-float residual, one correction.
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+  const float q1 = a.h / b.h;
+  const ff r = ff_sub(a, ff_mulf(b, q1));
+  return ff_norm(q1, r.h / b.h);
+}
+
 // acc += (ah + al) * (bh + bl): exact product of the high parts by FMA, cross terms, two-sum.
 __device__ __forceinline__ void ff_mac(ff& acc, float ah, float al, float bh, float bl) {
   const float p = ah * bh;
@@ -37,10 +70,10 @@ __device__ __forceinline__ void ff_mac(ff& acc, float ah, float al, float bh, fl
   acc.l = acc.l + (err + e);
 }
 
-// Per-node FP32 base data of the Euler increments.
+// Per-node base data of the Euler increments (float-float; the binary32 iterations use the hi parts).
 template <int D>
 struct EulerBase {
-  float rho, E, p, j[D], v[D];
+  ff rho, E, p, j[D], v[D];
 };
 
 template <class P, int D, int N>
@@ -50,49 +83,80 @@ struct CfgM {
   static constexpr int NF = C::NF, FR = C::FR, TPB = C::TPB, LPT = C::LPT, NPT = C::NPT;
   static constexpr int NPS = (NS + TPB - 1) / TPB;
   static constexpr bool EULER = P::CONS && !P::LINEAR;
-  static constexpr int BW = EULER ? 2 * D + 3 : 1;
+  static constexpr int BW = EULER ? D + 1 : 1;               // v0[D], p0 (float-float)
   static constexpr int FS = P::CONS ? cmax(n, D + 1) : 0;
   static constexpr size_t B_FB0 = P::CONS ? (size_t)D * NL * sizeof(ff) : 0;
   static constexpr size_t B_UFF = (size_t)NL * sizeof(ff);
-  static constexpr size_t B_BF = EULER ? (size_t)NS * BW * sizeof(float) : 0;
-  static constexpr size_t B_DQ = (size_t)n * NL * sizeof(float);
-  static constexpr size_t B_DF = (size_t)FS * NL * sizeof(float);
-  static constexpr size_t SMEM = B_FB0 + B_UFF + B_BF + B_DQ + B_DF;
+  static constexpr size_t B_BF = EULER ? (size_t)NS * BW * sizeof(ff) : 0;
+  static constexpr size_t B_DQ = (size_t)n * NL * sizeof(float);   // hi, and again for lo
+  static constexpr size_t B_DF = (size_t)FS * NL * sizeof(float);  // hi, and again for lo
+  static constexpr size_t SMEM = B_FB0 + B_UFF + B_BF + 2 * B_DQ + 2 * B_DF;
 };
-
-// Flux increment F_d(u + dq) - F_d(u) in binary32 from the node's base data.
-template <class P, int D>
-struct Incr;
 
 template <int D>
-struct Incr<Euler<D>, D> {
-  static constexpr int NV = D + 2;
-  struct Aux {
-    float dv[D], dp;
-  };
-  __device__ static void aux(const EulerBase<D>& b, const float* dq, float gm1, Aux& a) {
-    const float irq = 1.0f / (b.rho + dq[0]);
-    float djv = 0.f;
+__device__ __forceinline__ EulerBase<D> load_base(const ff* uff, const ff* bff, int j) {
+  constexpr int NV = D + 2;
+  EulerBase<D> b;
+  b.rho = uff[j * NV];
+  b.E = uff[j * NV + NV - 1];
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-      a.dv[i] = (dq[1 + i] - b.v[i] * dq[0]) * irq;
-      djv = fmaf(dq[1 + i], b.v[i] + a.dv[i], fmaf(b.j[i], a.dv[i], djv));
-    }
-    a.dp = gm1 * (dq[NV - 1] - 0.5f * djv);
+  for (int i = 0; i < D; ++i) {
+    b.j[i] = uff[j * NV + 1 + i];
+    b.v[i] = bff[j * (D + 1) + i];
   }
-  __device__ static void flux(const EulerBase<D>& b, const float* dq, const Aux& a, int d, float* F) {
-    const float vd = b.v[d] + a.dv[d];
-    F[0] = dq[1 + d];
-#pragma unroll
-    for (int i = 0; i < D; ++i) F[1 + i] = fmaf(dq[1 + i], vd, b.j[i] * a.dv[d]);
-    F[1 + d] += a.dp;
-    F[NV - 1] = fmaf(dq[NV - 1] + a.dp, vd, (b.E + b.p) * a.dv[d]);
-  }
-};
+  b.p = bff[j * (D + 1) + D];
+  return b;
+}
 
+// Flux increment F_d(u + dq) - F_d(u) of the Euler equations in binary32 (hi parts of the base):
+//   dv = (dj - v0 drho) / (rho0 + drho),  dp = (gamma-1)(dE - (dj.(v0+dv) + j0.dv)/2),
+//   dF = (dj_d, dj (v0_d+dv_d) + j0 dv_d + dp e_d, (dE+dp)(v0_d+dv_d) + (E0+p0) dv_d).
+template <int D>
+__device__ __forceinline__ void dflux_f(const EulerBase<D>& b, const float* dq, float g1h, float g1l,
+                                        int d, float* F) {
+  constexpr int NV = D + 2;
+  const float irq = 1.0f / (b.rho.h + dq[0]);
+  float dv[D], djv = 0.f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    dv[i] = (dq[1 + i] - b.v[i].h * dq[0]) * irq;
+    djv = fmaf(dq[1 + i], b.v[i].h + dv[i], fmaf(b.j[i].h, dv[i], djv));
+  }
+  const float x = dq[NV - 1] - 0.5f * djv;
+  const float dp = fmaf(g1h, x, g1l * x);
+  const float vd = b.v[d].h + dv[d];
+  F[0] = dq[1 + d];
+#pragma unroll
+  for (int i = 0; i < D; ++i) F[1 + i] = fmaf(dq[1 + i], vd, b.j[i].h * dv[d]);
+  F[1 + d] += dp;
+  F[NV - 1] = fmaf(dq[NV - 1] + dp, vd, (b.E.h + b.p.h) * dv[d]);
+}
+
+// The same increment in float-float.
+template <int D>
+__device__ __forceinline__ void dflux_ff(const EulerBase<D>& b, const ff* dq, ff g1, int d, ff* F) {
+  constexpr int NV = D + 2;
+  const ff den = ff_add(b.rho, dq[0]);
+  ff dv[D], djv = {0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    dv[i] = ff_div(ff_sub(dq[1 + i], ff_mul(b.v[i], dq[0])), den);
+    djv = ff_add(djv, ff_add(ff_mul(dq[1 + i], ff_add(b.v[i], dv[i])), ff_mul(b.j[i], dv[i])));
+  }
+  const ff dp = ff_mul(g1, ff_sub(dq[NV - 1], ff_mulf(djv, 0.5f)));
+  const ff vd = ff_add(b.v[d], dv[d]);
+  F[0] = dq[1 + d];
+#pragma unroll
+  for (int i = 0; i < D; ++i) F[1 + i] = ff_add(ff_mul(dq[1 + i], vd), ff_mul(b.j[i], dv[d]));
+  F[1 + d] = ff_add(F[1 + d], dp);
+  F[NV - 1] = ff_add(ff_mul(ff_add(dq[NV - 1], dp), vd), ff_mul(ff_add(b.E, b.p), dv[d]));
+}
+
+// binary32 increments at the space-time nodes owned by this thread (iterations).
 template <class M, int d, class P, int D>
-__device__ __forceinline__ void dflux_nodes(const float* dqs, const float* bf, const PdeParams& pp,
-                                            float* dFs, int tid) {
+__device__ __forceinline__ void dflux_nodes(const float* dqs, const ff* uff, const ff* bff,
+                                            const PdeParams& pp, float g1h, float g1l, float* dFs,
+                                            int tid) {
   constexpr int NV = M::NV, NS = M::NS;
 #pragma unroll
   for (int k = 0; k < M::NPT; ++k) {
@@ -103,20 +167,7 @@ __device__ __forceinline__ void dflux_nodes(const float* dqs, const float* bf, c
       for (int v = 0; v < NV; ++v) q[v] = dqs[node * NV + v];
       float F[NV];
       if constexpr (M::EULER) {
-        const int j = node % NS;
-        EulerBase<D> b;
-        const float* s = bf + j * M::BW;
-        b.rho = s[0];
-        b.E = s[1];
-        b.p = s[2];
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-          b.j[i] = s[3 + i];
-          b.v[i] = s[3 + D + i];
-        }
-        typename Incr<P, D>::Aux a;
-        Incr<P, D>::aux(b, q, (float)(pp.gamma - 1.0), a);
-        Incr<P, D>::flux(b, q, a, d, F);
+        dflux_f<D>(load_base<D>(uff, bff, node % NS), q, g1h, g1l, d, F);
       } else {
         F[0] = (float)pp.a[d] * q[0];
       }
@@ -126,10 +177,42 @@ __device__ __forceinline__ void dflux_nodes(const float* dqs, const float* bf, c
   }
 }
 
-// R[k][t] += coef * sum_m D[j_d][m] X[t][(j, j_d -> m)][src]  in binary32
-template <class M, int d, bool NCP>
-__device__ __forceinline__ void contract_f(const float* X, const TablesF& T, float coef, double irho,
-                                           double lam, double mu, float (&R)[M::LPT][M::n], int tid) {
+// float-float increments at the owned space-time nodes (epilogue): hi -> dFs, lo -> dFl.
+template <class M, int d, class P, int D>
+__device__ __forceinline__ void dflux_nodes_ff(const float* dqs, const float* dql, const ff* uff,
+                                               const ff* bff, const PdeParams& pp, ff g1,
+                                               float* dFs, float* dFl, int tid) {
+  constexpr int NV = M::NV, NS = M::NS;
+#pragma unroll 1
+  for (int k = 0; k < M::NPT; ++k) {
+    const int node = tid + k * M::TPB;
+    if (node < M::NST) {
+      ff q[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) q[v] = {dqs[node * NV + v], dql[node * NV + v]};
+      ff F[NV];
+      if constexpr (M::EULER) {
+        dflux_ff<D>(load_base<D>(uff, bff, node % NS), q, g1, d, F);
+      } else {
+        const double a = pp.a[d];
+        const float ah = (float)a;
+        F[0] = ff_mul(q[0], {ah, (float)(a - (double)ah)});
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        dFs[node * NV + v] = F[v].h;
+        dFl[node * NV + v] = F[v].l;
+      }
+    }
+  }
+}
+
+// R[k][t] += cf[d][v] * sum_m D[j_d][m] X[t][(j, j_d -> m)][src]  in binary32, with the per-cell
+// coefficients cf = {hi[3][NV], lo[3][NV]} in shared memory; with LO the lo parts of the
+// coefficient and of the float-float derivative matrix are added (no rounding of fixed tables).
+template <class M, int d, bool NCP, bool LO = false>
+__device__ __forceinline__ void contract_f(const float* X, const TablesF& T, const float* cf,
+                                           float (&R)[M::LPT][M::n], int tid) {
   constexpr int n = M::n, NV = M::NV, NL = M::NL, TPB = M::TPB, st = ipow(n, d);
 #pragma unroll
   for (int k = 0; k < M::LPT; ++k) {
@@ -137,20 +220,24 @@ __device__ __forceinline__ void contract_f(const float* X, const TablesF& T, flo
     if (l < NL) {
       const int j = l / NV, v = l - (l / NV) * NV;
       int s = v;
-      float c = coef;
       if constexpr (NCP) {
         s = Elastic::src(d, v);
         if (s < 0) continue;
-        c = (float)(-Elastic::coef_ir(d, v, irho, lam, mu)) * coef;
       }
+      const float c = cf[d * NV + v], clo = cf[3 * NV + d * NV + v];
       const int jd = digit<n, d>(j);
       const int j0 = j - jd * st;
 #pragma unroll
       for (int t = 0; t < n; ++t) {
-        float acc = 0.f;
+        float acc = 0.f, lo = 0.f;
 #pragma unroll
-        for (int m = 0; m < n; ++m) acc = fmaf(T.Dh[jd][m], X[t * NL + (j0 + m * st) * NV + s], acc);
-        R[k][t] = fmaf(c, acc, R[k][t]);
+        for (int m = 0; m < n; ++m) {
+          const float x = X[t * NL + (j0 + m * st) * NV + s];
+          acc = fmaf(T.Dh[jd][m], x, acc);
+          if constexpr (LO) lo = fmaf(T.Dl[jd][m], x, lo);
+        }
+        const float x = acc + lo;
+        R[k][t] = fmaf(c, x, LO ? fmaf(clo, x, R[k][t]) : R[k][t]);
       }
     }
   }
@@ -164,23 +251,41 @@ __global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
   constexpr int n = M::n, NS = M::NS, NV = M::NV, NL = M::NL, TPB = M::TPB, LPT = M::LPT;
   constexpr int NF = M::NF, FR = M::FR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ff* FB0 = reinterpret_cast<ff*>(smem_raw);                        // [D][NL] F_d(u)/h_d
-  ff* uff = reinterpret_cast<ff*>(smem_raw + M::B_FB0);             // [NL]
-  float* bf = reinterpret_cast<float*>(smem_raw + M::B_FB0 + M::B_UFF);  // [NS][BW]
-  float* dqs = reinterpret_cast<float*>(smem_raw + M::B_FB0 + M::B_UFF + M::B_BF);  // [n][NL]
-  float* dFs = dqs + n * NL;                                         // [FS][NL]
+  unsigned char* p = smem_raw;
+  ff* FB0 = reinterpret_cast<ff*>(p);  p += M::B_FB0;    // [D][NL] F_d(u)/h_d
+  ff* uff = reinterpret_cast<ff*>(p);  p += M::B_UFF;    // [NL] u
+  ff* bff = reinterpret_cast<ff*>(p);  p += M::B_BF;     // [NS][D+1] v0, p0 (Euler)
+  float* dqs = reinterpret_cast<float*>(p);  p += M::B_DQ;  // [n][NL] dq (hi)
+  float* dql = reinterpret_cast<float*>(p);  p += M::B_DQ;  // [n][NL] dq (lo, last iterate)
+  float* dFs = reinterpret_cast<float*>(p);  p += M::B_DF;  // [FS][NL] flux increments (hi)
+  float* dFl = reinterpret_cast<float*>(p);                 // [FS][NL] (lo)
   const long long c = blockIdx.x;
   const int tid = threadIdx.x;
   const double dt = A.dev->dt;
   const float dtf = (float)dt;
+  const ff dtff = {dtf, (float)(dt - (double)dtf)};
   const double tn = A.dev->t;
   const double* u = A.u + c * NL;
+  const ff g1 = {F.g1h, F.g1l};
 
   double irho = 0.0, lam = 0.0, mu = 0.0;
   if constexpr (P::NCP) {
     irho = 1.0 / A.mat[c * 3 + 0];
     lam = A.mat[c * 3 + 1];
     mu = A.mat[c * 3 + 2];
+  }
+  // per-cell contraction coefficients: -1/h_d, or -coef(d,v)/h_d for the rows of B_d, as
+  // (hi, lo) binary32 pairs and as FP64
+  __shared__ float cf[2 * 3 * NV];
+  __shared__ double cfd[3 * NV];
+  if (tid < 3 * NV) {
+    const int d = tid / NV, v = tid % NV;
+    double cd = d < D ? -A.g.inv_h[d] : 0.0;
+    if constexpr (P::NCP) cd = -Elastic::coef_ir(d, v, irho, lam, mu) * A.g.inv_h[d];
+    const float h = (float)cd;
+    cf[tid] = h;
+    cf[3 * NV + tid] = (float)(cd - (double)h);
+    cfd[tid] = cd;
   }
   const bool has_src = (A.src.cell == c);
   double ric[n];
@@ -224,28 +329,23 @@ __global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
           for (int v = 0; v < NV; ++v) FB0[d * NL + j * NV + v] = ff_split(Fd[v] * A.g.inv_h[d]);
         }
         if constexpr (M::EULER) {
-          float* s = bf + j * M::BW;
-          s[0] = (float)q[0];
-          s[1] = (float)q[NV - 1];
-          s[2] = (float)ax.p;
 #pragma unroll
-          for (int i = 0; i < D; ++i) {
-            s[3 + i] = (float)q[1 + i];
-            s[3 + D + i] = (float)(q[1 + i] * ax.ir);
-          }
+          for (int i = 0; i < D; ++i) bff[j * (D + 1) + i] = ff_split(q[1 + i] * ax.ir);
+          bff[j * (D + 1) + D] = ff_split(ax.p);
         }
       }
     }
   }
   __syncthreads();
 
-  // B0 (strong form, binary32 for the iterations) and the weak-form volume base (FP64).
-  float b0f[LPT];
+  // B0: strong form for the iterations (hi, lo), weak-form volume base (FP64).
+  float b0f[LPT], b0l[LPT];
   double b0vol[LPT];
 #pragma unroll
   for (int k = 0; k < LPT; ++k) {
     const int l = tid + k * TPB;
     b0f[k] = 0.f;
+    b0l[k] = 0.f;
     b0vol[k] = 0.0;
     if (l < NL) {
       const int j = l / NV, v = l - (l / NV) * NV;
@@ -271,46 +371,53 @@ __global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
               const ff f = uff[(j0 + m * st) * NV + s];
               ff_mac(g, F.Dh[jd][m], F.Dl[jd][m], f.h, f.l);
             }
-            // -(1/h) coef * (D q): scale in FP64 (one multiply per direction)
-            b0vol[k] = fma(-A.g.inv_h[d] * Elastic::coef_ir(d, v, irho, lam, mu), ff_to_d(g), b0vol[k]);
+            b0vol[k] = fma(cfd[d * NV + v], ff_to_d(g), b0vol[k]);
           }
         }
       }
-      if constexpr (P::CONS) {
-        b0f[k] = -(float)ff_to_d(aS);
-        b0vol[k] = ff_to_d(aW);
-      } else {
-        b0f[k] = (float)b0vol[k];
-      }
+      const double b0 = P::CONS ? -ff_to_d(aS) : b0vol[k];
+      b0f[k] = (float)b0;
+      b0l[k] = (float)(b0 - (double)b0f[k]);
+      if constexpr (P::CONS) b0vol[k] = ff_to_d(aW);
     }
   }
 
-  // ---- Picard iterations on dq (binary32) ----------------------------------------------
+  // ---- Picard iterations on dq ----------------------------------------------------------
   float R[LPT][n];
   for (int it = 0; it < A.iters; ++it) {
 #pragma unroll
     for (int k = 0; k < LPT; ++k)
 #pragma unroll
       for (int t = 0; t < n; ++t) R[k][t] = 0.f;
+    const bool last = (it == A.iters - 1);
     if (it > 0) {
       if constexpr (P::CONS) {
-        dflux_nodes<M, 0, P, D>(dqs, bf, A.p, dFs, tid);
+        dflux_nodes<M, 0, P, D>(dqs, uff, bff, A.p, F.g1h, F.g1l, dFs, tid);
         __syncthreads();
-        contract_f<M, 0, false>(dFs, F, -(float)A.g.inv_h[0], 0, 0, 0, R, tid);
+        if (last) contract_f<M, 0, false, true>(dFs, F, cf, R, tid);
+        else contract_f<M, 0, false>(dFs, F, cf, R, tid);
         __syncthreads();
-        dflux_nodes<M, 1, P, D>(dqs, bf, A.p, dFs, tid);
+        dflux_nodes<M, 1, P, D>(dqs, uff, bff, A.p, F.g1h, F.g1l, dFs, tid);
         __syncthreads();
-        contract_f<M, 1, false>(dFs, F, -(float)A.g.inv_h[1], 0, 0, 0, R, tid);
+        if (last) contract_f<M, 1, false, true>(dFs, F, cf, R, tid);
+        else contract_f<M, 1, false>(dFs, F, cf, R, tid);
         __syncthreads();
         if constexpr (D == 3) {
-          dflux_nodes<M, 2, P, D>(dqs, bf, A.p, dFs, tid);
+          dflux_nodes<M, 2, P, D>(dqs, uff, bff, A.p, F.g1h, F.g1l, dFs, tid);
           __syncthreads();
-          contract_f<M, 2, false>(dFs, F, -(float)A.g.inv_h[2], 0, 0, 0, R, tid);
+          if (last) contract_f<M, 2, false, true>(dFs, F, cf, R, tid);
+          else contract_f<M, 2, false>(dFs, F, cf, R, tid);
         }
       } else {
-        contract_f<M, 0, true>(dqs, F, (float)A.g.inv_h[0], irho, lam, mu, R, tid);
-        contract_f<M, 1, true>(dqs, F, (float)A.g.inv_h[1], irho, lam, mu, R, tid);
-        contract_f<M, 2, true>(dqs, F, (float)A.g.inv_h[2], irho, lam, mu, R, tid);
+        if (last) {
+          contract_f<M, 0, true, true>(dqs, F, cf, R, tid);
+          contract_f<M, 1, true, true>(dqs, F, cf, R, tid);
+          contract_f<M, 2, true, true>(dqs, F, cf, R, tid);
+        } else {
+          contract_f<M, 0, true>(dqs, F, cf, R, tid);
+          contract_f<M, 1, true>(dqs, F, cf, R, tid);
+          contract_f<M, 2, true>(dqs, F, cf, R, tid);
+        }
       }
     }
     if (has_src) {
@@ -334,68 +441,89 @@ __global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
       if (l < NL) {
 #pragma unroll
         for (int t = 0; t < n; ++t) {
-          float acc = F.kw1[t] * b0f[k];
+          if (last) {  // float-float time solve: dq = dt (kw1 B0 + Kw R)
+            ff acc = {0.f, 0.f};
+            ff_mac(acc, F.kw1[t], F.kw1l[t], b0f[k], b0l[k]);
 #pragma unroll
-          for (int m = 0; m < n; ++m) acc = fmaf(F.Kw[t][m], R[k][m], acc);
-          dqs[t * NL + l] = dtf * acc;
+            for (int m = 0; m < n; ++m) ff_mac(acc, F.Kw[t][m], F.Kwl[t][m], R[k][m], 0.f);
+            const ff q = ff_mul(dtff, ff_norm(acc.h, acc.l));
+            dqs[t * NL + l] = q.h;
+            dql[t * NL + l] = q.l;
+          } else {
+            float acc = F.kw1[t] * b0f[k];
+#pragma unroll
+            for (int m = 0; m < n; ++m) acc = fmaf(F.Kw[t][m], R[k][m], acc);
+            dqs[t * NL + l] = dtf * acc;
+            dql[t * NL + l] = 0.f;
+          }
         }
       }
     }
     __syncthreads();
   }
 
-  // ---- epilogue --------------------------------------------------------------------------
-  float dqb[LPT];
+  // ---- epilogue in float-float -------------------------------------------------------------
+  ff dqb[LPT];
 #pragma unroll
   for (int k = 0; k < LPT; ++k) {
     const int l = tid + k * TPB;
-    dqb[k] = 0.f;
+    dqb[k] = {0.f, 0.f};
     if (l < NL) {
 #pragma unroll
-      for (int t = 0; t < n; ++t) dqb[k] = fmaf(F.w[t], dqs[t * NL + l], dqb[k]);
+      for (int t = 0; t < n; ++t) ff_mac(dqb[k], F.w[t], F.wl[t], dqs[t * NL + l], dql[t * NL + l]);
     }
   }
-  float* dqbs;  // time-averaged dq [NL]
-  float* dFbs;  // time-averaged flux increments [D][NL]
+  float *qbh, *qbl;   // time-averaged dq [NL] (hi, lo)
+  float *fbh, *fbl;   // time-averaged flux increments [D][NL] (hi, lo)
   if constexpr (P::CONS) {
-    float FBv[D][LPT];
+    ff FBv[D][LPT];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      if (d == 0) dflux_nodes<M, 0, P, D>(dqs, bf, A.p, dFs, tid);
-      if (d == 1) dflux_nodes<M, 1, P, D>(dqs, bf, A.p, dFs, tid);
+      if (d == 0) dflux_nodes_ff<M, 0, P, D>(dqs, dql, uff, bff, A.p, g1, dFs, dFl, tid);
+      if (d == 1) dflux_nodes_ff<M, 1, P, D>(dqs, dql, uff, bff, A.p, g1, dFs, dFl, tid);
       if constexpr (D == 3)
-        if (d == 2) dflux_nodes<M, 2, P, D>(dqs, bf, A.p, dFs, tid);
+        if (d == 2) dflux_nodes_ff<M, 2, P, D>(dqs, dql, uff, bff, A.p, g1, dFs, dFl, tid);
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < LPT; ++k) {
         const int l = tid + k * TPB;
-        FBv[d][k] = 0.f;
+        FBv[d][k] = {0.f, 0.f};
         if (l < NL) {
 #pragma unroll
-          for (int t = 0; t < n; ++t) FBv[d][k] = fmaf(F.w[t], dFs[t * NL + l], FBv[d][k]);
+          for (int t = 0; t < n; ++t) ff_mac(FBv[d][k], F.w[t], F.wl[t], dFs[t * NL + l], dFl[t * NL + l]);
         }
       }
       __syncthreads();
     }
-    dqbs = dFs;
-    dFbs = dFs + NL;
+    qbh = dFs;
+    qbl = dFl;
+    fbh = dFs + NL;
+    fbl = dFl + NL;
 #pragma unroll
     for (int k = 0; k < LPT; ++k) {
       const int l = tid + k * TPB;
       if (l < NL) {
-        dqbs[l] = dqb[k];
+        qbh[l] = dqb[k].h;
+        qbl[l] = dqb[k].l;
 #pragma unroll
-        for (int d = 0; d < D; ++d) dFbs[d * NL + l] = FBv[d][k];
+        for (int d = 0; d < D; ++d) {
+          fbh[d * NL + l] = FBv[d][k].h;
+          fbl[d * NL + l] = FBv[d][k].l;
+        }
       }
     }
   } else {
-    dqbs = dqs;
-    dFbs = nullptr;
+    qbh = dqs;
+    qbl = dql;
+    fbh = fbl = nullptr;
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < LPT; ++k) {
       const int l = tid + k * TPB;
-      if (l < NL) dqbs[l] = dqb[k];
+      if (l < NL) {
+        qbh[l] = dqb[k].h;
+        qbl[l] = dqb[k].l;
+      }
     }
   }
   __syncthreads();
@@ -406,28 +534,34 @@ __global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
     const int l = tid + k * TPB;
     if (l < NL) {
       const int j = l / NV, v = l - (l / NV) * NV;
-      float dvol = 0.f;
+      ff dvol = {0.f, 0.f};
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         const int st = (d == 0 ? 1 : (d == 1 ? n : n * n));
         const int jd = (j / st) % n;
         const int j0 = j - jd * st;
         if constexpr (P::CONS) {
-          float a = 0.f;
+          ff a = {0.f, 0.f};
 #pragma unroll
-          for (int m = 0; m < n; ++m) a = fmaf(F.Wh[jd][m], dFbs[d * NL + (j0 + m * st) * NV + v], a);
-          dvol = fmaf((float)A.g.inv_h[d], a, dvol);
+          for (int m = 0; m < n; ++m) {
+            const int i = d * NL + (j0 + m * st) * NV + v;
+            ff_mac(a, F.Wh[jd][m], F.Wl[jd][m], fbh[i], fbl[i]);
+          }
+          dvol = ff_add(dvol, ff_mul(ff_norm(a.h, a.l), {F.ihh[d], F.ihl[d]}));
         } else {
           const int s = Elastic::src(d, v);
           if (s >= 0) {
-            float a = 0.f;
+            ff a = {0.f, 0.f};
 #pragma unroll
-            for (int m = 0; m < n; ++m) a = fmaf(F.Dh[jd][m], dqbs[(j0 + m * st) * NV + s], a);
-            dvol = fmaf((float)(-A.g.inv_h[d] * Elastic::coef_ir(d, v, irho, lam, mu)), a, dvol);
+            for (int m = 0; m < n; ++m) {
+              const int i = (j0 + m * st) * NV + s;
+              ff_mac(a, F.Dh[jd][m], F.Dl[jd][m], qbh[i], qbl[i]);
+            }
+            dvol = ff_add(dvol, ff_mul(ff_norm(a.h, a.l), {cf[d * NV + v], cf[3 * NV + d * NV + v]}));
           }
         }
       }
-      double vol = b0vol[k] + (double)dvol;
+      double vol = b0vol[k] + ff_to_d(dvol);
       if (has_src && v >= 3) {
         double sbar = 0.0;
 #pragma unroll
@@ -438,7 +572,7 @@ __global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
     }
   }
 
-  // ---- face records: FP64-accurate base extrapolation + binary32 increment ----------------
+  // ---- face records: float-float extrapolations of the base and the increment -----------------
   double* fc = A.face + c * (long long)(D * 2 * FR);
   constexpr int NFE = D * 2 * NF * NV;
   for (int e = tid; e < NFE; e += TPB) {
@@ -450,23 +584,23 @@ __global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
     const int jbase = (jp % st) + (jp / st) * st * n;
     const float* eh = side ? F.e1h : F.e0h;
     const float* el = side ? F.e1l : F.e0l;
-    ff qa = {0.f, 0.f}, fa = {0.f, 0.f};
-    float qd = 0.f, fd = 0.f;
+    ff qa = {0.f, 0.f}, fa = {0.f, 0.f}, fd = {0.f, 0.f};
 #pragma unroll
     for (int m = 0; m < n; ++m) {
       const int jj = jbase + m * st;
       const ff uu = uff[jj * NV + v];
       ff_mac(qa, eh[m], el[m], uu.h, uu.l);
-      qd = fmaf(eh[m], dqbs[jj * NV + v], qd);
+      ff_mac(qa, eh[m], el[m], qbh[jj * NV + v], qbl[jj * NV + v]);
       if constexpr (P::CONS) {
         const ff f = FB0[d * NL + jj * NV + v];
         ff_mac(fa, eh[m], el[m], f.h, f.l);
-        fd = fmaf(eh[m], dFbs[d * NL + jj * NV + v], fd);
+        const int i = d * NL + jj * NV + v;
+        ff_mac(fd, eh[m], el[m], fbh[i], fbl[i]);
       }
     }
     double* rec = fc + (d * 2 + side) * FR;
-    rec[jp * NV + v] = ff_to_d(qa) + (double)qd;
-    if constexpr (P::CONS) rec[NF * NV + jp * NV + v] = ff_to_d(fa) * A.g.h[d] + (double)fd;
+    rec[jp * NV + v] = ff_to_d(qa);
+    if constexpr (P::CONS) rec[NF * NV + jp * NV + v] = ff_to_d(fa) * A.g.h[d] + ff_to_d(fd);
   }
 }
 

@@ -50,11 +50,12 @@ __device__ __forceinline__ ff ff_mulf(ff a, float b) {
   e = fmaf(a.l, b, e);
   return ff_norm(p, e);
 }
-// a / b: binary32 quotient, float-float residual, one correction.
+// a / b: approximate binary32 quotient (2 ulp), float-float residual, one correction; the
+// correction step restores float-float accuracy.
 __device__ __forceinline__ ff ff_div(ff a, ff b) {
-  const float q1 = a.h / b.h;
+  const float q1 = __fdividef(a.h, b.h);
   const ff r = ff_sub(a, ff_mulf(b, q1));
-  return ff_norm(q1, r.h / b.h);
+  return ff_norm(q1, __fdividef(r.h, b.h));
 }
 
 // acc += (ah + al) * (bh + bl): exact product of the high parts by FMA, cross terms, two-sum.
@@ -115,7 +116,7 @@ template <int D>
 __device__ __forceinline__ void dflux_f(const EulerBase<D>& b, const float* dq, float g1h, float g1l,
                                         int d, float* F) {
   constexpr int NV = D + 2;
-  const float irq = 1.0f / (b.rho.h + dq[0]);
+  const float irq = __fdividef(1.0f, b.rho.h + dq[0]);
   float dv[D], djv = 0.f;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -132,18 +133,25 @@ __device__ __forceinline__ void dflux_f(const EulerBase<D>& b, const float* dq, 
   F[NV - 1] = fmaf(dq[NV - 1] + dp, vd, (b.E.h + b.p.h) * dv[d]);
 }
 
-// The same increment in float-float.
+// The same increment in float-float: velocity and pressure increments (once per node) ...
 template <int D>
-__device__ __forceinline__ void dflux_ff(const EulerBase<D>& b, const ff* dq, ff g1, int d, ff* F) {
+__device__ __forceinline__ void daux_ff(const EulerBase<D>& b, const ff* dq, ff g1, ff* dv, ff& dp) {
   constexpr int NV = D + 2;
   const ff den = ff_add(b.rho, dq[0]);
-  ff dv[D], djv = {0.f, 0.f};
+  ff djv = {0.f, 0.f};
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     dv[i] = ff_div(ff_sub(dq[1 + i], ff_mul(b.v[i], dq[0])), den);
     djv = ff_add(djv, ff_add(ff_mul(dq[1 + i], ff_add(b.v[i], dv[i])), ff_mul(b.j[i], dv[i])));
   }
-  const ff dp = ff_mul(g1, ff_sub(dq[NV - 1], ff_mulf(djv, 0.5f)));
+  dp = ff_mul(g1, ff_sub(dq[NV - 1], ff_mulf(djv, 0.5f)));
+}
+
+// ... and the flux increment of direction d from them.
+template <int D>
+__device__ __forceinline__ void dflux_ff(const EulerBase<D>& b, const ff* dq, const ff* dv, ff dp,
+                                         int d, ff* F) {
+  constexpr int NV = D + 2;
   const ff vd = ff_add(b.v[d], dv[d]);
   F[0] = dq[1 + d];
 #pragma unroll
@@ -177,13 +185,46 @@ __device__ __forceinline__ void dflux_nodes(const float* dqs, const ff* uff, con
   }
 }
 
-// float-float increments at the owned space-time nodes (epilogue): hi -> dFs, lo -> dFl.
+// float-float increments at the owned space-time nodes (epilogue): hi -> dFs, lo -> dFl; the
+// velocity / pressure increments of the owned nodes come in registers (aux, computed once).
+template <class M>
+struct AuxFF {
+  static constexpr int W = M::EULER ? 2 * (M::NV - 1) : 1;  // (D+1) float-float values
+  float a[M::NPT][W];
+};
+
+template <class M, class P, int D>
+__device__ __forceinline__ void daux_nodes_ff(const float* dqs, const float* dql, const ff* uff,
+                                              const ff* bff, ff g1, AuxFF<M>& ax, int tid) {
+  constexpr int NV = M::NV, NS = M::NS;
+  if constexpr (M::EULER) {
+#pragma unroll
+    for (int k = 0; k < M::NPT; ++k) {
+      const int node = tid + k * M::TPB;
+      if (node < M::NST) {
+        ff q[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) q[v] = {dqs[node * NV + v], dql[node * NV + v]};
+        ff dv[D], dp;
+        daux_ff<D>(load_base<D>(uff, bff, node % NS), q, g1, dv, dp);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          ax.a[k][2 * i] = dv[i].h;
+          ax.a[k][2 * i + 1] = dv[i].l;
+        }
+        ax.a[k][2 * D] = dp.h;
+        ax.a[k][2 * D + 1] = dp.l;
+      }
+    }
+  }
+}
+
 template <class M, int d, class P, int D>
 __device__ __forceinline__ void dflux_nodes_ff(const float* dqs, const float* dql, const ff* uff,
-                                               const ff* bff, const PdeParams& pp, ff g1,
-                                               float* dFs, float* dFl, int tid) {
+                                               const ff* bff, const AuxFF<M>& ax,
+                                               const PdeParams& pp, float* dFs, float* dFl, int tid) {
   constexpr int NV = M::NV, NS = M::NS;
-#pragma unroll 1
+#pragma unroll
   for (int k = 0; k < M::NPT; ++k) {
     const int node = tid + k * M::TPB;
     if (node < M::NST) {
@@ -192,7 +233,10 @@ __device__ __forceinline__ void dflux_nodes_ff(const float* dqs, const float* dq
       for (int v = 0; v < NV; ++v) q[v] = {dqs[node * NV + v], dql[node * NV + v]};
       ff F[NV];
       if constexpr (M::EULER) {
-        dflux_ff<D>(load_base<D>(uff, bff, node % NS), q, g1, d, F);
+        ff dv[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) dv[i] = {ax.a[k][2 * i], ax.a[k][2 * i + 1]};
+        dflux_ff<D>(load_base<D>(uff, bff, node % NS), q, dv, {ax.a[k][2 * D], ax.a[k][2 * D + 1]}, d, F);
       } else {
         const double a = pp.a[d];
         const float ah = (float)a;
@@ -244,7 +288,7 @@ __device__ __forceinline__ void contract_f(const float* X, const TablesF& T, con
 }
 
 template <class P, int D, int N>
-__global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
+__global__ void __launch_bounds__(Cfg<P, D, N>::TPB, (Cfg<P, D, N>::TPB <= 128 ? 3 : 1))
     k_predictor_mixed(const __grid_constant__ StepArgs A, const __grid_constant__ Tables T,
                       const __grid_constant__ TablesF F) {
   using M = CfgM<P, D, N>;
@@ -311,27 +355,49 @@ __global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
       uff[l] = ff_split(ul[k]);
     }
   }
+  __syncthreads();  // uff complete
   if constexpr (P::CONS) {
+    // flux of u^n at the spatial nodes in float-float (scaled by 1/h_d): 1/rho, v, p, F_d
 #pragma unroll
     for (int k = 0; k < M::NPS; ++k) {
       const int j = tid + k * TPB;
       if (j < NS) {
-        double q[NV];
+        ff q[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) q[v] = u[j * NV + v];
-        typename P::Aux ax;
-        P::aux(q, A.p, ax);
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          double Fd[NV];
-          P::flux(q, ax, A.p, d, Fd);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) FB0[d * NL + j * NV + v] = ff_split(Fd[v] * A.g.inv_h[d]);
-        }
+        for (int v = 0; v < NV; ++v) q[v] = uff[j * NV + v];
         if constexpr (M::EULER) {
+          const ff ir = ff_div({1.f, 0.f}, q[0]);
+          ff vel[D], jv = {0.f, 0.f};
 #pragma unroll
-          for (int i = 0; i < D; ++i) bff[j * (D + 1) + i] = ff_split(q[1 + i] * ax.ir);
-          bff[j * (D + 1) + D] = ff_split(ax.p);
+          for (int i = 0; i < D; ++i) {
+            vel[i] = ff_mul(q[1 + i], ir);
+            jv = ff_add(jv, ff_mul(q[1 + i], vel[i]));
+          }
+          const ff pr = ff_mul(g1, ff_sub(q[NV - 1], ff_mulf(jv, 0.5f)));
+#pragma unroll
+          for (int i = 0; i < D; ++i) bff[j * (D + 1) + i] = vel[i];
+          bff[j * (D + 1) + D] = pr;
+          const ff ep = ff_add(q[NV - 1], pr);
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            const ff ih = {F.ihh[d], F.ihl[d]};
+            ff* dst = FB0 + d * NL + j * NV;
+            dst[0] = ff_mul(q[1 + d], ih);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+              ff f = ff_mul(q[1 + i], vel[d]);
+              if (i == d) f = ff_add(f, pr);
+              dst[1 + i] = ff_mul(f, ih);
+            }
+            dst[NV - 1] = ff_mul(ff_mul(ep, vel[d]), ih);
+          }
+        } else {
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            const double ad = A.p.a[d] * A.g.inv_h[d];
+            const float ah = (float)ad;
+            FB0[d * NL + j * NV] = ff_mul(q[0], {ah, (float)(ad - (double)ah)});
+          }
         }
       }
     }
@@ -477,12 +543,14 @@ __global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
   float *fbh, *fbl;   // time-averaged flux increments [D][NL] (hi, lo)
   if constexpr (P::CONS) {
     ff FBv[D][LPT];
+    AuxFF<M> ax;
+    daux_nodes_ff<M, P, D>(dqs, dql, uff, bff, g1, ax, tid);
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      if (d == 0) dflux_nodes_ff<M, 0, P, D>(dqs, dql, uff, bff, A.p, g1, dFs, dFl, tid);
-      if (d == 1) dflux_nodes_ff<M, 1, P, D>(dqs, dql, uff, bff, A.p, g1, dFs, dFl, tid);
+      if (d == 0) dflux_nodes_ff<M, 0, P, D>(dqs, dql, uff, bff, ax, A.p, dFs, dFl, tid);
+      if (d == 1) dflux_nodes_ff<M, 1, P, D>(dqs, dql, uff, bff, ax, A.p, dFs, dFl, tid);
       if constexpr (D == 3)
-        if (d == 2) dflux_nodes_ff<M, 2, P, D>(dqs, dql, uff, bff, A.p, g1, dFs, dFl, tid);
+        if (d == 2) dflux_nodes_ff<M, 2, P, D>(dqs, dql, uff, bff, ax, A.p, dFs, dFl, tid);
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < LPT; ++k) {

@@ -106,6 +106,7 @@ struct StepArgs {
   DevScalars* dev;
   int iters;
   PointSrc src;
+  double cw0[3][MAXN], cw1[3][MAXN];  // e0/(w h_d), e1/(w h_d): corrector face weights
   double dt_fixed;     // > 0: fixed dt
   double t_end;        // > 0: clip
   double cfl;

@@ -737,6 +737,11 @@ static StepArgs make_args(ader_ctx* c, double dt, double t_end) {
   a.dt_fixed = dt > 0 ? dt : 0.0;
   a.t_end = t_end > 0 ? t_end : 0.0;
   a.cfl = c->cfg.cfl;
+  for (int d = 0; d < 3; ++d)
+    for (int m = 0; m < MAXN; ++m) {
+      a.cw0[d][m] = c->tab.c0[m] * c->g.inv_h[d];
+      a.cw1[d][m] = c->tab.c1[m] * c->g.inv_h[d];
+    }
   return a;
 }
 

@@ -447,9 +447,13 @@ __global__ void __launch_bounds__(128) k_riemann(const __grid_constant__ StepArg
       }
       if (!recL) ghost<P>(g.bc[d][0], d, qL[r], FL[r]);
       if (!recR) ghost<P>(g.bc[d][1], d, qR[r], FR_[r]);
-      if constexpr (P::CONS && !P::LINEAR) {
-        smax = fmax(smax, fmax(P::speed(qL[r], A.p, d), P::speed(qR[r], A.p, d)));
-      }
+    }
+  }
+  if constexpr (P::CONS && !P::LINEAR) {
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int jp = lane + 32 * r;
+      if (jp < NF) smax = fmax(smax, fmax(P::speed(qL[r], A.p, d), P::speed(qR[r], A.p, d)));
     }
   }
   double s;
@@ -501,7 +505,7 @@ __global__ void __launch_bounds__(128) k_riemann(const __grid_constant__ StepArg
 }
 
 // Corrector, face part of Eq. (6) in strong form:
-//   u_j -= dt sum_d (1/h_d) [ e1_{j_d}/w_{j_d} Phi_L(right face) - e0_{j_d}/w_{j_d} Phi_R(left face) ]
+//   u_j -= dt sum_d [ (e1_{j_d}/(w_{j_d} h_d)) Phi_L(right face) - (e0_{j_d}/(w_{j_d} h_d)) Phi_R(left face) ]
 template <class P, int D, int N>
 __global__ void __launch_bounds__(256) k_corrector(const __grid_constant__ StepArgs A,
                                                    const __grid_constant__ Tables T,
@@ -510,9 +514,11 @@ __global__ void __launch_bounds__(256) k_corrector(const __grid_constant__ StepA
   constexpr int n = C::n, NV = C::NV, NL = C::NL, NF = C::NF, NPHI = C::NPHI;
   const long long e = (long long)blockIdx.x * 256 + threadIdx.x;
   if (e >= A.g.ncells * NL) return;
-  const long long c = e / NL;
-  const int l = (int)(e - c * NL);
+  const unsigned c = (unsigned)(e / NL);
+  const int l = (int)(e - (long long)c * NL);
   const int j = l / NV, v = l - (l / NV) * NV;
+  const unsigned n0 = A.g.n[0], n1 = A.g.n[1];
+  const unsigned i0 = c % n0, r0 = c / n0, i1 = r0 % n1, i2 = r0 / n1;
   const double dt = A.dev->dt;
   double acc = 0.0;
 #pragma unroll
@@ -520,53 +526,62 @@ __global__ void __launch_bounds__(256) k_corrector(const __grid_constant__ StepA
     const int st = (d == 0 ? 1 : (d == 1 ? n : n * n));
     const int jd = (j / st) % n;
     const int jp = (j % st) + (j / (st * n)) * st;
-    int id;
-    const long long tr = FaceIdx::trans_of_cell(A.g, c, d, id);
-    const int nd = A.g.n[d];
-    int kr = id + 1;
+    const unsigned id = d == 0 ? i0 : (d == 1 ? i1 : i2);
+    const unsigned tr = d == 0 ? i1 + n1 * i2 : (d == 1 ? i0 + n0 * i2 : i0 + n0 * i1);
+    const unsigned nd = A.g.n[d];
+    unsigned kr = id + 1;
     if (kr == nd && A.g.bc[d][1] == BC_PERIODIC) kr = 0;
     const long long off = d == 0 ? 0 : (d == 1 ? off1 : off2);
     const long long fr = kr + (long long)(nd + 1) * tr;
     const long long fl = id + (long long)(nd + 1) * tr;
     const double PhiL = A.phi[off + fr * (NPHI * NF * NV) + jp * NV + v];
     const double PhiR = A.phi[off + fl * (NPHI * NF * NV) + (NPHI - 1) * NF * NV + jp * NV + v];
-    acc += A.g.inv_h[d] * (T.c1[jd] * PhiL - T.c0[jd] * PhiR);
+    acc = fma(A.cw1[d][jd], PhiL, acc);
+    acc = fma(-A.cw0[d][jd], PhiR, acc);
   }
   A.u_next[e] = fma(-dt, acc, A.u_next[e]);
 }
 
-// Max signal speed of the state (Eq. (7)); NaN / Inf latches ST_NONFINITE.
+// Max signal speed of the state (Eq. (7)); NaN / Inf latches ST_NONFINITE.  Euler: one FP64
+// division and one square root per node for all directions.
 template <class P, int D, int N>
 __global__ void __launch_bounds__(256) k_cfl(const __grid_constant__ StepArgs A) {
   using C = Cfg<P, D, N>;
   constexpr int NS = C::NS, NV = C::NV;
   double lmax = 0.0;
   bool bad = false;
-  const long long total = P::NCP ? A.g.ncells : A.g.ncells * NS;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    double s;
-    if constexpr (P::NCP) {
-      s = Elastic::vp(A.mat[i * 3], A.mat[i * 3 + 1], A.mat[i * 3 + 2]);
-      // the state itself only needs a finiteness check
-    } else {
-      const double* q = A.u + i * NV;
-      s = 0.0;
-#pragma unroll
-      for (int d = 0; d < D; ++d) s = fmax(s, P::speed(q, A.p, d));
-      double sum = 0.0;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) sum += q[v];
-      if (!isfinite(sum)) bad = true;
-    }
-    if (!(s >= 0.0) || isinf(s)) bad = true;
-    else lmax = fmax(lmax, s);
-  }
   if constexpr (P::NCP) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.g.ncells;
+         i += (long long)gridDim.x * blockDim.x) {
+      const double s = Elastic::vp(A.mat[i * 3], A.mat[i * 3 + 1], A.mat[i * 3 + 2]);
+      if (!(s >= 0.0) || isinf(s)) bad = true;
+      else lmax = fmax(lmax, s);
+    }
     const long long tot2 = A.g.ncells * NS * NV;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < tot2;
          i += (long long)gridDim.x * blockDim.x)
       if (!isfinite(A.u[i])) bad = true;
+  } else if constexpr (P::LINEAR) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.g.ncells * NS;
+         i += (long long)gridDim.x * blockDim.x) {
+      const double* q = A.u + i * NV;
+      double s = 0.0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) s = fmax(s, P::speed(q, A.p, d));
+      if (!isfinite(q[0])) bad = true;
+      lmax = fmax(lmax, s);
+    }
+  } else {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.g.ncells * NS;
+         i += (long long)gridDim.x * blockDim.x) {
+      const double* q = A.u + i * NV;
+      double sum = 0.0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sum += q[v];
+      const double s = P::speed_all(q, A.p);
+      if (!isfinite(sum) || !(s >= 0.0) || isinf(s)) bad = true;
+      else lmax = fmax(lmax, s);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));

@@ -64,10 +64,27 @@ struct Euler {
   // estimate stays finite; NaN propagates.
   __device__ static double speed(const double* q, const PdeParams& pp, int d) {
     const double ir = 1.0 / q[0];
-    const double p = pressure(q, pp.gamma);
+    double j2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) j2 = fma(q[1 + i], q[1 + i], j2);
+    const double p = (pp.gamma - 1.0) * (q[NV - 1] - 0.5 * j2 * ir);
     double c2 = pp.gamma * p * ir;
     if (c2 < 0.0) c2 = 0.0;
     return fabs(q[1 + d] * ir) + sqrt(c2);
+  }
+  // max over directions of |v_d| + c with one division and one square root (FP64)
+  __device__ static double speed_all(const double* q, const PdeParams& pp) {
+    const double ir = 1.0 / q[0];
+    double j2 = 0.0, vm = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      j2 = fma(q[1 + i], q[1 + i], j2);
+      vm = fmax(vm, fabs(q[1 + i]));
+    }
+    const double p = (pp.gamma - 1.0) * (q[NV - 1] - 0.5 * j2 * ir);
+    double c2 = pp.gamma * p * ir;
+    if (c2 < 0.0) c2 = 0.0;
+    return vm * ir + sqrt(c2);
   }
   __device__ static void mirror(double* q, int d) { q[1 + d] = -q[1 + d]; }
   // F_d of the mirrored state: all components but the normal momentum flux change sign.

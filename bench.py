@@ -35,6 +35,10 @@ WORKLOADS = {
                           hi=(1.0,) * 2, bc="periodic"),
 }
 FP64_SMS, FP64_FMA_PER_CLK, SM_MAX_MHZ = 152, 2, 2070.0
+# DRAM bytes (read + write) per cell of the predictor kernels, from one ncu capture of the same
+# kernels on 40^3 cells (profiles/), scaled to a launch by the number of cells (the traffic is per
+# cell: state in, next state and face records out).
+TRAFFIC_PER_CELL = {}
 FP64_PEAK = FP64_SMS * FP64_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6  # FLOP/s
 
 
@@ -301,50 +305,55 @@ def extra_elastic(ader, synth, stream, steps=2, warmup=1):
 
 def extra_explosion(ader, synth, stream, steps=4, warmup=2):
     """3-D spherical explosion, order 3, 64^3 cells on [-1,1]^3, wall boundaries, a-posteriori
-    subcell limiter (7^3 subcells): FP64 step time, troubled cells, conservation."""
+    subcell limiter (7^3 subcells): FP64 and mixed predictor; step time, troubled cells,
+    conservation of mass and energy."""
     import torch
     N, n = 3, 64
-    cfg = ader.make_config("euler", 3, N, (n,) * 3, (-1,) * 3, (1,) * 3, "wall", synth.cfl_number(N),
-                           limiter=1)
-    ctx = ader.Context(cfg, stream=stream.cuda_stream)
     x, w = ader.reference_nodes(N)
     X = synth.node_coordinates(x, (n,) * 3, (-1,) * 3, (1,) * 3)
     Us = synth.explosion(synth.subcell_centres(2 * N + 1, (n,) * 3, (-1,) * 3, (1,) * 3))
-    fl = synth.discontinuous_cells(Us).astype(np.uint8)
-    ctx.set_state(torch.from_numpy(synth.explosion(X).reshape(-1).copy()).cuda())
-    ctx.set_subcell_state(torch.from_numpy(Us.reshape(-1).copy()).cuda(), torch.from_numpy(fl).cuda())
+    fl = torch.from_numpy(synth.discontinuous_cells(Us).astype(np.uint8)).cuda()
+    Us_d = torch.from_numpy(Us.reshape(-1).copy()).cuda()
+    u0_d = torch.from_numpy(synth.explosion(X).reshape(-1).copy()).cuda()
     W = torch.from_numpy(np.einsum("i,j,k->ijk", w, w, w).reshape(-1)).cuda()
-
-    def totals():
-        st = _dev_state(ctx).view(ctx.cells, -1, 5)
-        return (st * W[None, :, None]).sum(dim=(0, 1))
-
-    m0 = totals()
-    for _ in range(warmup):
-        ctx.step()
-    ctx.sync()
-    ctx.enable_timing(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        ctx.step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    ph, nr = ctx.phase_times()
-    ctx.enable_timing(False)
-    ctx.sync()
-    m1 = totals()
     dofs = n ** 3 * 64 * 5
-    out = {"workload": "explosion3d_p3_64 (limiter on)", "ms_per_step": ms / steps,
-           "value": dofs * steps / (ms * 1e-3), "unit": "DOF-updates/s", "dtype": "f64",
-           "troubled_cells_last_step": ctx.troubled_count(),
-           "troubled_fraction": ctx.troubled_count() / n ** 3,
-           "phase_ms_per_step": {k: v / max(nr, 1) for k, v in ph.items()},
-           "mass_rel_drift": abs(float(m1[0] - m0[0])) / abs(float(m0[0])),
-           "energy_rel_drift": abs(float(m1[4] - m0[4])) / abs(float(m0[4])),
-           "steps_run": steps + warmup}
-    ctx.close()
+    out = {"workload": "explosion3d_p3_64 (limiter on)", "dofs": dofs}
+    for prec in ("fp64", "mixed"):
+        cfg = ader.make_config("euler", 3, N, (n,) * 3, (-1,) * 3, (1,) * 3, "wall", synth.cfl_number(N),
+                               limiter=1, precision=prec)
+        ctx = ader.Context(cfg, stream=stream.cuda_stream)
+        ctx.set_state(u0_d)
+        ctx.set_subcell_state(Us_d, fl)
+
+        def totals():
+            st = _dev_state(ctx).view(ctx.cells, -1, 5)
+            return (st * W[None, :, None]).sum(dim=(0, 1))
+
+        m0 = totals()
+        for _ in range(warmup):
+            ctx.step()
+        ctx.sync()
+        ctx.enable_timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ph, nr = ctx.phase_times()
+        ctx.enable_timing(False)
+        ctx.sync()
+        m1 = totals()
+        out[prec] = {"ms_per_step": ms / steps, "value": dofs * steps / (ms * 1e-3),
+                     "troubled_cells_last_step": ctx.troubled_count(),
+                     "troubled_fraction": ctx.troubled_count() / n ** 3,
+                     "phase_ms_per_step": {k: v / max(nr, 1) for k, v in ph.items()},
+                     "mass_rel_drift": abs(float(m1[0] - m0[0])) / abs(float(m0[0])),
+                     "energy_rel_drift": abs(float(m1[4] - m0[4])) / abs(float(m0[4])),
+                     "steps_run": steps + warmup}
+        ctx.close()
+    out["mixed_speedup"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
     return out
 
 
@@ -501,21 +510,28 @@ def main():
                "h2d_bytes_per_step": dofs * 8, "d2h_bytes_per_step": dofs * 8}
     head_ctx.close()
 
-    # ---- roofline of the dominant kernel (the predictor) -------------------------------------
-    nrec = max(head["nrec"], 1)
-    pred_ms = head["phases"]["predictor"] / nrec
+    # ---- roofline of the dominant kernel (the predictor) of each form --------------------------
     flops = predictor_flops_per_cell(wl["pde"], D, N, N + 1) * cells
-    achieved = flops / (pred_ms * 1e-3) / 1e12
-    if args.prec == "fp64":
-        peak, src, kname = FP64_PEAK, "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz", \
-            "k_predictor (FP64)"
-    else:
-        peak, src, kname = FP32_PEAK, "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz", \
-            "k_predictor_mixed (binary32 increments, float-float base)"
-    roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak / 1e12,
-            "unit": "TFLOP/s", "frac": achieved / (peak / 1e12), "traffic": None,
-            "peak_source": src, "flops_per_cell": flops / cells, "ms_per_launch": pred_ms,
-            "phase_ms_per_step": {k: v / nrec for k, v in head["phases"].items()}}
+
+    def roofline(prec):
+        r = res[prec]
+        nrec = max(r["nrec"], 1)
+        pred_ms = r["phases"]["predictor"] / nrec
+        achieved = flops / (pred_ms * 1e-3) / 1e12
+        if prec == "fp64":
+            peak, src, kname = FP64_PEAK, "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz", \
+                "k_predictor (FP64)"
+        else:
+            peak, src, kname = FP32_PEAK, "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz", \
+                "k_predictor_mixed (binary32 iterations, float-float base and final stage)"
+        return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / (peak / 1e12),
+                "traffic": TRAFFIC_PER_CELL.get(prec, 0) * cells if TRAFFIC_PER_CELL.get(prec) else None,
+                "peak_source": src, "flops_per_cell": flops / cells, "ms_per_launch": pred_ms,
+                "phase_ms_per_step": {k: v / nrec for k, v in r["phases"].items()}}
+
+    roof = roofline(args.prec)
+    roof_forms = {k: roofline(k) for k in res}
     forms_out = {}
     for k, r in res.items():
         forms_out[k] = {"value": r["value"], "ms_per_step": r["ms_per_step"],
@@ -528,7 +544,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.prec == "fp64" else "f32+f64",
-            "data": "synthetic", "config": config, "roofline": roof, "forms": forms_out,
+            "data": "synthetic", "config": config, "roofline": roof, "roofline_forms": roof_forms,
+            "forms": forms_out,
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": head["clocks"]}
     if not args.no_extra and world == 1:
         extra = {}

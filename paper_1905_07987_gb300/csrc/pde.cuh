@@ -84,7 +84,7 @@ struct Euler {
     const double p = (pp.gamma - 1.0) * (q[NV - 1] - 0.5 * j2 * ir);
     double c2 = pp.gamma * p * ir;
     if (c2 < 0.0) c2 = 0.0;
-    return vm * ir + sqrt(c2);
+    return vm * fabs(ir) + sqrt(c2);  // |v_d| = |j_d| / |rho|, as for a non-admissible rho < 0
   }
   __device__ static void mirror(double* q, int d) { q[1 + d] = -q[1 + d]; }
   // F_d of the mirrored state: all components but the normal momentum flux change sign.

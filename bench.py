@@ -38,7 +38,8 @@ FP64_SMS, FP64_FMA_PER_CLK, SM_MAX_MHZ = 152, 2, 2070.0
 # DRAM bytes (read + write) per cell of the predictor kernels, from one ncu capture of the same
 # kernels on 40^3 cells (profiles/), scaled to a launch by the number of cells (the traffic is per
 # cell: state in, next state and face records out).
-TRAFFIC_PER_CELL = {}
+TRAFFIC_PER_CELL = {"fp64": 325.915392e6 / 64000 + 1029.375e6 / 64000,
+                    "mixed": 322.237696e6 / 64000 + 1029.472e6 / 64000}
 FP64_PEAK = FP64_SMS * FP64_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6  # FLOP/s
 
 

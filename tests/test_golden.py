@@ -24,7 +24,7 @@ def test_workload_cfl_factors_are_below_the_stability_limits():
     for N, nu in lim.items():
         courant = synth.cfl_number(N) / (2 * N + 1)   # Eq. (7) with d = 1
         assert courant <= 0.9 * nu * 1.0001, (N, courant, nu)
-        assert synth.KAPPA[N] <= (2 * N + 1) * nu
+        assert synth.KAPPA[N] <= (2 * N + 1) * nu + 1e-5  # file holds 6 decimals
 
 
 def test_literal_eq7_exceeds_the_limits_for_N_at_least_2():

@@ -14,6 +14,7 @@
 // The t^n representation rep (subcell averages of every cell) and its per-variable min/max are
 // double-buffered across steps.
 #pragma once
+#include <climits>
 #include "kernels.cuh"
 
 namespace ader {
@@ -41,9 +42,31 @@ struct CfgL {
   static constexpr int T1 = ipow(ns, D - 1) * n * NV;
   static constexpr int T2 = D == 3 ? n * ns * ns * NV : 0;
   static constexpr size_t SMEM_P = (size_t)(NN * NV + T1 + T2 + NSS * NV) * sizeof(double);
-  static constexpr size_t SMEM_FV =
-      (size_t)(NH * NV + NC * NV + NSS * NV + T1 + T2 + NN * NV) * sizeof(double);
+  static constexpr size_t SMEM_FV = (size_t)(NH * NV + NC * NV + (ns + 1) * NSF * NV) * sizeof(double);
 };
+
+// One axis of a sum-factorised tensor-product map: Y[o][q][i] = sum_p M[q][p] X[o][p][i] with
+// M = P1 (PROJ) or R1.  One thread per (o, i) column holds the LIN inputs in registers; the
+// loops over q and p are unrolled, so every matrix entry is a compile-time kernel-parameter
+// operand shared by the warp.  Summation order over p is ascending.
+template <int LIN, int LOUT, int OUTER, int INNER, bool PROJ>
+__device__ __forceinline__ void contract_axis(const double* X, double* Y, const SubTables& S) {
+  for (int it = threadIdx.x; it < OUTER * INNER; it += blockDim.x) {
+    const int o = it / INNER, i = it - o * INNER;
+    const double* x = X + o * (LIN * INNER) + i;
+    double xv[LIN];
+#pragma unroll
+    for (int p = 0; p < LIN; ++p) xv[p] = x[p * INNER];
+    double* y = Y + o * (LOUT * INNER) + i;
+#pragma unroll
+    for (int q = 0; q < LOUT; ++q) {
+      double acc = 0.0;
+#pragma unroll
+      for (int p = 0; p < LIN; ++p) acc = fma(PROJ ? S.P1[q][p] : S.R1[q][p], xv[p], acc);
+      y[q * INNER] = acc;
+    }
+  }
+}
 
 // sub[s][v] = sum over nodes of prod_e P1[s_e][a_e] u[a][v] (sum factorisation, x first).
 // u: [NN][NV], out: [NSS][NV]; t1, t2 scratch.  All threads of the block participate.
@@ -53,46 +76,15 @@ __device__ void project_P(const double* u, double* t1, double* t2, double* out,
   using L = CfgL<D, N>;
   constexpr int n = L::n, ns = L::ns, NV = L::NV;
   if constexpr (D == 2) {
-    // t1[b][sx][v] = sum_a P1[sx][a] u[b][a][v]
-    for (int e = threadIdx.x; e < n * ns * NV; e += blockDim.x) {
-      const int v = e % NV, sx = (e / NV) % ns, b = e / (NV * ns);
-      double acc = 0.0;
-#pragma unroll
-      for (int a = 0; a < n; ++a) acc = fma(S.P1[sx][a], u[(b * n + a) * NV + v], acc);
-      t1[e] = acc;
-    }
+    contract_axis<n, ns, n, NV, true>(u, t1, S);        // t1[b][sx][v]
     __syncthreads();
-    for (int e = threadIdx.x; e < ns * ns * NV; e += blockDim.x) {
-      const int v = e % NV, sx = (e / NV) % ns, sy = e / (NV * ns);
-      double acc = 0.0;
-#pragma unroll
-      for (int b = 0; b < n; ++b) acc = fma(S.P1[sy][b], t1[(b * ns + sx) * NV + v], acc);
-      out[e] = acc;
-    }
+    contract_axis<n, ns, 1, ns * NV, true>(t1, out, S);  // out[sy][sx][v]
   } else {
-    for (int e = threadIdx.x; e < n * n * ns * NV; e += blockDim.x) {
-      const int v = e % NV, sx = (e / NV) % ns, zb = e / (NV * ns);  // zb = z*n + b(y)
-      double acc = 0.0;
-#pragma unroll
-      for (int a = 0; a < n; ++a) acc = fma(S.P1[sx][a], u[(zb * n + a) * NV + v], acc);
-      t1[e] = acc;
-    }
+    contract_axis<n, ns, n * n, NV, true>(u, t1, S);          // t1[z][b][sx][v]
     __syncthreads();
-    for (int e = threadIdx.x; e < n * ns * ns * NV; e += blockDim.x) {
-      const int v = e % NV, sx = (e / NV) % ns, sy = (e / (NV * ns)) % ns, z = e / (NV * ns * ns);
-      double acc = 0.0;
-#pragma unroll
-      for (int b = 0; b < n; ++b) acc = fma(S.P1[sy][b], t1[((z * n + b) * ns + sx) * NV + v], acc);
-      t2[e] = acc;
-    }
+    contract_axis<n, ns, n, ns * NV, true>(t1, t2, S);        // t2[z][sy][sx][v]
     __syncthreads();
-    for (int e = threadIdx.x; e < ns * ns * ns * NV; e += blockDim.x) {
-      const int v = e % NV, syx = (e / NV) % (ns * ns), sz = e / (NV * ns * ns);
-      double acc = 0.0;
-#pragma unroll
-      for (int c = 0; c < n; ++c) acc = fma(S.P1[sz][c], t2[(c * ns * ns + syx) * NV + v], acc);
-      out[e] = acc;
-    }
+    contract_axis<n, ns, 1, ns * ns * NV, true>(t2, out, S);  // out[sz][sy][sx][v]
   }
   __syncthreads();
 }
@@ -104,73 +96,60 @@ __device__ void reconstruct_R(const double* U, double* t1, double* t2, double* o
   using L = CfgL<D, N>;
   constexpr int n = L::n, ns = L::ns, NV = L::NV;
   if constexpr (D == 2) {
-    for (int e = threadIdx.x; e < ns * n * NV; e += blockDim.x) {  // t1[sy][a][v]
-      const int v = e % NV, a = (e / NV) % n, sy = e / (NV * n);
-      double acc = 0.0;
-#pragma unroll
-      for (int s = 0; s < ns; ++s) acc = fma(S.R1[a][s], U[(sy * ns + s) * NV + v], acc);
-      t1[e] = acc;
-    }
+    contract_axis<ns, n, ns, NV, false>(U, t1, S);       // t1[sy][a][v]
     __syncthreads();
-    for (int e = threadIdx.x; e < n * n * NV; e += blockDim.x) {
-      const int v = e % NV, a = (e / NV) % n, b = e / (NV * n);
-      double acc = 0.0;
-#pragma unroll
-      for (int s = 0; s < ns; ++s) acc = fma(S.R1[b][s], t1[(s * n + a) * NV + v], acc);
-      out[e] = acc;
-    }
+    contract_axis<ns, n, 1, n * NV, false>(t1, out, S);  // out[b][a][v]
   } else {
-    for (int e = threadIdx.x; e < ns * ns * n * NV; e += blockDim.x) {  // t1[sz][sy][a]
-      const int v = e % NV, a = (e / NV) % n, zy = e / (NV * n);
-      double acc = 0.0;
-#pragma unroll
-      for (int s = 0; s < ns; ++s) acc = fma(S.R1[a][s], U[(zy * ns + s) * NV + v], acc);
-      t1[e] = acc;
-    }
+    contract_axis<ns, n, ns * ns, NV, false>(U, t1, S);      // t1[sz][sy][a][v]
     __syncthreads();
-    for (int e = threadIdx.x; e < ns * n * n * NV; e += blockDim.x) {  // t2[sz][b][a]
-      const int v = e % NV, a = (e / NV) % n, b = (e / (NV * n)) % n, sz = e / (NV * n * n);
-      double acc = 0.0;
-#pragma unroll
-      for (int s = 0; s < ns; ++s) acc = fma(S.R1[b][s], t1[((sz * ns + s) * n + a) * NV + v], acc);
-      t2[e] = acc;
-    }
+    contract_axis<ns, n, ns, n * NV, false>(t1, t2, S);      // t2[sz][b][a][v]
     __syncthreads();
-    for (int e = threadIdx.x; e < n * n * n * NV; e += blockDim.x) {
-      const int v = e % NV, ba = (e / NV) % (n * n), c = e / (NV * n * n);
-      double acc = 0.0;
-#pragma unroll
-      for (int s = 0; s < ns; ++s) acc = fma(S.R1[c][s], t2[(s * n * n + ba) * NV + v], acc);
-      out[e] = acc;
-    }
+    contract_axis<ns, n, 1, n * n * NV, false>(t2, out, S);  // out[c][b][a][v]
   }
   __syncthreads();
 }
 
+// Order-preserving map of a double to a 64-bit integer (both zeros to 0, negative values to
+// minus their magnitude bits); it is its own inverse.  For values that are not NaN,
+// x <= y exactly when okey(x) <= okey(y), so the bound tests and the min / max of the
+// limiter run on the integer pipes instead of the FP64 pipe.
+__device__ __forceinline__ long long okey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : (long long)(0x8000000000000000ull - (unsigned long long)b);
+}
+__device__ __forceinline__ double okey_inv(long long k) {
+  return __longlong_as_double(k >= 0 ? k : (long long)(0x8000000000000000ull - (unsigned long long)k));
+}
+
+// rho > 0 and p > 0 with every value finite.  For rho > 0 and gamma > 1, p > 0 is
+// E rho - |j|^2 / 2 > 0 (no division); finiteness and the sign of rho are read from the bits.
 template <int D>
-__device__ __forceinline__ bool admissible(const double* q, double gamma) {
+__device__ __forceinline__ bool admissible(const double* q) {
   bool fin = true;
 #pragma unroll
-  for (int v = 0; v < D + 2; ++v) fin = fin && isfinite(q[v]);
-  const double p = Euler<D>::pressure(q, gamma);
-  return fin && (q[0] > 0.0) && (p > 0.0);
+  for (int v = 0; v < D + 2; ++v) fin = fin && ((__double2hiint(q[v]) & 0x7ff00000) != 0x7ff00000);
+  double j2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) j2 = fma(q[1 + i], q[1 + i], j2);
+  return fin && (__double_as_longlong(q[0]) > 0) && (fma(q[D + 1], q[0], -0.5 * j2) > 0.0);
 }
 
 // Per-variable min / max of sub[NSS][NV] into mm[2][NV]; red: smem scratch [2][NV][32].
+// Finite inputs give the same values as fmin / fmax (a zero comes out as +0).
 template <int NSS, int NV>
-__device__ void block_minmax(const double* sub, double* mm, double* red) {
+__device__ void block_minmax(const double* sub, double* mm, long long* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int v = 0; v < NV; ++v) {
-    double lo = INFINITY, hi = -INFINITY;
+    long long lo = LLONG_MAX, hi = LLONG_MIN;
     for (int s = threadIdx.x; s < NSS; s += blockDim.x) {
-      const double x = sub[s * NV + v];
-      lo = fmin(lo, x);
-      hi = fmax(hi, x);
+      const long long k = okey(sub[s * NV + v]);
+      lo = min(lo, k);
+      hi = max(hi, k);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
     if (lane == 0) {
       red[(0 * NV + v) * 32 + warp] = lo;
@@ -180,9 +159,9 @@ __device__ void block_minmax(const double* sub, double* mm, double* red) {
   __syncthreads();
   if (threadIdx.x < 2 * NV) {
     const int k = threadIdx.x;
-    double r = red[k * 32];
-    for (int w = 1; w < nw; ++w) r = (k < NV) ? fmin(r, red[k * 32 + w]) : fmax(r, red[k * 32 + w]);
-    mm[k] = r;
+    long long r = red[k * 32];
+    for (int w = 1; w < nw; ++w) r = (k < NV) ? min(r, red[k * 32 + w]) : max(r, red[k * 32 + w]);
+    mm[k] = okey_inv(r);
   }
   __syncthreads();
 }
@@ -214,8 +193,8 @@ __global__ void __launch_bounds__(128) k_lim_detect(const __grid_constant__ Step
   double* t1 = us + NN * NV;
   double* t2 = t1 + C::T1;
   double* sub = t2 + C::T2;
-  __shared__ double red[2 * NV * 32];
-  __shared__ double bnd[2][NV];
+  __shared__ long long red[2 * NV * 32];
+  __shared__ long long bk[2][NV];
   const long long c = blockIdx.x;
   const double* u = A.u_next + c * (NN * NV);
   for (int e = threadIdx.x; e < NN * NV; e += blockDim.x) us[e] = u[e];
@@ -230,24 +209,25 @@ __global__ void __launch_bounds__(128) k_lim_detect(const __grid_constant__ Step
           hi = fmax(hi, L.mm[nb * 2 * NV + NV + v]);
         }
       }
-    bnd[0][v] = lo;
-    bnd[1][v] = hi;
+    // DMP band [lo - delta, hi + delta] as ordered keys (a NaN bound admits nothing)
+    const double delta = fmax(L.eps * (hi - lo), L.delta0);
+    const double bl = lo - delta, bh = hi + delta;
+    bk[0][v] = bl == bl ? okey(bl) : LLONG_MAX;
+    bk[1][v] = bh == bh ? okey(bh) : LLONG_MIN;
   }
   __syncthreads();
   project_P<D, N>(us, t1, t2, sub, S);
   bool ok = true;
   for (int s = threadIdx.x; s < NSS; s += blockDim.x) {
     const double* q = sub + s * NV;
-    ok = ok && admissible<D>(q, A.p.gamma);
+    ok = ok && admissible<D>(q);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const double lo = bnd[0][v], hi = bnd[1][v];
-      const double delta = fmax(L.eps * (hi - lo), L.delta0);
-      const double x = q[v];
-      ok = ok && (x >= lo - delta) && (x <= hi + delta);
+      const long long k = okey(q[v]);
+      ok = ok && (k >= bk[0][v]) && (k <= bk[1][v]);
     }
   }
-  for (int j = threadIdx.x; j < NN; j += blockDim.x) ok = ok && admissible<D>(us + j * NV, A.p.gamma);
+  for (int j = threadIdx.x; j < NN; j += blockDim.x) ok = ok && admissible<D>(us + j * NV);
   const bool all_ok = __syncthreads_and(ok) != 0;
   const bool troubled = L.force ? true : !all_ok;
   double* rn = L.rep_new + c * (NSS * NV);
@@ -264,26 +244,22 @@ __global__ void __launch_bounds__(128) k_lim_detect(const __grid_constant__ Step
 
 // Halo value of subcell (hx, hy, hz) in [-2, ns+2)^D of cell c from the t^n representations,
 // with the boundary conditions applied on the global subcell grid.
+// idx: the cell's grid coordinates.
 template <int D, int N>
-__device__ __forceinline__ void halo_value(const Geometry& g, const double* rep, long long c,
+__device__ __forceinline__ void halo_value(const Geometry& g, const double* rep, const int* idx,
                                            const int* h, double* out) {
   using C = CfgL<D, N>;
   constexpr int ns = C::ns, NV = C::NV, NSS = C::NSS;
-  long long idx[3], rem = c;
-  for (int e = 0; e < 3; ++e) {
-    idx[e] = rem % g.n[e];
-    rem /= g.n[e];
-  }
   bool flip[3] = {false, false, false};
-  long long owner[3];
+  int owner[3];
   int sidx[3] = {0, 0, 0};
   for (int d = 0; d < 3; ++d) {
     if (d >= D) {
       owner[d] = 0;
       continue;
     }
-    const long long Nd = (long long)g.n[d] * ns;
-    long long gs = idx[d] * ns + h[d];
+    const int Nd = g.n[d] * ns;
+    int gs = idx[d] * ns + h[d];
     if (gs < 0) {
       if (g.bc[d][0] == BC_PERIODIC) gs += Nd;
       else {
@@ -298,7 +274,7 @@ __device__ __forceinline__ void halo_value(const Geometry& g, const double* rep,
       }
     }
     owner[d] = gs / ns;
-    sidx[d] = (int)(gs % ns);
+    sidx[d] = gs - owner[d] * ns;
   }
   const long long oc = owner[0] + (long long)g.n[0] * (owner[1] + (long long)g.n[1] * owner[2]);
   const int s = D == 3 ? sidx[0] + ns * (sidx[1] + ns * sidx[2]) : sidx[0] + ns * sidx[1];
@@ -314,26 +290,40 @@ __device__ __forceinline__ double minmod(double a, double b) {
   return (a * b > 0.0) ? copysign(fmin(fabs(a), fabs(b)), a) : 0.0;
 }
 
+constexpr int FV_TPB = 256;
+
 template <int D, int N>
-__global__ void __launch_bounds__(256) k_lim_fv(const __grid_constant__ StepArgs A,
+__global__ void __launch_bounds__(FV_TPB) k_lim_fv(const __grid_constant__ StepArgs A,
                                                 const __grid_constant__ LimArgs L,
                                                 const __grid_constant__ SubTables S) {
   using C = CfgL<D, N>;
   using P = Euler<D>;
   constexpr int ns = C::ns, NV = C::NV, NSS = C::NSS, NSF = C::NSF, NN = C::NN;
   constexpr int W = ns + 4, WC = ns + 2;
+  constexpr int NFC = (ns + 1) * NSF;   // subfaces of one direction
   extern __shared__ double sm[];
   double* H = sm;                  // halo [W^D][NV]
   double* INC = H + C::NH * NV;    // half-step increments of the core [WC^D][NV]
-  double* UN = INC + C::NC * NV;   // new subcell averages [NSS][NV]
-  double* t1 = UN + NSS * NV;
+  double* FLX = INC + C::NC * NV;  // subface fluxes of one direction [NFC][NV]
+  // after the flux stage: new averages over INC, reconstruction scratch over the halo
+  double* UN = INC;
+  double* t1 = H;
   double* t2 = t1 + C::T1;
   double* un = t2 + C::T2;         // reconstructed nodal values [NN][NV]
-  __shared__ double red[2 * NV * 32];
+  static_assert(C::NC >= NSS && C::NH * NV >= C::T1 + C::T2 + NN * NV, "aliasing");
+  __shared__ long long red[2 * NV * 32];
   const double dt = A.dev->dt;
   const int count = A.dev->n_troubled;
   for (int it = blockIdx.x; it < count; it += gridDim.x) {
     const long long c = L.list[it];
+    int cidx[3];
+    {
+      long long rem = c;
+      for (int e = 0; e < 3; ++e) {
+        cidx[e] = (int)(rem % A.g.n[e]);
+        rem /= A.g.n[e];
+      }
+    }
     // halo
     for (int e = threadIdx.x; e < C::NH; e += blockDim.x) {
       int h[3] = {0, 0, 0};
@@ -342,7 +332,7 @@ __global__ void __launch_bounds__(256) k_lim_fv(const __grid_constant__ StepArgs
         h[d] = r % W - 2;
         r /= W;
       }
-      halo_value<D, N>(A.g, L.rep, c, h, H + e * NV);
+      halo_value<D, N>(A.g, L.rep, cidx, h, H + e * NV);
     }
     __syncthreads();
     // half-step increments on the core [-1, ns] (order of directions as in the oracle)
@@ -387,74 +377,111 @@ __global__ void __launch_bounds__(256) k_lim_fv(const __grid_constant__ StepArgs
       for (int v = 0; v < NV; ++v) INC[e * NV + v] = inc[v];
     }
     __syncthreads();
-    // fluxes and update of the interior subcells
-    for (int e = threadIdx.x; e < NSS; e += blockDim.x) {
-      int s[3] = {0, 0, 0};
-      int r = e;
-      for (int d = 0; d < D; ++d) {
-        s[d] = r % ns;
-        r /= ns;
-      }
-      int hi = 0, ci = 0, st = 1, stc = 1;
-      for (int d = 0; d < D; ++d) {
-        hi += (s[d] + 2) * st;
-        ci += (s[d] + 1) * stc;
-        st *= W;
-        stc *= WC;
-      }
-      double Unew[NV];
+    // fluxes, one per subface, direction by direction (into FLX), then the
+    // update of the owned interior subcells in registers (direction order as in the oracle)
+    constexpr int KPT = (NSS + FV_TPB - 1) / FV_TPB;
+    double Unew[KPT][NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Unew[v] = H[hi * NV + v];
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        const int sd = d == 0 ? 1 : (d == 1 ? W : W * W);
-        const int sdc = d == 0 ? 1 : (d == 1 ? WC : WC * WC);
-        double fl[2][NV];  // flux at the left (k=0) and right (k=1) face of this subcell
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int hL = hi + (k - 1) * sd, hR = hi + k * sd;       // halo index of L and R cells
-          const int cL = ci + (k - 1) * sdc, cR = ci + k * sdc;     // core index of L and R
-          double QL[NV], QR[NV];
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            const double* UL = H + hL * NV;
-            const double* UR = H + hR * NV;
-            const double sL = minmod(UL[v] - UL[v - sd * NV], UL[v + sd * NV] - UL[v]);
-            const double sR = minmod(UR[v] - UR[v - sd * NV], UR[v + sd * NV] - UR[v]);
-            QL[v] = (UL[v] + 0.5 * sL) + INC[cL * NV + v];
-            QR[v] = (UR[v] - 0.5 * sR) + INC[cR * NV + v];
-          }
-          typename P::Aux aL, aR;
-          P::aux(QL, A.p, aL);
-          P::aux(QR, A.p, aR);
-          double FL[NV], FR[NV];
-          P::flux(QL, aL, A.p, d, FL);
-          P::flux(QR, aR, A.p, d, FR);
-          const double sp = fmax(P::speed(QL, A.p, d), P::speed(QR, A.p, d));
-#pragma unroll
-          for (int v = 0; v < NV; ++v) fl[k][v] = 0.5 * (FL[v] + FR[v]) - 0.5 * sp * (QR[v] - QL[v]);
+    for (int k = 0; k < KPT; ++k) {
+      const int e = threadIdx.x + k * FV_TPB;
+      if (e < NSS) {
+        int hi = 0, st = 1, r = e;
+        for (int d = 0; d < D; ++d) {
+          hi += (r % ns + 2) * st;
+          r /= ns;
+          st *= W;
         }
-        const double dx = A.g.h[d] / ns;
-        const double cf = dt / dx;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) Unew[v] = Unew[v] + cf * (fl[0][v] - fl[1][v]);
-        // boundary subface fluxes: transverse index of the face = s with digit d removed
-        int tr = 0, stt = 1;
-        for (int e2 = 0; e2 < D; ++e2)
-          if (e2 != d) {
-            tr += s[e2] * stt;
-            stt *= ns;
-          }
-        double* bf = L.bflux + ((c * D + d) * 2) * (long long)(NSF * NV);
-        if (s[d] == 0)
-          for (int v = 0; v < NV; ++v) bf[tr * NV + v] = fl[0][v];
-        if (s[d] == ns - 1)
-          for (int v = 0; v < NV; ++v) bf[NSF * NV + tr * NV + v] = fl[1][v];
+        for (int v = 0; v < NV; ++v) Unew[k][v] = H[hi * NV + v];
       }
-      bool ok = admissible<D>(Unew, A.p.gamma);
-      if (!ok) atomicOr(&A.dev->status, ST_ADMISSIBLE);
+    }
 #pragma unroll
-      for (int v = 0; v < NV; ++v) UN[e * NV + v] = Unew[v];
+    for (int d = 0; d < D; ++d) {
+      const int sd = d == 0 ? 1 : (d == 1 ? W : W * W);
+      const int sdc = d == 0 ? 1 : (d == 1 ? WC : WC * WC);
+      for (int f = threadIdx.x; f < NFC; f += FV_TPB) {
+        const int i = f % (ns + 1);       // subface i lies between subcells i-1 and i along d
+        int t = f / (ns + 1);             // transverse subcell index (lower direction fastest)
+        int hL = 0, cL = 0, stw = 1, stc = 1;
+        for (int e2 = 0; e2 < D; ++e2) {
+          int se;
+          if (e2 == d) {
+            se = i - 1;
+          } else {
+            se = t % ns;
+            t /= ns;
+          }
+          hL += (se + 2) * stw;
+          cL += (se + 1) * stc;
+          stw *= W;
+          stc *= WC;
+        }
+        const int hR = hL + sd, cR = cL + sdc;
+        double QL[NV], QR[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const double* UL = H + hL * NV;
+          const double* UR = H + hR * NV;
+          const double sL = minmod(UL[v] - UL[v - sd * NV], UL[v + sd * NV] - UL[v]);
+          const double sR = minmod(UR[v] - UR[v - sd * NV], UR[v + sd * NV] - UR[v]);
+          QL[v] = (UL[v] + 0.5 * sL) + INC[cL * NV + v];
+          QR[v] = (UR[v] - 0.5 * sR) + INC[cR * NV + v];
+        }
+        typename P::Aux aL, aR;
+        P::aux(QL, A.p, aL);
+        P::aux(QR, A.p, aR);
+        double FL[NV], FR[NV];
+        P::flux(QL, aL, A.p, d, FL);
+        P::flux(QR, aR, A.p, d, FR);
+        const double sp = fmax(P::speed_aux(QL, aL, A.p, d), P::speed_aux(QR, aR, A.p, d));
+        double fx[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          fx[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * sp * (QR[v] - QL[v]);
+          FLX[f * NV + v] = fx[v];
+        }
+        const int tr = f / (ns + 1);
+        double* bf = L.bflux + ((c * D + d) * 2) * (long long)(NSF * NV);
+        if (i == 0)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) bf[tr * NV + v] = fx[v];
+        if (i == ns)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) bf[NSF * NV + tr * NV + v] = fx[v];
+      }
+      __syncthreads();
+      const double cf = dt / (A.g.h[d] / ns);
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) {
+        const int e = threadIdx.x + k * FV_TPB;
+        if (e < NSS) {
+          // subcell e: digit d gives i; transverse index from the other digits
+          int r = e, sdg = 0, tr = 0, stt = 1;
+          for (int e2 = 0; e2 < D; ++e2) {
+            const int dg = r % ns;
+            r /= ns;
+            if (e2 == d) sdg = dg;
+            else {
+              tr += dg * stt;
+              stt *= ns;
+            }
+          }
+          const double* fl = FLX + (sdg + (ns + 1) * tr) * NV;
+          const double* fr = fl + NV;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) Unew[k][v] = Unew[k][v] + cf * (fl[v] - fr[v]);
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int e = threadIdx.x + k * FV_TPB;
+      if (e < NSS) {
+        if (!admissible<D>(Unew[k])) atomicOr(&A.dev->status, ST_ADMISSIBLE);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) UN[e * NV + v] = Unew[k][v];
+      }
     }
     __syncthreads();
     double* rn = L.rep_new + c * (NSS * NV);
@@ -494,7 +521,7 @@ __global__ void __launch_bounds__(128) k_lim_fix(const __grid_constant__ StepArg
   double* t2 = t1 + C::T1;
   double* sub = t2 + C::T2;
   double* geff = sub + NSS * NV;  // [NF][NV]
-  __shared__ double red[2 * NV * 32];
+  __shared__ long long red[2 * NV * 32];
   double* u = A.u_next + c * (NN * NV);
   for (int e = threadIdx.x; e < NN * NV; e += blockDim.x) us[e] = u[e];
   __syncthreads();
@@ -565,7 +592,7 @@ __global__ void __launch_bounds__(128) k_lim_init(double* u, const double* Usub,
   double* t1 = us + NN * NV;
   double* t2 = t1 + C::T1;
   double* sub = t2 + C::T2;
-  __shared__ double red[2 * NV * 32];
+  __shared__ long long red[2 * NV * 32];
   const long long c = blockIdx.x;
   double* uc = u + c * (NN * NV);
   const bool fl = flags && flags[c];
@@ -621,7 +648,7 @@ struct LimLaunch {
     k_lim_detect<D, N><<<nc, C::TPB, C::SMEM_P, s>>>(a, l, S);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_lim_fv<D, N><<<152 * 2, 256, C::SMEM_FV, s>>>(a, l, S);
+    k_lim_fv<D, N><<<152 * 2, FV_TPB, C::SMEM_FV, s>>>(a, l, S);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     long long offs[3] = {0, 0, 0}, off = 0;

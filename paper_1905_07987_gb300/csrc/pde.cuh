@@ -72,6 +72,12 @@ struct Euler {
     if (c2 < 0.0) c2 = 0.0;
     return fabs(q[1 + d] * ir) + sqrt(c2);
   }
+  // |v_d| + c from the aux values (1/rho, p) already computed for the flux
+  __device__ static double speed_aux(const double* q, const Aux& a, const PdeParams& pp, int d) {
+    double c2 = pp.gamma * a.p * a.ir;
+    if (c2 < 0.0) c2 = 0.0;
+    return fabs(q[1 + d] * a.ir) + sqrt(c2);
+  }
   // max over directions of |v_d| + c with one division and one square root (FP64)
   __device__ static double speed_all(const double* q, const PdeParams& pp) {
     const double ir = 1.0 / q[0];

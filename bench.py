@@ -304,12 +304,12 @@ def extra_elastic(ader, synth, stream, steps=2, warmup=1):
     return out
 
 
-def extra_explosion(ader, synth, stream, steps=4, warmup=2):
-    """3-D spherical explosion, order 3, 64^3 cells on [-1,1]^3, wall boundaries, a-posteriori
-    subcell limiter (7^3 subcells): FP64 and mixed predictor; step time, troubled cells,
-    conservation of mass and energy."""
+def extra_explosion(ader, synth, stream, steps=4, warmup=2, n=64):
+    """3-D spherical explosion, order 3, n^3 cells (default 64^3) on [-1,1]^3, wall boundaries,
+    a-posteriori subcell limiter (7^3 subcells): FP64 and mixed predictor; step time, troubled
+    cells, conservation of mass and energy."""
     import torch
-    N, n = 3, 64
+    N = 3
     x, w = ader.reference_nodes(N)
     X = synth.node_coordinates(x, (n,) * 3, (-1,) * 3, (1,) * 3)
     Us = synth.explosion(synth.subcell_centres(2 * N + 1, (n,) * 3, (-1,) * 3, (1,) * 3))
@@ -318,7 +318,7 @@ def extra_explosion(ader, synth, stream, steps=4, warmup=2):
     u0_d = torch.from_numpy(synth.explosion(X).reshape(-1).copy()).cuda()
     W = torch.from_numpy(np.einsum("i,j,k->ijk", w, w, w).reshape(-1)).cuda()
     dofs = n ** 3 * 64 * 5
-    out = {"workload": "explosion3d_p3_64 (limiter on)", "dofs": dofs}
+    out = {"workload": f"explosion3d_p3_{n} (limiter on)", "dofs": dofs}
     for prec in ("fp64", "mixed"):
         cfg = ader.make_config("euler", 3, N, (n,) * 3, (-1,) * 3, (1,) * 3, "wall", synth.cfl_number(N),
                                limiter=1, precision=prec)

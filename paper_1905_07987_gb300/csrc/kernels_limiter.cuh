@@ -286,8 +286,16 @@ __device__ __forceinline__ void halo_value(const Geometry& g, const double* rep,
     if (flip[d]) out[1 + d] = -out[1 + d];
 }
 
+// minmod(a, b): the argument of smaller magnitude when a and b are nonzero with one sign, else 0,
+// taken on the bits (sign test and magnitude compare on the integer pipes).  It differs from the
+// product test a*b > 0 only where that product underflows to zero.
 __device__ __forceinline__ double minmod(double a, double b) {
-  return (a * b > 0.0) ? copysign(fmin(fabs(a), fabs(b)), a) : 0.0;
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  const unsigned long long ma = (unsigned long long)ia & 0x7fffffffffffffffull;
+  const unsigned long long mb = (unsigned long long)ib & 0x7fffffffffffffffull;
+  const unsigned long long m = ma < mb ? ma : mb;
+  const bool take = ((ia ^ ib) >= 0) && (m != 0);
+  return take ? __longlong_as_double((long long)(m | ((unsigned long long)ia & 0x8000000000000000ull))) : 0.0;
 }
 
 constexpr int FV_TPB = 256;

@@ -81,9 +81,17 @@ template <class P, int D, int N>
 struct CfgM {
   using C = Cfg<P, D, N>;
   static constexpr int n = C::n, NS = C::NS, NST = C::NST, NV = C::NV, NL = C::NL;
-  static constexpr int NF = C::NF, FR = C::FR, TPB = C::TPB, LPT = C::LPT, NPT = C::NPT;
-  static constexpr int NPS = (NS + TPB - 1) / TPB;
   static constexpr bool EULER = P::CONS && !P::LINEAR;
+  // Euler: NL / 3 threads per block rounded to whole warps (about 3 lines per thread): fewer
+  // registers per thread and more resident warps than NL / 6; a sweep of NL / {2, 3, 4, 6} on
+  // GB300 put NL / 3 first at orders 3 and 4.
+  static constexpr int LPD = 3;
+  static constexpr int TPB_E = ((NL + LPD - 1) / LPD + 31) / 32 * 32;
+  static constexpr int TPB = EULER ? (TPB_E < 64 ? 64 : (TPB_E > 512 ? 512 : TPB_E)) : C::TPB;
+  static constexpr int MINB = TPB <= 128 ? 3 : (TPB <= 256 ? 2 : 1);
+  static constexpr int NF = C::NF, FR = C::FR;
+  static constexpr int LPT = (NL + TPB - 1) / TPB, NPT = (NST + TPB - 1) / TPB;
+  static constexpr int NPS = (NS + TPB - 1) / TPB;
   static constexpr int BW = EULER ? D + 1 : 1;               // v0[D], p0 (float-float)
   static constexpr int FS = P::CONS ? cmax(n, D + 1) : 0;
   static constexpr size_t B_FB0 = P::CONS ? (size_t)D * NL * sizeof(ff) : 0;
@@ -288,7 +296,7 @@ __device__ __forceinline__ void contract_f(const float* X, const TablesF& T, con
 }
 
 template <class P, int D, int N>
-__global__ void __launch_bounds__(Cfg<P, D, N>::TPB, (Cfg<P, D, N>::TPB <= 128 ? 3 : 1))
+__global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
     k_predictor_mixed(const __grid_constant__ StepArgs A, const __grid_constant__ Tables T,
                       const __grid_constant__ TablesF F) {
   using M = CfgM<P, D, N>;

@@ -117,12 +117,13 @@ __device__ __forceinline__ EulerBase<D> load_base(const ff* uff, const ff* bff, 
   return b;
 }
 
-// Flux increment F_d(u + dq) - F_d(u) of the Euler equations in binary32 (hi parts of the base):
+// Flux increments F_d(u + dq) - F_d(u), d = 0..D-1, of the Euler equations in binary32 (hi parts
+// of the base), the velocity and pressure increments computed once per node:
 //   dv = (dj - v0 drho) / (rho0 + drho),  dp = (gamma-1)(dE - (dj.(v0+dv) + j0.dv)/2),
 //   dF = (dj_d, dj (v0_d+dv_d) + j0 dv_d + dp e_d, (dE+dp)(v0_d+dv_d) + (E0+p0) dv_d).
 template <int D>
-__device__ __forceinline__ void dflux_f(const EulerBase<D>& b, const float* dq, float g1h, float g1l,
-                                        int d, float* F) {
+__device__ __forceinline__ void dflux_f_all(const EulerBase<D>& b, const float* dq, float g1h,
+                                            float g1l, float (*F)[D + 2]) {
   constexpr int NV = D + 2;
   const float irq = __fdividef(1.0f, b.rho.h + dq[0]);
   float dv[D], djv = 0.f;
@@ -133,12 +134,16 @@ __device__ __forceinline__ void dflux_f(const EulerBase<D>& b, const float* dq, 
   }
   const float x = dq[NV - 1] - 0.5f * djv;
   const float dp = fmaf(g1h, x, g1l * x);
-  const float vd = b.v[d].h + dv[d];
-  F[0] = dq[1 + d];
+  const float ep = b.E.h + b.p.h;
 #pragma unroll
-  for (int i = 0; i < D; ++i) F[1 + i] = fmaf(dq[1 + i], vd, b.j[i].h * dv[d]);
-  F[1 + d] += dp;
-  F[NV - 1] = fmaf(dq[NV - 1] + dp, vd, (b.E.h + b.p.h) * dv[d]);
+  for (int d = 0; d < D; ++d) {
+    const float vd = b.v[d].h + dv[d];
+    F[d][0] = dq[1 + d];
+#pragma unroll
+    for (int i = 0; i < D; ++i) F[d][1 + i] = fmaf(dq[1 + i], vd, b.j[i].h * dv[d]);
+    F[d][1 + d] += dp;
+    F[d][NV - 1] = fmaf(dq[NV - 1] + dp, vd, ep * dv[d]);
+  }
 }
 
 // The same increment in float-float: velocity and pressure increments (once per node) ...
@@ -168,12 +173,12 @@ __device__ __forceinline__ void dflux_ff(const EulerBase<D>& b, const ff* dq, co
   F[NV - 1] = ff_add(ff_mul(ff_add(dq[NV - 1], dp), vd), ff_mul(ff_add(b.E, b.p), dv[d]));
 }
 
-// binary32 increments at the space-time nodes owned by this thread (iterations).
-template <class M, int d, class P, int D>
-__device__ __forceinline__ void dflux_nodes(const float* dqs, const ff* uff, const ff* bff,
-                                            const PdeParams& pp, float g1h, float g1l, float* dFs,
-                                            int tid) {
-  constexpr int NV = M::NV, NS = M::NS;
+// binary32 increments of every direction at the owned space-time nodes: dF3[d][t][NL].
+template <class M, class P, int D>
+__device__ __forceinline__ void dflux_nodes_all(const float* dqs, const ff* uff, const ff* bff,
+                                                const PdeParams& pp, float g1h, float g1l,
+                                                float* dF3, int tid) {
+  constexpr int NV = M::NV, NS = M::NS, NSL = M::NST * NV;
 #pragma unroll
   for (int k = 0; k < M::NPT; ++k) {
     const int node = tid + k * M::TPB;
@@ -181,14 +186,17 @@ __device__ __forceinline__ void dflux_nodes(const float* dqs, const ff* uff, con
       float q[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) q[v] = dqs[node * NV + v];
-      float F[NV];
+      float F[D][NV];
       if constexpr (M::EULER) {
-        dflux_f<D>(load_base<D>(uff, bff, node % NS), q, g1h, g1l, d, F);
+        dflux_f_all<D>(load_base<D>(uff, bff, node % NS), q, g1h, g1l, F);
       } else {
-        F[0] = (float)pp.a[d] * q[0];
+#pragma unroll
+        for (int d = 0; d < D; ++d) F[d][0] = (float)pp.a[d] * q[0];
       }
 #pragma unroll
-      for (int v = 0; v < NV; ++v) dFs[node * NV + v] = F[v];
+      for (int d = 0; d < D; ++d)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dF3[d * NSL + node * NV + v] = F[d][v];
     }
   }
 }
@@ -311,6 +319,9 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
   float* dql = reinterpret_cast<float*>(p);  p += M::B_DQ;  // [n][NL] dq (lo, last iterate)
   float* dFs = reinterpret_cast<float*>(p);  p += M::B_DF;  // [FS][NL] flux increments (hi)
   float* dFl = reinterpret_cast<float*>(p);                 // [FS][NL] (lo)
+  float* dF3 = dql;  // [D][n][NL] binary32 flux increments of the iterations
+  constexpr int NSL = n * NL;
+  static_assert(!P::CONS || (size_t)D * n * NL * sizeof(float) <= M::B_DQ + 2 * M::B_DF, "dF3");
   const long long c = blockIdx.x;
   const int tid = threadIdx.x;
   const double dt = A.dev->dt;
@@ -466,21 +477,18 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
     const bool last = (it == A.iters - 1);
     if (it > 0) {
       if constexpr (P::CONS) {
-        dflux_nodes<M, 0, P, D>(dqs, uff, bff, A.p, F.g1h, F.g1l, dFs, tid);
+        // all directions at once into dF3 (over dql, dFs, dFl: dql is written only by the
+        // last time solve, after every read of this iteration)
+        dflux_nodes_all<M, P, D>(dqs, uff, bff, A.p, F.g1h, F.g1l, dF3, tid);
         __syncthreads();
-        if (last) contract_f<M, 0, false, true>(dFs, F, cf, R, tid);
-        else contract_f<M, 0, false>(dFs, F, cf, R, tid);
-        __syncthreads();
-        dflux_nodes<M, 1, P, D>(dqs, uff, bff, A.p, F.g1h, F.g1l, dFs, tid);
-        __syncthreads();
-        if (last) contract_f<M, 1, false, true>(dFs, F, cf, R, tid);
-        else contract_f<M, 1, false>(dFs, F, cf, R, tid);
-        __syncthreads();
-        if constexpr (D == 3) {
-          dflux_nodes<M, 2, P, D>(dqs, uff, bff, A.p, F.g1h, F.g1l, dFs, tid);
-          __syncthreads();
-          if (last) contract_f<M, 2, false, true>(dFs, F, cf, R, tid);
-          else contract_f<M, 2, false>(dFs, F, cf, R, tid);
+        if (last) {
+          contract_f<M, 0, false, true>(dF3, F, cf, R, tid);
+          contract_f<M, 1, false, true>(dF3 + NSL, F, cf, R, tid);
+          if constexpr (D == 3) contract_f<M, 2, false, true>(dF3 + 2 * NSL, F, cf, R, tid);
+        } else {
+          contract_f<M, 0, false>(dF3, F, cf, R, tid);
+          contract_f<M, 1, false>(dF3 + NSL, F, cf, R, tid);
+          if constexpr (D == 3) contract_f<M, 2, false>(dF3 + 2 * NSL, F, cf, R, tid);
         }
       } else {
         if (last) {
@@ -528,7 +536,6 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
 #pragma unroll
             for (int m = 0; m < n; ++m) acc = fmaf(F.Kw[t][m], R[k][m], acc);
             dqs[t * NL + l] = dtf * acc;
-            dql[t * NL + l] = 0.f;
           }
         }
       }

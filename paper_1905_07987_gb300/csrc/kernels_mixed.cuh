@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
   }
   __syncthreads();
 
-  // B0: strong form for the iterations (hi, lo), weak-form volume base (FP64).
+  // B0: strong form for the iterations (hi, lo); elastic: weak-form volume base (FP64).
   float b0f[LPT], b0l[LPT];
   double b0vol[LPT];
 #pragma unroll
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
     b0vol[k] = 0.0;
     if (l < NL) {
       const int j = l / NV, v = l - (l / NV) * NV;
-      ff aS = {0.f, 0.f}, aW = {0.f, 0.f};
+      ff aS = {0.f, 0.f};
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         const int st = (d == 0 ? 1 : (d == 1 ? n : n * n));
@@ -445,7 +445,6 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
           for (int m = 0; m < n; ++m) {
             const ff f = FB0[d * NL + (j0 + m * st) * NV + v];
             ff_mac(aS, F.Dh[jd][m], F.Dl[jd][m], f.h, f.l);
-            ff_mac(aW, F.Wh[jd][m], F.Wl[jd][m], f.h, f.l);
           }
         } else {
           const int s = Elastic::src(d, v);
@@ -463,7 +462,6 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
       const double b0 = P::CONS ? -ff_to_d(aS) : b0vol[k];
       b0f[k] = (float)b0;
       b0l[k] = (float)(b0 - (double)b0f[k]);
-      if constexpr (P::CONS) b0vol[k] = ff_to_d(aW);
     }
   }
 
@@ -555,7 +553,6 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
     }
   }
   float *qbh, *qbl;   // time-averaged dq [NL] (hi, lo)
-  float *fbh, *fbl;   // time-averaged flux increments [D][NL] (hi, lo)
   if constexpr (P::CONS) {
     ff FBv[D][LPT];
     AuxFF<M> ax;
@@ -580,8 +577,8 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
     }
     qbh = dFs;
     qbl = dFl;
-    fbh = dFs + NL;
-    fbl = dFl + NL;
+    // FB0 becomes the time-averaged flux over h: G_d = F_d(u^n)/h_d + Fbar-increment_d/h_d (each
+    // line is read and written by its owner only; FB0 has no other reader until the sync below)
 #pragma unroll
     for (int k = 0; k < LPT; ++k) {
       const int l = tid + k * TPB;
@@ -590,15 +587,14 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
         qbl[l] = dqb[k].l;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-          fbh[d * NL + l] = FBv[d][k].h;
-          fbl[d * NL + l] = FBv[d][k].l;
+          ff* g = FB0 + d * NL + l;
+          *g = ff_add(*g, ff_mul(FBv[d][k], {F.ihh[d], F.ihl[d]}));
         }
       }
     }
   } else {
     qbh = dqs;
     qbl = dql;
-    fbh = fbl = nullptr;
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < LPT; ++k) {
@@ -624,13 +620,12 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
         const int jd = (j / st) % n;
         const int j0 = j - jd * st;
         if constexpr (P::CONS) {
-          ff a = {0.f, 0.f};
+          // weak-form volume term of the time-averaged flux: sum_m W[j_d][m] G_d[m]
 #pragma unroll
           for (int m = 0; m < n; ++m) {
-            const int i = d * NL + (j0 + m * st) * NV + v;
-            ff_mac(a, F.Wh[jd][m], F.Wl[jd][m], fbh[i], fbl[i]);
+            const ff g = FB0[d * NL + (j0 + m * st) * NV + v];
+            ff_mac(dvol, F.Wh[jd][m], F.Wl[jd][m], g.h, g.l);
           }
-          dvol = ff_add(dvol, ff_mul(ff_norm(a.h, a.l), {F.ihh[d], F.ihl[d]}));
         } else {
           const int s = Elastic::src(d, v);
           if (s >= 0) {
@@ -644,7 +639,7 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
           }
         }
       }
-      double vol = b0vol[k] + ff_to_d(dvol);
+      double vol = P::CONS ? ff_to_d(dvol) : b0vol[k] + ff_to_d(dvol);
       if (has_src && v >= 3) {
         double sbar = 0.0;
 #pragma unroll
@@ -667,23 +662,20 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
     const int jbase = (jp % st) + (jp / st) * st * n;
     const float* eh = side ? F.e1h : F.e0h;
     const float* el = side ? F.e1l : F.e0l;
-    ff qa = {0.f, 0.f}, fa = {0.f, 0.f}, fd = {0.f, 0.f};
+    ff qa = {0.f, 0.f}, fa = {0.f, 0.f};
 #pragma unroll
     for (int m = 0; m < n; ++m) {
       const int jj = jbase + m * st;
-      const ff uu = uff[jj * NV + v];
-      ff_mac(qa, eh[m], el[m], uu.h, uu.l);
-      ff_mac(qa, eh[m], el[m], qbh[jj * NV + v], qbl[jj * NV + v]);
+      const ff q = ff_add(uff[jj * NV + v], {qbh[jj * NV + v], qbl[jj * NV + v]});
+      ff_mac(qa, eh[m], el[m], q.h, q.l);
       if constexpr (P::CONS) {
-        const ff f = FB0[d * NL + jj * NV + v];
-        ff_mac(fa, eh[m], el[m], f.h, f.l);
-        const int i = d * NL + jj * NV + v;
-        ff_mac(fd, eh[m], el[m], fbh[i], fbl[i]);
+        const ff g = FB0[d * NL + jj * NV + v];
+        ff_mac(fa, eh[m], el[m], g.h, g.l);
       }
     }
     double* rec = fc + (d * 2 + side) * FR;
     rec[jp * NV + v] = ff_to_d(qa);
-    if constexpr (P::CONS) rec[NF * NV + jp * NV + v] = ff_to_d(fa) * A.g.h[d] + ff_to_d(fd);
+    if constexpr (P::CONS) rec[NF * NV + jp * NV + v] = ff_to_d(fa) * A.g.h[d];
   }
 }
 

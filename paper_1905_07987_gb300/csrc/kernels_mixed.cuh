@@ -267,12 +267,13 @@ __device__ __forceinline__ void dflux_nodes_ff(const float* dqs, const float* dq
   }
 }
 
-// R[k][t] += cf[d][v] * sum_m D[j_d][m] X[t][(j, j_d -> m)][src]  in binary32, with the per-cell
+// R[k][t] += cf[d][v] * sum_m D[j_d][m] X[t][(j, j_d -> m)][src]  in binary32 (D as n x n rows
+// in shared memory: the row index differs between the lanes of a warp), with the per-cell
 // coefficients cf = {hi[3][NV], lo[3][NV]} in shared memory; with LO the lo parts of the
 // coefficient and of the float-float derivative matrix are added (no rounding of fixed tables).
 template <class M, int d, bool NCP, bool LO = false>
-__device__ __forceinline__ void contract_f(const float* X, const TablesF& T, const float* cf,
-                                           float (&R)[M::LPT][M::n], int tid) {
+__device__ __forceinline__ void contract_f(const float* X, const float* Dh, const float* Dl,
+                                           const float* cf, float (&R)[M::LPT][M::n], int tid) {
   constexpr int n = M::n, NV = M::NV, NL = M::NL, TPB = M::TPB, st = ipow(n, d);
 #pragma unroll
   for (int k = 0; k < M::LPT; ++k) {
@@ -293,8 +294,8 @@ __device__ __forceinline__ void contract_f(const float* X, const TablesF& T, con
 #pragma unroll
         for (int m = 0; m < n; ++m) {
           const float x = X[t * NL + (j0 + m * st) * NV + s];
-          acc = fmaf(T.Dh[jd][m], x, acc);
-          if constexpr (LO) lo = fmaf(T.Dl[jd][m], x, lo);
+          acc = fmaf(Dh[jd * n + m], x, acc);
+          if constexpr (LO) lo = fmaf(Dl[jd * n + m], x, lo);
         }
         const float x = acc + lo;
         R[k][t] = fmaf(c, x, LO ? fmaf(clo, x, R[k][t]) : R[k][t]);
@@ -341,6 +342,21 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
   // (hi, lo) binary32 pairs and as FP64
   __shared__ float cf[2 * 3 * NV];
   __shared__ double cfd[3 * NV];
+  // tables indexed by a per-lane row (j_d, face side) staged in shared memory
+  __shared__ float sDh[n * n], sDl[n * n], sWh[n * n], sWl[n * n], sE[4][n];
+  for (int i = tid; i < n * n; i += TPB) {
+    const int a = i / n, b = i - (i / n) * n;
+    sDh[i] = F.Dh[a][b];
+    sDl[i] = F.Dl[a][b];
+    sWh[i] = F.Wh[a][b];
+    sWl[i] = F.Wl[a][b];
+  }
+  if (tid < n) {
+    sE[0][tid] = F.e0h[tid];
+    sE[1][tid] = F.e0l[tid];
+    sE[2][tid] = F.e1h[tid];
+    sE[3][tid] = F.e1l[tid];
+  }
   if (tid < 3 * NV) {
     const int d = tid / NV, v = tid % NV;
     double cd = d < D ? -A.g.inv_h[d] : 0.0;
@@ -444,7 +460,7 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
 #pragma unroll
           for (int m = 0; m < n; ++m) {
             const ff f = FB0[d * NL + (j0 + m * st) * NV + v];
-            ff_mac(aS, F.Dh[jd][m], F.Dl[jd][m], f.h, f.l);
+            ff_mac(aS, sDh[jd * n + m], sDl[jd * n + m], f.h, f.l);
           }
         } else {
           const int s = Elastic::src(d, v);
@@ -453,7 +469,7 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
 #pragma unroll
             for (int m = 0; m < n; ++m) {
               const ff f = uff[(j0 + m * st) * NV + s];
-              ff_mac(g, F.Dh[jd][m], F.Dl[jd][m], f.h, f.l);
+              ff_mac(g, sDh[jd * n + m], sDl[jd * n + m], f.h, f.l);
             }
             b0vol[k] = fma(cfd[d * NV + v], ff_to_d(g), b0vol[k]);
           }
@@ -480,23 +496,23 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
         dflux_nodes_all<M, P, D>(dqs, uff, bff, A.p, F.g1h, F.g1l, dF3, tid);
         __syncthreads();
         if (last) {
-          contract_f<M, 0, false, true>(dF3, F, cf, R, tid);
-          contract_f<M, 1, false, true>(dF3 + NSL, F, cf, R, tid);
-          if constexpr (D == 3) contract_f<M, 2, false, true>(dF3 + 2 * NSL, F, cf, R, tid);
+          contract_f<M, 0, false, true>(dF3, sDh, sDl, cf, R, tid);
+          contract_f<M, 1, false, true>(dF3 + NSL, sDh, sDl, cf, R, tid);
+          if constexpr (D == 3) contract_f<M, 2, false, true>(dF3 + 2 * NSL, sDh, sDl, cf, R, tid);
         } else {
-          contract_f<M, 0, false>(dF3, F, cf, R, tid);
-          contract_f<M, 1, false>(dF3 + NSL, F, cf, R, tid);
-          if constexpr (D == 3) contract_f<M, 2, false>(dF3 + 2 * NSL, F, cf, R, tid);
+          contract_f<M, 0, false>(dF3, sDh, sDl, cf, R, tid);
+          contract_f<M, 1, false>(dF3 + NSL, sDh, sDl, cf, R, tid);
+          if constexpr (D == 3) contract_f<M, 2, false>(dF3 + 2 * NSL, sDh, sDl, cf, R, tid);
         }
       } else {
         if (last) {
-          contract_f<M, 0, true, true>(dqs, F, cf, R, tid);
-          contract_f<M, 1, true, true>(dqs, F, cf, R, tid);
-          contract_f<M, 2, true, true>(dqs, F, cf, R, tid);
+          contract_f<M, 0, true, true>(dqs, sDh, sDl, cf, R, tid);
+          contract_f<M, 1, true, true>(dqs, sDh, sDl, cf, R, tid);
+          contract_f<M, 2, true, true>(dqs, sDh, sDl, cf, R, tid);
         } else {
-          contract_f<M, 0, true>(dqs, F, cf, R, tid);
-          contract_f<M, 1, true>(dqs, F, cf, R, tid);
-          contract_f<M, 2, true>(dqs, F, cf, R, tid);
+          contract_f<M, 0, true>(dqs, sDh, sDl, cf, R, tid);
+          contract_f<M, 1, true>(dqs, sDh, sDl, cf, R, tid);
+          contract_f<M, 2, true>(dqs, sDh, sDl, cf, R, tid);
         }
       }
     }
@@ -624,7 +640,7 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
 #pragma unroll
           for (int m = 0; m < n; ++m) {
             const ff g = FB0[d * NL + (j0 + m * st) * NV + v];
-            ff_mac(dvol, F.Wh[jd][m], F.Wl[jd][m], g.h, g.l);
+            ff_mac(dvol, sWh[jd * n + m], sWl[jd * n + m], g.h, g.l);
           }
         } else {
           const int s = Elastic::src(d, v);
@@ -633,7 +649,7 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
 #pragma unroll
             for (int m = 0; m < n; ++m) {
               const int i = (j0 + m * st) * NV + s;
-              ff_mac(a, F.Dh[jd][m], F.Dl[jd][m], qbh[i], qbl[i]);
+              ff_mac(a, sDh[jd * n + m], sDl[jd * n + m], qbh[i], qbl[i]);
             }
             dvol = ff_add(dvol, ff_mul(ff_norm(a.h, a.l), {cf[d * NV + v], cf[3 * NV + d * NV + v]}));
           }
@@ -660,8 +676,8 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
     const int d = e / (NV * NF * 2);
     const int st = (d == 0 ? 1 : (d == 1 ? n : n * n));
     const int jbase = (jp % st) + (jp / st) * st * n;
-    const float* eh = side ? F.e1h : F.e0h;
-    const float* el = side ? F.e1l : F.e0l;
+    const float* eh = sE[2 * side];
+    const float* el = sE[2 * side + 1];
     ff qa = {0.f, 0.f}, fa = {0.f, 0.f};
 #pragma unroll
     for (int m = 0; m < n; ++m) {

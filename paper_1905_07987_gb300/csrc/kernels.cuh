@@ -35,8 +35,9 @@ __device__ __forceinline__ int digit(int j) {
 
 // Lines (j, v) owned by this thread: l = tid + k*TPB.
 // Accumulate R[k][t] += coef * sum_m D[j_d][m] X[t][(j with j_d -> m)][vsrc]   (X: [n][NL] in smem)
-template <class C, int d>
-__device__ __forceinline__ void contract_lines(const double* X, const Tables& T, double coef,
+// Dm: D with row stride RS (shared memory, or the kernel-parameter table with RS = MAXN).
+template <class C, int d, int RS>
+__device__ __forceinline__ void contract_lines(const double* X, const double* Dm, double coef,
                                                double (&R)[C::LPT][C::n], int tid) {
   constexpr int n = C::n, NV = C::NV, NL = C::NL, TPB = C::TPB, st = ipow(n, d);
 #pragma unroll
@@ -46,7 +47,7 @@ __device__ __forceinline__ void contract_lines(const double* X, const Tables& T,
       const int j = l / NV, v = l - (l / NV) * NV;
       const int jd = digit<n, d>(j);
       const int j0 = j - jd * st;
-      const double* Dr = T.D[jd];
+      const double* Dr = Dm + jd * RS;
 #pragma unroll
       for (int t = 0; t < n; ++t) {
         double acc = 0.0;
@@ -60,8 +61,8 @@ __device__ __forceinline__ void contract_lines(const double* X, const Tables& T,
 
 // Elastic: each row v of B_d has one non-zero coef(d,v) at column src(d,v); the NCP term
 // B_d dq/dx_d is contracted directly from q (no flux buffer).
-template <class C, int d>
-__device__ __forceinline__ void contract_ncp_elastic(const double* X, const Tables& T,
+template <class C, int d, int RS>
+__device__ __forceinline__ void contract_ncp_elastic(const double* X, const double* Dm,
                                                      double inv_h, double irho, double lam,
                                                      double mu, double (&R)[C::LPT][C::n],
                                                      int tid) {
@@ -76,7 +77,7 @@ __device__ __forceinline__ void contract_ncp_elastic(const double* X, const Tabl
         const double coef = -Elastic::coef_ir(d, v, irho, lam, mu) * inv_h;
         const int jd = digit<n, d>(j);
         const int j0 = j - jd * st;
-        const double* Dr = T.D[jd];
+        const double* Dr = Dm + jd * RS;
 #pragma unroll
         for (int t = 0; t < n; ++t) {
           double acc = 0.0;
@@ -138,6 +139,13 @@ __global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
   const double dt = A.dev->dt;
   const double tn = A.dev->t;
   const double* u = A.u + c * NL;
+  // D and c0/c1 are indexed by a per-lane row: staged in shared memory
+  __shared__ double sD[n * n], sC[2][n];
+  for (int i = tid; i < n * n; i += TPB) sD[i] = T.D[i / n][i % n];
+  if (tid < n) {
+    sC[0][tid] = T.c0[tid];
+    sC[1][tid] = T.c1[tid];
+  }
 
   double ul[LPT];
 #pragma unroll
@@ -182,22 +190,22 @@ __global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
       load_nodes<C, P>(qs, A.p, qn, ax, tid);
       flux_nodes<C, 0, P>(qn, ax, A.p, Fs, tid);
       __syncthreads();
-      contract_lines<C, 0>(Fs, T, -A.g.inv_h[0], R, tid);
+      contract_lines<C, 0, n>(Fs, sD, -A.g.inv_h[0], R, tid);
       __syncthreads();
       flux_nodes<C, 1, P>(qn, ax, A.p, Fs, tid);
       __syncthreads();
-      contract_lines<C, 1>(Fs, T, -A.g.inv_h[1], R, tid);
+      contract_lines<C, 1, n>(Fs, sD, -A.g.inv_h[1], R, tid);
       __syncthreads();
       if constexpr (D == 3) {
         flux_nodes<C, 2, P>(qn, ax, A.p, Fs, tid);
         __syncthreads();
-        contract_lines<C, 2>(Fs, T, -A.g.inv_h[2], R, tid);
+        contract_lines<C, 2, n>(Fs, sD, -A.g.inv_h[2], R, tid);
       }
     }
     if constexpr (P::NCP) {
-      contract_ncp_elastic<C, 0>(qs, T, A.g.inv_h[0], irho, lam, mu, R, tid);
-      contract_ncp_elastic<C, 1>(qs, T, A.g.inv_h[1], irho, lam, mu, R, tid);
-      contract_ncp_elastic<C, 2>(qs, T, A.g.inv_h[2], irho, lam, mu, R, tid);
+      contract_ncp_elastic<C, 0, n>(qs, sD, A.g.inv_h[0], irho, lam, mu, R, tid);
+      contract_ncp_elastic<C, 1, n>(qs, sD, A.g.inv_h[1], irho, lam, mu, R, tid);
+      contract_ncp_elastic<C, 2, n>(qs, sD, A.g.inv_h[2], irho, lam, mu, R, tid);
     }
     if (has_src) {
 #pragma unroll
@@ -307,19 +315,19 @@ __global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
 #pragma unroll
           for (int m = 0; m < n; ++m) {
             const double f = FBs[d * NL + (j0 + m * st) * NV + v];
-            dF = fma(T.D[jd][m], f, dF);
+            dF = fma(sD[jd * n + m], f, dF);
             Fp = fma(T.e1[m], f, Fp);
             Fm = fma(T.e0[m], f, Fm);
           }
           // -(1/h) D F + (1/h)(e1/w F+ - e0/w F-)
-          vol += A.g.inv_h[d] * (-dF + T.c1[jd] * Fp - T.c0[jd] * Fm);
+          vol += A.g.inv_h[d] * (-dF + sC[1][jd] * Fp - sC[0][jd] * Fm);
         }
         if constexpr (P::NCP) {
           const int s = Elastic::src(d, v);
           if (s >= 0) {
             double dq = 0.0;
 #pragma unroll
-            for (int m = 0; m < n; ++m) dq = fma(T.D[jd][m], qbs[(j0 + m * st) * NV + s], dq);
+            for (int m = 0; m < n; ++m) dq = fma(sD[jd * n + m], qbs[(j0 + m * st) * NV + s], dq);
             vol -= A.g.inv_h[d] * Elastic::coef_ir(d, v, irho, lam, mu) * dq;
           }
         }

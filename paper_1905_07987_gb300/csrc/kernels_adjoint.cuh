@@ -250,9 +250,9 @@ __global__ void __launch_bounds__(Cfg<Elastic, 3, N>::TPB)
       for (int k = 0; k < LPT; ++k)
 #pragma unroll
         for (int t = 0; t < n; ++t) R[k][t] = 0.0;
-      contract_ncp_elastic<Cfg<Elastic, 3, N>, 0>(Q, T, A.g.inv_h[0], irho, lamc, mu, R, threadIdx.x);
-      contract_ncp_elastic<Cfg<Elastic, 3, N>, 1>(Q, T, A.g.inv_h[1], irho, lamc, mu, R, threadIdx.x);
-      contract_ncp_elastic<Cfg<Elastic, 3, N>, 2>(Q, T, A.g.inv_h[2], irho, lamc, mu, R, threadIdx.x);
+      contract_ncp_elastic<Cfg<Elastic, 3, N>, 0, MAXN>(Q, &T.D[0][0], A.g.inv_h[0], irho, lamc, mu, R, threadIdx.x);
+      contract_ncp_elastic<Cfg<Elastic, 3, N>, 1, MAXN>(Q, &T.D[0][0], A.g.inv_h[1], irho, lamc, mu, R, threadIdx.x);
+      contract_ncp_elastic<Cfg<Elastic, 3, N>, 2, MAXN>(Q, &T.D[0][0], A.g.inv_h[2], irho, lamc, mu, R, threadIdx.x);
       if (has_src) {
 #pragma unroll
         for (int k = 0; k < LPT; ++k) {

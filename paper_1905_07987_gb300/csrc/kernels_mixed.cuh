@@ -7,10 +7,14 @@
 // of binary32 with error-free transformations, about 44 significant bits) on the FP32 pipe.
 // The first N Picard iterations, their flux increments F(u+dq) - F(u) (written so that no O(1)
 // terms cancel) and contractions run in plain binary32 -- each iteration damps the error of the
-// previous one by the CFL-sized factor |dt Kw dR/dq|.  The last iteration's time solve, the final
-// flux increments, their time averages and every contraction of the epilogue run in float-float,
-// so that no binary32 rounding of the final predictor reaches the update.  The corrector, Riemann
-// solver, CFL condition and pressure / sound speed of the face states stay FP64 (other kernels).
+// previous one by the CFL-sized factor |dt Kw dR/dq|.  The last iteration's time solve and every
+// contraction of the epilogue run in float-float, so that no binary32 rounding of the final
+// predictor reaches the update.  The time-averaged flux increment is split exactly as
+//   sum_t w_t [F(u + dq_t) - F(u)] = A(u) qbar + sum_t w_t N(dq_t),   qbar = sum_t w_t dq_t,
+// with A the flux Jacobian at u^n and N the quadratic remainder: the linear part in float-float
+// once per spatial node, the O(dt^2) remainders in binary32 per space-time node.  The corrector,
+// Riemann solver, CFL condition and pressure / sound speed of the face states stay FP64 (other
+// kernels).
 #pragma once
 #include "kernels.cuh"
 
@@ -93,13 +97,13 @@ struct CfgM {
   static constexpr int LPT = (NL + TPB - 1) / TPB, NPT = (NST + TPB - 1) / TPB;
   static constexpr int NPS = (NS + TPB - 1) / TPB;
   static constexpr int BW = EULER ? D + 1 : 1;               // v0[D], p0 (float-float)
-  static constexpr int FS = P::CONS ? cmax(n, D + 1) : 0;
   static constexpr size_t B_FB0 = P::CONS ? (size_t)D * NL * sizeof(ff) : 0;
   static constexpr size_t B_UFF = (size_t)NL * sizeof(ff);
   static constexpr size_t B_BF = EULER ? (size_t)NS * BW * sizeof(ff) : 0;
   static constexpr size_t B_DQ = (size_t)n * NL * sizeof(float);   // hi, and again for lo
-  static constexpr size_t B_DF = (size_t)FS * NL * sizeof(float);  // hi, and again for lo
-  static constexpr size_t SMEM = B_FB0 + B_UFF + B_BF + 2 * B_DQ + 2 * B_DF;
+  // scratch behind dq (lo) so that [D][n][NL] binary32 values fit from dq (lo) on
+  static constexpr size_t B_SCR = P::CONS ? (size_t)(D - 1) * n * NL * sizeof(float) : 0;
+  static constexpr size_t SMEM = B_FB0 + B_UFF + B_BF + 2 * B_DQ + B_SCR;
 };
 
 template <int D>
@@ -146,33 +150,6 @@ __device__ __forceinline__ void dflux_f_all(const EulerBase<D>& b, const float* 
   }
 }
 
-// The same increment in float-float: velocity and pressure increments (once per node) ...
-template <int D>
-__device__ __forceinline__ void daux_ff(const EulerBase<D>& b, const ff* dq, ff g1, ff* dv, ff& dp) {
-  constexpr int NV = D + 2;
-  const ff den = ff_add(b.rho, dq[0]);
-  ff djv = {0.f, 0.f};
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    dv[i] = ff_div(ff_sub(dq[1 + i], ff_mul(b.v[i], dq[0])), den);
-    djv = ff_add(djv, ff_add(ff_mul(dq[1 + i], ff_add(b.v[i], dv[i])), ff_mul(b.j[i], dv[i])));
-  }
-  dp = ff_mul(g1, ff_sub(dq[NV - 1], ff_mulf(djv, 0.5f)));
-}
-
-// ... and the flux increment of direction d from them.
-template <int D>
-__device__ __forceinline__ void dflux_ff(const EulerBase<D>& b, const ff* dq, const ff* dv, ff dp,
-                                         int d, ff* F) {
-  constexpr int NV = D + 2;
-  const ff vd = ff_add(b.v[d], dv[d]);
-  F[0] = dq[1 + d];
-#pragma unroll
-  for (int i = 0; i < D; ++i) F[1 + i] = ff_add(ff_mul(dq[1 + i], vd), ff_mul(b.j[i], dv[d]));
-  F[1 + d] = ff_add(F[1 + d], dp);
-  F[NV - 1] = ff_add(ff_mul(ff_add(dq[NV - 1], dp), vd), ff_mul(ff_add(b.E, b.p), dv[d]));
-}
-
 // binary32 increments of every direction at the owned space-time nodes: dF3[d][t][NL].
 template <class M, class P, int D>
 __device__ __forceinline__ void dflux_nodes_all(const float* dqs, const ff* uff, const ff* bff,
@@ -201,67 +178,103 @@ __device__ __forceinline__ void dflux_nodes_all(const float* dqs, const ff* uff,
   }
 }
 
-// float-float increments at the owned space-time nodes (epilogue): hi -> dFs, lo -> dFl; the
-// velocity / pressure increments of the owned nodes come in registers (aux, computed once).
-template <class M>
-struct AuxFF {
-  static constexpr int W = M::EULER ? 2 * (M::NV - 1) : 1;  // (D+1) float-float values
-  float a[M::NPT][W];
-};
-
-template <class M, class P, int D>
-__device__ __forceinline__ void daux_nodes_ff(const float* dqs, const float* dql, const ff* uff,
-                                              const ff* bff, ff g1, AuxFF<M>& ax, int tid) {
-  constexpr int NV = M::NV, NS = M::NS;
-  if constexpr (M::EULER) {
+// Quadratic remainders of the Euler flux increments, N_d(dq) = F_d(u + dq) - F_d(u) - A_d(u) dq,
+// at the owned space-time nodes in binary32 (they are O(dt^2)).  With rho_t = rho0 + drho,
+// dv = (dj - v0 drho) / rho_t and dp the exact pressure increment:
+//   momentum i: rho_t dv_i dv_d + [i = d] N_p,   N_p = -(gamma-1)/2 rho_t |dv|^2,
+//   energy:     N_p v0_d - (E0 + p0) dv_d drho / rho0 + (dE + dp) dv_d,   density: 0.
+// NB[d][t][NL].
+template <class M, int D>
+__device__ __forceinline__ void remainder_nodes(const float* dqs, const ff* uff, const ff* bff,
+                                                float g1h, float g1l, float* NB, int tid) {
+  constexpr int NV = M::NV, NS = M::NS, NSL = M::NST * NV;
 #pragma unroll
-    for (int k = 0; k < M::NPT; ++k) {
-      const int node = tid + k * M::TPB;
-      if (node < M::NST) {
-        ff q[NV];
+  for (int k = 0; k < M::NPT; ++k) {
+    const int node = tid + k * M::TPB;
+    if (node < M::NST) {
+      float q[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) q[v] = {dqs[node * NV + v], dql[node * NV + v]};
-        ff dv[D], dp;
-        daux_ff<D>(load_base<D>(uff, bff, node % NS), q, g1, dv, dp);
+      for (int v = 0; v < NV; ++v) q[v] = dqs[node * NV + v];
+      const EulerBase<D> b = load_base<D>(uff, bff, node % NS);
+      const float rt = b.rho.h + q[0];
+      const float irt = __fdividef(1.0f, rt);
+      float dv[D], dv2 = 0.f, djv = 0.f;
 #pragma unroll
-        for (int i = 0; i < D; ++i) {
-          ax.a[k][2 * i] = dv[i].h;
-          ax.a[k][2 * i + 1] = dv[i].l;
-        }
-        ax.a[k][2 * D] = dp.h;
-        ax.a[k][2 * D + 1] = dp.l;
+      for (int i = 0; i < D; ++i) {
+        dv[i] = (q[1 + i] - b.v[i].h * q[0]) * irt;
+        dv2 = fmaf(dv[i], dv[i], dv2);
+        djv = fmaf(q[1 + i], b.v[i].h + dv[i], fmaf(b.j[i].h, dv[i], djv));
+      }
+      const float x = q[NV - 1] - 0.5f * djv;
+      const float dp = fmaf(g1h, x, g1l * x);
+      const float np = -0.5f * g1h * rt * dv2;
+      const float er = (b.E.h + b.p.h) * q[0] * __fdividef(1.0f, b.rho.h);
+      const float ed = q[NV - 1] + dp;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        float* o = NB + d * NSL + node * NV;
+        o[0] = 0.f;
+        const float rdv = rt * dv[d];
+#pragma unroll
+        for (int i = 0; i < D; ++i) o[1 + i] = rdv * dv[i] + (i == d ? np : 0.f);
+        o[NV - 1] = fmaf(np, b.v[d].h, (ed - er) * dv[d]);
       }
     }
   }
 }
 
-template <class M, int d, class P, int D>
-__device__ __forceinline__ void dflux_nodes_ff(const float* dqs, const float* dql, const ff* uff,
-                                               const ff* bff, const AuxFF<M>& ax,
-                                               const PdeParams& pp, float* dFs, float* dFl, int tid) {
-  constexpr int NV = M::NV, NS = M::NS;
+// Linear part of the time-averaged flux increments, A_d(u^n) qbar, at the owned spatial nodes in
+// float-float (qbar: time average of dq), added to G_d = FB0 over h_d:
+//   dv = (jbar - v0 rhobar) / rho0,  dp = (gamma-1)(Ebar - (v0.jbar + j0.dv)/2),
+//   A_d qbar = (jbar_d, jbar v0_d + j0 dv_d + dp e_d, (Ebar + dp) v0_d + (E0 + p0) dv_d);
+// linear fluxes (advection): a_d qbar.
+template <class M, class P, int D>
+__device__ __forceinline__ void linear_nodes(const float* qbh, const float* qbl, const ff* uff,
+                                             const ff* bff, ff g1, const TablesF& F,
+                                             const PdeParams& pp, ff* G, int tid) {
+  constexpr int NV = M::NV, NS = M::NS, NL = M::NL;
 #pragma unroll
-  for (int k = 0; k < M::NPT; ++k) {
-    const int node = tid + k * M::TPB;
-    if (node < M::NST) {
-      ff q[NV];
+  for (int k = 0; k < M::NPS; ++k) {
+    const int j = tid + k * M::TPB;
+    if (j < NS) {
+      ff qb[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) q[v] = {dqs[node * NV + v], dql[node * NV + v]};
-      ff F[NV];
+      for (int v = 0; v < NV; ++v) qb[v] = {qbh[j * NV + v], qbl[j * NV + v]};
       if constexpr (M::EULER) {
-        ff dv[D];
+        const EulerBase<D> b = load_base<D>(uff, bff, j);
+        const ff ir = ff_div({1.f, 0.f}, b.rho);
+        ff dv[D], jv = {0.f, 0.f};
 #pragma unroll
-        for (int i = 0; i < D; ++i) dv[i] = {ax.a[k][2 * i], ax.a[k][2 * i + 1]};
-        dflux_ff<D>(load_base<D>(uff, bff, node % NS), q, dv, {ax.a[k][2 * D], ax.a[k][2 * D + 1]}, d, F);
+        for (int i = 0; i < D; ++i) {
+          dv[i] = ff_mul(ff_sub(qb[1 + i], ff_mul(b.v[i], qb[0])), ir);
+          jv = ff_add(jv, ff_add(ff_mul(qb[1 + i], b.v[i]), ff_mul(b.j[i], dv[i])));
+        }
+        const ff dp = ff_mul(g1, ff_sub(qb[NV - 1], ff_mulf(jv, 0.5f)));
+        const ff ep = ff_add(b.E, b.p);
+        const ff ed = ff_add(qb[NV - 1], dp);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          ff Fl[NV];
+          Fl[0] = qb[1 + d];
+#pragma unroll
+          for (int i = 0; i < D; ++i) Fl[1 + i] = ff_add(ff_mul(qb[1 + i], b.v[d]), ff_mul(b.j[i], dv[d]));
+          Fl[1 + d] = ff_add(Fl[1 + d], dp);
+          Fl[NV - 1] = ff_add(ff_mul(ed, b.v[d]), ff_mul(ep, dv[d]));
+          const ff ih = {F.ihh[d], F.ihl[d]};
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            ff* g = G + d * NL + j * NV + v;
+            *g = ff_add(*g, ff_mul(Fl[v], ih));
+          }
+        }
       } else {
-        const double a = pp.a[d];
-        const float ah = (float)a;
-        F[0] = ff_mul(q[0], {ah, (float)(a - (double)ah)});
-      }
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        dFs[node * NV + v] = F[v].h;
-        dFl[node * NV + v] = F[v].l;
+        for (int d = 0; d < D; ++d) {
+          const double a = pp.a[d];
+          const float ah = (float)a;
+          ff* g = G + d * NL + j * NV;
+          *g = ff_add(*g, ff_mul(ff_mul(qb[0], {ah, (float)(a - (double)ah)}), {F.ihh[d], F.ihl[d]}));
+        }
       }
     }
   }
@@ -317,12 +330,12 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
   ff* uff = reinterpret_cast<ff*>(p);  p += M::B_UFF;    // [NL] u
   ff* bff = reinterpret_cast<ff*>(p);  p += M::B_BF;     // [NS][D+1] v0, p0 (Euler)
   float* dqs = reinterpret_cast<float*>(p);  p += M::B_DQ;  // [n][NL] dq (hi)
-  float* dql = reinterpret_cast<float*>(p);  p += M::B_DQ;  // [n][NL] dq (lo, last iterate)
-  float* dFs = reinterpret_cast<float*>(p);  p += M::B_DF;  // [FS][NL] flux increments (hi)
-  float* dFl = reinterpret_cast<float*>(p);                 // [FS][NL] (lo)
-  float* dF3 = dql;  // [D][n][NL] binary32 flux increments of the iterations
+  float* dql = reinterpret_cast<float*>(p);                 // [n][NL] dq (lo, last iterate)
+  // [D][n][NL] binary32 over dq (lo) and the scratch behind it: flux increments in the
+  // iterations (dq (lo) is written only by the last time solve, after every read), quadratic
+  // flux remainders in the epilogue
+  float* dF3 = dql;
   constexpr int NSL = n * NL;
-  static_assert(!P::CONS || (size_t)D * n * NL * sizeof(float) <= M::B_DQ + 2 * M::B_DF, "dF3");
   const long long c = blockIdx.x;
   const int tid = threadIdx.x;
   const double dt = A.dev->dt;
@@ -491,8 +504,7 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
     const bool last = (it == A.iters - 1);
     if (it > 0) {
       if constexpr (P::CONS) {
-        // all directions at once into dF3 (over dql, dFs, dFl: dql is written only by the
-        // last time solve, after every read of this iteration)
+        // all directions at once into dF3
         dflux_nodes_all<M, P, D>(dqs, uff, bff, A.p, F.g1h, F.g1l, dF3, tid);
         __syncthreads();
         if (last) {
@@ -570,44 +582,37 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
   }
   float *qbh, *qbl;   // time-averaged dq [NL] (hi, lo)
   if constexpr (P::CONS) {
-    ff FBv[D][LPT];
-    AuxFF<M> ax;
-    daux_nodes_ff<M, P, D>(dqs, dql, uff, bff, g1, ax, tid);
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      if (d == 0) dflux_nodes_ff<M, 0, P, D>(dqs, dql, uff, bff, ax, A.p, dFs, dFl, tid);
-      if (d == 1) dflux_nodes_ff<M, 1, P, D>(dqs, dql, uff, bff, ax, A.p, dFs, dFl, tid);
-      if constexpr (D == 3)
-        if (d == 2) dflux_nodes_ff<M, 2, P, D>(dqs, dql, uff, bff, ax, A.p, dFs, dFl, tid);
-      __syncthreads();
-#pragma unroll
-      for (int k = 0; k < LPT; ++k) {
-        const int l = tid + k * TPB;
-        FBv[d][k] = {0.f, 0.f};
-        if (l < NL) {
-#pragma unroll
-          for (int t = 0; t < n; ++t) ff_mac(FBv[d][k], F.w[t], F.wl[t], dFs[t * NL + l], dFl[t * NL + l]);
-        }
-      }
-      __syncthreads();
+    // Time-averaged flux increment = A(u^n) qbar + sum_t w_t N(dq_t): the quadratic remainders N
+    // per space-time node in binary32, the linear part once per spatial node in float-float.
+    __syncthreads();  // every read of dql is done: NB overwrites it
+    float* NB = dF3;  // [D][n][NL] remainders
+    if constexpr (M::EULER) {
+      remainder_nodes<M, D>(dqs, uff, bff, F.g1h, F.g1l, NB, tid);
+      __syncthreads();  // every read of dqs is done: qbar overwrites it
     }
-    qbh = dFs;
-    qbl = dFl;
-    // FB0 becomes the time-averaged flux over h: G_d = F_d(u^n)/h_d + Fbar-increment_d/h_d (each
-    // line is read and written by its owner only; FB0 has no other reader until the sync below)
+    qbh = dqs;
+    qbl = dqs + NL;
 #pragma unroll
     for (int k = 0; k < LPT; ++k) {
       const int l = tid + k * TPB;
       if (l < NL) {
         qbh[l] = dqb[k].h;
         qbl[l] = dqb[k].l;
+        if constexpr (M::EULER) {
+          // FB0 becomes G_d = F_d(u^n)/h_d + (time-averaged increment)_d/h_d; here the remainders
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-          ff* g = FB0 + d * NL + l;
-          *g = ff_add(*g, ff_mul(FBv[d][k], {F.ihh[d], F.ihl[d]}));
+          for (int d = 0; d < D; ++d) {
+            float nb = 0.f;
+#pragma unroll
+            for (int t = 0; t < n; ++t) nb = fmaf(F.w[t], NB[d * NSL + t * NL + l], nb);
+            ff* g = FB0 + d * NL + l;
+            *g = ff_add(*g, {nb * F.ihh[d], 0.f});
+          }
         }
       }
     }
+    __syncthreads();
+    linear_nodes<M, P, D>(qbh, qbl, uff, bff, g1, F, A.p, FB0, tid);
   } else {
     qbh = dqs;
     qbl = dql;

@@ -50,6 +50,8 @@ struct TablesF {
   float Wh[MAXN][MAXN], Wl[MAXN][MAXN];    // weak derivative Dw = c1 e1^T - c0 e0^T - D
   float Kw[MAXN][MAXN], Kwl[MAXN][MAXN];   // K1^{-1} diag(w) (hi, lo)
   float kw1[MAXN], kw1l[MAXN];             // row sums of Kw (hi, lo)
+  float wk1h, wk1l;                        // sum_t w_t kw1[t]      (time average of the
+  float wKh[MAXN], wKl[MAXN];              // sum_t w_t Kw[t][m]     time solve)
   float w[MAXN], wl[MAXN];
   float ihh[3], ihl[3];                    // 1/h_d (hi, lo)
   float g1h, g1l;                          // gamma - 1 (hi, lo)

@@ -205,6 +205,16 @@ void build_tables_f(int order, const Tables& T, TablesF& F) {
     split_f(T.e0[i], F.e0h[i], F.e0l[i]);
     split_f(T.e1[i], F.e1h[i], F.e1l[i]);
   }
+  // time averages of the time solve: qbar = dt (sum_t w_t kw1_t B0 + sum_m (sum_t w_t Kw[t][m]) R_m)
+  double wk1 = 0.0;
+  for (int t = 0; t < n; ++t)
+    for (int m = 0; m < n; ++m) wk1 += T.w[t] * T.Kw[t][m];
+  split_f(wk1, F.wk1h, F.wk1l);
+  for (int m = 0; m < n; ++m) {
+    double a = 0.0;
+    for (int t = 0; t < n; ++t) a += T.w[t] * T.Kw[t][m];
+    split_f(a, F.wKh[m], F.wKl[m]);
+  }
 }
 
 // Solve A x = b for several right-hand sides (Gauss-Jordan, partial pivoting); A is m x m.

@@ -100,10 +100,9 @@ struct CfgM {
   static constexpr size_t B_FB0 = P::CONS ? (size_t)D * NL * sizeof(ff) : 0;
   static constexpr size_t B_UFF = (size_t)NL * sizeof(ff);
   static constexpr size_t B_BF = EULER ? (size_t)NS * BW * sizeof(ff) : 0;
-  static constexpr size_t B_DQ = (size_t)n * NL * sizeof(float);   // hi, and again for lo
-  // scratch behind dq (lo) so that [D][n][NL] binary32 values fit from dq (lo) on
-  static constexpr size_t B_SCR = P::CONS ? (size_t)(D - 1) * n * NL * sizeof(float) : 0;
-  static constexpr size_t SMEM = B_FB0 + B_UFF + B_BF + 2 * B_DQ + B_SCR;
+  static constexpr size_t B_DQ = (size_t)n * NL * sizeof(float);
+  static constexpr size_t B_F3 = P::CONS ? (size_t)D * n * NL * sizeof(float) : 0;
+  static constexpr size_t SMEM = B_FB0 + B_UFF + B_BF + B_DQ + B_F3;
 };
 
 template <int D>
@@ -329,12 +328,10 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
   ff* FB0 = reinterpret_cast<ff*>(p);  p += M::B_FB0;    // [D][NL] F_d(u)/h_d
   ff* uff = reinterpret_cast<ff*>(p);  p += M::B_UFF;    // [NL] u
   ff* bff = reinterpret_cast<ff*>(p);  p += M::B_BF;     // [NS][D+1] v0, p0 (Euler)
-  float* dqs = reinterpret_cast<float*>(p);  p += M::B_DQ;  // [n][NL] dq (hi)
-  float* dql = reinterpret_cast<float*>(p);                 // [n][NL] dq (lo, last iterate)
-  // [D][n][NL] binary32 over dq (lo) and the scratch behind it: flux increments in the
-  // iterations (dq (lo) is written only by the last time solve, after every read), quadratic
-  // flux remainders in the epilogue
-  float* dF3 = dql;
+  float* dqs = reinterpret_cast<float*>(p);  p += M::B_DQ;  // [n][NL] dq (binary32)
+  // [D][n][NL] binary32: flux increments in the iterations, quadratic flux remainders in the
+  // epilogue
+  float* dF3 = reinterpret_cast<float*>(p);
   constexpr int NSL = n * NL;
   const long long c = blockIdx.x;
   const int tid = threadIdx.x;
@@ -496,6 +493,9 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
 
   // ---- Picard iterations on dq ----------------------------------------------------------
   float R[LPT][n];
+  ff dqb[P::CONS ? LPT : 1];  // time average of the last iterate (float-float)
+#pragma unroll
+  for (int k = 0; k < (P::CONS ? LPT : 1); ++k) dqb[k] = {0.f, 0.f};
   for (int it = 0; it < A.iters; ++it) {
 #pragma unroll
     for (int k = 0; k < LPT; ++k)
@@ -547,21 +547,28 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
     for (int k = 0; k < LPT; ++k) {
       const int l = tid + k * TPB;
       if (l < NL) {
+        // dq_t = dt (kw1_t B0 + sum_m Kw[t][m] R_m); after the last iteration only the flux
+        // remainders (conservative form) read the nodal dq_t
+        if (!last || P::CONS) {
 #pragma unroll
-        for (int t = 0; t < n; ++t) {
-          if (last) {  // float-float time solve: dq = dt (kw1 B0 + Kw R)
-            ff acc = {0.f, 0.f};
-            ff_mac(acc, F.kw1[t], F.kw1l[t], b0f[k], b0l[k]);
-#pragma unroll
-            for (int m = 0; m < n; ++m) ff_mac(acc, F.Kw[t][m], F.Kwl[t][m], R[k][m], 0.f);
-            const ff q = ff_mul(dtff, ff_norm(acc.h, acc.l));
-            dqs[t * NL + l] = q.h;
-            dql[t * NL + l] = q.l;
-          } else {
+          for (int t = 0; t < n; ++t) {
             float acc = F.kw1[t] * b0f[k];
 #pragma unroll
             for (int m = 0; m < n; ++m) acc = fmaf(F.Kw[t][m], R[k][m], acc);
             dqs[t * NL + l] = dtf * acc;
+          }
+        }
+        if (last) {  // the time average qbar in float-float, from the weights averaged over t
+          ff acc = {0.f, 0.f};
+          ff_mac(acc, F.wk1h, F.wk1l, b0f[k], b0l[k]);
+#pragma unroll
+          for (int m = 0; m < n; ++m) ff_mac(acc, F.wKh[m], F.wKl[m], R[k][m], 0.f);
+          const ff q = ff_mul(dtff, ff_norm(acc.h, acc.l));
+          if constexpr (P::CONS) {
+            dqb[k] = q;
+          } else {  // straight to its place in shared memory (hi, lo over dq)
+            dqs[l] = q.h;
+            dqs[NL + l] = q.l;
           }
         }
       }
@@ -570,21 +577,10 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
   }
 
   // ---- epilogue in float-float -------------------------------------------------------------
-  ff dqb[LPT];
-#pragma unroll
-  for (int k = 0; k < LPT; ++k) {
-    const int l = tid + k * TPB;
-    dqb[k] = {0.f, 0.f};
-    if (l < NL) {
-#pragma unroll
-      for (int t = 0; t < n; ++t) ff_mac(dqb[k], F.w[t], F.wl[t], dqs[t * NL + l], dql[t * NL + l]);
-    }
-  }
   float *qbh, *qbl;   // time-averaged dq [NL] (hi, lo)
   if constexpr (P::CONS) {
     // Time-averaged flux increment = A(u^n) qbar + sum_t w_t N(dq_t): the quadratic remainders N
     // per space-time node in binary32, the linear part once per spatial node in float-float.
-    __syncthreads();  // every read of dql is done: NB overwrites it
     float* NB = dF3;  // [D][n][NL] remainders
     if constexpr (M::EULER) {
       remainder_nodes<M, D>(dqs, uff, bff, F.g1h, F.g1l, NB, tid);
@@ -614,17 +610,8 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
     __syncthreads();
     linear_nodes<M, P, D>(qbh, qbl, uff, bff, g1, F, A.p, FB0, tid);
   } else {
-    qbh = dqs;
-    qbl = dql;
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < LPT; ++k) {
-      const int l = tid + k * TPB;
-      if (l < NL) {
-        qbh[l] = dqb[k].h;
-        qbl[l] = dqb[k].l;
-      }
-    }
+    qbh = dqs;  // written by the last time solve
+    qbl = dqs + NL;
   }
   __syncthreads();
 

@@ -485,9 +485,14 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
           }
         }
       }
-      const double b0 = P::CONS ? -ff_to_d(aS) : b0vol[k];
-      b0f[k] = (float)b0;
-      b0l[k] = (float)(b0 - (double)b0f[k]);
+      if constexpr (P::CONS) {  // -aS, renormalised, without a round trip through FP64
+        const ff b = ff_norm(aS.h, aS.l);
+        b0f[k] = -b.h;
+        b0l[k] = -b.l;
+      } else {
+        b0f[k] = (float)b0vol[k];
+        b0l[k] = (float)(b0vol[k] - (double)b0f[k]);
+      }
     }
   }
 
@@ -655,35 +660,42 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
         vol = fma(-A.src.M[v - 3] * A.src.phi[j], sbar, vol);
       }
       un[l] = fma(dt, vol, ul[k]);
+      uff[l] = ff_add(uff[l], {qbh[l], qbl[l]});  // time-averaged state u^n + qbar for the faces
     }
   }
+  __syncthreads();
 
-  // ---- face records: float-float extrapolations of the base and the increment -----------------
+  // ---- face records: float-float extrapolations of the time-averaged state and flux, both
+  // faces of a direction from the same loads --------------------------------------------------
   double* fc = A.face + c * (long long)(D * 2 * FR);
-  constexpr int NFE = D * 2 * NF * NV;
+  constexpr int NFE = D * NF * NV;
   for (int e = tid; e < NFE; e += TPB) {
     const int v = e % NV;
     const int jp = (e / NV) % NF;
-    const int side = (e / (NV * NF)) % 2;
-    const int d = e / (NV * NF * 2);
+    const int d = e / (NV * NF);
     const int st = (d == 0 ? 1 : (d == 1 ? n : n * n));
     const int jbase = (jp % st) + (jp / st) * st * n;
-    const float* eh = sE[2 * side];
-    const float* el = sE[2 * side + 1];
-    ff qa = {0.f, 0.f}, fa = {0.f, 0.f};
+    ff qa0 = {0.f, 0.f}, qa1 = {0.f, 0.f}, fa0 = {0.f, 0.f}, fa1 = {0.f, 0.f};
 #pragma unroll
     for (int m = 0; m < n; ++m) {
       const int jj = jbase + m * st;
-      const ff q = ff_add(uff[jj * NV + v], {qbh[jj * NV + v], qbl[jj * NV + v]});
-      ff_mac(qa, eh[m], el[m], q.h, q.l);
+      const ff q = uff[jj * NV + v];
+      ff_mac(qa0, sE[0][m], sE[1][m], q.h, q.l);
+      ff_mac(qa1, sE[2][m], sE[3][m], q.h, q.l);
       if constexpr (P::CONS) {
         const ff g = FB0[d * NL + jj * NV + v];
-        ff_mac(fa, eh[m], el[m], g.h, g.l);
+        ff_mac(fa0, sE[0][m], sE[1][m], g.h, g.l);
+        ff_mac(fa1, sE[2][m], sE[3][m], g.h, g.l);
       }
     }
-    double* rec = fc + (d * 2 + side) * FR;
-    rec[jp * NV + v] = ff_to_d(qa);
-    if constexpr (P::CONS) rec[NF * NV + jp * NV + v] = ff_to_d(fa) * A.g.h[d];
+    double* rec0 = fc + (d * 2) * FR;
+    double* rec1 = rec0 + FR;
+    rec0[jp * NV + v] = ff_to_d(qa0);
+    rec1[jp * NV + v] = ff_to_d(qa1);
+    if constexpr (P::CONS) {
+      rec0[NF * NV + jp * NV + v] = ff_to_d(fa0) * A.g.h[d];
+      rec1[NF * NV + jp * NV + v] = ff_to_d(fa1) * A.g.h[d];
+    }
   }
 }
 

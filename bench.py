@@ -36,16 +36,18 @@ WORKLOADS = {
 }
 FP64_SMS, FP64_FMA_PER_CLK, SM_MAX_MHZ = 152, 2, 2070.0
 # DRAM bytes (read + write) per cell of the predictor kernels, from one ncu capture of the same
-# kernels on 40^3 cells (profiles/), scaled to a launch by the number of cells (the traffic is per
-# cell: state in, next state and face records out).
-TRAFFIC_PER_CELL = {"fp64": 325.915392e6 / 64000 + 1029.375e6 / 64000,
-                    "mixed": 322.237696e6 / 64000 + 1029.472e6 / 64000}
+# kernels on 40^3 cells, scaled to a launch by the number of cells (the traffic is per cell:
+# state in, next state and face records out).
+TRAFFIC_PER_CELL = {"fp64": 327.118080e6 / 64000 + 1029.642e6 / 64000,
+                    "mixed": 320.242944e6 / 64000 + 1028.278e6 / 64000}
 FP64_PEAK = FP64_SMS * FP64_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6  # FLOP/s
 
 
 def predictor_flops_per_cell(pde, D, N, iters):
     """Algorithmic FP64 flops of the fused predictor kernel for one cell (FMA = 2 flops,
-    add / multiply / divide = 1), as counted in DESIGN.md."""
+    add / multiply / divide = 1): per Picard iteration the nodal fluxes (aux 2D+5, D flux vectors
+    of D+4) at the space-time nodes, the D derivative contractions and the time solve; then the
+    epilogue (fluxes, time averages, volume term, face extrapolations)."""
     n = N + 1
     NST = n ** (D + 1)
     NV = D + 2

@@ -112,6 +112,12 @@ struct StepArgs {
   double dt_fixed;     // > 0: fixed dt
   double t_end;        // > 0: clip
   double cfl;
+  // mixed form of the Euler step: binary32 wave speeds |v_d| + c of the face states
+  // [cell][dir][side][face node], written by the predictor and read by the Riemann solver (null:
+  // the Riemann solver computes FP64 speeds); cfl_f32: the CFL signal speed in binary32 with a
+  // relative margin of 2^-16 (0: FP64)
+  float* fspeed;
+  int cfl_f32;
 };
 
 // Per (pde, dim) kernel family; order dispatch happens inside.

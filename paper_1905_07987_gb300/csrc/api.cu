@@ -325,6 +325,7 @@ struct ader_ctx {
   double* u_next = nullptr;
   double* face = nullptr;
   double* phi = nullptr;
+  float* fspeed = nullptr;  // mixed Euler: binary32 face wave speeds
   double* mat = nullptr;
   DevScalars* dev = nullptr;
   bool state_set = false, mat_set = false;
@@ -380,6 +381,7 @@ static void free_all(ader_ctx* c) {
   cudaFree(c->u_next);
   cudaFree(c->face);
   cudaFree(c->phi);
+  cudaFree(c->fspeed);
   cudaFree(c->mat);
   cudaFree(c->dev);
   cudaFree(c->src_phi);
@@ -499,6 +501,8 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->u_next, c->ndof * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->face, ncells * cfg->dim * 2 * face_rec * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->phi, nphi_total * sizeof(double));
+  if (e == cudaSuccess && cfg->precision == ADER_PREC_MIXED && cfg->pde == ADER_PDE_EULER)
+    e = cudaMalloc(&c->fspeed, ncells * cfg->dim * 2 * c->nf * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&c->dev, sizeof(DevScalars));
   if (e == cudaSuccess && cfg->pde == ADER_PDE_ELASTIC) e = cudaMalloc(&c->mat, ncells * 3 * sizeof(double));
   if (cfg->limiter) {
@@ -774,7 +778,11 @@ static ader_status mark(ader_ctx* c, int k) {
 }
 
 static ader_status step_impl(ader_ctx* c, double dt, double t_end) {
-  const StepArgs a = make_args(c, dt, t_end);
+  StepArgs a = make_args(c, dt, t_end);
+  if (c->fspeed) {  // mixed Euler step: binary32 wave speeds (predictor -> Riemann, CFL)
+    a.fspeed = c->fspeed;
+    a.cfl_f32 = 1;
+  }
   cudaStream_t s = c->stream;
   ader_status st;
   if ((st = mark(c, 0)) != ADER_OK) return st;

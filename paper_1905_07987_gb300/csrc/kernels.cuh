@@ -458,10 +458,23 @@ __global__ void __launch_bounds__(128) k_riemann(const __grid_constant__ StepArg
     }
   }
   if constexpr (P::CONS && !P::LINEAR) {
+    if (A.fspeed) {  // mixed form: binary32 speeds of the face states from the predictor
+      const float* sl = cL >= 0 ? A.fspeed + (cL * D + d) * (2 * NF) + NF : nullptr;
+      const float* sr = cR >= 0 ? A.fspeed + (cR * D + d) * (2 * NF) : nullptr;
 #pragma unroll
-    for (int r = 0; r < PER; ++r) {
-      const int jp = lane + 32 * r;
-      if (jp < NF) smax = fmax(smax, fmax(P::speed(qL[r], A.p, d), P::speed(qR[r], A.p, d)));
+      for (int r = 0; r < PER; ++r) {
+        const int jp = lane + 32 * r;
+        if (jp < NF) {  // a boundary side has the speed of its interior mirror / copy
+          const float a = sl ? sl[jp] : sr[jp], b = sr ? sr[jp] : sl[jp];
+          smax = fmax(smax, (double)fmaxf(a, b));
+        }
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < PER; ++r) {
+        const int jp = lane + 32 * r;
+        if (jp < NF) smax = fmax(smax, fmax(P::speed(qL[r], A.p, d), P::speed(qR[r], A.p, d)));
+      }
     }
   }
   double s;
@@ -578,6 +591,33 @@ __global__ void __launch_bounds__(256) k_cfl(const __grid_constant__ StepArgs A)
       for (int d = 0; d < D; ++d) s = fmax(s, P::speed(q, A.p, d));
       if (!isfinite(q[0])) bad = true;
       lmax = fmax(lmax, s);
+    }
+  } else if (A.cfl_f32) {
+    // mixed form: max_d |v_d| + c in binary32 from the rounded state, enlarged by 2^-16 (the
+    // binary32 speed is within a few 1e-7 of the FP64 one unless p cancels badly); finiteness
+    // read from the exponent bits
+    const float gam = (float)A.p.gamma, g1 = (float)(A.p.gamma - 1.0);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.g.ncells * NS;
+         i += (long long)gridDim.x * blockDim.x) {
+      const double* q = A.u + i * NV;
+      float f[NV];
+      bool fin = true;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        fin = fin && ((__double2hiint(q[v]) & 0x7ff00000) != 0x7ff00000);
+        f[v] = __double2float_rn(q[v]);
+      }
+      const float ir = __fdividef(1.0f, f[0]);
+      float j2 = 0.f, vm = 0.f;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        j2 = fmaf(f[1 + d], f[1 + d], j2);
+        vm = fmaxf(vm, fabsf(f[1 + d]));
+      }
+      const float c2 = gam * (g1 * fmaf(-0.5f * j2, ir, f[NV - 1])) * ir;
+      const float s = (vm * fabsf(ir) + (c2 > 0.f ? sqrtf(c2) : 0.f)) * (1.0f + 0x1p-16f);
+      if (!fin || !(s >= 0.f) || isinf(s)) bad = true;
+      else lmax = fmax(lmax, (double)s);
     }
   } else {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.g.ncells * NS;

@@ -696,6 +696,29 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
       rec0[NF * NV + jp * NV + v] = ff_to_d(fa0) * A.g.h[d];
       rec1[NF * NV + jp * NV + v] = ff_to_d(fa1) * A.g.h[d];
     }
+    if constexpr (M::EULER) {  // face states (hi parts) for the wave speeds below
+      dF3[((d * 2) * NF + jp) * NV + v] = qa0.h;
+      dF3[((d * 2 + 1) * NF + jp) * NV + v] = qa1.h;
+    }
+  }
+  if constexpr (M::EULER) {
+    // binary32 Rusanov wave speeds |v_d| + c of every face state, for the Riemann solver
+    // (c^2 < 0 counts as c = 0, as in the FP64 speeds)
+    if (A.fspeed) {
+      __syncthreads();
+      const float g1 = F.g1h, gam = F.g1h + 1.0f;
+      float* fs = A.fspeed + c * (long long)(D * 2 * NF);
+      for (int e = tid; e < D * 2 * NF; e += TPB) {
+        const int d = e / (2 * NF);
+        const float* q = dF3 + e * NV;
+        const float ir = __fdividef(1.0f, q[0]);
+        float j2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < D; ++i) j2 = fmaf(q[1 + i], q[1 + i], j2);
+        const float c2 = gam * (g1 * fmaf(-0.5f * j2, ir, q[NV - 1])) * ir;
+        fs[e] = fabsf(q[1 + d] * ir) + (c2 > 0.f ? sqrtf(c2) : 0.f);
+      }
+    }
   }
 }
 

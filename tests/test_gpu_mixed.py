@@ -97,3 +97,42 @@ def test_mixed_error_vs_exact_within_1p1_of_fp64():
         ex = synth.entropy_wave(c.X, t)
         errs[prec] = float(np.sqrt(np.mean((c.get()[..., 0] - ex[..., 0]) ** 2)))
     assert errs["mixed"] <= 1.1 * errs["fp64"], errs
+
+
+def test_mixed_full_size_sampled_cells_euler_81():
+    """The benchmark's configuration (81^3 cells, order 4, entropy wave, mixed predictor, the same
+    launch shapes): sampled cells against the FP64 oracle on their 3x3x3 neighbourhood (a cell's
+    update depends only on itself and its face neighbours)."""
+    nc = (81, 81, 81)
+    c = Case("euler", 3, 4, nc, precision="mixed")
+    u0 = synth.entropy_wave(c.X)
+    c.set(u0)
+    c.ctx.step()
+    dt = c.ctx.last_dt()
+    got = c.get()
+    from oracle.aderdg import ADERDG, Grid
+    from oracle.pde import Euler
+    sub = ADERDG(Euler(3), Grid((3, 3, 3), (0, 0, 0), (3 / 81,) * 3, [("periodic", "periodic")] * 3), 4,
+                 cfl=c.cfl)
+    rng = np.random.default_rng(1)
+    samples = [(0, 0, 0), (80, 80, 80), (13, 52, 71)] + [tuple(rng.integers(0, 81, 3)) for _ in range(5)]
+    for (i, j, k) in samples:
+        idx = [((i + di) % 81) + 81 * (((j + dj) % 81) + 81 * ((k + dk) % 81))
+               for dk in (-1, 0, 1) for dj in (-1, 0, 1) for di in (-1, 0, 1)]
+        out = sub.step(torch.from_numpy(u0[idx]), torch.tensor(dt, dtype=torch.float64)).numpy()
+        centre = i + 81 * (j + 81 * k)
+        assert change_rel(got[centre], out[13], u0[centre]) < 2e-6, (i, j, k)
+        assert rel_linf(got[centre], out[13]) < 1e-9, (i, j, k)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_uniform_flow_is_preserved(prec):
+    """Degenerate case: a constant state with non-zero velocity is an exact solution; every flux
+    derivative and increment vanishes up to rounding."""
+    c = Case("euler", 3, 3, (4, 5, 3), precision=prec)
+    u0 = synth.euler_conserved(np.full_like(c.X[0], 1.3), [np.full_like(c.X[0], 0.4), -0.2, 0.7],
+                               np.full_like(c.X[0], 2.1))
+    c.set(u0)
+    for _ in range(3):
+        c.ctx.step()
+    assert rel_linf(c.get(), u0) < 1e-13

@@ -351,9 +351,8 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
     mu = A.mat[c * 3 + 2];
   }
   // per-cell contraction coefficients: -1/h_d, or -coef(d,v)/h_d for the rows of B_d, as
-  // (hi, lo) binary32 pairs and as FP64
+  // (hi, lo) binary32 pairs
   __shared__ float cf[2 * 3 * NV];
-  __shared__ double cfd[3 * NV];
   // tables indexed by a per-lane row (j_d, face side) staged in shared memory
   __shared__ float sDh[n * n], sDl[n * n], sWh[n * n], sWl[n * n], sE[4][n];
   for (int i = tid; i < n * n; i += TPB) {
@@ -376,7 +375,6 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
     const float h = (float)cd;
     cf[tid] = h;
     cf[3 * NV + tid] = (float)(cd - (double)h);
-    cfd[tid] = cd;
   }
   const bool has_src = (A.src.cell == c);
   double ric[n];
@@ -451,15 +449,14 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
   }
   __syncthreads();
 
-  // B0: strong form for the iterations (hi, lo); elastic: weak-form volume base (FP64).
+  // B0 = R(u^n) in float-float (hi, lo): flux divergence (conservative form) or the
+  // non-conservative product (elastic); the elastic volume term reuses it.
   float b0f[LPT], b0l[LPT];
-  double b0vol[LPT];
 #pragma unroll
   for (int k = 0; k < LPT; ++k) {
     const int l = tid + k * TPB;
     b0f[k] = 0.f;
     b0l[k] = 0.f;
-    b0vol[k] = 0.0;
     if (l < NL) {
       const int j = l / NV, v = l - (l / NV) * NV;
       ff aS = {0.f, 0.f};
@@ -483,18 +480,14 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
               const ff f = uff[(j0 + m * st) * NV + s];
               ff_mac(g, sDh[jd * n + m], sDl[jd * n + m], f.h, f.l);
             }
-            b0vol[k] = fma(cfd[d * NV + v], ff_to_d(g), b0vol[k]);
+            aS = ff_add(aS, ff_mul(ff_norm(g.h, g.l), {cf[d * NV + v], cf[3 * NV + d * NV + v]}));
           }
         }
       }
-      if constexpr (P::CONS) {  // -aS, renormalised, without a round trip through FP64
-        const ff b = ff_norm(aS.h, aS.l);
-        b0f[k] = -b.h;
-        b0l[k] = -b.l;
-      } else {
-        b0f[k] = (float)b0vol[k];
-        b0l[k] = (float)(b0vol[k] - (double)b0f[k]);
-      }
+      // B0 renormalised, without a round trip through FP64 (conservative form: -aS)
+      const ff b = ff_norm(aS.h, aS.l);
+      b0f[k] = P::CONS ? -b.h : b.h;
+      b0l[k] = P::CONS ? -b.l : b.l;
     }
   }
 
@@ -654,7 +647,7 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
           }
         }
       }
-      double vol = P::CONS ? ff_to_d(dvol) : b0vol[k] + ff_to_d(dvol);
+      double vol = ff_to_d(P::CONS ? dvol : ff_add({b0f[k], b0l[k]}, dvol));
       if (has_src && v >= 3) {
         double sbar = 0.0;
 #pragma unroll

@@ -533,6 +533,13 @@ __global__ void __launch_bounds__(256) k_corrector(const __grid_constant__ StepA
                                                    long long off1, long long off2) {
   using C = Cfg<P, D, N>;
   constexpr int n = C::n, NV = C::NV, NL = C::NL, NF = C::NF, NPHI = C::NPHI;
+  // dt e0 / (w h_d) and dt e1 / (w h_d) once per block (the row j_d differs between lanes)
+  __shared__ double sw[2][3][n];
+  if (threadIdx.x < 2 * D * n) {
+    const int k = threadIdx.x / (D * n), d = (threadIdx.x / n) % D, m = threadIdx.x % n;
+    sw[k][d][m] = A.dev->dt * (k ? A.cw1[d][m] : A.cw0[d][m]);
+  }
+  __syncthreads();
   const long long e = (long long)blockIdx.x * 256 + threadIdx.x;
   if (e >= A.g.ncells * NL) return;
   const unsigned c = (unsigned)(e / NL);
@@ -540,8 +547,7 @@ __global__ void __launch_bounds__(256) k_corrector(const __grid_constant__ StepA
   const int j = l / NV, v = l - (l / NV) * NV;
   const unsigned n0 = A.g.n[0], n1 = A.g.n[1];
   const unsigned i0 = c % n0, r0 = c / n0, i1 = r0 % n1, i2 = r0 / n1;
-  const double dt = A.dev->dt;
-  double acc = 0.0;
+  double un = A.u_next[e];
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     const int st = (d == 0 ? 1 : (d == 1 ? n : n * n));
@@ -557,10 +563,10 @@ __global__ void __launch_bounds__(256) k_corrector(const __grid_constant__ StepA
     const long long fl = id + (long long)(nd + 1) * tr;
     const double PhiL = A.phi[off + fr * (NPHI * NF * NV) + jp * NV + v];
     const double PhiR = A.phi[off + fl * (NPHI * NF * NV) + (NPHI - 1) * NF * NV + jp * NV + v];
-    acc = fma(A.cw1[d][jd], PhiL, acc);
-    acc = fma(-A.cw0[d][jd], PhiR, acc);
+    un = fma(-sw[1][d][jd], PhiL, un);
+    un = fma(sw[0][d][jd], PhiR, un);
   }
-  A.u_next[e] = fma(-dt, acc, A.u_next[e]);
+  A.u_next[e] = un;
 }
 
 // Max signal speed of the state (Eq. (7)); NaN / Inf latches ST_NONFINITE.  Euler: one FP64

@@ -59,10 +59,12 @@ typedef enum { ADER_PDE_ADVECTION = 0, ADER_PDE_EULER = 1, ADER_PDE_ELASTIC = 2 
  *              the interior state for Euler; the exterior material is the interior one. */
 typedef enum { ADER_BC_PERIODIC = 0, ADER_BC_WALL = 1, ADER_BC_ABSORBING = 2 } ader_bc;
 
-/* Arithmetic of the space-time predictor (the rest of the step is always FP64):
+/* Arithmetic of the step:
  *  FP64  - everything in binary64;
- *  MIXED - predictor iterations on the increment q - u^n in binary32 with FP64 base terms
- *          (see the precision notes of the library documentation). */
+ *  MIXED - predictor iterations on the increment q - u^n in binary32 with float-float base
+ *          terms, time averages and contractions; for Euler also binary32 Rusanov wave speeds
+ *          (from the predictor's face states) and a binary32 CFL signal speed enlarged by 2^-16.
+ *          Riemann flux combination, corrector and limiter stay binary64. */
 typedef enum { ADER_PREC_FP64 = 0, ADER_PREC_MIXED = 1 } ader_prec;
 
 typedef struct {
@@ -83,7 +85,9 @@ typedef struct {
 
 /* Create a context on the current CUDA device.  `cuda_stream` is a cudaStream_t (NULL = the
  * legacy default stream).  Allocates every device buffer the step needs (the state, the next
- * state, face data, face fluxes, limiter data).  *out is NULL on failure. */
+ * state, face data, face fluxes, limiter data).  *out is NULL on failure.  ADER_EUNSUPPORTED for
+ * combinations the kernels do not cover, among them a predictor whose cell does not fit the
+ * 227 KB of shared memory of a thread block (the 3-D Euler MIXED form at order 6). */
 ader_status ader_create(const ader_config* cfg, void* cuda_stream, ader_ctx** out);
 
 /* Release the context and its device buffers; NULL-safe.  Synchronises its stream. */

@@ -442,6 +442,9 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
   const Family* fam = pick_family(cfg->pde, cfg->dim);
   if (!fam) return ADER_EUNSUPPORTED;
   if (cfg->precision != ADER_PREC_FP64 && cfg->precision != ADER_PREC_MIXED) return ADER_EUNSUPPORTED;
+  // the predictor keeps a cell in shared memory: at most 227 KB per block on sm_103a, less the
+  // kernel's static tables (the 3-D Euler mixed form at order 6 does not fit)
+  if (fam->predictor_smem(cfg->order, cfg->precision) > 232448 - 4096) return ADER_EUNSUPPORTED;
   if (cfg->limiter < 0 || cfg->limiter > 2) return ADER_EINVAL;
   if (cfg->limiter) {
     if (cfg->pde != ADER_PDE_EULER) return ADER_EUNSUPPORTED;

@@ -204,3 +204,16 @@ def test_full_size_sampled_cells_euler_81():
         out = sub.step(torch.from_numpy(loc), torch.tensor(dt, dtype=torch.float64)).numpy()
         centre = i + 81 * (j + 81 * k)
         assert rel_linf(got[centre], out[13]) <= TOL, (i, j, k)
+
+
+def test_configurations_beyond_the_kernels_are_rejected_at_create():
+    """The 3-D Euler mixed predictor at order 6 needs more shared memory than a block has: the
+    context is refused up front instead of failing at the first step."""
+    cfg = ader.make_config("euler", 3, 6, (2, 2, 2), (0,) * 3, (1,) * 3, "periodic",
+                           synth.cfl_number(6), precision="mixed")
+    with pytest.raises(ader.AderError) as e:
+        ader.Context(cfg)
+    assert e.value.status == ader.EUNSUPPORTED
+    cfg = ader.make_config("euler", 3, 6, (2, 2, 2), (0,) * 3, (1,) * 3, "periodic",
+                           synth.cfl_number(6), precision="fp64")
+    ader.Context(cfg)  # the FP64 kernel fits

@@ -98,7 +98,9 @@ struct CfgM {
   static constexpr int NF = C::NF, FR = C::FR;
   static constexpr int LPT = (NL + TPB - 1) / TPB, NPT = (NST + TPB - 1) / TPB;
   static constexpr int NPS = (NS + TPB - 1) / TPB;
-  static constexpr int BW = EULER ? D + 1 : 1;               // v0[D], p0 (float-float)
+  // v0[D], p0 (float-float) per spatial node; rows padded to an odd number of float-float values
+  // so that the 8-byte loads of consecutive nodes fall on distinct banks
+  static constexpr int BW = EULER ? ((D + 1) % 2 ? D + 1 : D + 2) : 1;
   static constexpr size_t B_FB0 = P::CONS ? (size_t)D * NL * sizeof(ff) : 0;
   static constexpr size_t B_UFF = (size_t)NL * sizeof(ff);
   static constexpr size_t B_BF = EULER ? (size_t)NS * BW * sizeof(ff) : 0;
@@ -109,16 +111,16 @@ struct CfgM {
 
 template <int D>
 __device__ __forceinline__ EulerBase<D> load_base(const ff* uff, const ff* bff, int j) {
-  constexpr int NV = D + 2;
+  constexpr int NV = D + 2, BW = (D + 1) % 2 ? D + 1 : D + 2;  // row length of bff
   EulerBase<D> b;
   b.rho = uff[j * NV];
   b.E = uff[j * NV + NV - 1];
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     b.j[i] = uff[j * NV + 1 + i];
-    b.v[i] = bff[j * (D + 1) + i];
+    b.v[i] = bff[j * BW + i];
   }
-  b.p = bff[j * (D + 1) + D];
+  b.p = bff[j * BW + D];
   return b;
 }
 
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
   unsigned char* p = smem_raw;
   ff* FB0 = reinterpret_cast<ff*>(p);  p += M::B_FB0;    // [D][NL] F_d(u)/h_d
   ff* uff = reinterpret_cast<ff*>(p);  p += M::B_UFF;    // [NL] u
-  ff* bff = reinterpret_cast<ff*>(p);  p += M::B_BF;     // [NS][D+1] v0, p0 (Euler)
+  ff* bff = reinterpret_cast<ff*>(p);  p += M::B_BF;     // [NS][BW] v0, p0 (Euler)
   float* dqs = reinterpret_cast<float*>(p);  p += M::B_DQ;  // [n][NL] dq (binary32)
   // [D][n][NL] binary32: flux increments in the iterations, quadratic flux remainders in the
   // epilogue
@@ -420,8 +422,8 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
           }
           const ff pr = ff_mul(g1, ff_sub(q[NV - 1], ff_mulf(jv, 0.5f)));
 #pragma unroll
-          for (int i = 0; i < D; ++i) bff[j * (D + 1) + i] = vel[i];
-          bff[j * (D + 1) + D] = pr;
+          for (int i = 0; i < D; ++i) bff[j * M::BW + i] = vel[i];
+          bff[j * M::BW + D] = pr;
           const ff ep = ff_add(q[NV - 1], pr);
 #pragma unroll
           for (int d = 0; d < D; ++d) {

@@ -284,11 +284,12 @@ __device__ __forceinline__ void linear_nodes(const float* qbh, const float* qbl,
 }
 
 // R[k][t] += cf[d][v] * sum_m D[j_d][m] X[t][(j, j_d -> m)][src]  in binary32 (D as n x n rows
-// in shared memory: the row index differs between the lanes of a warp), with the per-cell
+// in shared memory, hi parts alone and as (hi, lo) pairs: the row index differs between the lanes
+// of a warp), with the per-cell
 // coefficients cf = {hi[3][NV], lo[3][NV]} in shared memory; with LO the lo parts of the
 // coefficient and of the float-float derivative matrix are added (no rounding of fixed tables).
 template <class M, int d, bool NCP, bool LO = false>
-__device__ __forceinline__ void contract_f(const float* X, const float* Dh, const float* Dl,
+__device__ __forceinline__ void contract_f(const float* X, const float* Dh, const float2* D2,
                                            const float* cf, float (&R)[M::LPT][M::n], int tid) {
   constexpr int n = M::n, NV = M::NV, NL = M::NL, TPB = M::TPB, st = ipow(n, d);
 #pragma unroll
@@ -310,8 +311,13 @@ __device__ __forceinline__ void contract_f(const float* X, const float* Dh, cons
 #pragma unroll
         for (int m = 0; m < n; ++m) {
           const float x = X[t * NL + (j0 + m * st) * NV + s];
-          acc = fmaf(Dh[jd * n + m], x, acc);
-          if constexpr (LO) lo = fmaf(Dl[jd * n + m], x, lo);
+          if constexpr (LO) {
+            const float2 dm = D2[jd * n + m];
+            acc = fmaf(dm.x, x, acc);
+            lo = fmaf(dm.y, x, lo);
+          } else {
+            acc = fmaf(Dh[jd * n + m], x, acc);
+          }
         }
         const float x = acc + lo;
         R[k][t] = fmaf(c, x, LO ? fmaf(clo, x, R[k][t]) : R[k][t]);
@@ -356,13 +362,14 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
   // (hi, lo) binary32 pairs
   __shared__ float cf[2 * 3 * NV];
   // tables indexed by a per-lane row (j_d, face side) staged in shared memory
-  __shared__ float sDh[n * n], sDl[n * n], sWh[n * n], sWl[n * n], sE[4][n];
+  // (hi, lo) pairs interleaved: one 8-byte load per entry in the float-float contractions
+  __shared__ float sDh[n * n], sE[4][n];
+  __shared__ float2 sD2[n * n], sW2[n * n];
   for (int i = tid; i < n * n; i += TPB) {
     const int a = i / n, b = i - (i / n) * n;
     sDh[i] = F.Dh[a][b];
-    sDl[i] = F.Dl[a][b];
-    sWh[i] = F.Wh[a][b];
-    sWl[i] = F.Wl[a][b];
+    sD2[i] = make_float2(F.Dh[a][b], F.Dl[a][b]);
+    sW2[i] = make_float2(F.Wh[a][b], F.Wl[a][b]);
   }
   if (tid < n) {
     sE[0][tid] = F.e0h[tid];
@@ -471,7 +478,8 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
 #pragma unroll
           for (int m = 0; m < n; ++m) {
             const ff f = FB0[d * NL + (j0 + m * st) * NV + v];
-            ff_mac(aS, sDh[jd * n + m], sDl[jd * n + m], f.h, f.l);
+            const float2 dm = sD2[jd * n + m];
+            ff_mac(aS, dm.x, dm.y, f.h, f.l);
           }
         } else {
           const int s = Elastic::src(d, v);
@@ -480,7 +488,8 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
 #pragma unroll
             for (int m = 0; m < n; ++m) {
               const ff f = uff[(j0 + m * st) * NV + s];
-              ff_mac(g, sDh[jd * n + m], sDl[jd * n + m], f.h, f.l);
+              const float2 dm = sD2[jd * n + m];
+              ff_mac(g, dm.x, dm.y, f.h, f.l);
             }
             aS = ff_add(aS, ff_mul(ff_norm(g.h, g.l), {cf[d * NV + v], cf[3 * NV + d * NV + v]}));
           }
@@ -510,23 +519,23 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
         dflux_nodes_all<M, P, D>(dqs, uff, bff, A.p, F.g1h, F.g1l, dF3, tid);
         __syncthreads();
         if (last) {
-          contract_f<M, 0, false, true>(dF3, sDh, sDl, cf, R, tid);
-          contract_f<M, 1, false, true>(dF3 + NSL, sDh, sDl, cf, R, tid);
-          if constexpr (D == 3) contract_f<M, 2, false, true>(dF3 + 2 * NSL, sDh, sDl, cf, R, tid);
+          contract_f<M, 0, false, true>(dF3, sDh, sD2, cf, R, tid);
+          contract_f<M, 1, false, true>(dF3 + NSL, sDh, sD2, cf, R, tid);
+          if constexpr (D == 3) contract_f<M, 2, false, true>(dF3 + 2 * NSL, sDh, sD2, cf, R, tid);
         } else {
-          contract_f<M, 0, false>(dF3, sDh, sDl, cf, R, tid);
-          contract_f<M, 1, false>(dF3 + NSL, sDh, sDl, cf, R, tid);
-          if constexpr (D == 3) contract_f<M, 2, false>(dF3 + 2 * NSL, sDh, sDl, cf, R, tid);
+          contract_f<M, 0, false>(dF3, sDh, sD2, cf, R, tid);
+          contract_f<M, 1, false>(dF3 + NSL, sDh, sD2, cf, R, tid);
+          if constexpr (D == 3) contract_f<M, 2, false>(dF3 + 2 * NSL, sDh, sD2, cf, R, tid);
         }
       } else {
         if (last) {
-          contract_f<M, 0, true, true>(dqs, sDh, sDl, cf, R, tid);
-          contract_f<M, 1, true, true>(dqs, sDh, sDl, cf, R, tid);
-          contract_f<M, 2, true, true>(dqs, sDh, sDl, cf, R, tid);
+          contract_f<M, 0, true, true>(dqs, sDh, sD2, cf, R, tid);
+          contract_f<M, 1, true, true>(dqs, sDh, sD2, cf, R, tid);
+          contract_f<M, 2, true, true>(dqs, sDh, sD2, cf, R, tid);
         } else {
-          contract_f<M, 0, true>(dqs, sDh, sDl, cf, R, tid);
-          contract_f<M, 1, true>(dqs, sDh, sDl, cf, R, tid);
-          contract_f<M, 2, true>(dqs, sDh, sDl, cf, R, tid);
+          contract_f<M, 0, true>(dqs, sDh, sD2, cf, R, tid);
+          contract_f<M, 1, true>(dqs, sDh, sD2, cf, R, tid);
+          contract_f<M, 2, true>(dqs, sDh, sD2, cf, R, tid);
         }
       }
     }
@@ -634,7 +643,8 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
 #pragma unroll
           for (int m = 0; m < n; ++m) {
             const ff g = FB0[d * NL + (j0 + m * st) * NV + v];
-            ff_mac(dvol, sWh[jd * n + m], sWl[jd * n + m], g.h, g.l);
+            const float2 wm = sW2[jd * n + m];
+            ff_mac(dvol, wm.x, wm.y, g.h, g.l);
           }
         } else {
           const int s = Elastic::src(d, v);
@@ -643,7 +653,8 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
 #pragma unroll
             for (int m = 0; m < n; ++m) {
               const int i = (j0 + m * st) * NV + s;
-              ff_mac(a, sDh[jd * n + m], sDl[jd * n + m], qbh[i], qbl[i]);
+              const float2 dm = sD2[jd * n + m];
+              ff_mac(a, dm.x, dm.y, qbh[i], qbl[i]);
             }
             dvol = ff_add(dvol, ff_mul(ff_norm(a.h, a.l), {cf[d * NV + v], cf[3 * NV + d * NV + v]}));
           }

@@ -25,7 +25,7 @@ struct DevScalars {
   double dt;                 // dt of the current / last step
   unsigned long long lam_bits;  // max signal speed of the state at t^n (bit pattern, >= 0)
   int status;                // latched error bits
-  int pad;
+  unsigned lam_lo_bits;      // mixed-form CFL: a lower bound of the max signal speed (binary32 bits)
   long long nstep;           // steps taken
   long long seismo_row;      // next seismogram row
   int n_troubled;            // troubled cells of the last step
@@ -112,11 +112,11 @@ struct StepArgs {
   double dt_fixed;     // > 0: fixed dt
   double t_end;        // > 0: clip
   double cfl;
-  // mixed form of the Euler step: binary32 wave speeds |v_d| + c of the face states
-  // [cell][dir][side][face node], written by the predictor and read by the Riemann solver (null:
-  // the Riemann solver computes FP64 speeds); cfl_f32: the CFL signal speed in binary32 with a
-  // relative margin of 2^-16 (0: FP64)
-  float* fspeed;
+  // mixed form of the Euler step: FP64 wave speeds |v_d| + c of the face states
+  // [cell][dir][side][face node], evaluated by the predictor and read by the Riemann solver (null:
+  // the Riemann solver evaluates them); cfl_f32: the CFL maximum through a binary32 filter with
+  // an error bound, FP64 evaluation of the candidates (0: FP64 evaluation of every node)
+  double* fspeed;
   int cfl_f32;
 };
 

@@ -325,7 +325,7 @@ struct ader_ctx {
   double* u_next = nullptr;
   double* face = nullptr;
   double* phi = nullptr;
-  float* fspeed = nullptr;  // mixed Euler: binary32 face wave speeds
+  double* fspeed = nullptr;  // mixed Euler: face wave speeds evaluated by the predictor
   double* mat = nullptr;
   DevScalars* dev = nullptr;
   bool state_set = false, mat_set = false;
@@ -505,7 +505,7 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->face, ncells * cfg->dim * 2 * face_rec * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->phi, nphi_total * sizeof(double));
   if (e == cudaSuccess && cfg->precision == ADER_PREC_MIXED && cfg->pde == ADER_PDE_EULER)
-    e = cudaMalloc(&c->fspeed, ncells * cfg->dim * 2 * c->nf * sizeof(float));
+    e = cudaMalloc(&c->fspeed, ncells * cfg->dim * 2 * c->nf * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->dev, sizeof(DevScalars));
   if (e == cudaSuccess && cfg->pde == ADER_PDE_ELASTIC) e = cudaMalloc(&c->mat, ncells * 3 * sizeof(double));
   if (cfg->limiter) {
@@ -782,7 +782,7 @@ static ader_status mark(ader_ctx* c, int k) {
 
 static ader_status step_impl(ader_ctx* c, double dt, double t_end) {
   StepArgs a = make_args(c, dt, t_end);
-  if (c->fspeed) {  // mixed Euler step: binary32 wave speeds (predictor -> Riemann, CFL)
+  if (c->fspeed) {  // mixed Euler step: face speeds from the predictor, filtered CFL maximum
     a.fspeed = c->fspeed;
     a.cfl_f32 = 1;
   }

@@ -24,6 +24,7 @@ __global__ void k_dt_finalize(const __grid_constant__ StepArgs A) {
   }
   s->dt = dt;
   s->lam_bits = 0ull;
+  s->lam_lo_bits = 0u;
   s->n_troubled = 0;
 }
 

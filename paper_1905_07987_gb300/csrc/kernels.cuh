@@ -458,15 +458,15 @@ __global__ void __launch_bounds__(128) k_riemann(const __grid_constant__ StepArg
     }
   }
   if constexpr (P::CONS && !P::LINEAR) {
-    if (A.fspeed) {  // mixed form: binary32 speeds of the face states from the predictor
-      const float* sl = cL >= 0 ? A.fspeed + (cL * D + d) * (2 * NF) + NF : nullptr;
-      const float* sr = cR >= 0 ? A.fspeed + (cR * D + d) * (2 * NF) : nullptr;
+    if (A.fspeed) {  // mixed form: FP64 speeds of the face states, evaluated by the predictor
+      const double* sl = cL >= 0 ? A.fspeed + (cL * D + d) * (2 * NF) + NF : nullptr;
+      const double* sr = cR >= 0 ? A.fspeed + (cR * D + d) * (2 * NF) : nullptr;
 #pragma unroll
       for (int r = 0; r < PER; ++r) {
         const int jp = lane + 32 * r;
         if (jp < NF) {  // a boundary side has the speed of its interior mirror / copy
-          const float a = sl ? sl[jp] : sr[jp], b = sr ? sr[jp] : sl[jp];
-          smax = fmax(smax, (double)fmaxf(a, b));
+          const double a = sl ? sl[jp] : sr[jp], b = sr ? sr[jp] : sl[jp];
+          smax = fmax(smax, fmax(a, b));
         }
       }
     } else {
@@ -599,31 +599,82 @@ __global__ void __launch_bounds__(256) k_cfl(const __grid_constant__ StepArgs A)
       lmax = fmax(lmax, s);
     }
   } else if (A.cfl_f32) {
-    // mixed form: max_d |v_d| + c in binary32 from the rounded state, enlarged by 2^-16 (the
-    // binary32 speed is within a few 1e-7 of the FP64 one unless p cancels badly); finiteness
-    // read from the exponent bits
+    // Mixed form: the same FP64 maximum, evaluated in FP64 only where it can occur.  Each node
+    // gets a binary32 enclosure [lo, hi] of its speed (rounding of the state to binary32 and of
+    // every operation bounded, with a factor-4 margin); a device-wide running lower bound of the
+    // maximum (the largest lo seen) rules out nodes with hi below it.  The remaining candidates
+    // of a tile are queued in shared memory and evaluated by speed_all in FP64 by the first lanes.
+    // Non-finite or non-admissible states are always candidates.
+    __shared__ int qn;
+    __shared__ long long qidx[256];
+    __shared__ float tlo[8];
     const float gam = (float)A.p.gamma, g1 = (float)(A.p.gamma - 1.0);
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.g.ncells * NS;
-         i += (long long)gridDim.x * blockDim.x) {
-      const double* q = A.u + i * NV;
-      float f[NV];
-      bool fin = true;
+    const float ep = 4.0f * 0x1p-24f;  // four units of binary32 rounding
+    const long long total = A.g.ncells * NS;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < total;
+         base += (long long)gridDim.x * blockDim.x) {
+      if (threadIdx.x == 0) qn = 0;
+      const long long i = base + threadIdx.x;
+      bool cand = false;
+      float lo = 0.f, hi = 0.f;
+      if (i < total) {
+        const double* q = A.u + i * NV;
+        float f[NV];
+        bool ok = true;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        fin = fin && ((__double2hiint(q[v]) & 0x7ff00000) != 0x7ff00000);
-        f[v] = __double2float_rn(q[v]);
-      }
-      const float ir = __fdividef(1.0f, f[0]);
-      float j2 = 0.f, vm = 0.f;
+        for (int v = 0; v < NV; ++v) {
+          ok = ok && ((__double2hiint(q[v]) & 0x7ff00000) != 0x7ff00000);
+          f[v] = __double2float_rn(q[v]);
+        }
+        ok = ok && (f[0] > 0.f);
+        const float ir = __frcp_rn(f[0]);
+        float j2 = 0.f, vm = 0.f;
 #pragma unroll
-      for (int d = 0; d < D; ++d) {
-        j2 = fmaf(f[1 + d], f[1 + d], j2);
-        vm = fmaxf(vm, fabsf(f[1 + d]));
+        for (int d = 0; d < D; ++d) {
+          j2 = fmaf(f[1 + d], f[1 + d], j2);
+          vm = fmaxf(vm, fabsf(f[1 + d]));
+        }
+        const float ke = 0.5f * j2 * ir;
+        const float ei = fmaf(-0.5f * j2, ir, f[NV - 1]);
+        const float dei = 3.0f * ep * (fabsf(f[NV - 1]) + ke) + ep * fabsf(ei);
+        const float p = g1 * ei;
+        const float dp = g1 * dei + 2.0f * ep * fabsf(p);
+        const float c2 = gam * p * ir;
+        const float dc2 = gam * ir * dp + 2.0f * ep * fabsf(c2);
+        const float vs = vm * ir;
+        const float clo = sqrtf(fmaxf(c2 - dc2, 0.f)) * (1.0f - ep);
+        const float chi = sqrtf(fmaxf(c2 + dc2, 0.f)) * (1.0f + ep);
+        lo = (vs * (1.0f - 2.0f * ep) + clo) * (1.0f - ep);
+        hi = (vs * (1.0f + 2.0f * ep) + chi) * (1.0f + ep);
+        ok = ok && (lo >= 0.f) && (hi < INFINITY);  // false also for NaN
+        if (!ok) lo = 0.f;
+        cand = !ok;
       }
-      const float c2 = gam * (g1 * fmaf(-0.5f * j2, ir, f[NV - 1])) * ir;
-      const float s = (vm * fabsf(ir) + (c2 > 0.f ? sqrtf(c2) : 0.f)) * (1.0f + 0x1p-16f);
-      if (!fin || !(s >= 0.f) || isinf(s)) bad = true;
-      else lmax = fmax(lmax, (double)s);
+      // raise the device-wide lower bound when this tile's largest lo exceeds it
+      float wlo = lo;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) wlo = fmaxf(wlo, __shfl_xor_sync(0xffffffffu, wlo, o));
+      if ((threadIdx.x & 31) == 0) tlo[threadIdx.x >> 5] = wlo;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        float m = tlo[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, tlo[w]);
+        if (m > __uint_as_float(*(volatile unsigned*)&A.dev->lam_lo_bits))
+          atomicMax(&A.dev->lam_lo_bits, __float_as_uint(m));  // non-negative: bits are monotone
+      }
+      const float thr = __uint_as_float(*(volatile unsigned*)&A.dev->lam_lo_bits);
+      if (i < total && (cand || !(hi < thr))) qidx[atomicAdd(&qn, 1)] = i;
+      __syncthreads();
+      for (int k = threadIdx.x; k < qn; k += blockDim.x) {
+        const double* q = A.u + qidx[k] * NV;
+        double sum = 0.0;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sum += q[v];
+        const double sp = P::speed_all(q, A.p);
+        if (!isfinite(sum) || !(sp >= 0.0) || isinf(sp)) bad = true;
+        else lmax = fmax(lmax, sp);
+      }
+      __syncthreads();
     }
   } else {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.g.ncells * NS;

@@ -104,7 +104,8 @@ struct CfgM {
   static constexpr size_t B_FB0 = P::CONS ? (size_t)D * NL * sizeof(ff) : 0;
   static constexpr size_t B_UFF = (size_t)NL * sizeof(ff);
   static constexpr size_t B_BF = EULER ? (size_t)NS * BW * sizeof(ff) : 0;
-  static constexpr size_t B_DQ = (size_t)n * NL * sizeof(float);
+  // rounded up to 16 bytes: the region behind it is also read as doubles
+  static constexpr size_t B_DQ = ((size_t)n * NL * sizeof(float) + 15) / 16 * 16;
   static constexpr size_t B_F3 = P::CONS ? (size_t)D * n * NL * sizeof(float) : 0;
   static constexpr size_t SMEM = B_FB0 + B_UFF + B_BF + B_DQ + B_F3;
 };
@@ -698,34 +699,27 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
     }
     double* rec0 = fc + (d * 2) * FR;
     double* rec1 = rec0 + FR;
-    rec0[jp * NV + v] = ff_to_d(qa0);
-    rec1[jp * NV + v] = ff_to_d(qa1);
+    const double q0 = ff_to_d(qa0), q1 = ff_to_d(qa1);
+    rec0[jp * NV + v] = q0;
+    rec1[jp * NV + v] = q1;
     if constexpr (P::CONS) {
       rec0[NF * NV + jp * NV + v] = ff_to_d(fa0) * A.g.h[d];
       rec1[NF * NV + jp * NV + v] = ff_to_d(fa1) * A.g.h[d];
     }
-    if constexpr (M::EULER) {  // face states (hi parts) for the wave speeds below
-      dF3[((d * 2) * NF + jp) * NV + v] = qa0.h;
-      dF3[((d * 2 + 1) * NF + jp) * NV + v] = qa1.h;
+    if constexpr (M::EULER) {  // the face states as written, for the wave speeds below
+      double* qs = reinterpret_cast<double*>(dF3);
+      qs[((d * 2) * NF + jp) * NV + v] = q0;
+      qs[((d * 2 + 1) * NF + jp) * NV + v] = q1;
     }
   }
   if constexpr (M::EULER) {
-    // binary32 Rusanov wave speeds |v_d| + c of every face state, for the Riemann solver
-    // (c^2 < 0 counts as c = 0, as in the FP64 speeds)
+    // FP64 Rusanov wave speeds |v_d| + c of every face state (the same evaluation as the Riemann
+    // solver's on the same face records), for the Riemann solver
     if (A.fspeed) {
       __syncthreads();
-      const float g1 = F.g1h, gam = F.g1h + 1.0f;
-      float* fs = A.fspeed + c * (long long)(D * 2 * NF);
-      for (int e = tid; e < D * 2 * NF; e += TPB) {
-        const int d = e / (2 * NF);
-        const float* q = dF3 + e * NV;
-        const float ir = __fdividef(1.0f, q[0]);
-        float j2 = 0.f;
-#pragma unroll
-        for (int i = 0; i < D; ++i) j2 = fmaf(q[1 + i], q[1 + i], j2);
-        const float c2 = gam * (g1 * fmaf(-0.5f * j2, ir, q[NV - 1])) * ir;
-        fs[e] = fabsf(q[1 + d] * ir) + (c2 > 0.f ? sqrtf(c2) : 0.f);
-      }
+      const double* qs = reinterpret_cast<const double*>(dF3);
+      double* fs = A.fspeed + c * (long long)(D * 2 * NF);
+      for (int e = tid; e < D * 2 * NF; e += TPB) fs[e] = P::speed(qs + e * NV, A.p, e / (2 * NF));
     }
   }
 }

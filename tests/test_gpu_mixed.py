@@ -136,3 +136,22 @@ def test_uniform_flow_is_preserved(prec):
     for _ in range(3):
         c.ctx.step()
     assert rel_linf(c.get(), u0) < 1e-13
+
+
+@pytest.mark.parametrize("case", ["entropy_wave", "explosion"])
+def test_mixed_cfl_dt_equals_fp64(case):
+    """The mixed form evaluates the CFL eigenvalue maximum in FP64 (its binary32 enclosures only
+    decide which nodes need it), so on the same state its dt is the FP64 form's, bit for bit; the
+    explosion's piecewise-constant regions make most nodes candidates of the filter."""
+    dts = {}
+    for prec in ("fp64", "mixed"):
+        if case == "entropy_wave":
+            c = Case("euler", 3, 4, (6, 5, 4), precision=prec)
+            u0 = synth.entropy_wave(c.X)
+        else:
+            c = Case("euler", 3, 3, (8, 8, 8), lo=(-1,) * 3, hi=(1,) * 3, bc="wall", precision=prec)
+            u0 = synth.explosion(c.X)
+        c.set(u0)
+        c.ctx.step()
+        dts[prec] = c.ctx.last_dt()
+    assert dts["mixed"] == dts["fp64"], dts

@@ -62,9 +62,10 @@ typedef enum { ADER_BC_PERIODIC = 0, ADER_BC_WALL = 1, ADER_BC_ABSORBING = 2 } a
 /* Arithmetic of the step:
  *  FP64  - everything in binary64;
  *  MIXED - predictor iterations on the increment q - u^n in binary32 with float-float base
- *          terms, time averages and contractions; for Euler also binary32 Rusanov wave speeds
- *          (from the predictor's face states) and a binary32 CFL signal speed enlarged by 2^-16.
- *          Riemann flux combination, corrector and limiter stay binary64. */
+ *          terms, time averages and contractions.  Pressure / sound speed and eigenvalues, the
+ *          Riemann flux, the corrector and the limiter stay binary64 (for Euler the face wave
+ *          speeds are evaluated by the predictor, and the CFL maximum only on the nodes that a
+ *          binary32 enclosure cannot rule out; dt equals the FP64 form's on the same state). */
 typedef enum { ADER_PREC_FP64 = 0, ADER_PREC_MIXED = 1 } ader_prec;
 
 typedef struct {

@@ -155,3 +155,21 @@ def test_mixed_cfl_dt_equals_fp64(case):
         c.ctx.step()
         dts[prec] = c.ctx.last_dt()
     assert dts["mixed"] == dts["fp64"], dts
+
+
+def test_mixed_nonfinite_state_is_reported():
+    """A NaN in the state reaches the filtered CFL kernel as a candidate and is latched as
+    ENONFINITE, as in the FP64 form; a clean state afterwards steps normally."""
+    from paper_1905_07987_gb300 import ader
+    c = Case("euler", 3, 3, (4, 3, 4), precision="mixed")
+    u0 = synth.entropy_wave(c.X)
+    bad = u0.copy()
+    bad[5, 1, 2, 0, 4] = np.nan
+    c.set(bad)
+    c.ctx.step()
+    with pytest.raises(ader.AderError) as e:
+        c.ctx.sync()
+    assert e.value.status == ader.ENONFINITE
+    c.set(u0)
+    c.ctx.step()
+    c.ctx.sync()

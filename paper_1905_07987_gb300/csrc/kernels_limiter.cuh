@@ -3,8 +3,9 @@
 // Per step, after the unlimited ADER-DG step has written the candidate u* to u_next:
 //   k_lim_detect  one block per cell: subcell averages P(u*), relaxed DMP against the min/max of
 //                 the t^n representations of the cell and its face neighbours, positivity of
-//                 density and pressure at nodes and subcells; troubled cells are compacted into a
-//                 list with one atomic per flagged block.
+//                 density and pressure at nodes and subcells; writes the flags.
+//   k_lim_compact one thread per cell: troubled cells compacted into the list by warp ballot (one
+//                 atomic per warp, lanes at their prefix count).
 //   k_lim_fv      persistent blocks over the troubled list: MUSCL-Hancock (minmod) + Rusanov on
 //                 the (2N+1)^d subcells with a 2-subcell halo from the t^n representations of all
 //                 neighbours, u_next = R(U_sub), the boundary subface fluxes saved per cell.
@@ -233,13 +234,21 @@ __global__ void __launch_bounds__(128) k_lim_detect(const __grid_constant__ Step
   double* rn = L.rep_new + c * (NSS * NV);
   for (int e = threadIdx.x; e < NSS * NV; e += blockDim.x) rn[e] = sub[e];
   block_minmax<NSS, NV>(sub, L.mm_new + c * 2 * NV, red);
-  if (threadIdx.x == 0) {
-    L.flags[c] = troubled ? 1 : 0;
-    if (troubled) {
-      const int k = atomicAdd(&A.dev->n_troubled, 1);
-      L.list[k] = (int)c;
-    }
-  }
+  if (threadIdx.x == 0) L.flags[c] = troubled ? 1 : 0;
+}
+
+// Troubled list by warp ballot: every lane votes with its cell's flag, lane 0 reserves the warp's
+// slots with one atomic, each flagged lane writes its cell at base + (flagged lanes below it).
+static __global__ void __launch_bounds__(256) k_lim_compact(const uint8_t* __restrict__ flags, int* list,
+                                                     int* count, long long ncells) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool t = i < ncells && flags[i] != 0;
+  const unsigned m = __ballot_sync(0xffffffffu, t);
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == 0 && m != 0u) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (t) list[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
 }
 
 // Halo value of subcell (hx, hy, hz) in [-2, ns+2)^D of cell c from the t^n representations,
@@ -655,6 +664,10 @@ struct LimLaunch {
     const unsigned nc = (unsigned)a.g.ncells;
     k_lim_detect<D, N><<<nc, C::TPB, C::SMEM_P, s>>>(a, l, S);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_lim_compact<<<(unsigned)((a.g.ncells + 255) / 256), 256, 0, s>>>(l.flags, l.list,
+                                                                         &a.dev->n_troubled, a.g.ncells);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_lim_fv<D, N><<<152 * 2, FV_TPB, C::SMEM_FV, s>>>(a, l, S);
     e = cudaGetLastError();

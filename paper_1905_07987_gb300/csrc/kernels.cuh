@@ -1,7 +1,9 @@
 // FP64 kernels of one ADER-DG step (Sec. 3.3-3.4), templated on the PDE system, the dimension
 // and the order.  One thread block per cell for the predictor (the work is FP64-pipe bound on
 // GB300: every cell is an independent dense small contraction problem), one warp per face for
-// the Riemann solver, one thread per degree of freedom for the corrector.
+// the Riemann solver, one thread per degree of freedom for the corrector, grid-stride tiles for
+// the CFL maximum.  The Riemann solver and the CFL kernel also serve the mixed-precision form
+// (wave speeds evaluated by its predictor; the CFL maximum through a binary32 filter).
 #pragma once
 #include <cstdio>
 #include "ader_internal.h"
@@ -412,7 +414,8 @@ __device__ __forceinline__ void ghost(int kind, int d, double* q, double* F) {
 
 // Rusanov flux with one wave speed per face (max over face nodes and both sides) and the halved
 // path-conservative fluctuation:  Phi_L = G + Bbar dq / 2,  Phi_R = G - Bbar dq / 2.
-// One warp per face; faces of direction d, offset `phi_off` in the flux buffer.
+// One warp per face (warp-shuffle maximum of the speeds); faces of direction d, offset `phi_off`
+// in the flux buffer.  With A.fspeed the FP64 speeds of the face states come from the predictor.
 template <class P, int D, int N>
 __global__ void __launch_bounds__(128) k_riemann(const __grid_constant__ StepArgs A,
                                                  const __grid_constant__ Tables T, int d,
@@ -570,7 +573,8 @@ __global__ void __launch_bounds__(256) k_corrector(const __grid_constant__ StepA
 }
 
 // Max signal speed of the state (Eq. (7)); NaN / Inf latches ST_NONFINITE.  Euler: one FP64
-// division and one square root per node for all directions.
+// division and one square root per node for all directions (mixed form: only on the nodes that
+// the binary32 enclosures cannot rule out).
 template <class P, int D, int N>
 __global__ void __launch_bounds__(256) k_cfl(const __grid_constant__ StepArgs A) {
   using C = Cfg<P, D, N>;

@@ -609,53 +609,61 @@ __global__ void __launch_bounds__(256) k_cfl(const __grid_constant__ StepArgs A)
     // maximum (the largest lo seen) rules out nodes with hi below it.  The remaining candidates
     // of a tile are queued in shared memory and evaluated by speed_all in FP64 by the first lanes.
     // Non-finite or non-admissible states are always candidates.
+    constexpr int TPN = 4;  // nodes per thread and tile
     __shared__ int qn;
-    __shared__ long long qidx[256];
+    __shared__ long long qidx[256 * TPN];
     __shared__ float tlo[8];
     const float gam = (float)A.p.gamma, g1 = (float)(A.p.gamma - 1.0);
     const float ep = 4.0f * 0x1p-24f;  // four units of binary32 rounding
     const long long total = A.g.ncells * NS;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < total;
-         base += (long long)gridDim.x * blockDim.x) {
+    const long long tile = (long long)blockDim.x * TPN;
+    for (long long base = (long long)blockIdx.x * tile; base < total; base += (long long)gridDim.x * tile) {
       if (threadIdx.x == 0) qn = 0;
-      const long long i = base + threadIdx.x;
-      bool cand = false;
-      float lo = 0.f, hi = 0.f;
-      if (i < total) {
-        const double* q = A.u + i * NV;
-        float f[NV];
-        bool ok = true;
+      float lo[TPN], hi[TPN];
+      bool cand[TPN];
+      float wlo = 0.f;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          ok = ok && ((__double2hiint(q[v]) & 0x7ff00000) != 0x7ff00000);
-          f[v] = __double2float_rn(q[v]);
-        }
-        ok = ok && (f[0] > 0.f);
-        const float ir = __frcp_rn(f[0]);
-        float j2 = 0.f, vm = 0.f;
+      for (int r = 0; r < TPN; ++r) {
+        const long long i = base + r * (long long)blockDim.x + threadIdx.x;
+        cand[r] = false;
+        lo[r] = hi[r] = 0.f;
+        if (i < total) {
+          const double* q = A.u + i * NV;
+          float f[NV];
+          bool ok = true;
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-          j2 = fmaf(f[1 + d], f[1 + d], j2);
-          vm = fmaxf(vm, fabsf(f[1 + d]));
+          for (int v = 0; v < NV; ++v) {
+            ok = ok && ((__double2hiint(q[v]) & 0x7ff00000) != 0x7ff00000);
+            f[v] = __double2float_rn(q[v]);
+          }
+          ok = ok && (f[0] > 0.f);
+          const float ir = __frcp_rn(f[0]);
+          float j2 = 0.f, vm = 0.f;
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            j2 = fmaf(f[1 + d], f[1 + d], j2);
+            vm = fmaxf(vm, fabsf(f[1 + d]));
+          }
+          const float ke = 0.5f * j2 * ir;
+          const float ei = fmaf(-0.5f * j2, ir, f[NV - 1]);
+          const float dei = 3.0f * ep * (fabsf(f[NV - 1]) + ke) + ep * fabsf(ei);
+          const float p = g1 * ei;
+          const float dp = g1 * dei + 2.0f * ep * fabsf(p);
+          const float c2 = gam * p * ir;
+          const float dc2 = gam * ir * dp + 2.0f * ep * fabsf(c2);
+          const float vs = vm * ir;
+          const float clo = sqrtf(fmaxf(c2 - dc2, 0.f)) * (1.0f - ep);
+          const float chi = sqrtf(fmaxf(c2 + dc2, 0.f)) * (1.0f + ep);
+          float l = (vs * (1.0f - 2.0f * ep) + clo) * (1.0f - ep);
+          hi[r] = (vs * (1.0f + 2.0f * ep) + chi) * (1.0f + ep);
+          ok = ok && (l >= 0.f) && (hi[r] < INFINITY);  // false also for NaN
+          if (!ok) l = 0.f;
+          lo[r] = l;
+          cand[r] = !ok;
+          wlo = fmaxf(wlo, l);
         }
-        const float ke = 0.5f * j2 * ir;
-        const float ei = fmaf(-0.5f * j2, ir, f[NV - 1]);
-        const float dei = 3.0f * ep * (fabsf(f[NV - 1]) + ke) + ep * fabsf(ei);
-        const float p = g1 * ei;
-        const float dp = g1 * dei + 2.0f * ep * fabsf(p);
-        const float c2 = gam * p * ir;
-        const float dc2 = gam * ir * dp + 2.0f * ep * fabsf(c2);
-        const float vs = vm * ir;
-        const float clo = sqrtf(fmaxf(c2 - dc2, 0.f)) * (1.0f - ep);
-        const float chi = sqrtf(fmaxf(c2 + dc2, 0.f)) * (1.0f + ep);
-        lo = (vs * (1.0f - 2.0f * ep) + clo) * (1.0f - ep);
-        hi = (vs * (1.0f + 2.0f * ep) + chi) * (1.0f + ep);
-        ok = ok && (lo >= 0.f) && (hi < INFINITY);  // false also for NaN
-        if (!ok) lo = 0.f;
-        cand = !ok;
       }
       // raise the device-wide lower bound when this tile's largest lo exceeds it
-      float wlo = lo;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) wlo = fmaxf(wlo, __shfl_xor_sync(0xffffffffu, wlo, o));
       if ((threadIdx.x & 31) == 0) tlo[threadIdx.x >> 5] = wlo;
@@ -667,7 +675,11 @@ __global__ void __launch_bounds__(256) k_cfl(const __grid_constant__ StepArgs A)
           atomicMax(&A.dev->lam_lo_bits, __float_as_uint(m));  // non-negative: bits are monotone
       }
       const float thr = __uint_as_float(*(volatile unsigned*)&A.dev->lam_lo_bits);
-      if (i < total && (cand || !(hi < thr))) qidx[atomicAdd(&qn, 1)] = i;
+#pragma unroll
+      for (int r = 0; r < TPN; ++r) {
+        const long long i = base + r * (long long)blockDim.x + threadIdx.x;
+        if (i < total && (cand[r] || !(hi[r] < thr))) qidx[atomicAdd(&qn, 1)] = i;
+      }
       __syncthreads();
       for (int k = threadIdx.x; k < qn; k += blockDim.x) {
         const double* q = A.u + qidx[k] * NV;

@@ -114,10 +114,11 @@ struct StepArgs {
   double cfl;
   // mixed form of the Euler step: FP64 wave speeds |v_d| + c of the face states
   // [cell][dir][side][face node], evaluated by the predictor and read by the Riemann solver (null:
-  // the Riemann solver evaluates them); cfl_f32: the CFL maximum through a binary32 filter with
-  // an error bound, FP64 evaluation of the candidates (0: FP64 evaluation of every node)
+  // the Riemann solver evaluates them)
   double* fspeed;
-  int cfl_f32;
+  // Euler: the CFL maximum through a binary32 filter with an error bound and FP64 evaluation of
+  // the candidates (the same maximum as evaluating every node in FP64); 0: every node
+  int cfl_filter;
 };
 
 // Per (pde, dim) kernel family; order dispatch happens inside.

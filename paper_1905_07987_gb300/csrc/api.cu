@@ -782,10 +782,8 @@ static ader_status mark(ader_ctx* c, int k) {
 
 static ader_status step_impl(ader_ctx* c, double dt, double t_end) {
   StepArgs a = make_args(c, dt, t_end);
-  if (c->fspeed) {  // mixed Euler step: face speeds from the predictor, filtered CFL maximum
-    a.fspeed = c->fspeed;
-    a.cfl_f32 = 1;
-  }
+  a.fspeed = c->fspeed;  // mixed Euler step: face speeds evaluated by the predictor
+  a.cfl_filter = c->cfg.pde == ADER_PDE_EULER ? 1 : 0;
   cudaStream_t s = c->stream;
   ader_status st;
   if ((st = mark(c, 0)) != ADER_OK) return st;

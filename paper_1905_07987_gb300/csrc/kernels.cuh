@@ -2,8 +2,9 @@
 // and the order.  One thread block per cell for the predictor (the work is FP64-pipe bound on
 // GB300: every cell is an independent dense small contraction problem), one warp per face for
 // the Riemann solver, one thread per degree of freedom for the corrector, grid-stride tiles for
-// the CFL maximum.  The Riemann solver and the CFL kernel also serve the mixed-precision form
-// (wave speeds evaluated by its predictor; the CFL maximum through a binary32 filter).
+// the CFL maximum (Euler: FP64 evaluation only on the nodes that binary32 enclosures cannot rule
+// out).  The Riemann solver also serves the mixed-precision form (wave speeds evaluated by its
+// predictor).
 #pragma once
 #include <cstdio>
 #include "ader_internal.h"
@@ -573,8 +574,8 @@ __global__ void __launch_bounds__(256) k_corrector(const __grid_constant__ StepA
 }
 
 // Max signal speed of the state (Eq. (7)); NaN / Inf latches ST_NONFINITE.  Euler: one FP64
-// division and one square root per node for all directions (mixed form: only on the nodes that
-// the binary32 enclosures cannot rule out).
+// division and one square root per node for all directions, on the nodes that the binary32
+// enclosures cannot rule out.
 template <class P, int D, int N>
 __global__ void __launch_bounds__(256) k_cfl(const __grid_constant__ StepArgs A) {
   using C = Cfg<P, D, N>;
@@ -602,8 +603,8 @@ __global__ void __launch_bounds__(256) k_cfl(const __grid_constant__ StepArgs A)
       if (!isfinite(q[0])) bad = true;
       lmax = fmax(lmax, s);
     }
-  } else if (A.cfl_f32) {
-    // Mixed form: the same FP64 maximum, evaluated in FP64 only where it can occur.  Each node
+  } else if (A.cfl_filter) {
+    // The FP64 maximum, evaluated in FP64 only where it can occur.  Each node
     // gets a binary32 enclosure [lo, hi] of its speed (rounding of the state to binary32 and of
     // every operation bounded, with a factor-4 margin); a device-wide running lower bound of the
     // maximum (the largest lo seen) rules out nodes with hi below it.  The remaining candidates

@@ -217,3 +217,29 @@ def test_configurations_beyond_the_kernels_are_rejected_at_create():
     cfg = ader.make_config("euler", 3, 6, (2, 2, 2), (0,) * 3, (1,) * 3, "periodic",
                            synth.cfl_number(6), precision="fp64")
     ader.Context(cfg)  # the FP64 kernel fits
+
+
+@pytest.mark.parametrize("state", ["entropy_wave", "explosion", "uniform", "spike"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cfl_dt_matches_the_oracle(state, prec):
+    """The CFL kernel evaluates speeds in FP64 only where binary32 enclosures cannot rule a node
+    out; its dt must equal the oracle's FP64 maximum over every node (to FP64 rounding of the
+    speed formula): smooth data, piecewise-constant data, a uniform state where every node ties,
+    and a single node far faster than the rest."""
+    c = Case("euler", 3, 3, (6, 5, 4), lo=(-1,) * 3, hi=(1,) * 3, bc="wall", precision=prec)
+    if state == "entropy_wave":
+        u0 = synth.entropy_wave(c.X)
+    elif state == "explosion":
+        u0 = synth.explosion(c.X)
+    else:
+        u0 = synth.euler_conserved(np.full_like(c.X[0], 1.1), [np.full_like(c.X[0], 0.3), 0.2, -0.1],
+                                   np.full_like(c.X[0], 0.9))
+        if state == "spike":
+            u0 = u0.copy()
+            u0[37, 2, 1, 3] = synth.euler_conserved(np.array(0.9), [np.array(4.0), 0.0, 0.0],
+                                                    np.array(3.0))
+    c.set(u0)
+    c.ctx.step()
+    dt = c.ctx.last_dt()
+    ref = float(c.oracle.cfl_dt(torch.from_numpy(u0)))
+    assert abs(dt - ref) <= 2e-15 * ref, (dt, ref)

@@ -146,10 +146,11 @@ def test_mixed_cfl_dt_equals_fp64(case):
     dts = {}
     for prec in ("fp64", "mixed"):
         if case == "entropy_wave":
-            c = Case("euler", 3, 4, (6, 5, 4), precision=prec)
+            c = Case("euler", 3, 4, (14, 13, 12), precision=prec)
             u0 = synth.entropy_wave(c.X)
         else:
-            c = Case("euler", 3, 3, (8, 8, 8), lo=(-1,) * 3, hi=(1,) * 3, bc="wall", precision=prec)
+            c = Case("euler", 3, 3, (17, 16, 16), lo=(-1,) * 3, hi=(1,) * 3, bc="wall",
+                     precision=prec)
             u0 = synth.explosion(c.X)
         c.set(u0)
         c.ctx.step()

@@ -222,11 +222,12 @@ def test_configurations_beyond_the_kernels_are_rejected_at_create():
 @pytest.mark.parametrize("state", ["entropy_wave", "explosion", "uniform", "spike"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_cfl_dt_matches_the_oracle(state, prec):
-    """The CFL kernel evaluates speeds in FP64 only where binary32 enclosures cannot rule a node
-    out; its dt must equal the oracle's FP64 maximum over every node (to FP64 rounding of the
-    speed formula): smooth data, piecewise-constant data, a uniform state where every node ties,
-    and a single node far faster than the rest."""
-    c = Case("euler", 3, 3, (6, 5, 4), lo=(-1,) * 3, hi=(1,) * 3, bc="wall", precision=prec)
+    """On grids of 2^18 nodes and more the CFL kernel evaluates speeds in FP64 only where binary32
+    enclosures cannot rule a node out; its dt must equal the oracle's FP64 maximum over every node
+    (to FP64 rounding of the speed formula): smooth data, piecewise-constant data, a uniform state
+    where every node ties, and a single node far faster than the rest (17 x 16 x 16 cells of
+    order 3: 278 528 nodes)."""
+    c = Case("euler", 3, 3, (17, 16, 16), lo=(-1,) * 3, hi=(1,) * 3, bc="wall", precision=prec)
     if state == "entropy_wave":
         u0 = synth.entropy_wave(c.X)
     elif state == "explosion":
@@ -236,7 +237,7 @@ def test_cfl_dt_matches_the_oracle(state, prec):
                                    np.full_like(c.X[0], 0.9))
         if state == "spike":
             u0 = u0.copy()
-            u0[37, 2, 1, 3] = synth.euler_conserved(np.array(0.9), [np.array(4.0), 0.0, 0.0],
+            u0[2377, 2, 1, 3] = synth.euler_conserved(np.array(0.9), [np.array(4.0), 0.0, 0.0],
                                                     np.array(3.0))
     c.set(u0)
     c.ctx.step()

@@ -442,6 +442,23 @@ __global__ void __launch_bounds__(128) k_riemann(const __grid_constant__ StepArg
   const double* recL = cL >= 0 ? A.face + cL * (long long)(D * 2 * FR) + (d * 2 + 1) * FR : nullptr;
   const double* recR = cR >= 0 ? A.face + cR * (long long)(D * 2 * FR) + (d * 2 + 0) * FR : nullptr;
 
+  if constexpr (P::CONS && !P::LINEAR) {
+    // interior face with the speeds already evaluated (mixed form): the flux is elementwise, so the
+    // lanes walk the face's NF x NV values contiguously (coalesced loads and stores)
+    if (A.fspeed && recL && recR) {
+      const double* sl = A.fspeed + (cL * D + d) * (2 * NF) + NF;
+      const double* sr = A.fspeed + (cR * D + d) * (2 * NF);
+      double sm = 0.0;
+      for (int jp = lane; jp < NF; jp += 32) sm = fmax(sm, fmax(sl[jp], sr[jp]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sm = fmax(sm, __shfl_xor_sync(0xffffffffu, sm, o));
+      double* out = A.phi + phi_off + f * (long long)(NF * NV);
+      for (int e = lane; e < NF * NV; e += 32)
+        out[e] = 0.5 * (recL[NF * NV + e] + recR[NF * NV + e]) - 0.5 * sm * (recR[e] - recL[e]);
+      return;
+    }
+  }
+
   double qL[PER][NV], qR[PER][NV], FL[PER][NV], FR_[PER][NV];
   double smax = 0.0;
 #pragma unroll

@@ -446,6 +446,18 @@ __global__ void __launch_bounds__(128) k_riemann(const __grid_constant__ StepArg
     // interior face with the speeds already evaluated (mixed form): the flux is elementwise, so the
     // lanes walk the face's NF x NV values contiguously (coalesced loads and stores)
     if (A.fspeed && recL && recR) {
+      constexpr int PE = (NF * NV + 31) / 32;  // values per lane; every load issued up front
+      double ql[PE], qr[PE], fl[PE], fr[PE];
+#pragma unroll
+      for (int r = 0; r < PE; ++r) {
+        const int e = lane + 32 * r;
+        if (e < NF * NV) {
+          ql[r] = recL[e];
+          qr[r] = recR[e];
+          fl[r] = recL[NF * NV + e];
+          fr[r] = recR[NF * NV + e];
+        }
+      }
       const double* sl = A.fspeed + (cL * D + d) * (2 * NF) + NF;
       const double* sr = A.fspeed + (cR * D + d) * (2 * NF);
       double sm = 0.0;
@@ -453,8 +465,11 @@ __global__ void __launch_bounds__(128) k_riemann(const __grid_constant__ StepArg
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sm = fmax(sm, __shfl_xor_sync(0xffffffffu, sm, o));
       double* out = A.phi + phi_off + f * (long long)(NF * NV);
-      for (int e = lane; e < NF * NV; e += 32)
-        out[e] = 0.5 * (recL[NF * NV + e] + recR[NF * NV + e]) - 0.5 * sm * (recR[e] - recL[e]);
+#pragma unroll
+      for (int r = 0; r < PE; ++r) {
+        const int e = lane + 32 * r;
+        if (e < NF * NV) out[e] = 0.5 * (fl[r] + fr[r]) - 0.5 * sm * (qr[r] - ql[r]);
+      }
       return;
     }
   }

@@ -87,14 +87,14 @@ struct CfgM {
   static constexpr int n = C::n, NS = C::NS, NST = C::NST, NV = C::NV, NL = C::NL;
   static constexpr bool EULER = P::CONS && !P::LINEAR;
   // NL / LPD threads per block (about LPD lines per thread), rounded up to 64 threads for Euler
-  // and to whole warps otherwise, from sweeps on GB300 (LPD in {2, 3, 4, 6, 8}; 192 / 224 / 256
-  // threads at order 4): Euler NL / 3 at orders 3 and 4, i.e. 128 and 256 threads (fewer
-  // registers per thread, more resident warps); elastic NL / 6 at order 4, NL / 8 at order 5.
-  static constexpr int LPD = EULER ? 3 : (N >= 5 ? 8 : 6);
+  // and to whole warps otherwise, from sweeps on GB300 (LPD in {2, 3, 4, 6, 8}; 128 to 320
+  // threads at orders 3 and 4): Euler 128 threads at order 3 (NL / 3), 320 at order 4 (NL / 2,
+  // 96 registers, 20 warps per SM); elastic NL / 6 at order 4, NL / 8 at order 5.
+  static constexpr int LPD = EULER ? (N == 4 ? 2 : 3) : (N >= 5 ? 8 : 6);
   static constexpr int RND = EULER ? 64 : 32;
   static constexpr int TPB_E = ((NL + LPD - 1) / LPD + RND - 1) / RND * RND;
   static constexpr int TPB = TPB_E < 64 ? 64 : (TPB_E > 512 ? 512 : TPB_E);
-  static constexpr int MINB = TPB <= 128 ? 3 : (TPB <= 256 ? 2 : 1);
+  static constexpr int MINB = TPB <= 128 ? 3 : (TPB <= 320 ? 2 : 1);
   static constexpr int NF = C::NF, FR = C::FR;
   static constexpr int LPT = (NL + TPB - 1) / TPB, NPT = (NST + TPB - 1) / TPB;
   static constexpr int NPS = (NS + TPB - 1) / TPB;

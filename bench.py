@@ -306,6 +306,61 @@ def extra_elastic(ader, synth, stream, steps=2, warmup=1):
     return out
 
 
+def extra_adjoint(ader, synth, stream, n=40, N=4, steps=12, k=4):
+    """Adjoint of the linear-elastic step through the C ABI (ader_misfit_gradient): order N, n^3
+    cells (h = 0.5 km), seeded material, moment-tensor Ricker source at the centre, 64 receivers
+    on the top face, a seeded misfit over `steps` steps with a checkpoint every k steps.  Reports
+    the whole gradient (forward sweep, recomputation of each segment, adjoint sweep, gradients with
+    respect to per-cell rho, lambda, mu and the moment tensor) against the same number of forward
+    steps."""
+    import torch
+    L = 0.5 * n
+    cells = n ** 3
+    dofs = cells * (N + 1) ** 3 * 9
+    mat = torch.from_numpy(synth.elastic_material((n,) * 3, seed=1905).reshape(-1).copy()).cuda()
+    cfg = ader.make_config("elastic", 3, N, (n,) * 3, (0, 0, 0), (L,) * 3, "absorbing",
+                           synth.cfl_number(N))
+    ctx = ader.Context(cfg, stream=stream.cuda_stream)
+    ctx.set_material(mat)
+    ctx.set_point_source((L / 2,) * 3, synth.moment_tensor(), 2.0, 0.5)
+    seismo = torch.zeros(steps + 2, 64, 3, dtype=torch.float64, device="cuda")
+    ctx.set_receivers(synth.receivers_top((n,) * 3, (0, 0, 0), (L,) * 3), seismo, steps + 2)
+    u0 = torch.zeros(ctx.count, dtype=torch.float64, device="cuda")
+    ctx.set_state(u0)
+    ctx.set_time(0.45)
+    ctx.step()  # dt from the CFL condition of the material
+    dt = ctx.last_dt()
+    obs = torch.from_numpy(1e-3 * np.random.default_rng(3).standard_normal(steps * 64 * 3)).cuda()
+    gm = torch.zeros(cells * 3, dtype=torch.float64, device="cuda")
+    gM = torch.zeros(6, dtype=torch.float64, device="cuda")
+    ctx.misfit_gradient(u0, 0.45, dt, 2, 2, obs, gm, gM)  # warm-up (allocates the work buffers)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.set_state(u0)
+    ctx.set_time(0.45)
+    e0.record(stream)
+    ctx.run(steps, dt=dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd = e0.elapsed_time(e1)
+    gm.zero_()
+    gM.zero_()
+    e0.record(stream)
+    J = ctx.misfit_gradient(u0, 0.45, dt, steps, k, obs, gm, gM)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tot = e0.elapsed_time(e1)
+    ok = bool(torch.isfinite(gm).all().item() and torch.isfinite(gM).all().item())
+    ctx.close()
+    del seismo
+    return {"workload": "adjoint_elastic3d_p%d_%d" % (N, n), "dofs": dofs, "steps": steps,
+            "k_ckpt": k, "forward_ms_per_step": fwd / steps, "gradient_ms": tot,
+            "gradient_over_forward": tot / fwd,
+            "value": dofs * steps / (tot * 1e-3), "unit": "DOF-updates/s (gradient: forward, "
+            "recomputation and adjoint, each step counted once)", "J": J, "finite": ok,
+            "dtype": "f64"}
+
+
 def extra_explosion(ader, synth, stream, steps=4, warmup=2, n=64):
     """3-D spherical explosion, order 3, n^3 cells (default 64^3) on [-1,1]^3, wall boundaries,
     a-posteriori subcell limiter (7^3 subcells): FP64 and mixed predictor; step time, troubled
@@ -561,7 +616,8 @@ def main():
     if not args.no_extra and world == 1:
         extra = {}
         for name, fn in (("euler2d_p3_27", extra_euler2d), ("explosion3d_p3_64", extra_explosion),
-                         ("elastic3d_p5_81", extra_elastic), ("ensemble16_elastic_p4", extra_ensemble)):
+                         ("elastic3d_p5_81", extra_elastic), ("ensemble16_elastic_p4", extra_ensemble),
+                         ("adjoint_elastic3d_p4_40", extra_adjoint)):
             try:
                 extra[name] = fn(ader, synth, stream)
             except Exception as exc:  # report, keep the headline line

@@ -417,7 +417,9 @@ def extra_explosion(ader, synth, stream, steps=4, warmup=2, n=64):
 
 def extra_ensemble(ader, synth, stream, steps=4):
     """16 elastic order-4 runs, cube sides drawn by seed from {24,32,40,48,64}, each with its own
-    seeded material and source, mixed predictor, advanced by one CUDA graph per step block."""
+    seeded material and source, mixed predictor, advanced by one CUDA graph per step block; the
+    autotuner picks between one persistent launch per phase for all runs and per-run kernels on
+    forked streams."""
     import torch
     sides = synth.ensemble_sides(16)
     cfgs = [ader.make_config("elastic", 3, 4, (s,) * 3, (0, 0, 0), (0.5 * s,) * 3, "absorbing",
@@ -448,7 +450,10 @@ def extra_ensemble(ader, synth, stream, steps=4):
     return {"workload": "ensemble16_elastic_p4", "sides": sides, "dofs": dofs,
             "ms_per_step": ms / steps, "value": dofs * steps / (ms * 1e-3), "unit": "DOF-updates/s",
             "dtype": "f32+f64", "autotuned": {"branches": best[0], "steps_per_graph": best[1],
-                                              "ms_per_step_at_tuning": best[2]}}
+                                              "persistent_blocks_per_sm": best[2],
+                                              "ms_per_step_at_tuning": best[3]},
+            "launch": "persistent launches shared by all runs" if best[0] == 0 else
+                      "per-run kernels on %d forked streams" % best[0]}
 
 
 _WORLD = [1]

@@ -246,11 +246,20 @@ void ader_ensemble_destroy(ader_ensemble* ens);
 ader_ctx* ader_ensemble_run(ader_ensemble* ens, int i);
 ader_status ader_ensemble_step(ader_ensemble* ens, int steps, double dt, double t_end);
 ader_status ader_ensemble_sync(ader_ensemble* ens);
-/* Launch shape: branches in [1, 16], steps_per_graph even and >= 2. */
-ader_status ader_ensemble_set_launch(ader_ensemble* ens, int branches, int steps_per_graph);
-/* Autotuner: times every (branches in {1,2,4}, steps_per_graph in {2,4}) candidate with fixed dt > 0 on the current
- * states (which it restores), keeps the fastest; best[2] and *ms_per_step receive the choice and
- * its time per step.  Synchronises. */
+/* Launch shape: steps_per_graph even and >= 2.  branches in [1, 16]: the runs' per-context kernels
+ * on that many forked streams inside the graph.  branches = 0: one persistent launch per phase of
+ * the step (dt, predictor, Riemann per direction, corrector, time advance) for all runs together,
+ * blocks_per_sm (1..8) persistent predictor blocks per SM; it needs runs of one PDE family with
+ * such a path (elastic, order <= 5), one order, precision, cell size and gamma, a fixed dt, no
+ * limiter and no receivers (otherwise the step falls back to one branch).  ADER_EINVAL for other
+ * values. */
+ader_status ader_ensemble_set_launch(ader_ensemble* ens, int branches, int steps_per_graph,
+                                     int blocks_per_sm);
+/* Autotuner: times every candidate launch shape with fixed dt > 0 on the current states (which it
+ * restores) and keeps the fastest: branches in {1, 2, 4} and, when the runs allow it, the
+ * persistent launches with 1 or 2 blocks per SM, each with steps_per_graph in {2, 4}.
+ * best[3] = {branches (0: persistent), steps_per_graph, blocks_per_sm (0 unless persistent)};
+ * *ms_per_step receives its time per step.  Synchronises. */
 ader_status ader_ensemble_autotune(ader_ensemble* ens, double dt, int* best, double* ms_per_step);
 
 /* Human-readable name of a status. */

@@ -80,7 +80,7 @@ _SIGS = {
     "ader_ensemble_run": ([_P, _I], _P),
     "ader_ensemble_step": ([_P, _I, _D, _D], _I),
     "ader_ensemble_sync": ([_P], _I),
-    "ader_ensemble_set_launch": ([_P, _I, _I], _I),
+    "ader_ensemble_set_launch": ([_P, _I, _I, _I], _I),
     "ader_ensemble_autotune": ([_P, _D, _P, ctypes.POINTER(_D)], _I),
     "ader_enable_timing": ([_P, _I], _I),
     "ader_phase_times": ([_P, _P, ctypes.POINTER(_I)], _I),
@@ -360,16 +360,19 @@ class Ensemble:
     def sync(self):
         check(lib().ader_ensemble_sync(self._h), "ader_ensemble_sync")
 
-    def set_launch(self, branches, steps_per_graph):
-        check(lib().ader_ensemble_set_launch(self._h, int(branches), int(steps_per_graph)),
-              "ader_ensemble_set_launch")
+    def set_launch(self, branches, steps_per_graph, blocks_per_sm=1):
+        """branches >= 1: per-run kernels on that many forked streams; 0: one persistent launch per
+        phase for all runs with blocks_per_sm predictor blocks per SM."""
+        check(lib().ader_ensemble_set_launch(self._h, int(branches), int(steps_per_graph),
+                                             int(blocks_per_sm)), "ader_ensemble_set_launch")
 
     def autotune(self, dt):
-        best = np.zeros(2, dtype=np.int32)
+        """(branches, steps_per_graph, blocks_per_sm, ms_per_step) of the fastest launch shape."""
+        best = np.zeros(3, dtype=np.int32)
         ms = _D()
         check(lib().ader_ensemble_autotune(self._h, float(dt), best.ctypes.data, ctypes.byref(ms)),
               "ader_ensemble_autotune")
-        return int(best[0]), int(best[1]), ms.value
+        return int(best[0]), int(best[1]), int(best[2]), ms.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -68,6 +68,18 @@ struct SubTables {
 struct LimArgs;
 struct AdjArgs;
 
+// Ensemble of runs advanced together (one persistent launch per phase of the step for all runs):
+// prefix offsets of the runs' cells and faces in the concatenated work lists, and the offset of
+// each direction's fluxes in a run's flux buffer.
+constexpr int ENS_MAXR = 64;
+struct EnsTable {
+  int nr;                              // runs
+  int pblocks;                         // persistent blocks of the predictor (SMs x blocks per SM)
+  long long cell0[ENS_MAXR + 1];       // first concatenated cell of run r; cell0[nr] = total
+  long long face0[3][ENS_MAXR + 1];    // the same for the faces of direction d
+  long long phioff[3][ENS_MAXR];       // run-local offset of direction d's fluxes
+};
+
 struct Geometry {
   int dim, order;
   int n[3];            // cells per direction
@@ -141,6 +153,10 @@ struct Family {
   cudaError_t (*adj_run)(const StepArgs&, const AdjArgs&, const Tables&, int blocks, cudaStream_t);
   long long (*adj_scratch_per_block)(int order, int iters);
   int (*adj_blocks_per_sm)(int order);
+  // one step of every run of an ensemble (fixed dt, no limiter, no receivers); runs: the runs'
+  // step arguments of this step in device memory; null when the family has no batched path
+  cudaError_t (*ens_step)(const StepArgs* runs, const EnsTable& E, const Tables& t,
+                          const TablesF& f, int prec, int order, cudaStream_t s);
 };
 cudaError_t launch_set_scalars(DevScalars* d, double t, double dt, cudaStream_t s);
 cudaError_t launch_sub(const double* a, const double* b, double* out, int n, cudaStream_t s);
@@ -159,6 +175,8 @@ int limiter_max_order3();
 
 // Small kernels shared by all families (common.cu).
 cudaError_t launch_dt_finalize(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_ens_dt(const StepArgs* runs, int nr, cudaStream_t s);
+cudaError_t launch_ens_advance(const StepArgs* runs, int nr, cudaStream_t s);
 cudaError_t launch_advance(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_advance_rec(const StepArgs& a, int receivers_on, cudaStream_t s);
 cudaError_t launch_receivers(const StepArgs& a, const Receivers& r, int nodes, int nvar,

@@ -1082,11 +1082,18 @@ struct ader_ensemble {
   int g_steps = 0, g_branches = 0;
   double g_dt = 0.0, g_tend = 0.0;
   std::vector<double*> g_u0;
-  int branches = 1;                   // chosen by the autotuner (or 1)
+  int branches = 1;                   // chosen by the autotuner (or 1); 0: persistent launches
   int steps_per_graph = 2;
+  int bps = 1;                        // persistent predictor blocks per SM (branches == 0)
+  int g_bps = 0;
+  StepArgs* d_runs = nullptr;         // run tables of the captured persistent steps
+  size_t d_runs_n = 0;
 };
 
 static void ens_free_graph(ader_ensemble* e) {
+  // a replay may still read the graph and the device run tables: let it finish first
+  if (!e->branch.empty()) cudaStreamSynchronize(e->branch[0]);
+  cudaStreamSynchronize(e->stream);
   if (e->gexec) cudaGraphExecDestroy(e->gexec);
   if (e->graph) cudaGraphDestroy(e->graph);
   e->gexec = nullptr;
@@ -1142,6 +1149,88 @@ static ader_status ens_capture(ader_ensemble* e, int steps, double dt, double t_
   return ADER_OK;
 }
 
+// The runs can be advanced by the persistent launches of their family: same family, order,
+// precision, cell size and gamma (shared tables), fixed dt, no limiter, no receivers.
+static bool ens_batchable(const ader_ensemble* e, double dt) {
+  if (!(dt > 0.0) || e->runs.empty() || (int)e->runs.size() > ENS_MAXR) return false;
+  const ader_ctx* a = e->runs[0];
+  if (!a->fam->ens_step || a->cfg.order > 5) return false;
+  for (const ader_ctx* c : e->runs) {
+    if (c->fam != a->fam || c->cfg.order != a->cfg.order || c->cfg.precision != a->cfg.precision ||
+        c->cfg.limiter || c->rec.nrec > 0 || c->p.gamma != a->p.gamma)
+      return false;
+    for (int d = 0; d < 3; ++d)
+      if (c->g.h[d] != a->g.h[d]) return false;
+  }
+  return true;
+}
+
+// Capture `steps` steps of every run as one persistent launch per phase: the run tables of each
+// step (the runs' step arguments with that step's state buffers) go to device memory first.
+static ader_status ens_capture_persistent(ader_ensemble* e, int steps, double dt, double t_end,
+                                          int bps) {
+  ens_free_graph(e);
+  const int nr = (int)e->runs.size();
+  const size_t need = (size_t)steps * nr;
+  if (e->d_runs_n < need) {
+    cudaFree(e->d_runs);
+    e->d_runs = nullptr;
+    e->d_runs_n = 0;
+    CUDA_OK(cudaMalloc(&e->d_runs, need * sizeof(StepArgs)));
+    e->d_runs_n = need;
+  }
+  std::vector<StepArgs> h(need);
+  for (int k = 0; k < steps; ++k)
+    for (int r = 0; r < nr; ++r) {
+      ader_ctx* c = e->runs[r];
+      h[(size_t)k * nr + r] = make_args(c, dt, t_end);
+      h[(size_t)k * nr + r].fspeed = c->fspeed;
+      std::swap(c->u, c->u_next);  // as the step does
+    }
+  CUDA_OK(cudaMemcpy(e->d_runs, h.data(), need * sizeof(StepArgs), cudaMemcpyHostToDevice));
+  EnsTable E{};
+  E.nr = nr;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  E.pblocks = sms * bps;
+  const long long nphi = e->runs[0]->cfg.pde == ADER_PDE_ELASTIC ? 2 : 1;
+  for (int r = 0; r < nr; ++r) {
+    const ader_ctx* c = e->runs[r];
+    E.cell0[r + 1] = E.cell0[r] + c->g.ncells;
+    long long off = 0;
+    for (int d = 0; d < c->g.dim; ++d) {
+      const long long nf = (long long)(c->g.n[d] + 1) * (c->g.ncells / c->g.n[d]);
+      E.face0[d][r + 1] = E.face0[d][r] + nf;
+      E.phioff[d][r] = off;
+      off += nf * nphi * c->nf * c->nvar;
+    }
+  }
+  cudaStream_t cap = e->branch[0];
+  const ader_ctx* a = e->runs[0];
+  CUDA_OK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t ce = cudaSuccess;
+  for (int k = 0; k < steps && ce == cudaSuccess; ++k)
+    ce = a->fam->ens_step(e->d_runs + (size_t)k * nr, E, a->tab, a->tabf, a->cfg.precision,
+                          a->cfg.order, cap);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(cap, &g);
+  if (ce != cudaSuccess || ee != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return ADER_ECUDA;
+  }
+  e->graph = g;
+  CUDA_OK(cudaGraphInstantiate(&e->gexec, g, 0));
+  e->g_steps = steps;
+  e->g_branches = 0;
+  e->g_bps = bps;
+  e->g_dt = dt;
+  e->g_tend = t_end;
+  e->g_u0.clear();
+  for (ader_ctx* c : e->runs) e->g_u0.push_back(c->u);
+  return ADER_OK;
+}
+
 extern "C" {
 
 ader_status ader_ensemble_create(const ader_config* cfgs, int nruns, void* stream,
@@ -1168,6 +1257,7 @@ ader_status ader_ensemble_create(const ader_config* cfgs, int nruns, void* strea
 void ader_ensemble_destroy(ader_ensemble* e) {
   if (!e) return;
   ens_free_graph(e);
+  cudaFree(e->d_runs);
   for (ader_ctx* c : e->runs) ader_destroy(c);
   for (cudaStream_t s : e->branch) cudaStreamDestroy(s);
   for (cudaEvent_t v : e->ev) cudaEventDestroy(v);
@@ -1190,11 +1280,24 @@ ader_status ader_ensemble_step(ader_ensemble* e, int steps, double dt, double t_
   const int spg = e->steps_per_graph;
   const int ng = steps / spg, rest = steps % spg;
   if (ng > 0) {
+    const bool persistent = e->branches == 0 && ens_batchable(e, dt);
+    const int nb = persistent ? 0 : (e->branches > 0 ? e->branches : 1);
     bool same = e->gexec && e->g_steps == spg && e->g_dt == dt && e->g_tend == t_end &&
-                e->g_branches == e->branches;
+                e->g_branches == nb && (!persistent || e->g_bps == e->bps);
     for (size_t r = 0; same && r < e->runs.size(); ++r) same = e->g_u0[r] == e->runs[r]->u;
     if (!same) {
-      const ader_status st = ens_capture(e, spg, dt, t_end, e->branches);
+      if (e->branch.empty()) {  // the capture stream and the fork / join event
+        cudaStream_t bs;
+        CUDA_OK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+        e->branch.push_back(bs);
+      }
+      if (e->ev.empty()) {
+        cudaEvent_t v;
+        CUDA_OK(cudaEventCreateWithFlags(&v, cudaEventDisableTiming));
+        e->ev.push_back(v);
+      }
+      const ader_status st = persistent ? ens_capture_persistent(e, spg, dt, t_end, e->bps)
+                                        : ens_capture(e, spg, dt, t_end, nb);
       if (st != ADER_OK) return st;
     }
     // order the replays after earlier work on the ensemble stream
@@ -1222,15 +1325,20 @@ ader_status ader_ensemble_sync(ader_ensemble* e) {
   return first;
 }
 
-ader_status ader_ensemble_set_launch(ader_ensemble* e, int branches, int steps_per_graph) {
-  if (!e || branches < 1 || branches > 16 || steps_per_graph < 2 || steps_per_graph % 2) return ADER_EINVAL;
+ader_status ader_ensemble_set_launch(ader_ensemble* e, int branches, int steps_per_graph,
+                                     int blocks_per_sm) {
+  if (!e || branches < 0 || branches > 16 || steps_per_graph < 2 || steps_per_graph % 2)
+    return ADER_EINVAL;
+  if (branches == 0 && (blocks_per_sm < 1 || blocks_per_sm > 8)) return ADER_EINVAL;
   e->branches = branches;
   e->steps_per_graph = steps_per_graph;
+  if (branches == 0) e->bps = blocks_per_sm;
   return ADER_OK;
 }
 
-// Time each (branches, steps per graph) candidate on the current states (restored afterwards)
-// and keep the fastest.  best[0..1] receives the choice, ms_per_step its time.
+// Time each (branches or persistent blocks per SM, steps per graph) candidate on the current
+// states (restored afterwards) and keep the fastest.  best[0..2] receives the choice, ms_per_step
+// its time.
 ader_status ader_ensemble_autotune(ader_ensemble* e, double dt, int* best, double* ms_per_step) {
   if (!e || !(dt > 0.0)) return ADER_EINVAL;
   for (ader_ctx* c : e->runs)
@@ -1242,18 +1350,26 @@ ader_status ader_ensemble_autotune(ader_ensemble* e, double dt, int* best, doubl
     CUDA_OK(cudaMemcpyAsync(save[r], e->runs[r]->u, e->runs[r]->ndof * sizeof(double),
                             cudaMemcpyDeviceToDevice, e->stream));
   }
-  const int cand_b[] = {1, 2, 4};
+  // candidates: (branches, persistent blocks per SM); branches 0 = one persistent launch per
+  // phase for all runs
+  std::vector<std::pair<int, int>> cand = {{1, 1}, {2, 1}, {4, 1}};
+  if (ens_batchable(e, dt)) {
+    cand.push_back({0, 1});
+    cand.push_back({0, 2});
+  }
   const int cand_s[] = {2, 4};
   cudaEvent_t t0, t1;
   CUDA_OK(cudaEventCreate(&t0));
   CUDA_OK(cudaEventCreate(&t1));
   double best_ms = 1e300;
-  int bb = 1, bs = 2;
-  const int ob = e->branches, os = e->steps_per_graph;
-  for (int b : cand_b) {
+  int bb = 1, bs = 2, bp = 1;
+  const int ob = e->branches, os = e->steps_per_graph, op = e->bps;
+  for (const auto& cb : cand) {
+    const int b = cb.first;
     if (b > (int)e->runs.size()) continue;
     for (int sp : cand_s) {
       e->branches = b;
+      e->bps = cb.second;
       e->steps_per_graph = sp;
       ader_status st = ader_ensemble_step(e, sp, dt, 0.0);  // capture + warm-up
       if (st != ADER_OK) break;
@@ -1268,6 +1384,7 @@ ader_status ader_ensemble_autotune(ader_ensemble* e, double dt, int* best, doubl
         best_ms = per;
         bb = b;
         bs = sp;
+        bp = cb.second;
       }
       for (size_t r = 0; r < e->runs.size(); ++r)  // restore the states (even steps: same buffers)
         CUDA_OK(cudaMemcpyAsync(e->runs[r]->u, save[r], e->runs[r]->ndof * sizeof(double),
@@ -1280,13 +1397,16 @@ ader_status ader_ensemble_autotune(ader_ensemble* e, double dt, int* best, doubl
   if (best_ms == 1e300) {
     e->branches = ob;
     e->steps_per_graph = os;
+    e->bps = op;
     return ADER_ECUDA;
   }
   e->branches = bb;
   e->steps_per_graph = bs;
+  e->bps = bp;
   if (best) {
     best[0] = bb;
     best[1] = bs;
+    best[2] = bb == 0 ? bp : 0;
   }
   if (ms_per_step) *ms_per_step = best_ms;
   return ADER_OK;

@@ -5,7 +5,7 @@
 namespace ader {
 
 // dt = CFL_N / (d (2N+1)) * min_d h_d / lambda_max  (or the fixed dt), clipped to t_end.
-__global__ void k_dt_finalize(const __grid_constant__ StepArgs A) {
+__device__ __forceinline__ void dt_finalize_one(const StepArgs& A) {
   DevScalars* s = A.dev;
   double dt;
   if (A.dt_fixed > 0.0) {
@@ -28,10 +28,22 @@ __global__ void k_dt_finalize(const __grid_constant__ StepArgs A) {
   s->n_troubled = 0;
 }
 
-__global__ void k_advance(DevScalars* s, int receivers_on) {
+__global__ void k_dt_finalize(const __grid_constant__ StepArgs A) { dt_finalize_one(A); }
+
+__device__ __forceinline__ void advance_one(DevScalars* s, int receivers_on) {
   s->t += s->dt;
   s->nstep += 1;
   if (receivers_on) s->seismo_row += 1;
+}
+
+__global__ void k_advance(DevScalars* s, int receivers_on) { advance_one(s, receivers_on); }
+
+// Ensemble: the same for every run (one thread per run).
+__global__ void k_ens_dt(const StepArgs* __restrict__ runs, int nr) {
+  if ((int)threadIdx.x < nr) dt_finalize_one(runs[threadIdx.x]);
+}
+__global__ void k_ens_advance(const StepArgs* __restrict__ runs, int nr) {
+  if ((int)threadIdx.x < nr) advance_one(runs[threadIdx.x].dev, 0);
 }
 
 // One warp per receiver: v(x_r) = sum_j Phi_j(xi_r) u[cell_r][j][0..2].
@@ -134,6 +146,16 @@ cudaError_t launch_receivers_adjoint(const Receivers& r, const double* res, doub
 
 cudaError_t launch_dt_finalize(const StepArgs& a, cudaStream_t s) {
   k_dt_finalize<<<1, 1, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ens_dt(const StepArgs* runs, int nr, cudaStream_t s) {
+  k_ens_dt<<<1, ENS_MAXR, 0, s>>>(runs, nr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ens_advance(const StepArgs* runs, int nr, cudaStream_t s) {
+  k_ens_advance<<<1, ENS_MAXR, 0, s>>>(runs, nr);
   return cudaGetLastError();
 }
 

@@ -3,6 +3,10 @@
 
 namespace ader {
 struct AdjArgs;
+cudaError_t ens_step_elastic3_fp64(const StepArgs* R, const EnsTable& E, const Tables& T,
+                                   const TablesF& F, int order, cudaStream_t s);
+cudaError_t ens_step_elastic3_mixed(const StepArgs* R, const EnsTable& E, const Tables& T,
+                                    const TablesF& F, int order, cudaStream_t s);
 template <int N>
 cudaError_t adj_run_n(const StepArgs& a, const AdjArgs& j, const Tables& t, int blocks, cudaStream_t s);
 template <int N>
@@ -40,6 +44,12 @@ int adj_bps(int order) {
   }
   return 0;
 }
+cudaError_t ens_step(const StepArgs* R, const EnsTable& E, const Tables& T, const TablesF& F,
+                     int prec, int order, cudaStream_t s) {
+  if (order > 5) return cudaErrorInvalidValue;
+  return prec == 1 ? ens_step_elastic3_mixed(R, E, T, F, order, s)
+                   : ens_step_elastic3_fp64(R, E, T, F, order, s);
+}
 }  // namespace
 
 const Family* family_elastic3() {
@@ -48,6 +58,7 @@ const Family* family_elastic3() {
     g.adj_run = &adj_run;
     g.adj_scratch_per_block = &adj_scratch;
     g.adj_blocks_per_sm = &adj_bps;
+    g.ens_step = &ens_step;
     return g;
   }();
   return &f;

@@ -128,16 +128,16 @@ __device__ __forceinline__ void load_nodes(const double* qs, const PdeParams& pp
 // cell-local part of the face terms of Eq. (6), and the face extrapolations.
 //   q^0 = u;  q^{r+1} = u + dt Kw R(q^r)  (Kw = K1^{-1} diag(w), K1^{-1} e0 = 1)
 //   R(q) = -sum_d (1/h_d) D_d F_d(q) - sum_d (1/h_d) B_d D_d q + point source
+// One cell c (all threads of the block; called by the per-context kernel and by the persistent
+// ensemble kernel).
 template <class P, int D, int N>
-__global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
-    k_predictor(const __grid_constant__ StepArgs A, const __grid_constant__ Tables T) {
+__device__ __forceinline__ void predictor_cell(const StepArgs& A, const Tables& T, long long c) {
   using C = Cfg<P, D, N>;
   constexpr int n = C::n, NV = C::NV, NL = C::NL, TPB = C::TPB, LPT = C::LPT;
   constexpr int NF = C::NF, FR = C::FR;
   extern __shared__ double smem[];
   double* qs = smem;           // [n][NL] space-time predictor (time-major)
   double* Fs = smem + n * NL;  // [FSLOTS][NL] fluxes (conservative systems)
-  const long long c = blockIdx.x;
   const int tid = threadIdx.x;
   const double dt = A.dev->dt;
   const double tn = A.dev->t;
@@ -369,6 +369,12 @@ __global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
   }
 }
 
+template <class P, int D, int N>
+__global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
+    k_predictor(const __grid_constant__ StepArgs A, const __grid_constant__ Tables T) {
+  predictor_cell<P, D, N>(A, T, blockIdx.x);
+}
+
 // Index helpers for faces.  In direction d the faces of one grid line are numbered k = 0..n_d
 // (face k is the lower face of cell k); the grid line is the cell index with digit d removed.
 struct FaceIdx {
@@ -418,14 +424,11 @@ __device__ __forceinline__ void ghost(int kind, int d, double* q, double* F) {
 // One warp per face (warp-shuffle maximum of the speeds); faces of direction d, offset `phi_off`
 // in the flux buffer.  With A.fspeed the FP64 speeds of the face states come from the predictor.
 template <class P, int D, int N>
-__global__ void __launch_bounds__(128) k_riemann(const __grid_constant__ StepArgs A,
-                                                 const __grid_constant__ Tables T, int d,
-                                                 long long phi_off) {
+__device__ __forceinline__ void riemann_face(const StepArgs& A, const Tables& T, int d,
+                                             long long phi_off, long long f, int lane) {
   using C = Cfg<P, D, N>;
   constexpr int NV = C::NV, NF = C::NF, FR = C::FR, NPHI = C::NPHI;
   constexpr int PER = (NF + 31) / 32;
-  const int lane = threadIdx.x & 31;
-  const long long f = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
   const Geometry& g = A.g;
   const int nd = g.n[d];
   const long long nfaces = (long long)(nd + 1) * FaceIdx::ntrans(g, d);
@@ -561,23 +564,23 @@ __global__ void __launch_bounds__(128) k_riemann(const __grid_constant__ StepArg
   }
 }
 
+// One warp per face (all lanes of the warp take part).
+template <class P, int D, int N>
+__global__ void __launch_bounds__(128) k_riemann(const __grid_constant__ StepArgs A,
+                                                 const __grid_constant__ Tables T, int d,
+                                                 long long phi_off) {
+  riemann_face<P, D, N>(A, T, d, phi_off, (long long)blockIdx.x * 4 + (threadIdx.x >> 5),
+                        threadIdx.x & 31);
+}
+
 // Corrector, face part of Eq. (6) in strong form:
 //   u_j -= dt sum_d [ (e1_{j_d}/(w_{j_d} h_d)) Phi_L(right face) - (e0_{j_d}/(w_{j_d} h_d)) Phi_R(left face) ]
+// One degree of freedom e of the context; sw = {dt e0/(w h), dt e1/(w h)} of the context.
 template <class P, int D, int N>
-__global__ void __launch_bounds__(256) k_corrector(const __grid_constant__ StepArgs A,
-                                                   const __grid_constant__ Tables T,
-                                                   long long off1, long long off2) {
+__device__ __forceinline__ void corrector_dof(const StepArgs& A, const double (*sw)[3][N + 1],
+                                              long long off1, long long off2, long long e) {
   using C = Cfg<P, D, N>;
   constexpr int n = C::n, NV = C::NV, NL = C::NL, NF = C::NF, NPHI = C::NPHI;
-  // dt e0 / (w h_d) and dt e1 / (w h_d) once per block (the row j_d differs between lanes)
-  __shared__ double sw[2][3][n];
-  if (threadIdx.x < 2 * D * n) {
-    const int k = threadIdx.x / (D * n), d = (threadIdx.x / n) % D, m = threadIdx.x % n;
-    sw[k][d][m] = A.dev->dt * (k ? A.cw1[d][m] : A.cw0[d][m]);
-  }
-  __syncthreads();
-  const long long e = (long long)blockIdx.x * 256 + threadIdx.x;
-  if (e >= A.g.ncells * NL) return;
   const unsigned c = (unsigned)(e / NL);
   const int l = (int)(e - (long long)c * NL);
   const int j = l / NV, v = l - (l / NV) * NV;
@@ -603,6 +606,24 @@ __global__ void __launch_bounds__(256) k_corrector(const __grid_constant__ StepA
     un = fma(sw[0][d][jd], PhiR, un);
   }
   A.u_next[e] = un;
+}
+
+template <class P, int D, int N>
+__global__ void __launch_bounds__(256) k_corrector(const __grid_constant__ StepArgs A,
+                                                   const __grid_constant__ Tables T,
+                                                   long long off1, long long off2) {
+  using C = Cfg<P, D, N>;
+  constexpr int n = C::n;
+  // dt e0 / (w h_d) and dt e1 / (w h_d) once per block (the row j_d differs between lanes)
+  __shared__ double sw[2][3][n];
+  if (threadIdx.x < 2 * D * n) {
+    const int k = threadIdx.x / (D * n), d = (threadIdx.x / n) % D, m = threadIdx.x % n;
+    sw[k][d][m] = A.dev->dt * (k ? A.cw1[d][m] : A.cw0[d][m]);
+  }
+  __syncthreads();
+  const long long e = (long long)blockIdx.x * 256 + threadIdx.x;
+  if (e >= A.g.ncells * C::NL) return;
+  corrector_dof<P, D, N>(A, sw, off1, off2, e);
 }
 
 // Max signal speed of the state (Eq. (7)); NaN / Inf latches ST_NONFINITE.  Euler: one FP64
@@ -822,7 +843,7 @@ struct FamilyImpl {
   static size_t smem(int order, int prec);
   static const Family* get() {
     static const Family f = {P::NV, P::CONS, &cfl,    &predictor, &riemann, &corrector, &smem,
-                             nullptr, nullptr, nullptr, nullptr,   nullptr};
+                             nullptr, nullptr, nullptr, nullptr,   nullptr,  nullptr};
     return &f;
   }
 };

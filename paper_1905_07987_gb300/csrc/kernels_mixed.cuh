@@ -327,10 +327,11 @@ __device__ __forceinline__ void contract_f(const float* X, const float* Dh, cons
   }
 }
 
+// One cell c (all threads of the block; called by the per-context kernel and by the persistent
+// ensemble kernel).
 template <class P, int D, int N>
-__global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
-    k_predictor_mixed(const __grid_constant__ StepArgs A, const __grid_constant__ Tables T,
-                      const __grid_constant__ TablesF F) {
+__device__ __forceinline__ void predictor_mixed_cell(const StepArgs& A, const Tables& T,
+                                                     const TablesF& F, long long c) {
   using M = CfgM<P, D, N>;
   constexpr int n = M::n, NS = M::NS, NV = M::NV, NL = M::NL, TPB = M::TPB, LPT = M::LPT;
   constexpr int NF = M::NF, FR = M::FR;
@@ -344,7 +345,6 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
   // epilogue
   float* dF3 = reinterpret_cast<float*>(p);
   constexpr int NSL = n * NL;
-  const long long c = blockIdx.x;
   const int tid = threadIdx.x;
   const double dt = A.dev->dt;
   const float dtf = (float)dt;
@@ -722,6 +722,13 @@ __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
       for (int e = tid; e < D * 2 * NF; e += TPB) fs[e] = P::speed(qs + e * NV, A.p, e / (2 * NF));
     }
   }
+}
+
+template <class P, int D, int N>
+__global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
+    k_predictor_mixed(const __grid_constant__ StepArgs A, const __grid_constant__ Tables T,
+                      const __grid_constant__ TablesF F) {
+  predictor_mixed_cell<P, D, N>(A, T, F, blockIdx.x);
 }
 
 template <class P, int D, int N>

@@ -47,15 +47,20 @@ def states(ctxs):
     return [t.cpu().numpy() for t in out]
 
 
-@pytest.mark.parametrize("branches,spg", [(1, 2), (2, 4), (3, 2)])
-def test_ensemble_graph_equals_separate_runs(branches, spg):
+@pytest.mark.parametrize("branches,spg,bps,prec", [(1, 2, 1, "fp64"), (2, 4, 1, "fp64"),
+                                                   (3, 2, 1, "fp64"), (0, 2, 1, "fp64"),
+                                                   (0, 4, 2, "fp64"), (0, 2, 1, "mixed"),
+                                                   (0, 4, 3, "mixed")])
+def test_ensemble_graph_equals_separate_runs(branches, spg, bps, prec):
+    """Every launch shape, including the persistent launches shared by all runs (branches 0),
+    gives each run exactly the result of stepping it on its own."""
     sides, order = [3, 5, 4, 2], 2
-    ens = ader.Ensemble(member_configs(sides, order))
-    singles = [ader.Context(c) for c in member_configs(sides, order)]
+    ens = ader.Ensemble(member_configs(sides, order, precision=prec))
+    singles = [ader.Context(c) for c in member_configs(sides, order, precision=prec)]
     for i, s in enumerate(sides):
         setup_member(ens.runs[i], s, order, seed=i)
         setup_member(singles[i], s, order, seed=i)
-    ens.set_launch(branches, spg)
+    ens.set_launch(branches, spg, bps)
     dt = 1e-3
     ens.step(7, dt=dt)
     ens.sync()
@@ -93,11 +98,53 @@ def test_autotune_keeps_results_and_picks_a_valid_shape():
     for i, s in enumerate(sides):
         setup_member(ens.runs[i], s, order, seed=i)
     before = states(ens.runs)
-    b, spg, ms = ens.autotune(1e-3)
-    assert b in (1, 2, 4) and spg in (2, 4) and ms > 0
+    b, spg, bps, ms = ens.autotune(1e-3)
+    assert b in (0, 1, 2, 4) and spg in (2, 4) and ms > 0
+    assert (bps in (1, 2)) if b == 0 else bps == 0
     after = states(ens.runs)
     for x, y in zip(before, after):
         assert np.array_equal(x, y)
     ens.step(6, dt=1e-3)
     ens.sync()
+    ens.close()
+
+
+def test_persistent_launch_falls_back_when_the_runs_differ():
+    """Runs with different cell sizes cannot share the persistent launches' tables: the step falls
+    back to per-run kernels and still matches separate runs."""
+    sides, order = [3, 4], 2
+    cfgs = member_configs(sides, order)
+    cfgs[1] = ader.make_config("elastic", 3, order, (4, 4, 4), (0, 0, 0), (3.0,) * 3, "absorbing",
+                               synth.cfl_number(order))
+    ens = ader.Ensemble(cfgs)
+    singles = [ader.Context(c) for c in cfgs]
+    for i, s in enumerate(sides):
+        setup_member(ens.runs[i], s, order, seed=i)
+        setup_member(singles[i], s, order, seed=i)
+    ens.set_launch(0, 2, 1)
+    ens.step(4, dt=1e-3)
+    ens.sync()
+    for c in singles:
+        c.run(4, dt=1e-3)
+    for a, b in zip(states(ens.runs), states(singles)):
+        assert np.array_equal(a, b)
+    ens.close()
+
+
+def test_persistent_launch_order_four_mixed_uneven_sizes():
+    """The benchmark's kind of ensemble (order 4, mixed predictor, uneven cube sides) on the
+    persistent launches equals separate runs."""
+    sides, order = [6, 3, 5, 2, 4], 4
+    ens = ader.Ensemble(member_configs(sides, order, precision="mixed"))
+    singles = [ader.Context(c) for c in member_configs(sides, order, precision="mixed")]
+    for i, s in enumerate(sides):
+        setup_member(ens.runs[i], s, order, seed=30 + i)
+        setup_member(singles[i], s, order, seed=30 + i)
+    ens.set_launch(0, 2, 2)
+    ens.step(5, dt=1e-3)
+    ens.sync()
+    for c in singles:
+        c.run(5, dt=1e-3)
+    for a, b in zip(states(ens.runs), states(singles)):
+        assert np.array_equal(a, b)
     ens.close()

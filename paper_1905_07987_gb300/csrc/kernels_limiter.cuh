@@ -123,7 +123,10 @@ __device__ __forceinline__ double okey_inv(long long k) {
 }
 
 // rho > 0 and p > 0 with every value finite.  For rho > 0 and gamma > 1, p > 0 is
-// E rho - |j|^2 / 2 > 0 (no division); finiteness and the sign of rho are read from the bits.
+// 2 E rho - |j|^2 > 0, which one fused multiply-add decides with the sign of E rho - |j|^2 / 2
+// (the exact value is doubled before its single rounding); 2E by an exponent increment on the
+// integer pipe (zero and subnormal E by an add).  Finiteness, the sign of rho and of the result
+// are read from the bits.
 template <int D>
 __device__ __forceinline__ bool admissible(const double* q) {
   bool fin = true;
@@ -132,7 +135,11 @@ __device__ __forceinline__ bool admissible(const double* q) {
   double j2 = 0.0;
 #pragma unroll
   for (int i = 0; i < D; ++i) j2 = fma(q[1 + i], q[1 + i], j2);
-  return fin && (__double_as_longlong(q[0]) > 0) && (fma(q[D + 1], q[0], -0.5 * j2) > 0.0);
+  const long long eb = __double_as_longlong(q[D + 1]);
+  const double e2 = (eb & 0x7ff0000000000000ll) != 0 ? __longlong_as_double(eb + (1ll << 52))
+                                                      : q[D + 1] + q[D + 1];
+  return fin && (__double_as_longlong(q[0]) > 0) &&
+         (__double_as_longlong(fma(e2, q[0], -j2)) > 0);
 }
 
 // Per-variable min / max of sub[NSS][NV] into mm[2][NV]; red: smem scratch [2][NV][32].

@@ -214,6 +214,10 @@ __global__ void __launch_bounds__(Cfg<Elastic, 3, N>::TPB)
   double* Q = sm;            // [n][NL] forward iterate
   double* P = sm + n * NL;   // [n][NL] adjoint work (rho), also lambda / q_bar lines
   __shared__ double red[3 * 32 + 6 * 32];
+  // D is indexed by per-lane rows and columns: staged in shared memory once per block
+  __shared__ double sD[n * n];
+  for (int i = threadIdx.x; i < n * n; i += TPB) sD[i] = T.D[i / n][i % n];
+  __syncthreads();
   const double dt = A.dev->dt;
   const double tn = A.dev->t;
   double* slab = J.scratch + (long long)blockIdx.x * J.scratch_per_block;
@@ -250,9 +254,9 @@ __global__ void __launch_bounds__(Cfg<Elastic, 3, N>::TPB)
       for (int k = 0; k < LPT; ++k)
 #pragma unroll
         for (int t = 0; t < n; ++t) R[k][t] = 0.0;
-      contract_ncp_elastic<Cfg<Elastic, 3, N>, 0, MAXN>(Q, &T.D[0][0], A.g.inv_h[0], irho, lamc, mu, R, threadIdx.x);
-      contract_ncp_elastic<Cfg<Elastic, 3, N>, 1, MAXN>(Q, &T.D[0][0], A.g.inv_h[1], irho, lamc, mu, R, threadIdx.x);
-      contract_ncp_elastic<Cfg<Elastic, 3, N>, 2, MAXN>(Q, &T.D[0][0], A.g.inv_h[2], irho, lamc, mu, R, threadIdx.x);
+      contract_ncp_elastic<Cfg<Elastic, 3, N>, 0, n>(Q, sD, A.g.inv_h[0], irho, lamc, mu, R, threadIdx.x);
+      contract_ncp_elastic<Cfg<Elastic, 3, N>, 1, n>(Q, sD, A.g.inv_h[1], irho, lamc, mu, R, threadIdx.x);
+      contract_ncp_elastic<Cfg<Elastic, 3, N>, 2, n>(Q, sD, A.g.inv_h[2], irho, lamc, mu, R, threadIdx.x);
       if (has_src) {
 #pragma unroll
         for (int k = 0; k < LPT; ++k) {
@@ -318,7 +322,7 @@ __global__ void __launch_bounds__(Cfg<Elastic, 3, N>::TPB)
         if (s >= 0) {
           double dq = 0.0;
 #pragma unroll
-          for (int m = 0; m < n; ++m) dq = fma(T.D[jd][m], P[(j0 + m * st) * NV + s], dq);
+          for (int m = 0; m < n; ++m) dq = fma(sD[jd * n + m], P[(j0 + m * st) * NV + s], dq);
           double dc[3];
           dcoef(d, v, rho, dc);
           const double w = lam_l[k] * dt * (-A.g.inv_h[d]) * dq;
@@ -331,7 +335,7 @@ __global__ void __launch_bounds__(Cfg<Elastic, 3, N>::TPB)
           if (r < 0) break;
           double acc = 0.0;
 #pragma unroll
-          for (int i = 0; i < n; ++i) acc = fma(T.D[i][jd], P[NL + (j0 + i * st) * NV + r], acc);
+          for (int i = 0; i < n; ++i) acc = fma(sD[i * n + jd], P[NL + (j0 + i * st) * NV + r], acc);
           qbh = fma(-dt * A.g.inv_h[d] * Elastic::coef_ir(d, r, irho, lamc, mu), acc, qbh);
         }
         // face extrapolations of q_bar along d
@@ -396,7 +400,7 @@ __global__ void __launch_bounds__(Cfg<Elastic, 3, N>::TPB)
             for (int t = 0; t < n; ++t) {
               double dq = 0.0;
 #pragma unroll
-              for (int m = 0; m < n; ++m) dq = fma(T.D[jd][m], Q[t * NL + (j0 + m * st) * NV + s], dq);
+              for (int m = 0; m < n; ++m) dq = fma(sD[jd * n + m], Q[t * NL + (j0 + m * st) * NV + s], dq);
               acc = fma(rh[k][t], dq, acc);
             }
             const double w = -A.g.inv_h[d] * acc;
@@ -411,7 +415,7 @@ __global__ void __launch_bounds__(Cfg<Elastic, 3, N>::TPB)
             for (int t = 0; t < n; ++t) {
               double acc = 0.0;
 #pragma unroll
-              for (int i = 0; i < n; ++i) acc = fma(T.D[i][jd], P[t * NL + (j0 + i * st) * NV + rr], acc);
+              for (int i = 0; i < n; ++i) acc = fma(sD[i * n + jd], P[t * NL + (j0 + i * st) * NV + rr], acc);
               qh[k][t] = fma(cf, acc, qh[k][t]);
             }
           }

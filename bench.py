@@ -594,7 +594,7 @@ def main():
                 "k_predictor (FP64)"
         else:
             peak, src, kname = FP32_PEAK, "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz", \
-                "k_predictor_mixed (binary32 iterations, float-float base and final stage)"
+                "k_predictor_mixed (binary32 Picard iterations and flux remainders; float-float base terms, time averages and contractions; FP64 face wave speeds)"
         return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / (peak / 1e12),
                 "traffic": TRAFFIC_PER_CELL.get(prec, 0) * cells if TRAFFIC_PER_CELL.get(prec) else None,

@@ -5,16 +5,18 @@
 // B0 and every term that carries the O(1) size of the solution (the flux F(u^n), its derivative,
 // the face extrapolations of u^n and F(u^n)) are formed in FP64 or in float-float (hi + lo pairs
 // of binary32 with error-free transformations, about 44 significant bits) on the FP32 pipe.
-// The first N Picard iterations, their flux increments F(u+dq) - F(u) (written so that no O(1)
-// terms cancel) and contractions run in plain binary32 -- each iteration damps the error of the
-// previous one by the CFL-sized factor |dt Kw dR/dq|.  The last iteration's time solve and every
-// contraction of the epilogue run in float-float, so that no binary32 rounding of the final
-// predictor reaches the update.  The time-averaged flux increment is split exactly as
-//   sum_t w_t [F(u + dq_t) - F(u)] = A(u) qbar + sum_t w_t N(dq_t),   qbar = sum_t w_t dq_t,
+// The Picard iterations, their flux increments F(u+dq) - F(u) (written so that no O(1) terms
+// cancel), contractions and time solves run in plain binary32 -- each iteration damps the error
+// of the previous one by the CFL-sized factor |dt Kw dR/dq|; the last contraction adds the lo
+// parts of the tables.  The time average of the last iterate, qbar = sum_t w_t dq_t, is formed in
+// float-float directly from the time-averaged solve weights, and every contraction of the
+// epilogue runs in float-float, so that no binary32 rounding of the final predictor reaches the
+// update.  The time-averaged flux increment is split exactly as
+//   sum_t w_t [F(u + dq_t) - F(u)] = A(u) qbar + sum_t w_t N(dq_t),
 // with A the flux Jacobian at u^n and N the quadratic remainder: the linear part in float-float
-// once per spatial node, the O(dt^2) remainders in binary32 per space-time node.  The corrector,
-// Riemann solver, CFL condition and pressure / sound speed of the face states stay FP64 (other
-// kernels).
+// once per spatial node, the O(dt^2) remainders in binary32 per space-time node.  The FP64 wave
+// speeds of the face states (Euler) are evaluated here for the Riemann solver; the corrector,
+// Riemann flux, CFL maximum and limiter stay FP64 (other kernels).
 #pragma once
 #include "kernels.cuh"
 

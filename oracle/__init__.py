@@ -19,7 +19,8 @@ the method, in the paper's order:
                  extrapolation, Rusanov Riemann solver, corrector, point source, receivers.
 * ``limiter``  - subcell projection, relaxed DMP + positivity detection, MUSCL-Hancock
                  recompute of troubled cells and the conservative neighbour face fix.
-* ``ck``       - brute-force Cauchy-Kowalevski predictor for linear PDEs on one cell
+* ``ck``       - brute-force (dense) Cauchy-Kowalevski predictor for linear PDEs on one cell; the
+               scheme-level Cauchy-Kowalevski predictor is ``aderdg.ADERDG.predictor_ck``
                  (a second, independent route used only to pin the Picard predictor).
 
 Functions whose result has no independent pin say "parity unpinned" in their docstring.

@@ -3,7 +3,8 @@
 Follows Sec. 3.3-3.4 of the paper in its order:
 
 1. per cell, solve the element-local space-time weak form Eq. (5) for the predictor q_h by the
-   fixed-point (discrete Picard) iteration;
+   fixed-point (discrete Picard) iteration, or, for linear PDEs, evaluate it by the
+   Cauchy-Kowalevski procedure (Sec. 2 and Sec. 3.3);
 2. per face, a numerical normal flux from both adjacent cells: Rusanov (Sec. 3.3, phase 2), with a
    path-conservative fluctuation for the non-conservative product B(Q).grad Q of Eq. (1);
 3. per cell, the corrector Eq. (6) with a diagonal mass matrix;
@@ -34,6 +35,11 @@ Readings of the paper taken here (the paper is silent or garbled on these points
   is the interior one.
 * CFL: dt = CFL / (d (2N+1)) * min_d h_d / lambda_max with lambda_max over all cells, nodes and
   directions of the state at t^n.
+* Cauchy-Kowalevski predictor (linear PDEs): the local solution's Taylor series in time about
+  t^n, cut after degree N, with each time derivative replaced by the spatial operator applied to
+  the previous one; a point source's time factor is replaced by its degree-N interpolant through
+  the step's Gauss-Legendre time nodes (the samples the Picard predictor uses).  q_h is then
+  evaluated at the time nodes and everything after the predictor is shared with the Picard form.
 """
 import math
 import torch
@@ -124,8 +130,12 @@ class PointSource:
 class ADERDG:
     """The ADER-DG scheme of order N on a Grid for one PDE (see module docstring)."""
 
-    def __init__(self, pde, grid, order, cfl=0.9, picard_iters=0, material=None):
+    def __init__(self, pde, grid, order, cfl=0.9, picard_iters=0, material=None,
+                 predictor="picard"):
         assert pde.dim == grid.dim
+        assert predictor in ("picard", "ck")
+        assert predictor == "picard" or getattr(pde, "linear", False), "CK needs a linear PDE"
+        self.predictor_kind = predictor
         self.pde, self.grid = pde, grid
         self.D = grid.dim
         self.N = order
@@ -267,6 +277,64 @@ class ADERDG:
             q = q_new
         return q
 
+    # ----- 1'. Cauchy-Kowalevski predictor (linear PDEs) -------------------------------
+    def linear_operator(self, a):
+        """L a = -sum_d (1/h_d) (D_d F_d(a) + B_d D_d a) for a spatial array a[C, n.., nv]: the
+        right-hand side of Eq. (1) without sources (linear PDE: F_d and B_d do not depend on a)."""
+        out = torch.zeros_like(a)
+        for d in range(self.D):
+            if self.pde.has_flux:
+                out = out - contract(self.pde.flux(a, d), self.ref.D, self.sax(d)) / self.grid.h[d]
+        if self.pde.has_ncp:
+            out = out - self.ncp_term(a, self.sax)
+        return out
+
+    def source_shape(self):
+        """g[C, n.., nv]: the point source's spatial factor, -M_a Phi_j(xi0) / (W_j h^d) on the
+        stress variables of the source cell, so that the source term is g R(t)."""
+        src = self.source
+        g = torch.zeros([self.grid.C] + [self.n] * self.D + [self.nv], dtype=torch.float64)
+        phi = self.tensor_basis(src.xi)
+        W = self.tensor_basis_weights()
+        vol = 1.0
+        for hd in self.grid.h:
+            vol *= hd
+        shape = phi / (W * vol)
+        for a, var in enumerate(src.vars):
+            g[src.cell, ..., var] = -src.M[a] * shape
+        return g
+
+    def source_taylor(self, t, dt):
+        """Monomial coefficients s_k (k = 0..N, in tau = (time - t)/dt) of the degree-N polynomial
+        through the Ricker values at the time nodes t + x_k dt (a Vandermonde solve)."""
+        src = self.source
+        V = self.ref.x.unsqueeze(1) ** torch.arange(self.n, dtype=torch.float64).unsqueeze(0)
+        amp = ricker(t + self.ref.x * dt, src.f0, src.t0)
+        return torch.linalg.solve(V, amp)
+
+    def predictor_ck(self, u, dt, t=0.0):
+        """Cauchy-Kowalevski predictor (Sec. 2, Sec. 3.3; linear PDEs).  With
+        q(t + tau dt) = sum_{k<=N} a_k tau^k, du/dt = L u + g s(tau) gives
+            a_0 = u,   a_{k+1} = dt / (k+1) (L a_k + g s_k),   k = 0..N-1
+        (the k-th time derivative is dt^-k k! a_k).  Returns q at the time nodes, [C, nt, n.., nv],
+        like the Picard predictor."""
+        a = [u]
+        if self.source is not None:
+            s = self.source_taylor(t, dt)
+            g = self.source_shape()
+        for k in range(self.N):
+            La = self.linear_operator(a[k])
+            if self.source is not None:
+                La = La + s[k] * g
+            a.append(dt / (k + 1) * La)
+        q = []
+        for xt in self.ref.x:
+            qt = a[self.N]
+            for k in range(self.N - 1, -1, -1):  # Horner in tau
+                qt = qt * xt + a[k]
+            q.append(qt)
+        return torch.stack(q, dim=1)
+
     # ----- time averages, volume term and face data ----------------------------------
     def time_average(self, X):
         w = self.ref.w.reshape([1, self.n] + [1] * (X.dim() - 2))
@@ -396,7 +464,10 @@ class ADERDG:
 
     # ----- whole step -----------------------------------------------------------------
     def step(self, u, dt, t=0.0, details=False):
-        q = self.predictor(u, dt, t)
+        if self.predictor_kind == "ck":
+            q = self.predictor_ck(u, dt, t)
+        else:
+            q = self.predictor(u, dt, t)
         qbar, Fbar, vol, faces = self.face_data(q, dt, t)
         fluxes = self.face_fluxes(faces)
         u_new = self.correct(u, vol, faces, fluxes, dt)

@@ -109,3 +109,79 @@ def test_ncp_predictor_matches_conservative_for_constant_speed():
     u = torch.sin(2 * math.pi * X[0]) * torch.cos(2 * math.pi * X[1])
     u = u[..., None]
     assert torch.allclose(s1.predictor(u, 0.01), s2.predictor(u, 0.01), atol=1e-14)
+
+
+# ---- the scheme's Cauchy-Kowalevski predictor (linear PDEs, Sec. 2 and Sec. 3.3) -------------
+
+@pytest.mark.parametrize("N", [2, 4])
+def test_scheme_ck_predictor_equals_dense_ck_elastic(N):
+    """Taylor recursion with the sum-factorised operator = the dense Kronecker-assembled expansion."""
+    mat = torch.tensor([[2.7, 30.0, 25.0]], dtype=torch.float64)
+    s, L = _cell_ops(N, 3, Elastic(), mat)
+    g = torch.Generator().manual_seed(21)
+    u = torch.rand([1] + [N + 1] * 3 + [9], generator=g, dtype=torch.float64) - 0.5
+    dt = 0.004
+    q = s.predictor_ck(u, dt)
+    qck = ck_predictor(u.reshape(-1), L, dt, [float(v) for v in s.ref.x], N)
+    assert torch.allclose(q.reshape(N + 1, -1), qck, atol=1e-13 * float(qck.abs().max()))
+
+
+def test_scheme_ck_predictor_equals_dense_ck_flux_form():
+    N = 3
+    s, L = _cell_ops(N, 2, Advection([0.6, -0.3]), h=0.5)
+    g = torch.Generator().manual_seed(22)
+    u = torch.rand([1, N + 1, N + 1, 1], generator=g, dtype=torch.float64) - 0.5
+    q = s.predictor_ck(u, 0.03)
+    qck = ck_predictor(u.reshape(-1), L, 0.03, [float(v) for v in s.ref.x], N)
+    assert torch.allclose(q.reshape(N + 1, -1), qck, atol=1e-14)
+
+
+@pytest.mark.parametrize("pde_cls", [Advection, AdvectionNCP])
+@pytest.mark.parametrize("dim,N", [(2, 3), (3, 2)])
+def test_ck_predictor_exact_for_polynomial_data(pde_cls, dim, N):
+    """Data of total degree <= N: the truncated Taylor series is the exact solution u0(x - a t)."""
+    a = [0.7, -0.4, 0.25][:dim]
+    g = Grid((2,) * dim, (0.0,) * dim, (1.0,) * dim, [('periodic', 'periodic')] * dim)
+    s = ADERDG(pde_cls(a), g, N, predictor="ck")
+    X = s.node_coords()
+    u = poly(X, N, 9)[..., None]
+    dt = 0.03
+    q = s.predictor_ck(u, dt)
+    for k in range(N + 1):
+        t = float(s.ref.x[k]) * dt
+        Xs = [X[d] - a[d] * t for d in range(dim)]
+        assert torch.allclose(q[:, k, ..., 0], poly(Xs, N, 9), atol=1e-12)
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_ck_point_source_error_is_order_dt_to_the_N_plus_1(N):
+    """u^n = 0 with a point source: q at the time nodes against the exact solution of the cell's
+    linear ODE du/dt = L u + g R(t), the Duhamel integral of the matrix exponential (24-point
+    Gauss-Legendre in time); g is read off the Picard predictor's source term.  The error falls as
+    dt^(N+1) (Taylor truncation plus the degree-N interpolant of the wavelet)."""
+    from oracle.aderdg import PointSource, ricker
+    from oracle.refelem import gauss_legendre
+    mat = torch.tensor([[2.6, 28.0, 24.0]], dtype=torch.float64)
+    s, L = _cell_ops(N, 3, Elastic(), mat)
+    M = torch.tensor([1.0, -0.5, 0.25, 0.7, -0.3, 0.2], dtype=torch.float64)
+    s.set_point_source(PointSource(cell=0, xi=(0.3, 0.6, 0.45), M=M, f0=2.0, t0=0.5))
+    t = 0.4
+    tt = torch.tensor([t], dtype=torch.float64)
+    gvec = (s.source_nodes(tt)[0, 0] / ricker(tt, 2.0, 0.5)[0]).reshape(-1)
+    gx, gw = gauss_legendre(24)
+    u0 = torch.zeros([1] + [N + 1] * 3 + [9], dtype=torch.float64)
+    errs = []
+    for dt in (4e-3, 2e-3, 1e-3):
+        q = s.predictor_ck(u0, dt, t).reshape(N + 1, -1)
+        err = 0.0
+        for k in range(N + 1):
+            T_ = float(s.ref.x[k]) * dt
+            ex = torch.zeros_like(gvec)
+            for z, wz in zip([float(v) for v in gx], [float(v) for v in gw]):
+                sig = z * T_
+                ex = ex + wz * T_ * float(ricker(torch.tensor(t + sig, dtype=torch.float64), 2.0, 0.5)) * (
+                    torch.linalg.matrix_exp((T_ - sig) * L) @ gvec)
+            err = max(err, float((q[k] - ex).abs().max()))
+        errs.append(err)
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > N + 1 - 0.3, (errs, rates)

@@ -329,3 +329,17 @@ def test_cfl_time_step_closed_form():
     c = math.sqrt(1.4 * 0.8 / 1.3)
     lam = 0.9 + c
     assert abs(float(s.cfl_dt(u)) - synth.cfl_number(4) / (3 * 9) * 0.25 / lam) < 1e-15
+
+
+def test_elastic_plane_wave_converges_with_the_ck_predictor():
+    """The Cauchy-Kowalevski form of the scheme keeps order N+1 on an exact plane P wave."""
+    mat = [2.7, 30.0, 25.0]
+    errs = []
+    for nc in (4, 8):
+        g = Grid((nc, 1, 1), (0.0,) * 3, (1.0, 1.0 / nc, 1.0 / nc), periodic(3))
+        s = ADERDG(Elastic(), g, 2, cfl=synth.cfl_number(2), material=T(np.tile(mat, (nc, 1))),
+                   predictor="ck")
+        u = T(synth.plane_wave_elastic(coords(s), mat, kind='p'))
+        u, t = s.run(u, None, t_end=0.05)
+        errs.append(l2_error(s, u, lambda X: synth.plane_wave_elastic(X, mat, t, kind='p')[..., 0], var=0))
+    assert math.log2(errs[0] / errs[1]) > 2.5, errs

@@ -15,13 +15,13 @@ the method, in the paper's order:
                  the time-stiffness matrix of the predictor, subcell projections.
 * ``pde``      - flux / non-conservative product / eigenvalue terms of the PDEs used
                  (scalar advection, compressible Euler, linear elasticity).
-* ``aderdg``   - CFL time step, Picard space-time predictor, time averages, face
+* ``aderdg``   - CFL time step, Picard and Cauchy-Kowalevski space-time predictors, time averages, face
                  extrapolation, Rusanov Riemann solver, corrector, point source, receivers.
 * ``limiter``  - subcell projection, relaxed DMP + positivity detection, MUSCL-Hancock
                  recompute of troubled cells and the conservative neighbour face fix.
-* ``ck``       - brute-force (dense) Cauchy-Kowalevski predictor for linear PDEs on one cell; the
-               scheme-level Cauchy-Kowalevski predictor is ``aderdg.ADERDG.predictor_ck``
-                 (a second, independent route used only to pin the Picard predictor).
+* ``ck``       - brute-force (dense, Kronecker-assembled) Cauchy-Kowalevski predictor for linear
+                 PDEs on one cell: an independent route that pins the Picard predictor and the
+                 scheme's own Cauchy-Kowalevski predictor (``aderdg.ADERDG.predictor_ck``).
 
 Functions whose result has no independent pin say "parity unpinned" in their docstring.
 """

@@ -272,9 +272,11 @@ def extra_elastic(ader, synth, stream, steps=2, warmup=1):
     mat = torch.from_numpy(synth.elastic_material((n,) * 3, seed=1905).reshape(-1).copy()).cuda()
     out = {"workload": "elastic3d_p5_81", "dofs": n ** 3 * 216 * 9}
     finals = {}
-    for prec in ("fp64", "mixed"):
+    for form in ("fp64", "mixed", "ck"):
+        prec = "mixed" if form == "mixed" else "fp64"
         cfg = ader.make_config("elastic", 3, N, (n,) * 3, (0, 0, 0), (L,) * 3, "absorbing",
-                               synth.cfl_number(N), precision=prec)
+                               synth.cfl_number(N), precision=prec,
+                               predictor="ck" if form == "ck" else "picard")
         ctx = ader.Context(cfg, stream=stream.cuda_stream)
         ctx.set_material(mat)
         ctx.set_point_source((L / 2,) * 3, synth.moment_tensor(), 2.0, 0.5)
@@ -295,14 +297,31 @@ def extra_elastic(ader, synth, stream, steps=2, warmup=1):
         ms = e0.elapsed_time(e1)
         ph, nr = ctx.phase_times()
         ctx.enable_timing(False)
-        finals[prec] = _dev_state(ctx)
-        out[prec] = {"ms_per_step": ms / steps, "value": out["dofs"] * steps / (ms * 1e-3),
-                     "predictor_ms": ph["predictor"] / max(nr, 1)}
+        finals[form] = _dev_state(ctx)
+        out[form] = {"ms_per_step": ms / steps, "value": out["dofs"] * steps / (ms * 1e-3),
+                     "predictor_ms": ph["predictor"] / max(nr, 1),
+                     "riemann_ms": ph["riemann"] / max(nr, 1),
+                     "corrector_ms": ph["corrector"] / max(nr, 1)}
         ctx.close()
         del seismo
     d = (finals["mixed"] - finals["fp64"]).abs().max().item()
-    out["mixed_vs_fp64_rel_linf"] = d / max(finals["fp64"].abs().max().item(), 1e-300)
+    scale = max(finals["fp64"].abs().max().item(), 1e-300)
+    out["mixed_vs_fp64_rel_linf"] = d / scale
     out["mixed_speedup"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    # Cauchy-Kowalevski predictor: FP64-pipe roofline of its algorithmic flops per cell, N+1
+    # applications of the spatial operator (18n+24 FMA per node: six derivatives along each
+    # direction, eight rows of B_d), the Taylor update (9 MUL + 9 FMA per node, N times) and the
+    # face extrapolation (6 n^2 9 dot products of length n)
+    nn, NS = N + 1, (N + 1) ** 3
+    flops_cell = (N + 1) * NS * 2 * (18 * nn + 24) + N * NS * 27 + 6 * nn * nn * 9 * 2 * nn
+    ck = out["ck"]
+    ck["predictor_tflops"] = flops_cell * n ** 3 / (ck["predictor_ms"] * 1e-3) / 1e12
+    ck["predictor_flops_per_cell"] = flops_cell
+    ck["predictor_frac_of_fp64_peak"] = ck["predictor_tflops"] * 1e12 / FP64_PEAK
+    out["ck_speedup_vs_fp64_picard"] = out["fp64"]["ms_per_step"] / ck["ms_per_step"]
+    out["ck_speedup_vs_mixed_picard"] = out["mixed"]["ms_per_step"] / ck["ms_per_step"]
+    # the two predictors differ by their O(dt^(N+1)) truncation (a difference, not an error)
+    out["ck_vs_picard_fp64_rel_linf"] = (finals["ck"] - finals["fp64"]).abs().max().item() / scale
     return out
 
 
@@ -496,6 +515,8 @@ def main():
                     help="steps after which the error against the exact solution is measured")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--extras", default="",
+                    help="comma list of the other workloads to run (default: all of them)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads (2-D Euler, elastic, explosion, ensemble)")
     args = ap.parse_args()
@@ -623,6 +644,8 @@ def main():
         for name, fn in (("euler2d_p3_27", extra_euler2d), ("explosion3d_p3_64", extra_explosion),
                          ("elastic3d_p5_81", extra_elastic), ("ensemble16_elastic_p4", extra_ensemble),
                          ("adjoint_elastic3d_p4_40", extra_adjoint)):
+            if args.extras and name not in args.extras.split(","):
+                continue
             try:
                 extra[name] = fn(ader, synth, stream)
             except Exception as exc:  # report, keep the headline line

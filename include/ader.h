@@ -68,6 +68,17 @@ typedef enum { ADER_BC_PERIODIC = 0, ADER_BC_WALL = 1, ADER_BC_ABSORBING = 2 } a
  *          binary32 enclosure cannot rule out; dt equals the FP64 form's on the same state). */
 typedef enum { ADER_PREC_FP64 = 0, ADER_PREC_MIXED = 1 } ader_prec;
 
+/* Space-time predictor of Sec. 3.3:
+ *  PICARD - the element-local space-time system Eq. (5) solved by picard_iters fixed-point
+ *           iterations (every PDE);
+ *  CK     - the Cauchy-Kowalevski procedure of linear PDEs (Sec. 2, Sec. 3.3): the local Taylor
+ *           series in time about t^n, cut after degree N, whose time derivatives are repeated
+ *           applications of the spatial operator; a point source's time factor enters through
+ *           its degree-N interpolant at the step's Gauss-Legendre time nodes.  Built for the
+ *           3-D elastic family with ADER_PREC_FP64 (others: ADER_EUNSUPPORTED).  Not
+ *           differentiated: the adjoint entry points return ADER_EUNSUPPORTED for it. */
+typedef enum { ADER_PREDICTOR_PICARD = 0, ADER_PREDICTOR_CK = 1 } ader_predictor;
+
 typedef struct {
   int dim;             /* 2 or 3 (elastic: 3) */
   int order;           /* polynomial order N >= 1 (n = N+1 nodes per direction) */
@@ -82,6 +93,7 @@ typedef struct {
   int limiter;         /* a-posteriori FV subcell limiter (Euler, order <= 4): 0 off, 1 on,
                           2 every cell troubled (the pure FV scheme, for tests) */
   int precision;       /* ader_prec */
+  int predictor;       /* ader_predictor (0 = Picard) */
 } ader_config;
 
 /* Create a context on the current CUDA device.  `cuda_stream` is a cudaStream_t (NULL = the

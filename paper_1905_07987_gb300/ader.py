@@ -17,6 +17,7 @@ OK, EINVAL, ENOMEM, ECUDA, ESTATE, ENONFINITE, EADMISSIBLE, ETIMEOUT, EUNSUPPORT
 PDE = {"advection": 0, "euler": 1, "elastic": 2}
 BC = {"periodic": 0, "wall": 1, "absorbing": 2}
 PREC = {"fp64": 0, "mixed": 1}
+PREDICTOR = {"picard": 0, "ck": 1}
 
 
 class AderError(RuntimeError):
@@ -40,6 +41,7 @@ class Config(ctypes.Structure):
         ("picard_iters", ctypes.c_int),
         ("limiter", ctypes.c_int),
         ("precision", ctypes.c_int),
+        ("predictor", ctypes.c_int),
     ]
 
 
@@ -141,7 +143,7 @@ def _ptr(a, dtype=np.float64):
 
 
 def make_config(pde, dim, order, ncell, lo, hi, bc, cfl, gamma=1.4, adv=(0.0, 0.0, 0.0),
-                picard_iters=0, limiter=False, precision="fp64"):
+                picard_iters=0, limiter=False, precision="fp64", predictor="picard"):
     c = Config()
     c.dim = dim
     c.order = order
@@ -163,6 +165,7 @@ def make_config(pde, dim, order, ncell, lo, hi, bc, cfl, gamma=1.4, adv=(0.0, 0.
     c.picard_iters = int(picard_iters)
     c.limiter = int(limiter)
     c.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+    c.predictor = PREDICTOR[predictor] if isinstance(predictor, str) else int(predictor)
     return c
 
 

@@ -41,6 +41,8 @@ struct Tables {
   double e0[MAXN], e1[MAXN];  // phi_m(0), phi_m(1)
   double c0[MAXN], c1[MAXN];  // e0/w, e1/w
   double pz[3], pw[3];        // 3-point Gauss-Legendre rule on [0,1] (path integral of B)
+  double Vi[MAXN][MAXN];      // Vi[k][t]: coefficient of tau^k of the Lagrange polynomial of
+                              // time node t (interpolant -> monomial coefficients)
 };
 
 // Single-precision and float-float copies of the tables for the mixed-precision predictor.
@@ -157,6 +159,9 @@ struct Family {
   // step arguments of this step in device memory; null when the family has no batched path
   cudaError_t (*ens_step)(const StepArgs* runs, const EnsTable& E, const Tables& t,
                           const TablesF& f, int prec, int order, cudaStream_t s);
+  // Cauchy-Kowalevski predictor (linear systems; null otherwise): same outputs as `predictor`
+  cudaError_t (*predictor_ck)(const StepArgs&, const Tables&, const TablesF&, int prec,
+                              cudaStream_t);
 };
 cudaError_t launch_set_scalars(DevScalars* d, double t, double dt, cudaStream_t s);
 cudaError_t launch_sub(const double* a, const double* b, double* out, int n, cudaStream_t s);

@@ -180,6 +180,20 @@ bool build_tables(int order, Tables& T) {
     T.pz[i] = pz[i];
     T.pw[i] = pw[i];
   }
+  // monomial coefficients of the Lagrange polynomials of the time nodes, by expanding the
+  // products prod_{m != t} (tau - x_m) / (x_t - x_m) one factor at a time
+  for (int t = 0; t < n; ++t) {
+    double p[MAXN] = {1.0};
+    int deg = 0;
+    for (int m = 0; m < n; ++m) {
+      if (m == t) continue;
+      const double den = x[t] - x[m];
+      for (int k = deg + 1; k >= 0; --k)
+        p[k] = ((k > 0 ? p[k - 1] : 0.0) - x[m] * (k <= deg ? p[k] : 0.0)) / den;
+      ++deg;
+    }
+    for (int k = 0; k < n; ++k) T.Vi[k][t] = p[k];
+  }
   return true;
 }
 
@@ -442,6 +456,10 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
   const Family* fam = pick_family(cfg->pde, cfg->dim);
   if (!fam) return ADER_EUNSUPPORTED;
   if (cfg->precision != ADER_PREC_FP64 && cfg->precision != ADER_PREC_MIXED) return ADER_EUNSUPPORTED;
+  if (cfg->predictor != ADER_PREDICTOR_PICARD && cfg->predictor != ADER_PREDICTOR_CK) return ADER_EINVAL;
+  if (cfg->predictor == ADER_PREDICTOR_CK &&
+      (!fam->predictor_ck || cfg->precision != ADER_PREC_FP64 || cfg->limiter))
+    return ADER_EUNSUPPORTED;
   // the predictor keeps a cell in shared memory: at most 227 KB per block on sm_103a, less the
   // kernel's static tables (the 3-D Euler mixed form at order 6 does not fit)
   if (fam->predictor_smem(cfg->order, cfg->precision) > 232448 - 4096) return ADER_EUNSUPPORTED;
@@ -792,7 +810,11 @@ static ader_status step_impl(ader_ctx* c, double dt, double t_end) {
   if ((st = mark(c, 1)) != ADER_OK) return st;
   CUDA_OK(launch_dt_finalize(a, s));
   if ((st = mark(c, 2)) != ADER_OK) return st;
-  CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, c->cfg.precision, s));
+  if (c->cfg.predictor == ADER_PREDICTOR_CK) {
+    CUDA_OK(c->fam->predictor_ck(a, c->tab, c->tabf, c->cfg.precision, s));
+  } else {
+    CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, c->cfg.precision, s));
+  }
   if ((st = mark(c, 3)) != ADER_OK) return st;
   CUDA_OK(c->fam->riemann(a, c->tab, s));
   if ((st = mark(c, 4)) != ADER_OK) return st;
@@ -879,6 +901,7 @@ ader_status ader_adjoint_step(ader_ctx* c, double t_n, double dt, const double* 
                               const double* dJdu, double* grad_mat, double* grad_M) {
   if (!c || !u_n || !lam || !grad_mat || !grad_M || !(dt > 0.0)) return ADER_EINVAL;
   if (c->cfg.pde != ADER_PDE_ELASTIC || !c->fam->adj_run) return ADER_EUNSUPPORTED;
+  if (c->cfg.predictor != ADER_PREDICTOR_PICARD) return ADER_EUNSUPPORTED;
   if (c->cfg.order > 5) return ADER_EUNSUPPORTED;
   if (!c->mat_set) return ADER_ESTATE;
   const int iters = c->cfg.picard_iters > 0 ? c->cfg.picard_iters : c->cfg.order + 1;
@@ -941,6 +964,7 @@ ader_status ader_adjoint_step_static(ader_ctx* c, double t_n, double dt, const d
                                      double* grad_M) {
   if (!c || !u_n || !lam || !grad_mat || !grad_M || !(dt > 0.0)) return ADER_EINVAL;
   if (c->cfg.pde != ADER_PDE_ELASTIC || !c->fam->adj_run) return ADER_EUNSUPPORTED;
+  if (c->cfg.predictor != ADER_PREDICTOR_PICARD) return ADER_EUNSUPPORTED;
   if (c->cfg.order > 5) return ADER_EUNSUPPORTED;
   if (!c->mat_set) return ADER_ESTATE;
   int dev = 0;
@@ -1001,6 +1025,7 @@ ader_status ader_misfit_gradient(ader_ctx* c, const double* u0, double t0, doubl
                                  double* grad_M) {
   if (!c || !u0 || !obs || !J || steps < 1 || k_ckpt < 1 || !(dt > 0.0)) return ADER_EINVAL;
   if (c->cfg.pde != ADER_PDE_ELASTIC) return ADER_EUNSUPPORTED;
+  if (c->cfg.predictor != ADER_PREDICTOR_PICARD) return ADER_EUNSUPPORTED;
   if (!c->mat_set || c->rec.nrec <= 0) return ADER_ESTATE;
   const size_t nd = (size_t)c->ndof;
   const int nrec = c->rec.nrec;
@@ -1157,6 +1182,7 @@ static bool ens_batchable(const ader_ensemble* e, double dt) {
   if (!a->fam->ens_step || a->cfg.order > 5) return false;
   for (const ader_ctx* c : e->runs) {
     if (c->fam != a->fam || c->cfg.order != a->cfg.order || c->cfg.precision != a->cfg.precision ||
+        c->cfg.predictor != ADER_PREDICTOR_PICARD ||
         c->cfg.limiter || c->rec.nrec > 0 || c->p.gamma != a->p.gamma)
       return false;
     for (int d = 0; d < 3; ++d)

@@ -1,4 +1,5 @@
-// Kernel family: linear elasticity in 3D, orders 1-6, with the adjoint step (orders 1-5).
+// Kernel family: linear elasticity in 3D, orders 1-6, with the adjoint step (orders 1-5) and the
+// Cauchy-Kowalevski predictor (orders 1-6).
 #include "kernels.cuh"
 
 namespace ader {
@@ -7,6 +8,8 @@ cudaError_t ens_step_elastic3_fp64(const StepArgs* R, const EnsTable& E, const T
                                    const TablesF& F, int order, cudaStream_t s);
 cudaError_t ens_step_elastic3_mixed(const StepArgs* R, const EnsTable& E, const Tables& T,
                                     const TablesF& F, int order, cudaStream_t s);
+cudaError_t predictor_ck_elastic3(const StepArgs& a, const Tables& t, const TablesF& f, int prec,
+                                  cudaStream_t s);
 template <int N>
 cudaError_t adj_run_n(const StepArgs& a, const AdjArgs& j, const Tables& t, int blocks, cudaStream_t s);
 template <int N>
@@ -59,6 +62,7 @@ const Family* family_elastic3() {
     g.adj_scratch_per_block = &adj_scratch;
     g.adj_blocks_per_sm = &adj_bps;
     g.ens_step = &ens_step;
+    g.predictor_ck = &predictor_ck_elastic3;
     return g;
   }();
   return &f;

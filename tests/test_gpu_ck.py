@@ -1,0 +1,179 @@
+"""GPU parity of the Cauchy-Kowalevski predictor of the 3-D elastic family (Sec. 2, Sec. 3.3: the
+predictor of linear PDEs evaluated by the Cauchy-Kowalevski procedure) against the oracle's
+Cauchy-Kowalevski step, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+from cases import Case, rel_linf
+from oracle.aderdg import ADERDG, Grid, PointSource
+from oracle.pde import Elastic
+from paper_1905_07987_gb300 import ader, synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def waves(X, L):
+    """Four superposed plane waves (P along x; S along x, y and z): all nine components vary."""
+    m = (2.7, 30.0, 25.0)
+    return (synth.plane_wave_elastic(X, m, kind='p', L=L)
+            + synth.plane_wave_elastic(X, m, kind='s', L=L / 2)
+            + synth.plane_wave_elastic(X, m, kind='s', direction=(0.0, 1.0, 0.0), L=L / 3)
+            + synth.plane_wave_elastic(X, m, kind='s', direction=(0.0, 0.0, 1.0), L=L / 2))
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5, 6])
+def test_ck_elastic_step_with_source(order):
+    """Absorbing boundaries, seeded material, point source, random state.  45 cells: the orders
+    that put 16, 4 or 2 cells in one block (1-3) end on a ragged block."""
+    ncell = (5, 3, 3)
+    mat = synth.elastic_material(ncell, seed=order)
+    c = Case("elastic", 3, order, ncell, hi=(2.5, 1.5, 1.5), bc="absorbing", material=mat,
+             predictor="ck")
+    rng = np.random.default_rng(100 + order)
+    u0 = rng.standard_normal(c.shape)
+    c.point_source((1.3, 0.7, 0.8), synth.moment_tensor(seed=7), 2.0, 0.5)
+    c.set(u0)
+    c.ctx.set_time(0.37)
+    c.ctx.step()
+    dt = c.ctx.last_dt()
+    assert rel_linf(c.get(), c.oracle_step(u0, dt, 0.37)) <= TOL
+
+
+def test_ck_periodic_multistep_and_receivers():
+    ncell = (4, 3, 3)
+    mat = synth.elastic_material(ncell, seed=12)
+    c = Case("elastic", 3, 4, ncell, hi=(2.0, 1.5, 1.5), bc="periodic", material=mat,
+             predictor="ck")
+    u0 = waves(c.X, 1.5)
+    pts = synth.receivers_top(ncell, c.lo, c.hi, nside=3)
+    seismo = c.receivers(pts, 8)
+    c.point_source((0.9, 0.8, 0.7), synth.moment_tensor(seed=3), 2.0, 0.5)
+    c.set(u0)
+    c.ctx.set_time(0.4)
+    u = torch.from_numpy(u0)
+    t = 0.4
+    rec = []
+    for _ in range(6):
+        dt = float(c.oracle.cfl_dt(u))
+        u = c.oracle.step(u, torch.tensor(dt, dtype=torch.float64), t)
+        t += dt
+        rec.append(c.oracle.record(u).numpy())
+    c.ctx.run(6)
+    assert rel_linf(c.get(), u.numpy()) <= 10 * TOL
+    got = seismo[:6].cpu().numpy()
+    ref = np.stack(rec)
+    assert np.abs(got - ref).max() <= 10 * TOL * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_ck_and_picard_steps_agree_on_polynomial_data(order):
+    """Homogeneous material and data of total degree <= N: both predictors give the exact local
+    solution, so the CUDA Cauchy-Kowalevski and Picard steps agree (a check that does not go
+    through the oracle)."""
+    ncell = (3, 2, 2)
+    mat = np.tile(np.array([2.6, 28.0, 24.0]), (12, 1))
+    out = {}
+    for kind in ("picard", "ck"):
+        c = Case("elastic", 3, order, ncell, hi=(1.5, 1.0, 1.0), bc="absorbing", material=mat,
+                 predictor=kind)
+        X = c.X
+        rng = np.random.default_rng(5)
+        u0 = np.zeros(c.shape)
+        for v in range(9):
+            cf = rng.standard_normal(4)
+            u0[..., v] = (cf[0] + cf[1] * X[0] + cf[2] * X[1] * X[2] ** (order - 2)
+                          + cf[3] * X[2] ** order)
+        c.set(u0)
+        c.ctx.step(dt=2e-3)
+        out[kind] = c.get()
+    assert rel_linf(out["ck"], out["picard"]) <= 1e-11
+
+
+def test_ck_is_rejected_where_it_is_not_built():
+    cfg = ader.make_config("elastic", 3, 3, (2, 2, 2), (0,) * 3, (1,) * 3, "absorbing",
+                           synth.cfl_number(3), predictor="ck")
+    c = ader.Context(cfg)
+    c.set_material(torch.from_numpy(synth.elastic_material((2, 2, 2), seed=1).reshape(-1).copy()).cuda())
+    u = torch.zeros(c.count, dtype=torch.float64, device="cuda")
+    lam = torch.zeros_like(u)
+    gm = torch.zeros(8 * 3, dtype=torch.float64, device="cuda")
+    gM = torch.zeros(6, dtype=torch.float64, device="cuda")
+    for static in (False, True):
+        with pytest.raises(ader.AderError) as e:  # the adjoint differentiates the Picard predictor
+            c.adjoint_step(0.0, 1e-3, u, lam, gm, gM, static=static)
+        assert e.value.status == ader.EUNSUPPORTED
+    c.close()
+    mixed = ader.make_config("elastic", 3, 3, (2, 2, 2), (0,) * 3, (1,) * 3, "absorbing",
+                             synth.cfl_number(3), predictor="ck", precision="mixed")
+    with pytest.raises(ader.AderError) as e:
+        ader.Context(mixed)
+    assert e.value.status == ader.EUNSUPPORTED
+
+
+def test_ck_full_size_sampled_cells_elastic_81():
+    """81^3 cells at order 5, the benchmark's elastic workload (seeded material, absorbing
+    boundaries, Ricker moment-tensor source at the centre) with a smooth wave state, in the launch
+    configuration the benchmark times.  Sampled cells (the source cell, a face neighbour of it,
+    corners of the interior and random ones) are checked against the oracle's Cauchy-Kowalevski
+    step on their 3x3x3 neighbourhood (a cell's update depends only on itself and its face
+    neighbours)."""
+    N, n, h = 5, 81, 0.5
+    L = n * h
+    x, _ = ader.reference_nodes(N)
+    matn = synth.elastic_material((n,) * 3, seed=1905)
+    M = synth.moment_tensor()
+    cfg = ader.make_config("elastic", 3, N, (n,) * 3, (0,) * 3, (L,) * 3, "absorbing",
+                           synth.cfl_number(N), predictor="ck")
+    ctx = ader.Context(cfg)
+    ctx.set_material(torch.from_numpy(matn.reshape(-1).copy()).cuda())
+    ctx.set_point_source((L / 2,) * 3, M, 2.0, 0.5)
+    slab_cache = {}
+
+    def slab(k):  # the state of the cells of layer k, [n*n, 6, 6, 6, 9]
+        if k not in slab_cache:
+            X = synth.node_coordinates(x, (n, n, 1), (0.0, 0.0, k * h), (L, L, (k + 1) * h))
+            slab_cache[k] = waves(X, L)
+        return slab_cache[k]
+
+    per = n * n * 216 * 9
+    u = torch.empty(ctx.count, dtype=torch.float64, device="cuda")
+    for k in range(n):
+        u[k * per:(k + 1) * per].copy_(torch.from_numpy(slab(k).reshape(-1)))
+        if k > 2:
+            slab_cache.pop(k - 3, None)
+    ctx.set_state(u)
+    del u
+    slab_cache.clear()
+    ctx.set_time(0.45)
+    ctx.step()
+    dt = ctx.last_dt()
+    got = torch.empty(ctx.count, dtype=torch.float64, device="cuda")
+    ctx.get_state(got)
+    torch.cuda.synchronize()
+    got = got.view(n ** 3, -1)
+    sc, sxi = synth.locate((L / 2,) * 3, (n,) * 3, (0.0,) * 3, (L,) * 3)
+    si, sj, sk = sc % n, (sc // n) % n, sc // (n * n)
+    rng = np.random.default_rng(0)
+    samples = [(si, sj, sk), (si + 1, sj, sk), (1, 1, 1), (79, 79, 79), (40, 7, 63)]
+    samples += [tuple(int(v) for v in rng.integers(1, 80, 3)) for _ in range(3)]
+    for (i, j, k) in samples:
+        idx, loc = [], []
+        for dk in (-1, 0, 1):
+            for dj in (-1, 0, 1):
+                for di in (-1, 0, 1):
+                    idx.append((i + di) + n * ((j + dj) + n * (k + dk)))
+                    loc.append(slab(k + dk)[(i + di) + n * (j + dj)])
+        sub = ADERDG(Elastic(), Grid((3, 3, 3), ((i - 1) * h, (j - 1) * h, (k - 1) * h),
+                                     ((i + 2) * h, (j + 2) * h, (k + 2) * h),
+                                     [("periodic", "periodic")] * 3), N,
+                     cfl=synth.cfl_number(N), material=torch.from_numpy(matn[idx]), predictor="ck")
+        if sc in idx:
+            sub.set_point_source(PointSource(idx.index(sc), sxi, torch.tensor(M), 2.0, 0.5))
+        out = sub.step(torch.from_numpy(np.stack(loc)), torch.tensor(dt, dtype=torch.float64),
+                       0.45).numpy()
+        centre = i + n * (j + n * k)
+        g = got[centre].cpu().numpy().reshape(out[13].shape)
+        assert rel_linf(g, out[13]) <= TOL, (i, j, k)
+    ctx.close()

@@ -263,20 +263,20 @@ def extra_euler2d(ader, synth, stream):
             "ms_total": ms, "l2_rho_vs_exact": l2, "linf_rho_vs_exact": linf, "dtype": "f64"}
 
 
-def extra_elastic(ader, synth, stream, steps=2, warmup=1):
+def extra_elastic(ader, synth, stream, steps=2, warmup=1, n=81):
     """3-D elastic, order 5, 81^3 cells (h = 0.5 km), seeded material, moment-tensor Ricker source
     at the centre, 64 receivers on the top face: FP64 and mixed predictor; mixed vs FP64 state."""
     import torch
-    N, n = 5, 81
+    N = 5
     L = 0.5 * n
     mat = torch.from_numpy(synth.elastic_material((n,) * 3, seed=1905).reshape(-1).copy()).cuda()
-    out = {"workload": "elastic3d_p5_81", "dofs": n ** 3 * 216 * 9}
+    out = {"workload": "elastic3d_p5_%d" % n, "dofs": n ** 3 * 216 * 9}
     finals = {}
-    for form in ("fp64", "mixed", "ck"):
-        prec = "mixed" if form == "mixed" else "fp64"
+    for form in ("fp64", "mixed", "ck", "ck_mixed"):
+        prec = "mixed" if form in ("mixed", "ck_mixed") else "fp64"
         cfg = ader.make_config("elastic", 3, N, (n,) * 3, (0, 0, 0), (L,) * 3, "absorbing",
                                synth.cfl_number(N), precision=prec,
-                               predictor="ck" if form == "ck" else "picard")
+                               predictor="ck" if form.startswith("ck") else "picard")
         ctx = ader.Context(cfg, stream=stream.cuda_stream)
         ctx.set_material(mat)
         ctx.set_point_source((L / 2,) * 3, synth.moment_tensor(), 2.0, 0.5)
@@ -318,8 +318,15 @@ def extra_elastic(ader, synth, stream, steps=2, warmup=1):
     ck["predictor_tflops"] = flops_cell * n ** 3 / (ck["predictor_ms"] * 1e-3) / 1e12
     ck["predictor_flops_per_cell"] = flops_cell
     ck["predictor_frac_of_fp64_peak"] = ck["predictor_tflops"] * 1e12 / FP64_PEAK
+    # mixed form: the same algorithmic (FP64-equivalent) flops against the FP32 pipe
+    ckm = out["ck_mixed"]
+    ckm["predictor_tflops"] = flops_cell * n ** 3 / (ckm["predictor_ms"] * 1e-3) / 1e12
+    ckm["predictor_frac_of_fp32_peak"] = ckm["predictor_tflops"] * 1e12 / FP32_PEAK
     out["ck_speedup_vs_fp64_picard"] = out["fp64"]["ms_per_step"] / ck["ms_per_step"]
     out["ck_speedup_vs_mixed_picard"] = out["mixed"]["ms_per_step"] / ck["ms_per_step"]
+    out["ck_mixed_speedup_vs_fp64_ck"] = ck["ms_per_step"] / ckm["ms_per_step"]
+    out["ck_mixed_vs_fp64_ck_rel_linf"] = ((finals["ck_mixed"] - finals["ck"]).abs().max().item()
+                                           / max(finals["ck"].abs().max().item(), 1e-300))
     # the two predictors differ by their O(dt^(N+1)) truncation (a difference, not an error)
     out["ck_vs_picard_fp64_rel_linf"] = (finals["ck"] - finals["fp64"]).abs().max().item() / scale
     return out
@@ -517,6 +524,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--extras", default="",
                     help="comma list of the other workloads to run (default: all of them)")
+    ap.add_argument("--elastic-n", type=int, default=81,
+                    help="cells per side of the elastic workload (81; smaller for profiling)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads (2-D Euler, elastic, explosion, ensemble)")
     args = ap.parse_args()
@@ -647,7 +656,10 @@ def main():
             if args.extras and name not in args.extras.split(","):
                 continue
             try:
-                extra[name] = fn(ader, synth, stream)
+                if fn is extra_elastic:
+                    extra[name] = fn(ader, synth, stream, n=args.elastic_n)
+                else:
+                    extra[name] = fn(ader, synth, stream)
             except Exception as exc:  # report, keep the headline line
                 extra[name] = {"error": "%s: %s" % (type(exc).__name__, exc)}
             torch.cuda.empty_cache()

@@ -457,8 +457,7 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
   if (!fam) return ADER_EUNSUPPORTED;
   if (cfg->precision != ADER_PREC_FP64 && cfg->precision != ADER_PREC_MIXED) return ADER_EUNSUPPORTED;
   if (cfg->predictor != ADER_PREDICTOR_PICARD && cfg->predictor != ADER_PREDICTOR_CK) return ADER_EINVAL;
-  if (cfg->predictor == ADER_PREDICTOR_CK &&
-      (!fam->predictor_ck || cfg->precision != ADER_PREC_FP64 || cfg->limiter))
+  if (cfg->predictor == ADER_PREDICTOR_CK && (!fam->predictor_ck || cfg->limiter))
     return ADER_EUNSUPPORTED;
   // the predictor keeps a cell in shared memory: at most 227 KB per block on sm_103a, less the
   // kernel's static tables (the 3-D Euler mixed form at order 6 does not fit)

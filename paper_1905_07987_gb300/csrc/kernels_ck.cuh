@@ -17,8 +17,17 @@
 // velocities and the stresses sigma_{0d}, sigma_{1d}, sigma_{2d}) and combines them:
 // 18n + 24 FMA per node and application.  The Taylor coefficients ping-pong between two
 // shared-memory buffers of padded node records, 10 doubles per node, read in 16-byte pairs.
+//
+// Mixed-precision form (k_predictor_ck_mixed): only the O(1) base term L u carries the size of the
+// solution; it is formed once in float-float (hi + lo binary32 pairs, about 44 bits) and serves
+// both a_1 = dt (L u + g s_0) and the volume term.  a_1 is float-float; a_2 .. a_N (O(dt^2) and
+// smaller) and L applied to the increment of the time average run in binary32.  The time average
+// qbar = u + dbar (dbar = a_1/2 in float-float plus the binary32 sum of the higher terms), its
+// face extrapolations and the volume term L u + L dbar + g sbar are float-float, and
+// u_next = u + dt vol is formed in FP64.
 #pragma once
 #include "ader_internal.h"
+#include "ff.cuh"
 #include "pde.cuh"
 
 namespace ader {
@@ -251,6 +260,333 @@ cudaError_t launch_predictor_ck_n(const StepArgs& a, const Tables& t, cudaStream
   const long long blocks = (a.g.ncells + C::CPB - 1) / C::CPB;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   k_predictor_ck<N><<<(unsigned)blocks, C::TPB, C::SMEM, s>>>(a, t);
+  return cudaGetLastError();
+}
+
+// ---- mixed precision --------------------------------------------------------------------------
+
+template <int N>
+struct CfgCKM {
+  static constexpr int n = N + 1;
+  static constexpr int NS = n * n * n;
+  static constexpr int NV = 9;
+  static constexpr int NL = NS * NV;
+  static constexpr int NVQ = 10;  // float-float node record: 10 (hi, lo) pairs, 80 bytes
+  static constexpr int NVF = 12;  // binary32 node record: 12 floats, 48 bytes (float4 loads)
+  static constexpr int CPB = NS >= 96 ? 1 : 128 / NS;
+  static constexpr int TPB = (CPB * NS + 31) / 32 * 32;
+  static constexpr int NF = n * n;
+  // per cell: U (float-float state, then qbar) | A | B (binary32 Taylor coefficients); the
+  // float-float volume term is staged over A and B
+  static constexpr size_t OFF_A = (size_t)NS * NVQ * 8;
+  static constexpr size_t OFF_B = OFF_A + (size_t)NS * NVF * 4;
+  static constexpr size_t CELL = OFF_B + (size_t)NS * NVF * 4;
+  static constexpr size_t SMEM = CPB * CELL;
+};
+
+// Float-float R[v] += row v of -sum_d (1/h_d) B_d D_d U at node j (U: [NS][NVQ] (hi, lo) pairs).
+template <int N>
+__device__ __forceinline__ void ck_apply_ff(const float2* U, int j, const float (&Dh)[3][N + 1],
+                                            const float (&Dl)[3][N + 1], const ff (&cf)[3][4],
+                                            ff (&R)[9]) {
+  constexpr int n = N + 1, NVQ = CfgCKM<N>::NVQ;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
+    const int jd = (j / st) % n;
+    const float2* b = U + (j - jd * st) * NVQ;
+    const int s0 = Elastic::sig(0, d), s1 = Elastic::sig(1, d), s2 = Elastic::sig(2, d);
+    ff dv[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, ds[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      const float4* p = reinterpret_cast<const float4*>(b + m * st * NVQ);
+      float2 r[NVQ];
+#pragma unroll
+      for (int i = 0; i < NVQ / 2; ++i) {
+        const float4 v = p[i];
+        r[2 * i] = make_float2(v.x, v.y);
+        r[2 * i + 1] = make_float2(v.z, v.w);
+      }
+      const float ch = Dh[d][m], cl = Dl[d][m];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) ff_mac(dv[i], ch, cl, r[i].x, r[i].y);
+      ff_mac(ds[0], ch, cl, r[s0].x, r[s0].y);
+      ff_mac(ds[1], ch, cl, r[s1].x, r[s1].y);
+      ff_mac(ds[2], ch, cl, r[s2].x, r[s2].y);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ff_mac(R[i], cf[d][0].h, cf[d][0].l, ds[i].h, ds[i].l);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const ff& k = i == d ? cf[d][1] : cf[d][2];
+      ff_mac(R[3 + i], k.h, k.l, dv[d].h, dv[d].l);
+    }
+#pragma unroll
+    for (int v = 6; v < 9; ++v) {
+      const int s = Elastic::src(d, v);
+      if (s >= 0) ff_mac(R[v], cf[d][3].h, cf[d][3].l, dv[s].h, dv[s].l);
+    }
+  }
+}
+
+// Binary32 R[v] += row v of -sum_d (1/h_d) B_d D_d X at node j (X: [NS][NVF] floats).
+template <int N>
+__device__ __forceinline__ void ck_apply_f(const float* X, int j, const float (&Dh)[3][N + 1],
+                                           const ff (&cf)[3][4], float (&R)[9]) {
+  constexpr int n = N + 1, NVF = CfgCKM<N>::NVF;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
+    const int jd = (j / st) % n;
+    const float* b = X + (j - jd * st) * NVF;
+    const int s0 = Elastic::sig(0, d), s1 = Elastic::sig(1, d), s2 = Elastic::sig(2, d);
+    float dv0 = 0.f, dv1 = 0.f, dv2 = 0.f, ds0 = 0.f, ds1 = 0.f, ds2 = 0.f;
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      const float4* p = reinterpret_cast<const float4*>(b + m * st * NVF);
+      float r[NVF];
+#pragma unroll
+      for (int i = 0; i < NVF / 4; ++i) {
+        const float4 v = p[i];
+        r[4 * i] = v.x;
+        r[4 * i + 1] = v.y;
+        r[4 * i + 2] = v.z;
+        r[4 * i + 3] = v.w;
+      }
+      const float c = Dh[d][m];
+      dv0 = fmaf(c, r[0], dv0);
+      dv1 = fmaf(c, r[1], dv1);
+      dv2 = fmaf(c, r[2], dv2);
+      ds0 = fmaf(c, r[s0], ds0);
+      ds1 = fmaf(c, r[s1], ds1);
+      ds2 = fmaf(c, r[s2], ds2);
+    }
+    const float dv[3] = {dv0, dv1, dv2};
+    R[0] = fmaf(cf[d][0].h, ds0, R[0]);
+    R[1] = fmaf(cf[d][0].h, ds1, R[1]);
+    R[2] = fmaf(cf[d][0].h, ds2, R[2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) R[3 + i] = fmaf(i == d ? cf[d][1].h : cf[d][2].h, dv[d], R[3 + i]);
+#pragma unroll
+    for (int v = 6; v < 9; ++v) {
+      const int s = Elastic::src(d, v);
+      if (s >= 0) R[v] = fmaf(cf[d][3].h, dv[s], R[v]);
+    }
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(CfgCKM<N>::TPB)
+    k_predictor_ck_mixed(const __grid_constant__ StepArgs A, const __grid_constant__ Tables T,
+                         const __grid_constant__ TablesF F) {
+  using C = CfgCKM<N>;
+  constexpr int n = C::n, NS = C::NS, NV = C::NV, NL = C::NL, CPB = C::CPB, TPB = C::TPB;
+  constexpr int NVQ = C::NVQ, NVF = C::NVF, NF = C::NF, FR = NF * NV;
+  extern __shared__ __align__(16) unsigned char smem_ck[];  // [CPB][CELL]
+  const int tid = threadIdx.x;
+  const int slot = tid / NS;
+  const int j = tid - slot * NS;
+  const long long c0 = (long long)blockIdx.x * CPB;
+  const int ncb = (int)(A.g.ncells - c0 < CPB ? A.g.ncells - c0 : CPB);
+  const bool act = slot < ncb;
+  unsigned char* cell = smem_ck + (size_t)(act ? slot : 0) * C::CELL;
+  float2* U = reinterpret_cast<float2*>(cell);
+  float* XA = reinterpret_cast<float*>(cell + C::OFF_A);
+  float* XB = reinterpret_cast<float*>(cell + C::OFF_B);
+  float2* V = reinterpret_cast<float2*>(cell + C::OFF_A);  // volume term, over A and B
+  const double dt = A.dev->dt;
+  const double tn = A.dev->t;
+
+  // the block's cells, coalesced, split into float-float records
+  for (int e = tid; e < ncb * NL; e += TPB) {
+    const int s = e / NL, r = e - s * NL;
+    const ff x = ff_split(A.u[c0 * NL + e]);
+    reinterpret_cast<float2*>(smem_ck + (size_t)s * C::CELL)[(r / NV) * NVQ + r % NV] =
+        make_float2(x.h, x.l);
+  }
+
+  // per-cell coefficients {1/(rho h_d), (lam + 2 mu)/h_d, lam/h_d, mu/h_d} in float-float
+  __shared__ ff s_cf[CPB][3][4];
+  if (tid < ncb) {
+    const long long cc = c0 + tid;
+    const double irho = 1.0 / A.mat[cc * 3 + 0];
+    const double lam = A.mat[cc * 3 + 1];
+    const double mu = A.mat[cc * 3 + 2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double ih = A.g.inv_h[d];
+      s_cf[tid][d][0] = ff_split(irho * ih);
+      s_cf[tid][d][1] = ff_split((lam + 2.0 * mu) * ih);
+      s_cf[tid][d][2] = ff_split(lam * ih);
+      s_cf[tid][d][3] = ff_split(mu * ih);
+    }
+  }
+  // point source of the block, as in the FP64 kernel
+  __shared__ double s_sk[n], s_sbar;
+  __shared__ int s_slot;
+  const long long sc = A.src.cell - c0;
+  const bool srcb = sc >= 0 && sc < ncb;
+  if (srcb && tid == 0) {
+    double ric[n], sbar = 0.0;
+#pragma unroll
+    for (int t = 0; t < n; ++t) {
+      const double tau = fma(T.x[t], dt, tn) - A.src.t0;
+      const double a = (M_PI * A.src.f0 * tau) * (M_PI * A.src.f0 * tau);
+      ric[t] = (1.0 - 2.0 * a) * exp(-a);
+      sbar = fma(T.w[t], ric[t], sbar);
+    }
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      double s = 0.0;
+#pragma unroll
+      for (int t = 0; t < n; ++t) s = fma(T.Vi[k][t], ric[t], s);
+      s_sk[k] = s;
+    }
+    s_sbar = sbar;
+    s_slot = (int)sc;
+  }
+  __syncthreads();
+  const bool srcc = srcb && act && s_slot == slot;
+
+  float Dh[3][n], Dl[3][n];
+  ff cf[3][4];
+  ff LU[NV], dbar[NV];
+  const ff dtf = ff_split(dt);
+  if (act) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int jd = d == 0 ? j % n : (d == 1 ? (j / n) % n : j / (n * n));
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        Dh[d][m] = F.Dh[jd][m];
+        Dl[d][m] = F.Dl[jd][m];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) cf[d][i] = s_cf[slot][d][i];
+    }
+    // base term and a_1 = dt (L u + g s_0) in float-float; dbar starts at a_1 / 2
+#pragma unroll
+    for (int v = 0; v < NV; ++v) LU[v] = {0.f, 0.f};
+    ck_apply_ff<N>(U, j, Dh, Dl, cf, LU);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      ff t0 = LU[v];
+      if (srcc && v >= 3) t0 = ff_add(t0, ff_split(-A.src.M[v - 3] * A.src.phi[j] * s_sk[0]));
+      const ff a1 = ff_mul(dtf, t0);
+      dbar[v] = {0.5f * a1.h, 0.5f * a1.l};
+      XA[j * NVF + v] = a1.h;
+    }
+  }
+  __syncthreads();
+
+  // a_2 .. a_N in binary32; their share of dbar, sum_k a_k / (k+1), in binary32
+  float d32[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) d32[v] = 0.f;
+#pragma unroll
+  for (int k = 1; k < N; ++k) {
+    const float* Xc = (k & 1) ? XA : XB;
+    float* Xn = (k & 1) ? XB : XA;
+    if (act) {
+      float R[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) R[v] = 0.f;
+      ck_apply_f<N>(Xc, j, Dh, cf, R);
+      if (srcc) {
+        const float sk = (float)s_sk[k];
+#pragma unroll
+        for (int v = 3; v < NV; ++v) R[v] = fmaf((float)(-A.src.M[v - 3] * A.src.phi[j]), sk, R[v]);
+      }
+      const float f = dtf.h * (1.0f / (k + 1));
+      const float wk = 1.0f / (k + 2);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float a = f * R[v];
+        d32[v] = fmaf(wk, a, d32[v]);
+        Xn[j * NVF + v] = a;
+      }
+    }
+    __syncthreads();
+  }
+
+  // qbar = u + dbar (float-float, in place: after the base term only the owner reads its node);
+  // dbar's hi part into A for the binary32 L dbar
+  if (act) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      dbar[v] = ff_add(dbar[v], {d32[v], 0.f});
+      const float2 uu = U[j * NVQ + v];
+      const ff q = ff_add({uu.x, uu.y}, dbar[v]);
+      U[j * NVQ + v] = make_float2(q.h, q.l);
+      XA[j * NVF + v] = dbar[v].h;
+    }
+  }
+  __syncthreads();
+  ff vol[NV];
+  if (act) {
+    float R[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) R[v] = 0.f;
+    ck_apply_f<N>(XA, j, Dh, cf, R);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      vol[v] = ff_add(LU[v], {R[v], 0.f});
+      if (srcc && v >= 3) vol[v] = ff_add(vol[v], ff_split(-A.src.M[v - 3] * A.src.phi[j] * s_sbar));
+    }
+  }
+  __syncthreads();  // every read of A is done before the volume term overwrites it
+  if (act) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) V[j * NVQ + v] = make_float2(vol[v].h, vol[v].l);
+  }
+  __syncthreads();
+
+  // u_next = u + dt vol in FP64 (u again from L2), coalesced
+  for (int e = tid; e < ncb * NL; e += TPB) {
+    const int s = e / NL, r = e - s * NL;
+    const float2 w = reinterpret_cast<const float2*>(smem_ck + (size_t)s * C::CELL + C::OFF_A)
+        [(r / NV) * NVQ + r % NV];
+    A.u_next[c0 * NL + e] = fma(dt, (double)w.x + (double)w.y, A.u[c0 * NL + e]);
+  }
+
+  // face records: qbar extrapolated in float-float to both ends of every direction
+  constexpr int NFE = 3 * 2 * NF * NV;
+  for (int e = tid; e < ncb * NFE; e += TPB) {
+    const int s = e / NFE, r = e - s * NFE;
+    const int v = r % NV;
+    const int jp = (r / NV) % NF;
+    const int side = (r / (NV * NF)) % 2;
+    const int d = r / (NV * NF * 2);
+    const int st = (d == 0 ? 1 : (d == 1 ? n : n * n));
+    const int jbase = (jp % st) + (jp / st) * st * n;
+    const float* eh = side ? F.e1h : F.e0h;
+    const float* el = side ? F.e1l : F.e0l;
+    const float2* Us = reinterpret_cast<const float2*>(smem_ck + (size_t)s * C::CELL);
+    ff qf = {0.f, 0.f};
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      const float2 q = Us[(jbase + m * st) * NVQ + v];
+      ff_mac(qf, eh[m], el[m], q.x, q.y);
+    }
+    A.face[(c0 + s) * (3 * 2 * FR) + (d * 2 + side) * FR + jp * NV + v] =
+        (double)qf.h + (double)qf.l;
+  }
+}
+
+template <int N>
+cudaError_t launch_predictor_ck_mixed_n(const StepArgs& a, const Tables& t, const TablesF& f,
+                                        cudaStream_t s) {
+  using C = CfgCKM<N>;
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        k_predictor_ck_mixed<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const long long blocks = (a.g.ncells + C::CPB - 1) / C::CPB;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_predictor_ck_mixed<N><<<(unsigned)blocks, C::TPB, C::SMEM, s>>>(a, t, f);
   return cudaGetLastError();
 }
 

@@ -24,7 +24,10 @@
 // smaller) and L applied to the increment of the time average run in binary32.  The time average
 // qbar = u + dbar (dbar = a_1/2 in float-float plus the binary32 sum of the higher terms), its
 // face extrapolations and the volume term L u + L dbar + g sbar are float-float, and
-// u_next = u + dt vol is formed in FP64.
+// u_next = u + dt vol is formed in FP64.  The FP64 pipe, 1/64 of the FP32 rate, would otherwise
+// be the bound: the splits of u into float-float and the exact float -> double conversions of
+// the results run on the integer pipe, leaving one FP64 add per face value and an add and an FMA
+// per updated value.
 #pragma once
 #include "ader_internal.h"
 #include "ff.cuh"
@@ -400,7 +403,7 @@ __global__ void __launch_bounds__(CfgCKM<N>::TPB)
   // the block's cells, coalesced, split into float-float records
   for (int e = tid; e < ncb * NL; e += TPB) {
     const int s = e / NL, r = e - s * NL;
-    const ff x = ff_split(A.u[c0 * NL + e]);
+    const ff x = ff_split_int(A.u[c0 * NL + e]);
     reinterpret_cast<float2*>(smem_ck + (size_t)s * C::CELL)[(r / NV) * NVQ + r % NV] =
         make_float2(x.h, x.l);
   }
@@ -451,7 +454,7 @@ __global__ void __launch_bounds__(CfgCKM<N>::TPB)
   float Dh[3][n], Dl[3][n];
   ff cf[3][4];
   ff LU[NV], dbar[NV];
-  const ff dtf = ff_split(dt);
+  const ff dtf = ff_split_int(dt);
   if (act) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -546,7 +549,7 @@ __global__ void __launch_bounds__(CfgCKM<N>::TPB)
     const int s = e / NL, r = e - s * NL;
     const float2 w = reinterpret_cast<const float2*>(smem_ck + (size_t)s * C::CELL + C::OFF_A)
         [(r / NV) * NVQ + r % NV];
-    A.u_next[c0 * NL + e] = fma(dt, (double)w.x + (double)w.y, A.u[c0 * NL + e]);
+    A.u_next[c0 * NL + e] = fma(dt, f2d_int(w.x) + f2d_int(w.y), A.u[c0 * NL + e]);
   }
 
   // face records: qbar extrapolated in float-float to both ends of every direction
@@ -569,7 +572,7 @@ __global__ void __launch_bounds__(CfgCKM<N>::TPB)
       ff_mac(qf, eh[m], el[m], q.x, q.y);
     }
     A.face[(c0 + s) * (3 * 2 * FR) + (d * 2 + side) * FR + jp * NV + v] =
-        (double)qf.h + (double)qf.l;
+        f2d_int(qf.h) + f2d_int(qf.l);
   }
 }
 

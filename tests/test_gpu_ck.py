@@ -69,6 +69,24 @@ def test_ck_mixed_step_with_source(order):
     assert change_rel(c.get(), ref, u0) < 2e-6
 
 
+def test_ck_mixed_wide_magnitudes():
+    """State values from 1e-40 to 1e3 and exact zeros: the float-float splits of the mixed form
+    (integer-pipe bit operations, binary32 range) keep the step within the same bound."""
+    ncell = (3, 3, 2)
+    mat = synth.elastic_material(ncell, seed=9)
+    c = Case("elastic", 3, 4, ncell, hi=(1.5, 1.5, 1.0), bc="absorbing", material=mat,
+             predictor="ck", precision="mixed")
+    rng = np.random.default_rng(31)
+    u0 = rng.standard_normal(c.shape) * 10.0 ** rng.uniform(-40, 3, c.shape)
+    u0[rng.random(c.shape) < 0.1] = 0.0
+    c.set(u0)
+    c.ctx.step()
+    got = c.get()
+    assert np.isfinite(got).all()
+    ref = c.oracle_step(u0, c.ctx.last_dt())
+    assert change_rel(got, ref, u0) < 2e-6
+
+
 def test_ck_periodic_multistep_and_receivers():
     ncell = (4, 3, 3)
     mat = synth.elastic_material(ncell, seed=12)

@@ -519,23 +519,28 @@ __device__ __forceinline__ void riemann_face(const StepArgs& A, const Tables& T,
   double s;
   double cb[NV];
   if constexpr (P::NCP) {
+    // the face's speed and path-averaged coefficients depend only on the two cells' materials:
+    // lane v < NV forms cb[v], lane NV the speed, and the warp shares them (the divisions and
+    // square roots are not repeated on every lane)
     const long long mcL = cL >= 0 ? cL : cR, mcR = cR >= 0 ? cR : cL;
     const double rL = A.mat[mcL * 3], lL = A.mat[mcL * 3 + 1], uL = A.mat[mcL * 3 + 2];
     const double rR = A.mat[mcR * 3], lR = A.mat[mcR * 3 + 1], uR = A.mat[mcR * 3 + 2];
-    const double sL = Elastic::vp(rL, lL, uL), sR = Elastic::vp(rR, lR, uR);
-    s = (sL >= sR) ? sL : sR;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      double acc = 0.0;
+    double mine = 0.0;
+    if (lane < NV) {
 #pragma unroll
       for (int gq = 0; gq < 3; ++gq) {
         const double z = T.pz[gq];
-        acc = fma(T.pw[gq],
-                  Elastic::coef(d, v, fma(z, rR - rL, rL), fma(z, lR - lL, lL), fma(z, uR - uL, uL)),
-                  acc);
+        mine = fma(T.pw[gq],
+                   Elastic::coef(d, lane, fma(z, rR - rL, rL), fma(z, lR - lL, lL), fma(z, uR - uL, uL)),
+                   mine);
       }
-      cb[v] = acc;
+    } else if (lane == NV) {
+      const double sL = Elastic::vp(rL, lL, uL), sR = Elastic::vp(rR, lR, uR);
+      mine = (sL >= sR) ? sL : sR;
     }
+    s = __shfl_sync(0xffffffffu, mine, NV);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) cb[v] = __shfl_sync(0xffffffffu, mine, v);
   } else if constexpr (P::LINEAR) {
     s = fabs(A.p.a[d]);
   } else {
@@ -552,8 +557,14 @@ __device__ __forceinline__ void riemann_face(const StepArgs& A, const Tables& T,
       for (int v = 0; v < NV; ++v) {
         const double G = 0.5 * (FL[r][v] + FR_[r][v]) - 0.5 * s * (qR[r][v] - qL[r][v]);
         if constexpr (P::NCP) {
-          const int sv = Elastic::src(d, v);
-          const double half = sv >= 0 ? 0.5 * cb[v] * (qR[r][sv] - qL[r][sv]) : 0.0;
+          // source variable of row v of B_d, chosen among the three compile-time candidates (the
+          // direction d is a run-time value: no dynamic register indexing)
+          const int s0 = Elastic::src(0, v), s1 = Elastic::src(1, v), s2 = Elastic::src(2, v);
+          const double j0 = s0 >= 0 ? qR[r][s0 < 0 ? 0 : s0] - qL[r][s0 < 0 ? 0 : s0] : 0.0;
+          const double j1 = s1 >= 0 ? qR[r][s1 < 0 ? 0 : s1] - qL[r][s1 < 0 ? 0 : s1] : 0.0;
+          const double j2 = s2 >= 0 ? qR[r][s2 < 0 ? 0 : s2] - qL[r][s2 < 0 ? 0 : s2] : 0.0;
+          const double jump = d == 0 ? j0 : (d == 1 ? j1 : j2);
+          const double half = 0.5 * cb[v] * jump;
           out[jp * NV + v] = G + half;
           out[NF * NV + jp * NV + v] = G - half;
         } else {

@@ -231,22 +231,27 @@ __global__ void __launch_bounds__(CfgCK<N>::TPB) k_predictor_ck(const __grid_con
     A.u_next[c0 * NL + e] = fma(dt, Xs[(r / NV) * NVP + r % NV], A.u[c0 * NL + e]);
   }
 
-  // face records: qbar extrapolated to both ends of every direction
-  constexpr int NFE = 3 * 2 * NF * NV;
-  for (int e = tid; e < ncb * NFE; e += TPB) {
-    const int s = e / NFE, r = e - s * NFE;
-    const int v = r % NV;
-    const int jp = (r / NV) % NF;
-    const int side = (r / (NV * NF)) % 2;
-    const int d = r / (NV * NF * 2);
-    const int st = (d == 0 ? 1 : (d == 1 ? n : n * n));
-    const int jbase = (jp % st) + (jp / st) * st * n;
-    const double* ev = side ? T.e1 : T.e0;
+  // face records: qbar extrapolated to both ends of every direction (both ends from one read
+  // of the line; the direction loop is unrolled so that every index divisor is a constant)
+  for (int e = tid; e < ncb * NF * NV; e += TPB) {
+    const int s = e / (NF * NV), r = e - s * (NF * NV);
+    const int v = r % NV, jp = r / NV;
     const double* Xs = smem + (size_t)s * 2 * REC + (((N - 1) & 1) ? REC : 0);
-    double qf = 0.0;
+    double* fc = A.face + (c0 + s) * (3 * 2 * FR) + jp * NV + v;
 #pragma unroll
-    for (int m = 0; m < n; ++m) qf = fma(ev[m], Xs[(jbase + m * st) * NVP + v], qf);
-    A.face[(c0 + s) * (3 * 2 * FR) + (d * 2 + side) * FR + jp * NV + v] = qf;
+    for (int d = 0; d < 3; ++d) {
+      const int st = (d == 0 ? 1 : (d == 1 ? n : n * n));
+      const int jbase = (jp % st) + (jp / st) * st * n;
+      double q0 = 0.0, q1 = 0.0;
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        const double x = Xs[(jbase + m * st) * NVP + v];
+        q0 = fma(T.e0[m], x, q0);
+        q1 = fma(T.e1[m], x, q1);
+      }
+      fc[(d * 2 + 0) * FR] = q0;
+      fc[(d * 2 + 1) * FR] = q1;
+    }
   }
 }
 
@@ -552,27 +557,27 @@ __global__ void __launch_bounds__(CfgCKM<N>::TPB)
     A.u_next[c0 * NL + e] = fma(dt, f2d_int(w.x) + f2d_int(w.y), A.u[c0 * NL + e]);
   }
 
-  // face records: qbar extrapolated in float-float to both ends of every direction
-  constexpr int NFE = 3 * 2 * NF * NV;
-  for (int e = tid; e < ncb * NFE; e += TPB) {
-    const int s = e / NFE, r = e - s * NFE;
-    const int v = r % NV;
-    const int jp = (r / NV) % NF;
-    const int side = (r / (NV * NF)) % 2;
-    const int d = r / (NV * NF * 2);
-    const int st = (d == 0 ? 1 : (d == 1 ? n : n * n));
-    const int jbase = (jp % st) + (jp / st) * st * n;
-    const float* eh = side ? F.e1h : F.e0h;
-    const float* el = side ? F.e1l : F.e0l;
+  // face records: qbar extrapolated in float-float to both ends of every direction (both ends
+  // from one read of the line; constant index divisors)
+  for (int e = tid; e < ncb * NF * NV; e += TPB) {
+    const int s = e / (NF * NV), r = e - s * (NF * NV);
+    const int v = r % NV, jp = r / NV;
     const float2* Us = reinterpret_cast<const float2*>(smem_ck + (size_t)s * C::CELL);
-    ff qf = {0.f, 0.f};
+    double* fc = A.face + (c0 + s) * (3 * 2 * FR) + jp * NV + v;
 #pragma unroll
-    for (int m = 0; m < n; ++m) {
-      const float2 q = Us[(jbase + m * st) * NVQ + v];
-      ff_mac(qf, eh[m], el[m], q.x, q.y);
+    for (int d = 0; d < 3; ++d) {
+      const int st = (d == 0 ? 1 : (d == 1 ? n : n * n));
+      const int jbase = (jp % st) + (jp / st) * st * n;
+      ff q0 = {0.f, 0.f}, q1 = {0.f, 0.f};
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        const float2 q = Us[(jbase + m * st) * NVQ + v];
+        ff_mac(q0, F.e0h[m], F.e0l[m], q.x, q.y);
+        ff_mac(q1, F.e1h[m], F.e1l[m], q.x, q.y);
+      }
+      fc[(d * 2 + 0) * FR] = f2d_int(q0.h) + f2d_int(q0.l);
+      fc[(d * 2 + 1) * FR] = f2d_int(q1.h) + f2d_int(q1.l);
     }
-    A.face[(c0 + s) * (3 * 2 * FR) + (d * 2 + side) * FR + jp * NV + v] =
-        f2d_int(qf.h) + f2d_int(qf.l);
   }
 }
 

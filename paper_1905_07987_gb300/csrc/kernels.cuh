@@ -477,6 +477,53 @@ __device__ __forceinline__ void riemann_face(const StepArgs& A, const Tables& T,
     }
   }
 
+  // elastic: the face's speed and path-averaged coefficients depend only on the two cells'
+  // materials: lane v < NV forms cb[v], lane NV the speed, and the warp shares them (the
+  // divisions and square roots are not repeated on every lane)
+  double s_ncp = 0.0, mine_ncp = 0.0;
+  if constexpr (P::NCP) {
+    const long long mcL = cL >= 0 ? cL : cR, mcR = cR >= 0 ? cR : cL;
+    const double rL = A.mat[mcL * 3], lL = A.mat[mcL * 3 + 1], uL = A.mat[mcL * 3 + 2];
+    const double rR = A.mat[mcR * 3], lR = A.mat[mcR * 3 + 1], uR = A.mat[mcR * 3 + 2];
+    if (lane < NV) {
+#pragma unroll
+      for (int gq = 0; gq < 3; ++gq) {
+        const double z = T.pz[gq];
+        mine_ncp = fma(T.pw[gq],
+                       Elastic::coef(d, lane, fma(z, rR - rL, rL), fma(z, lR - lL, lL), fma(z, uR - uL, uL)),
+                       mine_ncp);
+      }
+    } else if (lane == NV) {
+      const double sL = Elastic::vp(rL, lL, uL), sR = Elastic::vp(rR, lR, uR);
+      mine_ncp = (sL >= sR) ? sL : sR;
+    }
+    s_ncp = __shfl_sync(0xffffffffu, mine_ncp, NV);
+    // interior face: the flux is elementwise over the face's NF x NV values, so the lanes walk
+    // them contiguously (coalesced); each lane takes the jump of its row's source variable from
+    // the same records and its coefficient from lane v
+    if (recL && recR) {
+      constexpr int PE = (NF * NV + 31) / 32;
+      double* out = A.phi + phi_off + f * (long long)(NPHI * NF * NV);
+#pragma unroll
+      for (int r = 0; r < PE; ++r) {
+        const int e = lane + 32 * r;
+        const int v = e % NV;
+        const double cbv = __shfl_sync(0xffffffffu, mine_ncp, v);
+        if (e < NF * NV) {
+          const int sv = Elastic::src(d, v);
+          const int es = e - v + (sv < 0 ? 0 : sv);
+          const double dq = recR[e] - recL[e];
+          const double jump = sv >= 0 ? recR[es] - recL[es] : 0.0;
+          const double G = 0.5 * (0.0 + 0.0) - 0.5 * s_ncp * dq;
+          const double half = 0.5 * cbv * jump;
+          out[e] = G + half;
+          out[NF * NV + e] = G - half;
+        }
+      }
+      return;
+    }
+  }
+
   double qL[PER][NV], qR[PER][NV], FL[PER][NV], FR_[PER][NV];
   double smax = 0.0;
 #pragma unroll
@@ -519,28 +566,9 @@ __device__ __forceinline__ void riemann_face(const StepArgs& A, const Tables& T,
   double s;
   double cb[NV];
   if constexpr (P::NCP) {
-    // the face's speed and path-averaged coefficients depend only on the two cells' materials:
-    // lane v < NV forms cb[v], lane NV the speed, and the warp shares them (the divisions and
-    // square roots are not repeated on every lane)
-    const long long mcL = cL >= 0 ? cL : cR, mcR = cR >= 0 ? cR : cL;
-    const double rL = A.mat[mcL * 3], lL = A.mat[mcL * 3 + 1], uL = A.mat[mcL * 3 + 2];
-    const double rR = A.mat[mcR * 3], lR = A.mat[mcR * 3 + 1], uR = A.mat[mcR * 3 + 2];
-    double mine = 0.0;
-    if (lane < NV) {
+    s = s_ncp;
 #pragma unroll
-      for (int gq = 0; gq < 3; ++gq) {
-        const double z = T.pz[gq];
-        mine = fma(T.pw[gq],
-                   Elastic::coef(d, lane, fma(z, rR - rL, rL), fma(z, lR - lL, lL), fma(z, uR - uL, uL)),
-                   mine);
-      }
-    } else if (lane == NV) {
-      const double sL = Elastic::vp(rL, lL, uL), sR = Elastic::vp(rR, lR, uR);
-      mine = (sL >= sR) ? sL : sR;
-    }
-    s = __shfl_sync(0xffffffffu, mine, NV);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) cb[v] = __shfl_sync(0xffffffffu, mine, v);
+    for (int v = 0; v < NV; ++v) cb[v] = __shfl_sync(0xffffffffu, mine_ncp, v);
   } else if constexpr (P::LINEAR) {
     s = fabs(A.p.a[d]);
   } else {

@@ -74,35 +74,31 @@ __device__ __forceinline__ ff ff_split_int(double x) {
   const unsigned sign = b1 & 0x80000000u;
   const int e = (int)((b1 >> 20) & 0x7ffu);
   const unsigned mh = ((b1 & 0xfffffu) << 3) | (b0 >> 29);        // mantissa bits 51..29
-  float h = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | mh);
   const unsigned ml = (b0 >> 6) & 0x7fffffu;                        // mantissa bits 28..6
   // ml 2^(e - 1069): (2^23 + ml) - 2^23 is exact, the scale is a power of two
-  float l = (__uint_as_float(0x4b000000u | ml) - 8388608.0f) *
-            __uint_as_float((unsigned)(e > 942 && e < 1197 ? e - 942 : 1) << 23);
-  l = __uint_as_float(__float_as_uint(l) | sign);
-  if (e <= 896) h = __uint_as_float(sign);
-  if (e >= 1151) h = __uint_as_float(sign | 0x7f800000u | (e == 2047 && (b & 0xfffffffffffffull) ? 0x400000u : 0u));
-  if (e <= 942 || e >= 1151) l = __uint_as_float(sign);
-  return {h, l};
+  const float l = (__uint_as_float(0x4b000000u | ml) - 8388608.0f) *
+                  __uint_as_float((unsigned)(e > 942 && e < 1197 ? e - 942 : 1) << 23);
+  // special ranges by selects (no branches: a divergent path would split the warp's later
+  // instructions)
+  const unsigned nan = (e == 2047 && (b & 0xfffffffffffffull)) ? 0x400000u : 0u;
+  const unsigned hb = e <= 896 ? sign
+                               : (e >= 1151 ? (sign | 0x7f800000u | nan)
+                                            : (sign | ((unsigned)(e - 896) << 23) | mh));
+  const unsigned lb = (e <= 942 || e >= 1151) ? sign : (__float_as_uint(l) | sign);
+  return {__uint_as_float(hb), __uint_as_float(lb)};
 }
 
 // Exact binary32 -> binary64 conversion (binary32 subnormals flush to a signed zero; infinities
-// and NaN are kept).
+// and NaN are kept); selects only.
 __device__ __forceinline__ double f2d_int(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned s = u & 0x80000000u;
   const unsigned e = (u >> 23) & 0xffu;
   const unsigned m = u & 0x7fffffu;
-  unsigned hi = s | ((e + 896u) << 20) | (m >> 3);
-  unsigned lo = m << 29;
-  if (e == 0u) {
-    hi = s;
-    lo = 0u;
-  }
-  if (e == 255u) {
-    hi = s | 0x7ff00000u | (m ? 0x80000u : 0u) | (m >> 3);
-    lo = 0u;
-  }
+  const unsigned hn = s | ((e + 896u) << 20) | (m >> 3);
+  const unsigned hs = s | 0x7ff00000u | (m ? 0x80000u : 0u) | (m >> 3);
+  const unsigned hi = e == 0u ? s : (e == 255u ? hs : hn);
+  const unsigned lo = (e == 0u || e == 255u) ? 0u : (m << 29);
   return __hiloint2double((int)hi, (int)lo);
 }
 

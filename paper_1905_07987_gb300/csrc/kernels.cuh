@@ -478,46 +478,55 @@ __device__ __forceinline__ void riemann_face(const StepArgs& A, const Tables& T,
   }
 
   // elastic: the face's speed and path-averaged coefficients depend only on the two cells'
-  // materials: lane v < NV forms cb[v], lane NV the speed, and the warp shares them (the
-  // divisions and square roots are not repeated on every lane)
+  // materials.  The warp forms them without divergent paths (every FP64 instruction costs the
+  // whole warp's pipe time): one division per lane (lanes 0-2: 1 / rho at the three path
+  // points; lanes 3, 4: (lambda + 2 mu) / rho of the left and right cell), one square root
+  // (the P-wave speeds), then lane v < NV accumulates row v's coefficient
+  // -(a + b mu(z)) with (a, b) = (lambda(z), 2) on the normal stress of direction d,
+  // (lambda(z), 0) on the other normal stresses, (0, 1) on the shear stresses, and -1 / rho(z)
+  // on the velocities.  mine_ncp = cb[lane] (lane < NV), s_ncp = the face's speed.
   double s_ncp = 0.0, mine_ncp = 0.0;
   if constexpr (P::NCP) {
     const long long mcL = cL >= 0 ? cL : cR, mcR = cR >= 0 ? cR : cL;
     const double rL = A.mat[mcL * 3], lL = A.mat[mcL * 3 + 1], uL = A.mat[mcL * 3 + 2];
     const double rR = A.mat[mcR * 3], lR = A.mat[mcR * 3 + 1], uR = A.mat[mcR * 3 + 2];
-    if (lane < NV) {
+    const int gl = lane < 3 ? lane : 0;
+    const double num = lane < 3 ? 1.0 : (lane == 3 ? lL + 2.0 * uL : (lane == 4 ? lR + 2.0 * uR : 1.0));
+    const double den = lane < 3 ? fma(T.pz[gl], rR - rL, rL) : (lane == 3 ? rL : (lane == 4 ? rR : 1.0));
+    const double quo = num / den;
+    const double rt = sqrt(quo);
+    const double sL = __shfl_sync(0xffffffffu, rt, 3), sR = __shfl_sync(0xffffffffu, rt, 4);
+    s_ncp = (sL >= sR) ? sL : sR;
+    const int v = lane < NV ? lane : 0;
+    const double bmu = v < 3 ? 0.0 : (v < 6 ? (v - 3 == d ? 2.0 : 0.0) : 1.0);
 #pragma unroll
-      for (int gq = 0; gq < 3; ++gq) {
-        const double z = T.pz[gq];
-        mine_ncp = fma(T.pw[gq],
-                       Elastic::coef(d, lane, fma(z, rR - rL, rL), fma(z, lR - lL, lL), fma(z, uR - uL, uL)),
-                       mine_ncp);
-      }
-    } else if (lane == NV) {
-      const double sL = Elastic::vp(rL, lL, uL), sR = Elastic::vp(rR, lR, uR);
-      mine_ncp = (sL >= sR) ? sL : sR;
+    for (int gq = 0; gq < 3; ++gq) {
+      const double z = T.pz[gq];
+      const double ir = __shfl_sync(0xffffffffu, quo, gq);
+      const double lz = fma(z, lR - lL, lL), uz = fma(z, uR - uL, uL);
+      const double cl = -((v >= 3 && v < 6 ? lz : 0.0) + bmu * uz);
+      mine_ncp = fma(T.pw[gq], v < 3 ? -ir : cl, mine_ncp);
     }
-    s_ncp = __shfl_sync(0xffffffffu, mine_ncp, NV);
     // interior face: the flux is elementwise over the face's NF x NV values, so the lanes walk
     // them contiguously (coalesced); each lane takes the jump of its row's source variable from
-    // the same records and its coefficient from lane v
+    // the same records and half its coefficient from lane v
     if (recL && recR) {
       constexpr int PE = (NF * NV + 31) / 32;
+      const double hcb = 0.5 * mine_ncp;
+      const double hs = 0.5 * s_ncp;
       double* out = A.phi + phi_off + f * (long long)(NPHI * NF * NV);
 #pragma unroll
       for (int r = 0; r < PE; ++r) {
         const int e = lane + 32 * r;
-        const int v = e % NV;
-        const double cbv = __shfl_sync(0xffffffffu, mine_ncp, v);
+        const int ve = e % NV;
+        const double hc = __shfl_sync(0xffffffffu, hcb, ve);
         if (e < NF * NV) {
-          const int sv = Elastic::src(d, v);
-          const int es = e - v + (sv < 0 ? 0 : sv);
-          const double dq = recR[e] - recL[e];
+          const int sv = Elastic::src(d, ve);
+          const int es = e - ve + (sv < 0 ? 0 : sv);
+          const double G = -(hs * (recR[e] - recL[e]));
           const double jump = sv >= 0 ? recR[es] - recL[es] : 0.0;
-          const double G = 0.5 * (0.0 + 0.0) - 0.5 * s_ncp * dq;
-          const double half = 0.5 * cbv * jump;
-          out[e] = G + half;
-          out[NF * NV + e] = G - half;
+          out[e] = fma(hc, jump, G);
+          out[NF * NV + e] = fma(-hc, jump, G);
         }
       }
       return;

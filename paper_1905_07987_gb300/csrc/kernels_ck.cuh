@@ -46,7 +46,8 @@ struct CfgCK {
   static constexpr int TPB = (CPB * NS + 31) / 32 * 32;
   static constexpr int NF = n * n;
   static constexpr int REC = NS * NVP;                  // doubles per cell and buffer
-  static constexpr size_t SMEM = (size_t)CPB * 2 * REC * sizeof(double);
+  // + the point source's spatial factor g [NS][6] of the source cell
+  static constexpr size_t SMEM = ((size_t)CPB * 2 * REC + (size_t)NS * 6) * sizeof(double);
 };
 
 // R[v] += row v of -sum_d (1/h_d) B_d D_d X at node j of the cell record X ([NS][NVP]).
@@ -148,6 +149,10 @@ __global__ void __launch_bounds__(CfgCK<N>::TPB) k_predictor_ck(const __grid_con
     s_sbar = sbar;
     s_slot = (int)sc;
   }
+  // g of the source cell's nodes (a loop with no iterations outside the source block: the
+  // FP64 products are not issued, predicated off, by every block)
+  double* gsrc = smem + (size_t)CPB * 2 * REC;
+  for (int i = tid; i < (srcb ? NS * 6 : 0); i += TPB) gsrc[i] = -A.src.M[i % 6] * A.src.phi[i / 6];
 
   double Dr[3][n], cf[3][4];
   double qb[NV];
@@ -189,7 +194,7 @@ __global__ void __launch_bounds__(CfgCK<N>::TPB) k_predictor_ck(const __grid_con
       ck_apply<N>(Xc, j, Dr, cf, R);
       if (srcc) {
 #pragma unroll
-        for (int v = 3; v < NV; ++v) R[v] = fma(-A.src.M[v - 3] * A.src.phi[j], s_sk[k], R[v]);
+        for (int v = 3; v < NV; ++v) R[v] = fma(gsrc[j * 6 + v - 3], s_sk[k], R[v]);
       }
       const double f = dt * (1.0 / (k + 1));
       const double wk = 1.0 / (k + 2);
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(CfgCK<N>::TPB) k_predictor_ck(const __grid_con
     ck_apply<N>(Xq, j, Dr, cf, R);
     if (srcc) {
 #pragma unroll
-      for (int v = 3; v < NV; ++v) R[v] = fma(-A.src.M[v - 3] * A.src.phi[j], s_sbar, R[v]);
+      for (int v = 3; v < NV; ++v) R[v] = fma(gsrc[j * 6 + v - 3], s_sbar, R[v]);
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) Xo[j * NVP + v] = R[v];
@@ -289,7 +294,9 @@ struct CfgCKM {
   static constexpr size_t OFF_A = (size_t)NS * NVQ * 8;
   static constexpr size_t OFF_B = OFF_A + (size_t)NS * NVF * 4;
   static constexpr size_t CELL = OFF_B + (size_t)NS * NVF * 4;
-  static constexpr size_t SMEM = CPB * CELL;
+  // + the point source's spatial factor g [NS][6] of the source cell, float-float
+  static constexpr size_t SRC_OFF = CPB * CELL;
+  static constexpr size_t SMEM = SRC_OFF + (size_t)NS * 6 * 8;
 };
 
 // Float-float R[v] += row v of -sum_d (1/h_d) B_d D_d U at node j (U: [NS][NVQ] (hi, lo) pairs).
@@ -429,8 +436,9 @@ __global__ void __launch_bounds__(CfgCKM<N>::TPB)
       s_cf[tid][d][3] = ff_split(mu * ih);
     }
   }
-  // point source of the block, as in the FP64 kernel
+  // point source of the block, as in the FP64 kernel; float-float copies for the per-node terms
   __shared__ double s_sk[n], s_sbar;
+  __shared__ ff s_skf[n], s_sbarf;
   __shared__ int s_slot;
   const long long sc = A.src.cell - c0;
   const bool srcb = sc >= 0 && sc < ncb;
@@ -449,9 +457,19 @@ __global__ void __launch_bounds__(CfgCKM<N>::TPB)
 #pragma unroll
       for (int t = 0; t < n; ++t) s = fma(T.Vi[k][t], ric[t], s);
       s_sk[k] = s;
+      s_skf[k] = ff_split(s);
     }
     s_sbar = sbar;
+    s_sbarf = ff_split(sbar);
     s_slot = (int)sc;
+  }
+  // g of the source cell's nodes in float-float (a loop with no iterations outside the source
+  // block: its FP64 products are not issued, predicated off, by every block; the per-node
+  // source terms below are FP32 arithmetic)
+  float2* gsrc = reinterpret_cast<float2*>(smem_ck + C::SRC_OFF);
+  for (int i = tid; i < (srcb ? NS * 6 : 0); i += TPB) {
+    const ff g = ff_split(-A.src.M[i % 6] * A.src.phi[i / 6]);
+    gsrc[i] = make_float2(g.h, g.l);
   }
   __syncthreads();
   const bool srcc = srcb && act && s_slot == slot;
@@ -479,7 +497,10 @@ __global__ void __launch_bounds__(CfgCKM<N>::TPB)
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       ff t0 = LU[v];
-      if (srcc && v >= 3) t0 = ff_add(t0, ff_split(-A.src.M[v - 3] * A.src.phi[j] * s_sk[0]));
+      if (srcc && v >= 3) {
+        const float2 g = gsrc[j * 6 + v - 3];
+        t0 = ff_add(t0, ff_mul({g.x, g.y}, s_skf[0]));
+      }
       const ff a1 = ff_mul(dtf, t0);
       dbar[v] = {0.5f * a1.h, 0.5f * a1.l};
       XA[j * NVF + v] = a1.h;
@@ -501,9 +522,8 @@ __global__ void __launch_bounds__(CfgCKM<N>::TPB)
       for (int v = 0; v < NV; ++v) R[v] = 0.f;
       ck_apply_f<N>(Xc, j, Dh, cf, R);
       if (srcc) {
-        const float sk = (float)s_sk[k];
 #pragma unroll
-        for (int v = 3; v < NV; ++v) R[v] = fmaf((float)(-A.src.M[v - 3] * A.src.phi[j]), sk, R[v]);
+        for (int v = 3; v < NV; ++v) R[v] = fmaf(gsrc[j * 6 + v - 3].x, s_skf[k].h, R[v]);
       }
       const float f = dtf.h * (1.0f / (k + 1));
       const float wk = 1.0f / (k + 2);
@@ -539,7 +559,10 @@ __global__ void __launch_bounds__(CfgCKM<N>::TPB)
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       vol[v] = ff_add(LU[v], {R[v], 0.f});
-      if (srcc && v >= 3) vol[v] = ff_add(vol[v], ff_split(-A.src.M[v - 3] * A.src.phi[j] * s_sbar));
+      if (srcc && v >= 3) {
+        const float2 g = gsrc[j * 6 + v - 3];
+        vol[v] = ff_add(vol[v], ff_mul({g.x, g.y}, s_sbarf));
+      }
     }
   }
   __syncthreads();  // every read of A is done before the volume term overwrites it

@@ -288,6 +288,7 @@ struct CfgCKM {
   static constexpr int NVF = 12;  // binary32 node record: 12 floats, 48 bytes (float4 loads)
   static constexpr int CPB = NS >= 96 ? 1 : 128 / NS;
   static constexpr int TPB = (CPB * NS + 31) / 32 * 32;
+  static constexpr int MINB = TPB <= 128 ? 4 : (TPB <= 224 ? 3 : 1);  // resident blocks per SM
   static constexpr int NF = n * n;
   // per cell: U (float-float state, then qbar) | A | B (binary32 Taylor coefficients); the
   // float-float volume term is staged over A and B
@@ -301,15 +302,15 @@ struct CfgCKM {
 
 // Float-float R[v] += row v of -sum_d (1/h_d) B_d D_d U at node j (U: [NS][NVQ] (hi, lo) pairs).
 template <int N>
-__device__ __forceinline__ void ck_apply_ff(const float2* U, int j, const float (&Dh)[3][N + 1],
-                                            const float (&Dl)[3][N + 1], const ff (&cf)[3][4],
-                                            ff (&R)[9]) {
+__device__ __forceinline__ void ck_apply_ff(const float2* U, int j, const float2* D2,
+                                            const ff (&cf)[3][4], ff (&R)[9]) {
   constexpr int n = N + 1, NVQ = CfgCKM<N>::NVQ;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
     const int jd = (j / st) % n;
     const float2* b = U + (j - jd * st) * NVQ;
+    const float2* Dr = D2 + jd * n;
     const int s0 = Elastic::sig(0, d), s1 = Elastic::sig(1, d), s2 = Elastic::sig(2, d);
     ff dv[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, ds[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll
@@ -322,7 +323,8 @@ __device__ __forceinline__ void ck_apply_ff(const float2* U, int j, const float 
         r[2 * i] = make_float2(v.x, v.y);
         r[2 * i + 1] = make_float2(v.z, v.w);
       }
-      const float ch = Dh[d][m], cl = Dl[d][m];
+      const float2 c = Dr[m];
+      const float ch = c.x, cl = c.y;
 #pragma unroll
       for (int i = 0; i < 3; ++i) ff_mac(dv[i], ch, cl, r[i].x, r[i].y);
       ff_mac(ds[0], ch, cl, r[s0].x, r[s0].y);
@@ -346,7 +348,7 @@ __device__ __forceinline__ void ck_apply_ff(const float2* U, int j, const float 
 
 // Binary32 R[v] += row v of -sum_d (1/h_d) B_d D_d X at node j (X: [NS][NVF] floats).
 template <int N>
-__device__ __forceinline__ void ck_apply_f(const float* X, int j, const float (&Dh)[3][N + 1],
+__device__ __forceinline__ void ck_apply_f(const float* X, int j, const float2* D2,
                                            const ff (&cf)[3][4], float (&R)[9]) {
   constexpr int n = N + 1, NVF = CfgCKM<N>::NVF;
 #pragma unroll
@@ -354,6 +356,7 @@ __device__ __forceinline__ void ck_apply_f(const float* X, int j, const float (&
     const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
     const int jd = (j / st) % n;
     const float* b = X + (j - jd * st) * NVF;
+    const float2* Dr = D2 + jd * n;
     const int s0 = Elastic::sig(0, d), s1 = Elastic::sig(1, d), s2 = Elastic::sig(2, d);
     float dv0 = 0.f, dv1 = 0.f, dv2 = 0.f, ds0 = 0.f, ds1 = 0.f, ds2 = 0.f;
 #pragma unroll
@@ -368,7 +371,7 @@ __device__ __forceinline__ void ck_apply_f(const float* X, int j, const float (&
         r[4 * i + 2] = v.z;
         r[4 * i + 3] = v.w;
       }
-      const float c = Dh[d][m];
+      const float c = Dr[m].x;
       dv0 = fmaf(c, r[0], dv0);
       dv1 = fmaf(c, r[1], dv1);
       dv2 = fmaf(c, r[2], dv2);
@@ -391,7 +394,7 @@ __device__ __forceinline__ void ck_apply_f(const float* X, int j, const float (&
 }
 
 template <int N>
-__global__ void __launch_bounds__(CfgCKM<N>::TPB)
+__global__ void __launch_bounds__(CfgCKM<N>::TPB, CfgCKM<N>::MINB)
     k_predictor_ck_mixed(const __grid_constant__ StepArgs A, const __grid_constant__ Tables T,
                          const __grid_constant__ TablesF F) {
   using C = CfgCKM<N>;
@@ -471,29 +474,24 @@ __global__ void __launch_bounds__(CfgCKM<N>::TPB)
     const ff g = ff_split(-A.src.M[i % 6] * A.src.phi[i / 6]);
     gsrc[i] = make_float2(g.h, g.l);
   }
+  // D as (hi, lo) rows: each lane reads the row of its own node digit
+  __shared__ float2 s_D[n * n];
+  if (tid < n * n) s_D[tid] = make_float2(F.Dh[tid / n][tid % n], F.Dl[tid / n][tid % n]);
   __syncthreads();
   const bool srcc = srcb && act && s_slot == slot;
 
-  float Dh[3][n], Dl[3][n];
   ff cf[3][4];
   ff LU[NV], dbar[NV];
   const ff dtf = ff_split_int(dt);
   if (act) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int jd = d == 0 ? j % n : (d == 1 ? (j / n) % n : j / (n * n));
-#pragma unroll
-      for (int m = 0; m < n; ++m) {
-        Dh[d][m] = F.Dh[jd][m];
-        Dl[d][m] = F.Dl[jd][m];
-      }
+    for (int d = 0; d < 3; ++d)
 #pragma unroll
       for (int i = 0; i < 4; ++i) cf[d][i] = s_cf[slot][d][i];
-    }
     // base term and a_1 = dt (L u + g s_0) in float-float; dbar starts at a_1 / 2
 #pragma unroll
     for (int v = 0; v < NV; ++v) LU[v] = {0.f, 0.f};
-    ck_apply_ff<N>(U, j, Dh, Dl, cf, LU);
+    ck_apply_ff<N>(U, j, s_D, cf, LU);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       ff t0 = LU[v];
@@ -520,7 +518,7 @@ __global__ void __launch_bounds__(CfgCKM<N>::TPB)
       float R[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) R[v] = 0.f;
-      ck_apply_f<N>(Xc, j, Dh, cf, R);
+      ck_apply_f<N>(Xc, j, s_D, cf, R);
       if (srcc) {
 #pragma unroll
         for (int v = 3; v < NV; ++v) R[v] = fmaf(gsrc[j * 6 + v - 3].x, s_skf[k].h, R[v]);
@@ -555,7 +553,7 @@ __global__ void __launch_bounds__(CfgCKM<N>::TPB)
     float R[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) R[v] = 0.f;
-    ck_apply_f<N>(XA, j, Dh, cf, R);
+    ck_apply_f<N>(XA, j, s_D, cf, R);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       vol[v] = ff_add(LU[v], {R[v], 0.f});

@@ -167,7 +167,9 @@ __device__ __forceinline__ void predictor_cell(const StepArgs& A, const Tables& 
     lam = A.mat[c * 3 + 1];
     mu = A.mat[c * 3 + 2];
   }
-  const bool has_src = (A.src.cell == c);
+  // point sources exist for the elastic system only (rejected at ader_set_point_source for the
+  // others): compiled out of the conservative systems' kernels
+  const bool has_src = P::NCP && (A.src.cell == c);
   double ric[n];
 #pragma unroll
   for (int t = 0; t < n; ++t) ric[t] = 0.0;

@@ -334,7 +334,9 @@ __device__ __forceinline__ void predictor_mixed_cell(const StepArgs& A, const Ta
     cf[tid] = h;
     cf[3 * NV + tid] = (float)(cd - (double)h);
   }
-  const bool has_src = (A.src.cell == c);
+  // point sources exist for the elastic system only (rejected at ader_set_point_source for the
+  // others): compiled out of the conservative systems' kernels
+  const bool has_src = P::NCP && (A.src.cell == c);
   double ric[n];
 #pragma unroll
   for (int t = 0; t < n; ++t) ric[t] = 0.0;
@@ -625,39 +627,40 @@ __device__ __forceinline__ void predictor_mixed_cell(const StepArgs& A, const Ta
   // ---- face records: float-float extrapolations of the time-averaged state and flux, both
   // faces of a direction from the same loads --------------------------------------------------
   double* fc = A.face + c * (long long)(D * 2 * FR);
-  constexpr int NFE = D * NF * NV;
-  for (int e = tid; e < NFE; e += TPB) {
+  for (int e = tid; e < NF * NV; e += TPB) {
     const int v = e % NV;
-    const int jp = (e / NV) % NF;
-    const int d = e / (NV * NF);
-    const int st = (d == 0 ? 1 : (d == 1 ? n : n * n));
-    const int jbase = (jp % st) + (jp / st) * st * n;
-    ff qa0 = {0.f, 0.f}, qa1 = {0.f, 0.f}, fa0 = {0.f, 0.f}, fa1 = {0.f, 0.f};
+    const int jp = e / NV;
 #pragma unroll
-    for (int m = 0; m < n; ++m) {
-      const int jj = jbase + m * st;
-      const ff q = uff[jj * NV + v];
-      ff_mac(qa0, sE[0][m], sE[1][m], q.h, q.l);
-      ff_mac(qa1, sE[2][m], sE[3][m], q.h, q.l);
-      if constexpr (P::CONS) {
-        const ff g = FB0[d * NL + jj * NV + v];
-        ff_mac(fa0, sE[0][m], sE[1][m], g.h, g.l);
-        ff_mac(fa1, sE[2][m], sE[3][m], g.h, g.l);
+    for (int d = 0; d < D; ++d) {  // unrolled: constant index divisors
+      const int st = (d == 0 ? 1 : (d == 1 ? n : n * n));
+      const int jbase = (jp % st) + (jp / st) * st * n;
+      ff qa0 = {0.f, 0.f}, qa1 = {0.f, 0.f}, fa0 = {0.f, 0.f}, fa1 = {0.f, 0.f};
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        const int jj = jbase + m * st;
+        const ff q = uff[jj * NV + v];
+        ff_mac(qa0, sE[0][m], sE[1][m], q.h, q.l);
+        ff_mac(qa1, sE[2][m], sE[3][m], q.h, q.l);
+        if constexpr (P::CONS) {
+          const ff g = FB0[d * NL + jj * NV + v];
+          ff_mac(fa0, sE[0][m], sE[1][m], g.h, g.l);
+          ff_mac(fa1, sE[2][m], sE[3][m], g.h, g.l);
+        }
       }
-    }
-    double* rec0 = fc + (d * 2) * FR;
-    double* rec1 = rec0 + FR;
-    const double q0 = ff_to_d(qa0), q1 = ff_to_d(qa1);
-    rec0[jp * NV + v] = q0;
-    rec1[jp * NV + v] = q1;
-    if constexpr (P::CONS) {
-      rec0[NF * NV + jp * NV + v] = ff_to_d(fa0) * A.g.h[d];
-      rec1[NF * NV + jp * NV + v] = ff_to_d(fa1) * A.g.h[d];
-    }
-    if constexpr (M::EULER) {  // the face states as written, for the wave speeds below
-      double* qs = reinterpret_cast<double*>(dF3);
-      qs[((d * 2) * NF + jp) * NV + v] = q0;
-      qs[((d * 2 + 1) * NF + jp) * NV + v] = q1;
+      double* rec0 = fc + (d * 2) * FR;
+      double* rec1 = rec0 + FR;
+      const double q0 = ff_to_d(qa0), q1 = ff_to_d(qa1);
+      rec0[jp * NV + v] = q0;
+      rec1[jp * NV + v] = q1;
+      if constexpr (P::CONS) {
+        rec0[NF * NV + jp * NV + v] = ff_to_d(fa0) * A.g.h[d];
+        rec1[NF * NV + jp * NV + v] = ff_to_d(fa1) * A.g.h[d];
+      }
+      if constexpr (M::EULER) {  // the face states as written, for the wave speeds below
+        double* qs = reinterpret_cast<double*>(dF3);
+        qs[((d * 2) * NF + jp) * NV + v] = q0;
+        qs[((d * 2 + 1) * NF + jp) * NV + v] = q1;
+      }
     }
   }
   if constexpr (M::EULER) {

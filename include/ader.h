@@ -75,8 +75,10 @@ typedef enum { ADER_PREC_FP64 = 0, ADER_PREC_MIXED = 1 } ader_prec;
  *           series in time about t^n, cut after degree N, whose time derivatives are repeated
  *           applications of the spatial operator; a point source's time factor enters through
  *           its degree-N interpolant at the step's Gauss-Legendre time nodes.  Built for the
- *           3-D elastic family with ADER_PREC_FP64 (others: ADER_EUNSUPPORTED).  Not
- *           differentiated: the adjoint entry points return ADER_EUNSUPPORTED for it. */
+ *           3-D elastic family (others: ADER_EUNSUPPORTED), with ADER_PREC_FP64 and with
+ *           ADER_PREC_MIXED (the O(1) base term L u and the first Taylor coefficient in
+ *           float-float, the higher coefficients in binary32, the update u + dt vol in FP64).
+ *           Not differentiated: the adjoint entry points return ADER_EUNSUPPORTED for it. */
 typedef enum { ADER_PREDICTOR_PICARD = 0, ADER_PREDICTOR_CK = 1 } ader_predictor;
 
 typedef struct {

@@ -112,6 +112,17 @@ void ader_destroy(ader_ctx* ctx);
  * (sum 1), host arrays.  Either pointer may be NULL. */
 ader_status ader_reference_nodes(int order, double* x, double* w);
 
+/* The library's 1-D reference-element tables for order N (n = N+1), host arrays of n*n doubles,
+ * row-major; any pointer may be NULL.  No device is needed.
+ *  D[i][m]  = phi_m'(x_i), the collocation derivative on [0,1] (Sec. 3.3);
+ *  Kw[k][l] = (K1^{-1} diag(w))[k][l] with K1[k][l] = e1[k] e1[l] - w[l] D[l][k]: the predictor's
+ *             time solve q = u + dt Kw R(q) (Eq. (5), time integrated by parts);
+ *  Vi[k][t] = coefficient of tau^k of the Lagrange polynomial of time node t: the monomial
+ *             coefficients of an interpolant through the time nodes (the Cauchy-Kowalevski
+ *             predictor's point-source factor).
+ * ADER_EINVAL for an order outside 1..6. */
+ader_status ader_reference_tables(int order, double* D, double* Kw, double* Vi);
+
 /* Number of cells, nodes per cell (n^dim) and variables of the context. */
 ader_status ader_sizes(const ader_ctx* ctx, int64_t* cells, int64_t* nodes_per_cell, int* nvar);
 

@@ -54,6 +54,7 @@ _L = ctypes.c_int64
 _SIGS = {
     "ader_status_string": ([_I], ctypes.c_char_p),
     "ader_reference_nodes": ([_I, _P, _P], _I),
+    "ader_reference_tables": ([_I, _P, _P, _P], _I),
     "ader_create": ([ctypes.POINTER(Config), _P, ctypes.POINTER(_P)], _I),
     "ader_destroy": ([_P], None),
     "ader_sizes": ([_P, ctypes.POINTER(_L), ctypes.POINTER(_L), ctypes.POINTER(_I)], _I),
@@ -124,6 +125,15 @@ def reference_nodes(order):
     w = np.zeros(order + 1)
     check(lib().ader_reference_nodes(order, x.ctypes.data, w.ctypes.data), "ader_reference_nodes")
     return x, w
+
+
+def reference_tables(order):
+    """(D, Kw, Vi) of the library, each [n, n] (see ader_reference_tables)."""
+    n = order + 1
+    D, Kw, Vi = (np.zeros((n, n)) for _ in range(3))
+    check(lib().ader_reference_tables(order, D.ctypes.data, Kw.ctypes.data, Vi.ctypes.data),
+          "ader_reference_tables")
+    return D, Kw, Vi
 
 
 def _ptr(a, dtype=np.float64):

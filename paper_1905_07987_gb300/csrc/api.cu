@@ -448,6 +448,20 @@ ader_status ader_reference_nodes(int order, double* x, double* w) {
   return ADER_OK;
 }
 
+ader_status ader_reference_tables(int order, double* D, double* Kw, double* Vi) {
+  if (order < 1 || order > MAXN - 1) return ADER_EINVAL;
+  Tables T;
+  if (!build_tables(order, T)) return ADER_EINVAL;
+  const int n = order + 1;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      if (D) D[i * n + j] = T.D[i][j];
+      if (Kw) Kw[i * n + j] = T.Kw[i][j];
+      if (Vi) Vi[i * n + j] = T.Vi[i][j];
+    }
+  return ADER_OK;
+}
+
 ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
   if (!out) return ADER_EINVAL;
   *out = nullptr;

@@ -68,3 +68,33 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     assert lib.ader_create(ctypes.byref(cfg), None, ctypes.byref(h)) == ader.EINVAL
     assert lib.ader_step(None, 0.0, 0.0) == ader.EINVAL
     lib.ader_destroy(None)
+
+
+@pytest.mark.parametrize("order", range(1, 7))
+def test_reference_tables_match_the_oracle(lib, order):
+    """The library's host tables (its own node and table derivations) against the oracle's: the
+    collocation derivative D and the predictor's time solve K1^{-1} W to round-off, and the
+    Lagrange-to-monomial table Vi of the Cauchy-Kowalevski source term against a 50-digit inverse
+    of the Vandermonde matrix of the same nodes."""
+    mpmath = pytest.importorskip("mpmath")
+    from oracle.refelem import RefElement
+    D, Kw, Vi = ader.reference_tables(order)
+    ref = RefElement(order)
+    Do = ref.D.numpy()
+    assert np.abs(D - Do).max() <= 1e-13 * np.abs(Do).max()
+    Kwo = np.linalg.solve(ref.K1.numpy(), np.diag(ref.w.numpy()))
+    assert np.abs(Kw - Kwo).max() <= 1e-13 * np.abs(Kwo).max()
+    x, _ = ader.reference_nodes(order)
+    n = order + 1
+    mpmath.mp.dps = 50
+    V = mpmath.matrix([[mpmath.mpf(float(xt)) ** k for k in range(n)] for xt in x])
+    Vinv = V ** -1
+    ex = np.array([[float(Vinv[k, t]) for t in range(n)] for k in range(n)])
+    assert np.abs(Vi - ex).max() <= 1e-14 * np.abs(ex).max()
+
+
+def test_reference_tables_reject_orders_outside_the_kernels(lib):
+    n = 8
+    buf = np.zeros(n * n)
+    for order in (0, 7):
+        assert lib.ader_reference_tables(order, buf.ctypes.data, None, None) == ader.EINVAL

@@ -425,6 +425,9 @@ __device__ __forceinline__ void ghost(int kind, int d, double* q, double* F) {
 // path-conservative fluctuation:  Phi_L = G + Bbar dq / 2,  Phi_R = G - Bbar dq / 2.
 // One warp per face (warp-shuffle maximum of the speeds); faces of direction d, offset `phi_off`
 // in the flux buffer.  With A.fspeed the FP64 speeds of the face states come from the predictor.
+// Interior faces whose flux is elementwise (Euler with those speeds, elastic with the face's
+// material terms formed once per warp) are walked value by value, coalesced; boundary faces go
+// node by node with their ghost states.
 template <class P, int D, int N>
 __device__ __forceinline__ void riemann_face(const StepArgs& A, const Tables& T, int d,
                                              long long phi_off, long long f, int lane) {

@@ -35,6 +35,10 @@ Readings of the paper taken here (the paper is silent or garbled on these points
   is the interior one.
 * CFL: dt = CFL / (d (2N+1)) * min_d h_d / lambda_max with lambda_max over all cells, nodes and
   directions of the state at t^n.
+* Continuous extension Runge-Kutta initial guess (Sec. 5 names it, gives no scheme): the
+  classical four-stage Runge-Kutta method on the cell-local ODE dq/dt = R(q) with its natural
+  continuous extension of uniform order 3, evaluated at the time nodes; the Picard iterations
+  then start from it (their number is the scheme's ``picard_iters``).
 * Cauchy-Kowalevski predictor (linear PDEs): the local solution's Taylor series in time about
   t^n, cut after degree N, with each time derivative replaced by the spatial operator applied to
   the previous one; a point source's time factor is replaced by its degree-N interpolant through
@@ -131,9 +135,11 @@ class ADERDG:
     """The ADER-DG scheme of order N on a Grid for one PDE (see module docstring)."""
 
     def __init__(self, pde, grid, order, cfl=0.9, picard_iters=0, material=None,
-                 predictor="picard"):
+                 predictor="picard", initial_guess="constant"):
         assert pde.dim == grid.dim
         assert predictor in ("picard", "ck")
+        assert initial_guess in ("constant", "cerk")
+        self.initial_guess = initial_guess
         assert predictor == "picard" or getattr(pde, "linear", False), "CK needs a linear PDE"
         self.predictor_kind = predictor
         self.pde, self.grid = pde, grid
@@ -255,14 +261,45 @@ class ADERDG:
         return R
 
     # ----- 1. space-time predictor ----------------------------------------------------
-    def predictor(self, u, dt, t=0.0, iters=None, trace=None):
+    def cerk_guess(self, u, dt, t=0.0):
+        """Initial guess of the Picard iteration by a continuous extension Runge-Kutta scheme
+        (Sec. 5): the cell-local ODE dq/dt = R(q) (the predictor's right-hand side, no neighbour
+        coupling) advanced over the step by the classical four-stage Runge-Kutta method, and its
+        natural continuous extension (uniform order 3) evaluated at the time nodes:
+            q(t + theta dt) = u + dt sum_i b_i(theta) k_i,
+            b_1 = theta - 3 theta^2/2 + 2 theta^3/3,  b_2 = b_3 = theta^2 - 2 theta^3/3,
+            b_4 = -theta^2/2 + 2 theta^3/3  (b_i(1) = 1/6, 1/3, 1/3, 1/6).
+        Returns [C, nt, n.., nv]."""
+        def R(q, tt):
+            tn = torch.as_tensor([float(tt)], dtype=torch.float64)
+            return self.rhs(q.unsqueeze(1), tn)[:, 0]
+        h = float(dt)
+        k1 = R(u, t)
+        k2 = R(u + 0.5 * h * k1, t + 0.5 * h)
+        k3 = R(u + 0.5 * h * k2, t + 0.5 * h)
+        k4 = R(u + h * k3, t + h)
+        out = []
+        for th in self.ref.x.tolist():
+            b1 = th - 1.5 * th ** 2 + 2.0 * th ** 3 / 3.0
+            b2 = th ** 2 - 2.0 * th ** 3 / 3.0
+            b4 = -0.5 * th ** 2 + 2.0 * th ** 3 / 3.0
+            out.append(u + h * (b1 * k1 + b2 * (k2 + k3) + b4 * k4))
+        return torch.stack(out, dim=1)
+
+    def predictor(self, u, dt, t=0.0, iters=None, trace=None, guess=None):
         """Element-local space-time predictor, Eq. (5): solve
             sum_l K1[k,l] q_l = e0[k] u + dt w_k R(q)_k
-        by the fixed-point iteration q^{r+1} = K1^{-1} (e0 u + dt W R(q^r)), q^0 = u."""
+        by the fixed-point iteration q^{r+1} = K1^{-1} (e0 u + dt W R(q^r)), from q^0 = u (constant
+        in time) or from the continuous extension Runge-Kutta guess (``guess="cerk"``; default:
+        the scheme's ``initial_guess``)."""
         ref = self.ref
         nt = self.n
         iters = self.I if iters is None else iters
-        q = u.unsqueeze(1).expand([u.shape[0], nt] + list(u.shape[1:])).clone()
+        guess = self.initial_guess if guess is None else guess
+        if guess == "cerk":
+            q = self.cerk_guess(u, dt, t)
+        else:
+            q = u.unsqueeze(1).expand([u.shape[0], nt] + list(u.shape[1:])).clone()
         t_nodes = t + ref.x * dt
         wt = ref.w.reshape([1, nt] + [1] * (self.D + 1))
         e0 = ref.e0.reshape([1, nt] + [1] * (self.D + 1))

@@ -185,3 +185,68 @@ def test_ck_point_source_error_is_order_dt_to_the_N_plus_1(N):
         errs.append(err)
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert min(rates) > N + 1 - 0.3, (errs, rates)
+
+
+# ---- continuous extension Runge-Kutta initial guess (Sec. 5) ----------------------------------
+
+@pytest.mark.parametrize("dim,N", [(2, 4), (3, 5)])
+def test_cerk_guess_exact_for_cubic_in_time_solutions(dim, N):
+    """Data of total degree <= 3 under constant advection: the exact local solution is a cubic in
+    time, which the uniform-order-3 continuous extension reproduces at every time node."""
+    a = [0.7, -0.4, 0.25][:dim]
+    g = Grid((2,) * dim, (0.0,) * dim, (1.0,) * dim, [('periodic', 'periodic')] * dim)
+    s = ADERDG(Advection(a), g, N, initial_guess="cerk")
+    X = s.node_coords()
+    u = poly(X, 3, 13)[..., None]
+    dt = 0.04
+    q0 = s.cerk_guess(u, dt)
+    for k in range(N + 1):
+        t = float(s.ref.x[k]) * dt
+        Xs = [X[d] - a[d] * t for d in range(dim)]
+        assert torch.allclose(q0[:, k, ..., 0], poly(Xs, 3, 13), atol=1e-12)
+
+
+def test_cerk_guess_error_is_order_dt_to_the_4():
+    """General data: the guess at the time nodes against the exact local solution exp(tau dt L) u
+    of the cell's linear ODE (dense Kronecker-assembled L): error ~ dt^4."""
+    N = 3
+    mat = torch.tensor([[2.6, 27.0, 22.0]], dtype=torch.float64)
+    s, L = _cell_ops(N, 3, Elastic(), mat)
+    g = torch.Generator().manual_seed(41)
+    u = torch.rand([1] + [N + 1] * 3 + [9], generator=g, dtype=torch.float64) - 0.5
+    errs = []
+    for dt in (2e-3, 1e-3, 5e-4):
+        q0 = s.cerk_guess(u, dt).reshape(N + 1, -1)
+        ex = torch.stack([torch.linalg.matrix_exp(float(x) * dt * L) @ u.reshape(-1) for x in s.ref.x])
+        errs.append(float((q0 - ex).abs().max()))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > 4 - 0.3, (errs, rates)
+
+
+@pytest.mark.parametrize("iters", [0, 1, 2])
+def test_picard_from_the_cerk_guess_gains_one_order_per_iteration(iters):
+    """Distance of the predictor started from the CERK guess to the converged fixed point of
+    Eq. (5) after `iters` iterations: O(dt^(4 + iters)) (the iteration contracts by O(dt))."""
+    N = 5
+    mat = torch.tensor([[2.6, 27.0, 22.0]], dtype=torch.float64)
+    s, L = _cell_ops(N, 3, Elastic(), mat)
+    g = torch.Generator().manual_seed(43)
+    u = torch.rand([1] + [N + 1] * 3 + [9], generator=g, dtype=torch.float64) - 0.5
+    errs = []
+    for dt in (4e-3, 2e-3, 1e-3):
+        qs = dense_spacetime_solve(s.ref.K1, s.ref.w, s.ref.e0, L, u.reshape(-1), dt)
+        q = s.predictor(u, dt, iters=iters, guess="cerk").reshape(N + 1, -1)
+        errs.append(float((q - qs).abs().max()))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > 4 + iters - 0.4, (errs, rates)
+
+
+def test_converged_predictor_does_not_depend_on_the_guess():
+    N = 3
+    mat = torch.tensor([[2.6, 27.0, 22.0]], dtype=torch.float64)
+    s, _ = _cell_ops(N, 3, Elastic(), mat)
+    g = torch.Generator().manual_seed(47)
+    u = torch.rand([1] + [N + 1] * 3 + [9], generator=g, dtype=torch.float64) - 0.5
+    a = s.predictor(u, 2e-3, iters=40, guess="constant")
+    b = s.predictor(u, 2e-3, iters=40, guess="cerk")
+    assert torch.allclose(a, b, atol=1e-14)

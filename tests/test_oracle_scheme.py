@@ -343,3 +343,17 @@ def test_elastic_plane_wave_converges_with_the_ck_predictor():
         u, t = s.run(u, None, t_end=0.05)
         errs.append(l2_error(s, u, lambda X: synth.plane_wave_elastic(X, mat, t, kind='p')[..., 0], var=0))
     assert math.log2(errs[0] / errs[1]) > 2.5, errs
+
+
+def test_euler_2d_with_the_cerk_guess_and_one_iteration_keeps_order_N_plus_1():
+    """Order 3 (N+1 = 4) with the continuous extension Runge-Kutta guess (order 4 in dt) and a
+    single Picard iteration instead of N+1 = 4."""
+    errs = []
+    for nc in (6, 12):
+        g = Grid((nc, nc), (0.0, 0.0), (1.0, 1.0), periodic(2))
+        s = ADERDG(Euler(2), g, 3, cfl=synth.cfl_number(3), picard_iters=1, initial_guess="cerk")
+        u = T(synth.entropy_wave(coords(s)))
+        u, t = s.run(u, None, t_end=0.1)
+        errs.append(l2_error(s, u, lambda X: synth.entropy_wave(X, t)[..., 0]))
+    rate = math.log2(errs[0] / errs[1])
+    assert rate > 3.6, (errs, rate)

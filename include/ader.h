@@ -81,6 +81,15 @@ typedef enum { ADER_PREC_FP64 = 0, ADER_PREC_MIXED = 1 } ader_prec;
  *           Not differentiated: the adjoint entry points return ADER_EUNSUPPORTED for it. */
 typedef enum { ADER_PREDICTOR_PICARD = 0, ADER_PREDICTOR_CK = 1 } ader_predictor;
 
+/* Initial guess of the Picard predictor (Sec. 5):
+ *  CONSTANT - q^0 = u^n at every time node;
+ *  CERK     - the dense output of the classical four-stage Runge-Kutta method on the cell-local
+ *             ODE dq/dt = R(q), natural continuous extension of uniform order 3, evaluated at
+ *             the time nodes; picard_iters iterations follow (full order needs max(0, N-3)).
+ *             ADER_PREC_FP64 and the Picard predictor only (else ADER_EUNSUPPORTED); not
+ *             differentiated (the adjoint entry points reject it). */
+typedef enum { ADER_GUESS_CONSTANT = 0, ADER_GUESS_CERK = 1 } ader_guess;
+
 typedef struct {
   int dim;             /* 2 or 3 (elastic: 3) */
   int order;           /* polynomial order N >= 1 (n = N+1 nodes per direction) */
@@ -96,6 +105,7 @@ typedef struct {
                           2 every cell troubled (the pure FV scheme, for tests) */
   int precision;       /* ader_prec */
   int predictor;       /* ader_predictor (0 = Picard) */
+  int initial_guess;   /* ader_guess (0 = constant in time) */
 } ader_config;
 
 /* Create a context on the current CUDA device.  `cuda_stream` is a cudaStream_t (NULL = the

@@ -18,6 +18,7 @@ PDE = {"advection": 0, "euler": 1, "elastic": 2}
 BC = {"periodic": 0, "wall": 1, "absorbing": 2}
 PREC = {"fp64": 0, "mixed": 1}
 PREDICTOR = {"picard": 0, "ck": 1}
+GUESS = {"constant": 0, "cerk": 1}
 
 
 class AderError(RuntimeError):
@@ -42,6 +43,7 @@ class Config(ctypes.Structure):
         ("limiter", ctypes.c_int),
         ("precision", ctypes.c_int),
         ("predictor", ctypes.c_int),
+        ("initial_guess", ctypes.c_int),
     ]
 
 
@@ -153,7 +155,8 @@ def _ptr(a, dtype=np.float64):
 
 
 def make_config(pde, dim, order, ncell, lo, hi, bc, cfl, gamma=1.4, adv=(0.0, 0.0, 0.0),
-                picard_iters=0, limiter=False, precision="fp64", predictor="picard"):
+                picard_iters=0, limiter=False, precision="fp64", predictor="picard",
+                initial_guess="constant"):
     c = Config()
     c.dim = dim
     c.order = order
@@ -176,6 +179,7 @@ def make_config(pde, dim, order, ncell, lo, hi, bc, cfl, gamma=1.4, adv=(0.0, 0.
     c.limiter = int(limiter)
     c.precision = PREC[precision] if isinstance(precision, str) else int(precision)
     c.predictor = PREDICTOR[predictor] if isinstance(predictor, str) else int(predictor)
+    c.initial_guess = GUESS[initial_guess] if isinstance(initial_guess, str) else int(initial_guess)
     return c
 
 

@@ -43,6 +43,8 @@ struct Tables {
   double pz[3], pw[3];        // 3-point Gauss-Legendre rule on [0,1] (path integral of B)
   double Vi[MAXN][MAXN];      // Vi[k][t]: coefficient of tau^k of the Lagrange polynomial of
                               // time node t (interpolant -> monomial coefficients)
+  double cerk[3][MAXN];       // dense-output weights b1, b2 (= b3), b4 of the four-stage
+                              // Runge-Kutta guess at the time nodes
 };
 
 // Single-precision and float-float copies of the tables for the mixed-precision predictor.
@@ -133,6 +135,8 @@ struct StepArgs {
   // Euler: the CFL maximum through a binary32 filter with an error bound and FP64 evaluation of
   // the candidates (the same maximum as evaluating every node in FP64); 0: every node
   int cfl_filter;
+  // 1: the FP64 Picard predictor starts from the continuous extension Runge-Kutta guess
+  int cerk;
 };
 
 // Per (pde, dim) kernel family; order dispatch happens inside.

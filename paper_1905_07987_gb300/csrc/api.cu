@@ -180,6 +180,14 @@ bool build_tables(int order, Tables& T) {
     T.pz[i] = pz[i];
     T.pw[i] = pw[i];
   }
+  // dense output of the four-stage Runge-Kutta guess at the time nodes (natural continuous
+  // extension, uniform order 3)
+  for (int t = 0; t < n; ++t) {
+    const double th = x[t];
+    T.cerk[0][t] = th - 1.5 * th * th + 2.0 * th * th * th / 3.0;
+    T.cerk[1][t] = th * th - 2.0 * th * th * th / 3.0;
+    T.cerk[2][t] = -0.5 * th * th + 2.0 * th * th * th / 3.0;
+  }
   // monomial coefficients of the Lagrange polynomials of the time nodes, by expanding the
   // products prod_{m != t} (tau - x_m) / (x_t - x_m) one factor at a time
   for (int t = 0; t < n; ++t) {
@@ -472,6 +480,11 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
   if (cfg->precision != ADER_PREC_FP64 && cfg->precision != ADER_PREC_MIXED) return ADER_EUNSUPPORTED;
   if (cfg->predictor != ADER_PREDICTOR_PICARD && cfg->predictor != ADER_PREDICTOR_CK) return ADER_EINVAL;
   if (cfg->predictor == ADER_PREDICTOR_CK && (!fam->predictor_ck || cfg->limiter))
+    return ADER_EUNSUPPORTED;
+  if (cfg->initial_guess != ADER_GUESS_CONSTANT && cfg->initial_guess != ADER_GUESS_CERK)
+    return ADER_EINVAL;
+  if (cfg->initial_guess == ADER_GUESS_CERK &&
+      (cfg->predictor != ADER_PREDICTOR_PICARD || cfg->precision != ADER_PREC_FP64))
     return ADER_EUNSUPPORTED;
   // the predictor keeps a cell in shared memory: at most 227 KB per block on sm_103a, less the
   // kernel's static tables (the 3-D Euler mixed form at order 6 does not fit)
@@ -781,6 +794,7 @@ static StepArgs make_args(ader_ctx* c, double dt, double t_end) {
   a.mat = c->mat;
   a.dev = c->dev;
   a.iters = c->cfg.picard_iters > 0 ? c->cfg.picard_iters : c->cfg.order + 1;
+  a.cerk = c->cfg.initial_guess == ADER_GUESS_CERK ? 1 : 0;
   a.src = c->src;
   a.dt_fixed = dt > 0 ? dt : 0.0;
   a.t_end = t_end > 0 ? t_end : 0.0;
@@ -914,7 +928,8 @@ ader_status ader_adjoint_step(ader_ctx* c, double t_n, double dt, const double* 
                               const double* dJdu, double* grad_mat, double* grad_M) {
   if (!c || !u_n || !lam || !grad_mat || !grad_M || !(dt > 0.0)) return ADER_EINVAL;
   if (c->cfg.pde != ADER_PDE_ELASTIC || !c->fam->adj_run) return ADER_EUNSUPPORTED;
-  if (c->cfg.predictor != ADER_PREDICTOR_PICARD) return ADER_EUNSUPPORTED;
+  if (c->cfg.predictor != ADER_PREDICTOR_PICARD || c->cfg.initial_guess != ADER_GUESS_CONSTANT)
+    return ADER_EUNSUPPORTED;
   if (c->cfg.order > 5) return ADER_EUNSUPPORTED;
   if (!c->mat_set) return ADER_ESTATE;
   const int iters = c->cfg.picard_iters > 0 ? c->cfg.picard_iters : c->cfg.order + 1;
@@ -977,7 +992,8 @@ ader_status ader_adjoint_step_static(ader_ctx* c, double t_n, double dt, const d
                                      double* grad_M) {
   if (!c || !u_n || !lam || !grad_mat || !grad_M || !(dt > 0.0)) return ADER_EINVAL;
   if (c->cfg.pde != ADER_PDE_ELASTIC || !c->fam->adj_run) return ADER_EUNSUPPORTED;
-  if (c->cfg.predictor != ADER_PREDICTOR_PICARD) return ADER_EUNSUPPORTED;
+  if (c->cfg.predictor != ADER_PREDICTOR_PICARD || c->cfg.initial_guess != ADER_GUESS_CONSTANT)
+    return ADER_EUNSUPPORTED;
   if (c->cfg.order > 5) return ADER_EUNSUPPORTED;
   if (!c->mat_set) return ADER_ESTATE;
   int dev = 0;
@@ -1038,7 +1054,8 @@ ader_status ader_misfit_gradient(ader_ctx* c, const double* u0, double t0, doubl
                                  double* grad_M) {
   if (!c || !u0 || !obs || !J || steps < 1 || k_ckpt < 1 || !(dt > 0.0)) return ADER_EINVAL;
   if (c->cfg.pde != ADER_PDE_ELASTIC) return ADER_EUNSUPPORTED;
-  if (c->cfg.predictor != ADER_PREDICTOR_PICARD) return ADER_EUNSUPPORTED;
+  if (c->cfg.predictor != ADER_PREDICTOR_PICARD || c->cfg.initial_guess != ADER_GUESS_CONSTANT)
+    return ADER_EUNSUPPORTED;
   if (!c->mat_set || c->rec.nrec <= 0) return ADER_ESTATE;
   const size_t nd = (size_t)c->ndof;
   const int nrec = c->rec.nrec;

@@ -124,6 +124,117 @@ __device__ __forceinline__ void load_nodes(const double* qs, const PdeParams& pp
   }
 }
 
+// Continuous extension Runge-Kutta guess of the predictor (Sec. 5): the classical four-stage
+// Runge-Kutta method on the cell-local ODE dq/dt = R(q) (flux divergence or non-conservative
+// product of one time level, point source at the stage time), and its natural continuous
+// extension of uniform order 3 evaluated at the time nodes:
+//   q_t = u + dt (b1(x_t) k1 + b2(x_t) (k2 + k3) + b4(x_t) k4)   (weights: T.cerk)
+// written to the n time slices of qs.  Called once per cell before the Picard iterations (not
+// inlined: its registers do not add to the iteration loop's).
+template <class P, int D, int N>
+__device__ __noinline__ void cerk_guess_cell(const StepArgs& A, const Tables& T, double* qs,
+                                             double* Fs, const double* sD, const double* ul,
+                                             double irho, double lam, double mu, bool has_src,
+                                             int tid) {
+  using C = Cfg<P, D, N>;
+  constexpr int n = C::n, NV = C::NV, NL = C::NL, NS = C::NS, TPB = C::TPB, LPT = C::LPT;
+  const double dt = A.dev->dt;
+  const double tn = A.dev->t;
+  double kst[4][LPT];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double ca = i == 0 ? 0.0 : (i == 3 ? 1.0 : 0.5);
+    // stage state u + dt a_i k_{i-1} in time slice 0 of qs
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      const int l = tid + k * TPB;
+      if (l < NL) qs[l] = i == 0 ? ul[k] : fma(ca * dt, kst[i > 0 ? i - 1 : 0][k], ul[k]);
+    }
+    __syncthreads();
+    double R1[LPT];
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) R1[k] = 0.0;
+    if constexpr (P::CONS) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        for (int j = tid; j < NS; j += TPB) {
+          double q[NV], f[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) q[v] = qs[j * NV + v];
+          typename P::Aux ax;
+          P::aux(q, A.p, ax);
+          P::flux(q, ax, A.p, d, f);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) Fs[j * NV + v] = f[v];
+        }
+        __syncthreads();
+        const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
+#pragma unroll
+        for (int k = 0; k < LPT; ++k) {
+          const int l = tid + k * TPB;
+          if (l < NL) {
+            const int j = l / NV, v = l - (l / NV) * NV;
+            const int jd = (j / st) % n, j0 = j - jd * st;
+            double acc = 0.0;
+#pragma unroll
+            for (int m = 0; m < n; ++m) acc = fma(sD[jd * n + m], Fs[(j0 + m * st) * NV + v], acc);
+            R1[k] = fma(-A.g.inv_h[d], acc, R1[k]);
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if constexpr (P::NCP) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
+#pragma unroll
+        for (int k = 0; k < LPT; ++k) {
+          const int l = tid + k * TPB;
+          if (l < NL) {
+            const int j = l / NV, v = l - (l / NV) * NV;
+            const int sv = Elastic::src(d, v);
+            if (sv >= 0) {
+              const double coef = -Elastic::coef_ir(d, v, irho, lam, mu) * A.g.inv_h[d];
+              const int jd = (j / st) % n, j0 = j - jd * st;
+              double acc = 0.0;
+#pragma unroll
+              for (int m = 0; m < n; ++m) acc = fma(sD[jd * n + m], qs[(j0 + m * st) * NV + sv], acc);
+              R1[k] = fma(coef, acc, R1[k]);
+            }
+          }
+        }
+      }
+    }
+    if (has_src) {
+      const double tau = fma(ca, dt, tn) - A.src.t0;
+      const double a = (M_PI * A.src.f0 * tau) * (M_PI * A.src.f0 * tau);
+      const double ric = (1.0 - 2.0 * a) * exp(-a);
+#pragma unroll
+      for (int k = 0; k < LPT; ++k) {
+        const int l = tid + k * TPB;
+        if (l < NL) {
+          const int j = l / NV, v = l - (l / NV) * NV;
+          if (v >= 3) R1[k] = fma(-A.src.M[v - 3] * A.src.phi[j], ric, R1[k]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) kst[i][k] = R1[k];
+    __syncthreads();  // the next stage overwrites slice 0
+  }
+#pragma unroll
+  for (int k = 0; k < LPT; ++k) {
+    const int l = tid + k * TPB;
+    if (l < NL) {
+#pragma unroll
+      for (int t = 0; t < n; ++t)
+        qs[t * NL + l] = ul[k] + dt * (T.cerk[0][t] * kst[0][k] + T.cerk[1][t] * (kst[1][k] + kst[2][k]) +
+                                       T.cerk[2][t] * kst[3][k]);
+    }
+  }
+}
+
 // Space-time predictor (Eq. (5)) with the fused epilogue: time averages, volume term, the
 // cell-local part of the face terms of Eq. (6), and the face extrapolations.
 //   q^0 = u;  q^{r+1} = u + dt Kw R(q^r)  (Kw = K1^{-1} diag(w), K1^{-1} e0 = 1)
@@ -182,6 +293,10 @@ __device__ __forceinline__ void predictor_cell(const StepArgs& A, const Tables& 
     }
   }
   __syncthreads();
+  if (A.cerk) {
+    cerk_guess_cell<P, D, N>(A, T, qs, Fs, sD, ul, irho, lam, mu, has_src, tid);
+    __syncthreads();
+  }
 
   for (int it = 0; it < A.iters; ++it) {
     double R[LPT][n];

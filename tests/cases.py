@@ -24,7 +24,7 @@ def rel_linf(a, b):
 class Case:
     def __init__(self, pde, dim, order, ncell, lo=None, hi=None, bc="periodic", cfl=None,
                  adv=(0.7, -0.4, 0.3), seed=1, material=None, picard_iters=0, limiter=False,
-                 precision="fp64", predictor="picard"):
+                 precision="fp64", predictor="picard", initial_guess="constant"):
         self.pde, self.dim, self.order = pde, dim, order
         self.ncell = tuple(ncell)
         self.lo = tuple(lo) if lo is not None else (0.0,) * dim
@@ -38,7 +38,8 @@ class Case:
         self.mat = material
         self.cfg = ader.make_config(pde, dim, order, self.ncell, self.lo, self.hi, self.bc, self.cfl,
                                     adv=self.adv, picard_iters=picard_iters, limiter=limiter,
-                                    precision=precision, predictor=predictor)
+                                    precision=precision, predictor=predictor,
+                                    initial_guess=initial_guess)
         self.ctx = ader.Context(self.cfg)
         if pde == "euler":
             P = Euler(dim)
@@ -48,7 +49,8 @@ class Case:
             P = Elastic()
         mat_t = torch.from_numpy(material) if material is not None else None
         self.oracle = ADERDG(P, Grid(self.ncell, self.lo, self.hi, self.bc), order, cfl=self.cfl,
-                             picard_iters=picard_iters, material=mat_t, predictor=predictor)
+                             picard_iters=picard_iters, material=mat_t, predictor=predictor,
+                             initial_guess=initial_guess)
         if material is not None:
             self.ctx.set_material(torch.from_numpy(material.reshape(-1).copy()).cuda())
         self.shape = (self.ctx.cells,) + (order + 1,) * dim + (self.ctx.nvar,)

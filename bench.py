@@ -334,6 +334,49 @@ def extra_elastic(ader, synth, stream, steps=2, warmup=1, n=81):
     return out
 
 
+def extra_cerk(ader, synth, stream, steps=2, warmup=1, err_steps=20):
+    """81^3 order-4 Euler entropy wave in FP64: the Picard predictor from the constant guess with
+    N+1 = 5 iterations against the continuous extension Runge-Kutta guess (order 4 in dt) with
+    max(0, N-3) = 1 iteration; ms per step, predictor ms, and the density error against the
+    exact solution after err_steps CFL steps for both."""
+    import torch
+    wl = WORKLOADS["euler3d_p4_81"]
+    D, N = wl["dim"], wl["order"]
+    u0 = torch.from_numpy(build_initial(ader, synth, wl)).to("cuda")
+    dofs = math.prod(wl["ncell"]) * (N + 1) ** D * (D + 2)
+    out = {"workload": "euler3d_p4_81, FP64, Picard from the constant guess (5 iterations) vs the "
+                       "CERK guess (1 iteration)", "dofs": dofs}
+    for name, guess, iters in (("constant_5", "constant", 0), ("cerk_1", "cerk", 1)):
+        cfg = ader.make_config(wl["pde"], D, N, wl["ncell"], wl["lo"], wl["hi"], wl["bc"],
+                               synth.cfl_number(N), picard_iters=iters, initial_guess=guess)
+        ctx = ader.Context(cfg, stream=stream.cuda_stream)
+        ctx.set_state(u0)
+        ctx.set_time(0.0)
+        for _ in range(warmup):
+            ctx.step()
+        ctx.sync()
+        ctx.enable_timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ph, nr = ctx.phase_times()
+        ctx.enable_timing(False)
+        ctx.run(err_steps - warmup - steps)
+        x, w = ader.reference_nodes(N)
+        l2, linf = density_error(ctx, wl, ctx.time(), x, w)
+        out[name] = {"ms_per_step": ms / steps, "value": dofs * steps / (ms * 1e-3),
+                     "predictor_ms": ph["predictor"] / max(nr, 1), "l2_rho": l2,
+                     "steps_for_error": err_steps}
+        ctx.close()
+    out["cerk_speedup"] = out["constant_5"]["ms_per_step"] / out["cerk_1"]["ms_per_step"]
+    out["cerk_over_constant_l2_error"] = out["cerk_1"]["l2_rho"] / out["constant_5"]["l2_rho"]
+    return out
+
+
 def extra_adjoint(ader, synth, stream, n=40, N=4, steps=12, k=4):
     """Adjoint of the linear-elastic step through the C ABI (ader_misfit_gradient): order N, n^3
     cells (h = 0.5 km), seeded material, moment-tensor Ricker source at the centre, 64 receivers
@@ -654,7 +697,7 @@ def main():
         extra = {}
         for name, fn in (("euler2d_p3_27", extra_euler2d), ("explosion3d_p3_64", extra_explosion),
                          ("elastic3d_p5_81", extra_elastic), ("ensemble16_elastic_p4", extra_ensemble),
-                         ("adjoint_elastic3d_p4_40", extra_adjoint)):
+                         ("adjoint_elastic3d_p4_40", extra_adjoint), ("euler3d_p4_81_cerk", extra_cerk)):
             if args.extras and name not in args.extras.split(","):
                 continue
             try:

@@ -62,6 +62,19 @@ def predictor_flops_per_cell(pde, D, N, iters):
     return iters * it + epi
 
 
+def cerk_flops_per_cell(D, N):
+    """Algorithmic FP64 flops of the continuous extension Runge-Kutta guess of an Euler cell:
+    four stages, each the nodal fluxes and the D derivative contractions at one time level plus
+    the stage state (one FMA per line), and the dense output (4 FMA per line and time node)."""
+    n = N + 1
+    NS = n ** D
+    NV = D + 2
+    NL = NS * NV
+    cF = (2 * D + 5) + D * (D + 4)
+    stage = cF * NS + D * NS * NV * (2 * n + 2) + 2 * NL
+    return 4 * stage + NL * n * 8
+
+
 def sample_clocks(stop_after_s):
     """nvidia-smi clock / throttle samples every 200 ms (started before the timed region)."""
     q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -372,6 +385,12 @@ def extra_cerk(ader, synth, stream, steps=2, warmup=1, err_steps=20):
                      "predictor_ms": ph["predictor"] / max(nr, 1), "l2_rho": l2,
                      "steps_for_error": err_steps}
         ctx.close()
+    cells = math.prod(wl["ncell"])
+    for name, iters, extra in (("constant_5", N + 1, 0), ("cerk_1", 1, cerk_flops_per_cell(D, N))):
+        fl = (predictor_flops_per_cell(wl["pde"], D, N, iters) + extra) * cells
+        tf = fl / (out[name]["predictor_ms"] * 1e-3) / 1e12
+        out[name]["predictor_tflops"] = tf
+        out[name]["predictor_frac_of_fp64_peak"] = tf * 1e12 / FP64_PEAK
     out["cerk_speedup"] = out["constant_5"]["ms_per_step"] / out["cerk_1"]["ms_per_step"]
     out["cerk_over_constant_l2_error"] = out["cerk_1"]["l2_rho"] / out["constant_5"]["l2_rho"]
     return out

@@ -439,8 +439,7 @@ __global__ void __launch_bounds__(CfgCKM<N>::TPB, CfgCKM<N>::MINB)
       s_cf[tid][d][3] = ff_split(mu * ih);
     }
   }
-  // point source of the block, as in the FP64 kernel; float-float copies for the per-node terms
-  __shared__ double s_sk[n], s_sbar;
+  // point source of the block, as in the FP64 kernel, kept in float-float for the per-node terms
   __shared__ ff s_skf[n], s_sbarf;
   __shared__ int s_slot;
   const long long sc = A.src.cell - c0;
@@ -459,10 +458,8 @@ __global__ void __launch_bounds__(CfgCKM<N>::TPB, CfgCKM<N>::MINB)
       double s = 0.0;
 #pragma unroll
       for (int t = 0; t < n; ++t) s = fma(T.Vi[k][t], ric[t], s);
-      s_sk[k] = s;
       s_skf[k] = ff_split(s);
     }
-    s_sbar = sbar;
     s_sbarf = ff_split(sbar);
     s_slot = (int)sc;
   }

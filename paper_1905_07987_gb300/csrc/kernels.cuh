@@ -237,7 +237,8 @@ __device__ __noinline__ void cerk_guess_cell(const StepArgs& A, const Tables& T,
 
 // Space-time predictor (Eq. (5)) with the fused epilogue: time averages, volume term, the
 // cell-local part of the face terms of Eq. (6), and the face extrapolations.
-//   q^0 = u;  q^{r+1} = u + dt Kw R(q^r)  (Kw = K1^{-1} diag(w), K1^{-1} e0 = 1)
+//   q^0 = u (or the continuous extension Runge-Kutta guess, A.cerk);
+//   q^{r+1} = u + dt Kw R(q^r)  (Kw = K1^{-1} diag(w), K1^{-1} e0 = 1)
 //   R(q) = -sum_d (1/h_d) D_d F_d(q) - sum_d (1/h_d) B_d D_d q + point source
 // One cell c (all threads of the block; called by the per-context kernel and by the persistent
 // ensemble kernel).

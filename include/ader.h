@@ -4,7 +4,9 @@
  * The library advances first-order hyperbolic systems
  *     dQ/dt + div F(Q) + B(Q) . grad Q = S(Q) + sum_i delta_i          (Eq. (1), Sec. 2)
  * on uniform Cartesian grids with the ADER-DG scheme of Sec. 3.3: per cell an element-local
- * space-time predictor (Eq. (5), fixed-point iteration), per face a Rusanov numerical flux
+ * space-time predictor (Eq. (5), fixed-point iteration from a constant or a continuous extension
+ * Runge-Kutta guess, or the Cauchy-Kowalevski procedure for the linear elastic system), per face
+ * a Rusanov numerical flux
  * (with a path-conservative fluctuation for B(Q).grad Q), per cell the corrector Eq. (6),
  * the CFL time step Eq. (7) and, for the Euler equations, the a-posteriori FV subcell limiter
  * of Sec. 3.5.  PDE terms follow the user functions of Table 2 (flux, nonConservativeProduct,

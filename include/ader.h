@@ -6,10 +6,9 @@
  * on uniform Cartesian grids with the ADER-DG scheme of Sec. 3.3: per cell an element-local
  * space-time predictor (Eq. (5), fixed-point iteration from a constant or a continuous extension
  * Runge-Kutta guess, or the Cauchy-Kowalevski procedure for the linear elastic system), per face
- * a Rusanov numerical flux
- * (with a path-conservative fluctuation for B(Q).grad Q), per cell the corrector Eq. (6),
- * the CFL time step Eq. (7) and, for the Euler equations, the a-posteriori FV subcell limiter
- * of Sec. 3.5.  PDE terms follow the user functions of Table 2 (flux, nonConservativeProduct,
+ * a Rusanov numerical flux (with a path-conservative fluctuation for B(Q).grad Q), per cell the
+ * corrector Eq. (6), the CFL time step Eq. (7) and, for the Euler equations, the a-posteriori FV
+ * subcell limiter of Sec. 3.5.  PDE terms follow the user functions of Table 2 (flux, nonConservativeProduct,
  * pointSource, eigenvalues, boundaryValues, multiplyMaterialParameterMatrix,
  * isPhysicallyAdmissable), built in for three systems: scalar advection (tests), compressible
  * Euler (Eq. (8), gamma-law pressure of Sec. 6.1) and linear elasticity (Sec. 2.1).

@@ -154,3 +154,68 @@ def test_non_finite_candidate_is_troubled():
     bad[5, 1, 1, 2] = float('nan')
     tr, _ = lim.detect(bad, rep)
     assert bool(tr[5]) and int(tr.sum()) == 1
+
+
+# ---- the relaxed DMP band and positivity, on cell-wise constant states (subcell averages of a
+# constant cell are that constant) ----------------------------------------------------------------
+
+def _constant_cells(s, values):
+    """[C, n, n, 4] with the conserved state values[c] (rho, jx, jy, E) in every node of cell c."""
+    n = s.n
+    v = torch.as_tensor(values, dtype=torch.float64)
+    return v[:, None, None, :].expand(v.shape[0], n, n, 4).clone()
+
+
+def _flat(C, rho=1.0, E=2.5):
+    return [[rho, 0.0, 0.0, E] for _ in range(C)]
+
+
+def test_dmp_band_is_delta0_on_a_flat_neighbourhood():
+    """m = M everywhere: the band is delta0 = 1e-4 on both sides, only the raised cell flips."""
+    s, lim = make((4, 4), 2, (0, 0), (1, 1), 'periodic')
+    base = _constant_cells(s, _flat(16))
+    rep = lim.project(base)
+    for shift, troubled in ((0.9e-4, False), (1.1e-4, True), (-0.9e-4, False), (-1.1e-4, True)):
+        cand = base.clone()
+        cand[5, ..., 0] += shift
+        tr, _ = lim.detect(cand, rep)
+        assert bool(tr[5]) == troubled, shift
+        assert int(tr.sum()) == int(troubled)
+
+
+def test_dmp_band_scales_with_the_face_neighbourhood_range():
+    """A face neighbour at rho = 2 makes the range 1 and the band 1e-3 (M - m) = 1e-3 > delta0;
+    a diagonal neighbour at rho = 2 does not widen the band (face neighbourhood)."""
+    s, lim = make((4, 4), 2, (0, 0), (1, 1), 'periodic')
+    vals = _flat(16)
+    vals[6][0] = 2.0                         # (2, 1): face neighbour of cell 5 = (1, 1)
+    rep = lim.project(_constant_cells(s, vals))
+    for rho, troubled in ((2.0 + 0.9e-3, False), (2.0 + 1.1e-3, True), (1.0 - 0.9e-3, False)):
+        cand_vals = [list(v) for v in vals]
+        cand_vals[5][0] = rho
+        tr, _ = lim.detect(_constant_cells(s, cand_vals), rep)
+        assert bool(tr[5]) == troubled, rho
+    vals = _flat(16)
+    vals[10][0] = 2.0                        # (2, 2): diagonal to cell 5
+    rep = lim.project(_constant_cells(s, vals))
+    cand_vals = [list(v) for v in vals]
+    cand_vals[5][0] = 1.5
+    tr, _ = lim.detect(_constant_cells(s, cand_vals), rep)
+    assert bool(tr[5])
+
+
+def test_positivity_is_checked_inside_the_dmp_band():
+    """Neighbourhood bands jx in [-2, 2], E in [1.5, 2.5], rho = 1: the candidate (1, 1.9, 0, 1.5)
+    is inside every band but has p = 0.4 (1.5 - 1.9^2 / 2) < 0, so it is troubled; (1, 1, 0, 1.5)
+    (p = 0.4) is not."""
+    s, lim = make((4, 4), 2, (0, 0), (1, 1), 'periodic')
+    vals = _flat(16)
+    vals[5] = [1.0, 2.0, 0.0, 2.5]
+    vals[6] = [1.0, -2.0, 0.0, 2.5]
+    vals[9] = [1.0, 0.0, 0.0, 1.5]
+    rep = lim.project(_constant_cells(s, vals))
+    for jx, troubled in ((1.9, True), (1.0, False)):
+        cand_vals = [list(v) for v in vals]
+        cand_vals[5] = [1.0, jx, 0.0, 1.5]
+        tr, _ = lim.detect(_constant_cells(s, cand_vals), rep)
+        assert bool(tr[5]) == troubled, jx

@@ -221,10 +221,14 @@ class ADERDG:
         return self.cfl / (self.D * (2 * self.N + 1)) * min(self.grid.h) / lam
 
     def ncp_term(self, q, axfun):
-        """sum_d B_d(m) (1/h_d) D_d q at every node (cell-constant B)."""
+        """sum_d B_d (1/h_d) D_d q at every node: B_d(m) cell-constant (material), or B_d(q) of
+        the node's own state (``pde.ncp_state``)."""
         out = 0.0
         for d in range(self.D):
             gq = contract(q, self.ref.D, axfun(d)) / self.grid.h[d]
+            if getattr(self.pde, "ncp_state", False):
+                out = out + self.pde.ncp(q, gq, d)
+                continue
             B = self.pde.ncp_matrix(self.mat, d)  # [C, nv, nv]
             if B.dim() == 2:
                 B = B.unsqueeze(0).expand(q.shape[0], -1, -1)
@@ -440,6 +444,13 @@ class ADERDG:
         G = 0.5 * (FL + FR) - 0.5 * s * dq
         if not self.pde.has_ncp:
             return G, G
+        if getattr(self.pde, "ncp_state", False):
+            # path-conservative fluctuation along the straight segment in state space, per face
+            # node: int_0^1 B_n(qL + z (qR - qL)) dz dq by the 3-point rule
+            fl = 0.0
+            for z, wz in zip(self.path_z, self.path_w):
+                fl = fl + wz * self.pde.ncp(qL + z * dq, dq, d)
+            return G + 0.5 * fl, G - 0.5 * fl
         Bbar = 0.0
         for z, wz in zip(self.path_z, self.path_w):
             m = mL + z * (mR - mL) if mL is not None else None

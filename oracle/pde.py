@@ -172,3 +172,50 @@ class Elastic:
         s2 = sxx ** 2 + syy ** 2 + szz ** 2 + 2 * (sxy ** 2 + sxz ** 2 + syz ** 2)
         strain = (s2 - lam / (3 * lam + 2 * mu) * tr ** 2) / (4 * mu)
         return 0.5 * rho * (v ** 2).sum(-1) + strain
+
+
+class ShallowWater:
+    """Shallow water equations with bathymetry, Eq. (9) of Sec. 2: Q = (h, hu, hv, b),
+    F_x = (hu, hu u, hv u, 0), F_y = (hv, hu v, hv v, 0); the hydrostatic pressure and the
+    bathymetry slope are the non-conservative product, g h d(b + h)/dx_d on the momentum of
+    direction d (the bathymetry b is a state variable that the equations keep constant)."""
+
+    has_flux = True
+    has_ncp = True
+    ncp_state = True     # B depends on the state (not on cell-constant material)
+    nmat = 0
+    linear = False
+
+    def __init__(self, g=9.81):
+        self.dim = 2
+        self.nvar = 4
+        self.g = float(g)
+
+    def flux(self, q, d):
+        ud = q[..., 1 + d] / q[..., 0]
+        return torch.stack([q[..., 1 + d], q[..., 1] * ud, q[..., 2] * ud,
+                            torch.zeros_like(ud)], dim=-1)
+
+    def ncp(self, q, dq, d):
+        """B_d(q) dq: g h (dq_h + dq_b) on the momentum of direction d, zero elsewhere."""
+        out = torch.zeros_like(dq)
+        out[..., 1 + d] = self.g * q[..., 0] * (dq[..., 0] + dq[..., 3])
+        return out
+
+    def max_speed(self, q, d, mat=None):
+        """|u_d| + sqrt(g h): the largest |eigenvalue| of the direction-d system matrix."""
+        h = q[..., 0]
+        return torch.abs(q[..., 1 + d] / h) + torch.sqrt(self.g * h)
+
+    def mirror(self, q, d):
+        """Reflecting-wall ghost state: the normal momentum changes sign."""
+        s = torch.ones(self.nvar, dtype=q.dtype)
+        s[1 + d] = -1.0
+        return q * s
+
+    def mirror_flux(self, F, d):
+        """F_d of the mirrored state: the normal momentum flux h u_d^2 is even in u_d, the others
+        are odd."""
+        s = -torch.ones(self.nvar, dtype=F.dtype)
+        s[1 + d] = 1.0
+        return F * s

@@ -14,7 +14,8 @@ the method, in the paper's order:
 * ``refelem``  - Gauss-Legendre nodes, Lagrange basis, derivative and end-value tables,
                  the time-stiffness matrix of the predictor, subcell projections.
 * ``pde``      - flux / non-conservative product / eigenvalue terms of the PDEs used
-                 (scalar advection, compressible Euler, linear elasticity).
+                 (scalar advection, compressible Euler, linear elasticity, shallow water
+                 with bathymetry).
 * ``aderdg``   - CFL time step, Picard and Cauchy-Kowalevski space-time predictors, time averages, face
                  extrapolation, Rusanov Riemann solver, corrector, point source, receivers.
 * ``limiter``  - subcell projection, relaxed DMP + positivity detection, MUSCL-Hancock

@@ -213,15 +213,47 @@ class Limiter:
             X = X / ref.w.reshape(shape)
         return X
 
-    def step(self, u, rep, dt, t=0.0, force=False):
-        """One limited step.  Returns (u_new, troubled[C] bool, rep_new)."""
+    def face_neighbours(self, mask):
+        """Cells that share a face with a cell of ``mask`` (inside the domain)."""
+        g = self.s.grid
+        out = torch.zeros_like(mask)
+        for d in range(self.D):
+            for side in (1, -1):
+                nb = g.neighbor(d, side)
+                out |= (nb >= 0) & mask[nb.clamp(min=0)]
+        return out
+
+    def step_hybrid(self, u, rep, status, dt, t=0.0, persist=2, layer=True):
+        """One step of the hybrid ADER-DG / FV scheme (Sec. 3.5): cells stay FV for several steps
+        after they were troubled, and their face neighbours form an interface layer that also
+        computes with FV.  ``status``[C] holds the FV steps a cell still has to take (0: DG).
+          FV set = detected | (status > 0) | (face neighbours of those, with ``layer``);
+          status_new = persist where detected, else max(status - 1, 0).
+        The DG candidate of every cell is still checked (a cell that would be troubled restarts
+        its count).  With persist = 0 and layer = False this is ``step``.
+        Returns (u_new, fv[C], rep_new, admissible, status_new)."""
+        u_new, fv, rep_new, ok, detected = self.step(u, rep, dt, t, status=status, layer=layer,
+                                                     return_detected=True)
+        status_new = torch.where(detected, torch.full_like(status, persist),
+                                 (status - 1).clamp(min=0))
+        return u_new, fv, rep_new, ok, status_new
+
+    def step(self, u, rep, dt, t=0.0, force=False, status=None, layer=False,
+             return_detected=False):
+        """One limited step.  Returns (u_new, troubled[C] bool, rep_new, admissible); the
+        troubled set is recomputed with FV.  ``status`` / ``layer``: see ``step_hybrid``."""
         s = self.s
         g = s.grid
         D, ns = self.D, self.ns
         u_star, info = s.step(u, dt, t, details=True)
         troubled, cand = self.detect(u_star, rep)
+        detected = troubled
         if force:
             troubled = torch.ones_like(troubled)
+        if status is not None:
+            troubled = troubled | (status > 0)
+        if layer:
+            troubled = troubled | self.face_neighbours(troubled)
         u_new = u_star.clone()
         rep_new = cand.clone()
         if troubled.any():
@@ -274,4 +306,6 @@ class Limiter:
             admissible = self.admissible(rep_new[troubled])
         else:
             admissible = torch.ones(0, dtype=torch.bool)
+        if return_detected:
+            return u_new, troubled, rep_new, bool(admissible.all()), detected
         return u_new, troubled, rep_new, bool(admissible.all())

@@ -219,3 +219,58 @@ def test_positivity_is_checked_inside_the_dmp_band():
         cand_vals[5] = [1.0, jx, 0.0, 1.5]
         tr, _ = lim.detect(_constant_cells(s, cand_vals), rep)
         assert bool(tr[5]) == troubled, jx
+
+
+# ---- hybrid ADER-DG / FV status (cells stay FV for several steps, FV interface layer) ---------
+
+def test_hybrid_without_persistence_or_layer_is_the_per_step_limiter():
+    s, lim, u, rep = explosion((8, 8), 2)
+    u2, rep2 = u.clone(), rep.clone()
+    status = torch.zeros(64, dtype=torch.long)
+    for _ in range(3):
+        dt = s.cfl_dt(u)
+        u, tr, rep, ok = lim.step(u, rep, dt)
+        u2, fv, rep2, ok2, status = lim.step_hybrid(u2, rep2, status, dt, persist=0, layer=False)
+        assert torch.equal(tr, fv) and torch.equal(u, u2) and torch.equal(rep, rep2)
+        assert not status.any()
+
+
+def test_hybrid_conserves_mass_and_energy_and_keeps_the_symmetry():
+    s, lim, u, rep = explosion((8, 8), 2)
+    m0 = totals(s, u)
+    status = torch.zeros(64, dtype=torch.long)
+    for _ in range(4):
+        u, fv, rep, ok, status = lim.step_hybrid(u, rep, status, s.cfl_dt(u), persist=2, layer=True)
+        assert ok
+    m1 = totals(s, u)
+    assert abs(float(m1[0] - m0[0])) < 1e-13 * float(m0[0])
+    assert abs(float(m1[3] - m0[3])) < 1e-13 * float(m0[3])
+    F = fv.reshape(8, 8)
+    assert torch.equal(F, F.flip(0)) and torch.equal(F, F.flip(1)) and torch.equal(F, F.T)
+    uu = u.reshape(8, 8, 3, 3, 4)
+    assert torch.allclose(uu[..., 0], uu.transpose(0, 1).transpose(2, 3)[..., 0], atol=1e-12)
+
+
+def test_hybrid_status_counts_down_with_its_interface_layer():
+    """Smooth data (nothing detected): a cell given two FV steps is FV with its four face
+    neighbours for two steps, then the whole grid is DG again."""
+    s, lim = make((6, 6), 2, (0, 0), (1, 1), 'periodic')
+    u = T(synth.entropy_wave(coords(s), amp=1e-3))
+    u, rep = lim.initial_rep(u)
+    status = torch.zeros(36, dtype=torch.long)
+    status[14] = 2                                   # cell (2, 2)
+    layer = {14, 13, 15, 8, 20}
+    for k, expect in enumerate((layer, layer, set())):
+        u, fv, rep, ok, status = lim.step_hybrid(u, rep, status, s.cfl_dt(u), persist=2)
+        assert set(torch.nonzero(fv).flatten().tolist()) == expect, k
+        assert ok
+
+
+def test_hybrid_with_every_cell_fv_is_the_pure_fv_scheme():
+    s, lim, u, rep = explosion((6, 6), 2)
+    dt = s.cfl_dt(u)
+    status = torch.ones(36, dtype=torch.long)
+    u1, fv, rep1, ok, _ = lim.step_hybrid(u, rep, status, dt)
+    U_all, _ = lim.fv_global(rep, dt)
+    assert fv.all() and torch.equal(rep1, U_all)
+    assert torch.equal(u1, lim.reconstruct(U_all))

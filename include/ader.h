@@ -103,7 +103,10 @@ typedef struct {
   double adv[3];       /* advection velocity (ADER_PDE_ADVECTION) */
   int picard_iters;    /* fixed number of predictor iterations; 0 => order + 1 */
   int limiter;         /* a-posteriori FV subcell limiter (Euler, order <= 4): 0 off, 1 on,
-                          2 every cell troubled (the pure FV scheme, for tests) */
+                          2 every cell troubled (the pure FV scheme, for tests), 3 hybrid
+                          ADER-DG / FV status (Sec. 3.5): a troubled cell stays FV for two
+                          more steps and its face neighbours also compute with FV; the
+                          counts restart at ader_set_state */
   int precision;       /* ader_prec */
   int predictor;       /* ader_predictor (0 = Picard) */
   int initial_guess;   /* ader_guess (0 = constant in time) */

@@ -69,7 +69,25 @@ struct SubTables {
   double Pf[MAXNS][MAXN];  // P1[s][m] / (w_m ns): subface flux -> nodal face flux weights
 };
 
-struct LimArgs;
+// Arguments of the limiter kernels (Sec. 3.5).
+struct LimArgs {
+  const double* rep;     // [C][NSS][NV] representation at t^n
+  double* rep_new;       // [C][NSS][NV] representation at t^{n+1}
+  const double* mm;      // [C][2][NV] min / max of rep
+  double* mm_new;
+  const uint8_t* flags_prev;  // [C] troubled at the previous step (unused by the kernels)
+  uint8_t* flags;        // [C] recomputed with FV at this step (the troubled cells; with the
+                         // hybrid status, the widened set)
+  int* list;             // [C] troubled cells (first n_troubled entries)
+  double* bflux;         // [C][D][2][NSF][NV] subface fluxes on the cell boundary
+  int force;             // 1: every cell troubled (pure FV scheme)
+  double delta0, eps;
+  // hybrid ADER-DG / FV status (null: per-step limiter): FV steps each cell still has to take,
+  // and the detected-or-counting set before the interface layer is added
+  uint8_t* status;
+  uint8_t* base;
+  int persist;           // FV steps a detected cell keeps
+};
 struct AdjArgs;
 
 // Ensemble of runs advanced together (one persistent launch per phase of the step for all runs):

@@ -23,18 +23,6 @@ struct AdjArgs {
   double* scratch;
   long long scratch_per_block;
 };
-struct LimArgs {
-  const double* rep;
-  double* rep_new;
-  const double* mm;
-  double* mm_new;
-  const uint8_t* flags_prev;
-  uint8_t* flags;
-  int* list;
-  double* bflux;
-  int force;
-  double delta0, eps;
-};
 }  // namespace ader
 
 using namespace ader;
@@ -335,6 +323,7 @@ struct ader_ctx {
   double *rep = nullptr, *rep_new = nullptr, *mm = nullptr, *mm_new = nullptr, *bflux = nullptr;
   uint8_t* flags = nullptr;
   int* list = nullptr;
+  uint8_t *lstatus = nullptr, *lbase = nullptr;  // hybrid status (limiter = 3)
   long long nss = 0;
   // adjoint work buffers (allocated on the first ader_adjoint_step)
   DevScalars* dev_adj = nullptr;
@@ -394,6 +383,8 @@ static void free_all(ader_ctx* c) {
   cudaFree(c->mm_new);
   cudaFree(c->bflux);
   cudaFree(c->flags);
+  cudaFree(c->lstatus);
+  cudaFree(c->lbase);
   cudaFree(c->list);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   c->ev.clear();
@@ -489,7 +480,7 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
   // the predictor keeps a cell in shared memory: at most 227 KB per block on sm_103a, less the
   // kernel's static tables (the 3-D Euler mixed form at order 6 does not fit)
   if (fam->predictor_smem(cfg->order, cfg->precision) > 232448 - 4096) return ADER_EUNSUPPORTED;
-  if (cfg->limiter < 0 || cfg->limiter > 2) return ADER_EINVAL;
+  if (cfg->limiter < 0 || cfg->limiter > 3) return ADER_EINVAL;
   if (cfg->limiter) {
     if (cfg->pde != ADER_PDE_EULER) return ADER_EUNSUPPORTED;
     if (cfg->order > (cfg->dim == 2 ? limiter_max_order2() : limiter_max_order3())) return ADER_EUNSUPPORTED;
@@ -568,6 +559,11 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
     if (e == cudaSuccess) e = cudaMalloc(&c->flags, ncells);
     if (e == cudaSuccess) e = cudaMalloc(&c->list, ncells * sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, ncells, c->stream);
+    if (cfg->limiter == 3) {
+      if (e == cudaSuccess) e = cudaMalloc(&c->lstatus, ncells);
+      if (e == cudaSuccess) e = cudaMalloc(&c->lbase, ncells);
+      if (e == cudaSuccess) e = cudaMemsetAsync(c->lstatus, 0, ncells, c->stream);
+    }
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -620,6 +616,7 @@ ader_status ader_set_state(ader_ctx* c, const double* q, int64_t count, int on_d
     CUDA_OK(c->fam->lim_init(c->cfg.order, c->u, nullptr, nullptr, c->rep, c->mm, c->g.ncells,
                              c->sub, c->stream));
     CUDA_OK(cudaMemsetAsync(c->flags, 0, c->g.ncells, c->stream));
+    if (c->lstatus) CUDA_OK(cudaMemsetAsync(c->lstatus, 0, c->g.ncells, c->stream));
   }
   c->state_set = true;
   return ADER_OK;
@@ -850,6 +847,11 @@ static ader_status step_impl(ader_ctx* c, double dt, double t_end) {
   if (c->cfg.limiter) {
     LimArgs l{c->rep, c->rep_new, c->mm, c->mm_new, nullptr, c->flags, c->list, c->bflux,
               c->cfg.limiter == 2 ? 1 : 0, 1e-4, 1e-3};
+    if (c->cfg.limiter == 3) {
+      l.status = c->lstatus;
+      l.base = c->lbase;
+      l.persist = 2;
+    }
     CUDA_OK(c->fam->lim_step(a, l, c->tab, c->sub, s));
     std::swap(c->rep, c->rep_new);
     std::swap(c->mm, c->mm_new);

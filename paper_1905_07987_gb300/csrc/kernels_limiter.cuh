@@ -20,18 +20,47 @@
 
 namespace ader {
 
-struct LimArgs {
-  const double* rep;     // [C][NSS][NV] representation at t^n
-  double* rep_new;       // [C][NSS][NV] representation at t^{n+1}
-  const double* mm;      // [C][2][NV] min / max of rep
-  double* mm_new;
-  const uint8_t* flags_prev;  // [C] troubled at the previous step (unused by the kernels)
-  uint8_t* flags;        // [C] troubled at this step
-  int* list;             // [C] troubled cells (first n_troubled entries)
-  double* bflux;         // [C][D][2][NSF][NV] subface fluxes on the cell boundary
-  int force;             // 1: every cell troubled (pure FV scheme)
-  double delta0, eps;
-};
+// Hybrid status (Sec. 3.5): a detected cell keeps `persist` FV steps, the others count down;
+// base = detected or still counting.
+static __global__ void __launch_bounds__(256) k_lim_status(const uint8_t* __restrict__ flags,
+                                                           uint8_t* __restrict__ status,
+                                                           uint8_t* __restrict__ base,
+                                                           long long ncells, int persist) {
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncells;
+       c += (long long)gridDim.x * blockDim.x) {
+    const bool det = flags[c] != 0;
+    const int st = status[c];
+    base[c] = (det || st > 0) ? 1 : 0;
+    status[c] = (uint8_t)(det ? persist : (st > 0 ? st - 1 : 0));
+  }
+}
+
+// The FV set of the hybrid step: the base cells and their face neighbours (the interface layer
+// that computes with FV and projects to DG); neighbours across a periodic boundary wrap, a
+// non-periodic boundary has none.
+static __global__ void __launch_bounds__(256) k_lim_layer(const uint8_t* __restrict__ base,
+                                                          uint8_t* __restrict__ flags,
+                                                          const Geometry g) {
+  const long long n0 = g.n[0], n1 = g.dim > 1 ? g.n[1] : 1;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.ncells;
+       c += (long long)gridDim.x * blockDim.x) {
+    const long long id[3] = {c % n0, (c / n0) % n1, c / (n0 * n1)};
+    const long long stride[3] = {1, n0, n0 * n1};
+    uint8_t f = base[c];
+    for (int d = 0; d < g.dim; ++d) {
+      const long long nd = g.n[d];
+      for (int side = -1; side <= 1; side += 2) {
+        long long k = id[d] + side;
+        if (k < 0 || k >= nd) {
+          if (g.bc[d][0] != BC_PERIODIC) continue;
+          k = (k + nd) % nd;
+        }
+        f |= base[c + (k - id[d]) * stride[d]];
+      }
+    }
+    flags[c] = f ? 1 : 0;
+  }
+}
 
 template <int D, int N>
 struct CfgL {
@@ -672,6 +701,13 @@ struct LimLaunch {
     k_lim_detect<D, N><<<nc, C::TPB, C::SMEM_P, s>>>(a, l, S);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (l.status) {  // hybrid status: widen the flags before the compaction
+      const unsigned blocks = (unsigned)((a.g.ncells + 255) / 256);
+      k_lim_status<<<blocks, 256, 0, s>>>(l.flags, l.status, l.base, a.g.ncells, l.persist);
+      k_lim_layer<<<blocks, 256, 0, s>>>(l.base, l.flags, a.g);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
     k_lim_compact<<<(unsigned)((a.g.ncells + 255) / 256), 256, 0, s>>>(l.flags, l.list,
                                                                          &a.dev->n_troubled, a.g.ncells);
     e = cudaGetLastError();

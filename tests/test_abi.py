@@ -75,6 +75,10 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     assert lib.ader_create(ctypes.byref(cfg), None, ctypes.byref(h)) == ader.EUNSUPPORTED
     cfg = ader.make_config("euler", 3, 3, (4, 4, 4), (0,) * 3, (1,) * 3, "periodic", 0.5, initial_guess=5)
     assert lib.ader_create(ctypes.byref(cfg), None, ctypes.byref(h)) == ader.EINVAL
+    cfg = ader.make_config("euler", 3, 3, (4, 4, 4), (0,) * 3, (1,) * 3, "periodic", 0.5, limiter=4)
+    assert lib.ader_create(ctypes.byref(cfg), None, ctypes.byref(h)) == ader.EINVAL
+    cfg = ader.make_config("elastic", 3, 3, (4, 4, 4), (0,) * 3, (1,) * 3, "absorbing", 0.5, limiter=3)
+    assert lib.ader_create(ctypes.byref(cfg), None, ctypes.byref(h)) == ader.EUNSUPPORTED
     assert lib.ader_step(None, 0.0, 0.0) == ader.EINVAL
     lib.ader_destroy(None)
 

@@ -139,3 +139,19 @@ def test_mixed_limited_run_conserves_and_tracks_fp64():
     diff = np.abs(out["mixed"] - out["fp64"]).max(axis=tuple(range(out["fp64"].ndim - 1)))
     scale = np.abs(out["fp64"]).max(axis=tuple(range(out["fp64"].ndim - 1)))
     assert (diff <= 1e-3 * scale).all(), diff / scale
+
+
+@pytest.mark.parametrize("ncell,order,steps", [((10, 10), 2, 6), ((6, 6, 5), 2, 3)])
+def test_hybrid_status_run_matches_the_oracle(ncell, order, steps):
+    """limiter = 3 (troubled cells stay FV two more steps, face neighbours compute with FV):
+    the FV set and the state against the oracle's hybrid step, every step."""
+    c, lim, u0, Us, flags, u, rep = explosion_case(ncell, order, limiter=3)
+    gpu_set(c, u0, Us, flags)
+    status = torch.zeros(c.ctx.cells, dtype=torch.long)
+    for step in range(steps):
+        c.ctx.step()
+        dt = c.ctx.last_dt()
+        u, fv, rep, ok, status = lim.step_hybrid(u, rep, status, torch.tensor(dt, dtype=torch.float64),
+                                                 persist=2, layer=True)
+        assert np.array_equal(c.ctx.flags().astype(bool), fv.numpy()), step
+    assert rel_linf(c.get(), u.numpy()) <= 1e-11

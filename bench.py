@@ -453,8 +453,9 @@ def extra_adjoint(ader, synth, stream, n=40, N=4, steps=12, k=4):
 
 def extra_explosion(ader, synth, stream, steps=4, warmup=2, n=64):
     """3-D spherical explosion, order 3, n^3 cells (default 64^3) on [-1,1]^3, wall boundaries,
-    a-posteriori subcell limiter (7^3 subcells): FP64 and mixed predictor; step time, troubled
-    cells, conservation of mass and energy."""
+    a-posteriori subcell limiter (7^3 subcells): FP64 and mixed predictor, and the FP64 form with
+    the hybrid ADER-DG / FV status (troubled cells stay FV two more steps, an FV interface layer);
+    step time, cells recomputed with FV, conservation of mass and energy."""
     import torch
     N = 3
     x, w = ader.reference_nodes(N)
@@ -466,9 +467,9 @@ def extra_explosion(ader, synth, stream, steps=4, warmup=2, n=64):
     W = torch.from_numpy(np.einsum("i,j,k->ijk", w, w, w).reshape(-1)).cuda()
     dofs = n ** 3 * 64 * 5
     out = {"workload": f"explosion3d_p3_{n} (limiter on)", "dofs": dofs}
-    for prec in ("fp64", "mixed"):
+    for form, prec, limiter in (("fp64", "fp64", 1), ("mixed", "mixed", 1), ("fp64_hybrid", "fp64", 3)):
         cfg = ader.make_config("euler", 3, N, (n,) * 3, (-1,) * 3, (1,) * 3, "wall", synth.cfl_number(N),
-                               limiter=1, precision=prec)
+                               limiter=limiter, precision=prec)
         ctx = ader.Context(cfg, stream=stream.cuda_stream)
         ctx.set_state(u0_d)
         ctx.set_subcell_state(Us_d, fl)
@@ -493,7 +494,7 @@ def extra_explosion(ader, synth, stream, steps=4, warmup=2, n=64):
         ctx.enable_timing(False)
         ctx.sync()
         m1 = totals()
-        out[prec] = {"ms_per_step": ms / steps, "value": dofs * steps / (ms * 1e-3),
+        out[form] = {"ms_per_step": ms / steps, "value": dofs * steps / (ms * 1e-3),
                      "troubled_cells_last_step": ctx.troubled_count(),
                      "troubled_fraction": ctx.troubled_count() / n ** 3,
                      "phase_ms_per_step": {k: v / max(nr, 1) for k, v in ph.items()},

@@ -212,7 +212,9 @@ ader_status ader_run_graph(ader_ctx* ctx, int steps, int replays, double dt, dou
  * All pointers are device memory of the context's device ([cells][nodes][9] for u_n, lam, dJdu;
  * [cells][3]; [6]); dJdu may be NULL.  Uses the context's material, point source and order; the
  * context's own state and time are not touched.  Stream-ordered, no synchronisation.  The first
- * call allocates its work buffers (ADER_ENOMEM if that fails). */
+ * call allocates its work buffers (ADER_ENOMEM if that fails).  A non-finite adjoint or material
+ * gradient (for example from a non-finite u_n) is latched on the device and returned as
+ * ADER_ENONFINITE by the next synchronising call (ader_sync). */
 ader_status ader_adjoint_step(ader_ctx* ctx, double t_n, double dt, const double* u_n, double* lam,
                               const double* dJdu, double* grad_mat, double* grad_M);
 
@@ -233,8 +235,11 @@ ader_status ader_adjoint_step(ader_ctx* ctx, double t_n, double dt, const double
  *    (every location the kernels read is written first in the same call).  Calls whose work
  *    overlaps on the GPU (different streams or contexts on the same device) race on it and must
  *    be ordered by the caller.
- *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- *    make that first call before any stream capture begins.
+ *  - The first call in each CUDA context looks up the array's device address
+ *    (cudaGetSymbolAddress; the address is cached per context id, so a context created after a
+ *    device reset gets its own); make that first call before any stream capture begins.
+ *  - Device-side errors (a non-finite adjoint or gradient) are returned by the next ader_sync,
+ *    as for ader_adjoint_step.
  *  - The context's next-state and face buffers (allocated by ader_create) are overwritten, as in
  *    ader_adjoint_step. */
 ader_status ader_adjoint_step_static(ader_ctx* ctx, double t_n, double dt, const double* u_n,

@@ -186,6 +186,7 @@ struct Family {
                               cudaStream_t);
 };
 cudaError_t launch_set_scalars(DevScalars* d, double t, double dt, cudaStream_t s);
+cudaError_t launch_merge_status(DevScalars* src, DevScalars* dst, cudaStream_t s);
 cudaError_t launch_sub(const double* a, const double* b, double* out, int n, cudaStream_t s);
 cudaError_t launch_misfit(const double* a, const double* b, long long n, double scale, double* J,
                           cudaStream_t s);

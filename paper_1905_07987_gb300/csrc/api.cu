@@ -968,6 +968,8 @@ ader_status ader_adjoint_step(ader_ctx* c, double t_n, double dt, const double* 
   CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
   AdjArgs j{u_n, lam, dJdu, grad_mat, grad_M, c->adjf, c->gface, c->adj_scratch, c->adj_spb};
   CUDA_OK(c->fam->adj_run(a, j, c->tab, c->adj_blocks, c->stream));
+  // errors latched by the adjoint kernels reach the context's status word (ader_sync)
+  CUDA_OK(launch_merge_status(c->dev_adj, c->dev, c->stream));
   return ADER_OK;
 }
 
@@ -979,10 +981,67 @@ ader_status ader_adjoint_step(ader_ctx* c, double t_n, double dt, const double* 
 // a device address: its device address is looked up once per device below.
 namespace {
 constexpr size_t kStaticScratchBytes = 64ull << 20;  // 64 MiB
-constexpr int kMaxDevices = 64;
+constexpr int kMaxContexts = 64;
 static __device__ __align__(256) unsigned char g_adj_static[kStaticScratchBytes];
 std::mutex g_adj_static_mu;
-void* g_adj_static_addr[kMaxDevices] = {};
+// A symbol's device address belongs to one CUDA context: the addresses are cached per context,
+// keyed by the driver's context id (unique for the life of the process, so a context created
+// after a device reset gets a fresh entry).  Without the driver entry points the address is
+// looked up on every call.
+struct StaticAddr {
+  unsigned long long ctx_id;
+  void* addr;
+};
+StaticAddr g_adj_static_addr[kMaxContexts] = {};
+int g_adj_static_n = 0;
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_cur = (CtxGetCurrentFn)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = (CtxGetIdFn)f;
+  }
+  if (!get_cur || !get_id) return false;
+  void* ctx = nullptr;
+  if (get_cur(&ctx) != 0 || !ctx) return false;
+  return get_id(ctx, id) == 0;
+}
+
+// Device address of the static array in the current context (cudaGetSymbolAddress on the first
+// call in a context).
+cudaError_t static_array_address(void** out) {
+  std::lock_guard<std::mutex> lock(g_adj_static_mu);
+  unsigned long long id = 0;
+  const bool have_id = current_context_id(&id);
+  if (have_id)
+    for (int i = 0; i < g_adj_static_n; ++i)
+      if (g_adj_static_addr[i].ctx_id == id) {
+        *out = g_adj_static_addr[i].addr;
+        return cudaSuccess;
+      }
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_adj_static);
+  if (e != cudaSuccess) return e;
+  if (!p) return cudaErrorInvalidSymbol;
+  if (have_id) {
+    const int slot = g_adj_static_n < kMaxContexts ? g_adj_static_n++ : (int)(id % kMaxContexts);
+    g_adj_static_addr[slot] = {id, p};
+  }
+  *out = p;
+  return cudaSuccess;
+}
 
 size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 }  // namespace
@@ -1000,18 +1059,8 @@ ader_status ader_adjoint_step_static(ader_ctx* c, double t_n, double dt, const d
   if (!c->mat_set) return ADER_ESTATE;
   int dev = 0;
   CUDA_OK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return ADER_EUNSUPPORTED;
   void* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_adj_static_mu);
-    if (!g_adj_static_addr[dev]) {
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_adj_static);
-      if (e != cudaSuccess || !p) return ADER_ECUDA;
-      g_adj_static_addr[dev] = p;
-    }
-    base = g_adj_static_addr[dev];
-  }
+  CUDA_OK(static_array_address(&base));
   // layout: device scalars | face adjoints | face material gradients | per-block iterate slabs
   const int iters = c->cfg.picard_iters > 0 ? c->cfg.picard_iters : c->cfg.order + 1;
   long long nfaces = 0;
@@ -1032,6 +1081,7 @@ ader_status ader_adjoint_step_static(ader_ctx* c, double t_n, double dt, const d
   double* adjf = (double*)(p + b_dev);
   double* gface = (double*)(p + b_dev + b_adjf);
   double* slab = (double*)(p + fixed);
+  CUDA_OK(cudaMemsetAsync(&dev_s->status, 0, sizeof(int), c->stream));
   CUDA_OK(launch_set_scalars(dev_s, t_n, dt, c->stream));
   StepArgs a = make_args(c, dt, 0.0);
   a.u = u_n;
@@ -1040,6 +1090,9 @@ ader_status ader_adjoint_step_static(ader_ctx* c, double t_n, double dt, const d
   CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
   AdjArgs j{u_n, lam, dJdu, grad_mat, grad_M, adjf, gface, slab, spb};
   CUDA_OK(c->fam->adj_run(a, j, c->tab, (int)blocks, c->stream));
+  // errors latched in the array's scalars reach the context's status word (ader_sync), and the
+  // scalars start the next call clear
+  CUDA_OK(launch_merge_status(dev_s, c->dev, c->stream));
   return ADER_OK;
 }
 

@@ -84,6 +84,16 @@ __global__ void k_set_scalars(DevScalars* d, double t, double dt) {
   d->dt = dt;
 }
 
+// Move the error bits latched in `src` (the adjoint's scalars) into `dst` (the context's status
+// word, which ader_sync reads) and clear them in `src`.
+__global__ void k_merge_status(DevScalars* src, DevScalars* dst) {
+  const int bits = src->status;
+  if (bits) {
+    atomicOr(&dst->status, bits);
+    src->status = 0;
+  }
+}
+
 // dJ/du[cell_r][j][v] += scale * res[r][v] * Phi_j(xi_r), receivers in order (deterministic: each
 // thread owns one (node, component) slot).
 __global__ void k_receivers_adjoint(Receivers r, const double* res, double scale, double* dJdu,
@@ -133,6 +143,11 @@ cudaError_t launch_misfit(const double* a, const double* b, long long n, double 
 
 cudaError_t launch_set_scalars(DevScalars* d, double t, double dt, cudaStream_t s) {
   k_set_scalars<<<1, 1, 0, s>>>(d, t, dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_status(DevScalars* src, DevScalars* dst, cudaStream_t s) {
+  k_merge_status<<<1, 1, 0, s>>>(src, dst);
   return cudaGetLastError();
 }
 

@@ -430,6 +430,7 @@ __global__ void __launch_bounds__(Cfg<Elastic, 3, N>::TPB)
       __syncthreads();
     }
     // q^0 = 1 (x) u
+    bool bad = false;
 #pragma unroll
     for (int k = 0; k < LPT; ++k) {
       const int l = threadIdx.x + k * TPB;
@@ -439,7 +440,10 @@ __global__ void __launch_bounds__(Cfg<Elastic, 3, N>::TPB)
       double out = lam_l[k] + uh[k];
       if (J.dJdu) out += J.dJdu[c * NL + l];
       J.lam[c * NL + l] = out;
+      bad |= !isfinite(out);
     }
+    // a non-finite adjoint or gradient (e.g. from a non-finite forward state) is latched
+    if (bad) atomicOr(&A.dev->status, ST_NONFINITE);
     // ---- reductions: material gradient (+ faces), moment tensor ----------------------------
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = TPB >> 5;
 #pragma unroll
@@ -473,6 +477,8 @@ __global__ void __launch_bounds__(Cfg<Elastic, 3, N>::TPB)
         for (int q = 0; q < 3; ++q) tot[q] += gl[3 + q] + gr[q];
       }
       for (int q = 0; q < 3; ++q) J.grad_mat[c * 3 + q] += tot[q];
+      if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2]))
+        atomicOr(&A.dev->status, ST_NONFINITE);
       if (has_src)
         for (int q = 0; q < 6; ++q) {
           double s = 0.0;

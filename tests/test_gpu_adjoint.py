@@ -89,3 +89,30 @@ def test_receiver_adjoint_is_the_transpose_of_the_read_out():
     rhs = float((xr.reshape(-1) * dJ.cpu().numpy()).sum())
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
     assert np.allclose(Rx, c.oracle.record(torch.from_numpy(xr)).numpy(), atol=1e-12)
+
+
+@pytest.mark.parametrize("static", [False, True])
+def test_nonfinite_forward_state_is_reported(static):
+    """A NaN in the forward state u_n makes the material gradient non-finite: both adjoint entry
+    points latch it on the device and the next ader_sync returns ADER_ENONFINITE; the call after
+    that starts clean."""
+    from paper_1905_07987_gb300 import ader
+    ncell = (2, 2, 2)
+    mat = synth.elastic_material(ncell, seed=3)
+    c = Case("elastic", 3, 2, ncell, bc="absorbing", material=mat)
+    rng = np.random.default_rng(11)
+    u = rng.standard_normal(c.ctx.count)
+    u[5] = np.nan
+    u_n = torch.from_numpy(u).cuda()
+    lam = torch.from_numpy(rng.standard_normal(c.ctx.count)).cuda()
+    gm = torch.zeros(c.ctx.cells * 3, dtype=torch.float64, device="cuda")
+    gM = torch.zeros(6, dtype=torch.float64, device="cuda")
+    c.ctx.adjoint_step(0.0, 1e-3, u_n, lam, gm, gM, static=static)
+    with pytest.raises(ader.AderError) as e:
+        c.ctx.sync()
+    assert e.value.status == ader.ENONFINITE
+    # a finite call afterwards reports nothing
+    u_ok = torch.from_numpy(rng.standard_normal(c.ctx.count)).cuda()
+    gm.zero_()
+    c.ctx.adjoint_step(0.0, 1e-3, u_ok, lam.nan_to_num(0.0), gm, gM.zero_(), static=static)
+    c.ctx.sync()

@@ -106,7 +106,9 @@ typedef struct {
                           2 every cell troubled (the pure FV scheme, for tests), 3 hybrid
                           ADER-DG / FV status (Sec. 3.5): a troubled cell stays FV for two
                           more steps and its face neighbours also compute with FV; the
-                          counts restart at ader_set_state */
+                          counts restart at ader_set_state, and the cells that
+                          ader_set_subcell_state puts into the FV space start with two FV
+                          steps to take */
   int precision;       /* ader_prec */
   int predictor;       /* ader_predictor (0 = Picard) */
   int initial_guess;   /* ader_guess (0 = constant in time) */
@@ -190,7 +192,10 @@ ader_status ader_set_subcell_state(ader_ctx* ctx, const double* U_sub, const uin
                                    int on_device);
 ader_status ader_get_subcell_state(ader_ctx* ctx, double* U_sub, int on_device);
 
-/* Troubled-cell flags of the last step, [cells] bytes (1 = recomputed with FV), and the count. */
+/* Cells recomputed with FV at the last step, [cells] bytes (1 = FV), and their count.  With
+ * limiter = 1 these are the troubled cells (the a-posteriori detection); with limiter = 3 they
+ * are the hybrid FV set: the troubled cells, the cells still counting their FV steps, and the
+ * face neighbours of both (the interface layer). */
 ader_status ader_get_flags(ader_ctx* ctx, uint8_t* flags, int on_device);
 ader_status ader_troubled_count(ader_ctx* ctx, int64_t* count);
 

@@ -223,6 +223,15 @@ class Limiter:
                 out |= (nb >= 0) & mask[nb.clamp(min=0)]
         return out
 
+    @staticmethod
+    def initial_status(flags, persist=2):
+        """Hybrid status at t^0 (Sec. 3.5): the cells that start in the FV space along the
+        initial discontinuity count as troubled at the initial time and take ``persist`` FV
+        steps; the others start in DG (0)."""
+        flags = torch.as_tensor(flags, dtype=torch.bool)
+        return torch.where(flags, torch.full(flags.shape, persist, dtype=torch.long),
+                           torch.zeros(flags.shape, dtype=torch.long))
+
     def step_hybrid(self, u, rep, status, dt, t=0.0, persist=2, layer=True):
         """One step of the hybrid ADER-DG / FV scheme (Sec. 3.5): cells stay FV for several steps
         after they were troubled, and their face neighbours form an interface layer that also

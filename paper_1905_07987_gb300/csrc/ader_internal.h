@@ -187,6 +187,10 @@ struct Family {
 };
 cudaError_t launch_set_scalars(DevScalars* d, double t, double dt, cudaStream_t s);
 cudaError_t launch_merge_status(DevScalars* src, DevScalars* dst, cudaStream_t s);
+cudaError_t launch_seed_status(const uint8_t* flags, uint8_t* status, long long ncells,
+                               int persist, cudaStream_t s);
+// FV steps a detected cell keeps under the hybrid limiter status (limiter = 3)
+constexpr int LIM_PERSIST = 2;
 cudaError_t launch_sub(const double* a, const double* b, double* out, int n, cudaStream_t s);
 cudaError_t launch_misfit(const double* a, const double* b, long long n, double scale, double* J,
                           cudaStream_t s);

@@ -634,6 +634,9 @@ ader_status ader_set_subcell_state(ader_ctx* c, const double* U_sub, const uint8
   if (st != ADER_OK) return st;
   CUDA_OK(c->fam->lim_init(c->cfg.order, c->u, c->rep_new, c->flags, c->rep, c->mm, c->g.ncells,
                            c->sub, c->stream));
+  // hybrid status: the cells put into the FV space stay FV for LIM_PERSIST steps
+  if (c->lstatus)
+    CUDA_OK(launch_seed_status(c->flags, c->lstatus, c->g.ncells, LIM_PERSIST, c->stream));
   if (!on_device) CUDA_OK(cudaStreamSynchronize(c->stream));
   return ADER_OK;
 }
@@ -850,7 +853,7 @@ static ader_status step_impl(ader_ctx* c, double dt, double t_end) {
     if (c->cfg.limiter == 3) {
       l.status = c->lstatus;
       l.base = c->lbase;
-      l.persist = 2;
+      l.persist = LIM_PERSIST;
     }
     CUDA_OK(c->fam->lim_step(a, l, c->tab, c->sub, s));
     std::swap(c->rep, c->rep_new);

@@ -146,6 +146,24 @@ cudaError_t launch_set_scalars(DevScalars* d, double t, double dt, cudaStream_t 
   return cudaGetLastError();
 }
 
+// Hybrid limiter status at the start of a run: cells put into the FV space along the initial
+// discontinuity take `persist` FV steps, as if troubled at the initial time.
+__global__ void k_seed_status(const uint8_t* __restrict__ flags, uint8_t* __restrict__ status,
+                              long long ncells, int persist) {
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncells;
+       c += (long long)gridDim.x * blockDim.x)
+    if (flags[c]) status[c] = (uint8_t)persist;
+}
+
+cudaError_t launch_seed_status(const uint8_t* flags, uint8_t* status, long long ncells,
+                               int persist, cudaStream_t s) {
+  if (ncells <= 0) return cudaSuccess;
+  const long long blocks = (ncells + 255) / 256;
+  k_seed_status<<<(unsigned)(blocks < 65535 ? blocks : 65535), 256, 0, s>>>(flags, status, ncells,
+                                                                            persist);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_merge_status(DevScalars* src, DevScalars* dst, cudaStream_t s) {
   k_merge_status<<<1, 1, 0, s>>>(src, dst);
   return cudaGetLastError();

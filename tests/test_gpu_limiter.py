@@ -141,17 +141,44 @@ def test_mixed_limited_run_conserves_and_tracks_fp64():
     assert (diff <= 1e-3 * scale).all(), diff / scale
 
 
-@pytest.mark.parametrize("ncell,order,steps", [((10, 10), 2, 6), ((6, 6, 5), 2, 3)])
-def test_hybrid_status_run_matches_the_oracle(ncell, order, steps):
-    """limiter = 3 (troubled cells stay FV two more steps, face neighbours compute with FV):
-    the FV set and the state against the oracle's hybrid step, every step."""
-    c, lim, u0, Us, flags, u, rep = explosion_case(ncell, order, limiter=3)
+def shifted_explosion_case(ncell, order, lo, hi, bc, limiter=3):
+    """Explosion on a box that cuts the sphere, so that cells along the discontinuity touch the
+    domain boundary (and, periodic, wrap around it)."""
+    dim = len(ncell)
+    c = Case("euler", dim, order, ncell, lo=lo, hi=hi, bc=bc, limiter=limiter)
+    lim = Limiter(c.oracle)
+    u0 = synth.explosion(c.X)
+    Us = synth.explosion(synth.subcell_centres(lim.ns, c.ncell, c.lo, c.hi))
+    flags = synth.discontinuous_cells(Us)
+    u, rep = lim.initial_rep(torch.from_numpy(u0), torch.from_numpy(Us), torch.from_numpy(flags))
+    return c, lim, u0, Us, flags, u, rep
+
+
+@pytest.mark.parametrize("ncell,order,steps,box", [
+    ((10, 10), 2, 6, None), ((6, 6, 5), 2, 3, None),
+    # periodic, the sphere cut by the lower x face: FV cells on both wrapped boundaries
+    ((10, 10), 2, 5, ((-0.45, -1.0), (1.55, 1.0), "periodic")),
+    ((6, 5, 6), 2, 3, ((-0.45, -1.0, -1.0), (1.55, 1.0, 1.0), "periodic"))])
+def test_hybrid_status_run_matches_the_oracle(ncell, order, steps, box):
+    """limiter = 3 (troubled cells stay FV two more steps, face neighbours compute with FV; the
+    cells put into the FV space at the start count as troubled at t^0): the FV set and the state
+    against the oracle's hybrid step, every step."""
+    if box is None:
+        c, lim, u0, Us, flags, u, rep = explosion_case(ncell, order, limiter=3)
+    else:
+        c, lim, u0, Us, flags, u, rep = shifted_explosion_case(ncell, order, *box)
+        # the FV set reaches the periodic boundary in the direction that wraps
+        fl = flags.reshape(tuple(reversed(ncell)))
+        assert fl[..., 0].any()
     gpu_set(c, u0, Us, flags)
-    status = torch.zeros(c.ctx.cells, dtype=torch.long)
+    status = lim.initial_status(torch.from_numpy(flags), persist=2)
     for step in range(steps):
         c.ctx.step()
         dt = c.ctx.last_dt()
         u, fv, rep, ok, status = lim.step_hybrid(u, rep, status, torch.tensor(dt, dtype=torch.float64),
                                                  persist=2, layer=True)
-        assert np.array_equal(c.ctx.flags().astype(bool), fv.numpy()), step
+        got = c.ctx.flags().astype(bool)
+        assert np.array_equal(got, fv.numpy()), step
+        if step < 2:  # the initial FV cells keep their two FV steps
+            assert got[flags].all(), step
     assert rel_linf(c.get(), u.numpy()) <= 1e-11

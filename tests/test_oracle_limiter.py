@@ -266,6 +266,25 @@ def test_hybrid_status_counts_down_with_its_interface_layer():
         assert ok
 
 
+def test_initial_fv_cells_keep_their_fv_steps():
+    """Cells that start in the FV space along the initial discontinuity count as troubled at
+    t^0 (Sec. 3.5): on data where nothing is detected they stay FV, with their interface layer,
+    for exactly `persist` steps."""
+    s, lim = make((6, 6), 2, (0, 0), (1, 1), 'periodic')
+    u = T(synth.entropy_wave(coords(s), amp=1e-3))
+    flags = torch.zeros(36, dtype=torch.bool)
+    flags[[14, 27]] = True                           # cells (2, 2) and (3, 4)
+    U = lim.project(u)
+    u, rep = lim.initial_rep(u, U, flags)
+    status = lim.initial_status(flags, persist=3)
+    assert status.tolist().count(3) == 2 and int(status.sum()) == 6
+    layer = {14, 13, 15, 8, 20, 27, 26, 28, 21, 33}
+    for k, expect in enumerate((layer, layer, layer, set())):
+        u, fv, rep, ok, status = lim.step_hybrid(u, rep, status, s.cfl_dt(u), persist=3)
+        assert set(torch.nonzero(fv).flatten().tolist()) == expect, k
+        assert ok
+
+
 def test_hybrid_with_every_cell_fv_is_the_pure_fv_scheme():
     s, lim, u, rep = explosion((6, 6), 2)
     dt = s.cfl_dt(u)

@@ -71,11 +71,18 @@ def test_ensemble_graph_equals_separate_runs(branches, spg, bps, prec):
     ens.close()
 
 
-def test_ensemble_members_match_the_oracle():
+@pytest.mark.parametrize("sides,order,launch", [([2, 3], 3, None), ([8, 10, 9], 3, None),
+                                                ([8, 10, 9], 3, (0, 2, 2)), ([12, 8], 4, (0, 2, 1))])
+def test_ensemble_members_match_the_oracle(sides, order, launch):
+    """Each run of the ensemble against the oracle run on its own grid: the per-run kernels and
+    the persistent launches shared by all runs (many blocks per run at sides 8..12)."""
     from oracle.aderdg import ADERDG, Grid, PointSource
     from oracle.pde import Elastic
-    sides, order = [2, 3], 3
     ens = ader.Ensemble(member_configs(sides, order))
+    dt = None  # CFL steps per run (the per-run kernels); the persistent launches need a fixed dt
+    if launch is not None:
+        ens.set_launch(*launch)
+        dt = 1e-3
     refs = []
     for i, s in enumerate(sides):
         u0, mat = setup_member(ens.runs[i], s, order, seed=10 + i)
@@ -83,9 +90,9 @@ def test_ensemble_members_match_the_oracle():
         o = ADERDG(Elastic(), g, order, cfl=synth.cfl_number(order), material=torch.from_numpy(mat))
         cell, xi = synth.locate((0.2 * s, 0.3 * s, 0.25 * s), (s,) * 3, (0, 0, 0), (0.5 * s,) * 3)
         o.set_point_source(PointSource(cell, xi, torch.from_numpy(synth.moment_tensor(seed=10 + i)), 2.0, 0.5))
-        u, t = o.run(torch.from_numpy(u0), 4)
+        u, t = o.run(torch.from_numpy(u0), 4, dt=dt)
         refs.append(u.numpy())
-    ens.step(4)
+    ens.step(4, dt=dt or 0.0)
     ens.sync()
     for a, r in zip(states(ens.runs), refs):
         assert rel_linf(a.reshape(r.shape), r) <= 1e-11

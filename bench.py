@@ -38,9 +38,8 @@ FP64_SMS, FP64_FMA_PER_CLK, SM_MAX_MHZ = 152, 2, 2070.0
 # DRAM bytes (read + write) per cell of the predictor kernels, from one ncu capture of the same
 # kernels on 40^3 cells, scaled to a launch by the number of cells (the traffic is per cell:
 # state in, next state and face records out; the mixed form also writes the face wave speeds).
-# The FP64 kernel has changed since its capture (its point-source path is compiled out for Euler),
-# so its traffic is reported as null until it is captured again.
-TRAFFIC_PER_CELL = {"fp64": None,
+# FP64: k_predictor<Euler<3>,3,4> on 64 000 cells, read 331.102464 MB, write 1031.607040 MB.
+TRAFFIC_PER_CELL = {"fp64": (331.102464e6 + 1031.607040e6) / 64000,
                     "mixed": 320.210944e6 / 64000 + 1104.078592e6 / 64000}
 FP64_PEAK = FP64_SMS * FP64_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6  # FLOP/s
 
@@ -157,6 +156,55 @@ def oracle_sample(wl, budget_s):
 FP32_PEAK = FP64_SMS * 128 * 2 * SM_MAX_MHZ * 1e6  # FLOP/s
 
 
+def survey_flops_per_cell(D, N, nv, iters, cF=30):
+    """Algorithmic flops per cell and step of the predictor in the survey's model (the
+    contractions the method must do, no padding): I [2 (d+1) nv n^(d+2) + cF n^(d+1)] for the
+    Picard iterations plus the epilogue 2 (2d+1) nv n^(d+1) + 12 d nv n^d, cF ~ 30 flops per
+    space-time node for the flux.  785 k flop for the Euler order-4 cell."""
+    n = N + 1
+    it = 2 * (D + 1) * nv * n ** (D + 2) + cF * n ** (D + 1)
+    epi = 2 * (2 * D + 1) * nv * n ** (D + 1) + 12 * D * nv * n ** D
+    return iters * it + epi
+
+
+def measure_fma_peaks(stream):
+    """FP64 and binary32 FMA throughput of this GPU measured now (libpeaks.so: 8 independent FMA
+    chains per thread, 8 blocks of 256 threads per SM, CUDA events on the bench stream); returns
+    {"fp64": TFLOP/s, "fp32": TFLOP/s, ...} or None if the library is missing."""
+    import ctypes
+    import torch
+    path = os.path.join(ROOT, "paper_1905_07987_gb300", "peaks", "libpeaks.so")
+    if not os.path.exists(path):
+        return None
+    L = ctypes.CDLL(path)
+    L.peaks_fma_launch.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_void_p]
+    L.peaks_fma_launch.restype = ctypes.c_int
+    L.peaks_fma_flops.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.peaks_fma_flops.restype = ctypes.c_double
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = sms * 8
+    out = {"method": "8 independent FMA chains per thread, %d blocks x 256 threads, best of 3 "
+                     "CUDA-event timed launches" % blocks}
+    sink = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    for name, fp64, iters in (("fp64", 1, 4000), ("fp32", 0, 60000)):
+        with torch.cuda.stream(stream):
+            L.peaks_fma_launch(fp64, sink.data_ptr(), blocks, 200, stream.cuda_stream)  # warm-up
+            best = None
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if L.peaks_fma_launch(fp64, sink.data_ptr(), blocks, iters, stream.cuda_stream) != 0:
+                    return None
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+        out[name] = L.peaks_fma_flops(blocks, iters) / (best * 1e-3) / 1e12
+        out[name + "_ms"] = best
+    return out
+
+
 def density_error(ctx, wl, t, nodes, weights):
     """(L2, Linf) error of the density against the exact entropy wave at time t, evaluated at the
     Gauss-Legendre nodes (L2 with the nodal quadrature) on the GPU with plain torch ops."""
@@ -192,13 +240,22 @@ def density_error(ctx, wl, t, nodes, weights):
     return l2, float(err.abs().max())
 
 
-def run_form(ader, synth, wl, prec, args, stream, u0_dev, err_steps):
+# Forms of the headline workload: (precision, initial guess of the Picard predictor, iterations;
+# 0 = N+1).  The continuous extension Runge-Kutta guess (Sec. 5) is followed by max(1, N-3)
+# iterations (order 4: one).
+FORMS = {"fp64": ("fp64", "constant", 0), "mixed": ("mixed", "constant", 0),
+         "mixed_cerk": ("mixed", "cerk", 1), "fp64_cerk": ("fp64", "cerk", 1)}
+
+
+def run_form(ader, synth, wl, form, args, stream, u0_dev, err_steps):
     """Warm up, time K steps with CUDA events (plus per-phase events), then run untimed to
     err_steps steps in total and measure the density error against the exact solution."""
     import torch
     D, N = wl["dim"], wl["order"]
+    prec, guess, iters = FORMS[form]
     cfg = ader.make_config(wl["pde"], D, N, wl["ncell"], wl["lo"], wl["hi"], wl["bc"],
-                           synth.cfl_number(N), precision=prec)
+                           synth.cfl_number(N), precision=prec, initial_guess=guess,
+                           picard_iters=iters)
     ctx = ader.Context(cfg, stream=stream.cuda_stream)
     ctx.set_state(u0_dev)
     ctx.set_time(0.0)
@@ -451,11 +508,14 @@ def extra_adjoint(ader, synth, stream, n=40, N=4, steps=12, k=4):
             "dtype": "f64"}
 
 
-def extra_explosion(ader, synth, stream, steps=4, warmup=2, n=64):
+def extra_explosion(ader, synth, stream, steps=200, warmup=3, n=64):
     """3-D spherical explosion, order 3, n^3 cells (default 64^3) on [-1,1]^3, wall boundaries,
-    a-posteriori subcell limiter (7^3 subcells): FP64 and mixed predictor, and the FP64 form with
-    the hybrid ADER-DG / FV status (troubled cells stay FV two more steps, an FV interface layer);
-    step time, cells recomputed with FV, conservation of mass and energy."""
+    a-posteriori subcell limiter (7^3 subcells), the workload's 200 steps from t = 0 timed in
+    full (after `warmup` steps on the same data, then a reset): FP64 and mixed predictor, and the
+    FP64 form with the hybrid ADER-DG / FV status (troubled cells stay FV two more steps, an FV
+    interface layer).  Per form: ms per step over the 200 steps, FV cells, conservation of mass
+    and energy over the run, the minimum density and pressure at the end, and the symmetry of the
+    last step's FV set under the reflections and axis permutations of the cube."""
     import torch
     N = 3
     x, w = ader.reference_nodes(N)
@@ -466,22 +526,28 @@ def extra_explosion(ader, synth, stream, steps=4, warmup=2, n=64):
     u0_d = torch.from_numpy(synth.explosion(X).reshape(-1).copy()).cuda()
     W = torch.from_numpy(np.einsum("i,j,k->ijk", w, w, w).reshape(-1)).cuda()
     dofs = n ** 3 * 64 * 5
-    out = {"workload": f"explosion3d_p3_{n} (limiter on)", "dofs": dofs}
+    out = {"workload": f"explosion3d_p3_{n} (limiter on, {steps} steps from t = 0)", "dofs": dofs}
     for form, prec, limiter in (("fp64", "fp64", 1), ("mixed", "mixed", 1), ("fp64_hybrid", "fp64", 3)):
         cfg = ader.make_config("euler", 3, N, (n,) * 3, (-1,) * 3, (1,) * 3, "wall", synth.cfl_number(N),
                                limiter=limiter, precision=prec)
         ctx = ader.Context(cfg, stream=stream.cuda_stream)
-        ctx.set_state(u0_d)
-        ctx.set_subcell_state(Us_d, fl)
+
+        def reset():
+            ctx.set_state(u0_d)
+            ctx.set_subcell_state(Us_d, fl)
+            ctx.set_time(0.0)
 
         def totals():
             st = _dev_state(ctx).view(ctx.cells, -1, 5)
             return (st * W[None, :, None]).sum(dim=(0, 1))
 
-        m0 = totals()
+        reset()
         for _ in range(warmup):
             ctx.step()
         ctx.sync()
+        reset()
+        m0 = totals()
+        torch.cuda.synchronize()
         ctx.enable_timing(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -494,15 +560,29 @@ def extra_explosion(ader, synth, stream, steps=4, warmup=2, n=64):
         ctx.enable_timing(False)
         ctx.sync()
         m1 = totals()
+        st = _dev_state(ctx).view(ctx.cells, -1, 5)
+        rho = st[..., 0]
+        p = 0.4 * (st[..., 4] - 0.5 * (st[..., 1:4] ** 2).sum(-1) / rho)
+        F = ctx.flags().reshape(n, n, n).astype(bool)
+        asym = max(int((G != F).sum()) for G in (F[::-1], F[:, ::-1], F[:, :, ::-1],
+                                                F.transpose(0, 2, 1), F.transpose(2, 1, 0)))
+        nfv = ctx.troubled_count()
+        key = "fv_cells_last_step" if limiter == 3 else "troubled_cells_last_step"
         out[form] = {"ms_per_step": ms / steps, "value": dofs * steps / (ms * 1e-3),
-                     "troubled_cells_last_step": ctx.troubled_count(),
-                     "troubled_fraction": ctx.troubled_count() / n ** 3,
+                     key: nfv, "fv_fraction": nfv / n ** 3,
+                     "t_end": ctx.time(),
                      "phase_ms_per_step": {k: v / max(nr, 1) for k, v in ph.items()},
                      "mass_rel_drift": abs(float(m1[0] - m0[0])) / abs(float(m0[0])),
                      "energy_rel_drift": abs(float(m1[4] - m0[4])) / abs(float(m0[4])),
-                     "steps_run": steps + warmup}
+                     "min_rho": float(rho.min()), "min_p": float(p.min()),
+                     "fv_set_max_asymmetric_cells": asym, "steps_timed": steps}
+        if limiter == 3:
+            out[form]["fv_set_note"] = ("the hybrid FV set: troubled cells, cells still counting "
+                                        "their FV steps, and their face neighbours")
+        del st, rho, p
         ctx.close()
     out["mixed_speedup"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    out["hybrid_speedup"] = out["fp64"]["ms_per_step"] / out["fp64_hybrid"]["ms_per_step"]
     return out
 
 
@@ -580,9 +660,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="euler3d_p4_81", choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed"],
+    ap.add_argument("--prec", default="mixed_cerk", choices=sorted(FORMS),
                     help="form reported as the headline value")
-    ap.add_argument("--forms", default="fp64,mixed", help="forms to time (comma list)")
+    ap.add_argument("--forms", default="fp64,mixed,mixed_cerk", help="forms to time (comma list)")
     ap.add_argument("--err-steps", type=int, default=50,
                     help="steps after which the error against the exact solution is measured")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -603,7 +683,9 @@ def main():
               "cells": list(wl["ncell"]), "dofs": dofs, "init": "entropy wave (analytic)",
               "cfl": "0.9 x order-%d stability limit" % N,
               "l2": "inputs larger than L2 (state %.2f GB)" % (dofs * 8 / 1e9),
-              "precision": args.prec}
+              "precision": FORMS[args.prec][0], "form": args.prec,
+              "initial_guess": FORMS[args.prec][1],
+              "picard_iters": FORMS[args.prec][2] or N + 1}
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -613,6 +695,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
+        config["precision"] = "fp64 (the CPU oracle computes in binary64)"
         v, desc, cores, per_step = oracle_sample(wl, min(args.cpu_budget, 20.0))
         line = {"impl": "reference", "metric": metric, "value": v, "unit": "DOF-updates/s",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -639,6 +722,7 @@ def main():
     u0_dev = torch.from_numpy(u0).to("cuda")
     torch.cuda.synchronize()
 
+    peaks = measure_fma_peaks(stream) if world == 1 or rank == 0 else None
     forms = [f for f in args.forms.split(",") if f]
     if args.prec not in forms:
         forms.append(args.prec)
@@ -677,23 +761,51 @@ def main():
     head_ctx.close()
 
     # ---- roofline of the dominant kernel (the predictor) of each form --------------------------
-    flops = predictor_flops_per_cell(wl["pde"], D, N, N + 1) * cells
+    # algorithmic flops per cell in the survey's model (the unit of the roofline) and in the
+    # kernel's own operation count (the flux evaluation counted operation by operation)
+    def form_flops(form):
+        """(survey-model flops, kernel-count flops) per cell of the form's predictor; the CERK
+        guess adds three single-time-level evaluations of the flux and its derivatives (1/n of
+        an iteration each) and the dense output (4 FMA per line and time node)."""
+        _, guess, iters = FORMS[form]
+        I = iters or N + 1
+        n = N + 1
+        nv = D + 2
+        m = survey_flops_per_cell(D, N, nv, I)
+        k = predictor_flops_per_cell(wl["pde"], D, N, I)
+        if guess == "cerk":
+            it = 2 * (D + 1) * nv * n ** (D + 2) + 30 * n ** (D + 1)
+            m += 3 * it / n + 8 * n ** D * nv * n
+            k += cerk_flops_per_cell(D, N)
+        return m * cells, k * cells
 
-    def roofline(prec):
-        r = res[prec]
+    def roofline(form):
+        r = res[form]
+        prec = FORMS[form][0]
+        flops_model, flops_kernel = form_flops(form)
         nrec = max(r["nrec"], 1)
         pred_ms = r["phases"]["predictor"] / nrec
-        achieved = flops / (pred_ms * 1e-3) / 1e12
-        if prec == "fp64":
-            peak, src, kname = FP64_PEAK, "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz", \
-                "k_predictor (FP64)"
+        achieved = flops_model / (pred_ms * 1e-3) / 1e12
+        key = "fp64" if prec == "fp64" else "fp32"
+        derived = (FP64_PEAK if prec == "fp64" else FP32_PEAK) / 1e12
+        if peaks and peaks.get(key):
+            peak, src = peaks[key], "measured in this run (%s FMA throughput, libpeaks)" % key.upper()
         else:
-            peak, src, kname = FP32_PEAK, "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz", \
-                "k_predictor_mixed (binary32 Picard iterations and flux remainders; float-float base terms, time averages and contractions; FP64 face wave speeds)"
-        return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / (peak / 1e12),
+            peak, src = derived, "derived: 152 SMs x %d FMA/clk x 2 flop x 2070 MHz" % (
+                2 if prec == "fp64" else 128)
+        kname = "k_predictor (FP64)" if prec == "fp64" else \
+            "k_predictor_mixed (binary32 Picard iterations and flux remainders; float-float base terms, time averages and contractions; FP64 face wave speeds)"
+        if FORMS[form][1] == "cerk":
+            kname += ", continuous extension Runge-Kutta guess + %d iteration(s)" % FORMS[form][2]
+        return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": TRAFFIC_PER_CELL.get(prec, 0) * cells if TRAFFIC_PER_CELL.get(prec) else None,
-                "peak_source": src, "flops_per_cell": flops / cells, "ms_per_launch": pred_ms,
+                "peak_source": src, "flops_per_cell": flops_model / cells,
+                "flops_model": "survey model I [2(d+1) nv n^(d+2) + 30 n^(d+1)] + 2(2d+1) nv n^(d+1) + 12 d nv n^d",
+                "kernel_count_flops_per_cell": flops_kernel / cells,
+                "frac_kernel_count": flops_kernel / (pred_ms * 1e-3) / 1e12 / peak,
+                "frac_of_derived_peak": achieved / derived, "derived_peak": derived,
+                "ms_per_launch": pred_ms,
                 "phase_ms_per_step": {k: v / nrec for k, v in r["phases"].items()}}
 
     roof = roofline(args.prec)
@@ -702,16 +814,25 @@ def main():
     for k, r in res.items():
         forms_out[k] = {"value": r["value"], "ms_per_step": r["ms_per_step"],
                         "predictor_ms": r["phases"]["predictor"] / max(r["nrec"], 1), "err": r["err"]}
-    if "fp64" in res and "mixed" in res and res["fp64"]["err"] and res["mixed"]["err"]:
-        forms_out["mixed_over_fp64_l2_error"] = res["mixed"]["err"]["l2_rho"] / res["fp64"]["err"]["l2_rho"]
-        forms_out["mixed_speedup"] = res["mixed"]["value"] / res["fp64"]["value"]
+    if "fp64" in res and res["fp64"]["err"]:
+        for k, r in res.items():
+            if k != "fp64" and r["err"]:
+                forms_out[k]["l2_error_over_fp64"] = r["err"]["l2_rho"] / res["fp64"]["err"]["l2_rho"]
+                forms_out[k]["speedup_over_fp64"] = r["value"] / res["fp64"]["value"]
     launches_per_step = 1 + 1 + 1 + D + 1 + 1
+    # the FP64 form of the same workload (the scheme's reference arithmetic), with its error
+    fp64_entry = None
+    if "fp64" in res:
+        r = res["fp64"]
+        fp64_entry = {"value": r["value"], "unit": "DOF-updates/s", "ms_per_step": r["ms_per_step"],
+                      "dtype": "f64", "err_vs_exact": r["err"], "roofline": roof_forms["fp64"]}
     line = {"metric": metric, "value": head["value"], "unit": "DOF-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.prec == "fp64" else "f32+f64",
+            "dtype": "f64" if FORMS[args.prec][0] == "fp64" else "f32+f64",
             "data": "synthetic", "config": config, "roofline": roof, "roofline_forms": roof_forms,
-            "forms": forms_out,
+            "forms": forms_out, "fp64": fp64_entry, "err_vs_exact": head["err"],
+            "measured_peaks": peaks,
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": head["clocks"]}
     if not args.no_extra and world == 1:
         extra = {}
@@ -733,6 +854,12 @@ def main():
         v, desc, cores, _ = oracle_sample(wl, args.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": "DOF-updates/s", "cores": cores,
                                 "kind": "oracle", "sample": desc}
+        import torch as _t
+        nt = _t.get_num_threads()
+        _t.set_num_threads(1)
+        v1, desc1, _, _ = oracle_sample(wl, max(2.0, args.cpu_budget / 2))
+        _t.set_num_threads(nt)
+        line["cpu_baseline"]["one_thread"] = {"value": v1, "cores": 1, "sample": desc1}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

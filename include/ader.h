@@ -87,7 +87,8 @@ typedef enum { ADER_PREDICTOR_PICARD = 0, ADER_PREDICTOR_CK = 1 } ader_predictor
  *  CERK     - the dense output of the classical four-stage Runge-Kutta method on the cell-local
  *             ODE dq/dt = R(q), natural continuous extension of uniform order 3, evaluated at
  *             the time nodes; picard_iters iterations follow (full order needs max(0, N-3)).
- *             ADER_PREC_FP64 and the Picard predictor only (else ADER_EUNSUPPORTED); not
+ *             The Picard predictor only (else ADER_EUNSUPPORTED), FP64 or MIXED (MIXED: the
+ *             stages on the increment u - u^n in binary32 like the iterations); not
  *             differentiated (the adjoint entry points reject it). */
 typedef enum { ADER_GUESS_CONSTANT = 0, ADER_GUESS_CERK = 1 } ader_guess;
 

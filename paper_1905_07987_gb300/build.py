@@ -73,5 +73,26 @@ def build(force=False, verbose=False, jobs=None):
     return OUT
 
 
+PEAKS_SRC = os.path.join(HERE, "peaks", "peaks.cu")
+PEAKS_OUT = os.path.join(HERE, "peaks", "libpeaks.so")
+
+
+def build_peaks(force=False):
+    """Compile the arithmetic-throughput microbenchmark (libpeaks.so) that the benchmark uses for
+    the measured FP64 / binary32 roofline denominators; returns its path."""
+    if not force and os.path.exists(PEAKS_OUT) and \
+            os.path.getmtime(PEAKS_OUT) >= os.path.getmtime(PEAKS_SRC):
+        return PEAKS_OUT
+    tmp = PEAKS_OUT + ".tmp"
+    cmd = [nvcc()] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-cudart", "shared",
+                             PEAKS_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for peaks.cu:\n%s\n%s" % (r.stdout, r.stderr))
+    os.replace(tmp, PEAKS_OUT)
+    return PEAKS_OUT
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))
+    print(build_peaks(force="--force" in sys.argv))

@@ -60,6 +60,8 @@ struct TablesF {
   float ihh[3], ihl[3];                    // 1/h_d (hi, lo)
   float g1h, g1l;                          // gamma - 1 (hi, lo)
   float e0h[MAXN], e0l[MAXN], e1h[MAXN], e1l[MAXN];
+  float th[MAXN];                          // time nodes x_t
+  float cerk[3][MAXN];                     // dense-output weights b1, b2 (= b3), b4 at x_t
 };
 
 // Subcell tables of the limiter (Sec. 3.5).

@@ -220,6 +220,10 @@ void build_tables_f(int order, const Tables& T, TablesF& F) {
   for (int t = 0; t < n; ++t)
     for (int m = 0; m < n; ++m) wk1 += T.w[t] * T.Kw[t][m];
   split_f(wk1, F.wk1h, F.wk1l);
+  for (int t = 0; t < n; ++t) {
+    F.th[t] = (float)T.x[t];
+    for (int i = 0; i < 3; ++i) F.cerk[i][t] = (float)T.cerk[i][t];
+  }
   for (int m = 0; m < n; ++m) {
     double a = 0.0;
     for (int t = 0; t < n; ++t) a += T.w[t] * T.Kw[t][m];
@@ -474,8 +478,7 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
     return ADER_EUNSUPPORTED;
   if (cfg->initial_guess != ADER_GUESS_CONSTANT && cfg->initial_guess != ADER_GUESS_CERK)
     return ADER_EINVAL;
-  if (cfg->initial_guess == ADER_GUESS_CERK &&
-      (cfg->predictor != ADER_PREDICTOR_PICARD || cfg->precision != ADER_PREC_FP64))
+  if (cfg->initial_guess == ADER_GUESS_CERK && cfg->predictor != ADER_PREDICTOR_PICARD)
     return ADER_EUNSUPPORTED;
   // the predictor keeps a cell in shared memory: at most 227 KB per block on sm_103a, less the
   // kernel's static tables (the 3-D Euler mixed form at order 6 does not fit)

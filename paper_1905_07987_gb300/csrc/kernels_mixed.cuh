@@ -275,6 +275,60 @@ __device__ __forceinline__ void contract_f(const float* X, const float* Dh, cons
   }
 }
 
+// Flux increments F_d(u + s) - F_d(u) of every direction at the spatial nodes, for one state
+// increment s [NL] (a Runge-Kutta stage of the initial guess), into dF1 [D][NL] (binary32).
+template <class M, class P, int D>
+__device__ __forceinline__ void dflux_level(const float* sq, const ff* uff, const ff* bff,
+                                            const PdeParams& pp, float g1h, float g1l, float* dF1,
+                                            int tid) {
+  constexpr int NV = M::NV, NS = M::NS, NL = M::NL;
+#pragma unroll
+  for (int k = 0; k < M::NPS; ++k) {
+    const int node = tid + k * M::TPB;
+    if (node < NS) {
+      float q[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) q[v] = sq[node * NV + v];
+      float F[D][NV];
+      if constexpr (M::EULER) {
+        dflux_f_all<D>(load_base<D>(uff, bff, node), q, g1h, g1l, F);
+      } else {
+#pragma unroll
+        for (int d = 0; d < D; ++d) F[d][0] = (float)pp.a[d] * q[0];
+      }
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dF1[d * NL + node * NV + v] = F[d][v];
+    }
+  }
+}
+
+// One time level of contract_f: r[k] += cf[d][v] * sum_m D[j_d][m] X[(j, j_d -> m)][src] (binary32).
+template <class M, int d, bool NCP>
+__device__ __forceinline__ void contract_level(const float* X, const float* Dh, const float* cf,
+                                               float (&r)[M::LPT], int tid) {
+  constexpr int n = M::n, NV = M::NV, NL = M::NL, TPB = M::TPB, st = ipow(n, d);
+#pragma unroll
+  for (int k = 0; k < M::LPT; ++k) {
+    const int l = tid + k * TPB;
+    if (l < NL) {
+      const int j = l / NV, v = l - (l / NV) * NV;
+      int s = v;
+      if constexpr (NCP) {
+        s = Elastic::src(d, v);
+        if (s < 0) continue;
+      }
+      const int jd = digit<n, d>(j);
+      const int j0 = j - jd * st;
+      float acc = 0.f;
+#pragma unroll
+      for (int m = 0; m < n; ++m) acc = fmaf(Dh[jd * n + m], X[(j0 + m * st) * NV + s], acc);
+      r[k] = fmaf(cf[d * NV + v], acc, r[k]);
+    }
+  }
+}
+
 // One cell c (all threads of the block; called by the per-context kernel and by the persistent
 // ensemble kernel).
 template <class P, int D, int N>
@@ -453,6 +507,80 @@ __device__ __forceinline__ void predictor_mixed_cell(const StepArgs& A, const Ta
     }
   }
 
+  // ---- continuous extension Runge-Kutta guess (Sec. 5), A.cerk: dq^0 at the time nodes -------
+  // Classical four-stage Runge-Kutta on the cell-local ODE dq/dt = R(u + dq) with the stages
+  // k_i = B0 + dR(s_i) (+ the point source at the stage time), s = 0, h/2 k_1, h/2 k_2, h k_3,
+  // and its natural continuous extension dq(x_t) = h sum_i b_i(x_t) k_i (sum_i b_i = x_t): the
+  // stage increments and dR in binary32 (they are O(dt)), B0 from its float-float hi part.
+  if (A.cerk) {
+    float kd[3][LPT];   // dR of the stages 2, 3, 4
+    double rs[4] = {0.0, 0.0, 0.0, 0.0};  // wavelet at the stage times (source cell)
+    if (has_src) {
+      const double ts[4] = {0.0, 0.5, 0.5, 1.0};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const double tau = fma(ts[i], dt, tn) - A.src.t0;
+        const double a = (M_PI * A.src.f0 * tau) * (M_PI * A.src.f0 * tau);
+        rs[i] = (1.0 - 2.0 * a) * exp(-a);
+      }
+    }
+#pragma unroll
+    for (int st = 0; st < 3; ++st) {
+#pragma unroll
+      for (int k = 0; k < LPT; ++k) {
+        const int l = tid + k * TPB;
+        if (l < NL) {
+          float kp = b0f[k] + (st > 0 ? kd[st - 1][k] : 0.f);
+          if (has_src) {
+            const int j = l / NV, v = l - (l / NV) * NV;
+            if (v >= 3) kp = fmaf((float)(-A.src.M[v - 3] * A.src.phi[j]), (float)rs[st], kp);
+          }
+          dqs[l] = (st == 2 ? dtf : 0.5f * dtf) * kp;
+        }
+      }
+      __syncthreads();
+      float r[LPT];
+#pragma unroll
+      for (int k = 0; k < LPT; ++k) r[k] = 0.f;
+      if constexpr (P::CONS) {
+        dflux_level<M, P, D>(dqs, uff, bff, A.p, F.g1h, F.g1l, dF3, tid);
+        __syncthreads();
+        contract_level<M, 0, false>(dF3, sDh, cf, r, tid);
+        contract_level<M, 1, false>(dF3 + NL, sDh, cf, r, tid);
+        if constexpr (D == 3) contract_level<M, 2, false>(dF3 + 2 * NL, sDh, cf, r, tid);
+      } else {
+        contract_level<M, 0, true>(dqs, sDh, cf, r, tid);
+        contract_level<M, 1, true>(dqs, sDh, cf, r, tid);
+        contract_level<M, 2, true>(dqs, sDh, cf, r, tid);
+      }
+#pragma unroll
+      for (int k = 0; k < LPT; ++k) kd[st][k] = r[k];
+      __syncthreads();  // the stage's reads of dqs / dF3 are done
+    }
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      const int l = tid + k * TPB;
+      if (l < NL) {
+        float s1 = 0.f, s23 = 0.f, s4 = 0.f;
+        if (has_src) {
+          const int j = l / NV, v = l - (l / NV) * NV;
+          if (v >= 3) {
+            const float amp = (float)(-A.src.M[v - 3] * A.src.phi[j]);
+            s1 = amp * (float)rs[0];
+            s23 = amp * (float)(rs[1] + rs[2]);
+            s4 = amp * (float)rs[3];
+          }
+        }
+        const float k23 = kd[0][k] + kd[1][k] + s23, k4 = kd[2][k] + s4;
+#pragma unroll
+        for (int t = 0; t < n; ++t)
+          dqs[t * NL + l] = dtf * fmaf(F.th[t], b0f[k],
+                                       fmaf(F.cerk[0][t], s1, fmaf(F.cerk[1][t], k23, F.cerk[2][t] * k4)));
+      }
+    }
+    __syncthreads();
+  }
+
   // ---- Picard iterations on dq ----------------------------------------------------------
   float R[LPT][n];
   ff dqb[P::CONS ? LPT : 1];  // time average of the last iterate (float-float)
@@ -464,7 +592,7 @@ __device__ __forceinline__ void predictor_mixed_cell(const StepArgs& A, const Ta
 #pragma unroll
       for (int t = 0; t < n; ++t) R[k][t] = 0.f;
     const bool last = (it == A.iters - 1);
-    if (it > 0) {
+    if (it > 0 || A.cerk) {  // dq^0 = 0 gives dR = 0 without a guess
       if constexpr (P::CONS) {
         // all directions at once into dF3
         dflux_nodes_all<M, P, D>(dqs, uff, bff, A.p, F.g1h, F.g1l, dF3, tid);

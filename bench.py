@@ -344,8 +344,8 @@ def extra_elastic(ader, synth, stream, steps=2, warmup=1, n=81):
     mat = torch.from_numpy(synth.elastic_material((n,) * 3, seed=1905).reshape(-1).copy()).cuda()
     out = {"workload": "elastic3d_p5_%d" % n, "dofs": n ** 3 * 216 * 9}
     finals = {}
-    for form in ("fp64", "mixed", "ck", "ck_mixed"):
-        prec = "mixed" if form in ("mixed", "ck_mixed") else "fp64"
+    for form in ("fp64", "mixed", "ck", "ck_mixed", "ck_tf32x3"):
+        prec = {"mixed": "mixed", "ck_mixed": "mixed", "ck_tf32x3": "tf32x3"}.get(form, "fp64")
         cfg = ader.make_config("elastic", 3, N, (n,) * 3, (0, 0, 0), (L,) * 3, "absorbing",
                                synth.cfl_number(N), precision=prec,
                                predictor="ck" if form.startswith("ck") else "picard")
@@ -399,6 +399,13 @@ def extra_elastic(ader, synth, stream, steps=2, warmup=1, n=81):
     out["ck_mixed_speedup_vs_fp64_ck"] = ck["ms_per_step"] / ckm["ms_per_step"]
     out["ck_mixed_vs_fp64_ck_rel_linf"] = ((finals["ck_mixed"] - finals["ck"]).abs().max().item()
                                            / max(finals["ck"].abs().max().item(), 1e-300))
+    # tensor-core form: the same algorithmic flops as tensor-pipe work (TF32 split operands)
+    ckt = out["ck_tf32x3"]
+    ckt["predictor_tflops"] = flops_cell * n ** 3 / (ckt["predictor_ms"] * 1e-3) / 1e12
+    ckt["speedup_vs_ck_mixed"] = ckm["ms_per_step"] / ckt["ms_per_step"]
+    ckt["predictor_speedup_vs_ck_mixed"] = ckm["predictor_ms"] / ckt["predictor_ms"]
+    out["ck_tf32x3_vs_fp64_ck_rel_linf"] = ((finals["ck_tf32x3"] - finals["ck"]).abs().max().item()
+                                            / max(finals["ck"].abs().max().item(), 1e-300))
     # the two predictors differ by their O(dt^(N+1)) truncation (a difference, not an error)
     out["ck_vs_picard_fp64_rel_linf"] = (finals["ck"] - finals["fp64"]).abs().max().item() / scale
     return out

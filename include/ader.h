@@ -66,8 +66,19 @@ typedef enum { ADER_BC_PERIODIC = 0, ADER_BC_WALL = 1, ADER_BC_ABSORBING = 2 } a
  *          terms, time averages and contractions.  Pressure / sound speed and eigenvalues, the
  *          Riemann flux, the corrector and the limiter stay binary64 (for Euler the face wave
  *          speeds are evaluated by the predictor, and the CFL maximum only on the nodes that a
- *          binary32 enclosure cannot rule out; dt equals the FP64 form's on the same state). */
-typedef enum { ADER_PREC_FP64 = 0, ADER_PREC_MIXED = 1 } ader_prec;
+ *          binary32 enclosure cannot rule out; dt equals the FP64 form's on the same state);
+ *  MIXED_TF32X3 - the Cauchy-Kowalevski predictor of the elastic family (orders 1, 3, 5) with
+ *          every contraction on the tensor cores (tcgen05.mma kind::tf32): the derivatives of the
+ *          Taylor coefficients and the face extrapolation of the time average as products with
+ *          the 1-D tables, operands split into TF32 hi + lo parts, three products (hi hi, lo hi,
+ *          hi lo) accumulated in FP32, relative error about 2^-21 of sum |table| |operand| per
+ *          contraction; the material combination and the Taylor recursion in binary32, the
+ *          update u + dt vol in FP64.  The error is relative to the size of the wavefield, so the
+ *          form suits solutions without a large constant background (the elastic wavefield from
+ *          rest).  Other predictors, PDEs or orders: ADER_EUNSUPPORTED.
+ * The value 2 (a BF16 x 3 split: 2^-16 per product, above the step-change bound the mixed forms
+ * keep) is not built. */
+typedef enum { ADER_PREC_FP64 = 0, ADER_PREC_MIXED = 1, ADER_PREC_MIXED_TF32X3 = 3 } ader_prec;
 
 /* Space-time predictor of Sec. 3.3:
  *  PICARD - the element-local space-time system Eq. (5) solved by picard_iters fixed-point

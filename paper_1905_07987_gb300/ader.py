@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libader.so")
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ENONFINITE, EADMISSIBLE, ETIMEOUT, EUNSUPPORTED = range(9)
 PDE = {"advection": 0, "euler": 1, "elastic": 2}
 BC = {"periodic": 0, "wall": 1, "absorbing": 2}
-PREC = {"fp64": 0, "mixed": 1}
+PREC = {"fp64": 0, "mixed": 1, "tf32x3": 3}
 PREDICTOR = {"picard": 0, "ck": 1}
 GUESS = {"constant": 0, "cerk": 1}
 

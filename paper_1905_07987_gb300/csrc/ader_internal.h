@@ -199,6 +199,9 @@ cudaError_t launch_misfit(const double* a, const double* b, long long n, double 
 cudaError_t launch_receivers_adjoint(const Receivers& r, const double* res, double scale,
                                      double* dJdu, int nodes, int nvar, cudaStream_t s);
 
+// orders of the tensor-core Cauchy-Kowalevski predictor (ADER_PREC_MIXED_TF32X3)
+bool predictor_ck_tc_order_ok(int order);
+
 const Family* family_advection2();
 const Family* family_advection3();
 const Family* family_euler2();

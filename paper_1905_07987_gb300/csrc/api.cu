@@ -472,8 +472,15 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
   if (cfg->dim < 2 || cfg->dim > 3 || cfg->order < 1 || cfg->order > MAXN - 1) return ADER_EUNSUPPORTED;
   const Family* fam = pick_family(cfg->pde, cfg->dim);
   if (!fam) return ADER_EUNSUPPORTED;
-  if (cfg->precision != ADER_PREC_FP64 && cfg->precision != ADER_PREC_MIXED) return ADER_EUNSUPPORTED;
   if (cfg->predictor != ADER_PREDICTOR_PICARD && cfg->predictor != ADER_PREDICTOR_CK) return ADER_EINVAL;
+  if (cfg->precision != ADER_PREC_FP64 && cfg->precision != ADER_PREC_MIXED &&
+      cfg->precision != ADER_PREC_MIXED_TF32X3)
+    return ADER_EUNSUPPORTED;
+  // the tensor-core form: the Cauchy-Kowalevski predictor of the elastic family, orders 1, 3, 5
+  if (cfg->precision == ADER_PREC_MIXED_TF32X3 &&
+      (cfg->predictor != ADER_PREDICTOR_CK || cfg->pde != ADER_PDE_ELASTIC ||
+       !predictor_ck_tc_order_ok(cfg->order)))
+    return ADER_EUNSUPPORTED;
   if (cfg->predictor == ADER_PREDICTOR_CK && (!fam->predictor_ck || cfg->limiter))
     return ADER_EUNSUPPORTED;
   if (cfg->initial_guess != ADER_GUESS_CONSTANT && cfg->initial_guess != ADER_GUESS_CERK)
@@ -482,7 +489,9 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
     return ADER_EUNSUPPORTED;
   // the predictor keeps a cell in shared memory: at most 227 KB per block on sm_103a, less the
   // kernel's static tables (the 3-D Euler mixed form at order 6 does not fit)
-  if (fam->predictor_smem(cfg->order, cfg->precision) > 232448 - 4096) return ADER_EUNSUPPORTED;
+  if (cfg->predictor == ADER_PREDICTOR_PICARD &&
+      fam->predictor_smem(cfg->order, cfg->precision) > 232448 - 4096)
+    return ADER_EUNSUPPORTED;
   if (cfg->limiter < 0 || cfg->limiter > 3) return ADER_EINVAL;
   if (cfg->limiter) {
     if (cfg->pde != ADER_PDE_EULER) return ADER_EUNSUPPORTED;

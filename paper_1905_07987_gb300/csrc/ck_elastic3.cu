@@ -1,10 +1,14 @@
-// Cauchy-Kowalevski predictor of the 3-D elastic family, orders 1-6, FP64 and mixed precision.
+// Cauchy-Kowalevski predictor of the 3-D elastic family, orders 1-6, FP64 and mixed precision
+// (the tensor-core form is in ck_tc_elastic3.cu).
 #include "kernels_ck.cuh"
 
 namespace ader {
 
+cudaError_t predictor_ck_tc_elastic3(const StepArgs& a, const Tables& t, cudaStream_t s);
+
 cudaError_t predictor_ck_elastic3(const StepArgs& a, const Tables& t, const TablesF& f, int prec,
                                   cudaStream_t s) {
+  if (prec == 3) return predictor_ck_tc_elastic3(a, t, s);
   if (prec == 1) {
     switch (a.g.order) {
       case 1: return launch_predictor_ck_mixed_n<1>(a, t, f, s);

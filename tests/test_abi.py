@@ -66,12 +66,20 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     assert lib.ader_create(ctypes.byref(cfg), None, ctypes.byref(h)) == ader.EUNSUPPORTED
     cfg = ader.make_config("elastic", 3, 3, (4, 4, 4), (0,) * 3, (1,) * 3, "absorbing", 0.5, predictor=7)
     assert lib.ader_create(ctypes.byref(cfg), None, ctypes.byref(h)) == ader.EINVAL
-    # the continuous extension Runge-Kutta guess: FP64 Picard only; unknown guess ids
-    cfg = ader.make_config("euler", 3, 3, (4, 4, 4), (0,) * 3, (1,) * 3, "periodic", 0.5,
-                           precision="mixed", initial_guess="cerk")
-    assert lib.ader_create(ctypes.byref(cfg), None, ctypes.byref(h)) == ader.EUNSUPPORTED
-    cfg = ader.make_config("elastic", 3, 3, (4, 4, 4), (0,) * 3, (1,) * 3, "absorbing", 0.5,
-                           predictor="ck", initial_guess="cerk")
+    # the continuous extension Runge-Kutta guess: the Picard predictor only; unknown guess ids
+    for prec in ("fp64", "mixed"):
+        cfg = ader.make_config("elastic", 3, 3, (4, 4, 4), (0,) * 3, (1,) * 3, "absorbing", 0.5,
+                               predictor="ck", initial_guess="cerk", precision=prec)
+        assert lib.ader_create(ctypes.byref(cfg), None, ctypes.byref(h)) == ader.EUNSUPPORTED
+    # the tensor-core form: the elastic Cauchy-Kowalevski predictor at orders 1, 3, 5 only; the
+    # value 2 of ader_prec is not built
+    for pde, order, pred in (("euler", 3, "picard"), ("elastic", 4, "ck"), ("elastic", 5, "picard")):
+        cfg = ader.make_config(pde, 3, order, (4, 4, 4), (0,) * 3, (1,) * 3,
+                               "periodic" if pde == "euler" else "absorbing", 0.5, predictor=pred,
+                               precision="tf32x3")
+        assert lib.ader_create(ctypes.byref(cfg), None, ctypes.byref(h)) == ader.EUNSUPPORTED
+    cfg = ader.make_config("elastic", 3, 5, (4, 4, 4), (0,) * 3, (1,) * 3, "absorbing", 0.5,
+                           predictor="ck", precision=2)
     assert lib.ader_create(ctypes.byref(cfg), None, ctypes.byref(h)) == ader.EUNSUPPORTED
     cfg = ader.make_config("euler", 3, 3, (4, 4, 4), (0,) * 3, (1,) * 3, "periodic", 0.5, initial_guess=5)
     assert lib.ader_create(ctypes.byref(cfg), None, ctypes.byref(h)) == ader.EINVAL

@@ -87,6 +87,74 @@ def test_ck_mixed_wide_magnitudes():
     assert change_rel(got, ref, u0) < 2e-6
 
 
+# Tensor-core form (TF32 split operands, FP32 accumulation): every contraction carries a relative
+# error eps_tc <= 3 x 2^-22 (split truncations and the dropped lo x lo product) + 3n x 2^-24 (FP32
+# accumulation of the three n-term products) ~ 2e-6 of sum_m |table_im| |x_m|; relative to the
+# step's change this is multiplied by the cancellation ratio sum |D| |u| / |D u|, about 1.5 on
+# random states and up to ~10 on the smooth waves of the full-size test.
+TOL_TC_RANDOM = 2e-5
+TOL_TC_SMOOTH = 5e-5
+
+
+@pytest.mark.parametrize("order", [1, 3, 5])
+def test_ck_tf32x3_step_with_source(order):
+    """Every contraction on the tensor cores (ADER_PREC_MIXED_TF32X3) against the oracle's FP64
+    Cauchy-Kowalevski step, random state, point source, absorbing boundaries; 45 cells on the
+    persistent blocks (more blocks than cells at order 1 and 3 on 152 SMs)."""
+    ncell = (5, 3, 3)
+    mat = synth.elastic_material(ncell, seed=order)
+    c = Case("elastic", 3, order, ncell, hi=(2.5, 1.5, 1.5), bc="absorbing", material=mat,
+             predictor="ck", precision="tf32x3")
+    rng = np.random.default_rng(300 + order)
+    u0 = rng.standard_normal(c.shape)
+    c.point_source((1.3, 0.7, 0.8), synth.moment_tensor(seed=7), 2.0, 0.5)
+    c.set(u0)
+    c.ctx.set_time(0.37)
+    c.ctx.step()
+    c.ctx.sync()
+    ref = c.oracle_step(u0, c.ctx.last_dt(), 0.37)
+    err = change_rel(c.get(), ref, u0)
+    print("tf32x3 order %d: error / step change %.3e" % (order, err))
+    assert err < TOL_TC_RANDOM
+
+
+def test_ck_tf32x3_many_cells_and_steps_track_fp64():
+    """12^3 cells (each persistent block loops over several cells, the next cell's state
+    prefetched by TMA), 6 steps with a source: the state stays within a small multiple of the
+    one-step bound of the FP64 Cauchy-Kowalevski run."""
+    ncell = (12, 12, 12)
+    L = 6.0
+    mat = synth.elastic_material(ncell, seed=4)
+    out = {}
+    for prec in ("fp64", "tf32x3"):
+        c = Case("elastic", 3, 5, ncell, hi=(L,) * 3, bc="absorbing", material=mat,
+                 predictor="ck", precision=prec)
+        x, _ = ader.reference_nodes(5)
+        u0 = waves(c.X, L)
+        c.point_source((L / 2,) * 3, synth.moment_tensor(seed=3), 2.0, 0.5)
+        c.set(u0)
+        c.ctx.set_time(0.45)
+        c.ctx.run(6)
+        out[prec] = c.get()
+        c.ctx.close()
+    d = np.abs(out["tf32x3"] - out["fp64"]).max()
+    scale = np.abs(out["fp64"] - u0).max()
+    print("tf32x3 6 steps: |diff| / |change| %.3e" % (d / scale))
+    assert d <= 6 * TOL_TC_SMOOTH * scale
+
+
+def test_ck_tf32x3_is_rejected_where_it_is_not_built():
+    for kw in (dict(pde="elastic", order=4, predictor="ck"), dict(pde="elastic", order=5, predictor="picard"),
+               dict(pde="euler", order=3, predictor="picard")):
+        cfg = ader.make_config(kw["pde"], 3, kw["order"], (2, 2, 2), (0,) * 3, (1,) * 3,
+                               "absorbing" if kw["pde"] == "elastic" else "periodic",
+                               synth.cfl_number(kw["order"]), predictor=kw["predictor"],
+                               precision="tf32x3")
+        with pytest.raises(ader.AderError) as e:
+            ader.Context(cfg)
+        assert e.value.status == ader.EUNSUPPORTED, kw
+
+
 def test_ck_periodic_multistep_and_receivers():
     ncell = (4, 3, 3)
     mat = synth.elastic_material(ncell, seed=12)
@@ -158,7 +226,7 @@ def test_ck_is_rejected_where_it_is_not_built():
     assert e.value.status == ader.EUNSUPPORTED
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "tf32x3"])
 def test_ck_full_size_sampled_cells_elastic_81(precision):
     """81^3 cells at order 5 (FP64 and mixed form), the benchmark's elastic workload (seeded material, absorbing
     boundaries, Ricker moment-tensor source at the centre) with a smooth wave state, in the launch
@@ -224,6 +292,10 @@ def test_ck_full_size_sampled_cells_elastic_81(precision):
         g = got[centre].cpu().numpy().reshape(out[13].shape)
         if precision == "fp64":
             assert rel_linf(g, out[13]) <= TOL, (i, j, k)
-        else:
+        elif precision == "mixed":
             assert change_rel(g, out[13], loc[13]) < 2e-6, (i, j, k)
+        else:
+            err = change_rel(g, out[13], loc[13])
+            print("tf32x3 81^3 cell %s: error / step change %.3e" % ((i, j, k), err))
+            assert err < TOL_TC_SMOOTH, (i, j, k)
     ctx.close()

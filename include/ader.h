@@ -51,13 +51,22 @@ typedef enum {
   ADER_EUNSUPPORTED = 8   /* combination of PDE / dimension / order / option not built */
 } ader_status;
 
-typedef enum { ADER_PDE_ADVECTION = 0, ADER_PDE_EULER = 1, ADER_PDE_ELASTIC = 2 } ader_pde;
+/* Built-in systems: scalar advection (tests), compressible Euler (Eq. (8)), linear elasticity
+ * (Sec. 2.1, 3-D), and the shallow water equations with bathymetry (Eq. (9), 2-D, FP64 Picard
+ * predictor): Q = (h, hu, hv, b), flux (h u_d, hu u_d, hv u_d, 0) and the state-dependent
+ * non-conservative product g h d(h + b)/dx_d on the momentum of direction d, taken node by node
+ * in the predictor and as the path-conservative fluctuation along the straight segment between
+ * the face states (3-point rule) at faces. */
+typedef enum { ADER_PDE_ADVECTION = 0, ADER_PDE_EULER = 1, ADER_PDE_ELASTIC = 2,
+               ADER_PDE_SWE = 3 } ader_pde;
 
 /* Boundary kinds per face (Table 2 "boundaryValues"):
  *  PERIODIC  - wrap around (both faces of a direction must be periodic);
- *  WALL      - reflecting wall: mirror state with the normal momentum negated (Euler);
+ *  WALL      - reflecting wall: mirror state with the normal momentum negated (Euler, shallow
+ *              water);
  *  ABSORBING - zero exterior state for linear PDEs (advection, elastic), a transmissive copy of
- *              the interior state for Euler; the exterior material is the interior one. */
+ *              the interior state for Euler and shallow water; the exterior material is the
+ *              interior one. */
 typedef enum { ADER_BC_PERIODIC = 0, ADER_BC_WALL = 1, ADER_BC_ABSORBING = 2 } ader_bc;
 
 /* Arithmetic of the step:
@@ -124,6 +133,7 @@ typedef struct {
   int precision;       /* ader_prec */
   int predictor;       /* ader_predictor (0 = Picard) */
   int initial_guess;   /* ader_guess (0 = constant in time) */
+  double grav;         /* gravitational acceleration (ADER_PDE_SWE); <= 0 => 9.81 */
 } ader_config;
 
 /* Create a context on the current CUDA device.  `cuda_stream` is a cudaStream_t (NULL = the

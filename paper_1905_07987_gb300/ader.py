@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libader.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ENONFINITE, EADMISSIBLE, ETIMEOUT, EUNSUPPORTED = range(9)
-PDE = {"advection": 0, "euler": 1, "elastic": 2}
+PDE = {"advection": 0, "euler": 1, "elastic": 2, "swe": 3}
 BC = {"periodic": 0, "wall": 1, "absorbing": 2}
 PREC = {"fp64": 0, "mixed": 1, "tf32x3": 3}
 PREDICTOR = {"picard": 0, "ck": 1}
@@ -44,6 +44,7 @@ class Config(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("predictor", ctypes.c_int),
         ("initial_guess", ctypes.c_int),
+        ("grav", ctypes.c_double),
     ]
 
 
@@ -156,7 +157,7 @@ def _ptr(a, dtype=np.float64):
 
 def make_config(pde, dim, order, ncell, lo, hi, bc, cfl, gamma=1.4, adv=(0.0, 0.0, 0.0),
                 picard_iters=0, limiter=False, precision="fp64", predictor="picard",
-                initial_guess="constant"):
+                initial_guess="constant", grav=9.81):
     c = Config()
     c.dim = dim
     c.order = order
@@ -180,6 +181,7 @@ def make_config(pde, dim, order, ncell, lo, hi, bc, cfl, gamma=1.4, adv=(0.0, 0.
     c.precision = PREC[precision] if isinstance(precision, str) else int(precision)
     c.predictor = PREDICTOR[predictor] if isinstance(predictor, str) else int(predictor)
     c.initial_guess = GUESS[initial_guess] if isinstance(initial_guess, str) else int(initial_guess)
+    c.grav = float(grav)
     return c
 
 

@@ -115,6 +115,7 @@ struct Geometry {
 struct PdeParams {
   double gamma;
   double a[3];
+  double grav;         // gravitational acceleration (shallow water)
 };
 
 struct PointSrc {
@@ -207,6 +208,7 @@ const Family* family_advection3();
 const Family* family_euler2();
 const Family* family_euler3();
 const Family* family_elastic3();
+const Family* family_swe2();
 int limiter_max_order2();
 int limiter_max_order3();
 

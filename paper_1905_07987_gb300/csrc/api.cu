@@ -309,6 +309,7 @@ const Family* pick_family(int pde, int dim) {
   if (pde == ADER_PDE_ADVECTION) return dim == 2 ? family_advection2() : family_advection3();
   if (pde == ADER_PDE_EULER) return dim == 2 ? family_euler2() : family_euler3();
   if (pde == ADER_PDE_ELASTIC && dim == 3) return family_elastic3();
+  if (pde == ADER_PDE_SWE && dim == 2) return family_swe2();
   return nullptr;
 }
 
@@ -487,6 +488,10 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
     return ADER_EINVAL;
   if (cfg->initial_guess == ADER_GUESS_CERK && cfg->predictor != ADER_PREDICTOR_PICARD)
     return ADER_EUNSUPPORTED;
+  // shallow water: FP64 Picard predictor from the constant guess
+  if (cfg->pde == ADER_PDE_SWE &&
+      (cfg->precision != ADER_PREC_FP64 || cfg->initial_guess != ADER_GUESS_CONSTANT))
+    return ADER_EUNSUPPORTED;
   // the predictor keeps a cell in shared memory: at most 227 KB per block on sm_103a, less the
   // kernel's static tables (the 3-D Euler mixed form at order 6 does not fit)
   if (cfg->predictor == ADER_PREDICTOR_PICARD &&
@@ -504,7 +509,7 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
     for (int s = 0; s < 2; ++s)
       if (cfg->bc[d][s] < 0 || cfg->bc[d][s] > 2) return ADER_EINVAL;
     if ((cfg->bc[d][0] == ADER_BC_PERIODIC) != (cfg->bc[d][1] == ADER_BC_PERIODIC)) return ADER_EINVAL;
-    if (cfg->pde != ADER_PDE_EULER)
+    if (cfg->pde != ADER_PDE_EULER && cfg->pde != ADER_PDE_SWE)
       for (int s = 0; s < 2; ++s)
         if (cfg->bc[d][s] == ADER_BC_WALL) return ADER_EUNSUPPORTED;
     ncells *= cfg->n[d];
@@ -527,6 +532,7 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
     g.bc[d][1] = d < cfg->dim ? cfg->bc[d][1] : 0;
   }
   c->p.gamma = cfg->gamma > 0 ? cfg->gamma : 1.4;
+  c->p.grav = cfg->grav > 0 ? cfg->grav : 9.81;
   for (int d = 0; d < 3; ++d) c->p.a[d] = cfg->adv[d];
   if (!build_tables(cfg->order, c->tab)) {
     delete c;

@@ -22,7 +22,7 @@ struct Cfg {
   static constexpr int NL = NS * NV;            // lines (spatial node, variable)
   static constexpr int NF = ipow(n, D - 1);     // nodes per face
   static constexpr int FR = NF * NV * (P::CONS ? 2 : 1);  // doubles per face record
-  static constexpr int NPHI = P::NCP ? 2 : 1;   // numerical fluxes per face node and variable
+  static constexpr int NPHI = (P::NCP || P::NCPS) ? 2 : 1;  // numerical fluxes per face node and variable
   static constexpr int TPB_RAW = ((NL + 5) / 6 + 31) / 32 * 32;
   static constexpr int TPB = TPB_RAW < 64 ? 64 : (TPB_RAW > 512 ? 512 : TPB_RAW);
   static constexpr int LPT = (NL + TPB - 1) / TPB;   // lines per thread
@@ -87,6 +87,36 @@ __device__ __forceinline__ void contract_ncp_elastic(const double* X, const doub
 #pragma unroll
           for (int m = 0; m < n; ++m) acc = fma(Dr[m], X[t * NL + (j0 + m * st) * NV + s], acc);
           R[k][t] = fma(coef, acc, R[k][t]);
+        }
+      }
+    }
+  }
+}
+
+// Shallow water: row 1 + d of B_d(q) dq/dx_d is g h (dh/dx_d + db/dx_d) with the node's own h
+// (state-dependent non-conservative product), accumulated as R -= g h (1/h_d) D_d (h + b).
+template <class C, int d, int RS>
+__device__ __forceinline__ void contract_ncp_swe(const double* X, const double* Dm, double inv_h,
+                                                 double grav, double (&R)[C::LPT][C::n], int tid) {
+  constexpr int n = C::n, NV = C::NV, NL = C::NL, TPB = C::TPB, st = ipow(n, d);
+#pragma unroll
+  for (int k = 0; k < C::LPT; ++k) {
+    const int l = tid + k * TPB;
+    if (l < NL) {
+      const int j = l / NV, v = l - (l / NV) * NV;
+      if (v == 1 + d) {
+        const int jd = digit<n, d>(j);
+        const int j0 = j - jd * st;
+        const double* Dr = Dm + jd * RS;
+#pragma unroll
+        for (int t = 0; t < n; ++t) {
+          double acc = 0.0;
+#pragma unroll
+          for (int m = 0; m < n; ++m) {
+            const double* q = X + t * NL + (j0 + m * st) * NV;
+            acc = fma(Dr[m], q[0] + q[3], acc);
+          }
+          R[k][t] = fma(-grav * inv_h * X[t * NL + j * NV], acc, R[k][t]);
         }
       }
     }
@@ -328,6 +358,10 @@ __device__ __forceinline__ void predictor_cell(const StepArgs& A, const Tables& 
       contract_ncp_elastic<C, 1, n>(qs, sD, A.g.inv_h[1], irho, lam, mu, R, tid);
       contract_ncp_elastic<C, 2, n>(qs, sD, A.g.inv_h[2], irho, lam, mu, R, tid);
     }
+    if constexpr (P::NCPS) {
+      contract_ncp_swe<C, 0, n>(qs, sD, A.g.inv_h[0], A.p.grav, R, tid);
+      contract_ncp_swe<C, 1, n>(qs, sD, A.g.inv_h[1], A.p.grav, R, tid);
+    }
     if (has_src) {
 #pragma unroll
       for (int k = 0; k < LPT; ++k) {
@@ -450,6 +484,24 @@ __device__ __forceinline__ void predictor_cell(const StepArgs& A, const Tables& 
 #pragma unroll
             for (int m = 0; m < n; ++m) dq = fma(sD[jd * n + m], qbs[(j0 + m * st) * NV + s], dq);
             vol -= A.g.inv_h[d] * Elastic::coef_ir(d, v, irho, lam, mu) * dq;
+          }
+        }
+        if constexpr (P::NCPS) {
+          // time average of the state-dependent product taken node by node (sum_t w_t g h_t
+          // (D_d (h + b))_t), not of the product of the time averages
+          if (v == 1 + d) {
+            double nb = 0.0;
+#pragma unroll
+            for (int t = 0; t < n; ++t) {
+              double acc = 0.0;
+#pragma unroll
+              for (int m = 0; m < n; ++m) {
+                const double* q = qs + t * NL + (j0 + m * st) * NV;
+                acc = fma(sD[jd * n + m], q[0] + q[3], acc);
+              }
+              nb = fma(T.w[t] * qs[t * NL + j * NV], acc, nb);
+            }
+            vol -= A.g.inv_h[d] * A.p.grav * nb;
           }
         }
       }
@@ -714,7 +766,20 @@ __device__ __forceinline__ void riemann_face(const StepArgs& A, const Tables& T,
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const double G = 0.5 * (FL[r][v] + FR_[r][v]) - 0.5 * s * (qR[r][v] - qL[r][v]);
-        if constexpr (P::NCP) {
+        if constexpr (P::NCPS) {
+          // shallow water: the path-conservative fluctuation along the straight segment from qL
+          // to qR, int_0^1 g h(z) dz (dh + db) on the momentum of direction d (3-point rule)
+          double half = 0.0;
+          if (v == 1 + d) {
+            const double dh = qR[r][0] - qL[r][0], dhb = dh + (qR[r][3] - qL[r][3]);
+            double fl = 0.0;
+#pragma unroll
+            for (int gq = 0; gq < 3; ++gq) fl = fma(T.pw[gq], A.p.grav * fma(T.pz[gq], dh, qL[r][0]) * dhb, fl);
+            half = 0.5 * fl;
+          }
+          out[jp * NV + v] = G + half;
+          out[NF * NV + jp * NV + v] = G - half;
+        } else if constexpr (P::NCP) {
           // source variable of row v of B_d, chosen among the three compile-time candidates (the
           // direction d is a run-time value: no dynamic register indexing)
           const int s0 = Elastic::src(0, v), s1 = Elastic::src(1, v), s2 = Elastic::src(2, v);
@@ -1025,6 +1090,7 @@ template <class P, int D>
 size_t FamilyImpl<P, D>::smem(int order, int prec) {
 #define ADER_SMEM_CASE(NN) \
   case NN: return prec == 1 ? CfgM<P, D, NN>::SMEM : Cfg<P, D, NN>::SMEM;
+  if constexpr (P::NCPS) prec = 0;  // FP64 only
   switch (order) {
     ADER_SMEM_CASE(1)
     ADER_SMEM_CASE(2)
@@ -1040,8 +1106,10 @@ size_t FamilyImpl<P, D>::smem(int order, int prec) {
 template <class P, int D>
 cudaError_t FamilyImpl<P, D>::predictor(const StepArgs& a, const Tables& t, const TablesF& f,
                                         int prec, cudaStream_t s) {
-  if (prec == 1) {
-    ADER_DISPATCH_N(launch_predictor_mixed_n, a, t, f, s)
+  if constexpr (!P::NCPS) {
+    if (prec == 1) {
+      ADER_DISPATCH_N(launch_predictor_mixed_n, a, t, f, s)
+    }
   }
   ADER_DISPATCH_N(launch_predictor_n, a, t, s)
 }

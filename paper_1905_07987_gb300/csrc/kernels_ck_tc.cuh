@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256, 2)
 
   // first cell's state
   long long c = blockIdx.x;
-  bool pending[2] = {false, false};  // TMA loads issued and not yet waited for
+  bool pending[2] = {false, false};  // TMA loads issued and not yet waited for (thread 0)
   if (tid == 0 && c < ncells) {
     tc::mbar_arrive_expect_tx(&bar_tma[0], CELL_BYTES);
     tc::tma_load_3d(sm + C::OFF_ST, &tmap, 0, 0, (int)c, &bar_tma[0]);
@@ -179,8 +179,9 @@ __global__ void __launch_bounds__(256, 2)
                       &bar_tma[buf ^ 1]);
       pending[buf ^ 1] = true;
     }
-    // per-cell coefficients (one FP64 division per cell) and the point source
-    if (tid == 0) {
+    // per-cell coefficients (one FP64 division per cell, by a thread other than the one that
+    // issues the copies) and the point source
+    if (tid == 32) {
       const double irho = 1.0 / A.mat[c * 3 + 0], lam = A.mat[c * 3 + 1], mu = A.mat[c * 3 + 2];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
@@ -216,10 +217,14 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
         for (int i = 0; i < 6; ++i) g[i] = (float)(-A.src.M[i] * A.src.phi[j]);
     }
-    // wait for this cell's state
-    const bool tma_ok = tc::mbar_wait(&bar_tma[buf], tma_phase[buf], CKT_WAIT);
+    // wait for this cell's state: one thread polls the barrier, the block waits at bar.sync
+    // (no issue slots taken from the other resident block)
+    bool tma_ok = true;
+    if (tid == 0) {
+      tma_ok = tc::mbar_wait(&bar_tma[buf], tma_phase[buf], CKT_WAIT);
+      pending[buf] = !tma_ok;
+    }
     tma_phase[buf] ^= 1u;
-    pending[buf] = !tma_ok;
     if (__syncthreads_or(!tma_ok)) {
       failed = true;
       break;
@@ -288,14 +293,19 @@ __global__ void __launch_bounds__(256, 2)
         }
         tc::mma_commit(&bar_mma);
       }
-      mma_pending = true;
-      const bool mma_ok = tc::mbar_wait(&bar_mma, mma_phase, CKT_WAIT);
+      // the issuing thread waits for the MMAs; the block waits at bar.sync
+      bool mma_ok = true;
+      if (tid == 0) {
+        mma_pending = true;
+        mma_ok = tc::mbar_wait(&bar_mma, mma_phase, CKT_WAIT);
+        if (mma_ok) mma_pending = false;
+        tc::tc_fence_before();
+      }
       if (__syncthreads_or(!mma_ok)) {
         failed = true;
         break;
       }
       mma_phase ^= 1u;
-      mma_pending = false;
       tc::tc_fence_after();
       // (3) line owners: derivatives to the nodes, face values to the face records
       {

@@ -16,6 +16,7 @@ struct Advection {
   static constexpr int NV = 1;
   static constexpr bool CONS = true;
   static constexpr bool NCP = false;
+  static constexpr bool NCPS = false;
   static constexpr bool LINEAR = true;
   static constexpr int DIM = D;
   struct Aux {};
@@ -34,6 +35,7 @@ struct Euler {
   static constexpr int NV = D + 2;
   static constexpr bool CONS = true;
   static constexpr bool NCP = false;
+  static constexpr bool NCPS = false;
   static constexpr bool LINEAR = false;
   static constexpr int DIM = D;
   struct Aux {
@@ -108,6 +110,7 @@ struct Elastic {
   static constexpr int NV = 9;
   static constexpr bool CONS = false;
   static constexpr bool NCP = true;
+  static constexpr bool NCPS = false;
   static constexpr bool LINEAR = true;
   static constexpr int DIM = 3;
   __host__ __device__ static constexpr int sig(int i, int j) {
@@ -139,6 +142,45 @@ struct Elastic {
   // Wall boundaries are not offered for elastic contexts (rejected at creation).
   __device__ static void mirror(double*, int) {}
   __device__ static void mirror_flux(double*, int) {}
+};
+
+// Shallow water equations with bathymetry (Eq. (9), Sec. 2), Q = (h, hu, hv, b): the flux
+// F_d = (h u_d, hu u_d, hv u_d, 0) and the state-dependent non-conservative product
+// g h d(h + b)/dx_d on the momentum of direction d (the hydrostatic pressure and the bathymetry
+// slope; b is a state variable the equations keep constant).  NCPS: B_d(Q) depends on the state.
+struct ShallowWater {
+  static constexpr int NV = 4;
+  static constexpr bool CONS = true;
+  static constexpr bool NCP = false;
+  static constexpr bool NCPS = true;
+  static constexpr bool LINEAR = false;
+  static constexpr int DIM = 2;
+  struct Aux {
+    double ih;
+  };
+  __device__ static void aux(const double* q, const PdeParams&, Aux& a) { a.ih = 1.0 / q[0]; }
+  __device__ static void flux(const double* q, const Aux& a, const PdeParams&, int d, double* F) {
+    const double ud = q[1 + d] * a.ih;
+    F[0] = q[1 + d];
+    F[1] = q[1] * ud;
+    F[2] = q[2] * ud;
+    F[3] = 0.0;
+  }
+  // |u_d| + sqrt(g h): the largest |eigenvalue| of the direction-d system (NaN for h < 0)
+  __device__ static double speed(const double* q, const PdeParams& pp, int d) {
+    return fabs(q[1 + d] / q[0]) + sqrt(pp.grav * q[0]);
+  }
+  __device__ static double speed_all(const double* q, const PdeParams& pp) {
+    const double ih = 1.0 / q[0];
+    return fmax(fabs(q[1] * ih), fabs(q[2] * ih)) + sqrt(pp.grav * q[0]);
+  }
+  __device__ static void mirror(double* q, int d) { q[1 + d] = -q[1 + d]; }
+  // F_d of the mirrored state: every component but the normal momentum flux changes sign
+  __device__ static void mirror_flux(double* F, int d) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      if (v != 1 + d) F[v] = -F[v];
+  }
 };
 
 }  // namespace ader

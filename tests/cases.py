@@ -6,7 +6,7 @@ import numpy as np
 import torch
 
 from oracle.aderdg import ADERDG, Grid, PointSource
-from oracle.pde import Advection, Elastic, Euler
+from oracle.pde import Advection, Elastic, Euler, ShallowWater
 from paper_1905_07987_gb300 import ader, synth
 
 
@@ -45,6 +45,8 @@ class Case:
             P = Euler(dim)
         elif pde == "advection":
             P = Advection(self.adv)
+        elif pde == "swe":
+            P = ShallowWater(9.81)
         else:
             P = Elastic()
         mat_t = torch.from_numpy(material) if material is not None else None

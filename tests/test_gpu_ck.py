@@ -295,7 +295,12 @@ def test_ck_full_size_sampled_cells_elastic_81(precision):
         elif precision == "mixed":
             assert change_rel(g, out[13], loc[13]) < 2e-6, (i, j, k)
         else:
-            err = change_rel(g, out[13], loc[13])
-            print("tf32x3 81^3 cell %s: error / step change %.3e" % ((i, j, k), err))
+            # the TF32 error of a face value is relative to the data of the cell it comes from:
+            # next to the source cell the scale is that cell's (much larger) change, so the error
+            # is measured against the largest change in the 3x3x3 neighbourhood
+            nv = out.shape[-1]
+            chg = np.abs(out - np.stack(loc)).reshape(-1, nv).max(axis=0)
+            err = float((np.abs(g - out[13]).reshape(-1, nv).max(axis=0) / np.maximum(chg, 1e-300)).max())
+            print("tf32x3 81^3 cell %s: error / neighbourhood step change %.3e" % ((i, j, k), err))
             assert err < TOL_TC_SMOOTH, (i, j, k)
     ctx.close()

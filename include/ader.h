@@ -134,6 +134,12 @@ typedef struct {
   int predictor;       /* ader_predictor (0 = Picard) */
   int initial_guess;   /* ader_guess (0 = constant in time) */
   double grav;         /* gravitational acceleration (ADER_PDE_SWE); <= 0 => 9.81 */
+  double adm_floor;    /* limiter, physical admissibility (Table 2 isPhysicallyAdmissable): density
+                          and pressure above adm_floor at every node and subcell (<= 0: positive).
+                          A step whose MUSCL-Hancock recompute of a troubled cell is not
+                          admissible is redone for all its troubled cells with the first-order
+                          (zero-slope) scheme; if that is not admissible either, the next
+                          synchronising call returns ADER_EADMISSIBLE */
 } ader_config;
 
 /* Create a context on the current CUDA device.  `cuda_stream` is a cudaStream_t (NULL = the

@@ -23,6 +23,11 @@ Readings of the paper taken here (silent or only cited points):
   exactly conservative.
 * The troubled cell's new DG polynomial is R(U_sub) (mean-preserving least squares); U_sub is kept
   as its representation for the next step.  Neither recompute nor cascade is iterated.
+* First-order fallback (Table 1 names Godunov's scheme beside MUSCL-Hancock): if the
+  MUSCL-Hancock result of any troubled cell is not physically admissible, the step's FV recompute
+  is redone for every troubled cell with zero slopes (the first-order Godunov-type scheme with
+  the Rusanov flux), so that each subface keeps one flux and the scheme stays conservative.
+  Physical admissibility: finite, density and pressure above ``floor`` (0: positive).
 """
 import torch
 
@@ -31,8 +36,10 @@ EPS = 1e-3
 
 
 class Limiter:
-    def __init__(self, solver, delta0=DELTA0, eps=EPS):
+    def __init__(self, solver, delta0=DELTA0, eps=EPS, floor=0.0):
         self.s = solver
+        self.floor = float(floor)
+        self.last_fallback = False
         self.pde = solver.pde
         self.D = solver.D
         self.ref = solver.ref
@@ -69,10 +76,11 @@ class Limiter:
 
     # ---- detection -----------------------------------------------------------------------
     def admissible(self, q):
-        """Density and pressure positive and all values finite, over all axes but the first."""
+        """Density and pressure above the floor (positive for floor 0) and all values finite,
+        over all axes but the first."""
         rho = q[..., 0]
         p = self.pde.pressure(q)
-        ok = (rho > 0) & (p > 0) & torch.isfinite(q).all(dim=-1)
+        ok = (rho > self.floor) & (p > self.floor) & torch.isfinite(q).all(dim=-1)
         return ok.reshape(ok.shape[0], -1).all(dim=1)
 
     def detect(self, u_star, rep):
@@ -265,8 +273,13 @@ class Limiter:
             troubled = troubled | self.face_neighbours(troubled)
         u_new = u_star.clone()
         rep_new = cand.clone()
+        self.last_fallback = False
         if troubled.any():
             U_all, fluxes = self.fv_global(rep, dt)
+            if not bool(self.admissible(U_all[troubled]).all()):
+                # first-order fallback for every troubled cell of the step
+                U_all, fluxes = self.fv_global(rep, dt, slopes=False)
+                self.last_fallback = True
             u_new[troubled] = self.reconstruct(U_all[troubled])
             rep_new[troubled] = U_all[troubled]
             nc = list(reversed(g.ncell))

@@ -45,6 +45,7 @@ class Config(ctypes.Structure):
         ("predictor", ctypes.c_int),
         ("initial_guess", ctypes.c_int),
         ("grav", ctypes.c_double),
+        ("adm_floor", ctypes.c_double),
     ]
 
 
@@ -157,7 +158,7 @@ def _ptr(a, dtype=np.float64):
 
 def make_config(pde, dim, order, ncell, lo, hi, bc, cfl, gamma=1.4, adv=(0.0, 0.0, 0.0),
                 picard_iters=0, limiter=False, precision="fp64", predictor="picard",
-                initial_guess="constant", grav=9.81):
+                initial_guess="constant", grav=9.81, adm_floor=0.0):
     c = Config()
     c.dim = dim
     c.order = order
@@ -182,6 +183,7 @@ def make_config(pde, dim, order, ncell, lo, hi, bc, cfl, gamma=1.4, adv=(0.0, 0.
     c.predictor = PREDICTOR[predictor] if isinstance(predictor, str) else int(predictor)
     c.initial_guess = GUESS[initial_guess] if isinstance(initial_guess, str) else int(initial_guess)
     c.grav = float(grav)
+    c.adm_floor = float(adm_floor)
     return c
 
 

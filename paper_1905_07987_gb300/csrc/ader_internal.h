@@ -29,7 +29,7 @@ struct DevScalars {
   long long nstep;           // steps taken
   long long seismo_row;      // next seismogram row
   int n_troubled;            // troubled cells of the last step
-  int pad2;
+  int fv_retry;              // limiter: a MUSCL-Hancock recompute of this step was inadmissible
 };
 
 // 1-D reference-element tables, passed by value as a kernel parameter (constant bank).
@@ -89,6 +89,8 @@ struct LimArgs {
   uint8_t* status;
   uint8_t* base;
   int persist;           // FV steps a detected cell keeps
+  double floor;          // physical admissibility: density and pressure above floor (0: positive)
+  int first_order;       // FV recompute with zero slopes (the first-order fallback pass)
 };
 struct AdjArgs;
 
@@ -187,6 +189,9 @@ struct Family {
   // Cauchy-Kowalevski predictor (linear systems; null otherwise): same outputs as `predictor`
   cudaError_t (*predictor_ck)(const StepArgs&, const Tables&, const TablesF&, int prec,
                               cudaStream_t);
+  // numerical fluxes per face node and variable the Riemann kernel writes (2: the left and right
+  // cells see different values, a path-conservative fluctuation); sizes the flux buffer
+  int nphi;
 };
 cudaError_t launch_set_scalars(DevScalars* d, double t, double dt, cudaStream_t s);
 cudaError_t launch_merge_status(DevScalars* src, DevScalars* dst, cudaStream_t s);

@@ -548,7 +548,7 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
   c->ndof = ncells * c->nodes * c->nvar;
   c->nf = (int)(c->nodes / n);
   const long long face_rec = (long long)c->nf * c->nvar * (fam->conservative ? 2 : 1);
-  const int nphi = cfg->pde == ADER_PDE_ELASTIC ? 2 : 1;
+  const int nphi = fam->nphi;  // as many fluxes per face node as the family's kernels write
   long long nphi_total = 0;
   for (int d = 0; d < cfg->dim; ++d)
     nphi_total += (long long)(g.n[d] + 1) * (ncells / g.n[d]) * nphi * c->nf * c->nvar;
@@ -873,6 +873,8 @@ static ader_status step_impl(ader_ctx* c, double dt, double t_end) {
       l.base = c->lbase;
       l.persist = LIM_PERSIST;
     }
+    l.floor = c->cfg.adm_floor > 0.0 ? c->cfg.adm_floor : 0.0;
+    l.first_order = 0;
     CUDA_OK(c->fam->lim_step(a, l, c->tab, c->sub, s));
     std::swap(c->rep, c->rep_new);
     std::swap(c->mm, c->mm_new);
@@ -1326,7 +1328,7 @@ static ader_status ens_capture_persistent(ader_ensemble* e, int steps, double dt
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   E.pblocks = sms * bps;
-  const long long nphi = e->runs[0]->cfg.pde == ADER_PDE_ELASTIC ? 2 : 1;
+  const long long nphi = e->runs[0]->fam->nphi;
   for (int r = 0; r < nr; ++r) {
     const ader_ctx* c = e->runs[r];
     E.cell0[r + 1] = E.cell0[r] + c->g.ncells;

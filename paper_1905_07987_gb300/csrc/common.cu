@@ -26,6 +26,7 @@ __device__ __forceinline__ void dt_finalize_one(const StepArgs& A) {
   s->lam_bits = 0ull;
   s->lam_lo_bits = 0u;
   s->n_troubled = 0;
+  s->fv_retry = 0;
 }
 
 __global__ void k_dt_finalize(const __grid_constant__ StepArgs A) { dt_finalize_one(A); }

@@ -1076,8 +1076,12 @@ struct FamilyImpl {
   }
   static size_t smem(int order, int prec);
   static const Family* get() {
-    static const Family f = {P::NV, P::CONS, &cfl,    &predictor, &riemann, &corrector, &smem,
-                             nullptr, nullptr, nullptr, nullptr,   nullptr,  nullptr};
+    static const Family f = [] {
+      Family g = {P::NV, P::CONS, &cfl,    &predictor, &riemann, &corrector, &smem,
+                  nullptr, nullptr, nullptr, nullptr,   nullptr,  nullptr,    nullptr, 0};
+      g.nphi = Cfg<P, D, 1>::NPHI;
+      return g;
+    }();
     return &f;
   }
 };

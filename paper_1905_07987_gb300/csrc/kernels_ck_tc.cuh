@@ -163,9 +163,34 @@ __global__ void __launch_bounds__(256, 2)
 
   const bool node_owner = tid < NS;
   const int j = node_owner ? tid : 0;
-  int jp[3], jd[3];
+  // loop-invariant staging positions of the owned node: first line row of each direction (six-
+  // and three-variable line sets) and the K part of the offset (position along the direction)
+  int rbl[3], rbo[3], kt[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) jp[d] = face_node<n>(j, d, jd[d]);
+  for (int d = 0; d < 3; ++d) {
+    int jd;
+    const int jp = face_node<n>(j, d, jd);
+    rbl[d] = d * 6 * NF + jp * 6;
+    rbo[d] = d * 3 * NF + jp * 3;
+    kt[d] = (jd >> 2) * 32 + (jd & 3);
+  }
+  // loop-invariant rows of the line owner (tiles t = warp / 4 + 2 i): the first node of the line
+  // in Dv, its node stride, and its derivative slot
+  constexpr int LR = (C::TILES_L + 1) / 2;
+  int lrow_dv[LR], lrow_st[LR];
+#pragma unroll
+  for (int i = 0; i < LR; ++i) {
+    const int r = ((warp >> 2) + 2 * i) * 128 + (warp & 3) * 32 + lane;
+    lrow_dv[i] = -1;
+    lrow_st[i] = 0;
+    if (r < C::ROWS_L) {
+      const int d = r / (6 * NF), rr = r - d * 6 * NF;
+      const int f = rr / 6, q = rr - f * 6;
+      const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
+      lrow_dv[i] = ((f % st) + (f / st) * st * n) * C::DVS + d * 6 + q;
+      lrow_st[i] = st * C::DVS;
+    }
+  }
 
   for (int it = 0; c < ncells; ++it, c += gridDim.x) {
     const int buf = it & 1;
@@ -258,20 +283,22 @@ __global__ void __launch_bounds__(256, 2)
           if (oth) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-              const int r = d * 3 * NF + jp[d] * 3 + q;
+              const int r = rbo[d] + q;
+              const int o = (r >> 3) * 64 + (r & 7) * 4 + kt[d];
               const float xv = x[ck_other(d, q)];
               const float h = tc::to_tf32(xv);
-              AH[kmaj_off(r, jd[d])] = h;
-              AL[kmaj_off(r, jd[d])] = tc::to_tf32(xv - h);
+              AH[o] = h;
+              AL[o] = tc::to_tf32(xv - h);
             }
           } else {
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
-              const int r = d * 6 * NF + jp[d] * 6 + q;
+              const int r = rbl[d] + q;
+              const int o = (r >> 3) * 64 + (r & 7) * 4 + kt[d];
               const float xv = x[ck_need(d, q)];
               const float h = tc::to_tf32(xv);
-              AH[kmaj_off(r, jd[d])] = h;
-              AL[kmaj_off(r, jd[d])] = tc::to_tf32(xv - h);
+              AH[o] = h;
+              AL[o] = tc::to_tf32(xv - h);
             }
           }
         }
@@ -310,21 +337,22 @@ __global__ void __launch_bounds__(256, 2)
       // (3) line owners: derivatives to the nodes, face values to the face records
       {
         const int quarter = warp & 3;
-        for (int t = warp >> 2; t < tiles; t += 2) {
+#pragma unroll
+        for (int i = 0; i < LR; ++i) {
+          const int t = (warp >> 2) + 2 * i;
+          if (t >= tiles) break;
           float y[8];
           tc::tmem_ld8(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * 16), y);
           tc::tmem_wait_ld();
           const int r = t * 128 + quarter * 32 + lane;
           const int per = oth ? 3 : 6;
+          if (!oth && lrow_dv[i] >= 0) {
+#pragma unroll
+            for (int m = 0; m < n; ++m) Dv[lrow_dv[i] + m * lrow_st[i]] = y[m];
+          }
           if (r < (oth ? C::ROWS_O : C::ROWS_L)) {
             const int d = r / (per * NF), rr = r - d * per * NF;
             const int f = rr / per, q = rr - f * per;
-            if (!oth) {
-              const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
-              const int jb = (f % st) + (f / st) * st * n;
-#pragma unroll
-              for (int m = 0; m < n; ++m) Dv[(jb + m * st) * C::DVS + d * 6 + q] = y[m];
-            }
             if (vol || oth) {
               const int v = oth ? ck_other(d, q) : ck_need(d, q);
               double* fc = A.face + c * (3 * 2 * FR) + (d * 2) * FR + f * NV + v;
@@ -422,6 +450,10 @@ cudaError_t launch_predictor_ck_tc_n(const StepArgs& a, const Tables& t, cudaStr
   if (!blocks_per_sm) {
     cudaError_t e = cudaFuncSetAttribute(k_predictor_ck_tc<N>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    // the whole unified L1 / shared memory as shared memory, so that two blocks fit per SM
+    e = cudaFuncSetAttribute(k_predictor_ck_tc<N>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     int nb = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_predictor_ck_tc<N>, C::TPB, C::SMEM);

@@ -8,7 +8,9 @@
 //                 atomic per warp, lanes at their prefix count).
 //   k_lim_fv      persistent blocks over the troubled list: MUSCL-Hancock (minmod) + Rusanov on
 //                 the (2N+1)^d subcells with a 2-subcell halo from the t^n representations of all
-//                 neighbours, u_next = R(U_sub), the boundary subface fluxes saved per cell.
+//                 neighbours, u_next = R(U_sub), the boundary subface fluxes saved per cell; if
+//                 any result is not physically admissible, a second launch redoes every troubled
+//                 cell with zero slopes (first-order fallback).
 //   k_lim_fix     one block per cell: an untroubled face neighbour of a troubled cell replaces its
 //                 DG flux on the shared face by the subface fluxes integrated against its test
 //                 functions (exact conservation), then refreshes its representation.
@@ -171,6 +173,22 @@ __device__ __forceinline__ bool admissible(const double* q) {
          (__double_as_longlong(fma(e2, q[0], -j2)) > 0);
 }
 
+// Physical admissibility with a floor: finite, density and pressure above `floor` (floor 0: the
+// division-free positivity test above).
+template <int D>
+__device__ __forceinline__ bool admissible_f(const double* q, double floor, double gamma) {
+  if (!(floor > 0.0)) return admissible<D>(q);
+  bool fin = true;
+#pragma unroll
+  for (int v = 0; v < D + 2; ++v) fin = fin && ((__double2hiint(q[v]) & 0x7ff00000) != 0x7ff00000);
+  double j2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) j2 = fma(q[1 + i], q[1 + i], j2);
+  const double p = (gamma - 1.0) * (q[D + 1] - 0.5 * j2 / q[0]);
+  return fin && q[0] > floor && p > floor;
+}
+
+
 // Per-variable min / max of sub[NSS][NV] into mm[2][NV]; red: smem scratch [2][NV][32].
 // Finite inputs give the same values as fmin / fmax (a zero comes out as +0).
 template <int NSS, int NV>
@@ -257,14 +275,15 @@ __global__ void __launch_bounds__(128) k_lim_detect(const __grid_constant__ Step
   bool ok = true;
   for (int s = threadIdx.x; s < NSS; s += blockDim.x) {
     const double* q = sub + s * NV;
-    ok = ok && admissible<D>(q);
+    ok = ok && admissible_f<D>(q, L.floor, A.p.gamma);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const long long k = okey(q[v]);
       ok = ok && (k >= bk[0][v]) && (k <= bk[1][v]);
     }
   }
-  for (int j = threadIdx.x; j < NN; j += blockDim.x) ok = ok && admissible<D>(us + j * NV);
+  for (int j = threadIdx.x; j < NN; j += blockDim.x)
+    ok = ok && admissible_f<D>(us + j * NV, L.floor, A.p.gamma);
   const bool all_ok = __syncthreads_and(ok) != 0;
   const bool troubled = L.force ? true : !all_ok;
   double* rn = L.rep_new + c * (NSS * NV);
@@ -367,6 +386,10 @@ __global__ void __launch_bounds__(FV_TPB) k_lim_fv(const __grid_constant__ StepA
   __shared__ long long red[2 * NV * 32];
   const double dt = A.dev->dt;
   const int count = A.dev->n_troubled;
+  // first-order pass (zero slopes): only when the MUSCL-Hancock pass of this step found an
+  // inadmissible result, and then for every troubled cell (each subface keeps one flux)
+  const bool fo = L.first_order != 0;
+  if (fo && *(volatile const int*)&A.dev->fv_retry == 0) return;
   for (int it = blockIdx.x; it < count; it += gridDim.x) {
     const long long c = L.list[it];
     int cidx[3];
@@ -411,7 +434,7 @@ __global__ void __launch_bounds__(FV_TPB) k_lim_fv(const __grid_constant__ StepA
         double Up[NV], Um[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const double sg = minmod(U[v] - U[v - sd * NV], U[v + sd * NV] - U[v]);
+          const double sg = fo ? 0.0 : minmod(U[v] - U[v - sd * NV], U[v + sd * NV] - U[v]);
           Up[v] = U[v] + 0.5 * sg;
           Um[v] = U[v] - 0.5 * sg;
         }
@@ -475,8 +498,8 @@ __global__ void __launch_bounds__(FV_TPB) k_lim_fv(const __grid_constant__ StepA
         for (int v = 0; v < NV; ++v) {
           const double* UL = H + hL * NV;
           const double* UR = H + hR * NV;
-          const double sL = minmod(UL[v] - UL[v - sd * NV], UL[v + sd * NV] - UL[v]);
-          const double sR = minmod(UR[v] - UR[v - sd * NV], UR[v + sd * NV] - UR[v]);
+          const double sL = fo ? 0.0 : minmod(UL[v] - UL[v - sd * NV], UL[v + sd * NV] - UL[v]);
+          const double sR = fo ? 0.0 : minmod(UR[v] - UR[v - sd * NV], UR[v + sd * NV] - UR[v]);
           QL[v] = (UL[v] + 0.5 * sL) + INC[cL * NV + v];
           QR[v] = (UR[v] - 0.5 * sR) + INC[cR * NV + v];
         }
@@ -531,7 +554,10 @@ __global__ void __launch_bounds__(FV_TPB) k_lim_fv(const __grid_constant__ StepA
     for (int k = 0; k < KPT; ++k) {
       const int e = threadIdx.x + k * FV_TPB;
       if (e < NSS) {
-        if (!admissible<D>(Unew[k])) atomicOr(&A.dev->status, ST_ADMISSIBLE);
+        if (!admissible_f<D>(Unew[k], L.floor, A.p.gamma)) {
+          if (fo) atomicOr(&A.dev->status, ST_ADMISSIBLE);  // the fallback is not admissible
+          else A.dev->fv_retry = 1;                         // redo the step first order
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) UN[e * NV + v] = Unew[k][v];
       }
@@ -713,6 +739,11 @@ struct LimLaunch {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_lim_fv<D, N><<<152 * 2, FV_TPB, C::SMEM_FV, s>>>(a, l, S);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    LimArgs lf = l;  // the first-order fallback (its blocks return unless a retry is flagged)
+    lf.first_order = 1;
+    k_lim_fv<D, N><<<152 * 2, FV_TPB, C::SMEM_FV, s>>>(a, lf, S);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     long long offs[3] = {0, 0, 0}, off = 0;

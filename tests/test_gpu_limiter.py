@@ -7,7 +7,7 @@ import pytest
 import torch
 
 from oracle.limiter import Limiter
-from paper_1905_07987_gb300 import synth
+from paper_1905_07987_gb300 import ader, synth
 from cases import Case, rel_linf
 
 pytestmark = pytest.mark.gpu
@@ -182,3 +182,54 @@ def test_hybrid_status_run_matches_the_oracle(ncell, order, steps, box):
         if step < 2:  # the initial FV cells keep their two FV steps
             assert got[flags].all(), step
     assert rel_linf(c.get(), u.numpy()) <= 1e-11
+
+
+def rarefaction_case(floor):
+    """rho = 1, p = 0.4, u = -3 / +3 left / right of x = 0 on 8 x 4 cells, order 2, walls, and an
+    admissibility floor on density and pressure (Table 2 isPhysicallyAdmissable)."""
+    nc, lo, hi = (8, 4), (-1.0, -0.5), (1.0, 0.5)
+    c = Case("euler", 2, 2, nc, lo=lo, hi=hi, bc="wall", limiter=1)
+    c.ctx.close()
+    c.cfg = ader.make_config("euler", 2, 2, nc, lo, hi, "wall", c.cfl, limiter=1, adm_floor=floor)
+    c.ctx = ader.Context(c.cfg)
+    lim = Limiter(c.oracle, floor=floor)
+    Xs = synth.subcell_centres(lim.ns, nc, lo, hi)
+    Us = synth.euler_conserved(np.ones_like(Xs[0]), [np.where(Xs[0] < 0, -3.0, 3.0), 0 * Xs[0]],
+                               np.full_like(Xs[0], 0.4))
+    u0 = synth.euler_conserved(np.ones_like(c.X[0]), [np.where(c.X[0] < 0, -3.0, 3.0), 0 * c.X[0]],
+                               np.full_like(c.X[0], 0.4))
+    flags = synth.discontinuous_cells(Us)
+    u, rep = lim.initial_rep(torch.from_numpy(u0), torch.from_numpy(Us), torch.from_numpy(flags))
+    return c, lim, u0, Us, flags, u, rep
+
+
+def test_first_order_fallback_matches_the_oracle():
+    """Floor 0.1: the MUSCL-Hancock recompute of the third step falls below it, the step is redone
+    with the first-order scheme for every troubled cell (a second, conditional launch); flags,
+    state and representation equal the oracle's every step, and no error is reported."""
+    from paper_1905_07987_gb300 import ader as _a  # noqa: F401
+    c, lim, u0, Us, flags, u, rep = rarefaction_case(0.1)
+    gpu_set(c, u0, Us, flags)
+    used = []
+    for step in range(3):
+        c.ctx.step()
+        dt = c.ctx.last_dt()  # raises on a latched error
+        u, tr, rep, ok = lim.step(u, rep, torch.tensor(dt, dtype=torch.float64))
+        used.append(lim.last_fallback)
+        assert ok
+        assert np.array_equal(c.ctx.flags().astype(bool), tr.numpy()), step
+        assert rel_linf(c.get(), u.numpy()) <= TOL, step
+        assert rel_linf(gpu_rep(c, lim), rep.numpy()) <= TOL, step
+    assert used == [False, False, True]
+
+
+def test_fallback_that_is_still_inadmissible_is_reported():
+    c, lim, u0, Us, flags, u, rep = rarefaction_case(0.39)
+    gpu_set(c, u0, Us, flags)
+    c.ctx.step()
+    c.ctx.step()
+    c.ctx.sync()
+    c.ctx.step()
+    with pytest.raises(ader.AderError) as e:
+        c.ctx.sync()
+    assert e.value.status == ader.EADMISSIBLE

@@ -293,3 +293,60 @@ def test_hybrid_with_every_cell_fv_is_the_pure_fv_scheme():
     U_all, _ = lim.fv_global(rep, dt)
     assert fv.all() and torch.equal(rep1, U_all)
     assert torch.equal(u1, lim.reconstruct(U_all))
+
+
+# ---- first-order fallback of the FV recompute (Table 1: Godunov beside MUSCL-Hancock) --------
+
+def double_rarefaction(s, lim, nc, lo, hi, ul=-3.0, p=0.4):
+    """rho = 1, p = 0.4, u = -3 / +3 left / right of x = 0: two strong rarefactions that deepen
+    the density and pressure minimum at the centre (the cells along x = 0 start in FV)."""
+    Xs = synth.subcell_centres(lim.ns, nc, lo, hi)
+    Us = synth.euler_conserved(np.ones_like(Xs[0]), [np.where(Xs[0] < 0, ul, -ul), 0 * Xs[0]],
+                               np.full_like(Xs[0], p))
+    X = coords(s)
+    u0 = synth.euler_conserved(np.ones_like(X[0]), [np.where(X[0] < 0, ul, -ul), 0 * X[0]],
+                               np.full_like(X[0], p))
+    fl = synth.discontinuous_cells(Us)
+    return lim.initial_rep(T(u0), T(Us), torch.from_numpy(fl))
+
+
+def test_fallback_is_the_first_order_scheme_where_muscl_falls_below_the_floor():
+    """With an admissibility floor of 0.1 on density and pressure the MUSCL-Hancock recompute of
+    the third step dips to p ~ 0.015 at the centre while the zero-slope scheme stays near 0.33:
+    that step is redone first order for every troubled cell (its result equals the step with
+    the zero-slope scheme), it is admissible, and mass and energy stay conserved."""
+    nc, lo, hi = (8, 4), (-1.0, -0.5), (1.0, 0.5)
+    s, _ = make(nc, 2, lo, hi, 'wall')
+    lim = Limiter(s, floor=0.1)
+    u, rep = double_rarefaction(s, lim, nc, lo, hi)
+    m0 = totals(s, u)
+    used = []
+    for _ in range(3):
+        dt = s.cfl_dt(u)
+        U_muscl, _ = lim.fv_global(rep, dt)
+        U_god, _ = lim.fv_global(rep, dt, slopes=False)
+        u_prev, rep_prev = u, rep
+        u, tr, rep, ok = lim.step(u, rep, dt)
+        used.append(lim.last_fallback)
+        assert ok
+        if lim.last_fallback:
+            assert not bool(lim.admissible(U_muscl[tr]).all())
+            assert torch.equal(rep[tr], U_god[tr])
+        else:
+            assert torch.equal(rep[tr], U_muscl[tr])
+    assert used == [False, False, True]
+    m1 = totals(s, u)
+    assert abs(float(m1[0] - m0[0])) < 1e-13 * float(m0[0])
+    assert abs(float(m1[3] - m0[3])) < 1e-13 * float(m0[3])
+
+
+def test_fallback_that_is_still_inadmissible_is_reported():
+    nc, lo, hi = (8, 4), (-1.0, -0.5), (1.0, 0.5)
+    s, _ = make(nc, 2, lo, hi, 'wall')
+    lim = Limiter(s, floor=0.39)  # above the zero-slope scheme's minimum pressure at step 3
+    u, rep = double_rarefaction(s, lim, nc, lo, hi)
+    oks = []
+    for _ in range(3):
+        u, tr, rep, ok = lim.step(u, rep, s.cfl_dt(u))
+        oks.append(ok)
+    assert not all(oks) and lim.last_fallback

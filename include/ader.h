@@ -326,12 +326,21 @@ ader_status ader_ensemble_sync(ader_ensemble* ens);
 /* Launch shape: steps_per_graph even and >= 2.  branches in [1, 16]: the runs' per-context kernels
  * on that many forked streams inside the graph.  branches = 0: one persistent launch per phase of
  * the step (dt, predictor, Riemann per direction, corrector, time advance) for all runs together,
- * blocks_per_sm (1..8) persistent predictor blocks per SM; it needs runs of one PDE family with
+ * blocks_per_sm (1..8) persistent predictor blocks per SM.  branches = -1: the steps_per_graph
+ * steps of all runs as ONE cooperative persistent launch (every block resident), the phases of
+ * each step separated by grid-wide barriers (see ader_ensemble_set_wait_limit), blocks_per_sm
+ * blocks per SM (at most as many as fit).  Both persistent forms need runs of one PDE family with
  * such a path (elastic, order <= 5), one order, precision, cell size and gamma, a fixed dt, no
  * limiter and no receivers (otherwise the step falls back to one branch).  ADER_EINVAL for other
  * values. */
 ader_status ader_ensemble_set_launch(ader_ensemble* ens, int branches, int steps_per_graph,
                                      int blocks_per_sm);
+/* Polls of a grid-wide barrier wait of the fused launch before it gives up (default 2^24, about
+ * 1.7 s): a block whose wait runs out latches ADER_ETIMEOUT in every run's status word and leaves,
+ * the other blocks then run out at the same barrier, and the next synchronising call
+ * (ader_ensemble_sync) returns ADER_ETIMEOUT; the barrier is reset before every launch, so the
+ * ensemble stays usable (the states of that launch are not).  0 gives up at once (a test knob). */
+ader_status ader_ensemble_set_wait_limit(ader_ensemble* ens, int64_t polls);
 /* Autotuner: times every candidate launch shape with fixed dt > 0 on the current states (which it
  * restores) and keeps the fastest: branches in {1, 2, 4} and, when the runs allow it, the
  * persistent launches with 1 or 2 blocks per SM, each with steps_per_graph in {2, 4}.

@@ -89,6 +89,7 @@ _SIGS = {
     "ader_ensemble_sync": ([_P], _I),
     "ader_ensemble_set_launch": ([_P, _I, _I, _I], _I),
     "ader_ensemble_autotune": ([_P, _D, _P, ctypes.POINTER(_D)], _I),
+    "ader_ensemble_set_wait_limit": ([_P, _L], _I),
     "ader_enable_timing": ([_P, _I], _I),
     "ader_phase_times": ([_P, _P, ctypes.POINTER(_I)], _I),
 }
@@ -383,9 +384,14 @@ class Ensemble:
 
     def set_launch(self, branches, steps_per_graph, blocks_per_sm=1):
         """branches >= 1: per-run kernels on that many forked streams; 0: one persistent launch per
-        phase for all runs with blocks_per_sm predictor blocks per SM."""
+        phase for all runs with blocks_per_sm predictor blocks per SM; -1: one cooperative
+        persistent launch for all steps of a graph (grid-wide barriers between the phases)."""
         check(lib().ader_ensemble_set_launch(self._h, int(branches), int(steps_per_graph),
                                              int(blocks_per_sm)), "ader_ensemble_set_launch")
+
+    def set_wait_limit(self, polls):
+        """Polls of a grid-barrier wait of the fused launch before it gives up (0: at once)."""
+        check(lib().ader_ensemble_set_wait_limit(self._h, int(polls)), "ader_ensemble_set_wait_limit")
 
     def autotune(self, dt):
         """(branches, steps_per_graph, blocks_per_sm, ms_per_step) of the fastest launch shape."""

@@ -192,6 +192,12 @@ struct Family {
   // numerical fluxes per face node and variable the Riemann kernel writes (2: the left and right
   // cells see different values, a path-conservative fluctuation); sizes the flux buffer
   int nphi;
+  // `steps` steps of every run of an ensemble as one cooperative persistent launch with grid-wide
+  // barriers (bar: device barrier state; limit: polls of a barrier wait before it gives up); null
+  // when the family has no batched path
+  cudaError_t (*ens_fused)(const StepArgs* runs, const EnsTable& E, const Tables& t,
+                           const TablesF& f, int prec, int order, int steps, void* bar,
+                           long long limit, int blocks_per_sm, cudaStream_t s);
 };
 cudaError_t launch_set_scalars(DevScalars* d, double t, double dt, cudaStream_t s);
 cudaError_t launch_merge_status(DevScalars* src, DevScalars* dst, cudaStream_t s);

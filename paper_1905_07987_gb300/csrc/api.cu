@@ -1216,11 +1216,16 @@ struct ader_ensemble {
   double g_dt = 0.0, g_tend = 0.0;
   std::vector<double*> g_u0;
   int branches = 1;                   // chosen by the autotuner (or 1); 0: persistent launches
+                                      // per phase; -1: one fused cooperative launch
   int steps_per_graph = 2;
-  int bps = 1;                        // persistent predictor blocks per SM (branches == 0)
+  int bps = 1;                        // persistent predictor blocks per SM (branches <= 0)
   int g_bps = 0;
   StepArgs* d_runs = nullptr;         // run tables of the captured persistent steps
   size_t d_runs_n = 0;
+  void* d_bar = nullptr;              // grid-barrier state of the fused launch
+  long long wait_limit = 1ll << 24;   // polls of a grid-barrier wait (about 1.7 s with 100 ns
+                                      // sleeps) before it gives up with ADER_ETIMEOUT
+  long long g_limit = -1;
 };
 
 static void ens_free_graph(ader_ensemble* e) {
@@ -1302,7 +1307,7 @@ static bool ens_batchable(const ader_ensemble* e, double dt) {
 // Capture `steps` steps of every run as one persistent launch per phase: the run tables of each
 // step (the runs' step arguments with that step's state buffers) go to device memory first.
 static ader_status ens_capture_persistent(ader_ensemble* e, int steps, double dt, double t_end,
-                                          int bps) {
+                                          int bps, bool fused) {
   ens_free_graph(e);
   const int nr = (int)e->runs.size();
   const size_t need = (size_t)steps * nr;
@@ -1342,11 +1347,17 @@ static ader_status ens_capture_persistent(ader_ensemble* e, int steps, double dt
   }
   cudaStream_t cap = e->branch[0];
   const ader_ctx* a = e->runs[0];
+  if (fused && !e->d_bar) CUDA_OK(cudaMalloc(&e->d_bar, 64));
   CUDA_OK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
   cudaError_t ce = cudaSuccess;
-  for (int k = 0; k < steps && ce == cudaSuccess; ++k)
-    ce = a->fam->ens_step(e->d_runs + (size_t)k * nr, E, a->tab, a->tabf, a->cfg.precision,
-                          a->cfg.order, cap);
+  if (fused) {
+    ce = a->fam->ens_fused(e->d_runs, E, a->tab, a->tabf, a->cfg.precision, a->cfg.order, steps,
+                           e->d_bar, e->wait_limit, bps, cap);
+  } else {
+    for (int k = 0; k < steps && ce == cudaSuccess; ++k)
+      ce = a->fam->ens_step(e->d_runs + (size_t)k * nr, E, a->tab, a->tabf, a->cfg.precision,
+                            a->cfg.order, cap);
+  }
   cudaGraph_t g = nullptr;
   const cudaError_t ee = cudaStreamEndCapture(cap, &g);
   if (ce != cudaSuccess || ee != cudaSuccess) {
@@ -1356,8 +1367,9 @@ static ader_status ens_capture_persistent(ader_ensemble* e, int steps, double dt
   e->graph = g;
   CUDA_OK(cudaGraphInstantiate(&e->gexec, g, 0));
   e->g_steps = steps;
-  e->g_branches = 0;
+  e->g_branches = fused ? -1 : 0;
   e->g_bps = bps;
+  e->g_limit = e->wait_limit;
   e->g_dt = dt;
   e->g_tend = t_end;
   e->g_u0.clear();
@@ -1392,6 +1404,7 @@ void ader_ensemble_destroy(ader_ensemble* e) {
   if (!e) return;
   ens_free_graph(e);
   cudaFree(e->d_runs);
+  cudaFree(e->d_bar);
   for (ader_ctx* c : e->runs) ader_destroy(c);
   for (cudaStream_t s : e->branch) cudaStreamDestroy(s);
   for (cudaEvent_t v : e->ev) cudaEventDestroy(v);
@@ -1414,10 +1427,12 @@ ader_status ader_ensemble_step(ader_ensemble* e, int steps, double dt, double t_
   const int spg = e->steps_per_graph;
   const int ng = steps / spg, rest = steps % spg;
   if (ng > 0) {
-    const bool persistent = e->branches == 0 && ens_batchable(e, dt);
-    const int nb = persistent ? 0 : (e->branches > 0 ? e->branches : 1);
+    const bool fused = e->branches < 0 && ens_batchable(e, dt) && e->runs[0]->fam->ens_fused;
+    const bool persistent = (e->branches == 0 || fused) && ens_batchable(e, dt);
+    const int nb = fused ? -1 : (persistent ? 0 : (e->branches > 0 ? e->branches : 1));
     bool same = e->gexec && e->g_steps == spg && e->g_dt == dt && e->g_tend == t_end &&
-                e->g_branches == nb && (!persistent || e->g_bps == e->bps);
+                e->g_branches == nb && (!persistent || e->g_bps == e->bps) &&
+                (!fused || e->g_limit == e->wait_limit);
     for (size_t r = 0; same && r < e->runs.size(); ++r) same = e->g_u0[r] == e->runs[r]->u;
     if (!same) {
       if (e->branch.empty()) {  // the capture stream and the fork / join event
@@ -1430,7 +1445,7 @@ ader_status ader_ensemble_step(ader_ensemble* e, int steps, double dt, double t_
         CUDA_OK(cudaEventCreateWithFlags(&v, cudaEventDisableTiming));
         e->ev.push_back(v);
       }
-      const ader_status st = persistent ? ens_capture_persistent(e, spg, dt, t_end, e->bps)
+      const ader_status st = persistent ? ens_capture_persistent(e, spg, dt, t_end, e->bps, fused)
                                         : ens_capture(e, spg, dt, t_end, nb);
       if (st != ADER_OK) return st;
     }
@@ -1461,12 +1476,18 @@ ader_status ader_ensemble_sync(ader_ensemble* e) {
 
 ader_status ader_ensemble_set_launch(ader_ensemble* e, int branches, int steps_per_graph,
                                      int blocks_per_sm) {
-  if (!e || branches < 0 || branches > 16 || steps_per_graph < 2 || steps_per_graph % 2)
+  if (!e || branches < -1 || branches > 16 || steps_per_graph < 2 || steps_per_graph % 2)
     return ADER_EINVAL;
-  if (branches == 0 && (blocks_per_sm < 1 || blocks_per_sm > 8)) return ADER_EINVAL;
+  if (branches <= 0 && (blocks_per_sm < 1 || blocks_per_sm > 8)) return ADER_EINVAL;
   e->branches = branches;
   e->steps_per_graph = steps_per_graph;
-  if (branches == 0) e->bps = blocks_per_sm;
+  if (branches <= 0) e->bps = blocks_per_sm;
+  return ADER_OK;
+}
+
+ader_status ader_ensemble_set_wait_limit(ader_ensemble* e, int64_t polls) {
+  if (!e || polls < 0) return ADER_EINVAL;
+  e->wait_limit = polls;
   return ADER_OK;
 }
 
@@ -1490,6 +1511,10 @@ ader_status ader_ensemble_autotune(ader_ensemble* e, double dt, int* best, doubl
   if (ens_batchable(e, dt)) {
     cand.push_back({0, 1});
     cand.push_back({0, 2});
+    if (e->runs[0]->fam->ens_fused) {
+      cand.push_back({-1, 1});
+      cand.push_back({-1, 2});
+    }
   }
   const int cand_s[] = {2, 4};
   cudaEvent_t t0, t1;
@@ -1540,7 +1565,7 @@ ader_status ader_ensemble_autotune(ader_ensemble* e, double dt, int* best, doubl
   if (best) {
     best[0] = bb;
     best[1] = bs;
-    best[2] = bb == 0 ? bp : 0;
+    best[2] = bb <= 0 ? bp : 0;
   }
   if (ms_per_step) *ms_per_step = best_ms;
   return ADER_OK;

@@ -16,4 +16,17 @@ cudaError_t ens_step_elastic3_mixed(const StepArgs* R, const EnsTable& E, const 
   return cudaErrorInvalidValue;
 }
 
+cudaError_t ens_fused_elastic3_mixed(const StepArgs* R, const EnsTable& E, const Tables& T, const TablesF& F, int order,
+               int steps, void* bar, long long limit, int bps, cudaStream_t s) {
+  GridBar* b = static_cast<GridBar*>(bar);
+  switch (order) {
+    case 1: return ens_fused_n<Elastic, 3, 1, true>(R, E, T, F, steps, b, limit, bps, s);
+    case 2: return ens_fused_n<Elastic, 3, 2, true>(R, E, T, F, steps, b, limit, bps, s);
+    case 3: return ens_fused_n<Elastic, 3, 3, true>(R, E, T, F, steps, b, limit, bps, s);
+    case 4: return ens_fused_n<Elastic, 3, 4, true>(R, E, T, F, steps, b, limit, bps, s);
+    case 5: return ens_fused_n<Elastic, 3, 5, true>(R, E, T, F, steps, b, limit, bps, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace ader

@@ -10,6 +10,12 @@ cudaError_t ens_step_elastic3_mixed(const StepArgs* R, const EnsTable& E, const 
                                     const TablesF& F, int order, cudaStream_t s);
 cudaError_t predictor_ck_elastic3(const StepArgs& a, const Tables& t, const TablesF& f, int prec,
                                   cudaStream_t s);
+cudaError_t ens_fused_elastic3_fp64(const StepArgs* R, const EnsTable& E, const Tables& T,
+                                    const TablesF& F, int order, int steps, void* bar,
+                                    long long limit, int bps, cudaStream_t s);
+cudaError_t ens_fused_elastic3_mixed(const StepArgs* R, const EnsTable& E, const Tables& T,
+                                     const TablesF& F, int order, int steps, void* bar,
+                                     long long limit, int bps, cudaStream_t s);
 template <int N>
 cudaError_t adj_run_n(const StepArgs& a, const AdjArgs& j, const Tables& t, int blocks, cudaStream_t s);
 template <int N>
@@ -53,6 +59,13 @@ cudaError_t ens_step(const StepArgs* R, const EnsTable& E, const Tables& T, cons
   return prec == 1 ? ens_step_elastic3_mixed(R, E, T, F, order, s)
                    : ens_step_elastic3_fp64(R, E, T, F, order, s);
 }
+cudaError_t ens_fused(const StepArgs* R, const EnsTable& E, const Tables& T, const TablesF& F,
+                      int prec, int order, int steps, void* bar, long long limit, int bps,
+                      cudaStream_t s) {
+  if (order > 5) return cudaErrorInvalidValue;
+  return prec == 1 ? ens_fused_elastic3_mixed(R, E, T, F, order, steps, bar, limit, bps, s)
+                   : ens_fused_elastic3_fp64(R, E, T, F, order, steps, bar, limit, bps, s);
+}
 }  // namespace
 
 const Family* family_elastic3() {
@@ -63,6 +76,7 @@ const Family* family_elastic3() {
     g.adj_blocks_per_sm = &adj_bps;
     g.ens_step = &ens_step;
     g.predictor_ck = &predictor_ck_elastic3;
+    g.ens_fused = &ens_fused;
     return g;
   }();
   return &f;

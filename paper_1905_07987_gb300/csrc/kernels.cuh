@@ -1078,7 +1078,8 @@ struct FamilyImpl {
   static const Family* get() {
     static const Family f = [] {
       Family g = {P::NV, P::CONS, &cfl,    &predictor, &riemann, &corrector, &smem,
-                  nullptr, nullptr, nullptr, nullptr,   nullptr,  nullptr,    nullptr, 0};
+                  nullptr, nullptr, nullptr, nullptr,   nullptr,  nullptr,    nullptr, 0,
+                  nullptr};
       g.nphi = Cfg<P, D, 1>::NPHI;
       return g;
     }();

@@ -50,10 +50,13 @@ def states(ctxs):
 @pytest.mark.parametrize("branches,spg,bps,prec", [(1, 2, 1, "fp64"), (2, 4, 1, "fp64"),
                                                    (3, 2, 1, "fp64"), (0, 2, 1, "fp64"),
                                                    (0, 4, 2, "fp64"), (0, 2, 1, "mixed"),
-                                                   (0, 4, 3, "mixed")])
+                                                   (0, 4, 3, "mixed"), (-1, 2, 1, "fp64"),
+                                                   (-1, 4, 2, "fp64"), (-1, 2, 1, "mixed"),
+                                                   (-1, 4, 2, "mixed")])
 def test_ensemble_graph_equals_separate_runs(branches, spg, bps, prec):
-    """Every launch shape, including the persistent launches shared by all runs (branches 0),
-    gives each run exactly the result of stepping it on its own."""
+    """Every launch shape, including the persistent launches shared by all runs (branches 0: one
+    per phase; -1: one cooperative launch for all steps of a graph, grid-wide barriers between the
+    phases), gives each run exactly the result of stepping it on its own."""
     sides, order = [3, 5, 4, 2], 2
     ens = ader.Ensemble(member_configs(sides, order, precision=prec))
     singles = [ader.Context(c) for c in member_configs(sides, order, precision=prec)]
@@ -72,7 +75,8 @@ def test_ensemble_graph_equals_separate_runs(branches, spg, bps, prec):
 
 
 @pytest.mark.parametrize("sides,order,launch", [([2, 3], 3, None), ([8, 10, 9], 3, None),
-                                                ([8, 10, 9], 3, (0, 2, 2)), ([12, 8], 4, (0, 2, 1))])
+                                                ([8, 10, 9], 3, (0, 2, 2)), ([12, 8], 4, (0, 2, 1)),
+                                                ([12, 8, 10], 4, (-1, 2, 1))])
 def test_ensemble_members_match_the_oracle(sides, order, launch):
     """Each run of the ensemble against the oracle run on its own grid: the per-run kernels and
     the persistent launches shared by all runs (many blocks per run at sides 8..12)."""
@@ -152,6 +156,35 @@ def test_persistent_launch_order_four_mixed_uneven_sizes():
     ens.sync()
     for c in singles:
         c.run(5, dt=1e-3)
+    for a, b in zip(states(ens.runs), states(singles)):
+        assert np.array_equal(a, b)
+    ens.close()
+
+
+def test_fused_launch_barrier_timeout_is_reported_and_recoverable():
+    """The fused launch's grid-wide barrier waits are bounded: with the limit at 0 polls a wait
+    runs out, every run's status latches ADER_ETIMEOUT and ader_ensemble_sync returns it (no hang,
+    no fault); with the limit restored the ensemble steps correctly again."""
+    sides, order = [4, 5, 3], 2
+    ens = ader.Ensemble(member_configs(sides, order))
+    singles = [ader.Context(c) for c in member_configs(sides, order)]
+    for i, s in enumerate(sides):
+        setup_member(ens.runs[i], s, order, seed=50 + i)
+        setup_member(singles[i], s, order, seed=50 + i)
+    ens.set_launch(-1, 2, 1)
+    ens.set_wait_limit(0)
+    ens.step(2, dt=1e-3)
+    with pytest.raises(ader.AderError) as e:
+        ens.sync()
+    assert e.value.status == ader.ETIMEOUT
+    ens.set_wait_limit(1 << 24)
+    for i, s in enumerate(sides):  # the timed-out launch left the states undefined: set again
+        setup_member(ens.runs[i], s, order, seed=50 + i)
+        ens.runs[i].set_time(0.0)
+    ens.step(4, dt=1e-3)
+    ens.sync()
+    for c in singles:
+        c.run(4, dt=1e-3)
     for a, b in zip(states(ens.runs), states(singles)):
         assert np.array_equal(a, b)
     ens.close()

@@ -184,6 +184,17 @@ def test_hybrid_status_run_matches_the_oracle(ncell, order, steps, box):
     assert rel_linf(c.get(), u.numpy()) <= 1e-11
 
 
+def rel_linf_floored(a, b):
+    """rel_linf with a variable that is zero up to round-off (its largest value below 1e-8 of the
+    state's) measured against the size of the state."""
+    nv = b.shape[-1]
+    a, b = np.asarray(a).reshape(-1, nv), np.asarray(b).reshape(-1, nv)
+    g = np.abs(b).max()
+    scale = np.abs(b).max(axis=0)
+    scale = np.where(scale > 1e-8 * g, scale, g)
+    return float((np.abs(a - b).max(axis=0) / scale).max())
+
+
 def rarefaction_case(floor):
     """rho = 1, p = 0.4, u = -3 / +3 left / right of x = 0 on 8 x 4 cells, order 2, walls, and an
     admissibility floor on density and pressure (Table 2 isPhysicallyAdmissable)."""
@@ -218,8 +229,10 @@ def test_first_order_fallback_matches_the_oracle():
         used.append(lim.last_fallback)
         assert ok
         assert np.array_equal(c.ctx.flags().astype(bool), tr.numpy()), step
-        assert rel_linf(c.get(), u.numpy()) <= TOL, step
-        assert rel_linf(gpu_rep(c, lim), rep.numpy()) <= TOL, step
+        # the y momentum of this flow is zero up to round-off: variable scales are floored at the
+        # size of the state
+        assert rel_linf_floored(c.get(), u.numpy()) <= TOL, step
+        assert rel_linf_floored(gpu_rep(c, lim), rep.numpy()) <= TOL, step
     assert used == [False, False, True]
 
 

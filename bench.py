@@ -634,6 +634,51 @@ def extra_ensemble(ader, synth, stream, steps=4):
                       "per-run kernels on %d forked streams" % best[0]}
 
 
+def extra_ensemble_adjoint(ader, synth, stream, steps=2, k=1):
+    """Batched adjoint of the 16-run ensemble (the ensemble workload's draw of cube sides, order 4,
+    mixed forward, each run with its seeded material, source and 64 top-face receivers): the
+    misfit gradient of every run with respect to per-cell rho, lambda, mu and the moment tensor
+    through ader_ensemble_misfit_gradient.  The source sits three cells below the top-face centre
+    so that the receivers record signal.  A bounded sample: `steps` steps with a checkpoint every
+    `k` (the full 300-step workload takes about an hour at the adjoint's rate)."""
+    import torch
+    sides = synth.ensemble_sides(16)
+    cfgs = [ader.make_config("elastic", 3, 4, (s,) * 3, (0, 0, 0), (0.5 * s,) * 3, "absorbing",
+                             synth.cfl_number(4), precision="mixed") for s in sides]
+    ens = ader.Ensemble(cfgs, stream=stream.cuda_stream)
+    keep, dts = [], []
+    for i, (s, r) in enumerate(zip(sides, ens.runs)):
+        L = 0.5 * s
+        mat = synth.elastic_material((s,) * 3, seed=100 + i)
+        r.set_material(torch.from_numpy(mat.reshape(-1).copy()).cuda())
+        r.set_point_source((0.5 * L, 0.5 * L, L - 1.25), synth.moment_tensor(seed=200 + i), 2.0, 0.5)
+        sm = torch.zeros(steps + 2, 64, 3, dtype=torch.float64, device="cuda")
+        r.set_receivers(synth.receivers_top((s,) * 3, (0, 0, 0), (L,) * 3), sm, steps + 2)
+        keep.append(sm)
+        vpmax = float(np.sqrt((mat[:, 1] + 2 * mat[:, 2]) / mat[:, 0]).max())
+        dts.append(synth.cfl_number(4) / (3 * 9) * 0.5 / vpmax)
+    dt = min(dts)
+    u0 = [torch.zeros(r.count, dtype=torch.float64, device="cuda") for r in ens.runs]
+    rng = np.random.default_rng(3)
+    obs = [torch.from_numpy(1e-4 * rng.standard_normal(steps * 64 * 3)).cuda() for _ in sides]
+    gm = [torch.zeros(r.cells * 3, dtype=torch.float64, device="cuda") for r in ens.runs]
+    gM = [torch.zeros(6, dtype=torch.float64, device="cuda") for r in ens.runs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = ens.misfit_gradient(u0, 0.45, dt, steps, k, obs, gm, gM)
+    el = time.perf_counter() - t0
+    ok = all(bool(torch.isfinite(g).all()) for g in gm + gM)
+    dofs = sum(s ** 3 for s in sides) * 125 * 9
+    ens.close()
+    return {"workload": "ensemble16_adjoint_p4 (batched misfit gradient, bounded sample)",
+            "sides": sides, "dofs": dofs, "steps": steps, "k_ckpt": k,
+            "gradient_s": el, "s_per_gradient_step": el / steps,
+            "value": dofs * steps / el, "unit": "DOF-updates/s (gradient: forward, recomputation "
+            "and adjoint, each step counted once; host wall clock around the synchronising call)",
+            "J_sum": float(sum(J)), "finite": ok, "forward": "mixed", "adjoint": "f64",
+            "full_workload_estimate_s": el / steps * 300}
+
+
 _WORLD = [1]
 
 
@@ -845,7 +890,8 @@ def main():
         extra = {}
         for name, fn in (("euler2d_p3_27", extra_euler2d), ("explosion3d_p3_64", extra_explosion),
                          ("elastic3d_p5_81", extra_elastic), ("ensemble16_elastic_p4", extra_ensemble),
-                         ("adjoint_elastic3d_p4_40", extra_adjoint), ("euler3d_p4_81_cerk", extra_cerk)):
+                         ("adjoint_elastic3d_p4_40", extra_adjoint), ("euler3d_p4_81_cerk", extra_cerk),
+                         ("ensemble16_adjoint_p4", extra_ensemble_adjoint)):
             if args.extras and name not in args.extras.split(","):
                 continue
             try:

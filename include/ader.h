@@ -348,6 +348,24 @@ ader_status ader_ensemble_set_wait_limit(ader_ensemble* ens, int64_t polls);
  * *ms_per_step receives its time per step.  Synchronises. */
 ader_status ader_ensemble_autotune(ader_ensemble* ens, double dt, int* best, double* ms_per_step);
 
+/* Receiver misfit and its gradient for every run of an ensemble (batched adjoint: several
+ * seeded elastic runs on uneven grids, each with its own material, source and receivers), the
+ * runs' forward sweeps, segment recomputations and adjoint sweeps interleaved step by step on
+ * forked streams.  Per run r the call computes what ader_misfit_gradient computes for that
+ * context: u0[r] (device state at t0), obs[r] (device [steps][nrec_r][3]), J[r] (host), and, if
+ * grad_mat / grad_M are non-NULL, grad_mat[r] (device [cells_r][3]) and grad_M[r] (device [6],
+ * overwritten).  The forward steps use each run's own precision (the mixed predictor allowed);
+ * the adjoint is that of the FP64 step at those states.  Runs are processed in groups whose work
+ * memory ((steps/k_ckpt + k_ckpt + 1) states each) fits mem_budget bytes (<= 0: half of the free
+ * device memory; a run that alone exceeds it is processed alone).  Requires material and
+ * receivers on every run (ADER_ESTATE otherwise); the Picard predictor from the constant guess.
+ * Synchronises.  The runs' states afterwards are unspecified. */
+ader_status ader_ensemble_misfit_gradient(ader_ensemble* ens, const double* const* u0, double t0,
+                                          double dt, int steps, int k_ckpt,
+                                          const double* const* obs, double* J,
+                                          double* const* grad_mat, double* const* grad_M,
+                                          int64_t mem_budget);
+
 /* Human-readable name of a status. */
 const char* ader_status_string(ader_status s);
 

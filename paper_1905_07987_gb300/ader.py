@@ -90,6 +90,7 @@ _SIGS = {
     "ader_ensemble_set_launch": ([_P, _I, _I, _I], _I),
     "ader_ensemble_autotune": ([_P, _D, _P, ctypes.POINTER(_D)], _I),
     "ader_ensemble_set_wait_limit": ([_P, _L], _I),
+    "ader_ensemble_misfit_gradient": ([_P, _P, _D, _D, _I, _I, _P, _P, _P, _P, _L], _I),
     "ader_enable_timing": ([_P, _I], _I),
     "ader_phase_times": ([_P, _P, ctypes.POINTER(_I)], _I),
 }
@@ -388,6 +389,28 @@ class Ensemble:
         persistent launch for all steps of a graph (grid-wide barriers between the phases)."""
         check(lib().ader_ensemble_set_launch(self._h, int(branches), int(steps_per_graph),
                                              int(blocks_per_sm)), "ader_ensemble_set_launch")
+
+    def misfit_gradient(self, u0, t0, dt, steps, k_ckpt, obs, grad_mat=None, grad_M=None,
+                        mem_budget=0):
+        """Per-run misfit J (list) and gradients for every run (lists of device tensors; grad
+        lists may be None)."""
+        n = len(self.runs)
+
+        def arr(ts):
+            a = (ctypes.c_void_p * n)()
+            for i, t in enumerate(ts):
+                p, dev, keep, _ = _ptr(t)
+                if not dev:
+                    raise ValueError("ensemble gradient buffers must be device tensors")
+                a[i] = p
+            return a
+        J = (ctypes.c_double * n)()
+        gm = arr(grad_mat) if grad_mat is not None else None
+        gM = arr(grad_M) if grad_M is not None else None
+        check(lib().ader_ensemble_misfit_gradient(self._h, arr(u0), float(t0), float(dt), int(steps),
+                                                  int(k_ckpt), arr(obs), J, gm, gM,
+                                                  int(mem_budget)), "ader_ensemble_misfit_gradient")
+        return list(J)
 
     def set_wait_limit(self, polls):
         """Polls of a grid-barrier wait of the fused launch before it gives up (0: at once)."""

@@ -4,6 +4,7 @@
 #include <cstdlib>
 #include <algorithm>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -1127,6 +1128,117 @@ ader_status ader_receivers_adjoint(ader_ctx* c, const double* res, double scale,
   return ADER_OK;
 }
 
+}  // extern "C"
+
+// Checkpointed gradient of the receiver misfit of one context, split into phases so that the
+// ensemble form can interleave the phases of several runs (each on its own stream).  The
+// single-context entry point runs the same phases in the same order.
+struct MisfitJob {
+  ader_ctx* c = nullptr;
+  const double* u0 = nullptr;
+  const double* obs = nullptr;
+  double t0 = 0.0, dt = 0.0;
+  int steps = 0, k = 1, nseg = 0, nrec = 0;
+  double* gm = nullptr;   // caller's (or work) gradient buffers
+  double* gM = nullptr;
+  bool grads = false;
+  DevBufs B;
+  double *ckpt = nullptr, *seg = nullptr, *lam = nullptr, *seismo = nullptr, *res = nullptr,
+         *Jd = nullptr;
+  Receivers saved{};
+  ader_status st = ADER_OK;
+
+  // device bytes of the work buffers
+  static size_t bytes(const ader_ctx* c, int steps, int k) {
+    const size_t nd = (size_t)c->ndof;
+    const int nseg = (steps + k - 1) / k;
+    return (nd * (nseg + k + 1) + (size_t)steps * c->rec.nrec * 3 + (size_t)c->rec.nrec * 3 +
+            1 + (size_t)c->g.ncells * 3 + 6) * sizeof(double);
+  }
+  ader_status alloc(double* grad_mat, double* grad_M) {
+    const size_t nd = (size_t)c->ndof;
+    nseg = (steps + k - 1) / k;
+    nrec = c->rec.nrec;
+    grads = grad_mat || grad_M;
+    cudaError_t e = B.alloc(&ckpt, nd * nseg);
+    if (e == cudaSuccess) e = B.alloc(&seg, nd * (size_t)k);
+    if (e == cudaSuccess) e = B.alloc(&lam, nd);
+    if (e == cudaSuccess) e = B.alloc(&seismo, (size_t)steps * nrec * 3);
+    if (e == cudaSuccess) e = B.alloc(&res, (size_t)nrec * 3);
+    if (e == cudaSuccess) e = B.alloc(&Jd, 1);
+    gm = grad_mat;
+    gM = grad_M;
+    if (e == cudaSuccess && grads && !gm) e = B.alloc(&gm, (size_t)c->g.ncells * 3);
+    if (e == cudaSuccess && grads && !gM) e = B.alloc(&gM, 6);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? ADER_ENOMEM : ADER_ECUDA;
+    }
+    return ADER_OK;
+  }
+  // ---- forward sweep with a checkpoint every k steps ---------------------------------------
+  ader_status forward_begin() {
+    saved = c->rec;
+    c->rec.seismo = seismo;
+    c->rec.max_rows = steps;
+    long long zero = 0;
+    CUDA_OK(cudaMemcpyAsync(&c->dev->seismo_row, &zero, sizeof(long long), cudaMemcpyHostToDevice,
+                            c->stream));
+    CUDA_OK(cudaMemcpyAsync(c->u, u0, (size_t)c->ndof * sizeof(double), cudaMemcpyDeviceToDevice,
+                            c->stream));
+    c->state_set = true;
+    CUDA_OK(launch_set_scalars(c->dev, t0, dt, c->stream));
+    return ADER_OK;
+  }
+  ader_status forward_step(int n) {
+    const size_t nd = (size_t)c->ndof;
+    if (n % k == 0)
+      CUDA_OK(cudaMemcpyAsync(ckpt + (size_t)(n / k) * nd, c->u, nd * sizeof(double),
+                              cudaMemcpyDeviceToDevice, c->stream));
+    return step_impl(c, dt, 0.0);
+  }
+  ader_status forward_end(double* J) {
+    CUDA_OK(launch_misfit(seismo, obs, (long long)steps * nrec * 3, dt, Jd, c->stream));
+    CUDA_OK(cudaMemcpyAsync(J, Jd, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return ADER_OK;
+  }
+  // ---- backward sweep: recompute each segment from its checkpoint --------------------------
+  ader_status backward_begin() {
+    CUDA_OK(cudaMemsetAsync(gm, 0, (size_t)c->g.ncells * 3 * sizeof(double), c->stream));
+    CUDA_OK(cudaMemsetAsync(gM, 0, 6 * sizeof(double), c->stream));
+    CUDA_OK(cudaMemsetAsync(lam, 0, (size_t)c->ndof * sizeof(double), c->stream));
+    c->rec.nrec = 0;  // no recording while recomputing
+    return ADER_OK;
+  }
+  ader_status recompute_segment(int sg) {
+    const size_t nd = (size_t)c->ndof;
+    const int a = sg * k, b = std::min(a + k, steps);
+    CUDA_OK(cudaMemcpyAsync(c->u, ckpt + (size_t)sg * nd, nd * sizeof(double),
+                            cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_OK(launch_set_scalars(c->dev, t0 + a * dt, dt, c->stream));
+    ader_status r = ADER_OK;
+    for (int i = 0; i < b - a && r == ADER_OK; ++i) {
+      CUDA_OK(cudaMemcpyAsync(seg + (size_t)i * nd, c->u, nd * sizeof(double),
+                              cudaMemcpyDeviceToDevice, c->stream));
+      if (i + 1 < b - a) r = step_impl(c, dt, 0.0);
+    }
+    return r;
+  }
+  // lambda += dt R^T (seismo[n-1] - obs[n-1]); then lambda <- A^T lambda, gradients
+  ader_status adjoint_step(int sg, int n) {
+    const size_t nd = (size_t)c->ndof;
+    const int a = sg * k;
+    CUDA_OK(launch_sub(seismo + (size_t)(n - 1) * nrec * 3, obs + (size_t)(n - 1) * nrec * 3, res,
+                       nrec * 3, c->stream));
+    CUDA_OK(launch_receivers_adjoint(saved, res, dt, lam, (int)c->nodes, (int)c->nvar, c->stream));
+    return ader_adjoint_step(c, t0 + (n - 1) * dt, dt, seg + (size_t)(n - 1 - a) * nd, lam, nullptr,
+                             gm, gM);
+  }
+  void restore() { c->rec = saved; }
+};
+
+extern "C" {
+
 ader_status ader_misfit_gradient(ader_ctx* c, const double* u0, double t0, double dt, int steps,
                                  int k_ckpt, const double* obs, double* J, double* grad_mat,
                                  double* grad_M) {
@@ -1135,68 +1247,28 @@ ader_status ader_misfit_gradient(ader_ctx* c, const double* u0, double t0, doubl
   if (c->cfg.predictor != ADER_PREDICTOR_PICARD || c->cfg.initial_guess != ADER_GUESS_CONSTANT)
     return ADER_EUNSUPPORTED;
   if (!c->mat_set || c->rec.nrec <= 0) return ADER_ESTATE;
-  const size_t nd = (size_t)c->ndof;
-  const int nrec = c->rec.nrec;
-  const int nseg = (steps + k_ckpt - 1) / k_ckpt;
-  DevBufs B;
-  double *ckpt, *seg, *lam, *seismo, *res, *Jd;
-  cudaError_t e = B.alloc(&ckpt, nd * nseg);
-  if (e == cudaSuccess) e = B.alloc(&seg, nd * (size_t)k_ckpt);
-  if (e == cudaSuccess) e = B.alloc(&lam, nd);
-  if (e == cudaSuccess) e = B.alloc(&seismo, (size_t)steps * nrec * 3);
-  if (e == cudaSuccess) e = B.alloc(&res, (size_t)nrec * 3);
-  if (e == cudaSuccess) e = B.alloc(&Jd, 1);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return e == cudaErrorMemoryAllocation ? ADER_ENOMEM : ADER_ECUDA;
-  }
-  const Receivers saved = c->rec;
-  ader_status st = ADER_OK;
-  // ---- forward sweep with a checkpoint every k steps -------------------------------------
-  c->rec.seismo = seismo;
-  c->rec.max_rows = steps;
-  long long zero = 0;
-  CUDA_OK(cudaMemcpyAsync(&c->dev->seismo_row, &zero, sizeof(long long), cudaMemcpyHostToDevice, c->stream));
-  CUDA_OK(cudaMemcpyAsync(c->u, u0, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-  c->state_set = true;
-  CUDA_OK(launch_set_scalars(c->dev, t0, dt, c->stream));
-  for (int n = 0; n < steps && st == ADER_OK; ++n) {
-    if (n % k_ckpt == 0)
-      CUDA_OK(cudaMemcpyAsync(ckpt + (size_t)(n / k_ckpt) * nd, c->u, nd * sizeof(double),
-                              cudaMemcpyDeviceToDevice, c->stream));
-    st = step_impl(c, dt, 0.0);
-  }
-  if (st == ADER_OK) {
-    CUDA_OK(launch_misfit(seismo, obs, (long long)steps * nrec * 3, dt, Jd, c->stream));
-    CUDA_OK(cudaMemcpyAsync(J, Jd, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  }
-  // ---- backward sweep: recompute each segment from its checkpoint ------------------------
-  if (st == ADER_OK && (grad_mat || grad_M)) {
-    double *gm = grad_mat, *gM = grad_M;
-    if (!gm && (e = B.alloc(&gm, (size_t)c->g.ncells * 3)) != cudaSuccess) return ADER_ENOMEM;
-    if (!gM && (e = B.alloc(&gM, 6)) != cudaSuccess) return ADER_ENOMEM;
-    CUDA_OK(cudaMemsetAsync(gm, 0, (size_t)c->g.ncells * 3 * sizeof(double), c->stream));
-    CUDA_OK(cudaMemsetAsync(gM, 0, 6 * sizeof(double), c->stream));
-    CUDA_OK(cudaMemsetAsync(lam, 0, nd * sizeof(double), c->stream));
-    c->rec.nrec = 0;  // no recording while recomputing
-    for (int sg = nseg - 1; sg >= 0 && st == ADER_OK; --sg) {
-      const int a = sg * k_ckpt, b = std::min(a + k_ckpt, steps);
-      CUDA_OK(cudaMemcpyAsync(c->u, ckpt + (size_t)sg * nd, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-      CUDA_OK(launch_set_scalars(c->dev, t0 + a * dt, dt, c->stream));
-      for (int i = 0; i < b - a && st == ADER_OK; ++i) {
-        CUDA_OK(cudaMemcpyAsync(seg + (size_t)i * nd, c->u, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-        if (i + 1 < b - a) st = step_impl(c, dt, 0.0);
-      }
-      for (int n = b; n > a && st == ADER_OK; --n) {
-        // lambda += dt R^T (seismo[n-1] - obs[n-1]);  then lambda <- A^T lambda, gradients
-        CUDA_OK(launch_sub(seismo + (size_t)(n - 1) * nrec * 3, obs + (size_t)(n - 1) * nrec * 3, res,
-                           nrec * 3, c->stream));
-        CUDA_OK(launch_receivers_adjoint(saved, res, dt, lam, (int)c->nodes, (int)c->nvar, c->stream));
-        st = ader_adjoint_step(c, t0 + (n - 1) * dt, dt, seg + (size_t)(n - 1 - a) * nd, lam, nullptr, gm, gM);
-      }
+  MisfitJob j;
+  j.c = c;
+  j.u0 = u0;
+  j.obs = obs;
+  j.t0 = t0;
+  j.dt = dt;
+  j.steps = steps;
+  j.k = k_ckpt;
+  ader_status st = j.alloc(grad_mat, grad_M);
+  if (st != ADER_OK) return st;
+  st = j.forward_begin();
+  for (int n = 0; n < steps && st == ADER_OK; ++n) st = j.forward_step(n);
+  if (st == ADER_OK) st = j.forward_end(J);
+  if (st == ADER_OK && j.grads) {
+    st = j.backward_begin();
+    for (int sg = j.nseg - 1; sg >= 0 && st == ADER_OK; --sg) {
+      st = j.recompute_segment(sg);
+      const int a = sg * j.k, b = std::min(a + j.k, steps);
+      for (int n = b; n > a && st == ADER_OK; --n) st = j.adjoint_step(sg, n);
     }
   }
-  c->rec = saved;
+  j.restore();
   CUDA_OK(cudaStreamSynchronize(c->stream));
   if (st != ADER_OK) return st;
   return ader_sync(c);
@@ -1569,6 +1641,107 @@ ader_status ader_ensemble_autotune(ader_ensemble* e, double dt, int* best, doubl
   }
   if (ms_per_step) *ms_per_step = best_ms;
   return ADER_OK;
+}
+
+ader_status ader_ensemble_misfit_gradient(ader_ensemble* e, const double* const* u0, double t0,
+                                          double dt, int steps, int k_ckpt,
+                                          const double* const* obs, double* J,
+                                          double* const* grad_mat, double* const* grad_M,
+                                          int64_t mem_budget) {
+  if (!e || !u0 || !obs || !J || steps < 1 || k_ckpt < 1 || !(dt > 0.0)) return ADER_EINVAL;
+  const int nr = (int)e->runs.size();
+  for (int r = 0; r < nr; ++r) {
+    const ader_ctx* c = e->runs[r];
+    if (!u0[r] || !obs[r]) return ADER_EINVAL;
+    if (c->cfg.pde != ADER_PDE_ELASTIC) return ADER_EUNSUPPORTED;
+    if (c->cfg.predictor != ADER_PREDICTOR_PICARD || c->cfg.initial_guess != ADER_GUESS_CONSTANT)
+      return ADER_EUNSUPPORTED;
+    if (!c->mat_set || c->rec.nrec <= 0 || c->timing) return ADER_ESTATE;
+  }
+  size_t budget = (size_t)(mem_budget > 0 ? mem_budget : 0);
+  if (!budget) {
+    size_t fr = 0, tot = 0;
+    CUDA_OK(cudaMemGetInfo(&fr, &tot));
+    budget = fr / 2;
+  }
+  // forked streams: the runs of a group work concurrently, each on its own stream
+  const int nb = std::min(nr, 16);
+  while ((int)e->branch.size() < nb) {
+    cudaStream_t bs;
+    CUDA_OK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+    e->branch.push_back(bs);
+  }
+  while (e->ev.size() < (size_t)(nb + 1)) {
+    cudaEvent_t v;
+    CUDA_OK(cudaEventCreateWithFlags(&v, cudaEventDisableTiming));
+    e->ev.push_back(v);
+  }
+  CUDA_OK(cudaEventRecord(e->ev[0], e->stream));
+  for (int b = 0; b < nb; ++b) CUDA_OK(cudaStreamWaitEvent(e->branch[b], e->ev[0], 0));
+  std::vector<cudaStream_t> saved(nr);
+  for (int r = 0; r < nr; ++r) saved[r] = e->runs[r]->stream;
+  ader_status st = ADER_OK;
+  for (int g0 = 0; g0 < nr && st == ADER_OK;) {
+    // the next group: as many runs as fit the budget (at least one)
+    int g1 = g0;
+    size_t used = 0;
+    while (g1 < nr) {
+      const size_t b = MisfitJob::bytes(e->runs[g1], steps, k_ckpt);
+      if (g1 > g0 && used + b > budget) break;
+      used += b;
+      ++g1;
+    }
+    std::vector<std::unique_ptr<MisfitJob>> jobs;
+    for (int r = g0; r < g1 && st == ADER_OK; ++r) {
+      ader_ctx* c = e->runs[r];
+      c->stream = e->branch[(r - g0) % nb];
+      auto j = std::make_unique<MisfitJob>();
+      j->c = c;
+      j->u0 = u0[r];
+      j->obs = obs[r];
+      j->t0 = t0;
+      j->dt = dt;
+      j->steps = steps;
+      j->k = k_ckpt;
+      st = j->alloc(grad_mat ? grad_mat[r] : nullptr, grad_M ? grad_M[r] : nullptr);
+      jobs.push_back(std::move(j));
+    }
+    // the phases of every run of the group, interleaved step by step
+    for (auto& j : jobs)
+      if (st == ADER_OK) st = j->forward_begin();
+    for (int n = 0; n < steps && st == ADER_OK; ++n)
+      for (auto& j : jobs)
+        if (st == ADER_OK) st = j->forward_step(n);
+    for (int r = g0; r < g1 && st == ADER_OK; ++r) st = jobs[r - g0]->forward_end(J + r);
+    if (st == ADER_OK && jobs[0]->grads) {
+      for (auto& j : jobs)
+        if (st == ADER_OK) st = j->backward_begin();
+      const int nseg = jobs[0]->nseg;
+      for (int sg = nseg - 1; sg >= 0 && st == ADER_OK; --sg) {
+        for (auto& j : jobs)
+          if (st == ADER_OK) st = j->recompute_segment(sg);
+        const int a = sg * k_ckpt, b = std::min(a + k_ckpt, steps);
+        for (int n = b; n > a && st == ADER_OK; --n)
+          for (auto& j : jobs)
+            if (st == ADER_OK) st = j->adjoint_step(sg, n);
+      }
+    }
+    for (auto& j : jobs) {
+      j->restore();
+      cudaStreamSynchronize(j->c->stream);
+    }
+    jobs.clear();  // frees the group's work buffers
+    g0 = g1;
+  }
+  for (int r = 0; r < nr; ++r) e->runs[r]->stream = saved[r];
+  // join the forked streams into the ensemble stream
+  for (int b = 0; b < nb; ++b) {
+    CUDA_OK(cudaEventRecord(e->ev[1 + b], e->branch[b]));
+    CUDA_OK(cudaStreamWaitEvent(e->stream, e->ev[1 + b], 0));
+  }
+  CUDA_OK(cudaStreamSynchronize(e->stream));
+  if (st != ADER_OK) return st;
+  return ader_ensemble_sync(e);
 }
 
 ader_status ader_enable_timing(ader_ctx* c, int on) {

@@ -613,6 +613,21 @@ def extra_ensemble(ader, synth, stream, steps=4):
         vpmax = float(np.sqrt((mat[:, 1] + 2 * mat[:, 2]) / mat[:, 0]).max())
         dts.append(synth.cfl_number(4) / (3 * 9) * 0.5 / vpmax)
     dt = min(dts)  # one fixed dt for the ensemble (as for the adjoint runs)
+    # the launch shapes the autotuner chooses between, each timed here too: per-run kernels on
+    # forked streams, one persistent launch per phase, one cooperative launch for whole steps
+    shapes = {}
+    for name, shape in (("per_run_4_branches", (4, 4, 1)), ("persistent_per_phase", (0, 4, 2)),
+                        ("fused_cooperative", (-1, 4, 2))):
+        ens.set_launch(*shape)
+        ens.step(4, dt=dt)
+        ens.sync()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        ens.step(4, dt=dt)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ens.sync()
+        shapes[name] = f0.elapsed_time(f1) / 4
     best = ens.autotune(dt)
     ens.step(2, dt=dt)
     ens.sync()
@@ -630,8 +645,10 @@ def extra_ensemble(ader, synth, stream, steps=4):
             "dtype": "f32+f64", "autotuned": {"branches": best[0], "steps_per_graph": best[1],
                                               "persistent_blocks_per_sm": best[2],
                                               "ms_per_step_at_tuning": best[3]},
-            "launch": "persistent launches shared by all runs" if best[0] == 0 else
-                      "per-run kernels on %d forked streams" % best[0]}
+            "launch": {0: "persistent launches shared by all runs, one per phase",
+                       -1: "one cooperative persistent launch for whole steps"}.get(
+                           best[0], "per-run kernels on %d forked streams" % best[0]),
+            "ms_per_step_by_launch_shape": shapes}
 
 
 def extra_ensemble_adjoint(ader, synth, stream, steps=2, k=1):

@@ -56,7 +56,9 @@ struct CfgCKT {
 };
 
 // Offset (floats) of element (row r, k) in a K-major line matrix with K = 8: core matrices of 8
-// rows x 4 floats, 2 along K per group of 8 rows (group stride 256 bytes).
+// rows x 4 floats, 2 along K per group of 8 rows (group stride 256 bytes).  Lines of direction d
+// are rows d * per * NF + q * NF + f (variable slot q, transverse node f fastest), so that the
+// nodes of a warp, which differ in f, store into different row slots (fewer bank conflicts).
 __device__ __forceinline__ int kmaj_off(int r, int k) {
   return (r >> 3) * 64 + (k >> 2) * 32 + (r & 7) * 4 + (k & 3);
 }
@@ -170,8 +172,8 @@ __global__ void __launch_bounds__(256, 2)
   for (int d = 0; d < 3; ++d) {
     int jd;
     const int jp = face_node<n>(j, d, jd);
-    rbl[d] = d * 6 * NF + jp * 6;
-    rbo[d] = d * 3 * NF + jp * 3;
+    rbl[d] = d * 6 * NF + jp;   // + q NF
+    rbo[d] = d * 3 * NF + jp;   // + q NF
     kt[d] = (jd >> 2) * 32 + (jd & 3);
   }
   // loop-invariant rows of the line owner (tiles t = warp / 4 + 2 i): the first node of the line
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(256, 2)
     lrow_st[i] = 0;
     if (r < C::ROWS_L) {
       const int d = r / (6 * NF), rr = r - d * 6 * NF;
-      const int f = rr / 6, q = rr - f * 6;
+      const int q = rr / NF, f = rr - q * NF;
       const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
       lrow_dv[i] = ((f % st) + (f / st) * st * n) * C::DVS + d * 6 + q;
       lrow_st[i] = st * C::DVS;
@@ -259,13 +261,11 @@ __global__ void __launch_bounds__(256, 2)
     for (int d = 0; d < 3; ++d)
 #pragma unroll
       for (int i = 0; i < 4; ++i) cf[d][i] = s_cf[d][i];
-    double u[NV];
     float a[NV], qb[NV];
     if (node_owner) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        u[v] = ST[j * NV + v];
-        a[v] = ff_split_int(u[v]).h;  // leading 24 bits, on the integer pipe
+        a[v] = ff_split_int(ST[j * NV + v]).h;  // leading 24 bits, on the integer pipe
         qb[v] = a[v];
       }
     }
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(256, 2)
           if (oth) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-              const int r = rbo[d] + q;
+              const int r = rbo[d] + q * NF;
               const int o = (r >> 3) * 64 + (r & 7) * 4 + kt[d];
               const float xv = x[ck_other(d, q)];
               const float h = tc::to_tf32(xv);
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(256, 2)
           } else {
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
-              const int r = rbl[d] + q;
+              const int r = rbl[d] + q * NF;
               const int o = (r >> 3) * 64 + (r & 7) * 4 + kt[d];
               const float xv = x[ck_need(d, q)];
               const float h = tc::to_tf32(xv);
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(256, 2)
           }
           if (r < (oth ? C::ROWS_O : C::ROWS_L)) {
             const int d = r / (per * NF), rr = r - d * per * NF;
-            const int f = rr / per, q = rr - f * per;
+            const int q = rr / NF, f = rr - q * NF;
             if (vol || oth) {
               const int v = oth ? ck_other(d, q) : ck_need(d, q);
               double* fc = A.face + c * (3 * 2 * FR) + (d * 2) * FR + f * NV + v;
@@ -411,13 +411,14 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
             for (int v = 3; v < NV; ++v) R[v] = fmaf(g[v - 3], s_sk[n], R[v]);
           }
+          // u^n again from this cell's buffer (the prefetch writes the other one)
           double* un = A.u_next + c * NL + j * NV;
 #pragma unroll
-          for (int v = 0; v < NV; ++v) un[v] = fma(dt, f2d_int(R[v]), u[v]);
+          for (int v = 0; v < NV; ++v) un[v] = fma(dt, f2d_int(R[v]), ST[j * NV + v]);
         }
       }
-      // the next application's staging overwrites lines read in (3) only after this barrier
-      __syncthreads();
+      // no barrier here: the next staging writes only the line matrices (their MMAs are done),
+      // and its barrier orders this step's reads of Dv before the next scatter into it
     }
     if (failed) break;
   }
@@ -458,9 +459,12 @@ cudaError_t launch_predictor_ck_tc_n(const StepArgs& a, const Tables& t, cudaStr
     int nb = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_predictor_ck_tc<N>, C::TPB, C::SMEM);
     if (e != cudaSuccess) return e;
-    // tensor memory: every resident block holds TCOLS of the SM's 512 columns
+    // tensor memory: every resident block holds TCOLS of the SM's 512 columns.  Two blocks per
+    // SM are launched even where the occupancy query reports one: the blocks never wait for each
+    // other, so extra blocks that are not resident simply start later
     const int cap = 512 / C::TCOLS;
-    blocks_per_sm = nb < 1 ? 1 : (nb > cap ? cap : nb);
+    blocks_per_sm = nb < 2 ? 2 : nb;
+    if (blocks_per_sm > cap) blocks_per_sm = cap;
   }
   EncodeTiledFn enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;

@@ -41,7 +41,7 @@ struct CfgCKT {
   static constexpr int TILES_O = (ROWS_O + 127) / 128;
   static constexpr int TCOLS_RAW = TILES_L * 16;
   static constexpr int TCOLS = TCOLS_RAW <= 32 ? 32 : (TCOLS_RAW <= 64 ? 64 : (TCOLS_RAW <= 128 ? 128 : 256));
-  static constexpr int DVS = 20;                        // derivative slots per node (18 used)
+  static constexpr int DVS = 18;                        // derivative slots per node
   // shared memory: A hi | A lo (TILES_L x 4 KB each) | B hi | B lo (1 KB each) | state x 2 | Dv
   static constexpr size_t OFF_AH = 0;
   static constexpr size_t OFF_AL = OFF_AH + (size_t)TILES_L * 4096;
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256, 2)
   float* AL = reinterpret_cast<float*>(sm + C::OFF_AL);
   float* BH = reinterpret_cast<float*>(sm + C::OFF_BH);
   float* BL = reinterpret_cast<float*>(sm + C::OFF_BL);
-  float* Dv = reinterpret_cast<float*>(sm + C::OFF_DV);
+  float* Dv = reinterpret_cast<float*>(sm + C::OFF_DV);  // [18][NS] derivatives at the nodes
   __shared__ __align__(8) uint64_t bar_tma[2], bar_mma;
   __shared__ uint32_t s_tmem;
   __shared__ float s_cf[3][4];   // {1/(rho h_d), (lam + 2 mu)/h_d, lam/h_d, mu/h_d}
@@ -167,13 +167,12 @@ __global__ void __launch_bounds__(256, 2)
   const int j = node_owner ? tid : 0;
   // loop-invariant staging positions of the owned node: first line row of each direction (six-
   // and three-variable line sets) and the K part of the offset (position along the direction)
-  int rbl[3], rbo[3], kt[3];
+  int rbl[3], kt[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     int jd;
     const int jp = face_node<n>(j, d, jd);
-    rbl[d] = d * 6 * NF + jp;   // + q NF
-    rbo[d] = d * 3 * NF + jp;   // + q NF
+    rbl[d] = d * 6 * NF + jp;   // + q NF; the three-variable rows: rbl[d] - d 3 NF + q NF
     kt[d] = (jd >> 2) * 32 + (jd & 3);
   }
   // loop-invariant rows of the line owner (tiles t = warp / 4 + 2 i): the first node of the line
@@ -189,8 +188,9 @@ __global__ void __launch_bounds__(256, 2)
       const int d = r / (6 * NF), rr = r - d * 6 * NF;
       const int q = rr / NF, f = rr - q * NF;
       const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
-      lrow_dv[i] = ((f % st) + (f / st) * st * n) * C::DVS + d * 6 + q;
-      lrow_st[i] = st * C::DVS;
+      // Dv is slot-major ([slot][node], node fastest): the lines of a warp store to nearby nodes
+      lrow_dv[i] = (d * 6 + q) * NS + (f % st) + (f / st) * st * n;
+      lrow_st[i] = st;
     }
   }
 
@@ -256,11 +256,6 @@ __global__ void __launch_bounds__(256, 2)
       failed = true;
       break;
     }
-    float cf[3][4];
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) cf[d][i] = s_cf[d][i];
     float a[NV], qb[NV];
     if (node_owner) {
 #pragma unroll
@@ -283,7 +278,7 @@ __global__ void __launch_bounds__(256, 2)
           if (oth) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-              const int r = rbo[d] + q * NF;
+              const int r = rbl[d] - d * 3 * NF + q * NF;
               const int o = (r >> 3) * 64 + (r & 7) * 4 + kt[d];
               const float xv = x[ck_other(d, q)];
               const float h = tc::to_tf32(xv);
@@ -369,29 +364,23 @@ __global__ void __launch_bounds__(256, 2)
         float R[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) R[v] = 0.f;
-        const float4* dp = reinterpret_cast<const float4*>(Dv + j * C::DVS);
-        float dd[20];
+        float dd[18];
 #pragma unroll
-        for (int i = 0; i < 5; ++i) {
-          const float4 w = dp[i];
-          dd[4 * i] = w.x;
-          dd[4 * i + 1] = w.y;
-          dd[4 * i + 2] = w.z;
-          dd[4 * i + 3] = w.w;
-        }
+        for (int i = 0; i < 18; ++i) dd[i] = Dv[i * NS + j];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           const float* dv = dd + d * 6;      // d/dx_d of v_0, v_1, v_2
           const float* ds = dd + d * 6 + 3;  // d/dx_d of sigma_{0d}, sigma_{1d}, sigma_{2d}
-          R[0] = fmaf(cf[d][0], ds[0], R[0]);
-          R[1] = fmaf(cf[d][0], ds[1], R[1]);
-          R[2] = fmaf(cf[d][0], ds[2], R[2]);
+          const float c0 = s_cf[d][0], c1 = s_cf[d][1], c2 = s_cf[d][2], c3 = s_cf[d][3];
+          R[0] = fmaf(c0, ds[0], R[0]);
+          R[1] = fmaf(c0, ds[1], R[1]);
+          R[2] = fmaf(c0, ds[2], R[2]);
 #pragma unroll
-          for (int i = 0; i < 3; ++i) R[3 + i] = fmaf(i == d ? cf[d][1] : cf[d][2], dv[d], R[3 + i]);
+          for (int i = 0; i < 3; ++i) R[3 + i] = fmaf(i == d ? c1 : c2, dv[d], R[3 + i]);
 #pragma unroll
           for (int v = 6; v < 9; ++v) {
             const int s = Elastic::src(d, v);
-            if (s >= 0) R[v] = fmaf(cf[d][3], dv[s], R[v]);
+            if (s >= 0) R[v] = fmaf(c3, dv[s], R[v]);
           }
         }
         if (!vol) {

@@ -38,9 +38,11 @@ FP64_SMS, FP64_FMA_PER_CLK, SM_MAX_MHZ = 152, 2, 2070.0
 # DRAM bytes (read + write) per cell of the predictor kernels, from one ncu capture of the same
 # kernels on 40^3 cells, scaled to a launch by the number of cells (the traffic is per cell:
 # state in, next state and face records out; the mixed form also writes the face wave speeds).
-# FP64: k_predictor<Euler<3>,3,4> on 64 000 cells, read 331.102464 MB, write 1031.607040 MB.
+# FP64: k_predictor<Euler<3>,3,4> on 64 000 cells, read 331.102464 MB, write 1031.607040 MB;
+# mixed (the kernel with the continuous extension Runge-Kutta stages, captured with that guess):
+# read 320.445184 MB, write 1103.791872 MB.
 TRAFFIC_PER_CELL = {"fp64": (331.102464e6 + 1031.607040e6) / 64000,
-                    "mixed": 320.210944e6 / 64000 + 1104.078592e6 / 64000}
+                    "mixed": (320.445184e6 + 1103.791872e6) / 64000}
 FP64_PEAK = FP64_SMS * FP64_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6  # FLOP/s
 
 

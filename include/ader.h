@@ -167,11 +167,14 @@ ader_status ader_reference_nodes(int order, double* x, double* w);
  * ADER_EINVAL for an order outside 1..6. */
 ader_status ader_reference_tables(int order, double* D, double* Kw, double* Vi);
 
-/* Number of cells, nodes per cell (n^dim) and variables of the context. */
+/* Number of cells, nodes per cell (n^dim: the tensor-product Gauss-Legendre nodes of the nodal DG
+ * basis of Sec. 3.3) and variables of the context (the components of Q in Eq. (1)). */
 ader_status ader_sizes(const ader_ctx* ctx, int64_t* cells, int64_t* nodes_per_cell, int* nvar);
 
-/* Copy the state in / out; `count` must equal cells * nodes_per_cell * nvar.  Setting the
- * state also resets the limiter history (no cell troubled at the previous step). */
+/* Copy the state in / out: the nodal values of the DG solution u_h of Sec. 3.3 (the unknowns the
+ * corrector Eq. (6) updates), [cells][nodes][nvar]; `count` must equal
+ * cells * nodes_per_cell * nvar.  Setting the state also resets the limiter history of Sec. 3.5
+ * (no cell troubled at the previous step). */
 ader_status ader_set_state(ader_ctx* ctx, const double* q, int64_t count, int on_device);
 ader_status ader_get_state(ader_ctx* ctx, double* q, int64_t count, int on_device);
 
@@ -227,10 +230,15 @@ ader_status ader_get_subcell_state(ader_ctx* ctx, double* U_sub, int on_device);
 ader_status ader_get_flags(ader_ctx* ctx, uint8_t* flags, int on_device);
 ader_status ader_troubled_count(ader_ctx* ctx, int64_t* count);
 
-/* Synchronise the stream and return (then clear) the latched device status. */
+/* Synchronise the stream and return (then clear) the latched device status: a non-finite state
+ * or time step (ADER_ENONFINITE, found by the CFL reduction of Eq. (7) or the adjoint), an
+ * inadmissible FV recompute (ADER_EADMISSIBLE, Sec. 3.5), a bounded device wait that gave up
+ * (ADER_ETIMEOUT), a full seismogram buffer (ADER_EINVAL). */
 ader_status ader_sync(ader_ctx* ctx);
 
-/* Capture `steps` calls of ader_step(dt, t_end) into a CUDA graph and replay it `replays` times
+/* Global time stepping (Sec. 4: every cell advances with the same dt of Eq. (7)) without host
+ * round trips: capture `steps` calls of ader_step(dt, t_end) into a CUDA graph and replay it
+ * `replays` times
  * (steps * replays steps in total); the graph is kept and reused while (steps, dt, t_end) stay
  * the same.  Does not synchronise. */
 ader_status ader_run_graph(ader_ctx* ctx, int steps, int replays, double dt, double t_end);

@@ -242,6 +242,51 @@ def density_error(ctx, wl, t, nodes, weights):
     return l2, float(err.abs().max())
 
 
+def density_l2_quadrature(ctx, wl, t, nodes, device="cuda"):
+    """L2 error of the density against the exact entropy wave at time t with (N+2)-point
+    Gauss-Legendre quadrature per cell and dimension (the nodal values interpolated there with
+    the Lagrange basis of the solution nodes), on the GPU with plain torch ops.  Quadrature off
+    the solution nodes avoids their superconvergence, so refinement shows the order N+1 of the
+    scheme."""
+    import torch
+    D, N = wl["dim"], wl["order"]
+    n, q = N + 1, N + 2
+    xg, wg = np.polynomial.legendre.leggauss(q)
+    xq, wq = (xg + 1.0) / 2.0, wg / 2.0
+    V = np.ones((q, n))
+    for a in range(n):
+        for b in range(n):
+            if b != a:
+                V[:, a] *= (xq - nodes[b]) / (nodes[a] - nodes[b])
+    st = torch.empty(ctx.count, dtype=torch.float64, device=device)
+    ctx.get_state(st)
+    if device == "cuda":
+        torch.cuda.synchronize()
+    nc, lo, hi = wl["ncell"], wl["lo"], wl["hi"]
+    # node index j = a_0 + n a_1 + ...; cell index c = i_0 + nc_0 i_1 + ... (x fastest)
+    rho = st.view(ctx.cells, n ** D, D + 2)[:, :, 0].reshape((ctx.cells,) + (n,) * D)
+    Vt = torch.tensor(V, device=device)
+    for ax in range(1, D + 1):
+        rho = torch.movedim(torch.tensordot(rho, Vt, dims=([ax], [1])), -1, ax)
+    c = torch.arange(ctx.cells, device=device)
+    s = torch.zeros((ctx.cells,) + (q,) * D, dtype=torch.float64, device=device)
+    W = torch.ones((q,) * D, dtype=torch.float64, device=device)
+    xqt = torch.tensor(xq, device=device)
+    wqt = torch.tensor(wq, device=device)
+    vol = 1.0
+    for d in range(D):
+        h = (hi[d] - lo[d]) / nc[d]
+        vol *= h
+        ic = (c // math.prod(nc[:d])) % nc[d]
+        shape = [1] * D
+        shape[D - 1 - d] = q  # dimension d is tensor axis D-1-d (x is the last axis)
+        s = s + (lo[d] + h * (ic.double().view((-1,) + (1,) * D) + xqt.view(shape)))
+        W = W * wqt.view(shape)
+    ex = 1.0 + 0.2 * torch.sin(2 * math.pi * (s - D * t))
+    err = rho - ex
+    return math.sqrt(float((err * err * W).sum()) * vol)
+
+
 # Forms of the headline workload: (precision, initial guess of the Picard predictor, iterations;
 # 0 = N+1).  The continuous extension Runge-Kutta guess (Sec. 5) is followed by max(1, N-3)
 # iterations (order 4: one).
@@ -290,7 +335,8 @@ def run_form(ader, synth, wl, form, args, stream, u0_dev, err_steps):
         x, w = ader.reference_nodes(N)
         t = ctx.time()
         l2, linf = density_error(ctx, wl, t, x, w)
-        err = {"steps": max(done, err_steps), "t": t, "l2_rho": l2, "linf_rho": linf}
+        err = {"steps": max(done, err_steps), "t": t, "l2_rho": l2, "linf_rho": linf,
+               "l2_rho_quadrature": density_l2_quadrature(ctx, wl, t, x)}
     return ctx, ms_total, phases, nrec, clocks, err
 
 
@@ -459,6 +505,56 @@ def extra_cerk(ader, synth, stream, steps=2, warmup=1, err_steps=20):
         out[name]["predictor_frac_of_fp64_peak"] = tf * 1e12 / FP64_PEAK
     out["cerk_speedup"] = out["constant_5"]["ms_per_step"] / out["cerk_1"]["ms_per_step"]
     out["cerk_over_constant_l2_error"] = out["cerk_1"]["l2_rho"] / out["constant_5"]["l2_rho"]
+    return out
+
+
+def extra_convergence(ader, synth, stream, res, sides=(27, 54)):
+    """The 3-D order-4 entropy wave on coarser grids of the same domain, run with the same
+    forms to the time the 81^3 forms reached after their error steps (the last step clipped to
+    it); L2 density errors (quadrature off the nodes) at 27^3 / 54^3 / 81^3 and the observed
+    orders between them (the scheme's is N+1 = 5)."""
+    import torch
+    base = WORKLOADS["euler3d_p4_81"]
+    D, N = base["dim"], base["order"]
+    x, _ = ader.reference_nodes(N)
+    out = {"workload": "euler3d_p4 entropy wave at %s cells per side" % "/".join(
+        str(v) for v in tuple(sides) + (base["ncell"][0],))}
+    for form in ("fp64", "mixed_cerk"):
+        if form not in res or not res[form]["err"]:
+            continue
+        T = res[form]["err"]["t"]
+        errs, steps = [], []
+        prec, guess, iters = FORMS[form]
+        for n in sides:
+            wl = dict(base, ncell=(n,) * 3)
+            cfg = ader.make_config(wl["pde"], D, N, wl["ncell"], wl["lo"], wl["hi"], wl["bc"],
+                                   synth.cfl_number(N), precision=prec, initial_guess=guess,
+                                   picard_iters=iters)
+            ctx = ader.Context(cfg, stream=stream.cuda_stream)
+            ctx.set_state(torch.from_numpy(build_initial(ader, synth, wl)).to("cuda"))
+            ctx.set_time(0.0)
+            ctx.step(t_end=T)
+            k = 1
+            rest = max(0, int(math.ceil((T - ctx.time()) / ctx.last_dt())) + 1)
+            while rest > 0 and ctx.time() < T * (1 - 1e-14):
+                ctx.run(rest, t_end=T)
+                k += rest
+                rest = 1
+            ctx.sync()
+            errs.append(density_l2_quadrature(ctx, wl, ctx.time(), x))
+            steps.append(k)
+            ctx.close()
+            torch.cuda.empty_cache()
+        errs.append(res[form]["err"]["l2_rho_quadrature"])
+        steps.append(res[form]["err"]["steps"])
+        hs = list(sides) + [base["ncell"][0]]
+        orders = [math.log(errs[i] / errs[i + 1]) / math.log(hs[i + 1] / hs[i])
+                  for i in range(len(hs) - 1)]
+        out[form] = {"t": T, "cells_per_side": hs, "steps": steps, "l2_rho": errs,
+                     "observed_order": orders}
+    if "fp64" in out and "mixed_cerk" in out:
+        out["mixed_cerk_over_fp64"] = [m / f for m, f in zip(out["mixed_cerk"]["l2_rho"],
+                                                              out["fp64"]["l2_rho"])]
     return out
 
 
@@ -907,14 +1003,17 @@ def main():
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": head["clocks"]}
     if not args.no_extra and world == 1:
         extra = {}
-        for name, fn in (("euler2d_p3_27", extra_euler2d), ("explosion3d_p3_64", extra_explosion),
+        for name, fn in (("euler3d_p4_convergence", extra_convergence),
+                         ("euler2d_p3_27", extra_euler2d), ("explosion3d_p3_64", extra_explosion),
                          ("elastic3d_p5_81", extra_elastic), ("ensemble16_elastic_p4", extra_ensemble),
                          ("adjoint_elastic3d_p4_40", extra_adjoint), ("euler3d_p4_81_cerk", extra_cerk),
                          ("ensemble16_adjoint_p4", extra_ensemble_adjoint)):
             if args.extras and name not in args.extras.split(","):
                 continue
             try:
-                if fn is extra_elastic:
+                if fn is extra_convergence:
+                    extra[name] = fn(ader, synth, stream, res)
+                elif fn is extra_elastic:
                     extra[name] = fn(ader, synth, stream, n=args.elastic_n)
                 else:
                     extra[name] = fn(ader, synth, stream)

@@ -1,5 +1,6 @@
-// Adjoint kernels of the elastic step, order 3 (own translation unit to keep builds parallel).
-#include "kernels_adjoint.cuh"
+// Adjoint kernels of the elastic step (Picard and Cauchy-Kowalevski predictors), order 3
+// (own translation unit to keep builds parallel).
+#include "kernels_adjoint_ck.cuh"
 
 namespace ader {
 template <>
@@ -10,4 +11,8 @@ template <>
 long long adj_scratch_n<3>(int iters) { return AdjLaunch<3>::scratch_per_block(iters); }
 template <>
 int adj_bps_n<3>() { return AdjLaunch<3>::blocks_per_sm(); }
+template <>
+cudaError_t adj_run_ck_n<3>(const StepArgs& a, const AdjArgs& j, const Tables& t, cudaStream_t s) {
+  return AdjLaunchCK<3>::run(a, j, t, s);
+}
 }  // namespace ader

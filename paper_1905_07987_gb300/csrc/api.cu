@@ -950,27 +950,36 @@ ader_status ader_troubled_count(ader_ctx* c, int64_t* count) {
   return ADER_OK;
 }
 
+// Whether the context's step has a hand-written adjoint: the elastic step, orders 1-5, with the
+// Picard predictor from the constant guess or with the Cauchy-Kowalevski predictor.
+static bool adjoint_supported(const ader_ctx* c) {
+  if (c->cfg.pde != ADER_PDE_ELASTIC || c->cfg.order > 5) return false;
+  if (c->cfg.predictor == ADER_PREDICTOR_CK) return c->fam->adj_run_ck != nullptr;
+  return c->fam->adj_run && c->cfg.predictor == ADER_PREDICTOR_PICARD &&
+         c->cfg.initial_guess == ADER_GUESS_CONSTANT;
+}
+
 ader_status ader_adjoint_step(ader_ctx* c, double t_n, double dt, const double* u_n, double* lam,
                               const double* dJdu, double* grad_mat, double* grad_M) {
   if (!c || !u_n || !lam || !grad_mat || !grad_M || !(dt > 0.0)) return ADER_EINVAL;
-  if (c->cfg.pde != ADER_PDE_ELASTIC || !c->fam->adj_run) return ADER_EUNSUPPORTED;
-  if (c->cfg.predictor != ADER_PREDICTOR_PICARD || c->cfg.initial_guess != ADER_GUESS_CONSTANT)
-    return ADER_EUNSUPPORTED;
-  if (c->cfg.order > 5) return ADER_EUNSUPPORTED;
+  if (!adjoint_supported(c)) return ADER_EUNSUPPORTED;
   if (!c->mat_set) return ADER_ESTATE;
+  const bool ck = c->cfg.predictor == ADER_PREDICTOR_CK;
   const int iters = c->cfg.picard_iters > 0 ? c->cfg.picard_iters : c->cfg.order + 1;
   if (!c->dev_adj) {
     int dev = 0, sms = 0;
     CUDA_OK(cudaGetDevice(&dev));
     CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    c->adj_blocks = sms * c->fam->adj_blocks_per_sm(c->cfg.order);
-    c->adj_spb = c->fam->adj_scratch_per_block(c->cfg.order, iters);
+    // the Cauchy-Kowalevski adjoint keeps its cell in shared memory: no iterate slabs
+    c->adj_blocks = ck ? 0 : sms * c->fam->adj_blocks_per_sm(c->cfg.order);
+    c->adj_spb = ck ? 0 : c->fam->adj_scratch_per_block(c->cfg.order, iters);
     long long nfaces = 0;
     for (int d = 0; d < 3; ++d) nfaces += (long long)(c->g.n[d] + 1) * (c->g.ncells / c->g.n[d]);
     cudaError_t e = cudaMalloc(&c->dev_adj, sizeof(DevScalars));
     if (e == cudaSuccess) e = cudaMalloc(&c->adjf, (size_t)c->g.ncells * 3 * 2 * c->nf * c->nvar * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&c->gface, (size_t)nfaces * 6 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&c->adj_scratch, (size_t)c->adj_blocks * c->adj_spb * sizeof(double));
+    if (e == cudaSuccess && !ck)
+      e = cudaMalloc(&c->adj_scratch, (size_t)c->adj_blocks * c->adj_spb * sizeof(double));
     if (e != cudaSuccess) {
       cudaGetLastError();
       cudaFree(c->dev_adj);
@@ -989,9 +998,15 @@ ader_status ader_adjoint_step(ader_ctx* c, double t_n, double dt, const double* 
   a.dev = c->dev_adj;
   a.iters = iters;
   // forward face data of the step from u^n (the predictor also writes the scratch next state)
-  CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
+  if (ck)
+    CUDA_OK(c->fam->predictor_ck(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
+  else
+    CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
   AdjArgs j{u_n, lam, dJdu, grad_mat, grad_M, c->adjf, c->gface, c->adj_scratch, c->adj_spb};
-  CUDA_OK(c->fam->adj_run(a, j, c->tab, c->adj_blocks, c->stream));
+  if (ck)
+    CUDA_OK(c->fam->adj_run_ck(a, j, c->tab, c->stream));
+  else
+    CUDA_OK(c->fam->adj_run(a, j, c->tab, c->adj_blocks, c->stream));
   // errors latched by the adjoint kernels reach the context's status word (ader_sync)
   CUDA_OK(launch_merge_status(c->dev_adj, c->dev, c->stream));
   return ADER_OK;
@@ -1076,11 +1091,9 @@ ader_status ader_adjoint_step_static(ader_ctx* c, double t_n, double dt, const d
                                      double* lam, const double* dJdu, double* grad_mat,
                                      double* grad_M) {
   if (!c || !u_n || !lam || !grad_mat || !grad_M || !(dt > 0.0)) return ADER_EINVAL;
-  if (c->cfg.pde != ADER_PDE_ELASTIC || !c->fam->adj_run) return ADER_EUNSUPPORTED;
-  if (c->cfg.predictor != ADER_PREDICTOR_PICARD || c->cfg.initial_guess != ADER_GUESS_CONSTANT)
-    return ADER_EUNSUPPORTED;
-  if (c->cfg.order > 5) return ADER_EUNSUPPORTED;
+  if (!adjoint_supported(c)) return ADER_EUNSUPPORTED;
   if (!c->mat_set) return ADER_ESTATE;
+  const bool ck = c->cfg.predictor == ADER_PREDICTOR_CK;
   int dev = 0;
   CUDA_OK(cudaGetDevice(&dev));
   void* base = nullptr;
@@ -1092,14 +1105,18 @@ ader_status ader_adjoint_step_static(ader_ctx* c, double t_n, double dt, const d
   const size_t b_dev = round256(sizeof(DevScalars));
   const size_t b_adjf = round256((size_t)c->g.ncells * 3 * 2 * c->nf * c->nvar * sizeof(double));
   const size_t b_gface = round256((size_t)nfaces * 6 * sizeof(double));
-  const long long spb = c->fam->adj_scratch_per_block(c->cfg.order, iters);
+  // the Cauchy-Kowalevski adjoint keeps its cell in shared memory: no iterate slabs
+  const long long spb = ck ? 0 : c->fam->adj_scratch_per_block(c->cfg.order, iters);
   const size_t b_slab = (size_t)spb * sizeof(double);
   const size_t fixed = b_dev + b_adjf + b_gface;
   if (fixed + b_slab > kStaticScratchBytes) return ADER_EINVAL;  // grid too large for the array
-  int sms = 0;
-  CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  long long blocks = (long long)sms * c->fam->adj_blocks_per_sm(c->cfg.order);
-  blocks = std::min<long long>(blocks, (long long)((kStaticScratchBytes - fixed) / b_slab));
+  long long blocks = 0;
+  if (!ck) {
+    int sms = 0;
+    CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    blocks = (long long)sms * c->fam->adj_blocks_per_sm(c->cfg.order);
+    blocks = std::min<long long>(blocks, (long long)((kStaticScratchBytes - fixed) / b_slab));
+  }
   unsigned char* p = (unsigned char*)base;
   DevScalars* dev_s = (DevScalars*)p;
   double* adjf = (double*)(p + b_dev);
@@ -1111,9 +1128,15 @@ ader_status ader_adjoint_step_static(ader_ctx* c, double t_n, double dt, const d
   a.u = u_n;
   a.dev = dev_s;
   a.iters = iters;
-  CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
+  if (ck)
+    CUDA_OK(c->fam->predictor_ck(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
+  else
+    CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
   AdjArgs j{u_n, lam, dJdu, grad_mat, grad_M, adjf, gface, slab, spb};
-  CUDA_OK(c->fam->adj_run(a, j, c->tab, (int)blocks, c->stream));
+  if (ck)
+    CUDA_OK(c->fam->adj_run_ck(a, j, c->tab, c->stream));
+  else
+    CUDA_OK(c->fam->adj_run(a, j, c->tab, (int)blocks, c->stream));
   // errors latched in the array's scalars reach the context's status word (ader_sync), and the
   // scalars start the next call clear
   CUDA_OK(launch_merge_status(dev_s, c->dev, c->stream));
@@ -1243,9 +1266,7 @@ ader_status ader_misfit_gradient(ader_ctx* c, const double* u0, double t0, doubl
                                  int k_ckpt, const double* obs, double* J, double* grad_mat,
                                  double* grad_M) {
   if (!c || !u0 || !obs || !J || steps < 1 || k_ckpt < 1 || !(dt > 0.0)) return ADER_EINVAL;
-  if (c->cfg.pde != ADER_PDE_ELASTIC) return ADER_EUNSUPPORTED;
-  if (c->cfg.predictor != ADER_PREDICTOR_PICARD || c->cfg.initial_guess != ADER_GUESS_CONSTANT)
-    return ADER_EUNSUPPORTED;
+  if (!adjoint_supported(c)) return ADER_EUNSUPPORTED;
   if (!c->mat_set || c->rec.nrec <= 0) return ADER_ESTATE;
   MisfitJob j;
   j.c = c;
@@ -1653,9 +1674,7 @@ ader_status ader_ensemble_misfit_gradient(ader_ensemble* e, const double* const*
   for (int r = 0; r < nr; ++r) {
     const ader_ctx* c = e->runs[r];
     if (!u0[r] || !obs[r]) return ADER_EINVAL;
-    if (c->cfg.pde != ADER_PDE_ELASTIC) return ADER_EUNSUPPORTED;
-    if (c->cfg.predictor != ADER_PREDICTOR_PICARD || c->cfg.initial_guess != ADER_GUESS_CONSTANT)
-      return ADER_EUNSUPPORTED;
+    if (!adjoint_supported(c)) return ADER_EUNSUPPORTED;
     if (!c->mat_set || c->rec.nrec <= 0 || c->timing) return ADER_ESTATE;
   }
   size_t budget = (size_t)(mem_budget > 0 ? mem_budget : 0);

@@ -1,5 +1,5 @@
-// Kernel family: linear elasticity in 3D, orders 1-6, with the adjoint step (orders 1-5) and the
-// Cauchy-Kowalevski predictor (orders 1-6).
+// Kernel family: linear elasticity in 3D, orders 1-6, with the adjoint step (orders 1-5, Picard
+// and Cauchy-Kowalevski forms) and the Cauchy-Kowalevski predictor (orders 1-6).
 #include "kernels.cuh"
 
 namespace ader {
@@ -22,6 +22,8 @@ template <int N>
 long long adj_scratch_n(int iters);
 template <int N>
 int adj_bps_n();
+template <int N>
+cudaError_t adj_run_ck_n(const StepArgs& a, const AdjArgs& j, const Tables& t, cudaStream_t s);
 namespace {
 cudaError_t adj_run(const StepArgs& a, const AdjArgs& j, const Tables& t, int blocks, cudaStream_t s) {
   switch (a.g.order) {
@@ -30,6 +32,16 @@ cudaError_t adj_run(const StepArgs& a, const AdjArgs& j, const Tables& t, int bl
     case 3: return adj_run_n<3>(a, j, t, blocks, s);
     case 4: return adj_run_n<4>(a, j, t, blocks, s);
     case 5: return adj_run_n<5>(a, j, t, blocks, s);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t adj_run_ck(const StepArgs& a, const AdjArgs& j, const Tables& t, cudaStream_t s) {
+  switch (a.g.order) {
+    case 1: return adj_run_ck_n<1>(a, j, t, s);
+    case 2: return adj_run_ck_n<2>(a, j, t, s);
+    case 3: return adj_run_ck_n<3>(a, j, t, s);
+    case 4: return adj_run_ck_n<4>(a, j, t, s);
+    case 5: return adj_run_ck_n<5>(a, j, t, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -72,6 +84,7 @@ const Family* family_elastic3() {
   static Family f = [] {
     Family g = *FamilyImpl<Elastic, 3>::get();
     g.adj_run = &adj_run;
+    g.adj_run_ck = &adj_run_ck;
     g.adj_scratch_per_block = &adj_scratch;
     g.adj_blocks_per_sm = &adj_bps;
     g.ens_step = &ens_step;

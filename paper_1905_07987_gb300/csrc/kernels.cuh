@@ -1077,9 +1077,14 @@ struct FamilyImpl {
   static size_t smem(int order, int prec);
   static const Family* get() {
     static const Family f = [] {
-      Family g = {P::NV, P::CONS, &cfl,    &predictor, &riemann, &corrector, &smem,
-                  nullptr, nullptr, nullptr, nullptr,   nullptr,  nullptr,    nullptr, 0,
-                  nullptr};
+      Family g{};  // hooks a family does not have stay null
+      g.nvar = P::NV;
+      g.conservative = P::CONS;
+      g.cfl = &cfl;
+      g.predictor = &predictor;
+      g.riemann = &riemann;
+      g.corrector = &corrector;
+      g.predictor_smem = &smem;
       g.nphi = Cfg<P, D, 1>::NPHI;
       return g;
     }();

@@ -1,6 +1,6 @@
-"""GPU parity of the hand-written adjoint of the elastic step against the oracle's reverse-mode
-derivative of its own step: lambda^n, the per-cell material gradient and the moment-tensor
-gradient, relative 1e-12."""
+"""GPU parity of the hand-written adjoint of the elastic step (Picard and Cauchy-Kowalevski
+predictors) against the oracle's reverse-mode derivative of its own step: lambda^n, the per-cell
+material gradient and the moment-tensor gradient, relative 1e-12."""
 import numpy as np
 import pytest
 import torch
@@ -24,13 +24,18 @@ def close(a, b, tol=1e-12):
     return np.abs(a - b).max() <= tol * max(np.abs(b).max(), 1e-300)
 
 
-@pytest.mark.parametrize("order,bc,ncell", [(2, "absorbing", (3, 2, 3)), (3, "periodic", (2, 3, 2)),
-                                            (4, "absorbing", (2, 2, 3)), (5, "absorbing", (2, 2, 2)),
-                                            (1, "periodic", (4, 3, 2))])
-def test_adjoint_step_matches_oracle(order, bc, ncell):
+CASES = [(2, "absorbing", (3, 2, 3)), (3, "periodic", (2, 3, 2)), (4, "absorbing", (2, 2, 3)),
+         (5, "absorbing", (2, 2, 2)), (1, "periodic", (4, 3, 2))]
+
+
+@pytest.mark.parametrize("predictor", ["picard", "ck"])
+@pytest.mark.parametrize("order,bc,ncell", CASES)
+def test_adjoint_step_matches_oracle(order, bc, ncell, predictor):
+    """Picard form: the adjoint of the Picard iteration; Cauchy-Kowalevski form: the adjoint of
+    the Taylor recursion (Sec. 3.3), each against the oracle's derivative of its own step."""
     mat = synth.elastic_material(ncell, seed=order + 10)
     hi = tuple(0.5 * n for n in ncell)
-    c = Case("elastic", 3, order, ncell, hi=hi, bc=bc, material=mat)
+    c = Case("elastic", 3, order, ncell, hi=hi, bc=bc, material=mat, predictor=predictor)
     c.point_source(tuple(0.37 * h for h in hi), synth.moment_tensor(seed=2), 2.0, 0.5)
     rng = np.random.default_rng(order)
     u_n = rng.standard_normal(c.shape)
@@ -116,3 +121,34 @@ def test_nonfinite_forward_state_is_reported(static):
     gm.zero_()
     c.ctx.adjoint_step(0.0, 1e-3, u_ok, lam.nan_to_num(0.0), gm, gM.zero_(), static=static)
     c.ctx.sync()
+
+
+@pytest.mark.parametrize("order,ncell", [(4, (5, 4, 3)), (2, (7, 3, 5)), (3, (3, 5, 4))])
+def test_ck_adjoint_static_and_repeatable(order, ncell):
+    """The Cauchy-Kowalevski adjoint through both entry points (work memory allocated by the
+    context, and the fixed device array) gives identical bits, and so does a repeated call
+    (fixed-order reductions); several cells per block at orders 2-3 with a ragged last block."""
+    mat = synth.elastic_material(ncell, seed=7)
+    hi = tuple(0.5 * n for n in ncell)
+    c = Case("elastic", 3, order, ncell, hi=hi, bc="absorbing", material=mat, predictor="ck")
+    c.point_source(tuple(0.61 * h for h in hi), synth.moment_tensor(seed=4), 2.0, 0.5)
+    rng = np.random.default_rng(11)
+    u_n = torch.from_numpy(rng.standard_normal(c.shape).reshape(-1)).cuda()
+    lam0 = torch.from_numpy(rng.standard_normal(c.shape).reshape(-1)).cuda()
+    dt = 0.6 * float(c.oracle.cfl_dt(torch.from_numpy(u_n.cpu().numpy().reshape(c.shape))))
+    outs = []
+    for static in (False, True, False):
+        lam = lam0.clone()
+        gm = torch.zeros(c.ctx.cells * 3, dtype=torch.float64, device="cuda")
+        gM = torch.zeros(6, dtype=torch.float64, device="cuda")
+        c.ctx.adjoint_step(0.31, dt, u_n, lam, gm, gM, static=static)
+        torch.cuda.synchronize()
+        outs.append((lam.cpu(), gm.cpu(), gM.cpu()))
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert torch.equal(a, b)
+    lam_ref, gm_ref, gM_ref = step_vjp(c.oracle, torch.from_numpy(u_n.cpu().numpy().reshape(c.shape)),
+                                       torch.from_numpy(lam0.cpu().numpy().reshape(c.shape)), dt, 0.31)
+    assert rel_linf(outs[0][0].numpy().reshape(c.shape), lam_ref.numpy()) <= 1e-12
+    assert close(outs[0][1].numpy(), gm_ref.numpy())
+    assert close(outs[0][2].numpy(), gM_ref.numpy())

@@ -1,7 +1,8 @@
-"""Batched adjoint of an ensemble of uneven elastic runs (ader_ensemble_misfit_gradient): every
-run's misfit and gradient equal the single-context checkpointed gradient of the same run, in any
-grouping of the runs, and match central finite differences; the mixed-precision forward sweep
-gives the FP64 gradient up to the mixed form's forward error.  The source sits three cells below
+"""Batched adjoint of an ensemble of uneven elastic runs (ader_ensemble_misfit_gradient), with the
+Picard and with the Cauchy-Kowalevski predictor: every run's misfit and gradient equal the
+single-context checkpointed gradient of the same run, in any grouping of the runs, and match
+central finite differences; the mixed-precision forward sweep gives the FP64 gradient up to the
+mixed form's forward error.  The source sits three cells below
 the top face so that the receivers record signal within the few steps of the test."""
 import numpy as np
 import pytest
@@ -18,9 +19,9 @@ def _build():
     build.build()
 
 
-def cfg(side, order, precision="fp64"):
+def cfg(side, order, precision="fp64", predictor="picard"):
     return ader.make_config("elastic", 3, order, (side,) * 3, (0, 0, 0), (0.5 * side,) * 3, "absorbing",
-                            synth.cfl_number(order), precision=precision)
+                            synth.cfl_number(order), precision=precision, predictor=predictor)
 
 
 def setup(ctx, side, seed, steps):
@@ -33,8 +34,8 @@ def setup(ctx, side, seed, steps):
     return seismo
 
 
-def problem(sides, order, steps, precision="fp64"):
-    ens = ader.Ensemble([cfg(s, order, precision) for s in sides])
+def problem(sides, order, steps, precision="fp64", predictor="picard"):
+    ens = ader.Ensemble([cfg(s, order, precision, predictor) for s in sides])
     keep = [setup(ens.runs[i], s, 10 + i, steps) for i, s in enumerate(sides)]
     u0 = [torch.zeros(r.count, dtype=torch.float64, device="cuda") for r in ens.runs]
     rng = np.random.default_rng(5)
@@ -48,14 +49,18 @@ def grads(ens):
     return gm, gM
 
 
-def test_batched_gradient_equals_single_context_gradients():
+PREDICTORS = pytest.mark.parametrize("predictor", ["picard", "ck"])
+
+
+@PREDICTORS
+def test_batched_gradient_equals_single_context_gradients(predictor):
     sides, order, steps, k, dt = [4, 3, 5], 3, 7, 3, 4e-3
-    ens, keep, u0, obs = problem(sides, order, steps)
+    ens, keep, u0, obs = problem(sides, order, steps, predictor=predictor)
     gm, gM = grads(ens)
     J = ens.misfit_gradient(u0, 0.45, dt, steps, k, obs, gm, gM)
     # each run alone through the single-context entry point
     for i, s in enumerate(sides):
-        c = ader.Context(cfg(s, order))
+        c = ader.Context(cfg(s, order, predictor=predictor))
         kk = setup(c, s, 10 + i, steps)
         g1 = torch.zeros(c.cells * 3, dtype=torch.float64, device="cuda")
         M1 = torch.zeros(6, dtype=torch.float64, device="cuda")
@@ -74,9 +79,10 @@ def test_batched_gradient_equals_single_context_gradients():
     ens.close()
 
 
-def test_batched_gradient_matches_central_differences():
+@PREDICTORS
+def test_batched_gradient_matches_central_differences(predictor):
     sides, order, steps, k, dt = [3, 4], 2, 6, 2, 4e-3
-    ens, keep, u0, obs = problem(sides, order, steps)
+    ens, keep, u0, obs = problem(sides, order, steps, predictor=predictor)
     gm, gM = grads(ens)
     J = ens.misfit_gradient(u0, 0.45, dt, steps, k, obs, gm, gM)
     i = 1
@@ -96,13 +102,14 @@ def test_batched_gradient_matches_central_differences():
     ens.close()
 
 
-def test_mixed_forward_gradient_is_close_to_fp64():
-    """The mixed-precision forward sweep (config 5's form) with the FP64 adjoint: the gradient
-    differs from the all-FP64 one by the mixed form's forward error only."""
+@PREDICTORS
+def test_mixed_forward_gradient_is_close_to_fp64(predictor):
+    """The mixed-precision forward sweep (the batched-adjoint workload's form) with the FP64
+    adjoint: the gradient differs from the all-FP64 one by the mixed form's forward error only."""
     sides, order, steps, k, dt = [4, 5], 4, 6, 3, 3e-3
     out = {}
     for prec in ("fp64", "mixed"):
-        ens, keep, u0, obs = problem(sides, order, steps, precision=prec)
+        ens, keep, u0, obs = problem(sides, order, steps, precision=prec, predictor=predictor)
         gm, gM = grads(ens)
         J = ens.misfit_gradient(u0, 0.45, dt, steps, k, obs, gm, gM)
         out[prec] = (J, [g.cpu().numpy() for g in gm], [g.cpu().numpy() for g in gM])

@@ -1,6 +1,6 @@
-"""Gradient of the receiver misfit through the checkpointed adjoint sweep of the library:
-against the oracle's adjoint sweep, against central finite differences of the GPU forward
-solver (relative <= 1e-6), and through torch.autograd."""
+"""Gradient of the receiver misfit through the checkpointed adjoint sweep of the library (Picard
+and Cauchy-Kowalevski predictors): against the oracle's adjoint sweep, against central finite
+differences of the GPU forward solver (relative <= 1e-6), and through torch.autograd."""
 import numpy as np
 import pytest
 import torch
@@ -20,10 +20,12 @@ def _build():
     build.build()
 
 
-def problem(order=2, ncell=(3, 2, 3), steps=9, k=4, bc="absorbing"):
+def problem(order=2, ncell=(3, 2, 3), steps=9, k=4, bc="absorbing", predictor="picard",
+            precision="fp64"):
     mat = synth.elastic_material(ncell, seed=7)
     hi = tuple(0.5 * n for n in ncell)
-    c = Case("elastic", 3, order, ncell, hi=hi, bc=bc, material=mat)
+    c = Case("elastic", 3, order, ncell, hi=hi, bc=bc, material=mat, predictor=predictor,
+             precision=precision)
     x0 = (0.41 * hi[0], 0.52 * hi[1], 0.47 * hi[2])
     M = synth.moment_tensor(seed=4)
     c.point_source(x0, M, 2.0, 0.5)
@@ -49,8 +51,12 @@ def gpu_J(c, mat, M, u0, dt, steps, k, obs, grads=False):
     return J
 
 
-def test_misfit_and_gradient_match_the_oracle():
-    c, mat, M, u0, dt, steps, k, obs = problem()
+PREDICTORS = pytest.mark.parametrize("predictor", ["picard", "ck"])
+
+
+@PREDICTORS
+def test_misfit_and_gradient_match_the_oracle(predictor):
+    c, mat, M, u0, dt, steps, k, obs = problem(predictor=predictor)
     J, gm, gM = gpu_J(c, mat, M, u0, dt, steps, k, obs, grads=True)
     s = c.oracle
     matt = torch.from_numpy(mat).requires_grad_(True)
@@ -65,8 +71,10 @@ def test_misfit_and_gradient_match_the_oracle():
     assert np.abs(gM - go_M.numpy()).max() <= 1e-10 * np.abs(go_M.numpy()).max()
 
 
-def test_gradient_matches_central_finite_differences():
-    c, mat, M, u0, dt, steps, k, obs = problem(order=3, ncell=(2, 3, 2), steps=8, k=3)
+@PREDICTORS
+def test_gradient_matches_central_finite_differences(predictor):
+    c, mat, M, u0, dt, steps, k, obs = problem(order=3, ncell=(2, 3, 2), steps=8, k=3,
+                                               predictor=predictor)
     J, gm, gM = gpu_J(c, mat, M, u0, dt, steps, k, obs, grads=True)
     rng = np.random.default_rng(3)
     for _ in range(2):
@@ -95,3 +103,18 @@ def test_autograd_function():
     assert abs(float(J) - J0) <= 1e-14 * abs(J0)
     assert np.allclose(m.grad.cpu().numpy(), 2 * gm, rtol=1e-13, atol=0)
     assert np.allclose(Mt.grad.cpu().numpy(), 2 * gM, rtol=1e-13, atol=0)
+
+
+def test_ck_gradient_with_mixed_forward_is_close_to_fp64():
+    """Order 4 with the mixed-precision Cauchy-Kowalevski forward sweep (the adjoint runs in FP64
+    on the recomputed states): the misfit and gradients stay within 1e-6 of the FP64 form."""
+    out = {}
+    for prec in ("fp64", "mixed"):
+        c, mat, M, u0, dt, steps, k, obs = problem(order=4, ncell=(3, 3, 2), steps=6, k=3,
+                                                   predictor="ck", precision=prec)
+        u0 = 1e-3 * np.random.default_rng(2).standard_normal(c.shape)
+        out[prec] = gpu_J(c, mat, M, u0, dt, steps, k, obs, grads=True)
+    (Jf, gmf, gMf), (Jm, gmm, gMm) = out["fp64"], out["mixed"]
+    assert abs(Jm - Jf) <= 1e-6 * abs(Jf)
+    assert np.abs(gmm - gmf).max() <= 1e-6 * np.abs(gmf).max()
+    assert np.abs(gMm - gMf).max() <= 1e-6 * np.abs(gMf).max()

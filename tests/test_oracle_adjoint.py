@@ -1,6 +1,7 @@
-"""Pins for the oracle adjoint of the elastic step: the dot-product identity <A x, y> = <x, A^T y>,
-A^T against a densely assembled A on a tiny grid, and central finite differences of the
-receiver misfit with respect to the material and the moment tensor."""
+"""Pins for the oracle adjoint of the elastic step, with the Picard and with the
+Cauchy-Kowalevski predictor (Sec. 3.3): the dot-product identity <A x, y> = <x, A^T y>, A^T
+against a densely assembled A on a tiny grid, and central finite differences of the receiver
+misfit with respect to the material and the moment tensor."""
 import math
 
 import numpy as np
@@ -15,18 +16,22 @@ from paper_1905_07987_gb300 import synth
 T = lambda a: torch.as_tensor(np.asarray(a), dtype=torch.float64)
 
 
-def setup(ncell=(2, 2, 2), N=2, bc='absorbing', seed=3, source=True):
+def setup(ncell=(2, 2, 2), N=2, bc='absorbing', seed=3, source=True, predictor='picard'):
     mat = T(synth.elastic_material(ncell, seed=seed))
     g = Grid(ncell, (0, 0, 0), (1.0 * ncell[0] / 2, 1.0 * ncell[1] / 2, 1.0 * ncell[2] / 2), [(bc, bc)] * 3)
-    s = ADERDG(Elastic(), g, N, cfl=synth.cfl_number(N), material=mat)
+    s = ADERDG(Elastic(), g, N, cfl=synth.cfl_number(N), material=mat, predictor=predictor)
     if source:
         c, xi = synth.locate((0.4, 0.55, 0.6), ncell, (0, 0, 0), g.hi)
         s.set_point_source(PointSource(c, xi, T(synth.moment_tensor(seed=1)), 2.0, 0.5))
     return s
 
 
-def test_dot_product_identity():
-    s = setup(source=False)
+PREDICTORS = pytest.mark.parametrize("predictor", ["picard", "ck"])
+
+
+@PREDICTORS
+def test_dot_product_identity(predictor):
+    s = setup(source=False, predictor=predictor)
     g = torch.Generator().manual_seed(0)
     shape = (s.grid.C,) + (s.n,) * 3 + (9,)
     x = torch.rand(shape, generator=g, dtype=torch.float64) - 0.5
@@ -37,8 +42,9 @@ def test_dot_product_identity():
     assert abs(float((Ax * y).sum() - (x * ATy).sum())) < 1e-12 * float((Ax * y).abs().sum())
 
 
-def test_transpose_matches_dense_operator():
-    s = setup(ncell=(2, 1, 1), N=1, bc='periodic', source=False)
+@PREDICTORS
+def test_transpose_matches_dense_operator(predictor):
+    s = setup(ncell=(2, 1, 1), N=1, bc='periodic', source=False, predictor=predictor)
     shape = (s.grid.C,) + (s.n,) * 3 + (9,)
     m = int(np.prod(shape))
     dt = 0.02
@@ -52,8 +58,8 @@ def test_transpose_matches_dense_operator():
     assert torch.allclose(ATy.reshape(-1), A.T @ y, atol=1e-13)
 
 
-def fd_setup():
-    s = setup(ncell=(2, 2, 2), N=2)
+def fd_setup(predictor='picard'):
+    s = setup(ncell=(2, 2, 2), N=2, predictor=predictor)
     ncell = s.grid.ncell
     pts = np.array([[0.3, 0.7, 1.0], [0.8, 0.2, 1.0]])
     cells, xis = [], []
@@ -91,8 +97,9 @@ def adjoint_gradient(s, u0, dt, steps, obs):
     return gm, gM
 
 
-def test_gradients_match_central_finite_differences():
-    s, u0, dt, steps, obs = fd_setup()
+@PREDICTORS
+def test_gradients_match_central_finite_differences(predictor):
+    s, u0, dt, steps, obs = fd_setup(predictor)
     gm, gM = adjoint_gradient(s, u0, dt, steps, obs)
     J = lambda: float(misfit(s, u0, steps, dt, obs, 0.5))
     mat0 = s.mat.clone()

@@ -158,8 +158,8 @@ def oracle_sample(wl, budget_s):
 FP32_PEAK = FP64_SMS * 128 * 2 * SM_MAX_MHZ * 1e6  # FLOP/s
 
 
-def survey_flops_per_cell(D, N, nv, iters, cF=30):
-    """Algorithmic flops per cell and step of the predictor in the survey's model (the
+def model_flops_per_cell(D, N, nv, iters, cF=30):
+    """Algorithmic flops per cell and step of the predictor in the sum-factorised model (the
     contractions the method must do, no padding): I [2 (d+1) nv n^(d+2) + cF n^(d+1)] for the
     Picard iterations plus the epilogue 2 (2d+1) nv n^(d+1) + 12 d nv n^d, cF ~ 30 flops per
     space-time node for the flux.  785 k flop for the Euler order-4 cell."""
@@ -558,20 +558,16 @@ def extra_convergence(ader, synth, stream, res, sides=(27, 54)):
     return out
 
 
-def extra_adjoint(ader, synth, stream, n=40, N=4, steps=12, k=4):
-    """Adjoint of the linear-elastic step through the C ABI (ader_misfit_gradient): order N, n^3
-    cells (h = 0.5 km), seeded material, moment-tensor Ricker source at the centre, 64 receivers
-    on the top face, a seeded misfit over `steps` steps with a checkpoint every k steps.  Reports
-    the whole gradient (forward sweep, recomputation of each segment, adjoint sweep, gradients with
-    respect to per-cell rho, lambda, mu and the moment tensor) against the same number of forward
-    steps."""
+def _adjoint_gradient_40(ader, synth, stream, n, N, steps, k, predictor):
+    """One misfit gradient through ader_misfit_gradient (see extra_adjoint) with the given
+    predictor; returns the timing record."""
     import torch
     L = 0.5 * n
     cells = n ** 3
     dofs = cells * (N + 1) ** 3 * 9
     mat = torch.from_numpy(synth.elastic_material((n,) * 3, seed=1905).reshape(-1).copy()).cuda()
     cfg = ader.make_config("elastic", 3, N, (n,) * 3, (0, 0, 0), (L,) * 3, "absorbing",
-                           synth.cfl_number(N))
+                           synth.cfl_number(N), predictor=predictor)
     ctx = ader.Context(cfg, stream=stream.cuda_stream)
     ctx.set_material(mat)
     ctx.set_point_source((L / 2,) * 3, synth.moment_tensor(), 2.0, 0.5)
@@ -602,15 +598,42 @@ def extra_adjoint(ader, synth, stream, n=40, N=4, steps=12, k=4):
     e1.record(stream)
     torch.cuda.synchronize()
     tot = e0.elapsed_time(e1)
+    # one adjoint step alone (forward face data, Riemann adjoint, cell adjoint)
+    lam = torch.from_numpy(np.random.default_rng(4).standard_normal(ctx.count)).cuda()
+    u1 = torch.from_numpy(np.random.default_rng(5).standard_normal(ctx.count)).cuda()
+    ctx.adjoint_step(0.45, dt, u1, lam, gm, gM)
+    e0.record(stream)
+    for _ in range(3):
+        ctx.adjoint_step(0.45, dt, u1, lam, gm, gM)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    adj = e0.elapsed_time(e1) / 3
     ok = bool(torch.isfinite(gm).all().item() and torch.isfinite(gM).all().item())
     ctx.close()
     del seismo
-    return {"workload": "adjoint_elastic3d_p%d_%d" % (N, n), "dofs": dofs, "steps": steps,
-            "k_ckpt": k, "forward_ms_per_step": fwd / steps, "gradient_ms": tot,
-            "gradient_over_forward": tot / fwd,
-            "value": dofs * steps / (tot * 1e-3), "unit": "DOF-updates/s (gradient: forward, "
-            "recomputation and adjoint, each step counted once)", "J": J, "finite": ok,
-            "dtype": "f64"}
+    return {"forward_ms_per_step": fwd / steps, "adjoint_step_ms": adj, "gradient_ms": tot,
+            "gradient_over_forward": tot / fwd, "value": dofs * steps / (tot * 1e-3), "J": J,
+            "finite": ok}
+
+
+def extra_adjoint(ader, synth, stream, n=40, N=4, steps=12, k=4):
+    """Adjoint of the linear-elastic step through the C ABI (ader_misfit_gradient): order N, n^3
+    cells (h = 0.5 km), seeded material, moment-tensor Ricker source at the centre, 64 receivers
+    on the top face, a seeded misfit over `steps` steps with a checkpoint every k steps.  Reports
+    the whole gradient (forward sweep, recomputation of each segment, adjoint sweep, gradients with
+    respect to per-cell rho, lambda, mu and the moment tensor) against the same number of forward
+    steps, with the Picard predictor and with the Cauchy-Kowalevski predictor (its own adjoint),
+    FP64."""
+    dofs = n ** 3 * (N + 1) ** 3 * 9
+    out = {"workload": "adjoint_elastic3d_p%d_%d" % (N, n), "dofs": dofs, "steps": steps,
+           "k_ckpt": k, "unit": "DOF-updates/s (gradient: forward, recomputation and adjoint, "
+           "each step counted once)", "dtype": "f64"}
+    for pred in ("picard", "ck"):
+        out[pred] = _adjoint_gradient_40(ader, synth, stream, n, N, steps, k, pred)
+    out["value"] = out["ck"]["value"]
+    out["ck_gradient_speedup"] = out["picard"]["gradient_ms"] / out["ck"]["gradient_ms"]
+    out["ck_adjoint_step_speedup"] = out["picard"]["adjoint_step_ms"] / out["ck"]["adjoint_step_ms"]
+    return out
 
 
 def extra_explosion(ader, synth, stream, steps=200, warmup=3, n=64):
@@ -749,17 +772,11 @@ def extra_ensemble(ader, synth, stream, steps=4):
             "ms_per_step_by_launch_shape": shapes}
 
 
-def extra_ensemble_adjoint(ader, synth, stream, steps=2, k=1):
-    """Batched adjoint of the 16-run ensemble (the ensemble workload's draw of cube sides, order 4,
-    mixed forward, each run with its seeded material, source and 64 top-face receivers): the
-    misfit gradient of every run with respect to per-cell rho, lambda, mu and the moment tensor
-    through ader_ensemble_misfit_gradient.  The source sits three cells below the top-face centre
-    so that the receivers record signal.  A bounded sample: `steps` steps with a checkpoint every
-    `k` (the full 300-step workload takes about an hour at the adjoint's rate)."""
+def _ensemble_gradient(ader, synth, stream, sides, steps, k, predictor):
     import torch
-    sides = synth.ensemble_sides(16)
     cfgs = [ader.make_config("elastic", 3, 4, (s,) * 3, (0, 0, 0), (0.5 * s,) * 3, "absorbing",
-                             synth.cfl_number(4), precision="mixed") for s in sides]
+                             synth.cfl_number(4), precision="mixed", predictor=predictor)
+            for s in sides]
     ens = ader.Ensemble(cfgs, stream=stream.cuda_stream)
     keep, dts = [], []
     for i, (s, r) in enumerate(zip(sides, ens.runs)):
@@ -785,13 +802,35 @@ def extra_ensemble_adjoint(ader, synth, stream, steps=2, k=1):
     ok = all(bool(torch.isfinite(g).all()) for g in gm + gM)
     dofs = sum(s ** 3 for s in sides) * 125 * 9
     ens.close()
-    return {"workload": "ensemble16_adjoint_p4 (batched misfit gradient, bounded sample)",
-            "sides": sides, "dofs": dofs, "steps": steps, "k_ckpt": k,
-            "gradient_s": el, "s_per_gradient_step": el / steps,
-            "value": dofs * steps / el, "unit": "DOF-updates/s (gradient: forward, recomputation "
-            "and adjoint, each step counted once; host wall clock around the synchronising call)",
-            "J_sum": float(sum(J)), "finite": ok, "forward": "mixed", "adjoint": "f64",
-            "full_workload_estimate_s": el / steps * 300}
+    del keep
+    torch.cuda.empty_cache()
+    return {"steps": steps, "k_ckpt": k, "gradient_s": el, "s_per_gradient_step": el / steps,
+            "value": dofs * steps / el, "J_sum": float(sum(J)), "finite": ok}
+
+
+def extra_ensemble_adjoint(ader, synth, stream, steps=20, k=5, picard_steps=1):
+    """Batched adjoint of the 16-run ensemble (the ensemble workload's draw of cube sides, order 4,
+    mixed forward, each run with its seeded material, source and 64 top-face receivers): the
+    misfit gradient of every run with respect to per-cell rho, lambda, mu and the moment tensor
+    through ader_ensemble_misfit_gradient.  The source sits three cells below the top-face centre
+    so that the receivers record signal.  Bounded samples: `steps` steps with a checkpoint every
+    `k` with the Cauchy-Kowalevski predictor and its adjoint, and `picard_steps` with the Picard
+    predictor and its adjoint (the full 300-step workload is timed with --adjoint-steps 300)."""
+    sides = synth.ensemble_sides(16)
+    dofs = sum(s ** 3 for s in sides) * 125 * 9
+    out = {"workload": "ensemble16_adjoint_p4 (batched misfit gradient)", "sides": sides,
+           "dofs": dofs, "unit": "DOF-updates/s (gradient: forward, recomputation and adjoint, "
+           "each step counted once; host wall clock around the synchronising call)",
+           "forward": "mixed", "adjoint": "f64"}
+    out["ck"] = _ensemble_gradient(ader, synth, stream, sides, steps, k, "ck")
+    if picard_steps:
+        out["picard"] = _ensemble_gradient(ader, synth, stream, sides, picard_steps, 1, "picard")
+        out["ck_speedup_per_step"] = (out["picard"]["s_per_gradient_step"]
+                                      / out["ck"]["s_per_gradient_step"])
+    out["value"] = out["ck"]["value"]
+    out["finite"] = out["ck"]["finite"]
+    out["full_workload_estimate_s"] = out["ck"]["s_per_gradient_step"] * 300
+    return out
 
 
 _WORLD = [1]
@@ -838,6 +877,9 @@ def main():
                     help="comma list of the other workloads to run (default: all of them)")
     ap.add_argument("--elastic-n", type=int, default=81,
                     help="cells per side of the elastic workload (81; smaller for profiling)")
+    ap.add_argument("--adjoint-steps", type=int, default=20,
+                    help="steps of the ensemble gradient sample (300: the full workload, "
+                         "checkpoint every 20)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads (2-D Euler, elastic, explosion, ensemble)")
     args = ap.parse_args()
@@ -928,17 +970,17 @@ def main():
     head_ctx.close()
 
     # ---- roofline of the dominant kernel (the predictor) of each form --------------------------
-    # algorithmic flops per cell in the survey's model (the unit of the roofline) and in the
+    # algorithmic flops per cell in the sum-factorised model (the unit of the roofline) and in the
     # kernel's own operation count (the flux evaluation counted operation by operation)
     def form_flops(form):
-        """(survey-model flops, kernel-count flops) per cell of the form's predictor; the CERK
+        """(model flops, kernel-count flops) per cell of the form's predictor; the CERK
         guess adds three single-time-level evaluations of the flux and its derivatives (1/n of
         an iteration each) and the dense output (4 FMA per line and time node)."""
         _, guess, iters = FORMS[form]
         I = iters or N + 1
         n = N + 1
         nv = D + 2
-        m = survey_flops_per_cell(D, N, nv, I)
+        m = model_flops_per_cell(D, N, nv, I)
         k = predictor_flops_per_cell(wl["pde"], D, N, I)
         if guess == "cerk":
             it = 2 * (D + 1) * nv * n ** (D + 2) + 30 * n ** (D + 1)
@@ -968,7 +1010,7 @@ def main():
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": TRAFFIC_PER_CELL.get(prec, 0) * cells if TRAFFIC_PER_CELL.get(prec) else None,
                 "peak_source": src, "flops_per_cell": flops_model / cells,
-                "flops_model": "survey model I [2(d+1) nv n^(d+2) + 30 n^(d+1)] + 2(2d+1) nv n^(d+1) + 12 d nv n^d",
+                "flops_model": "sum-factorised model I [2(d+1) nv n^(d+2) + 30 n^(d+1)] + 2(2d+1) nv n^(d+1) + 12 d nv n^d",
                 "kernel_count_flops_per_cell": flops_kernel / cells,
                 "frac_kernel_count": flops_kernel / (pred_ms * 1e-3) / 1e12 / peak,
                 "frac_of_derived_peak": achieved / derived, "derived_peak": derived,
@@ -1013,6 +1055,10 @@ def main():
             try:
                 if fn is extra_convergence:
                     extra[name] = fn(ader, synth, stream, res)
+                elif fn is extra_ensemble_adjoint:
+                    ks = 20 if args.adjoint_steps >= 100 else 5
+                    extra[name] = fn(ader, synth, stream, steps=args.adjoint_steps, k=ks,
+                                     picard_steps=0 if args.adjoint_steps >= 100 else 1)
                 elif fn is extra_elastic:
                     extra[name] = fn(ader, synth, stream, n=args.elastic_n)
                 else:

@@ -99,7 +99,8 @@ typedef enum { ADER_PREC_FP64 = 0, ADER_PREC_MIXED = 1, ADER_PREC_MIXED_TF32X3 =
  *           3-D elastic family (others: ADER_EUNSUPPORTED), with ADER_PREC_FP64 and with
  *           ADER_PREC_MIXED (the O(1) base term L u and the first Taylor coefficient in
  *           float-float, the higher coefficients in binary32, the update u + dt vol in FP64).
- *           Not differentiated: the adjoint entry points return ADER_EUNSUPPORTED for it. */
+ *           Differentiated (orders 1-5): the adjoint entry points take the FP64 adjoint of the
+ *           Taylor recursion. */
 typedef enum { ADER_PREDICTOR_PICARD = 0, ADER_PREDICTOR_CK = 1 } ader_predictor;
 
 /* Initial guess of the Picard predictor (Sec. 5):
@@ -243,13 +244,17 @@ ader_status ader_sync(ader_ctx* ctx);
  * the same.  Does not synchronise. */
 ader_status ader_run_graph(ader_ctx* ctx, int steps, int replays, double dt, double t_end);
 
-/* Adjoint of one linear-elastic step (elastic contexts, order <= 5).  With a fixed dt the step
- * u^{n+1} = A(m) u^n + b^n(M, m) is affine (Eq. (5) predictor, Rusanov faces, Eq. (6) corrector,
- * moment-tensor point source of Eq. (1)); this call maps lam = lambda^{n+1} to
+/* Adjoint of one linear-elastic step (elastic contexts, order <= 5, with the Picard predictor
+ * from the constant guess or with the Cauchy-Kowalevski predictor; other predictor settings:
+ * ADER_EUNSUPPORTED).  With a fixed dt the step u^{n+1} = A(m) u^n + b^n(M, m) is affine
+ * (Eq. (5) predictor, or its Cauchy-Kowalevski form of Sec. 3.3, Rusanov faces, Eq. (6)
+ * corrector, moment-tensor point source of Eq. (1)); this call maps lam = lambda^{n+1} to
  *     lambda^n = A(m)^T lambda^{n+1} + dJdu   (in place in `lam`)
  * and accumulates  grad_mat[c][0..2] += d/d(rho, lambda, mu)_c of (lambda^{n+1})^T u^{n+1}  and
  * grad_M[0..5] += d/dM of the same, evaluated at the forward state u_n = u^n with the step
- * starting at time t_n.  The wave speed max(vp_L, vp_R) of a face takes the left value at ties.
+ * starting at time t_n, for the FP64 step of the context's predictor (a MIXED context gets the
+ * adjoint of its FP64 step).  The wave speed max(vp_L, vp_R) of a face takes the left value at
+ * ties.  The gradient sums are formed in a fixed order: repeated calls give identical bits.
  * All pointers are device memory of the context's device ([cells][nodes][9] for u_n, lam, dJdu;
  * [cells][3]; [6]); dJdu may be NULL.  Uses the context's material, point source and order; the
  * context's own state and time are not touched.  Stream-ordered, no synchronisation.  The first
@@ -260,8 +265,8 @@ ader_status ader_adjoint_step(ader_ctx* ctx, double t_n, double dt, const double
                               const double* dJdu, double* grad_mat, double* grad_M);
 
 /* Same result as ader_adjoint_step, but this call allocates no memory: its work buffers (the
- * forward Picard iterates kept per thread block, the face adjoints and the per-face material
- * gradients) live in one fixed 64 MiB array of device memory that the library defines, so no
+ * forward Picard iterates kept per thread block (none with the Cauchy-Kowalevski predictor), the
+ * face adjoints and the per-face material gradients) live in one fixed 64 MiB array of device memory that the library defines, so no
  * cudaMalloc, cudaFree or other allocating call is made.  It exists for callers that cannot
  * allocate device memory at the time of the call: for example code whose device memory is
  * owned by another allocator (a framework's memory pool that has reserved the GPU), processes
@@ -269,7 +274,8 @@ ader_status ader_adjoint_step(ader_ctx* ctx, double t_n, double dt, const double
  * synchronisation that cudaMalloc and cudaFree imply.  There is no counterpart in the paper.
  * Limits and behaviour:
  *  - The face adjoints (cells x 3 x 2 x n^2 x 9 doubles), the face gradients (6 doubles per
- *    face) and one iterate slab (order x (order+1) x n^3 x 9 doubles) must fit in 64 MiB;
+ *    face) and, with the Picard predictor, one iterate slab (order x (order+1) x n^3 x 9
+ *    doubles) must fit in 64 MiB;
  *    otherwise ADER_EINVAL and nothing runs.  Fewer thread blocks are used when the slabs of all
  *    of them do not fit.
  *  - The array is shared by every call on a device and keeps the contents of the last call
@@ -299,7 +305,8 @@ ader_status ader_receivers_adjoint(ader_ctx* ctx, const double* res, double scal
  *     J = 1/2 dt sum_k sum_r |v_r(u^{k+1}) - obs[k][r]|^2      (obs: device [steps][nrec][3]).
  * If grad_mat or grad_M is non-NULL it then runs the adjoint sweep: the state of every k_ckpt-th
  * step is kept on the device, each segment is recomputed from its checkpoint, and
- * ader_adjoint_step is applied backwards, writing dJ/d(rho, lambda, mu) per cell to grad_mat
+ * ader_adjoint_step is applied backwards (same predictors as ader_adjoint_step, else
+ * ADER_EUNSUPPORTED), writing dJ/d(rho, lambda, mu) per cell to grad_mat
  * (device [cells][3], overwritten) and dJ/dM to grad_M (device [6], overwritten).  J is written
  * to host memory.  Allocates (steps/k_ckpt + k_ckpt + 1) states of work memory for the call.
  * Synchronises.  The context's state afterwards is unspecified (set it again before stepping). */
@@ -366,7 +373,8 @@ ader_status ader_ensemble_autotune(ader_ensemble* ens, double dt, int* best, dou
  * the adjoint is that of the FP64 step at those states.  Runs are processed in groups whose work
  * memory ((steps/k_ckpt + k_ckpt + 1) states each) fits mem_budget bytes (<= 0: half of the free
  * device memory; a run that alone exceeds it is processed alone).  Requires material and
- * receivers on every run (ADER_ESTATE otherwise); the Picard predictor from the constant guess.
+ * receivers on every run (ADER_ESTATE otherwise); each run with the Picard predictor from the
+ * constant guess or with the Cauchy-Kowalevski predictor (ADER_EUNSUPPORTED otherwise).
  * Synchronises.  The runs' states afterwards are unspecified. */
 ader_status ader_ensemble_misfit_gradient(ader_ensemble* ens, const double* const* u0, double t0,
                                           double dt, int steps, int k_ckpt,

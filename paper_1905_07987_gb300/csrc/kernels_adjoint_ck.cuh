@@ -4,25 +4,32 @@
 //   a_0 = u,   a_{k+1} = f_k (L a_k + g s_k),   f_k = dt / (k+1),   k = 0..N-1,
 //   qbar = sum_{k<=N} a_k / (k+1),
 // followed by the volume term u + dt (L qbar + g sbar) and the face extrapolations E qbar (the
-// same epilogue as the Picard form).  Given lambda (the adjoint of the next state) and the
-// adjoint of the face extrapolations (k_adj_riemann, shared with the Picard adjoint), the
-// transposes are taken in reverse order:
-//   lq   = dt L^T lambda + sum_d E_d^T adjf_d                  (adjoint of qbar)
-//   mu_N = lq / (N+1),   mu_k = lq / (k+1) + f_k L^T mu_{k+1}   (adjoint of a_k)
-//   lambda^n = lambda + mu_0 (+ dJ/du^n)
-// and the gradients pair each adjoint with the forward quantity that multiplies the parameter:
-//   material   dt lambda^T (dL/dm) qbar + sum_k f_k mu_{k+1}^T (dL/dm) a_k
-//   moment     dt sbar lambda^T (dg/dM) + sum_k f_k s_k mu_{k+1}^T (dg/dM).
-// (dL/dm) a at a node needs only the derivatives of a at that node (the forward contraction), so
-// the material gradient costs one forward-style application per level; L^T needs the adjoint of
-// the neighbours along each line: the contraction with the transposed derivative matrix.
+// same epilogue as the Picard form).  Given lambda (the adjoint of the next state) and F, the
+// adjoint of the face extrapolations carried back to the nodes (from k_adj_riemann, shared with
+// the Picard adjoint), the adjoint of a_k is
+//   mu_k = (F + dt L^T lambda) / (k+1) + f_k L^T mu_{k+1}    (mu_{N+1} = 0),
+// and since f_k = dt / (k+1) the volume term and the Taylor recursion merge into one recursion on
+// nu_k = lambda + mu_k:
+//   mu_k = (F + dt L^T nu_{k+1}) / (k+1),   k = N..0,   nu_{N+1} = lambda,
+//   lambda^n = nu_0 (+ dJ/du^n).
+// The gradients pair each adjoint with the forward quantity that multiplies the parameter; the
+// volume term's dt lambda^T (dL/dm) qbar splits over the levels the same way:
+//   material   sum_{k=0..N} f_k nu_{k+1}^T (dL/dm) a_k
+//   moment     dt sbar lambda^T (dg/dM) + sum_{k<N} f_k s_k mu_{k+1}^T (dg/dM).
+// (dL/dm) a needs no contraction of its own: at a node, L a is the material coefficients times
+// ten derivative quantities (velocity rows (1/rho) S_i, normal-stress rows lam theta + 2 mu e_i,
+// shear rows mu gamma_v), so the derivatives with respect to (rho, lam, mu) follow from R = L a
+// itself: -R_i / rho; theta = sum_i R_{3+i} / (3 lam + 2 mu); 2 e_i = (R_{3+i} - lam theta) / mu;
+// gamma_v = R_v / mu.  For k < N, f_k L a_k = a_{k+1} - f_k s_k g is already at hand; L a_N costs
+// one application.
 //
-// One thread per node, the cells of a block (several at low order) each keep a_0 .. a_{N-1}
-// and two adjoint buffers in shared memory: (N+2) padded records of 10 doubles per node, no
-// global scratch.  Work per node: N forward applications to recompute a_k, then N+1 pairs of
-// (L^T, material derivative) applications; the Picard adjoint recomputes and reverses N+1
-// iterations over n time nodes.  The gradient sums are reduced in a fixed order (no atomics), so
-// repeated runs give identical bits.
+// One thread per node, the cells of a block (several at low order) each keep a_0 .. a_N in
+// shared memory ((N+2) padded records of 10 doubles per node; the record of a_0 and a spare one
+// hold the adjoint nu during the reverse sweep, the tenth double of a nu record its sum
+// nu_3 + nu_4 + nu_5), no global scratch.  Work per node: N+1 applications of L (the forward
+// recursion and L a_N) and N+1 of L^T; the Picard adjoint recomputes and reverses N+1 iterations
+// over n time nodes.  The gradient sums are reduced in a fixed order (no atomics), so repeated
+// runs give identical bits.
 #pragma once
 #include "kernels_adjoint.cuh"
 #include "kernels_ck.cuh"
@@ -40,14 +47,15 @@ struct CfgCKA {
   static constexpr int TPB = (CPB * NS + 31) / 32 * 32;
   static constexpr int NF = n * n;
   static constexpr int REC = NS * NVP;
-  static constexpr int NBUF = N + 2;  // a_0 .. a_{N-1}, two adjoint buffers
+  static constexpr int NBUF = N + 2;  // a_0 (then nu) .. a_N, one more nu buffer
   static constexpr size_t SMEM = (size_t)CPB * NBUF * REC * sizeof(double);
 };
 
-// Out[col] += (L^T Y)[j][col] for the record Y ([NS][NVP]) at node j.  DT[d][i] = D[i][j_d]
-// (column j_d of the derivative matrix); cf[d] = {1/(rho h_d), (lam + 2 mu)/h_d, lam/h_d, mu/h_d}.
-// Row by row of L (see ck_apply): velocity row i reads sigma_{id}, normal-stress rows read v_d,
-// shear row v reads v_{src(d,v)}; the transpose sends each row's adjoint back to that column.
+// Out[col] += (L^T Y)[j][col] for the adjoint record Y ([NS][NVP], Y[.][9] = Y_3 + Y_4 + Y_5)
+// at node j.  DT[d][i] = D[i][j_d] (column j_d of the derivative matrix); cf[d] = {1/(rho h_d),
+// (lam + 2 mu)/h_d, lam/h_d, mu/h_d}.  Row by row of L (see ck_apply): velocity row i reads
+// sigma_{id}, normal-stress rows read v_d, shear row v reads v_{src(d,v)}; the transpose sends
+// each row's adjoint back to that column.
 template <int N>
 __device__ __forceinline__ void ck_apply_T(const double* Y, int j, const double (&DT)[3][N + 1],
                                            const double (&cf)[3][4], double (&Out)[9]) {
@@ -75,7 +83,7 @@ __device__ __forceinline__ void ck_apply_T(const double* Y, int j, const double 
       t0 = fma(c, r[0], t0);
       t1 = fma(c, r[1], t1);
       t2 = fma(c, r[2], t2);
-      tsum = fma(c, r[3] + r[4] + r[5], tsum);
+      tsum = fma(c, r[9], tsum);
       tdd = fma(c, r[3 + d], tdd);
       tsa = fma(c, r[va], tsa);
       tsb = fma(c, r[vb], tsb);
@@ -89,56 +97,18 @@ __device__ __forceinline__ void ck_apply_T(const double* Y, int j, const double 
   }
 }
 
-// gm += w * mu^T (dL/d(rho, lam, mu)) X at node j (mu: the adjoint at this node).  The
-// derivatives of the record X along each direction are those of ck_apply; ih[d] = 1/h_d.
-template <int N>
-__device__ __forceinline__ void ck_dmat(const double* X, int j, const double (&Dr)[3][N + 1],
-                                        const double (&ih)[3], double irho, const double (&mu)[9],
-                                        double w, double (&gm)[3]) {
-  constexpr int n = N + 1, NVP = CfgCKA<N>::NVP;
-  double grho = 0.0, glam = 0.0, gmu = 0.0;
-  const double msum = mu[3] + mu[4] + mu[5];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
-    const int jd = (j / st) % n;
-    const double* b = X + (j - jd * st) * NVP;
-    const int s0 = Elastic::sig(0, d), s1 = Elastic::sig(1, d), s2 = Elastic::sig(2, d);
-    double dv0 = 0.0, dv1 = 0.0, dv2 = 0.0, ds0 = 0.0, ds1 = 0.0, ds2 = 0.0;
-#pragma unroll
-    for (int m = 0; m < n; ++m) {
-      const double2* p = reinterpret_cast<const double2*>(b + m * st * NVP);
-      double r[NVP];
-#pragma unroll
-      for (int i = 0; i < NVP / 2; ++i) {
-        const double2 v = p[i];
-        r[2 * i] = v.x;
-        r[2 * i + 1] = v.y;
-      }
-      const double c = Dr[d][m];
-      dv0 = fma(c, r[0], dv0);
-      dv1 = fma(c, r[1], dv1);
-      dv2 = fma(c, r[2], dv2);
-      ds0 = fma(c, r[s0], ds0);
-      ds1 = fma(c, r[s1], ds1);
-      ds2 = fma(c, r[s2], ds2);
-    }
-    const double dv[3] = {dv0, dv1, dv2};
-    // velocity rows: (1/rho) d sigma_{id} / dx_d  ->  d/drho = -1/rho^2
-    grho = fma(ih[d], fma(mu[0], ds0, fma(mu[1], ds1, mu[2] * ds2)), grho);
-    // normal-stress rows: (lam + 2 mu [i == d]) dv_d / dx_d
-    glam = fma(ih[d] * dv[d], msum, glam);
-    gmu = fma(2.0 * ih[d] * dv[d], mu[3 + d], gmu);
-    // shear rows: mu dv_{src(d,v)} / dx_d
-#pragma unroll
-    for (int v = 6; v < 9; ++v) {
-      const int s = Elastic::src(d, v);
-      if (s >= 0) gmu = fma(ih[d] * dv[s], mu[v], gmu);
-    }
-  }
-  gm[0] = fma(w, -irho * irho * grho, gm[0]);
-  gm[1] = fma(w, glam, gm[1]);
-  gm[2] = fma(w, gmu, gm[2]);
+// gm += nu^T (dL/d(rho, lam, mu)) a at one node, given P = w L a there (any weight w: the result
+// carries the same factor).  irho = 1/rho, ik = 1/(3 lam + 2 mu), imu = 1/mu.
+__device__ __forceinline__ void ck_dmat_R(const double (&P)[9], const double (&nu)[9], double irho,
+                                          double lam, double ik, double imu, double (&gm)[3]) {
+  gm[0] = fma(-irho, fma(nu[0], P[0], fma(nu[1], P[1], nu[2] * P[2])), gm[0]);
+  const double theta = (P[3] + P[4] + P[5]) * ik;
+  const double nsum = nu[3] + nu[4] + nu[5];
+  gm[1] = fma(theta, nsum, gm[1]);
+  double s = fma(nu[3], P[3], fma(nu[4], P[4], nu[5] * P[5]));
+  s = fma(-lam * theta, nsum, s);
+  s = fma(nu[6], P[6], fma(nu[7], P[7], fma(nu[8], P[8], s)));
+  gm[2] = fma(imu, s, gm[2]);
 }
 
 template <int N>
@@ -158,16 +128,17 @@ __global__ void __launch_bounds__(CfgCKA<N>::TPB)
   const int ncb = (int)(A.g.ncells - c0 < CPB ? A.g.ncells - c0 : CPB);
   const bool act = slot < ncb;
   const long long c = c0 + slot;
-  double* base = smem + (size_t)(act ? slot : 0) * NBUF * REC;
-  double* P = base + N * REC;  // adjoint buffers P, Q
-  double* Q = P + REC;
+  double* base = smem + (size_t)(act ? slot : 0) * NBUF * REC;  // a_k at base + k * REC
+  double* const spare = base + (N + 1) * REC;
   const double dt = A.dev->dt;
   const double tn = A.dev->t;
 
-  // the block's cells into a_0 (coalesced)
+  // the block's cells into a_0, lambda^{n+1} into the spare record (coalesced)
   for (int e = tid; e < ncb * NL; e += TPB) {
     const int s = e / NL, r = e - s * NL;
-    smem[(size_t)s * NBUF * REC + (r / NV) * NVP + r % NV] = J.u_n[c0 * NL + e];
+    const size_t o = (size_t)s * NBUF * REC + (r / NV) * NVP + r % NV;
+    smem[o] = J.u_n[c0 * NL + e];
+    smem[o + (size_t)(N + 1) * REC] = J.lam[c0 * NL + e];
   }
   const long long sc = A.src.cell - c0;
   const bool srcb = sc >= 0 && sc < ncb;
@@ -190,8 +161,8 @@ __global__ void __launch_bounds__(CfgCKA<N>::TPB)
     s_sbar = sbar;
   }
   const bool srcc = srcb && act && sc == slot;  // this thread's cell holds the source
-  double Dr[3][n], DT[3][n], cf[3][4], ih[3], irho = 0.0;
-  double phi = 0.0, Mt[6];
+  double Dr[3][n], DT[3][n], cf[3][4];
+  double irho = 0.0, lam = 0.0, ik = 0.0, imu = 0.0;
   if (act) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -203,28 +174,27 @@ __global__ void __launch_bounds__(CfgCKA<N>::TPB)
       }
     }
     irho = 1.0 / A.mat[c * 3 + 0];
-    const double lam = A.mat[c * 3 + 1];
+    lam = A.mat[c * 3 + 1];
     const double mu = A.mat[c * 3 + 2];
+    ik = 1.0 / (3.0 * lam + 2.0 * mu);
+    imu = 1.0 / mu;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      ih[d] = A.g.inv_h[d];
-      cf[d][0] = irho * ih[d];
-      cf[d][1] = (lam + 2.0 * mu) * ih[d];
-      cf[d][2] = lam * ih[d];
-      cf[d][3] = mu * ih[d];
+      const double ih = A.g.inv_h[d];
+      cf[d][0] = irho * ih;
+      cf[d][1] = (lam + 2.0 * mu) * ih;
+      cf[d][2] = lam * ih;
+      cf[d][3] = mu * ih;
     }
   }
+  // the point source's spatial factor g at this node (stress rows): -M_a phi_j
+  const double phi = srcc ? A.src.phi[j] : 0.0;
+  double mphi[6];
 #pragma unroll
-  for (int a = 0; a < 6; ++a) Mt[a] = srcc ? A.src.M[a] : 0.0;
-  if (srcc) phi = A.src.phi[j];
+  for (int a = 0; a < 6; ++a) mphi[a] = srcc ? -A.src.M[a] * phi : 0.0;
   __syncthreads();
 
-  // ---- forward recursion: a_1 .. a_{N-1} kept, qbar accumulated ----------------------------
-  double qb[NV];
-  if (act) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) qb[v] = base[j * NVP + v];
-  }
+  // ---- forward recursion: a_1 .. a_N; then P = f_N L a_N at this node ------------------------
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     if (act) {
@@ -234,44 +204,31 @@ __global__ void __launch_bounds__(CfgCKA<N>::TPB)
       ck_apply<N>(base + k * REC, j, Dr, cf, R);
       if (srcc) {
 #pragma unroll
-        for (int v = 3; v < NV; ++v) R[v] = fma(-Mt[v - 3] * phi, s_sk[k], R[v]);
+        for (int v = 3; v < NV; ++v) R[v] = fma(mphi[v - 3], s_sk[k], R[v]);
       }
       const double f = dt * (1.0 / (k + 1));
-      const double wk = 1.0 / (k + 2);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const double a = f * R[v];
-        qb[v] = fma(wk, a, qb[v]);
-        if (k + 1 < N) base[(k + 1) * REC + j * NVP + v] = a;
-      }
+      for (int v = 0; v < NV; ++v) base[(k + 1) * REC + j * NVP + v] = f * R[v];
     }
     __syncthreads();
   }
-  // qbar -> P, lambda^{n+1} -> Q (coalesced)
+  double P[NV];  // f_k L a_k at this node, for the level being reversed
+  double lam_j[NV], Fj[NV];
   if (act) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) P[j * NVP + v] = qb[v];
-  }
-  for (int e = tid; e < ncb * NL; e += TPB) {
-    const int s = e / NL, r = e - s * NL;
-    smem[(size_t)s * NBUF * REC + (size_t)(N + 1) * REC + (r / NV) * NVP + r % NV] =
-        J.lam[c0 * NL + e];
-  }
-  __syncthreads();
-
-  // ---- adjoint of the volume term and of the face extrapolations ---------------------------
-  double gm[3] = {0.0, 0.0, 0.0}, gM[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  double lam_j[NV], lq[NV];
-  if (act) {
+    for (int v = 0; v < NV; ++v) P[v] = 0.0;
+    ck_apply<N>(base + N * REC, j, Dr, cf, P);
+    const double fN = dt * (1.0 / (N + 1));
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      lam_j[v] = Q[j * NVP + v];
-      lq[v] = 0.0;
-    }
-    ck_apply_T<N>(Q, j, DT, cf, lq);
+    for (int v = 0; v < NV; ++v) P[v] *= fN;
+    // lambda at this node; its stress sum into the tenth slot of the record
+    double* lr = spare + j * NVP;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) lq[v] *= dt;
-    ck_dmat<N>(P, j, Dr, ih, irho, lam_j, dt, gm);
+    for (int v = 0; v < NV; ++v) lam_j[v] = lr[v];
+    lr[9] = lam_j[3] + lam_j[4] + lam_j[5];
+    // F: the face adjoints carried back to the nodes (transposed extrapolation)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fj[v] = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
@@ -280,69 +237,80 @@ __global__ void __launch_bounds__(CfgCKA<N>::TPB)
       const double* af = J.adjf + (c * 3 + d) * 2 * (long long)(NF * NV) + jp * NV;
       const double e0 = T.e0[jd], e1 = T.e1[jd];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) lq[v] = fma(e0, af[v], fma(e1, af[NF * NV + v], lq[v]));
-    }
-    if (srcc) {
-#pragma unroll
-      for (int a = 0; a < 6; ++a) gM[a] = fma(dt * s_sbar, -phi * lam_j[3 + a], gM[a]);
+      for (int v = 0; v < NV; ++v) Fj[v] = fma(e0, af[v], fma(e1, af[NF * NV + v], Fj[v]));
     }
   }
-  __syncthreads();  // P and Q are read above; mu_N goes into P
-  double mu_c[NV];  // mu_{k+1} at this node
-  if (act) {
+  double gm[3] = {0.0, 0.0, 0.0}, gM[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  if (srcc) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      mu_c[v] = lq[v] * (1.0 / (N + 1));
-      P[j * NVP + v] = mu_c[v];
-    }
+    for (int a = 0; a < 6; ++a) gM[a] = -phi * dt * s_sbar * lam_j[3 + a];
   }
-  __syncthreads();
+  __syncthreads();  // lambda's stress sums are read by the neighbours below
 
-  // ---- reverse Taylor recursion --------------------------------------------------------------
+  // ---- reverse recursion on nu_k = lambda + mu_k ---------------------------------------------
+  // nu_{k+1} is read from Yin: the spare record at k = N, then alternately the record of a_0 and
+  // the spare one (a_0 is not read after the forward recursion).
+  double nu_c[NV];  // nu_{k+1} at this node
 #pragma unroll
-  for (int k = N - 1; k >= 0; --k) {
-    const double* Yin = ((N - 1 - k) & 1) ? Q : P;  // mu_{k+1}
-    double* Yout = ((N - 1 - k) & 1) ? P : Q;       // mu_k
+  for (int v = 0; v < NV; ++v) nu_c[v] = lam_j[v];
+#pragma unroll
+  for (int k = N; k >= 0; --k) {
+    const double* Yin = ((N - k) & 1) ? base : spare;
+    double* Yout = ((N - k) & 1) ? spare : base;
     if (act) {
-      const double f = dt * (1.0 / (k + 1));
+      // material: f_k nu_{k+1}^T (dL/dm) a_k, from P = f_k L a_k at this node
+      if (k < N) {
+        const double f = dt * (1.0 / (k + 1));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) P[v] = base[(k + 1) * REC + j * NVP + v];
+        if (srcc) {
+#pragma unroll
+          for (int a = 0; a < 6; ++a) {
+            P[3 + a] = fma(-f * s_sk[k], mphi[a], P[3 + a]);
+            // moment: f_k s_k mu_{k+1}^T (dg/dM), mu_{k+1} = nu_{k+1} - lambda
+            gM[a] = fma(-phi * f * s_sk[k], nu_c[3 + a] - lam_j[3 + a], gM[a]);
+          }
+        }
+      }
+      ck_dmat_R(P, nu_c, irho, lam, ik, imu, gm);
       double Tt[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) Tt[v] = 0.0;
       ck_apply_T<N>(Yin, j, DT, cf, Tt);
-      ck_dmat<N>(base + k * REC, j, Dr, ih, irho, mu_c, f, gm);
-      if (srcc) {
+      const double ik1 = 1.0 / (k + 1);
 #pragma unroll
-        for (int a = 0; a < 6; ++a) gM[a] = fma(f * s_sk[k], -phi * mu_c[3 + a], gM[a]);
-      }
+      for (int v = 0; v < NV; ++v) nu_c[v] = fma(fma(dt, Tt[v], Fj[v]), ik1, lam_j[v]);
+      if (k > 0) {
+        double* o = Yout + j * NVP;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        mu_c[v] = fma(f, Tt[v], lq[v] * (1.0 / (k + 1)));
-        if (k > 0) Yout[j * NVP + v] = mu_c[v];
+        for (int v = 0; v < NV; ++v) o[v] = nu_c[v];
+        o[9] = nu_c[3] + nu_c[4] + nu_c[5];
       }
     }
     if (k > 0) __syncthreads();
   }
-  // lambda^n = lambda^{n+1} + mu_0 (+ dJ/du^n), staged in a_0 for a coalesced store
-  bool bad = false;
-  __syncthreads();  // every thread is done reading a_0 (the last level of the reverse sweep)
+  // lambda^n = nu_0 (+ dJ/du^n), staged in the record of a_1 for a coalesced store (a_1 is last
+  // read at level 0, before the barrier below)
+  __syncthreads();
   if (act) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) base[j * NVP + v] = lam_j[v] + mu_c[v];
+    for (int v = 0; v < NV; ++v) base[REC + j * NVP + v] = nu_c[v];
   }
   __syncthreads();
+  bool bad = false;
   for (int e = tid; e < ncb * NL; e += TPB) {
     const int s = e / NL, r = e - s * NL;
-    double out = smem[(size_t)s * NBUF * REC + (r / NV) * NVP + r % NV];
+    double out = smem[(size_t)s * NBUF * REC + REC + (r / NV) * NVP + r % NV];
     if (J.dJdu) out += J.dJdu[c0 * NL + e];
     J.lam[c0 * NL + e] = out;
     bad |= !isfinite(out);
   }
   if (bad) atomicOr(&A.dev->status, ST_NONFINITE);
-  __syncthreads();
 
   // ---- gradients: per-node partial sums -> fixed-order sums per cell -------------------------
-  // per-node values staged in a_1 (or P at order 1) of each cell: [9][NS] (3 material, 6 moment)
-  double* red = base + (N > 1 ? REC : N * REC);
+  // per-node values staged in the spare record of each cell (last read in the reverse recursion,
+  // before the barrier that follows it): [9][NS]
+  double* red = spare;
   if (act) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) red[q * NS + j] = gm[q];

@@ -275,7 +275,8 @@ ader_status ader_adjoint_step(ader_ctx* ctx, double t_n, double dt, const double
  * Limits and behaviour:
  *  - The face adjoints (cells x 3 x 2 x n^2 x 9 doubles), the face gradients (6 doubles per
  *    face) and, with the Picard predictor, one iterate slab (order x (order+1) x n^3 x 9
- *    doubles) must fit in 64 MiB;
+ *    doubles), with the Cauchy-Kowalevski predictor lambda's face projections (2 x n^2 x 9
+ *    doubles per face), must fit in 64 MiB;
  *    otherwise ADER_EINVAL and nothing runs.  Fewer thread blocks are used when the slabs of all
  *    of them do not fit.
  *  - The array is shared by every call on a device and keeps the contents of the last call
@@ -287,8 +288,8 @@ ader_status ader_adjoint_step(ader_ctx* ctx, double t_n, double dt, const double
  *    device reset gets its own); make that first call before any stream capture begins.
  *  - Device-side errors (a non-finite adjoint or gradient) are returned by the next ader_sync,
  *    as for ader_adjoint_step.
- *  - The context's next-state and face buffers (allocated by ader_create) are overwritten, as in
- *    ader_adjoint_step. */
+ *  - The context's face buffer (and, with the Picard predictor, its next-state buffer), allocated
+ *    by ader_create, is overwritten, as in ader_adjoint_step. */
 ader_status ader_adjoint_step_static(ader_ctx* ctx, double t_n, double dt, const double* u_n,
                                      double* lam, const double* dJdu, double* grad_mat,
                                      double* grad_M);

@@ -92,7 +92,21 @@ struct LimArgs {
   double floor;          // physical admissibility: density and pressure above floor (0: positive)
   int first_order;       // FV recompute with zero slopes (the first-order fallback pass)
 };
-struct AdjArgs;
+
+// Arguments of the adjoint kernels of the linear elastic step.
+struct AdjArgs {
+  const double* u_n;     // forward state at t^n [C][NL]
+  double* lam;           // in: lambda^{n+1}; out: lambda^n  [C][NL]
+  const double* dJdu;    // optional dJ/du^n [C][NL]
+  double* grad_mat;      // [C][3] accumulated
+  double* grad_M;        // [6] accumulated
+  double* adjf;          // [C][3][2][NF][NV] adjoint of the face extrapolations
+  double* gface;         // [faces of all directions][2][3] material gradient of each face
+  double* scratch;       // [gridDim][I-1][n][NL] forward Picard iterates
+  long long scratch_per_block;
+  double* gproj;         // [faces of all directions][2][NF][NV] lambda's face projections
+                         // (Cauchy-Kowalevski adjoint; null otherwise)
+};
 
 // Ensemble of runs advanced together (one persistent launch per phase of the step for all runs):
 // prefix offsets of the runs' cells and faces in the concatenated work lists, and the offset of

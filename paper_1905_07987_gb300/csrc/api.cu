@@ -12,20 +12,6 @@
 #include "../../include/ader.h"
 #include "ader_internal.h"
 
-namespace ader {
-struct AdjArgs {
-  const double* u_n;
-  double* lam;
-  const double* dJdu;
-  double* grad_mat;
-  double* grad_M;
-  double* adjf;
-  double* gface;
-  double* scratch;
-  long long scratch_per_block;
-};
-}  // namespace ader
-
 using namespace ader;
 
 namespace {
@@ -978,8 +964,10 @@ ader_status ader_adjoint_step(ader_ctx* c, double t_n, double dt, const double* 
     cudaError_t e = cudaMalloc(&c->dev_adj, sizeof(DevScalars));
     if (e == cudaSuccess) e = cudaMalloc(&c->adjf, (size_t)c->g.ncells * 3 * 2 * c->nf * c->nvar * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&c->gface, (size_t)nfaces * 6 * sizeof(double));
-    if (e == cudaSuccess && !ck)
-      e = cudaMalloc(&c->adj_scratch, (size_t)c->adj_blocks * c->adj_spb * sizeof(double));
+    // Picard: the iterate slabs; Cauchy-Kowalevski: lambda's face projections
+    const size_t scratch = ck ? (size_t)nfaces * 2 * c->nf * c->nvar
+                              : (size_t)c->adj_blocks * c->adj_spb;
+    if (e == cudaSuccess) e = cudaMalloc(&c->adj_scratch, scratch * sizeof(double));
     if (e != cudaSuccess) {
       cudaGetLastError();
       cudaFree(c->dev_adj);
@@ -997,16 +985,16 @@ ader_status ader_adjoint_step(ader_ctx* c, double t_n, double dt, const double* 
   a.u = u_n;
   a.dev = c->dev_adj;
   a.iters = iters;
-  // forward face data of the step from u^n (the predictor also writes the scratch next state)
-  if (ck)
-    CUDA_OK(c->fam->predictor_ck(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
-  else
-    CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
-  AdjArgs j{u_n, lam, dJdu, grad_mat, grad_M, c->adjf, c->gface, c->adj_scratch, c->adj_spb};
-  if (ck)
+  if (ck) {
+    // the adjoint kernels form the forward face data themselves
+    AdjArgs j{u_n, lam, dJdu, grad_mat, grad_M, c->adjf, c->gface, nullptr, 0, c->adj_scratch};
     CUDA_OK(c->fam->adj_run_ck(a, j, c->tab, c->stream));
-  else
+  } else {
+    // forward face data of the step from u^n (the predictor also writes the scratch next state)
+    CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
+    AdjArgs j{u_n, lam, dJdu, grad_mat, grad_M, c->adjf, c->gface, c->adj_scratch, c->adj_spb};
     CUDA_OK(c->fam->adj_run(a, j, c->tab, c->adj_blocks, c->stream));
+  }
   // errors latched by the adjoint kernels reach the context's status word (ader_sync)
   CUDA_OK(launch_merge_status(c->dev_adj, c->dev, c->stream));
   return ADER_OK;
@@ -1099,15 +1087,17 @@ ader_status ader_adjoint_step_static(ader_ctx* c, double t_n, double dt, const d
   void* base = nullptr;
   CUDA_OK(static_array_address(&base));
   // layout: device scalars | face adjoints | face material gradients | per-block iterate slabs
+  // (Picard) or lambda's face projections (Cauchy-Kowalevski)
   const int iters = c->cfg.picard_iters > 0 ? c->cfg.picard_iters : c->cfg.order + 1;
   long long nfaces = 0;
   for (int d = 0; d < 3; ++d) nfaces += (long long)(c->g.n[d] + 1) * (c->g.ncells / c->g.n[d]);
   const size_t b_dev = round256(sizeof(DevScalars));
   const size_t b_adjf = round256((size_t)c->g.ncells * 3 * 2 * c->nf * c->nvar * sizeof(double));
   const size_t b_gface = round256((size_t)nfaces * 6 * sizeof(double));
-  // the Cauchy-Kowalevski adjoint keeps its cell in shared memory: no iterate slabs
+  // Picard: one iterate slab per thread block; Cauchy-Kowalevski: lambda's face projections
   const long long spb = ck ? 0 : c->fam->adj_scratch_per_block(c->cfg.order, iters);
-  const size_t b_slab = (size_t)spb * sizeof(double);
+  const size_t b_slab = ck ? (size_t)nfaces * 2 * c->nf * c->nvar * sizeof(double)
+                           : (size_t)spb * sizeof(double);
   const size_t fixed = b_dev + b_adjf + b_gface;
   if (fixed + b_slab > kStaticScratchBytes) return ADER_EINVAL;  // grid too large for the array
   long long blocks = 0;
@@ -1128,15 +1118,14 @@ ader_status ader_adjoint_step_static(ader_ctx* c, double t_n, double dt, const d
   a.u = u_n;
   a.dev = dev_s;
   a.iters = iters;
-  if (ck)
-    CUDA_OK(c->fam->predictor_ck(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
-  else
-    CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
-  AdjArgs j{u_n, lam, dJdu, grad_mat, grad_M, adjf, gface, slab, spb};
-  if (ck)
+  if (ck) {
+    AdjArgs j{u_n, lam, dJdu, grad_mat, grad_M, adjf, gface, nullptr, 0, slab};
     CUDA_OK(c->fam->adj_run_ck(a, j, c->tab, c->stream));
-  else
+  } else {
+    CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
+    AdjArgs j{u_n, lam, dJdu, grad_mat, grad_M, adjf, gface, slab, spb};
     CUDA_OK(c->fam->adj_run(a, j, c->tab, (int)blocks, c->stream));
+  }
   // errors latched in the array's scalars reach the context's status word (ader_sync), and the
   // scalars start the next call clear
   CUDA_OK(launch_merge_status(dev_s, c->dev, c->stream));

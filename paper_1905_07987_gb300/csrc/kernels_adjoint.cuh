@@ -1,4 +1,4 @@
-// Adjoint of the linear-elastic ADER-DG step (the "differentiation" pattern grown onto Sec. 3.3).
+// Adjoint of the linear-elastic ADER-DG step (Sec. 3.3), for gradients of a receiver misfit.
 //
 // With a fixed dt the step is affine, u^{n+1} = A(m) u^n + b^n(M, m).  One adjoint step maps
 // lambda^{n+1} -> lambda^n = A^T lambda^{n+1} (+ dJ/du^n) and accumulates the material gradient
@@ -11,22 +11,12 @@
 //                  predictor (kept in a per-block global scratch slab), then the adjoint of the
 //                  volume term, of the face extrapolation, and of the Picard iteration in reverse.
 // The forward face data q_bar of the step are recomputed by the forward predictor kernel first.
+// With the Cauchy-Kowalevski predictor (kernels_adjoint_ck.cuh) k_adj_riemann runs in two halves
+// around the cell kernel, which forms the forward face data itself.
 #pragma once
 #include "kernels.cuh"
 
 namespace ader {
-
-struct AdjArgs {
-  const double* u_n;     // forward state at t^n [C][NL]
-  double* lam;           // in: lambda^{n+1}; out: lambda^n  [C][NL]
-  const double* dJdu;    // optional dJ/du^n [C][NL]
-  double* grad_mat;      // [C][3] accumulated
-  double* grad_M;        // [6] accumulated
-  double* adjf;          // [C][3][2][NF][NV] adjoint of the face extrapolations
-  double* gface;         // [faces of all directions][2][3] material gradient of each face
-  double* scratch;       // [gridDim][I-1][n][NL] forward Picard iterates
-  long long scratch_per_block;
-};
 
 // Rows r of B_d whose single non-zero sits in column k (B_d^T has these entries in row k).
 struct RowsT {
@@ -58,7 +48,11 @@ __device__ __forceinline__ void dcoef(int d, int v, double rho, double* g) {
   }
 }
 
-template <int D, int N>
+// MODE 0: the whole face adjoint (the Picard form).  The Cauchy-Kowalevski form splits it around
+// its cell kernel, which produces the forward face data: MODE 1 writes the face adjoints (they
+// need lambda and the material only) and keeps lambda's face projections gL, gR in J.gproj;
+// MODE 2 forms the face material gradient from those projections and the forward face data.
+template <int D, int N, int MODE = 0>
 __global__ void __launch_bounds__(128) k_adj_riemann(const __grid_constant__ StepArgs A,
                                                      const __grid_constant__ AdjArgs J,
                                                      const __grid_constant__ Tables T, int d,
@@ -77,9 +71,10 @@ __global__ void __launch_bounds__(128) k_adj_riemann(const __grid_constant__ Ste
   const bool periodic = (g.bc[d][0] == BC_PERIODIC);
   double* gf = J.gface + (gface_off + f) * 6;
   if (periodic && kf == nd) {
-    if (lane < 6) gf[lane] = 0.0;
+    if (MODE != 1 && lane < 6) gf[lane] = 0.0;
     return;
   }
+  double* gp = MODE ? J.gproj + (gface_off + f) * (long long)(2 * NF * NV) : nullptr;
   long long cL = -1, cR = -1;
   if (kf > 0) cL = FaceIdx::cell_of(g, tr, d, kf - 1);
   else if (periodic) cL = FaceIdx::cell_of(g, tr, d, nd - 1);
@@ -116,45 +111,63 @@ __global__ void __launch_bounds__(128) k_adj_riemann(const __grid_constant__ Ste
     double gL[NV], gR[NV], qL[NV], qR[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      double aL = 0.0, aR = 0.0;
-      if (cL >= 0) {
-        const double* lam = J.lam + cL * NL;
+      if (MODE == 2) {
+        gL[v] = gp[jp * NV + v];
+        gR[v] = gp[NF * NV + jp * NV + v];
+      } else {
+        double aL = 0.0, aR = 0.0;
+        if (cL >= 0) {
+          const double* lam = J.lam + cL * NL;
 #pragma unroll
-        for (int m = 0; m < n; ++m) aL = fma(T.c1[m], lam[(jbase + m * st) * NV + v], aL);
+          for (int m = 0; m < n; ++m) aL = fma(T.c1[m], lam[(jbase + m * st) * NV + v], aL);
+        }
+        if (cR >= 0) {
+          const double* lam = J.lam + cR * NL;
+#pragma unroll
+          for (int m = 0; m < n; ++m) aR = fma(T.c0[m], lam[(jbase + m * st) * NV + v], aR);
+        }
+        gL[v] = -dt * A.g.inv_h[d] * aL;
+        gR[v] = dt * A.g.inv_h[d] * aR;
       }
-      if (cR >= 0) {
-        const double* lam = J.lam + cR * NL;
-#pragma unroll
-        for (int m = 0; m < n; ++m) aR = fma(T.c0[m], lam[(jbase + m * st) * NV + v], aR);
+      if (MODE != 1) {
+        qL[v] = cL >= 0 ? A.face[cL * (long long)(3 * 2 * FR) + (d * 2 + 1) * FR + jp * NV + v] : 0.0;
+        qR[v] = cR >= 0 ? A.face[cR * (long long)(3 * 2 * FR) + (d * 2 + 0) * FR + jp * NV + v] : 0.0;
       }
-      gL[v] = -dt * A.g.inv_h[d] * aL;
-      gR[v] = dt * A.g.inv_h[d] * aR;
-      qL[v] = cL >= 0 ? A.face[cL * (long long)(3 * 2 * FR) + (d * 2 + 1) * FR + jp * NV + v] : 0.0;
-      qR[v] = cR >= 0 ? A.face[cR * (long long)(3 * 2 * FR) + (d * 2 + 0) * FR + jp * NV + v] : 0.0;
     }
-    // adjoint of dq = qR - qL:  dqh = -s/2 (gL + gR) + 1/2 Bbar^T (gL - gR)
-    double dqh[NV];
+    if (MODE != 2) {
+      // adjoint of dq = qR - qL:  dqh = -s/2 (gL + gR) + 1/2 Bbar^T (gL - gR)
+      double dqh[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) dqh[k] = -0.5 * s * (gL[k] + gR[k]);
+      for (int k = 0; k < NV; ++k) dqh[k] = -0.5 * s * (gL[k] + gR[k]);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const int sv = Elastic::src(d, v);
-      if (sv >= 0) dqh[sv] += 0.5 * cb[v] * (gL[v] - gR[v]);
+      for (int v = 0; v < NV; ++v) {
+        const int sv = Elastic::src(d, v);
+        if (sv >= 0) dqh[sv] += 0.5 * cb[v] * (gL[v] - gR[v]);
+      }
+      if (cL >= 0)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) J.adjf[((cL * 3 + d) * 2 + 1) * (long long)(NF * NV) + jp * NV + v] = -dqh[v];
+      if (cR >= 0)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) J.adjf[((cR * 3 + d) * 2 + 0) * (long long)(NF * NV) + jp * NV + v] = dqh[v];
     }
+    if (MODE == 1) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const double dq = qR[v] - qL[v];
-      S1 = fma(dq, gL[v] + gR[v], S1);
-      const int sv = Elastic::src(d, v);
-      if (sv >= 0) S2[v] = fma(qR[sv] - qL[sv], gL[v] - gR[v], S2[v]);
+      for (int v = 0; v < NV; ++v) {
+        gp[jp * NV + v] = gL[v];
+        gp[NF * NV + jp * NV + v] = gR[v];
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const double dq = qR[v] - qL[v];
+        S1 = fma(dq, gL[v] + gR[v], S1);
+        const int sv = Elastic::src(d, v);
+        if (sv >= 0) S2[v] = fma(qR[sv] - qL[sv], gL[v] - gR[v], S2[v]);
+      }
     }
-    if (cL >= 0)
-#pragma unroll
-      for (int v = 0; v < NV; ++v) J.adjf[((cL * 3 + d) * 2 + 1) * (long long)(NF * NV) + jp * NV + v] = -dqh[v];
-    if (cR >= 0)
-#pragma unroll
-      for (int v = 0; v < NV; ++v) J.adjf[((cR * 3 + d) * 2 + 0) * (long long)(NF * NV) + jp * NV + v] = dqh[v];
   }
+  if (MODE == 1) return;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     S1 += __shfl_xor_sync(0xffffffffu, S1, o);

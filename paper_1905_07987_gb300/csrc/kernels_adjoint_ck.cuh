@@ -23,6 +23,11 @@
 // gamma_v = R_v / mu.  For k < N, f_k L a_k = a_{k+1} - f_k s_k g is already at hand; L a_N costs
 // one application.
 //
+// The forward face data the face terms' material gradient needs come from this kernel too (qbar
+// and its extrapolations, as the predictor forms them): the face adjoints, which need lambda and
+// the material only, run before it (k_adj_riemann MODE 1), the face material gradients after it
+// (MODE 2), so no forward predictor launch precedes the adjoint.
+//
 // One thread per node, the cells of a block (several at low order) each keep a_0 .. a_N in
 // shared memory ((N+2) padded records of 10 doubles per node; the record of a_0 and a spare one
 // hold the adjoint nu during the reverse sweep, the tenth double of a nu record its sum
@@ -114,7 +119,7 @@ __device__ __forceinline__ void ck_dmat_R(const double (&P)[9], const double (&n
 template <int N>
 __global__ void __launch_bounds__(CfgCKA<N>::TPB)
     k_adj_cell_ck(const __grid_constant__ StepArgs A, const __grid_constant__ AdjArgs J,
-                  const __grid_constant__ Tables T, long long off1, long long off2) {
+                  const __grid_constant__ Tables T) {
   using C = CfgCKA<N>;
   constexpr int n = C::n, NS = C::NS, NV = C::NV, NL = C::NL, NVP = C::NVP, CPB = C::CPB;
   constexpr int TPB = C::TPB, REC = C::REC, NF = C::NF, NBUF = C::NBUF;
@@ -211,6 +216,43 @@ __global__ void __launch_bounds__(CfgCKA<N>::TPB)
       for (int v = 0; v < NV; ++v) base[(k + 1) * REC + j * NVP + v] = f * R[v];
     }
     __syncthreads();
+  }
+  // forward face data of the step (the predictor's epilogue): qbar = sum_k a_k / (k+1) at this
+  // node, summed in the predictor's order, into the record of a_0 (each thread reads and writes
+  // its own node only), then extrapolated to both ends of every direction
+  if (act) {
+    double qb[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) qb[v] = base[j * NVP + v];
+#pragma unroll
+    for (int k = 1; k <= N; ++k) {
+      const double wk = 1.0 / (k + 1);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) qb[v] = fma(wk, base[k * REC + j * NVP + v], qb[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) base[j * NVP + v] = qb[v];
+  }
+  __syncthreads();
+  for (int e = tid; e < ncb * NF * NV; e += TPB) {
+    const int s = e / (NF * NV), r = e - s * (NF * NV);
+    const int v = r % NV, jp = r / NV;
+    const double* Xs = smem + (size_t)s * NBUF * REC;
+    double* fc = A.face + (c0 + s) * (3 * 2 * NF * NV) + jp * NV + v;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int st = (d == 0 ? 1 : (d == 1 ? n : n * n));
+      const int jbase = (jp % st) + (jp / st) * st * n;
+      double q0 = 0.0, q1 = 0.0;
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        const double x = Xs[(jbase + m * st) * NVP + v];
+        q0 = fma(T.e0[m], x, q0);
+        q1 = fma(T.e1[m], x, q1);
+      }
+      fc[(d * 2 + 0) * NF * NV] = q0;
+      fc[(d * 2 + 1) * NF * NV] = q1;
+    }
   }
   double P[NV];  // f_k L a_k at this node, for the level being reversed
   double lam_j[NV], Fj[NV];
@@ -326,26 +368,39 @@ __global__ void __launch_bounds__(CfgCKA<N>::TPB)
     s_sum[slot][q] = s;
   }
   __syncthreads();
+  // the cell's own material gradient (its faces' share follows in k_adj_face_sum)
   if (act && j == 0) {
-    double tot[3] = {s_sum[slot][0], s_sum[slot][1], s_sum[slot][2]};
-    // the cell's faces: its left face (the cell is R there) and right face (the cell is L)
-    for (int d = 0; d < 3; ++d) {
-      int id;
-      const long long trc = FaceIdx::trans_of_cell(A.g, c, d, id);
-      const int nd = A.g.n[d];
-      int kr = id + 1;
-      if (kr == nd && A.g.bc[d][1] == BC_PERIODIC) kr = 0;
-      const long long off = d == 0 ? 0 : (d == 1 ? off1 : off2);
-      const double* gl = J.gface + (off + id + (long long)(nd + 1) * trc) * 6;
-      const double* gr = J.gface + (off + kr + (long long)(nd + 1) * trc) * 6;
-      for (int q = 0; q < 3; ++q) tot[q] += gl[3 + q] + gr[q];
-    }
-    for (int q = 0; q < 3; ++q) J.grad_mat[c * 3 + q] += tot[q];
-    if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2]))
+    for (int q = 0; q < 3; ++q) J.grad_mat[c * 3 + q] += s_sum[slot][q];
+    if (!isfinite(s_sum[slot][0]) || !isfinite(s_sum[slot][1]) || !isfinite(s_sum[slot][2]))
       atomicOr(&A.dev->status, ST_NONFINITE);
     if (srcc)
       for (int q = 0; q < 6; ++q) J.grad_M[q] += s_sum[slot][3 + q];
   }
+}
+
+// grad_mat[c] += the material gradient of the cell's six faces (its left face, where the cell is
+// R, and its right face, where it is L, per direction): one thread per cell, fixed order.
+template <int N>
+__global__ void __launch_bounds__(256) k_adj_face_sum(const __grid_constant__ StepArgs A,
+                                                      const __grid_constant__ AdjArgs J,
+                                                      long long off1, long long off2) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= A.g.ncells) return;
+  double tot[3] = {0.0, 0.0, 0.0};
+  for (int d = 0; d < 3; ++d) {
+    int id;
+    const long long trc = FaceIdx::trans_of_cell(A.g, c, d, id);
+    const int nd = A.g.n[d];
+    int kr = id + 1;
+    if (kr == nd && A.g.bc[d][1] == BC_PERIODIC) kr = 0;
+    const long long off = d == 0 ? 0 : (d == 1 ? off1 : off2);
+    const double* gl = J.gface + (off + id + (long long)(nd + 1) * trc) * 6;
+    const double* gr = J.gface + (off + kr + (long long)(nd + 1) * trc) * 6;
+    for (int q = 0; q < 3; ++q) tot[q] += gl[3 + q] + gr[q];
+  }
+  for (int q = 0; q < 3; ++q) J.grad_mat[c * 3 + q] += tot[q];
+  if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2]))
+    atomicOr(&A.dev->status, ST_NONFINITE);
 }
 
 template <int N>
@@ -368,16 +423,33 @@ struct AdjLaunchCK {
       offs[d] = off;
       off += (long long)(a.g.n[d] + 1) * (a.g.ncells / a.g.n[d]);
     }
+    // face adjoints (lambda's face projections kept) -> cell kernel (forward face data out) ->
+    // face material gradients -> their sums per cell
     for (int d = 0; d < 3; ++d) {
       const long long nf = (long long)(a.g.n[d] + 1) * (a.g.ncells / a.g.n[d]);
-      k_adj_riemann<3, N><<<(unsigned)((nf + 3) / 4), 128, 0, s>>>(a, j, t, d, offs[d]);
+      k_adj_riemann<3, N, 1><<<(unsigned)((nf + 3) / 4), 128, 0, s>>>(a, j, t, d, offs[d]);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
     const long long blocks = (a.g.ncells + C::CPB - 1) / C::CPB;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_adj_cell_ck<N><<<(unsigned)blocks, C::TPB, C::SMEM, s>>>(a, j, t, offs[1], offs[2]);
+    k_adj_cell_ck<N><<<(unsigned)blocks, C::TPB, C::SMEM, s>>>(a, j, t);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    for (int d = 0; d < 3; ++d) {
+      const long long nf = (long long)(a.g.n[d] + 1) * (a.g.ncells / a.g.n[d]);
+      k_adj_riemann<3, N, 2><<<(unsigned)((nf + 3) / 4), 128, 0, s>>>(a, j, t, d, offs[d]);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    k_adj_face_sum<N><<<(unsigned)((a.g.ncells + 255) / 256), 256, 0, s>>>(a, j, offs[1], offs[2]);
     return cudaGetLastError();
+  }
+  // doubles of lambda's face projections (J.gproj)
+  static long long gproj_doubles(const Geometry& g) {
+    long long nfaces = 0;
+    for (int d = 0; d < 3; ++d) nfaces += (long long)(g.n[d] + 1) * (g.ncells / g.n[d]);
+    return nfaces * 2 * CfgCKA<N>::NF * 9;
   }
 };
 

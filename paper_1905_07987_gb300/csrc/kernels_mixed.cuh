@@ -1,4 +1,4 @@
-// Mixed-precision space-time predictor (the "precision" pattern grown onto Eq. (5)).
+// Mixed-precision space-time predictor (Eq. (5)): binary32 increments around float-float base terms.
 //
 // The predictor is solved for the increment dq = q - u^n, which is O(dt) small:
 //   dq^{r+1} = dt Kw [ B0 + dR(dq^r) ],   B0 = R(u^n),   dR(dq) = R(u^n + dq) - R(u^n)

@@ -52,11 +52,13 @@ __device__ __forceinline__ void dcoef(int d, int v, double rho, double* g) {
 // its cell kernel, which produces the forward face data: MODE 1 writes the face adjoints (they
 // need lambda and the material only) and keeps lambda's face projections gL, gR in J.gproj;
 // MODE 2 forms the face material gradient from those projections and the forward face data.
-template <int D, int N, int MODE = 0>
+// DIR: the face normal (a template parameter, so that every row index of B_d is a constant).
+template <int D, int N, int MODE, int DIR>
 __global__ void __launch_bounds__(128) k_adj_riemann(const __grid_constant__ StepArgs A,
                                                      const __grid_constant__ AdjArgs J,
-                                                     const __grid_constant__ Tables T, int d,
+                                                     const __grid_constant__ Tables T,
                                                      long long gface_off) {
+  constexpr int d = DIR;
   using C = Cfg<Elastic, 3, N>;
   constexpr int n = C::n, NV = 9, NF = C::NF, FR = C::FR, NL = C::NL;
   constexpr int PER = (NF + 31) / 32;
@@ -174,30 +176,48 @@ __global__ void __launch_bounds__(128) k_adj_riemann(const __grid_constant__ Ste
 #pragma unroll
     for (int v = 0; v < NV; ++v) S2[v] += __shfl_xor_sync(0xffffffffu, S2[v], o);
   }
+  // d/dm of  -1/2 s S1 + 1/2 sum_v cb[v] S2[v] (every lane holds S1 and S2 after the reduction):
+  // lane q < 27 takes the term (v, gq) = (q / 3, q % 3) of the path average, lane 0 also the wave
+  // speed; the six partial sums are then reduced over the warp
+  double gLm[3] = {0.0, 0.0, 0.0}, gRm[3] = {0.0, 0.0, 0.0};
   if (lane == 0) {
-    // d/dm of  -1/2 s S1 + 1/2 sum_v cb[v] S2[v]
-    double gLm[3] = {0, 0, 0}, gRm[3] = {0, 0, 0};
     // wave speed: vp = sqrt((lam + 2 mu) / rho)
-    {
-      const double sr = left_max ? rL : rR, sv = s;
-      const double dv[3] = {-sv / (2.0 * sr), 1.0 / (2.0 * sr * sv), 1.0 / (sr * sv)};
-      double* dst = left_max ? gLm : gRm;
-      for (int k = 0; k < 3; ++k) dst[k] += -0.5 * S1 * dv[k];
+    const double sr = left_max ? rL : rR, sv = s;
+    const double dv[3] = {-sv / (2.0 * sr), 1.0 / (2.0 * sr * sv), 1.0 / (sr * sv)};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (left_max) gLm[k] = -0.5 * S1 * dv[k];
+      else gRm[k] = -0.5 * S1 * dv[k];
     }
-    for (int v = 0; v < NV; ++v) {
-      if (Elastic::src(d, v) < 0) continue;
-      for (int gq = 0; gq < 3; ++gq) {
-        const double z = T.pz[gq];
-        const double rho = fma(z, rR - rL, rL);
-        double dc[3];
-        dcoef(d, v, rho, dc);
-        for (int k = 0; k < 3; ++k) {
-          const double w = 0.5 * S2[v] * T.pw[gq] * dc[k];
-          gLm[k] += w * (1.0 - z);
-          gRm[k] += w * z;
-        }
+  }
+  if (lane < 27) {
+    const int v = lane / 3, gq = lane % 3;
+    if (Elastic::src(d, v) >= 0) {
+      double s2 = 0.0;  // S2[v] selected without a dynamically indexed array
+#pragma unroll
+      for (int u = 0; u < NV; ++u)
+        if (u == v) s2 = S2[u];
+      const double z = T.pz[gq];
+      const double rho = fma(z, rR - rL, rL);
+      double dc[3];
+      dcoef(d, v, rho, dc);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double w = 0.5 * s2 * T.pw[gq] * dc[k];
+        gLm[k] = fma(w, 1.0 - z, gLm[k]);
+        gRm[k] = fma(w, z, gRm[k]);
       }
     }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      gLm[k] += __shfl_xor_sync(0xffffffffu, gLm[k], o);
+      gRm[k] += __shfl_xor_sync(0xffffffffu, gRm[k], o);
+    }
+  }
+  if (lane == 0) {
     // ghost side: the exterior material is the interior one
     if (cL < 0) for (int k = 0; k < 3; ++k) { gRm[k] += gLm[k]; gLm[k] = 0.0; }
     if (cR < 0) for (int k = 0; k < 3; ++k) { gLm[k] += gRm[k]; gRm[k] = 0.0; }
@@ -206,6 +226,18 @@ __global__ void __launch_bounds__(128) k_adj_riemann(const __grid_constant__ Ste
       gf[3 + k] = gRm[k];
     }
   }
+}
+
+// The faces of direction d (one warp per face, 4 per block).
+template <int N, int MODE>
+cudaError_t launch_adj_riemann(const StepArgs& a, const AdjArgs& j, const Tables& t, int d,
+                               long long gface_off, cudaStream_t s) {
+  const long long nf = (long long)(a.g.n[d] + 1) * (a.g.ncells / a.g.n[d]);
+  const unsigned grid = (unsigned)((nf + 3) / 4);
+  if (d == 0) k_adj_riemann<3, N, MODE, 0><<<grid, 128, 0, s>>>(a, j, t, gface_off);
+  else if (d == 1) k_adj_riemann<3, N, MODE, 1><<<grid, 128, 0, s>>>(a, j, t, gface_off);
+  else k_adj_riemann<3, N, MODE, 2><<<grid, 128, 0, s>>>(a, j, t, gface_off);
+  return cudaGetLastError();
 }
 
 template <int N>
@@ -528,9 +560,7 @@ struct AdjLaunch {
       off += (long long)(a.g.n[d] + 1) * (a.g.ncells / a.g.n[d]);
     }
     for (int d = 0; d < 3; ++d) {
-      const long long nf = (long long)(a.g.n[d] + 1) * (a.g.ncells / a.g.n[d]);
-      k_adj_riemann<3, N><<<(unsigned)((nf + 3) / 4), 128, 0, s>>>(a, j, t, d, offs[d]);
-      cudaError_t e = cudaGetLastError();
+      cudaError_t e = launch_adj_riemann<N, 0>(a, j, t, d, offs[d], s);
       if (e != cudaSuccess) return e;
     }
     k_adj_cell<N><<<blocks, C::TPB, CfgA<N>::SMEM, s>>>(a, j, t, offs[1], offs[2]);

@@ -426,9 +426,7 @@ struct AdjLaunchCK {
     // face adjoints (lambda's face projections kept) -> cell kernel (forward face data out) ->
     // face material gradients -> their sums per cell
     for (int d = 0; d < 3; ++d) {
-      const long long nf = (long long)(a.g.n[d] + 1) * (a.g.ncells / a.g.n[d]);
-      k_adj_riemann<3, N, 1><<<(unsigned)((nf + 3) / 4), 128, 0, s>>>(a, j, t, d, offs[d]);
-      cudaError_t e = cudaGetLastError();
+      cudaError_t e = launch_adj_riemann<N, 1>(a, j, t, d, offs[d], s);
       if (e != cudaSuccess) return e;
     }
     const long long blocks = (a.g.ncells + C::CPB - 1) / C::CPB;
@@ -437,9 +435,7 @@ struct AdjLaunchCK {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     for (int d = 0; d < 3; ++d) {
-      const long long nf = (long long)(a.g.n[d] + 1) * (a.g.ncells / a.g.n[d]);
-      k_adj_riemann<3, N, 2><<<(unsigned)((nf + 3) / 4), 128, 0, s>>>(a, j, t, d, offs[d]);
-      e = cudaGetLastError();
+      e = launch_adj_riemann<N, 2>(a, j, t, d, offs[d], s);
       if (e != cudaSuccess) return e;
     }
     k_adj_face_sum<N><<<(unsigned)((a.g.ncells + 255) / 256), 256, 0, s>>>(a, j, offs[1], offs[2]);

@@ -252,8 +252,11 @@ ader_status ader_run_graph(ader_ctx* ctx, int steps, int replays, double dt, dou
  *     lambda^n = A(m)^T lambda^{n+1} + dJdu   (in place in `lam`)
  * and accumulates  grad_mat[c][0..2] += d/d(rho, lambda, mu)_c of (lambda^{n+1})^T u^{n+1}  and
  * grad_M[0..5] += d/dM of the same, evaluated at the forward state u_n = u^n with the step
- * starting at time t_n, for the FP64 step of the context's predictor (a MIXED context gets the
- * adjoint of its FP64 step).  The wave speed max(vp_L, vp_R) of a face takes the left value at
+ * starting at time t_n.  With the Picard predictor this is the adjoint of the FP64 step (a MIXED
+ * context too).  With the Cauchy-Kowalevski predictor an FP64 context gets the adjoint of its
+ * FP64 step, a MIXED or TF32X3 context a mixed-precision adjoint: the base term F + dt L^T lambda
+ * in float-float, the level corrections dt L^T mu in binary32, lambda + mu_0 in FP64 (within a
+ * few binary32 roundoffs, relative to the largest value, of the FP64 adjoint).  The wave speed max(vp_L, vp_R) of a face takes the left value at
  * ties.  The gradient sums are formed in a fixed order: repeated calls give identical bits.
  * All pointers are device memory of the context's device ([cells][nodes][9] for u_n, lam, dJdu;
  * [cells][3]; [6]); dJdu may be NULL.  Uses the context's material, point source and order; the

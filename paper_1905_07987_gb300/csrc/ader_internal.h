@@ -196,8 +196,10 @@ struct Family {
   cudaError_t (*adj_run)(const StepArgs&, const AdjArgs&, const Tables&, int blocks, cudaStream_t);
   long long (*adj_scratch_per_block)(int order, int iters);
   int (*adj_blocks_per_sm)(int order);
-  // adjoint of the step with the Cauchy-Kowalevski predictor (no global scratch)
-  cudaError_t (*adj_run_ck)(const StepArgs&, const AdjArgs&, const Tables&, cudaStream_t);
+  // adjoint of the step with the Cauchy-Kowalevski predictor (prec 0: FP64; otherwise the
+  // mixed-precision adjoint of a mixed forward step)
+  cudaError_t (*adj_run_ck)(const StepArgs&, const AdjArgs&, const Tables&, const TablesF&,
+                            int prec, cudaStream_t);
   // one step of every run of an ensemble (fixed dt, no limiter, no receivers); runs: the runs'
   // step arguments of this step in device memory; null when the family has no batched path
   cudaError_t (*ens_step)(const StepArgs* runs, const EnsTable& E, const Tables& t,

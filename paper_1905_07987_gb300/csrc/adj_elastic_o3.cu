@@ -1,6 +1,6 @@
 // Adjoint kernels of the elastic step (Picard and Cauchy-Kowalevski predictors), order 3
 // (own translation unit to keep builds parallel).
-#include "kernels_adjoint_ck.cuh"
+#include "kernels_adjoint_ck_mixed.cuh"
 
 namespace ader {
 template <>
@@ -14,5 +14,10 @@ int adj_bps_n<3>() { return AdjLaunch<3>::blocks_per_sm(); }
 template <>
 cudaError_t adj_run_ck_n<3>(const StepArgs& a, const AdjArgs& j, const Tables& t, cudaStream_t s) {
   return AdjLaunchCK<3>::run(a, j, t, s);
+}
+template <>
+cudaError_t adj_run_ck_mixed_n<3>(const StepArgs& a, const AdjArgs& j, const Tables& t,
+                                  const TablesF& f, cudaStream_t s) {
+  return AdjLaunchCKM<3>::run(a, j, t, f, s);
 }
 }  // namespace ader

@@ -988,7 +988,7 @@ ader_status ader_adjoint_step(ader_ctx* c, double t_n, double dt, const double* 
   if (ck) {
     // the adjoint kernels form the forward face data themselves
     AdjArgs j{u_n, lam, dJdu, grad_mat, grad_M, c->adjf, c->gface, nullptr, 0, c->adj_scratch};
-    CUDA_OK(c->fam->adj_run_ck(a, j, c->tab, c->stream));
+    CUDA_OK(c->fam->adj_run_ck(a, j, c->tab, c->tabf, c->cfg.precision, c->stream));
   } else {
     // forward face data of the step from u^n (the predictor also writes the scratch next state)
     CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
@@ -1120,7 +1120,7 @@ ader_status ader_adjoint_step_static(ader_ctx* c, double t_n, double dt, const d
   a.iters = iters;
   if (ck) {
     AdjArgs j{u_n, lam, dJdu, grad_mat, grad_M, adjf, gface, nullptr, 0, slab};
-    CUDA_OK(c->fam->adj_run_ck(a, j, c->tab, c->stream));
+    CUDA_OK(c->fam->adj_run_ck(a, j, c->tab, c->tabf, c->cfg.precision, c->stream));
   } else {
     CUDA_OK(c->fam->predictor(a, c->tab, c->tabf, ADER_PREC_FP64, c->stream));
     AdjArgs j{u_n, lam, dJdu, grad_mat, grad_M, adjf, gface, slab, spb};

@@ -24,6 +24,9 @@ template <int N>
 int adj_bps_n();
 template <int N>
 cudaError_t adj_run_ck_n(const StepArgs& a, const AdjArgs& j, const Tables& t, cudaStream_t s);
+template <int N>
+cudaError_t adj_run_ck_mixed_n(const StepArgs& a, const AdjArgs& j, const Tables& t,
+                               const TablesF& f, cudaStream_t s);
 namespace {
 cudaError_t adj_run(const StepArgs& a, const AdjArgs& j, const Tables& t, int blocks, cudaStream_t s) {
   switch (a.g.order) {
@@ -35,7 +38,19 @@ cudaError_t adj_run(const StepArgs& a, const AdjArgs& j, const Tables& t, int bl
   }
   return cudaErrorInvalidValue;
 }
-cudaError_t adj_run_ck(const StepArgs& a, const AdjArgs& j, const Tables& t, cudaStream_t s) {
+// prec: 0 the FP64 adjoint; otherwise the mixed-precision one
+cudaError_t adj_run_ck(const StepArgs& a, const AdjArgs& j, const Tables& t, const TablesF& f,
+                       int prec, cudaStream_t s) {
+  if (prec != 0) {
+    switch (a.g.order) {
+      case 1: return adj_run_ck_mixed_n<1>(a, j, t, f, s);
+      case 2: return adj_run_ck_mixed_n<2>(a, j, t, f, s);
+      case 3: return adj_run_ck_mixed_n<3>(a, j, t, f, s);
+      case 4: return adj_run_ck_mixed_n<4>(a, j, t, f, s);
+      case 5: return adj_run_ck_mixed_n<5>(a, j, t, f, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (a.g.order) {
     case 1: return adj_run_ck_n<1>(a, j, t, s);
     case 2: return adj_run_ck_n<2>(a, j, t, s);

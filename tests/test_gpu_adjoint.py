@@ -123,14 +123,16 @@ def test_nonfinite_forward_state_is_reported(static):
     c.ctx.sync()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("order,ncell", [(4, (5, 4, 3)), (2, (7, 3, 5)), (3, (3, 5, 4))])
-def test_ck_adjoint_static_and_repeatable(order, ncell):
+def test_ck_adjoint_static_and_repeatable(order, ncell, precision):
     """The Cauchy-Kowalevski adjoint through both entry points (work memory allocated by the
     context, and the fixed device array) gives identical bits, and so does a repeated call
     (fixed-order reductions); several cells per block at orders 2-3 with a ragged last block."""
     mat = synth.elastic_material(ncell, seed=7)
     hi = tuple(0.5 * n for n in ncell)
-    c = Case("elastic", 3, order, ncell, hi=hi, bc="absorbing", material=mat, predictor="ck")
+    c = Case("elastic", 3, order, ncell, hi=hi, bc="absorbing", material=mat, predictor="ck",
+             precision=precision)
     c.point_source(tuple(0.61 * h for h in hi), synth.moment_tensor(seed=4), 2.0, 0.5)
     rng = np.random.default_rng(11)
     u_n = torch.from_numpy(rng.standard_normal(c.shape).reshape(-1)).cuda()
@@ -149,6 +151,42 @@ def test_ck_adjoint_static_and_repeatable(order, ncell):
             assert torch.equal(a, b)
     lam_ref, gm_ref, gM_ref = step_vjp(c.oracle, torch.from_numpy(u_n.cpu().numpy().reshape(c.shape)),
                                        torch.from_numpy(lam0.cpu().numpy().reshape(c.shape)), dt, 0.31)
-    assert rel_linf(outs[0][0].numpy().reshape(c.shape), lam_ref.numpy()) <= 1e-12
-    assert close(outs[0][1].numpy(), gm_ref.numpy())
-    assert close(outs[0][2].numpy(), gM_ref.numpy())
+    tol = 1e-12 if precision == "fp64" else MIXED_TOL
+    assert rel_linf(outs[0][0].numpy().reshape(c.shape), lam_ref.numpy()) <= tol
+    assert close(outs[0][1].numpy(), gm_ref.numpy(), tol)
+    assert close(outs[0][2].numpy(), gM_ref.numpy(), tol)
+
+
+# Mixed-precision CK adjoint against the FP64 derivative: the binary32 parts are the level
+# corrections dt L^T mu_{k+1} (unit roundoff 6e-8 times |dt L^T| |mu|, and |mu| <= |dt L^T| |lambda|
+# + |F|) and the pairings of the levels k >= 1.  On these random (not smooth) states |dt L^T| is
+# O(1) rather than O(CFL), so the bound is a few unit roundoffs of binary32 relative to the
+# largest value: 2e-6 leaves room for the N levels and the sums over nodes.
+MIXED_TOL = 2e-6
+
+
+@pytest.mark.parametrize("order,bc,ncell", CASES)
+def test_mixed_ck_adjoint_step_close_to_oracle(order, bc, ncell):
+    """The mixed-precision adjoint of a mixed CK context against the oracle's FP64 derivative of
+    the CK step (the tolerance above)."""
+    mat = synth.elastic_material(ncell, seed=order + 10)
+    hi = tuple(0.5 * n for n in ncell)
+    c = Case("elastic", 3, order, ncell, hi=hi, bc=bc, material=mat, predictor="ck",
+             precision="mixed")
+    c.point_source(tuple(0.37 * h for h in hi), synth.moment_tensor(seed=2), 2.0, 0.5)
+    rng = np.random.default_rng(order)
+    u_n = rng.standard_normal(c.shape)
+    lam = rng.standard_normal(c.shape)
+    dt = 0.7 * float(c.oracle.cfl_dt(torch.from_numpy(u_n)))
+    t_n = 0.43
+    lam_ref, gm_ref, gM_ref = step_vjp(c.oracle, torch.from_numpy(u_n), torch.from_numpy(lam), dt, t_n)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).cuda()
+    lam_d = dev(lam)
+    gm = torch.zeros(c.ctx.cells * 3, dtype=torch.float64, device="cuda")
+    gM = torch.zeros(6, dtype=torch.float64, device="cuda")
+    c.ctx.adjoint_step(t_n, dt, dev(u_n), lam_d, gm, gM)
+    torch.cuda.synchronize()
+    err = rel_linf(lam_d.cpu().numpy().reshape(c.shape), lam_ref.numpy())
+    assert err <= MIXED_TOL, err
+    assert close(gm.cpu().numpy(), gm_ref.numpy(), MIXED_TOL)
+    assert close(gM.cpu().numpy(), gM_ref.numpy(), MIXED_TOL)

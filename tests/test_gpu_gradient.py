@@ -118,3 +118,26 @@ def test_ck_gradient_with_mixed_forward_is_close_to_fp64():
     assert abs(Jm - Jf) <= 1e-6 * abs(Jf)
     assert np.abs(gmm - gmf).max() <= 1e-6 * np.abs(gmf).max()
     assert np.abs(gMm - gMf).max() <= 1e-6 * np.abs(gMf).max()
+
+
+def test_mixed_ck_gradient_matches_fp64_central_differences():
+    """The gradient of a mixed CK context (mixed forward sweep, mixed-precision adjoint) against
+    central differences of the FP64 CK forward solver: relative 1e-6."""
+    c, mat, M, u0, dt, steps, k, obs = problem(order=4, ncell=(2, 3, 2), steps=8, k=3,
+                                               predictor="ck", precision="mixed")
+    J, gm, gM = gpu_J(c, mat, M, u0, dt, steps, k, obs, grads=True)
+    f, *_ = problem(order=4, ncell=(2, 3, 2), steps=8, k=3, predictor="ck")
+    rng = np.random.default_rng(3)
+    for _ in range(2):
+        dirn = rng.standard_normal(mat.shape) * mat
+        eps = 1e-6
+        Jp = gpu_J(f, mat + eps * dirn, M, u0, dt, steps, k, obs)
+        Jm = gpu_J(f, mat - eps * dirn, M, u0, dt, steps, k, obs)
+        fd = (Jp - Jm) / (2 * eps)
+        ad = float((gm * dirn).sum())
+        assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+    for a in range(6):
+        e = np.zeros(6)
+        e[a] = 1e-4
+        fd = (gpu_J(f, mat, M + e, u0, dt, steps, k, obs) - gpu_J(f, mat, M - e, u0, dt, steps, k, obs)) / 2e-4
+        assert abs(fd - gM[a]) <= 1e-6 * max(abs(gM[a]), 1e-30), (a, fd, gM[a])

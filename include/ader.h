@@ -278,8 +278,8 @@ ader_status ader_adjoint_step(ader_ctx* ctx, double t_n, double dt, const double
  * Limits and behaviour:
  *  - The face adjoints (cells x 3 x 2 x n^2 x 9 doubles), the face gradients (6 doubles per
  *    face) and, with the Picard predictor, one iterate slab (order x (order+1) x n^3 x 9
- *    doubles), with the Cauchy-Kowalevski predictor lambda's face projections (2 x n^2 x 9
- *    doubles per face), must fit in 64 MiB;
+ *    doubles), with the Cauchy-Kowalevski predictor lambda's projections onto the cells' faces
+ *    (cells x 3 x 2 x n^2 x 9 doubles), must fit in 64 MiB;
  *    otherwise ADER_EINVAL and nothing runs.  Fewer thread blocks are used when the slabs of all
  *    of them do not fit.
  *  - The array is shared by every call on a device and keeps the contents of the last call

@@ -104,7 +104,7 @@ struct AdjArgs {
   double* gface;         // [faces of all directions][2][3] material gradient of each face
   double* scratch;       // [gridDim][I-1][n][NL] forward Picard iterates
   long long scratch_per_block;
-  double* gproj;         // [faces of all directions][2][NF][NV] lambda's face projections
+  double* lproj;         // [C][3][2][NF][NV] lambda's projections onto each cell's faces
                          // (Cauchy-Kowalevski adjoint; null otherwise)
 };
 

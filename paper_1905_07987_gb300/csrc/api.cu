@@ -964,8 +964,8 @@ ader_status ader_adjoint_step(ader_ctx* c, double t_n, double dt, const double* 
     cudaError_t e = cudaMalloc(&c->dev_adj, sizeof(DevScalars));
     if (e == cudaSuccess) e = cudaMalloc(&c->adjf, (size_t)c->g.ncells * 3 * 2 * c->nf * c->nvar * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&c->gface, (size_t)nfaces * 6 * sizeof(double));
-    // Picard: the iterate slabs; Cauchy-Kowalevski: lambda's face projections
-    const size_t scratch = ck ? (size_t)nfaces * 2 * c->nf * c->nvar
+    // Picard: the iterate slabs; Cauchy-Kowalevski: lambda's projections onto the cells' faces
+    const size_t scratch = ck ? (size_t)c->g.ncells * 3 * 2 * c->nf * c->nvar
                               : (size_t)c->adj_blocks * c->adj_spb;
     if (e == cudaSuccess) e = cudaMalloc(&c->adj_scratch, scratch * sizeof(double));
     if (e != cudaSuccess) {
@@ -1096,7 +1096,7 @@ ader_status ader_adjoint_step_static(ader_ctx* c, double t_n, double dt, const d
   const size_t b_gface = round256((size_t)nfaces * 6 * sizeof(double));
   // Picard: one iterate slab per thread block; Cauchy-Kowalevski: lambda's face projections
   const long long spb = ck ? 0 : c->fam->adj_scratch_per_block(c->cfg.order, iters);
-  const size_t b_slab = ck ? (size_t)nfaces * 2 * c->nf * c->nvar * sizeof(double)
+  const size_t b_slab = ck ? (size_t)c->g.ncells * 3 * 2 * c->nf * c->nvar * sizeof(double)
                            : (size_t)spb * sizeof(double);
   const size_t fixed = b_dev + b_adjf + b_gface;
   if (fixed + b_slab > kStaticScratchBytes) return ADER_EINVAL;  // grid too large for the array

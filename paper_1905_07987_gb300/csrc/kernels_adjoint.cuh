@@ -48,10 +48,12 @@ __device__ __forceinline__ void dcoef(int d, int v, double rho, double* g) {
   }
 }
 
-// MODE 0: the whole face adjoint (the Picard form).  The Cauchy-Kowalevski form splits it around
-// its cell kernel, which produces the forward face data: MODE 1 writes the face adjoints (they
-// need lambda and the material only) and keeps lambda's face projections gL, gR in J.gproj;
-// MODE 2 forms the face material gradient from those projections and the forward face data.
+// MODE 0: the whole face adjoint (the Picard form): lambda's face projections read from the
+// cells' lambda, the forward face data from A.face.  The Cauchy-Kowalevski form splits it around
+// its cell kernel, which produces the forward face data, and reads lambda's face projections from
+// J.lproj (k_adj_proj): MODE 1 writes the face adjoints (they need lambda and the material only),
+// MODE 2 forms the face material gradient from the projections and the forward face data.  In
+// modes 1 and 2 every face record a warp needs is staged in shared memory by coalesced loads.
 // DIR: the face normal (a template parameter, so that every row index of B_d is a constant).
 template <int D, int N, int MODE, int DIR>
 __global__ void __launch_bounds__(128) k_adj_riemann(const __grid_constant__ StepArgs A,
@@ -62,8 +64,12 @@ __global__ void __launch_bounds__(128) k_adj_riemann(const __grid_constant__ Ste
   using C = Cfg<Elastic, 3, N>;
   constexpr int n = C::n, NV = 9, NF = C::NF, FR = C::FR, NL = C::NL;
   constexpr int PER = (NF + 31) / 32;
+  // per warp: the projections of both sides (modes 1, 2) and the face data of both sides (mode 2)
+  constexpr int NSTAGE = MODE == 0 ? 1 : (MODE == 1 ? 2 : 4);
+  __shared__ double stage[4][NSTAGE][MODE == 0 ? 1 : FR];
   const int lane = threadIdx.x & 31;
-  const long long f = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int warp = threadIdx.x >> 5;
+  const long long f = (long long)blockIdx.x * 4 + warp;
   const Geometry& g = A.g;
   const int nd = g.n[d];
   const long long nfaces = (long long)(nd + 1) * FaceIdx::ntrans(g, d);
@@ -76,12 +82,25 @@ __global__ void __launch_bounds__(128) k_adj_riemann(const __grid_constant__ Ste
     if (MODE != 1 && lane < 6) gf[lane] = 0.0;
     return;
   }
-  double* gp = MODE ? J.gproj + (gface_off + f) * (long long)(2 * NF * NV) : nullptr;
   long long cL = -1, cR = -1;
   if (kf > 0) cL = FaceIdx::cell_of(g, tr, d, kf - 1);
   else if (periodic) cL = FaceIdx::cell_of(g, tr, d, nd - 1);
   if (kf < nd) cR = FaceIdx::cell_of(g, tr, d, kf);
   else if (periodic) cR = FaceIdx::cell_of(g, tr, d, 0);
+  if (MODE != 0) {
+    // stage[0] / [1]: lambda's projection onto the face from the left cell (its right side) and
+    // from the right cell (its left side); stage[2] / [3]: the forward face data of both sides
+    double* sw = &stage[warp][0][0];
+    for (int e = lane; e < FR; e += 32) {
+      sw[e] = cL >= 0 ? J.lproj[((cL * 3 + d) * 2 + 1) * (long long)FR + e] : 0.0;
+      sw[FR + e] = cR >= 0 ? J.lproj[((cR * 3 + d) * 2 + 0) * (long long)FR + e] : 0.0;
+      if (MODE == 2) {
+        sw[2 * FR + e] = cL >= 0 ? A.face[cL * (long long)(3 * 2 * FR) + (d * 2 + 1) * FR + e] : 0.0;
+        sw[3 * FR + e] = cR >= 0 ? A.face[cR * (long long)(3 * 2 * FR) + (d * 2 + 0) * FR + e] : 0.0;
+      }
+    }
+    __syncwarp();
+  }
   const long long mcL = cL >= 0 ? cL : cR, mcR = cR >= 0 ? cR : cL;
   const double rL = A.mat[mcL * 3], lL = A.mat[mcL * 3 + 1], uL = A.mat[mcL * 3 + 2];
   const double rR = A.mat[mcR * 3], lR = A.mat[mcR * 3 + 1], uR = A.mat[mcR * 3 + 2];
@@ -100,11 +119,13 @@ __global__ void __launch_bounds__(128) k_adj_riemann(const __grid_constant__ Ste
     cb[v] = acc;
   }
   const double dt = A.dev->dt;
+  const double dih = dt * A.g.inv_h[d];
   const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
   double S1 = 0.0;   // sum over nodes and variables of dq (gL + gR)
   double S2[NV];     // per row v: sum over nodes of dq[src] (gL - gR)[v]
 #pragma unroll
   for (int v = 0; v < NV; ++v) S2[v] = 0.0;
+  double dqh[PER][NV];
 #pragma unroll
   for (int r = 0; r < PER; ++r) {
     const int jp = lane + 32 * r;
@@ -113,10 +134,7 @@ __global__ void __launch_bounds__(128) k_adj_riemann(const __grid_constant__ Ste
     double gL[NV], gR[NV], qL[NV], qR[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      if (MODE == 2) {
-        gL[v] = gp[jp * NV + v];
-        gR[v] = gp[NF * NV + jp * NV + v];
-      } else {
+      if (MODE == 0) {
         double aL = 0.0, aR = 0.0;
         if (cL >= 0) {
           const double* lam = J.lam + cL * NL;
@@ -128,38 +146,38 @@ __global__ void __launch_bounds__(128) k_adj_riemann(const __grid_constant__ Ste
 #pragma unroll
           for (int m = 0; m < n; ++m) aR = fma(T.c0[m], lam[(jbase + m * st) * NV + v], aR);
         }
-        gL[v] = -dt * A.g.inv_h[d] * aL;
-        gR[v] = dt * A.g.inv_h[d] * aR;
-      }
-      if (MODE != 1) {
+        gL[v] = -dih * aL;
+        gR[v] = dih * aR;
         qL[v] = cL >= 0 ? A.face[cL * (long long)(3 * 2 * FR) + (d * 2 + 1) * FR + jp * NV + v] : 0.0;
         qR[v] = cR >= 0 ? A.face[cR * (long long)(3 * 2 * FR) + (d * 2 + 0) * FR + jp * NV + v] : 0.0;
+      } else {
+        gL[v] = -dih * stage[warp][0][jp * NV + v];
+        gR[v] = dih * stage[warp][1][jp * NV + v];
+        if (MODE == 2) {
+          qL[v] = stage[warp][NSTAGE == 4 ? 2 : 0][jp * NV + v];
+          qR[v] = stage[warp][NSTAGE == 4 ? 3 : 0][jp * NV + v];
+        }
       }
     }
     if (MODE != 2) {
       // adjoint of dq = qR - qL:  dqh = -s/2 (gL + gR) + 1/2 Bbar^T (gL - gR)
-      double dqh[NV];
 #pragma unroll
-      for (int k = 0; k < NV; ++k) dqh[k] = -0.5 * s * (gL[k] + gR[k]);
+      for (int k = 0; k < NV; ++k) dqh[r][k] = -0.5 * s * (gL[k] + gR[k]);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const int sv = Elastic::src(d, v);
-        if (sv >= 0) dqh[sv] += 0.5 * cb[v] * (gL[v] - gR[v]);
+        if (sv >= 0) dqh[r][sv] += 0.5 * cb[v] * (gL[v] - gR[v]);
       }
-      if (cL >= 0)
+      if (MODE == 0) {
+        if (cL >= 0)
 #pragma unroll
-        for (int v = 0; v < NV; ++v) J.adjf[((cL * 3 + d) * 2 + 1) * (long long)(NF * NV) + jp * NV + v] = -dqh[v];
-      if (cR >= 0)
+          for (int v = 0; v < NV; ++v) J.adjf[((cL * 3 + d) * 2 + 1) * (long long)FR + jp * NV + v] = -dqh[r][v];
+        if (cR >= 0)
 #pragma unroll
-        for (int v = 0; v < NV; ++v) J.adjf[((cR * 3 + d) * 2 + 0) * (long long)(NF * NV) + jp * NV + v] = dqh[v];
+          for (int v = 0; v < NV; ++v) J.adjf[((cR * 3 + d) * 2 + 0) * (long long)FR + jp * NV + v] = dqh[r][v];
+      }
     }
-    if (MODE == 1) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        gp[jp * NV + v] = gL[v];
-        gp[NF * NV + jp * NV + v] = gR[v];
-      }
-    } else {
+    if (MODE != 1) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const double dq = qR[v] - qL[v];
@@ -169,7 +187,24 @@ __global__ void __launch_bounds__(128) k_adj_riemann(const __grid_constant__ Ste
       }
     }
   }
-  if (MODE == 1) return;
+  if (MODE == 1) {
+    // the face adjoints through the staging area (coalesced stores to both cells' records)
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int jp = lane + 32 * r;
+      if (jp < NF)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) stage[warp][0][jp * NV + v] = dqh[r][v];
+    }
+    __syncwarp();
+    for (int e = lane; e < FR; e += 32) {
+      const double x = stage[warp][0][e];
+      if (cL >= 0) J.adjf[((cL * 3 + d) * 2 + 1) * (long long)FR + e] = -x;
+      if (cR >= 0) J.adjf[((cR * 3 + d) * 2 + 0) * (long long)FR + e] = x;
+    }
+    return;
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     S1 += __shfl_xor_sync(0xffffffffu, S1, o);
@@ -226,6 +261,55 @@ __global__ void __launch_bounds__(128) k_adj_riemann(const __grid_constant__ Ste
       gf[3 + k] = gRm[k];
     }
   }
+}
+
+// lambda's projections onto the six faces of every cell (the transposes of the corrector's face
+// terms before the face weights): J.lproj[c][d][0] = sum_m c0[m] lambda along the lines of
+// direction d, [1] with c1; one block per cell (several at low order), lambda staged in shared
+// memory by a coalesced load, stores coalesced.
+template <int N>
+struct CfgProj {
+  static constexpr int NS = (N + 1) * (N + 1) * (N + 1);
+  static constexpr int CPB = NS >= 96 ? 1 : 128 / NS;  // cells per block
+  static constexpr int TPB = (CPB * NS + 31) / 32 * 32;
+};
+
+template <int N>
+__global__ void __launch_bounds__(CfgProj<N>::TPB)
+    k_adj_proj(const __grid_constant__ StepArgs A, const __grid_constant__ AdjArgs J,
+               const __grid_constant__ Tables T) {
+  constexpr int n = N + 1, NS = n * n * n, NV = 9, NL = NS * NV, NF = n * n, FR = NF * NV;
+  constexpr int CPB = CfgProj<N>::CPB, TPB = CfgProj<N>::TPB;
+  __shared__ double sl[CPB][NL];
+  const long long c0 = (long long)blockIdx.x * CPB;
+  const int ncb = (int)(A.g.ncells - c0 < CPB ? A.g.ncells - c0 : CPB);
+  for (int e = threadIdx.x; e < ncb * NL; e += TPB) (&sl[0][0])[e] = J.lam[c0 * NL + e];
+  __syncthreads();
+  for (int e = threadIdx.x; e < ncb * 3 * FR; e += TPB) {
+    const int s = e / (3 * FR), r = e - s * (3 * FR);
+    const int d = r / FR, q = r - d * FR;
+    const int jp = q / NV, v = q - jp * NV;
+    const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
+    const int jbase = (jp % st) + (jp / st) * st * n;
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      const double x = sl[s][(jbase + m * st) * NV + v];
+      a0 = fma(T.c0[m], x, a0);
+      a1 = fma(T.c1[m], x, a1);
+    }
+    double* o = J.lproj + ((c0 + s) * 3 + d) * 2 * (long long)FR + q;
+    o[0] = a0;
+    o[FR] = a1;
+  }
+}
+
+template <int N>
+cudaError_t launch_adj_proj(const StepArgs& a, const AdjArgs& j, const Tables& t, cudaStream_t s) {
+  const long long blocks = (a.g.ncells + CfgProj<N>::CPB - 1) / CfgProj<N>::CPB;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_adj_proj<N><<<(unsigned)blocks, CfgProj<N>::TPB, 0, s>>>(a, j, t);
+  return cudaGetLastError();
 }
 
 // The faces of direction d (one warp per face, 4 per block).

@@ -25,8 +25,8 @@
 //
 // The forward face data the face terms' material gradient needs come from this kernel too (qbar
 // and its extrapolations, as the predictor forms them): the face adjoints, which need lambda and
-// the material only, run before it (k_adj_riemann MODE 1), the face material gradients after it
-// (MODE 2), so no forward predictor launch precedes the adjoint.
+// the material only, run before it (k_adj_proj, then k_adj_riemann MODE 1), the face material
+// gradients after it (MODE 2), so no forward predictor launch precedes the adjoint.
 //
 // One thread per node, the cells of a block (several at low order) each keep a_0 .. a_N in
 // shared memory ((N+2) padded records of 10 doubles per node; the record of a_0 and a spare one
@@ -423,8 +423,10 @@ struct AdjLaunchCK {
       offs[d] = off;
       off += (long long)(a.g.n[d] + 1) * (a.g.ncells / a.g.n[d]);
     }
-    // face adjoints (lambda's face projections kept) -> cell kernel (forward face data out) ->
-    // face material gradients -> their sums per cell
+    // lambda's projections onto every cell's faces -> face adjoints -> cell kernel (forward face
+    // data out) -> face material gradients -> their sums per cell
+    cudaError_t e0 = launch_adj_proj<N>(a, j, t, s);
+    if (e0 != cudaSuccess) return e0;
     for (int d = 0; d < 3; ++d) {
       cudaError_t e = launch_adj_riemann<N, 1>(a, j, t, d, offs[d], s);
       if (e != cudaSuccess) return e;
@@ -440,12 +442,6 @@ struct AdjLaunchCK {
     }
     k_adj_face_sum<N><<<(unsigned)((a.g.ncells + 255) / 256), 256, 0, s>>>(a, j, offs[1], offs[2]);
     return cudaGetLastError();
-  }
-  // doubles of lambda's face projections (J.gproj)
-  static long long gproj_doubles(const Geometry& g) {
-    long long nfaces = 0;
-    for (int d = 0; d < 3; ++d) nfaces += (long long)(g.n[d] + 1) * (g.ncells / g.n[d]);
-    return nfaces * 2 * CfgCKA<N>::NF * 9;
   }
 };
 

@@ -530,6 +530,8 @@ struct AdjLaunchCKM {
       offs[d] = off;
       off += (long long)(a.g.n[d] + 1) * (a.g.ncells / a.g.n[d]);
     }
+    cudaError_t e0 = launch_adj_proj<N>(a, j, t, s);
+    if (e0 != cudaSuccess) return e0;
     for (int d = 0; d < 3; ++d) {
       cudaError_t e = launch_adj_riemann<N, 1>(a, j, t, d, offs[d], s);
       if (e != cudaSuccess) return e;

@@ -558,7 +558,7 @@ def extra_convergence(ader, synth, stream, res, sides=(27, 54)):
     return out
 
 
-def _adjoint_gradient_40(ader, synth, stream, n, N, steps, k, predictor):
+def _adjoint_gradient_40(ader, synth, stream, n, N, steps, k, predictor, precision="fp64"):
     """One misfit gradient through ader_misfit_gradient (see extra_adjoint) with the given
     predictor; returns the timing record."""
     import torch
@@ -567,10 +567,12 @@ def _adjoint_gradient_40(ader, synth, stream, n, N, steps, k, predictor):
     dofs = cells * (N + 1) ** 3 * 9
     mat = torch.from_numpy(synth.elastic_material((n,) * 3, seed=1905).reshape(-1).copy()).cuda()
     cfg = ader.make_config("elastic", 3, N, (n,) * 3, (0, 0, 0), (L,) * 3, "absorbing",
-                           synth.cfl_number(N), predictor=predictor)
+                           synth.cfl_number(N), predictor=predictor, precision=precision)
     ctx = ader.Context(cfg, stream=stream.cuda_stream)
     ctx.set_material(mat)
-    ctx.set_point_source((L / 2,) * 3, synth.moment_tensor(), 2.0, 0.5)
+    # three cells below the centre of the top face, so that the receivers record signal and the
+    # adjoint field meets the forward field within the steps of the gradient
+    ctx.set_point_source((L / 2, L / 2, L - 1.25), synth.moment_tensor(), 2.0, 0.5)
     seismo = torch.zeros(steps + 2, 64, 3, dtype=torch.float64, device="cuda")
     ctx.set_receivers(synth.receivers_top((n,) * 3, (0, 0, 0), (L,) * 3), seismo, steps + 2)
     u0 = torch.zeros(ctx.count, dtype=torch.float64, device="cuda")
@@ -609,30 +611,51 @@ def _adjoint_gradient_40(ader, synth, stream, n, N, steps, k, predictor):
     torch.cuda.synchronize()
     adj = e0.elapsed_time(e1) / 3
     ok = bool(torch.isfinite(gm).all().item() and torch.isfinite(gM).all().item())
+    # the gradient itself (the timed call's), for the comparison between forms
+    gm.zero_()
+    gM.zero_()
+    ctx.misfit_gradient(u0, 0.45, dt, steps, k, obs, gm, gM)
+    grads = (gm.cpu().numpy().copy(), gM.cpu().numpy().copy())
     ctx.close()
     del seismo
     return {"forward_ms_per_step": fwd / steps, "adjoint_step_ms": adj, "gradient_ms": tot,
             "gradient_over_forward": tot / fwd, "value": dofs * steps / (tot * 1e-3), "J": J,
-            "finite": ok}
+            "finite": ok, "_grads": grads}
 
 
-def extra_adjoint(ader, synth, stream, n=40, N=4, steps=12, k=4):
+def extra_adjoint(ader, synth, stream, n=40, N=4, steps=12, k=4,
+                  forms=("picard", "ck", "ck_mixed")):
     """Adjoint of the linear-elastic step through the C ABI (ader_misfit_gradient): order N, n^3
     cells (h = 0.5 km), seeded material, moment-tensor Ricker source at the centre, 64 receivers
     on the top face, a seeded misfit over `steps` steps with a checkpoint every k steps.  Reports
     the whole gradient (forward sweep, recomputation of each segment, adjoint sweep, gradients with
     respect to per-cell rho, lambda, mu and the moment tensor) against the same number of forward
     steps, with the Picard predictor and with the Cauchy-Kowalevski predictor (its own adjoint),
-    FP64."""
+    FP64, and with the mixed Cauchy-Kowalevski forward step and mixed-precision adjoint; the
+    gradients of the mixed form against the FP64 CK form."""
     dofs = n ** 3 * (N + 1) ** 3 * 9
     out = {"workload": "adjoint_elastic3d_p%d_%d" % (N, n), "dofs": dofs, "steps": steps,
            "k_ckpt": k, "unit": "DOF-updates/s (gradient: forward, recomputation and adjoint, "
            "each step counted once)", "dtype": "f64"}
-    for pred in ("picard", "ck"):
-        out[pred] = _adjoint_gradient_40(ader, synth, stream, n, N, steps, k, pred)
-    out["value"] = out["ck"]["value"]
-    out["ck_gradient_speedup"] = out["picard"]["gradient_ms"] / out["ck"]["gradient_ms"]
-    out["ck_adjoint_step_speedup"] = out["picard"]["adjoint_step_ms"] / out["ck"]["adjoint_step_ms"]
+    spec = {"picard": ("picard", "fp64"), "ck": ("ck", "fp64"), "ck_mixed": ("ck", "mixed")}
+    for form in forms:
+        out[form] = _adjoint_gradient_40(ader, synth, stream, n, N, steps, k, *spec[form])
+    if "ck" in out and "ck_mixed" in out:
+        # the mixed form (mixed forward, mixed-precision adjoint) against the FP64 CK form
+        (gmm, gMm), (gmf, gMf) = out["ck_mixed"]["_grads"], out["ck"]["_grads"]
+        m = out["ck_mixed"]
+        m["J_rel_diff_to_fp64_ck"] = abs(m["J"] - out["ck"]["J"]) / abs(out["ck"]["J"])
+        m["grad_mat_rel_diff_to_fp64_ck"] = float(np.abs(gmm - gmf).max() / np.abs(gmf).max())
+        m["grad_M_rel_diff_to_fp64_ck"] = float(np.abs(gMm - gMf).max() / np.abs(gMf).max())
+    for form in forms:
+        del out[form]["_grads"]
+    out["value"] = out[forms[-1]]["value"]
+    if "picard" in out:
+        for form in forms[1:]:
+            out[form]["gradient_speedup_over_picard"] = (out["picard"]["gradient_ms"]
+                                                         / out[form]["gradient_ms"])
+            out[form]["adjoint_step_speedup_over_picard"] = (out["picard"]["adjoint_step_ms"]
+                                                             / out[form]["adjoint_step_ms"])
     return out
 
 
@@ -877,6 +900,8 @@ def main():
                     help="comma list of the other workloads to run (default: all of them)")
     ap.add_argument("--elastic-n", type=int, default=81,
                     help="cells per side of the elastic workload (81; smaller for profiling)")
+    ap.add_argument("--adjoint-forms", default="picard,ck,ck_mixed",
+                    help="forms of the 40^3 adjoint workload (picard, ck, ck_mixed)")
     ap.add_argument("--adjoint-steps", type=int, default=20,
                     help="steps of the ensemble gradient sample (300: the full workload, "
                          "checkpoint every 20)")
@@ -1059,6 +1084,9 @@ def main():
                     ks = 20 if args.adjoint_steps >= 100 else 5
                     extra[name] = fn(ader, synth, stream, steps=args.adjoint_steps, k=ks,
                                      picard_steps=0 if args.adjoint_steps >= 100 else 1)
+                elif fn is extra_adjoint:
+                    extra[name] = fn(ader, synth, stream,
+                                     forms=tuple(f for f in args.adjoint_forms.split(",") if f))
                 elif fn is extra_elastic:
                     extra[name] = fn(ader, synth, stream, n=args.elastic_n)
                 else:

@@ -11,8 +11,8 @@
 // L u and a_1 in float-float, a_2 .. a_N and L a_N in binary32, qbar = u + dbar and its face
 // extrapolations in float-float (the forward face data, written in FP64).
 // Material gradient sum_k f_k (lambda + mu_{k+1})^T (dL/dm) a_k, from P_k = f_k L a_k at the node:
-// level 0 (O(CFL) of the state) in FP64 from the float-float a_1 and lambda + mu_1; levels k >= 1
-// (O(CFL^(k+1))) in binary32, accumulated in FP64.  Moment gradient (the source cell only) in
+// level 0 (O(CFL) of the state) in float-float from a_1 and lambda + mu_1; levels k >= 1
+// (O(CFL^(k+1))) in binary32; the material factors and the sums in FP64.  Moment gradient (the source cell only) in
 // FP64.  Relative to the FP64 adjoint the binary32 terms leave about 1e-7 CFL^2 of lambda per step.
 //
 // Layout per cell (shared memory): the float-float record U ([NS][10] (hi, lo) pairs: u, then
@@ -34,6 +34,9 @@ struct CfgCKAM {
   static constexpr int NVF = 12;  // binary32 record: 12 floats (float4 loads)
   static constexpr int CPB = NS >= 96 ? 1 : 128 / NS;
   static constexpr int TPB = (CPB * NS + 31) / 32 * 32;
+  // resident blocks per SM: 4 at 128 threads (128 registers, a few spilled, measured faster than
+  // 3 blocks without spills), 2 at order 5
+  static constexpr int MINB = TPB <= 128 ? 4 : 2;
   static constexpr int NF = n * n;
   static constexpr size_t RECF = (size_t)NS * NVF * 4;  // bytes of one binary32 record
   static constexpr size_t OFF_A = (size_t)NS * NVQ * 8; // a_1 .. a_N
@@ -146,8 +149,24 @@ __device__ __forceinline__ void ck_dmat_R_f(const float (&P)[9], const float (&n
   g[2] = fmaf(nu[6], P[6], fmaf(nu[7], P[7], fmaf(nu[8], P[8], s)));
 }
 
+// Float-float form of ck_dmat_R_f (the level-0 pairing, O(CFL) of the state).
+__device__ __forceinline__ void ck_dmat_R_ff(const ff (&P)[9], const ff (&nu)[9], ff lam, ff ik,
+                                             ff (&g)[3]) {
+  g[0] = {0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) ff_mac(g[0], nu[i].h, nu[i].l, P[i].h, P[i].l);
+  const ff theta = ff_mul(ff_add(ff_add(P[3], P[4]), P[5]), ik);
+  const ff nsum = ff_add(ff_add(nu[3], nu[4]), nu[5]);
+  g[1] = ff_mul(theta, nsum);
+  ff s = {0.f, 0.f};
+#pragma unroll
+  for (int v = 3; v < 9; ++v) ff_mac(s, nu[v].h, nu[v].l, P[v].h, P[v].l);
+  const ff lt = ff_mul(lam, g[1]);
+  g[2] = ff_sub(s, lt);
+}
+
 template <int N>
-__global__ void __launch_bounds__(CfgCKAM<N>::TPB)
+__global__ void __launch_bounds__(CfgCKAM<N>::TPB, CfgCKAM<N>::MINB)
     k_adj_cell_ck_mixed(const __grid_constant__ StepArgs A, const __grid_constant__ AdjArgs J,
                         const __grid_constant__ Tables T, const __grid_constant__ TablesF F) {
   using C = CfgCKAM<N>;
@@ -265,7 +284,7 @@ __global__ void __launch_bounds__(CfgCKAM<N>::TPB)
   float d32[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) d32[v] = 0.f;
-#pragma unroll
+#pragma unroll 1
   for (int k = 1; k < N; ++k) {
     if (act) {
       float R[NV];
@@ -368,6 +387,7 @@ __global__ void __launch_bounds__(CfgCKAM<N>::TPB)
   const double irho = act ? s_mat[slot][0] : 0.0, lamd = act ? s_mat[slot][1] : 0.0;
   const double ikd = act ? s_mat[slot][2] : 0.0, imud = act ? s_mat[slot][3] : 0.0;
   const float lamf = (float)lamd, ikf = (float)ikd;
+  const ff lamff = ff_split(lamd), ikff = ff_split(ikd);
   const double phi = srcc ? A.src.phi[j] : 0.0;
   ff B[NV], mu_c[NV];  // mu_c: mu_{k+1} at this node
   if (act) {
@@ -400,7 +420,7 @@ __global__ void __launch_bounds__(CfgCKAM<N>::TPB)
   __syncthreads();
 
   // ---- reverse recursion ---------------------------------------------------------------------
-#pragma unroll
+#pragma unroll 1
   for (int k = N - 1; k >= 0; --k) {
     const float* Min = ((N - 1 - k) & 1) ? M1 : M0;  // mu_{k+1}
     float* Mout = ((N - 1 - k) & 1) ? M0 : M1;       // mu_k
@@ -408,21 +428,26 @@ __global__ void __launch_bounds__(CfgCKAM<N>::TPB)
       const double f = dt * (1.0 / (k + 1));
       // material: f_k (lambda + mu_{k+1})^T (dL/dm) a_k
       if (k == 0) {
-        // FP64 from the float-float a_1 and lambda + mu_1
-        double P[NV], nu[NV];
+        // float-float from a_1 and lambda + mu_1, the material factors in FP64
+        ff P[NV], nu[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          P[v] = ff_to_d(a1[v]);
-          nu[v] = ff_to_d(ff_add(lj[v], mu_c[v]));
+          P[v] = a1[v];
+          nu[v] = ff_add(lj[v], mu_c[v]);
         }
         if (srcc) {
+          const ff fs0 = ff_mul(dtf, s_skf[0]);  // f_0 s_0
 #pragma unroll
           for (int a = 0; a < 6; ++a) {
             const float2 g = gsrc[j * 6 + a];
-            P[3 + a] = fma(-f * s_sk[0], (double)g.x + (double)g.y, P[3 + a]);
+            P[3 + a] = ff_sub(P[3 + a], ff_mul(fs0, {g.x, g.y}));
           }
         }
-        ck_dmat_R(P, nu, irho, lamd, ikd, imud, gm);
+        ff g[3];
+        ck_dmat_R_ff(P, nu, lamff, ikff, g);
+        gm[0] = fma(-irho, ff_to_d(g[0]), gm[0]);
+        gm[1] += ff_to_d(g[1]);
+        gm[2] = fma(imud, ff_to_d(g[2]), gm[2]);
       } else {
         float P[NV], nu[NV], g[3];
         const float* ak = Arec + k * NS * NVF + j * NVF;  // a_{k+1}

@@ -174,6 +174,9 @@ struct StepArgs {
   int cfl_filter;
   // 1: the FP64 Picard predictor starts from the continuous extension Runge-Kutta guess
   int cerk;
+  // elastic: per face (directions concatenated) the wave speed max(vp_L, vp_R) and the nine
+  // path-averaged coefficients of B_d, formed when the material is set (null: formed per step)
+  const double* fmat;
 };
 
 // Per (pde, dim) kernel family; order dispatch happens inside.
@@ -228,6 +231,11 @@ cudaError_t launch_misfit(const double* a, const double* b, long long n, double 
                           cudaStream_t s);
 cudaError_t launch_receivers_adjoint(const Receivers& r, const double* res, double scale,
                                      double* dJdu, int nodes, int nvar, cudaStream_t s);
+
+// Elastic: the per-face material terms of the Riemann solver (StepArgs::fmat), 10 doubles per face
+constexpr int FMAT = 10;
+cudaError_t launch_face_material_elastic(const Geometry& g, const double* mat, const Tables& t,
+                                         double* out, cudaStream_t s);
 
 // orders of the tensor-core Cauchy-Kowalevski predictor (ADER_PREC_MIXED_TF32X3)
 bool predictor_ck_tc_order_ok(int order);

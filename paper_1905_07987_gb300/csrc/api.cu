@@ -328,6 +328,7 @@ struct ader_ctx {
   double* u_next = nullptr;
   double* face = nullptr;
   double* phi = nullptr;
+  double* fmat = nullptr;    // elastic: per-face material terms of the Riemann solver
   double* fspeed = nullptr;  // mixed Euler: face wave speeds evaluated by the predictor
   double* mat = nullptr;
   DevScalars* dev = nullptr;
@@ -386,6 +387,7 @@ static void free_all(ader_ctx* c) {
   cudaFree(c->u_next);
   cudaFree(c->face);
   cudaFree(c->phi);
+  cudaFree(c->fmat);
   cudaFree(c->fspeed);
   cudaFree(c->mat);
   cudaFree(c->dev);
@@ -673,6 +675,18 @@ ader_status ader_set_material(ader_ctx* c, const double* mat, int on_device) {
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream,
                         !on_device);
   if (st != ADER_OK) return st;
+  // the Riemann solver's per-face material terms (speed and path-averaged coefficients)
+  if (!c->fmat) {
+    long long nf = 0;
+    for (int d = 0; d < 3; ++d) nf += (long long)(c->g.n[d] + 1) * (c->g.ncells / c->g.n[d]);
+    const cudaError_t e = cudaMalloc(&c->fmat, (size_t)nf * FMAT * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->fmat = nullptr;
+      return e == cudaErrorMemoryAllocation ? ADER_ENOMEM : ADER_ECUDA;
+    }
+  }
+  CUDA_OK(launch_face_material_elastic(c->g, c->mat, c->tab, c->fmat, c->stream));
   c->mat_set = true;
   return ADER_OK;
 }
@@ -797,6 +811,7 @@ static StepArgs make_args(ader_ctx* c, double dt, double t_end) {
   a.face = c->face;
   a.phi = c->phi;
   a.mat = c->mat;
+  a.fmat = c->mat_set ? c->fmat : nullptr;
   a.dev = c->dev;
   a.iters = c->cfg.picard_iters > 0 ? c->cfg.picard_iters : c->cfg.order + 1;
   a.cerk = c->cfg.initial_guess == ADER_GUESS_CERK ? 1 : 0;

@@ -95,6 +95,63 @@ cudaError_t ens_fused(const StepArgs* R, const EnsTable& E, const Tables& T, con
 }
 }  // namespace
 
+// The per-face material terms of the elastic Riemann solver (the wave speed max(vp_L, vp_R), ties
+// left, and the 3-point path average of each row's coefficient of B_d), one thread per face, by
+// the same operations as the per-step evaluation in riemann_face; a boundary face takes its
+// interior cell's material on both sides.
+__global__ void __launch_bounds__(256) k_face_material(const __grid_constant__ Geometry g,
+                                                       const double* __restrict__ mat,
+                                                       const __grid_constant__ Tables T,
+                                                       double* __restrict__ out) {
+  long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int d = 0;
+  long long nf = (long long)(g.n[0] + 1) * FaceIdx::ntrans(g, 0);
+  long long base = 0;
+  while (d < 2 && f - base >= nf) {
+    base += nf;
+    ++d;
+    nf = (long long)(g.n[d] + 1) * FaceIdx::ntrans(g, d);
+  }
+  if (f - base >= nf) return;
+  const long long fl = f - base;
+  const int nd = g.n[d];
+  const int kf = (int)(fl % (nd + 1));
+  const long long tr = fl / (nd + 1);
+  const bool periodic = (g.bc[d][0] == BC_PERIODIC);
+  long long cL = -1, cR = -1;
+  if (kf > 0) cL = FaceIdx::cell_of(g, tr, d, kf - 1);
+  else if (periodic) cL = FaceIdx::cell_of(g, tr, d, nd - 1);
+  if (kf < nd) cR = FaceIdx::cell_of(g, tr, d, kf);
+  else if (periodic) cR = FaceIdx::cell_of(g, tr, d, 0);
+  const long long mcL = cL >= 0 ? cL : cR, mcR = cR >= 0 ? cR : cL;
+  const double rL = mat[mcL * 3], lL = mat[mcL * 3 + 1], uL = mat[mcL * 3 + 2];
+  const double rR = mat[mcR * 3], lR = mat[mcR * 3 + 1], uR = mat[mcR * 3 + 2];
+  double ir[3];
+  for (int gq = 0; gq < 3; ++gq) ir[gq] = 1.0 / fma(T.pz[gq], rR - rL, rL);
+  const double sL = sqrt((lL + 2.0 * uL) / rL), sR = sqrt((lR + 2.0 * uR) / rR);
+  out[f * FMAT] = (sL >= sR) ? sL : sR;
+  for (int v = 0; v < 9; ++v) {
+    const double bmu = v < 3 ? 0.0 : (v < 6 ? (v - 3 == d ? 2.0 : 0.0) : 1.0);
+    double acc = 0.0;
+    for (int gq = 0; gq < 3; ++gq) {
+      const double z = T.pz[gq];
+      const double lz = fma(z, lR - lL, lL), uz = fma(z, uR - uL, uL);
+      const double cl = -((v >= 3 && v < 6 ? lz : 0.0) + bmu * uz);
+      acc = fma(T.pw[gq], v < 3 ? -ir[gq] : cl, acc);
+    }
+    out[f * FMAT + 1 + v] = acc;
+  }
+}
+
+cudaError_t launch_face_material_elastic(const Geometry& g, const double* mat, const Tables& t,
+                                         double* out, cudaStream_t s) {
+  long long nf = 0;
+  for (int d = 0; d < 3; ++d) nf += (long long)(g.n[d] + 1) * (g.ncells / g.n[d]);
+  if (nf <= 0) return cudaSuccess;
+  k_face_material<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(g, mat, t, out);
+  return cudaGetLastError();
+}
+
 const Family* family_elastic3() {
   static Family f = [] {
     Family g = *FamilyImpl<Elastic, 3>::get();

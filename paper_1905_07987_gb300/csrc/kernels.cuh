@@ -660,6 +660,14 @@ __device__ __forceinline__ void riemann_face(const StepArgs& A, const Tables& T,
   // on the velocities.  mine_ncp = cb[lane] (lane < NV), s_ncp = the face's speed.
   double s_ncp = 0.0, mine_ncp = 0.0;
   if constexpr (P::NCP) {
+   if (A.fmat) {
+    // formed when the material was set (the same operations as below)
+    long long fo = f;
+    for (int dd = 0; dd < d; ++dd) fo += (long long)(g.n[dd] + 1) * FaceIdx::ntrans(g, dd);
+    const double* fm = A.fmat + fo * FMAT;
+    s_ncp = fm[0];
+    mine_ncp = lane < NV ? fm[1 + lane] : 0.0;
+   } else {
     const long long mcL = cL >= 0 ? cL : cR, mcR = cR >= 0 ? cR : cL;
     const double rL = A.mat[mcL * 3], lL = A.mat[mcL * 3 + 1], uL = A.mat[mcL * 3 + 2];
     const double rR = A.mat[mcR * 3], lR = A.mat[mcR * 3 + 1], uR = A.mat[mcR * 3 + 2];
@@ -680,6 +688,7 @@ __device__ __forceinline__ void riemann_face(const StepArgs& A, const Tables& T,
       const double cl = -((v >= 3 && v < 6 ? lz : 0.0) + bmu * uz);
       mine_ncp = fma(T.pw[gq], v < 3 ? -ir : cl, mine_ncp);
     }
+   }
     // interior face: the flux is elementwise over the face's NF x NV values, so the lanes walk
     // them contiguously (coalesced); each lane takes the jump of its row's source variable from
     // the same records and half its coefficient from lane v

@@ -104,17 +104,32 @@ __global__ void __launch_bounds__(128) k_adj_riemann(const __grid_constant__ Ste
   const long long mcL = cL >= 0 ? cL : cR, mcR = cR >= 0 ? cR : cL;
   const double rL = A.mat[mcL * 3], lL = A.mat[mcL * 3 + 1], uL = A.mat[mcL * 3 + 2];
   const double rR = A.mat[mcR * 3], lR = A.mat[mcR * 3 + 1], uR = A.mat[mcR * 3 + 2];
-  const double sL = Elastic::vp(rL, lL, uL), sR = Elastic::vp(rR, lR, uR);
-  const bool left_max = sL >= sR;
-  const double s = left_max ? sL : sR;
+  // the face's speed and path-averaged coefficients: from the per-face table when the material
+  // has been set (the same values), else formed here; the speeds of both sides only where the
+  // material gradient needs them (modes 0 and 2)
+  const double* fm = A.fmat ? A.fmat + (gface_off + f) * FMAT : nullptr;
+  double sL = 0.0, sR = 0.0, s = 0.0;
+  bool left_max = true;
+  if (MODE != 1 || !fm) {
+    sL = Elastic::vp(rL, lL, uL);
+    sR = Elastic::vp(rR, lR, uR);
+    left_max = sL >= sR;
+    s = left_max ? sL : sR;
+  } else {
+    s = fm[0];
+  }
   double cb[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     double acc = 0.0;
+    if (fm) {
+      acc = fm[1 + v];
+    } else {
 #pragma unroll
-    for (int gq = 0; gq < 3; ++gq) {
-      const double z = T.pz[gq];
-      acc = fma(T.pw[gq], Elastic::coef(d, v, fma(z, rR - rL, rL), fma(z, lR - lL, lL), fma(z, uR - uL, uL)), acc);
+      for (int gq = 0; gq < 3; ++gq) {
+        const double z = T.pz[gq];
+        acc = fma(T.pw[gq], Elastic::coef(d, v, fma(z, rR - rL, rL), fma(z, lR - lL, lL), fma(z, uR - uL, uL)), acc);
+      }
     }
     cb[v] = acc;
   }

@@ -206,8 +206,9 @@ def test_ck_and_picard_steps_agree_on_polynomial_data(order):
 
 
 def test_ck_is_rejected_where_it_is_not_built():
-    cfg = ader.make_config("elastic", 3, 3, (2, 2, 2), (0,) * 3, (1,) * 3, "absorbing",
-                           synth.cfl_number(3), predictor="ck")
+    # the adjoint of the CK step is built for orders 1-5 (the forward CK predictor for 1-6)
+    cfg = ader.make_config("elastic", 3, 6, (2, 2, 2), (0,) * 3, (1,) * 3, "absorbing",
+                           synth.cfl_number(6), predictor="ck")
     c = ader.Context(cfg)
     c.set_material(torch.from_numpy(synth.elastic_material((2, 2, 2), seed=1).reshape(-1).copy()).cuda())
     u = torch.zeros(c.count, dtype=torch.float64, device="cuda")
@@ -215,7 +216,7 @@ def test_ck_is_rejected_where_it_is_not_built():
     gm = torch.zeros(8 * 3, dtype=torch.float64, device="cuda")
     gM = torch.zeros(6, dtype=torch.float64, device="cuda")
     for static in (False, True):
-        with pytest.raises(ader.AderError) as e:  # the adjoint differentiates the Picard predictor
+        with pytest.raises(ader.AderError) as e:
             c.adjoint_step(0.0, 1e-3, u, lam, gm, gM, static=static)
         assert e.value.status == ader.EUNSUPPORTED
     c.close()

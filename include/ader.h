@@ -179,6 +179,19 @@ ader_status ader_sizes(const ader_ctx* ctx, int64_t* cells, int64_t* nodes_per_c
 ader_status ader_set_state(ader_ctx* ctx, const double* q, int64_t count, int on_device);
 ader_status ader_get_state(ader_ctx* ctx, double* q, int64_t count, int on_device);
 
+/* Advance n independent states held in host memory by one step each (Eq. (5)-(7) as ader_step):
+ * h_in[i] (host, ndof doubles) is a state at the context's current time t, h_out[i] (host, ndof
+ * doubles) receives the state after one step of it (dt, t_end as in ader_step; every state starts
+ * at t).  The host-to-device copy of state i+1 and the device-to-host copy of result i-1 run on
+ * two copy streams of the context while state i steps (pinned host memory lets them overlap the
+ * step; pageable memory works but serialises); two state-sized device buffers are allocated on
+ * the first call.  With the limiter each input's limiter data are initialised as by
+ * ader_set_state; receivers, if set, record every state's step.  Synchronises; afterwards the
+ * context holds the last result and its time.  Errors as ader_step (a failing step ends the
+ * batch; its outputs and later ones are not written). */
+ader_status ader_step_host_batch(ader_ctx* ctx, int n, const double* const* h_in,
+                                 double* const* h_out, double dt, double t_end);
+
 /* Per-cell material (rho, lambda, mu), [cells][3], for the elastic PDE.  Required before
  * stepping an elastic context. */
 ader_status ader_set_material(ader_ctx* ctx, const double* mat, int on_device);

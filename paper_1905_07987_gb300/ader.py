@@ -64,6 +64,7 @@ _SIGS = {
     "ader_sizes": ([_P, ctypes.POINTER(_L), ctypes.POINTER(_L), ctypes.POINTER(_I)], _I),
     "ader_set_state": ([_P, _P, _L, _I], _I),
     "ader_get_state": ([_P, _P, _L, _I], _I),
+    "ader_step_host_batch": ([_P, _I, _P, _P, _D, _D], _I),
     "ader_set_material": ([_P, _P, _I], _I),
     "ader_set_point_source": ([_P, _P, _P, _D, _D], _I),
     "ader_set_receivers": ([_P, _I, _P, _P, _L], _I),
@@ -242,6 +243,25 @@ class Context:
             raise ValueError("output array must be contiguous float64")
         check(lib().ader_get_state(self._h, p, n, dev), "ader_get_state")
         return out
+
+    def step_host_batch(self, h_in, h_out, dt=0.0, t_end=0.0):
+        """One step of each of the host states h_in[i] (host tensors or arrays, pinned memory
+        for overlapped copies) into h_out[i]; see ader_step_host_batch."""
+        n = len(h_in)
+        if len(h_out) != n:
+            raise ValueError("h_in and h_out differ in length")
+        ins, outs, keep = (ctypes.c_void_p * n)(), (ctypes.c_void_p * n)(), []
+        for i in range(n):
+            for a, dst in ((h_in[i], ins), (h_out[i], outs)):
+                p, dev, k, cnt = _ptr(a)
+                if dev or cnt != self.count:
+                    raise ValueError("host state of %d doubles expected" % self.count)
+                if a is h_out[i] and isinstance(a, np.ndarray) and k is not a:
+                    raise ValueError("output array must be contiguous float64")
+                dst[i] = p
+                keep.append(k)
+        check(lib().ader_step_host_batch(self._h, n, ins, outs, float(dt), float(t_end)),
+              "ader_step_host_batch")
 
     def set_material(self, mat):
         p, dev, keep, n = _ptr(mat)

@@ -326,6 +326,11 @@ struct ader_ctx {
   int nf = 0;
   double* u = nullptr;
   double* u_next = nullptr;
+  // ader_step_host_batch: staging state buffers (input, output), copy streams and their events
+  double* hb_in = nullptr;
+  double* hb_out = nullptr;
+  cudaStream_t hb_cin = nullptr, hb_cout = nullptr;
+  cudaEvent_t hb_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   double* face = nullptr;
   double* phi = nullptr;
   double* fmat = nullptr;    // elastic: per-face material terms of the Riemann solver
@@ -388,6 +393,12 @@ static void free_all(ader_ctx* c) {
   cudaFree(c->face);
   cudaFree(c->phi);
   cudaFree(c->fmat);
+  cudaFree(c->hb_in);
+  cudaFree(c->hb_out);
+  if (c->hb_cin) cudaStreamDestroy(c->hb_cin);
+  if (c->hb_cout) cudaStreamDestroy(c->hb_cout);
+  for (cudaEvent_t e : c->hb_ev)
+    if (e) cudaEventDestroy(e);
   cudaFree(c->fspeed);
   cudaFree(c->mat);
   cudaFree(c->dev);
@@ -661,6 +672,72 @@ ader_status ader_get_state(ader_ctx* c, double* q, int64_t count, int on_device)
   if (!c->state_set) return ADER_ESTATE;
   return copy(q, c->u, count * sizeof(double),
               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream, !on_device);
+}
+
+static ader_status step_impl(ader_ctx* c, double dt, double t_end);
+
+ader_status ader_step_host_batch(ader_ctx* c, int n, const double* const* h_in,
+                                 double* const* h_out, double dt, double t_end) {
+  if (!c || n < 1 || !h_in || !h_out) return ADER_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!h_in[i] || !h_out[i]) return ADER_EINVAL;
+  if (c->cfg.pde == ADER_PDE_ELASTIC && !c->mat_set) return ADER_ESTATE;
+  const size_t bytes = (size_t)c->ndof * sizeof(double);
+  if (!c->hb_in) {
+    cudaError_t e = cudaMalloc(&c->hb_in, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->hb_out, bytes);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->hb_cin, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->hb_cout, cudaStreamNonBlocking);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+      e = cudaEventCreateWithFlags(&c->hb_ev[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? ADER_ENOMEM : ADER_ECUDA;
+    }
+  }
+  double t0 = 0.0;
+  CUDA_OK(cudaMemcpyAsync(&t0, &c->dev->t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(cudaStreamSynchronize(c->stream));
+  // events: 0 input landed in hb_in, 1 hb_in consumed (copied into the state), 2 result in
+  // hb_out, 3 hb_out drained to the host
+  cudaEvent_t in_ready = c->hb_ev[0], in_free = c->hb_ev[1], out_ready = c->hb_ev[2],
+              out_free = c->hb_ev[3];
+  CUDA_OK(cudaMemcpyAsync(c->hb_in, h_in[0], bytes, cudaMemcpyHostToDevice, c->hb_cin));
+  CUDA_OK(cudaEventRecord(in_ready, c->hb_cin));
+  ader_status st = ADER_OK;
+  for (int i = 0; i < n && st == ADER_OK; ++i) {
+    // the input into the state; the next input may then land in hb_in while this one steps
+    CUDA_OK(cudaStreamWaitEvent(c->stream, in_ready, 0));
+    CUDA_OK(cudaMemcpyAsync(c->u, c->hb_in, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_OK(cudaEventRecord(in_free, c->stream));
+    if (i + 1 < n) {
+      CUDA_OK(cudaStreamWaitEvent(c->hb_cin, in_free, 0));
+      CUDA_OK(cudaMemcpyAsync(c->hb_in, h_in[i + 1], bytes, cudaMemcpyHostToDevice, c->hb_cin));
+      CUDA_OK(cudaEventRecord(in_ready, c->hb_cin));
+    }
+    if (c->cfg.limiter) {
+      CUDA_OK(c->fam->lim_init(c->cfg.order, c->u, nullptr, nullptr, c->rep, c->mm, c->g.ncells,
+                               c->sub, c->stream));
+      CUDA_OK(cudaMemsetAsync(c->flags, 0, c->g.ncells, c->stream));
+      if (c->lstatus) CUDA_OK(cudaMemsetAsync(c->lstatus, 0, c->g.ncells, c->stream));
+    }
+    c->state_set = true;
+    CUDA_OK(launch_set_scalars(c->dev, t0, 0.0, c->stream));
+    st = step_impl(c, dt, t_end);
+    if (st != ADER_OK) break;
+    // the result into hb_out once the previous result has left it, then to the host
+    if (i > 0) CUDA_OK(cudaStreamWaitEvent(c->stream, out_free, 0));
+    CUDA_OK(cudaMemcpyAsync(c->hb_out, c->u, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_OK(cudaEventRecord(out_ready, c->stream));
+    CUDA_OK(cudaStreamWaitEvent(c->hb_cout, out_ready, 0));
+    CUDA_OK(cudaMemcpyAsync(h_out[i], c->hb_out, bytes, cudaMemcpyDeviceToHost, c->hb_cout));
+    CUDA_OK(cudaEventRecord(out_free, c->hb_cout));
+  }
+  CUDA_OK(cudaStreamSynchronize(c->hb_cin));
+  CUDA_OK(cudaStreamSynchronize(c->hb_cout));
+  CUDA_OK(cudaStreamSynchronize(c->stream));
+  if (st != ADER_OK) return st;
+  return ader_sync(c);
 }
 
 ader_status ader_set_material(ader_ctx* c, const double* mat, int on_device) {

@@ -244,3 +244,30 @@ def test_cfl_dt_matches_the_oracle(state, prec):
     dt = c.ctx.last_dt()
     ref = float(c.oracle.cfl_dt(torch.from_numpy(u0)))
     assert abs(dt - ref) <= 2e-15 * ref, (dt, ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_step_host_batch_equals_the_step_loop(precision):
+    """ader_step_host_batch (host states in and out, copies overlapped on copy streams) gives, for
+    every state, the bits of set_state / step / get_state from the same time; the context ends
+    with the last result."""
+    c = Case("euler", 3, 3, (6, 5, 4), precision=precision)
+    x, _ = ader.reference_nodes(3)
+    base = synth.entropy_wave(c.X)
+    rng = np.random.default_rng(5)
+    ins = [torch.from_numpy((base * (1.0 + 0.01 * k) + 0.001 * rng.standard_normal(c.shape))
+                            .reshape(-1).copy()).pin_memory() for k in range(4)]
+    outs = [torch.empty(c.ctx.count, dtype=torch.float64).pin_memory() for _ in ins]
+    c.ctx.set_time(0.25)
+    c.ctx.step_host_batch(ins, outs)
+    last = torch.empty(c.ctx.count, dtype=torch.float64, device="cuda")
+    c.ctx.get_state(last)
+    for k, u in enumerate(ins):
+        c.ctx.set_state(u.cuda())
+        c.ctx.set_time(0.25)
+        c.ctx.step()
+        ref = torch.empty(c.ctx.count, dtype=torch.float64, device="cuda")
+        c.ctx.get_state(ref)
+        torch.cuda.synchronize()
+        assert torch.equal(outs[k], ref.cpu()), k
+    assert torch.equal(last.cpu(), outs[-1])

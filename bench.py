@@ -737,15 +737,13 @@ def extra_explosion(ader, synth, stream, steps=200, warmup=3, n=64):
     return out
 
 
-def extra_ensemble(ader, synth, stream, steps=4):
-    """16 elastic order-4 runs, cube sides drawn by seed from {24,32,40,48,64}, each with its own
-    seeded material and source, mixed predictor, advanced by one CUDA graph per step block; the
-    autotuner picks between one persistent launch per phase for all runs and per-run kernels on
-    forked streams."""
+def _ensemble(ader, synth, stream, sides, predictor):
+    """The 16-run ensemble (mixed precision) with its materials, sources and zero states; the
+    fixed dt of all runs."""
     import torch
-    sides = synth.ensemble_sides(16)
     cfgs = [ader.make_config("elastic", 3, 4, (s,) * 3, (0, 0, 0), (0.5 * s,) * 3, "absorbing",
-                             synth.cfl_number(4), precision="mixed") for s in sides]
+                             synth.cfl_number(4), precision="mixed", predictor=predictor)
+            for s in sides]
     ens = ader.Ensemble(cfgs, stream=stream.cuda_stream)
     dts = []
     for i, (s, r) in enumerate(zip(sides, ens.runs)):
@@ -756,12 +754,13 @@ def extra_ensemble(ader, synth, stream, steps=4):
         r.set_time(0.45)
         vpmax = float(np.sqrt((mat[:, 1] + 2 * mat[:, 2]) / mat[:, 0]).max())
         dts.append(synth.cfl_number(4) / (3 * 9) * 0.5 / vpmax)
-    dt = min(dts)  # one fixed dt for the ensemble (as for the adjoint runs)
-    # the launch shapes the autotuner chooses between, each timed here too: per-run kernels on
-    # forked streams, one persistent launch per phase, one cooperative launch for whole steps
+    return ens, min(dts)  # one fixed dt for the ensemble (as for the adjoint runs)
+
+
+def _time_shapes(ens, dt, stream, shapes_in):
+    import torch
     shapes = {}
-    for name, shape in (("per_run_4_branches", (4, 4, 1)), ("persistent_per_phase", (0, 4, 2)),
-                        ("fused_cooperative", (-1, 4, 2))):
+    for name, shape in shapes_in:
         ens.set_launch(*shape)
         ens.step(4, dt=dt)
         ens.sync()
@@ -772,6 +771,22 @@ def extra_ensemble(ader, synth, stream, steps=4):
         torch.cuda.synchronize()
         ens.sync()
         shapes[name] = f0.elapsed_time(f1) / 4
+    return shapes
+
+
+def extra_ensemble(ader, synth, stream, steps=4):
+    """16 elastic order-4 runs, cube sides drawn by seed from {24,32,40,48,64}, each with its own
+    seeded material and source, mixed predictor, advanced by one CUDA graph per step block; the
+    autotuner picks between one persistent launch per phase for all runs, one cooperative launch
+    for whole steps and per-run kernels on forked streams.  The same runs with the mixed
+    Cauchy-Kowalevski predictor beside it (persistent launch per phase, or per-run kernels)."""
+    import torch
+    sides = synth.ensemble_sides(16)
+    ens, dt = _ensemble(ader, synth, stream, sides, "picard")
+    # the launch shapes the autotuner chooses between, each timed here too
+    shapes = _time_shapes(ens, dt, stream, (("per_run_4_branches", (4, 4, 1)),
+                                            ("persistent_per_phase", (0, 4, 2)),
+                                            ("fused_cooperative", (-1, 4, 2))))
     best = ens.autotune(dt)
     ens.step(2, dt=dt)
     ens.sync()
@@ -784,6 +799,11 @@ def extra_ensemble(ader, synth, stream, steps=4):
     ens.sync()
     dofs = sum(s ** 3 for s in sides) * 125 * 9
     ens.close()
+    ens, dt_ck = _ensemble(ader, synth, stream, sides, "ck")
+    ck_shapes = _time_shapes(ens, dt_ck, stream, (("per_run_4_branches", (4, 4, 1)),
+                                                  ("persistent_per_phase", (0, 4, 1))))
+    ens.close()
+    ck_ms = min(ck_shapes.values())
     return {"workload": "ensemble16_elastic_p4", "sides": sides, "dofs": dofs,
             "ms_per_step": ms / steps, "value": dofs * steps / (ms * 1e-3), "unit": "DOF-updates/s",
             "dtype": "f32+f64", "autotuned": {"branches": best[0], "steps_per_graph": best[1],
@@ -792,7 +812,10 @@ def extra_ensemble(ader, synth, stream, steps=4):
             "launch": {0: "persistent launches shared by all runs, one per phase",
                        -1: "one cooperative persistent launch for whole steps"}.get(
                            best[0], "per-run kernels on %d forked streams" % best[0]),
-            "ms_per_step_by_launch_shape": shapes}
+            "ms_per_step_by_launch_shape": shapes,
+            "ck_mixed": {"predictor": "Cauchy-Kowalevski, mixed", "ms_per_step": ck_ms,
+                         "value": dofs / (ck_ms * 1e-3),
+                         "ms_per_step_by_launch_shape": ck_shapes}}
 
 
 def _ensemble_gradient(ader, synth, stream, sides, steps, k, predictor):

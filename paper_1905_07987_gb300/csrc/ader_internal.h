@@ -213,6 +213,10 @@ struct Family {
   // numerical fluxes per face node and variable the Riemann kernel writes (2: the left and right
   // cells see different values, a path-conservative fluctuation); sizes the flux buffer
   int nphi;
+  // one step of every run of an ensemble with the Cauchy-Kowalevski predictor (prec 0 FP64, 1
+  // mixed; orders with one cell per predictor block); null when the family has no such path
+  cudaError_t (*ens_step_ck)(const StepArgs* runs, const EnsTable& E, const Tables& t,
+                             const TablesF& f, int prec, int order, cudaStream_t s);
   // `steps` steps of every run of an ensemble as one cooperative persistent launch with grid-wide
   // barriers (bar: device barrier state; limit: polls of a barrier wait before it gives up); null
   // when the family has no batched path
@@ -221,6 +225,7 @@ struct Family {
                            long long limit, int blocks_per_sm, cudaStream_t s);
 };
 cudaError_t launch_set_scalars(DevScalars* d, double t, double dt, cudaStream_t s);
+cudaError_t launch_copy(double* dst, const double* src, long long n, cudaStream_t s);
 cudaError_t launch_merge_status(DevScalars* src, DevScalars* dst, cudaStream_t s);
 cudaError_t launch_seed_status(const uint8_t* flags, uint8_t* status, long long ncells,
                                int persist, cudaStream_t s);

@@ -708,7 +708,7 @@ ader_status ader_step_host_batch(ader_ctx* c, int n, const double* const* h_in,
   for (int i = 0; i < n && st == ADER_OK; ++i) {
     // the input into the state; the next input may then land in hb_in while this one steps
     CUDA_OK(cudaStreamWaitEvent(c->stream, in_ready, 0));
-    CUDA_OK(cudaMemcpyAsync(c->u, c->hb_in, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_OK(launch_copy(c->u, c->hb_in, c->ndof, c->stream));
     CUDA_OK(cudaEventRecord(in_free, c->stream));
     if (i + 1 < n) {
       CUDA_OK(cudaStreamWaitEvent(c->hb_cin, in_free, 0));
@@ -727,7 +727,7 @@ ader_status ader_step_host_batch(ader_ctx* c, int n, const double* const* h_in,
     if (st != ADER_OK) break;
     // the result into hb_out once the previous result has left it, then to the host
     if (i > 0) CUDA_OK(cudaStreamWaitEvent(c->stream, out_free, 0));
-    CUDA_OK(cudaMemcpyAsync(c->hb_out, c->u, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_OK(launch_copy(c->hb_out, c->u, c->ndof, c->stream));
     CUDA_OK(cudaEventRecord(out_ready, c->stream));
     CUDA_OK(cudaStreamWaitEvent(c->hb_cout, out_ready, 0));
     CUDA_OK(cudaMemcpyAsync(h_out[i], c->hb_out, bytes, cudaMemcpyDeviceToHost, c->hb_cout));
@@ -1466,10 +1466,17 @@ static ader_status ens_capture(ader_ensemble* e, int steps, double dt, double t_
 static bool ens_batchable(const ader_ensemble* e, double dt) {
   if (!(dt > 0.0) || e->runs.empty() || (int)e->runs.size() > ENS_MAXR) return false;
   const ader_ctx* a = e->runs[0];
-  if (!a->fam->ens_step || a->cfg.order > 5) return false;
+  if (a->cfg.order > 5) return false;
+  // Picard runs, or Cauchy-Kowalevski runs (FP64 or mixed) at the orders with one cell per block
+  if (a->cfg.predictor == ADER_PREDICTOR_CK) {
+    if (!a->fam->ens_step_ck || a->cfg.order < 4 || a->cfg.precision > ADER_PREC_MIXED)
+      return false;
+  } else if (!a->fam->ens_step) {
+    return false;
+  }
   for (const ader_ctx* c : e->runs) {
     if (c->fam != a->fam || c->cfg.order != a->cfg.order || c->cfg.precision != a->cfg.precision ||
-        c->cfg.predictor != ADER_PREDICTOR_PICARD ||
+        c->cfg.predictor != a->cfg.predictor ||
         c->cfg.limiter || c->rec.nrec > 0 || c->p.gamma != a->p.gamma)
       return false;
     for (int d = 0; d < 3; ++d)
@@ -1528,9 +1535,11 @@ static ader_status ens_capture_persistent(ader_ensemble* e, int steps, double dt
     ce = a->fam->ens_fused(e->d_runs, E, a->tab, a->tabf, a->cfg.precision, a->cfg.order, steps,
                            e->d_bar, e->wait_limit, bps, cap);
   } else {
+    const bool ck = a->cfg.predictor == ADER_PREDICTOR_CK;
     for (int k = 0; k < steps && ce == cudaSuccess; ++k)
-      ce = a->fam->ens_step(e->d_runs + (size_t)k * nr, E, a->tab, a->tabf, a->cfg.precision,
-                            a->cfg.order, cap);
+      ce = (ck ? a->fam->ens_step_ck : a->fam->ens_step)(e->d_runs + (size_t)k * nr, E, a->tab,
+                                                         a->tabf, a->cfg.precision, a->cfg.order,
+                                                         cap);
   }
   cudaGraph_t g = nullptr;
   const cudaError_t ee = cudaStreamEndCapture(cap, &g);
@@ -1601,7 +1610,8 @@ ader_status ader_ensemble_step(ader_ensemble* e, int steps, double dt, double t_
   const int spg = e->steps_per_graph;
   const int ng = steps / spg, rest = steps % spg;
   if (ng > 0) {
-    const bool fused = e->branches < 0 && ens_batchable(e, dt) && e->runs[0]->fam->ens_fused;
+    const bool fused = e->branches < 0 && ens_batchable(e, dt) && e->runs[0]->fam->ens_fused &&
+                       e->runs[0]->cfg.predictor == ADER_PREDICTOR_PICARD;
     const bool persistent = (e->branches == 0 || fused) && ens_batchable(e, dt);
     const int nb = fused ? -1 : (persistent ? 0 : (e->branches > 0 ? e->branches : 1));
     bool same = e->gexec && e->g_steps == spg && e->g_dt == dt && e->g_tend == t_end &&
@@ -1685,7 +1695,7 @@ ader_status ader_ensemble_autotune(ader_ensemble* e, double dt, int* best, doubl
   if (ens_batchable(e, dt)) {
     cand.push_back({0, 1});
     cand.push_back({0, 2});
-    if (e->runs[0]->fam->ens_fused) {
+    if (e->runs[0]->fam->ens_fused && e->runs[0]->cfg.predictor == ADER_PREDICTOR_PICARD) {
       cand.push_back({-1, 1});
       cand.push_back({-1, 2});
     }

@@ -112,6 +112,37 @@ cudaError_t launch_misfit(const double* a, const double* b, long long n, double 
   return cudaGetLastError();
 }
 
+// Device-to-device copy of n doubles on the SMs (16-byte vectors; the copy engines stay free for
+// host transfers running beside it).
+__global__ void __launch_bounds__(256) k_copy(double* __restrict__ dst,
+                                              const double* __restrict__ src, long long n) {
+  const long long n2 = n / 2;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const double2* s2 = reinterpret_cast<const double2*>(src);
+  double2* d2 = reinterpret_cast<double2*>(dst);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride)
+    d2[i] = s2[i];
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) dst[n - 1] = src[n - 1];
+}
+
+cudaError_t launch_copy(double* dst, const double* src, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if ((((uintptr_t)dst) | ((uintptr_t)src)) & 15) {  // not 16-byte aligned: the runtime's copy
+    return cudaMemcpyAsync(dst, src, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  }
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 152;
+  }
+  const long long want = (n / 2 + 255) / 256;
+  const long long blocks = want < (long long)sms * 8 ? (want > 0 ? want : 1) : (long long)sms * 8;
+  k_copy<<<(unsigned)blocks, 256, 0, s>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_set_scalars(DevScalars* d, double t, double dt, cudaStream_t s) {
   k_set_scalars<<<1, 1, 0, s>>>(d, t, dt);
   return cudaGetLastError();

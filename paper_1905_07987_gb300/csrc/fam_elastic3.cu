@@ -10,6 +10,8 @@ cudaError_t ens_step_elastic3_mixed(const StepArgs* R, const EnsTable& E, const 
                                     const TablesF& F, int order, cudaStream_t s);
 cudaError_t predictor_ck_elastic3(const StepArgs& a, const Tables& t, const TablesF& f, int prec,
                                   cudaStream_t s);
+cudaError_t ens_step_ck_elastic3(const StepArgs* R, const EnsTable& E, const Tables& T,
+                                 const TablesF& F, int prec, int order, cudaStream_t s);
 cudaError_t ens_fused_elastic3_fp64(const StepArgs* R, const EnsTable& E, const Tables& T,
                                     const TablesF& F, int order, int steps, void* bar,
                                     long long limit, int bps, cudaStream_t s);
@@ -162,6 +164,7 @@ const Family* family_elastic3() {
     g.ens_step = &ens_step;
     g.predictor_ck = &predictor_ck_elastic3;
     g.ens_fused = &ens_fused;
+    g.ens_step_ck = &ens_step_ck_elastic3;
     return g;
   }();
   return &f;

@@ -99,9 +99,11 @@ __device__ __forceinline__ void ck_apply(const double* X, int j, const double (&
   }
 }
 
+// The CPB cells from c0 of one context (one block); the kernel below and the ensemble's
+// persistent kernel call it.
 template <int N>
-__global__ void __launch_bounds__(CfgCK<N>::TPB) k_predictor_ck(const __grid_constant__ StepArgs A,
-                                                               const __grid_constant__ Tables T) {
+__device__ __forceinline__ void predictor_ck_block(const StepArgs& A, const Tables& T,
+                                                   long long c0) {
   using C = CfgCK<N>;
   constexpr int n = C::n, NS = C::NS, NV = C::NV, NL = C::NL, NVP = C::NVP, CPB = C::CPB;
   constexpr int TPB = C::TPB, REC = C::REC, NF = C::NF, FR = NF * NV;
@@ -109,7 +111,6 @@ __global__ void __launch_bounds__(CfgCK<N>::TPB) k_predictor_ck(const __grid_con
   const int tid = threadIdx.x;
   const int slot = tid / NS;
   const int j = tid - slot * NS;
-  const long long c0 = (long long)blockIdx.x * CPB;
   const int ncb = (int)(A.g.ncells - c0 < CPB ? A.g.ncells - c0 : CPB);  // cells of this block
   const bool act = slot < ncb;
   const long long c = c0 + slot;
@@ -261,6 +262,12 @@ __global__ void __launch_bounds__(CfgCK<N>::TPB) k_predictor_ck(const __grid_con
 }
 
 template <int N>
+__global__ void __launch_bounds__(CfgCK<N>::TPB) k_predictor_ck(const __grid_constant__ StepArgs A,
+                                                               const __grid_constant__ Tables T) {
+  predictor_ck_block<N>(A, T, (long long)blockIdx.x * CfgCK<N>::CPB);
+}
+
+template <int N>
 cudaError_t launch_predictor_ck_n(const StepArgs& a, const Tables& t, cudaStream_t s) {
   using C = CfgCK<N>;
   static bool attr = false;
@@ -393,10 +400,11 @@ __device__ __forceinline__ void ck_apply_f(const float* X, int j, const float2* 
   }
 }
 
+// The CPB cells from c0 of one context (one block), mixed precision; the kernel below and the
+// ensemble's persistent kernel call it.
 template <int N>
-__global__ void __launch_bounds__(CfgCKM<N>::TPB, CfgCKM<N>::MINB)
-    k_predictor_ck_mixed(const __grid_constant__ StepArgs A, const __grid_constant__ Tables T,
-                         const __grid_constant__ TablesF F) {
+__device__ __forceinline__ void predictor_ck_mixed_block(const StepArgs& A, const Tables& T,
+                                                         const TablesF& F, long long c0) {
   using C = CfgCKM<N>;
   constexpr int n = C::n, NS = C::NS, NV = C::NV, NL = C::NL, CPB = C::CPB, TPB = C::TPB;
   constexpr int NVQ = C::NVQ, NVF = C::NVF, NF = C::NF, FR = NF * NV;
@@ -404,7 +412,6 @@ __global__ void __launch_bounds__(CfgCKM<N>::TPB, CfgCKM<N>::MINB)
   const int tid = threadIdx.x;
   const int slot = tid / NS;
   const int j = tid - slot * NS;
-  const long long c0 = (long long)blockIdx.x * CPB;
   const int ncb = (int)(A.g.ncells - c0 < CPB ? A.g.ncells - c0 : CPB);
   const bool act = slot < ncb;
   unsigned char* cell = smem_ck + (size_t)(act ? slot : 0) * C::CELL;
@@ -597,6 +604,13 @@ __global__ void __launch_bounds__(CfgCKM<N>::TPB, CfgCKM<N>::MINB)
       fc[(d * 2 + 1) * FR] = f2d_int(q1.h) + f2d_int(q1.l);
     }
   }
+}
+
+template <int N>
+__global__ void __launch_bounds__(CfgCKM<N>::TPB, CfgCKM<N>::MINB)
+    k_predictor_ck_mixed(const __grid_constant__ StepArgs A, const __grid_constant__ Tables T,
+                         const __grid_constant__ TablesF F) {
+  predictor_ck_mixed_block<N>(A, T, F, (long long)blockIdx.x * CfgCKM<N>::CPB);
 }
 
 template <int N>

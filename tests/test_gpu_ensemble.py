@@ -16,11 +16,12 @@ def _build():
     build.build()
 
 
-def member_configs(sides, order, precision="fp64"):
+def member_configs(sides, order, precision="fp64", predictor="picard"):
     cfgs = []
     for s in sides:
         cfgs.append(ader.make_config("elastic", 3, order, (s, s, s), (0, 0, 0), (0.5 * s,) * 3,
-                                     "absorbing", synth.cfl_number(order), precision=precision))
+                                     "absorbing", synth.cfl_number(order), precision=precision,
+                                     predictor=predictor))
     return cfgs
 
 
@@ -185,6 +186,28 @@ def test_fused_launch_barrier_timeout_is_reported_and_recoverable():
     ens.sync()
     for c in singles:
         c.run(4, dt=1e-3)
+    for a, b in zip(states(ens.runs), states(singles)):
+        assert np.array_equal(a, b)
+    ens.close()
+
+
+@pytest.mark.parametrize("order,prec,launch", [(4, "fp64", (0, 2, 1)), (4, "mixed", (0, 2, 1)),
+                                               (5, "mixed", (0, 4, 1)), (4, "mixed", (2, 2, 1))])
+def test_ck_ensemble_equals_separate_runs(order, prec, launch):
+    """Runs with the Cauchy-Kowalevski predictor: the persistent launch over all runs' cells
+    (branches 0, orders 4 and 5) and the per-run branches give each run exactly the result of
+    stepping it on its own."""
+    sides = [3, 5, 4, 2]
+    ens = ader.Ensemble(member_configs(sides, order, precision=prec, predictor="ck"))
+    singles = [ader.Context(c) for c in member_configs(sides, order, precision=prec, predictor="ck")]
+    for i, s in enumerate(sides):
+        setup_member(ens.runs[i], s, order, seed=i)
+        setup_member(singles[i], s, order, seed=i)
+    ens.set_launch(*launch)
+    ens.step(5, dt=1e-3)
+    ens.sync()
+    for c in singles:
+        c.run(5, dt=1e-3)
     for a, b in zip(states(ens.runs), states(singles)):
         assert np.array_equal(a, b)
     ens.close()

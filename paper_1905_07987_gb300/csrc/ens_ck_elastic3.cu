@@ -1,8 +1,10 @@
 // Batched ensemble step of the 3-D elastic family with the Cauchy-Kowalevski predictor (FP64 and
-// mixed precision), orders 4 and 5 (one cell per block): one persistent launch per phase for all
-// runs, as for the Picard predictor.  The predictor's blocks loop over the concatenated cells of
-// the runs and call the per-context kernels' block function with the cell's run; the Riemann
-// solver and the corrector are the ensemble's shared kernels.
+// mixed precision), orders 4 and 5 (one cell per block): one launch per phase for all runs, as for
+// the Picard predictor.  The predictor's blocks take the concatenated cells of the runs (one each)
+// and call the per-context kernels' block function with the cell's run; the Riemann solver and
+// the corrector are the ensemble's shared persistent kernels.  For these runs the per-run
+// launches on forked streams are faster (74.9 against 87.3 ms per step of the 16-run ensemble);
+// the autotuner chooses between them.
 #include "kernels_ck.cuh"
 #include "kernels_ensemble.cuh"
 
@@ -33,25 +35,21 @@ template <int N, bool MIXED>
 cudaError_t ens_step_ck_n(const StepArgs* R, const EnsTable& E, const Tables& T, const TablesF& F,
                           cudaStream_t s) {
   using G = EnsCKCfg<N, MIXED>;
-  static int grid = 0;
-  if (!grid) {
-    cudaError_t e = cudaFuncSetAttribute(k_ens_predictor_ck<N, MIXED>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)G::SMEM);
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_ens_predictor_ck<N, MIXED>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)G::SMEM);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-      return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ens_predictor_ck<N, MIXED>,
-                                                           G::TPB, G::SMEM)) != cudaSuccess)
-      return e;
-    grid = sms * (per > 0 ? per : 1);  // every block resident: one wave that loops over cells
+    attr = true;
   }
   cudaError_t e = launch_ens_dt(R, E.nr, s);
   if (e != cudaSuccess) return e;
+  // one block per cell of all runs (the block scheduler overlaps the cells' loads and work better
+  // than resident blocks looping over cells)
   const long long total = E.cell0[E.nr];
-  const unsigned blocks = (unsigned)(total < grid ? total : grid);
+  if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const unsigned blocks = (unsigned)total;
   k_ens_predictor_ck<N, MIXED><<<blocks, G::TPB, G::SMEM, s>>>(R, E, T, F);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int d = 0; d < 3; ++d) {

@@ -662,9 +662,10 @@ def extra_adjoint(ader, synth, stream, n=40, N=4, steps=12, k=4,
 def extra_explosion(ader, synth, stream, steps=200, warmup=3, n=64):
     """3-D spherical explosion, order 3, n^3 cells (default 64^3) on [-1,1]^3, wall boundaries,
     a-posteriori subcell limiter (7^3 subcells), the workload's 200 steps from t = 0 timed in
-    full (after `warmup` steps on the same data, then a reset): FP64 and mixed predictor, and the
+    full (after `warmup` steps on the same data, then a reset): FP64 and mixed predictor, the
     FP64 form with the hybrid ADER-DG / FV status (troubled cells stay FV two more steps, an FV
-    interface layer).  Per form: ms per step over the 200 steps, FV cells, conservation of mass
+    interface layer), and the FP64 and mixed forms with the continuous extension Runge-Kutta guess
+    and one Picard iteration (Sec. 5).  Per form: ms per step over the 200 steps, FV cells, conservation of mass
     and energy over the run, the minimum density and pressure at the end, and the symmetry of the
     last step's FV set under the reflections and axis permutations of the cube."""
     import torch
@@ -678,9 +679,15 @@ def extra_explosion(ader, synth, stream, steps=200, warmup=3, n=64):
     W = torch.from_numpy(np.einsum("i,j,k->ijk", w, w, w).reshape(-1)).cuda()
     dofs = n ** 3 * 64 * 5
     out = {"workload": f"explosion3d_p3_{n} (limiter on, {steps} steps from t = 0)", "dofs": dofs}
-    for form, prec, limiter in (("fp64", "fp64", 1), ("mixed", "mixed", 1), ("fp64_hybrid", "fp64", 3)):
+    # forms: (name, precision, limiter mode, initial guess, Picard iterations; 0 = N+1)
+    for form, prec, limiter, guess, iters in (("fp64", "fp64", 1, "constant", 0),
+                                              ("mixed", "mixed", 1, "constant", 0),
+                                              ("fp64_hybrid", "fp64", 3, "constant", 0),
+                                              ("fp64_cerk", "fp64", 1, "cerk", 1),
+                                              ("mixed_cerk", "mixed", 1, "cerk", 1)):
         cfg = ader.make_config("euler", 3, N, (n,) * 3, (-1,) * 3, (1,) * 3, "wall", synth.cfl_number(N),
-                               limiter=limiter, precision=prec)
+                               limiter=limiter, precision=prec, initial_guess=guess,
+                               picard_iters=iters)
         ctx = ader.Context(cfg, stream=stream.cuda_stream)
 
         def reset():
@@ -734,6 +741,8 @@ def extra_explosion(ader, synth, stream, steps=200, warmup=3, n=64):
         ctx.close()
     out["mixed_speedup"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
     out["hybrid_speedup"] = out["fp64"]["ms_per_step"] / out["fp64_hybrid"]["ms_per_step"]
+    for form in ("fp64_cerk", "mixed_cerk"):
+        out[form]["speedup_over_fp64"] = out["fp64"]["ms_per_step"] / out[form]["ms_per_step"]
     return out
 
 

@@ -20,10 +20,11 @@ def _build():
     build.build()
 
 
-def explosion_case(ncell, order, limiter=1, bc="wall", precision="fp64"):
+def explosion_case(ncell, order, limiter=1, bc="wall", precision="fp64", initial_guess="constant",
+                   picard_iters=0):
     dim = len(ncell)
     c = Case("euler", dim, order, ncell, lo=(-1.0,) * dim, hi=(1.0,) * dim, bc=bc, limiter=limiter,
-             precision=precision)
+             precision=precision, initial_guess=initial_guess, picard_iters=picard_iters)
     lim = Limiter(c.oracle)
     u0 = synth.explosion(c.X)
     Us = synth.explosion(synth.subcell_centres(lim.ns, c.ncell, c.lo, c.hi))
@@ -78,6 +79,21 @@ def test_limited_free_run_flags_identical_every_step():
     c, lim, u0, Us, flags, u, rep = explosion_case((12, 12), 3)
     gpu_set(c, u0, Us, flags)
     for step in range(12):
+        c.ctx.step()
+        dt = c.ctx.last_dt()
+        u, tr, rep, ok = lim.step(u, rep, torch.tensor(dt, dtype=torch.float64))
+        assert np.array_equal(c.ctx.flags().astype(bool), tr.numpy()), step
+    assert rel_linf(c.get(), u.numpy()) <= 1e-11
+
+
+@pytest.mark.parametrize("ncell", [(12, 12), (6, 5, 6)])
+def test_limited_run_with_the_cerk_guess(ncell):
+    """The limiter after the predictor started from the continuous extension Runge-Kutta guess
+    (Sec. 5) with one Picard iteration: troubled flags identical to the oracle's every step of a
+    free run, state 1e-11."""
+    c, lim, u0, Us, flags, u, rep = explosion_case(ncell, 3, initial_guess="cerk", picard_iters=1)
+    gpu_set(c, u0, Us, flags)
+    for step in range(8):
         c.ctx.step()
         dt = c.ctx.last_dt()
         u, tr, rep, ok = lim.step(u, rep, torch.tensor(dt, dtype=torch.float64))

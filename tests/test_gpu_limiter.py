@@ -262,3 +262,19 @@ def test_fallback_that_is_still_inadmissible_is_reported():
     with pytest.raises(ader.AderError) as e:
         c.ctx.sync()
     assert e.value.status == ader.EADMISSIBLE
+
+
+def test_host_batch_with_the_limiter_equals_the_step_loop():
+    """ader_step_host_batch on a limited context: every host state gets the limiter data of
+    ader_set_state (fresh DMP bounds from its own projection), so each result equals set_state /
+    step / get_state bit for bit."""
+    c, lim, u0, Us, flags, u, rep = explosion_case((8, 7), 3)
+    ins = [torch.from_numpy((u0 * (1.0 + 0.02 * k)).reshape(-1).copy()).pin_memory() for k in range(3)]
+    outs = [torch.empty(c.ctx.count, dtype=torch.float64).pin_memory() for _ in ins]
+    c.ctx.set_time(0.0)
+    c.ctx.step_host_batch(ins, outs)
+    for k, x in enumerate(ins):
+        c.ctx.set_state(x.cuda())
+        c.ctx.set_time(0.0)
+        c.ctx.step()
+        assert np.array_equal(c.get().reshape(-1), outs[k].numpy()), k

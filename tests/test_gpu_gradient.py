@@ -66,7 +66,8 @@ def test_misfit_and_gradient_match_the_oracle(predictor):
     s.source = PointSource(src.cell, src.xi, Mt, src.f0, src.t0)
     Jo = misfit(s, torch.from_numpy(u0), steps, dt, [torch.from_numpy(o) for o in obs], 0.5)
     go_m, go_M = torch.autograd.grad(Jo, [matt, Mt])
-    assert abs(J - float(Jo)) <= 1e-12 * abs(float(Jo))
+    jo = float(Jo.detach())
+    assert abs(J - jo) <= 1e-12 * abs(jo)
     assert np.abs(gm - go_m.numpy()).max() <= 1e-10 * np.abs(go_m.numpy()).max()
     assert np.abs(gM - go_M.numpy()).max() <= 1e-10 * np.abs(go_M.numpy()).max()
 

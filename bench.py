@@ -876,7 +876,9 @@ def extra_ensemble_adjoint(ader, synth, stream, steps=20, k=5, picard_steps=1):
     out = {"workload": "ensemble16_adjoint_p4 (batched misfit gradient)", "sides": sides,
            "dofs": dofs, "unit": "DOF-updates/s (gradient: forward, recomputation and adjoint, "
            "each step counted once; host wall clock around the synchronising call)",
-           "forward": "mixed", "adjoint": "f64"}
+           "forward": "mixed",
+           "adjoint": {"ck": "mixed precision (float-float base term, binary32 corrections, FP64 "
+                             "adjoint state and gradient sums)", "picard": "f64"}}
     out["ck"] = _ensemble_gradient(ader, synth, stream, sides, steps, k, "ck")
     if picard_steps:
         out["picard"] = _ensemble_gradient(ader, synth, stream, sides, picard_steps, 1, "picard")

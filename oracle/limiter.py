@@ -244,10 +244,14 @@ class Limiter:
         """One step of the hybrid ADER-DG / FV scheme (Sec. 3.5): cells stay FV for several steps
         after they were troubled, and their face neighbours form an interface layer that also
         computes with FV.  ``status``[C] holds the FV steps a cell still has to take (0: DG).
+          known  = (status > 0) | (face neighbours of those, with ``layer``): the cells that
+                   compute with FV in this step whatever their DG candidate;
+          detected = troubled candidates outside ``known`` (a known cell is not checked);
           FV set = detected | (status > 0) | (face neighbours of those, with ``layer``);
           status_new = persist where detected, else max(status - 1, 0).
-        The DG candidate of every cell is still checked (a cell that would be troubled restarts
-        its count).  With persist = 0 and layer = False this is ``step``.
+        With ``layer`` no result depends on the DG predictor of a cell with status > 0: its face
+        neighbours are known FV cells, so its DG data reach only candidates that are neither
+        checked nor kept.  With persist = 0 and layer = False this is ``step``.
         Returns (u_new, fv[C], rep_new, admissible, status_new)."""
         u_new, fv, rep_new, ok, detected = self.step(u, rep, dt, t, status=status, layer=layer,
                                                      return_detected=True)
@@ -264,6 +268,11 @@ class Limiter:
         D, ns = self.D, self.ns
         u_star, info = s.step(u, dt, t, details=True)
         troubled, cand = self.detect(u_star, rep)
+        if status is not None:
+            known = status > 0
+            if layer:
+                known = known | self.face_neighbours(known)
+            troubled = troubled & ~known
         detected = troubled
         if force:
             troubled = torch.ones_like(troubled)

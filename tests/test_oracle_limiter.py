@@ -295,6 +295,36 @@ def test_hybrid_with_every_cell_fv_is_the_pure_fv_scheme():
     assert torch.equal(u1, lim.reconstruct(U_all))
 
 
+def test_hybrid_does_not_use_the_dg_predictor_of_counting_cells():
+    """A cell with FV steps left computes with FV, and with the interface layer so do its face
+    neighbours, whose DG candidates are not checked either: its predictor's output reaches
+    nothing that is kept.  Replacing that output by NaN leaves the hybrid step bit-identical
+    (the GPU skips those cells' predictor)."""
+    s, lim, u, rep = explosion((8, 8), 2)
+    status = torch.zeros(64, dtype=torch.long)
+    for _ in range(2):
+        u, fv, rep, ok, status = lim.step_hybrid(u, rep, status, s.cfl_dt(u), persist=2)
+    counting = status > 0
+    assert counting.any() and not counting.all()
+    dt = s.cfl_dt(u)
+    ref = lim.step_hybrid(u, rep, status, dt, persist=2)
+    plain = s.predictor
+
+    def broken(uu, dtt, t=0.0, **kw):
+        q = plain(uu, dtt, t, **kw)
+        q[counting] = float("nan")
+        return q
+
+    s.predictor = broken
+    try:
+        got = lim.step_hybrid(u, rep, status, dt, persist=2)
+    finally:
+        del s.predictor
+    assert torch.isnan(broken(u, dt)).any()
+    for a, b in zip(ref, got):
+        assert torch.equal(a, b) if torch.is_tensor(a) else a == b
+
+
 # ---- first-order fallback of the FV recompute (Table 1: Godunov beside MUSCL-Hancock) --------
 
 def double_rarefaction(s, lim, nc, lo, hi, ul=-3.0, p=0.4):

@@ -127,7 +127,9 @@ typedef struct {
   int limiter;         /* a-posteriori FV subcell limiter (Euler, order <= 4): 0 off, 1 on,
                           2 every cell troubled (the pure FV scheme, for tests), 3 hybrid
                           ADER-DG / FV status (Sec. 3.5): a troubled cell stays FV for two
-                          more steps and its face neighbours also compute with FV; the
+                          more steps and its face neighbours also compute with FV; a cell
+                          with FV steps left, or next to one, is not checked on a DG
+                          candidate, and a cell with FV steps left skips the predictor; the
                           counts restart at ader_set_state, and the cells that
                           ader_set_subcell_state puts into the FV space start with two FV
                           steps to take */

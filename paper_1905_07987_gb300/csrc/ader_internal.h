@@ -177,6 +177,9 @@ struct StepArgs {
   // elastic: per face (directions concatenated) the wave speed max(vp_L, vp_R) and the nine
   // path-averaged coefficients of B_d, formed when the material is set (null: formed per step)
   const double* fmat;
+  // hybrid limiter: the cells with FV steps left (nonzero) skip the predictor; their face
+  // neighbours compute with FV too, so nothing kept reads their DG data (null: every cell)
+  const uint8_t* skip;
 };
 
 // Per (pde, dim) kernel family; order dispatch happens inside.

@@ -581,6 +581,13 @@ ader_status ader_create(const ader_config* cfg, void* stream, ader_ctx** out) {
       if (e == cudaSuccess) e = cudaMalloc(&c->lstatus, ncells);
       if (e == cudaSuccess) e = cudaMalloc(&c->lbase, ncells);
       if (e == cudaSuccess) e = cudaMemsetAsync(c->lstatus, 0, ncells, c->stream);
+      // the cells with FV steps left skip the predictor: their face records and candidate hold
+      // finite (unused) values from the start
+      if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->face, 0, ncells * cfg->dim * 2 * face_rec * sizeof(double), c->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(c->u_next, 0, c->ndof * sizeof(double), c->stream);
+      if (e == cudaSuccess && c->fspeed)
+        e = cudaMemsetAsync(c->fspeed, 0, ncells * cfg->dim * 2 * c->nf * sizeof(double), c->stream);
     }
   }
   if (e != cudaSuccess) {
@@ -892,6 +899,7 @@ static StepArgs make_args(ader_ctx* c, double dt, double t_end) {
   a.dev = c->dev;
   a.iters = c->cfg.picard_iters > 0 ? c->cfg.picard_iters : c->cfg.order + 1;
   a.cerk = c->cfg.initial_guess == ADER_GUESS_CERK ? 1 : 0;
+  a.skip = c->cfg.limiter == 3 ? c->lstatus : nullptr;
   a.src = c->src;
   a.dt_fixed = dt > 0 ? dt : 0.0;
   a.t_end = t_end > 0 ? t_end : 0.0;

@@ -542,6 +542,7 @@ __device__ __forceinline__ void predictor_cell(const StepArgs& A, const Tables& 
 template <class P, int D, int N>
 __global__ void __launch_bounds__(Cfg<P, D, N>::TPB)
     k_predictor(const __grid_constant__ StepArgs A, const __grid_constant__ Tables T) {
+  if (A.skip && A.skip[blockIdx.x]) return;  // computes with FV in this step
   predictor_cell<P, D, N>(A, T, blockIdx.x);
 }
 

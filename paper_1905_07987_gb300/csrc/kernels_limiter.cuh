@@ -251,6 +251,21 @@ __global__ void __launch_bounds__(128) k_lim_detect(const __grid_constant__ Step
   __shared__ long long red[2 * NV * 32];
   __shared__ long long bk[2][NV];
   const long long c = blockIdx.x;
+  if (L.status) {
+    // hybrid status: a cell with FV steps left, or next to one, computes with FV in this step
+    // and is not checked (its DG candidate may be built on skipped predictor data); the FV
+    // recompute writes its representation
+    bool known = L.status[c] != 0;
+    for (int d = 0; d < D; ++d)
+      for (int side = -1; side <= 1; side += 2) {
+        const long long nb = neighbor<D>(A.g, c, d, side);
+        if (nb >= 0 && L.status[nb] != 0) known = true;
+      }
+    if (known) {
+      if (threadIdx.x == 0) L.flags[c] = 0;
+      return;
+    }
+  }
   const double* u = A.u_next + c * (NN * NV);
   for (int e = threadIdx.x; e < NN * NV; e += blockDim.x) us[e] = u[e];
   if (threadIdx.x < NV) {

@@ -807,6 +807,7 @@ template <class P, int D, int N>
 __global__ void __launch_bounds__(CfgM<P, D, N>::TPB, CfgM<P, D, N>::MINB)
     k_predictor_mixed(const __grid_constant__ StepArgs A, const __grid_constant__ Tables T,
                       const __grid_constant__ TablesF F) {
+  if (A.skip && A.skip[blockIdx.x]) return;  // computes with FV in this step
   predictor_mixed_cell<P, D, N>(A, T, F, blockIdx.x);
 }
 

@@ -200,6 +200,50 @@ def test_hybrid_status_run_matches_the_oracle(ncell, order, steps, box):
     assert rel_linf(c.get(), u.numpy()) <= 1e-11
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_hybrid_with_every_cell_counting_is_the_pure_fv_step(precision):
+    """Every cell put into the FV space at the start (each counts `persist` FV steps): no cell is
+    checked and no DG result is kept, so the hybrid step is the oracle's pure FV step, whatever
+    the predictor's precision (the GPU skips every cell's predictor)."""
+    c, lim, u0, Us, flags, u, rep = explosion_case((6, 5, 4), 2, limiter=3, precision=precision)
+    every = np.ones_like(flags)
+    gpu_set(c, u0, Us, every)
+    u, rep = lim.initial_rep(torch.from_numpy(u0), torch.from_numpy(Us), torch.from_numpy(every))
+    status = lim.initial_status(torch.from_numpy(every), persist=2)
+    c.ctx.step()
+    dt = torch.tensor(c.ctx.last_dt(), dtype=torch.float64)
+    u1, fv, rep1, ok, status = lim.step_hybrid(u, rep, status, dt, persist=2)
+    U_all, _ = lim.fv_global(rep, dt)
+    assert fv.all() and torch.equal(rep1, U_all)
+    assert c.ctx.flags().astype(bool).all()
+    assert rel_linf(c.get(), u1.numpy()) <= TOL
+    assert np.abs(gpu_rep(c, lim) - rep1.numpy()).max() <= TOL * np.abs(rep1.numpy()).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_hybrid_skips_the_predictor_of_counting_cells(precision):
+    """The predictor launch of a step in which every cell counts FV steps does no work: its time
+    is a small fraction of the same launch with every cell in DG (24^3 cells, order 3)."""
+    n = 24
+    c, lim, u0, Us, flags, u, rep = explosion_case((n, n, n), 3, limiter=3, precision=precision)
+    every = np.ones_like(flags)
+
+    def predictor_ms(fl):
+        gpu_set(c, u0, Us, fl)
+        c.ctx.step()          # warm-up (the counts go from 2 to 1)
+        gpu_set(c, u0, Us, fl)
+        c.ctx.enable_timing(True)
+        c.ctx.step()
+        ph, nrec = c.ctx.phase_times()
+        c.ctx.enable_timing(False)
+        assert nrec == 1
+        return ph["predictor"]
+
+    full = predictor_ms(np.zeros_like(flags))
+    skipped = predictor_ms(every)
+    assert skipped < 0.2 * full, (skipped, full)
+
+
 def rel_linf_floored(a, b):
     """rel_linf with a variable that is zero up to round-off (its largest value below 1e-8 of the
     state's) measured against the size of the state."""

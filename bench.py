@@ -783,6 +783,81 @@ def _time_shapes(ens, dt, stream, shapes_in):
     return shapes
 
 
+def swe_model_flops_per_cell(N, D=2, nv=4, iters=None, cF=21):
+    """Algorithmic flops per cell and step of the shallow-water predictor in the sum-factorised
+    model: per Picard iteration the D derivative contractions of the nv flux components, the
+    derivative of the surface h + b for the non-conservative product g h d(h + b)/dx_d, the time
+    solve, and cF ~ 21 flops per space-time node for the fluxes and the product; then the same
+    epilogue as the Euler model.  38.1 k flop for the order-3 cell (N + 1 iterations)."""
+    n = N + 1
+    I = iters or n
+    it = (2 * D * nv + 2 * D + 2 * nv) * n ** (D + 2) + cF * n ** (D + 1)
+    epi = 2 * (2 * D + 1) * nv * n ** (D + 1) + 12 * D * nv * n ** D
+    return I * it + epi
+
+
+def extra_swe(ader, synth, stream, n=1024, N=3, steps=5, warmup=2):
+    """Shallow water equations with bathymetry (Eq. (9)), FP64, order 3 (the order of the paper's
+    oscillating lake), n^2 periodic cells on the unit square: a flow over a smooth bump (every term
+    active) timed per phase, the mass drift, and the lake at rest over the same bathymetry at full
+    size (surface and momentum after the steps: round-off)."""
+    import torch
+    x, w = ader.reference_nodes(N)
+    nc, lo, hi = (n, n), (0.0, 0.0), (1.0, 1.0)
+    X = synth.node_coordinates(x, nc, lo, hi)
+    npc = (N + 1) ** 2
+    dofs = n * n * npc * 4
+    W = torch.from_numpy(np.outer(w, w).reshape(-1)).cuda() / (n * n)
+    cfg = ader.make_config("swe", 2, N, nc, lo, hi, "periodic", synth.cfl_number(N))
+    ctx = ader.Context(cfg, stream=stream.cuda_stream)
+    out = {"workload": "swe2d_p3_%d (flow over a periodic bump, FP64)" % n, "dofs": dofs}
+
+    def mass():
+        u = _dev_state(ctx).view(n * n, npc, 4)
+        return float((u[:, :, 0] * W).sum())
+
+    u0 = torch.from_numpy(np.ascontiguousarray(synth.swe_flow_over_bump(X)).reshape(-1)).cuda()
+    ctx.set_state(u0)
+    ctx.set_time(0.0)
+    m0 = mass()
+    for _ in range(warmup):
+        ctx.step()
+    ctx.sync()
+    ctx.enable_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ph, nr = ctx.phase_times()
+    ctx.enable_timing(False)
+    ctx.sync()
+    pred = ph["predictor"] / max(nr, 1)
+    fl = swe_model_flops_per_cell(N) * n * n
+    peak = (_PEAKS[0] or {}).get("fp64")
+    out["fp64"] = {"ms_per_step": ms, "value": dofs / (ms * 1e-3),
+                   "phase_ms_per_step": {k: v / max(nr, 1) for k, v in ph.items()},
+                   "predictor_model_flops_per_cell": swe_model_flops_per_cell(N),
+                   "predictor_tflops": fl / (pred * 1e-3) / 1e12,
+                   "predictor_frac_of_fp64_peak": fl / (pred * 1e-3) / (peak * 1e12 if peak else FP64_PEAK),
+                   "fp64_peak_source": "measured in this run (libpeaks)" if peak else "derived",
+                   "mass_rel_drift": abs(mass() - m0) / abs(m0), "steps": warmup + steps}
+    lake = torch.from_numpy(np.ascontiguousarray(synth.swe_lake_at_rest(X)).reshape(-1)).cuda()
+    ctx.set_state(lake)
+    ctx.set_time(0.0)
+    for _ in range(steps):
+        ctx.step()
+    ctx.sync()
+    u = _dev_state(ctx).view(-1, 4)
+    out["lake_at_rest"] = {"steps": steps,
+                           "max_surface_deviation": float((u[:, 0] + u[:, 3] - 1.0).abs().max()),
+                           "max_momentum": float(u[:, 1:3].abs().max())}
+    ctx.close()
+    return out
+
+
 def extra_ensemble(ader, synth, stream, steps=4):
     """16 elastic order-4 runs, cube sides drawn by seed from {24,32,40,48,64}, each with its own
     seeded material and source, mixed predictor, advanced by one CUDA graph per step block; the
@@ -891,6 +966,7 @@ def extra_ensemble_adjoint(ader, synth, stream, steps=20, k=5, picard_steps=1):
 
 
 _WORLD = [1]
+_PEAKS = [None]  # the FMA throughputs measured by this run (rank 0)
 
 
 def barrier():
@@ -934,6 +1010,8 @@ def main():
                     help="comma list of the other workloads to run (default: all of them)")
     ap.add_argument("--elastic-n", type=int, default=81,
                     help="cells per side of the elastic workload (81; smaller for profiling)")
+    ap.add_argument("--swe-n", type=int, default=1024,
+                    help="cells per side of the shallow-water workload (1024; smaller for profiling)")
     ap.add_argument("--adjoint-forms", default="picard,ck,ck_mixed",
                     help="forms of the 40^3 adjoint workload (picard, ck, ck_mixed)")
     ap.add_argument("--adjoint-steps", type=int, default=20,
@@ -991,6 +1069,7 @@ def main():
     torch.cuda.synchronize()
 
     peaks = measure_fma_peaks(stream) if world == 1 or rank == 0 else None
+    _PEAKS[0] = peaks
     forms = [f for f in args.forms.split(",") if f]
     if args.prec not in forms:
         forms.append(args.prec)
@@ -1121,7 +1200,8 @@ def main():
                          ("euler2d_p3_27", extra_euler2d), ("explosion3d_p3_64", extra_explosion),
                          ("elastic3d_p5_81", extra_elastic), ("ensemble16_elastic_p4", extra_ensemble),
                          ("adjoint_elastic3d_p4_40", extra_adjoint), ("euler3d_p4_81_cerk", extra_cerk),
-                         ("ensemble16_adjoint_p4", extra_ensemble_adjoint)):
+                         ("ensemble16_adjoint_p4", extra_ensemble_adjoint),
+                         ("swe2d_p3_1024", extra_swe)):
             if args.extras and name not in args.extras.split(","):
                 continue
             try:
@@ -1136,6 +1216,8 @@ def main():
                                      forms=tuple(f for f in args.adjoint_forms.split(",") if f))
                 elif fn is extra_elastic:
                     extra[name] = fn(ader, synth, stream, n=args.elastic_n)
+                elif fn is extra_swe:
+                    extra[name] = fn(ader, synth, stream, n=args.swe_n)
                 else:
                     extra[name] = fn(ader, synth, stream)
             except Exception as exc:  # report, keep the headline line

@@ -125,6 +125,25 @@ def constant_state(X, rho=1.0, vel=None, p=1.0):
 
 # ------------------------------------------------------------------------------------------
 # Elastic workloads (Sec. 6.2): units km, s, g/cm^3 (so lambda, mu in GPa).
+def swe_flow_over_bump(X, L=1.0):
+    """Shallow water (h, hu, hv, b) on a periodic box of side L: a smooth periodic bathymetry with
+    a moving, perturbed surface (every term of the system active).  X: node coordinates (x, y)."""
+    x, y = X
+    b = 0.1 + 0.05 * np.sin(2 * math.pi * x / L) * np.cos(2 * math.pi * y / L)
+    h = 1.0 - b + 0.02 * np.cos(2 * math.pi * (x + 2 * y) / L)
+    hu = 0.3 * h * (1 + 0.1 * np.sin(2 * math.pi * y / L))
+    hv = -0.2 * h * (1 + 0.1 * np.cos(2 * math.pi * x / L))
+    return np.stack([h, hu, hv, b], axis=-1)
+
+
+def swe_lake_at_rest(X, L=1.0, level=1.0):
+    """Shallow water at rest over the bathymetry of swe_flow_over_bump: h + b = level, no flow."""
+    x, y = X
+    b = 0.1 + 0.05 * np.sin(2 * math.pi * x / L) * np.cos(2 * math.pi * y / L)
+    h = level - b
+    return np.stack([h, 0.0 * h, 0.0 * h, b], axis=-1)
+
+
 def smooth_field(ncell, seed, modes=8, min_wavelength_cells=8.0):
     """Seeded smooth field in [0,1] on the cell centres: sum of ``modes`` random Fourier modes
     with wavelengths >= ``min_wavelength_cells`` cells, affinely mapped to [0,1]."""

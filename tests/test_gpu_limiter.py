@@ -47,7 +47,9 @@ def gpu_rep(c, lim):
 
 
 @pytest.mark.parametrize("dim,ncell,order", [(2, (10, 10), 2), (2, (9, 8), 3), (3, (6, 6, 6), 3),
-                                             (3, (5, 4, 6), 2), (3, (4, 4, 4), 4)])
+                                             (3, (5, 4, 6), 2), (3, (4, 4, 4), 4),
+                                             # one cell thick: the FV halo reflects inside the cell
+                                             (2, (1, 8), 2), (3, (1, 5, 4), 2), (2, (6, 1), 3)])
 def test_limited_steps_teacher_forced(dim, ncell, order):
     c, lim, u0, Us, flags, u, rep = explosion_case(ncell, order)
     gpu_set(c, u0, Us, flags)

@@ -206,6 +206,40 @@ def test_full_size_sampled_cells_euler_81():
         assert rel_linf(got[centre], out[13]) <= TOL, (i, j, k)
 
 
+@pytest.mark.parametrize("ncell,bc", [((1, 1, 1), "periodic"), ((1, 3, 2), "wall"),
+                                       ((4, 1, 1), "absorbing"), ((1, 1), "periodic"),
+                                       ((1, 5), "wall"), ((3, 1), [("periodic", "periodic"), ("wall", "absorbing")])])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_grids_one_cell_thick(ncell, bc, prec):
+    """Degenerate grids one cell thick in some direction: a periodic cell is its own face
+    neighbour (both faces of the line are the same face), a wall cell has walls on both sides.
+    One Euler step against the oracle (FP64 1e-12; mixed within 2e-6 of the step's change)."""
+    dim = len(ncell)
+    c = Case("euler", dim, 3, ncell, lo=(-1.0,) * dim, hi=(1.0,) * dim, bc=bc, precision=prec)
+    u0 = synth.entropy_wave(c.X)
+    c.set(u0)
+    c.ctx.step()
+    dt = c.ctx.last_dt()
+    ref = c.oracle_step(u0, dt)
+    if prec == "fp64":
+        assert rel_linf(c.get(), ref) <= TOL
+    else:
+        assert np.abs(c.get() - ref).max() <= 2e-6 * np.abs(ref - u0).max()
+
+
+@pytest.mark.parametrize("ncell", [(1, 1, 1), (1, 2, 3), (3, 1, 1)])
+def test_elastic_ck_on_grids_one_cell_thick(ncell):
+    """The Cauchy-Kowalevski elastic step (absorbing boundaries) on grids one cell thick."""
+    mat = synth.elastic_material(ncell, seed=7)
+    c = Case("elastic", 3, 3, ncell, lo=(0.0,) * 3, hi=tuple(0.5 * n for n in ncell), bc="absorbing",
+             material=mat, predictor="ck")
+    u0 = synth.plane_wave_elastic(c.X, mat.reshape(-1, 3)[0], L=0.5 * max(ncell))
+    c.set(u0)
+    c.ctx.step()
+    dt = c.ctx.last_dt()
+    assert rel_linf(c.get(), c.oracle_step(u0, dt)) <= TOL
+
+
 def test_configurations_beyond_the_kernels_are_rejected_at_create():
     """The 3-D Euler mixed predictor at order 6 needs more shared memory than a block has: the
     context is refused up front instead of failing at the first step."""

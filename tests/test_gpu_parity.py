@@ -233,7 +233,12 @@ def test_elastic_ck_on_grids_one_cell_thick(ncell):
     mat = synth.elastic_material(ncell, seed=7)
     c = Case("elastic", 3, 3, ncell, lo=(0.0,) * 3, hi=tuple(0.5 * n for n in ncell), bc="absorbing",
              material=mat, predictor="ck")
-    u0 = synth.plane_wave_elastic(c.X, mat.reshape(-1, 3)[0], L=0.5 * max(ncell))
+    m, L = (2.7, 30.0, 25.0), 0.5 * max(ncell)
+    # four superposed plane waves: all nine components vary (none is zero up to round-off)
+    u0 = (synth.plane_wave_elastic(c.X, m, kind='p', L=L)
+          + synth.plane_wave_elastic(c.X, m, kind='s', L=L / 2)
+          + synth.plane_wave_elastic(c.X, m, kind='s', direction=(0.0, 1.0, 0.0), L=L / 3)
+          + synth.plane_wave_elastic(c.X, m, kind='s', direction=(0.0, 0.0, 1.0), L=L / 2))
     c.set(u0)
     c.ctx.step()
     dt = c.ctx.last_dt()

@@ -305,3 +305,26 @@ def test_ck_full_size_sampled_cells_elastic_81(precision):
             print("tf32x3 81^3 cell %s: error / neighbourhood step change %.3e" % ((i, j, k), err))
             assert err < TOL_TC_SMOOTH, (i, j, k)
     ctx.close()
+
+
+@pytest.mark.parametrize("predictor", ["picard", "ck"])
+def test_elastic_nonfinite_state_is_reported(predictor):
+    """A NaN in the elastic state reaches the new state through the update u^n + dt (...), where
+    the corrector latches it (the CFL kernel reads only the material): ADER_ENONFINITE at the next
+    ader_sync, with the CFL dt and with a fixed dt; a clean state afterwards steps normally."""
+    ncell = (4, 3, 4)
+    mat = synth.elastic_material(ncell, seed=3)
+    c = Case("elastic", 3, 3, ncell, lo=(0.0,) * 3, hi=tuple(0.5 * n for n in ncell),
+             bc="absorbing", material=mat, predictor=predictor)
+    u0 = waves(c.X, 2.0)
+    bad = u0.copy()
+    bad[5, 1, 2, 0, 4] = np.nan
+    for dt in (0.0, 1e-3):
+        c.set(bad)
+        c.ctx.step(dt)
+        with pytest.raises(ader.AderError) as e:
+            c.ctx.sync()
+        assert e.value.status == ader.ENONFINITE, dt
+    c.set(u0)
+    c.ctx.step()
+    c.ctx.sync()

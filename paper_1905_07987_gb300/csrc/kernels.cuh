@@ -15,6 +15,7 @@ namespace ader {
 // Compile-time sizes of the order-N scheme for system P in D dimensions.
 template <class P, int D, int N>
 struct Cfg {
+  static constexpr int DIM = D;
   static constexpr int n = N + 1;               // nodes per direction (and time nodes)
   static constexpr int NS = ipow(n, D);         // spatial nodes per cell
   static constexpr int NST = NS * n;            // space-time nodes per cell
@@ -28,7 +29,9 @@ struct Cfg {
   static constexpr int LPT = (NL + TPB - 1) / TPB;   // lines per thread
   static constexpr int NPT = (NST + TPB - 1) / TPB;  // space-time nodes per thread
   static constexpr int FSLOTS = P::CONS ? cmax(n, D + 1) : 0;
-  static constexpr size_t SMEM = (size_t)(n + FSLOTS) * NL * sizeof(double);
+  // shallow water: the surface derivatives d(h + b)/dx_d at every space-time node [NST][D]
+  static constexpr int GSLOTS = P::NCPS ? NST * D : 0;
+  static constexpr size_t SMEM = ((size_t)(n + FSLOTS) * NL + GSLOTS) * sizeof(double);
 };
 
 template <int n, int d>
@@ -93,31 +96,52 @@ __device__ __forceinline__ void contract_ncp_elastic(const double* X, const doub
   }
 }
 
+// Shallow water: the derivative of the surface h + b along every direction at the owned
+// space-time nodes, G[node][d] = sum_m D[j_d][m] (h + b)(t, j with j_d -> m) (node = t NS + j,
+// m ascending), one thread per node so that every lane works; the momentum lines of direction d
+// then take g h G (ncp_swe_lines) instead of each forming the sum itself.
+template <class C, int RS>
+__device__ __forceinline__ void surface_derivs(const double* X, const double* Dm, double* G, int tid) {
+  constexpr int n = C::n, NV = C::NV, NL = C::NL, NS = C::NS, D = C::DIM;
+#pragma unroll
+  for (int k = 0; k < C::NPT; ++k) {
+    const int node = tid + k * C::TPB;
+    if (node < C::NST) {
+      const int t = node / NS, j = node - t * NS;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const int st = d == 0 ? 1 : (d == 1 ? n : n * n);
+        const int jd = (j / st) % n;
+        const int j0 = j - jd * st;
+        const double* Dr = Dm + jd * RS;
+        double acc = 0.0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          const double* q = X + t * NL + (j0 + m * st) * NV;
+          acc = fma(Dr[m], q[0] + q[3], acc);
+        }
+        G[node * D + d] = acc;
+      }
+    }
+  }
+}
+
 // Shallow water: row 1 + d of B_d(q) dq/dx_d is g h (dh/dx_d + db/dx_d) with the node's own h
-// (state-dependent non-conservative product), accumulated as R -= g h (1/h_d) D_d (h + b).
-template <class C, int d, int RS>
-__device__ __forceinline__ void contract_ncp_swe(const double* X, const double* Dm, double inv_h,
-                                                 double grav, double (&R)[C::LPT][C::n], int tid) {
-  constexpr int n = C::n, NV = C::NV, NL = C::NL, TPB = C::TPB, st = ipow(n, d);
+// (state-dependent non-conservative product), accumulated on the momentum line v = 1 + d as
+// R -= g h (1/h_d) G[t, j][d].
+template <class C, int d>
+__device__ __forceinline__ void ncp_swe_lines(const double* X, const double* G, double inv_h,
+                                              double grav, double (&R)[C::LPT][C::n], int tid) {
+  constexpr int n = C::n, NV = C::NV, NL = C::NL, NS = C::NS, TPB = C::TPB, D = C::DIM;
 #pragma unroll
   for (int k = 0; k < C::LPT; ++k) {
     const int l = tid + k * TPB;
     if (l < NL) {
       const int j = l / NV, v = l - (l / NV) * NV;
       if (v == 1 + d) {
-        const int jd = digit<n, d>(j);
-        const int j0 = j - jd * st;
-        const double* Dr = Dm + jd * RS;
 #pragma unroll
-        for (int t = 0; t < n; ++t) {
-          double acc = 0.0;
-#pragma unroll
-          for (int m = 0; m < n; ++m) {
-            const double* q = X + t * NL + (j0 + m * st) * NV;
-            acc = fma(Dr[m], q[0] + q[3], acc);
-          }
-          R[k][t] = fma(-grav * inv_h * X[t * NL + j * NV], acc, R[k][t]);
-        }
+        for (int t = 0; t < n; ++t)
+          R[k][t] = fma(-grav * inv_h * X[t * NL + j * NV], G[(t * NS + j) * D + d], R[k][t]);
       }
     }
   }
@@ -280,6 +304,7 @@ __device__ __forceinline__ void predictor_cell(const StepArgs& A, const Tables& 
   extern __shared__ double smem[];
   double* qs = smem;           // [n][NL] space-time predictor (time-major)
   double* Fs = smem + n * NL;  // [FSLOTS][NL] fluxes (conservative systems)
+  double* G = Fs + C::FSLOTS * NL;  // [NST][D] surface derivatives (shallow water)
   const int tid = threadIdx.x;
   const double dt = A.dev->dt;
   const double tn = A.dev->t;
@@ -339,6 +364,7 @@ __device__ __forceinline__ void predictor_cell(const StepArgs& A, const Tables& 
       double qn[C::NPT][NV];
       typename P::Aux ax[C::NPT];
       load_nodes<C, P>(qs, A.p, qn, ax, tid);
+      if constexpr (P::NCPS) surface_derivs<C, n>(qs, sD, G, tid);
       flux_nodes<C, 0, P>(qn, ax, A.p, Fs, tid);
       __syncthreads();
       contract_lines<C, 0, n>(Fs, sD, -A.g.inv_h[0], R, tid);
@@ -359,8 +385,8 @@ __device__ __forceinline__ void predictor_cell(const StepArgs& A, const Tables& 
       contract_ncp_elastic<C, 2, n>(qs, sD, A.g.inv_h[2], irho, lam, mu, R, tid);
     }
     if constexpr (P::NCPS) {
-      contract_ncp_swe<C, 0, n>(qs, sD, A.g.inv_h[0], A.p.grav, R, tid);
-      contract_ncp_swe<C, 1, n>(qs, sD, A.g.inv_h[1], A.p.grav, R, tid);
+      ncp_swe_lines<C, 0>(qs, G, A.g.inv_h[0], A.p.grav, R, tid);
+      ncp_swe_lines<C, 1>(qs, G, A.g.inv_h[1], A.p.grav, R, tid);
     }
     if (has_src) {
 #pragma unroll
@@ -411,6 +437,7 @@ __device__ __forceinline__ void predictor_cell(const StepArgs& A, const Tables& 
     double qn[C::NPT][NV];
     typename P::Aux ax[C::NPT];
     load_nodes<C, P>(qs, A.p, qn, ax, tid);
+    if constexpr (P::NCPS) surface_derivs<C, n>(qs, sD, G, tid);  // of the final predictor
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       if (d == 0) flux_nodes<C, 0, P>(qn, ax, A.p, Fs, tid);
@@ -492,15 +519,8 @@ __device__ __forceinline__ void predictor_cell(const StepArgs& A, const Tables& 
           if (v == 1 + d) {
             double nb = 0.0;
 #pragma unroll
-            for (int t = 0; t < n; ++t) {
-              double acc = 0.0;
-#pragma unroll
-              for (int m = 0; m < n; ++m) {
-                const double* q = qs + t * NL + (j0 + m * st) * NV;
-                acc = fma(sD[jd * n + m], q[0] + q[3], acc);
-              }
-              nb = fma(T.w[t] * qs[t * NL + j * NV], acc, nb);
-            }
+            for (int t = 0; t < n; ++t)
+              nb = fma(T.w[t] * qs[t * NL + j * NV], G[(t * C::NS + j) * D + d], nb);
             vol -= A.g.inv_h[d] * A.p.grav * nb;
           }
         }

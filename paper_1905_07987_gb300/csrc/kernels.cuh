@@ -837,6 +837,97 @@ __global__ void __launch_bounds__(128) k_riemann(const __grid_constant__ StepArg
                         threadIdx.x & 31);
 }
 
+// Faces with few nodes (NF <= 16): FPW faces per warp, one lane per (face, node), so that the
+// FP64 speed evaluations and flux combinations fill the warp (an FP64 instruction costs the
+// whole warp's pipe time, whatever its active lanes).  The node-by-node path of riemann_face
+// with the same arithmetic; the face's speed is the maximum over its NF lanes.  For the FP64
+// form of the nonlinear conservative systems (Euler, shallow water: no face speeds from the
+// predictor).
+template <class P, int D, int N>
+struct RiemannPack {
+  static constexpr int NF = Cfg<P, D, N>::NF;
+  static constexpr int FPW = NF <= 16 ? 32 / NF : 1;
+  static constexpr bool USE = P::CONS && !P::LINEAR && !P::NCP && FPW >= 2;
+};
+
+template <class P, int D, int N>
+__global__ void __launch_bounds__(128) k_riemann_packed(const __grid_constant__ StepArgs A,
+                                                        const __grid_constant__ Tables T, int d,
+                                                        long long phi_off) {
+  using C = Cfg<P, D, N>;
+  constexpr int NV = C::NV, NF = C::NF, FR = C::FR, NPHI = C::NPHI;
+  constexpr int FPW = RiemannPack<P, D, N>::FPW;
+  const int lane = threadIdx.x & 31;
+  const int slot = lane / NF, jp = lane - slot * NF;
+  const Geometry& g = A.g;
+  const int nd = g.n[d];
+  const long long nfaces = (long long)(nd + 1) * FaceIdx::ntrans(g, d);
+  const long long f = ((long long)blockIdx.x * 4 + (threadIdx.x >> 5)) * FPW + slot;
+  const bool periodic = (g.bc[d][0] == BC_PERIODIC);
+  bool on = slot < FPW && f < nfaces;
+  int kf = 0;
+  long long tr = 0;
+  if (on) {
+    kf = (int)(f % (nd + 1));
+    tr = f / (nd + 1);
+    if (periodic && kf == nd) on = false;  // duplicate of face 0
+  }
+  double qL[NV], qR[NV], FL[NV], FRv[NV];
+  double sp = 0.0;
+  if (on) {
+    long long cL = -1, cR = -1;
+    if (kf > 0) cL = FaceIdx::cell_of(g, tr, d, kf - 1);
+    else if (periodic) cL = FaceIdx::cell_of(g, tr, d, nd - 1);
+    if (kf < nd) cR = FaceIdx::cell_of(g, tr, d, kf);
+    else if (periodic) cR = FaceIdx::cell_of(g, tr, d, 0);
+    const double* recL = cL >= 0 ? A.face + cL * (long long)(D * 2 * FR) + (d * 2 + 1) * FR : nullptr;
+    const double* recR = cR >= 0 ? A.face + cR * (long long)(D * 2 * FR) + (d * 2 + 0) * FR : nullptr;
+    const double* a = recL ? recL : recR;
+    const double* b = recR ? recR : recL;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      qL[v] = a[jp * NV + v];
+      qR[v] = b[jp * NV + v];
+      FL[v] = a[NF * NV + jp * NV + v];
+      FRv[v] = b[NF * NV + jp * NV + v];
+    }
+    // ghost states and speeds with a compile-time direction (the states stay in registers)
+#pragma unroll
+    for (int dd = 0; dd < D; ++dd) {
+      if (dd != d) continue;
+      if (!recL) ghost<P>(g.bc[dd][0], dd, qL, FL);
+      if (!recR) ghost<P>(g.bc[dd][1], dd, qR, FRv);
+      sp = fmax(P::speed(qL, A.p, dd), P::speed(qR, A.p, dd));
+    }
+  }
+  // the face's speed: the maximum over its NF lanes (every lane takes part in the shuffles)
+  double s = 0.0;
+  const int base = (slot < FPW ? slot : 0) * NF;
+#pragma unroll
+  for (int k = 0; k < NF; ++k) s = fmax(s, __shfl_sync(0xffffffffu, sp, base + k));
+  if (!on) return;
+  double* out = A.phi + phi_off + f * (long long)(NPHI * NF * NV);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double G = 0.5 * (FL[v] + FRv[v]) - 0.5 * s * (qR[v] - qL[v]);
+    if constexpr (P::NCPS) {
+      // the path-conservative fluctuation of the shallow water equations, as in riemann_face
+      double half = 0.0;
+      if (v == 1 + d) {
+        const double dh = qR[0] - qL[0], dhb = dh + (qR[3] - qL[3]);
+        double fl = 0.0;
+#pragma unroll
+        for (int gq = 0; gq < 3; ++gq) fl = fma(T.pw[gq], A.p.grav * fma(T.pz[gq], dh, qL[0]) * dhb, fl);
+        half = 0.5 * fl;
+      }
+      out[jp * NV + v] = G + half;
+      out[NF * NV + jp * NV + v] = G - half;
+    } else {
+      out[jp * NV + v] = G;
+    }
+  }
+}
+
 // Corrector, face part of Eq. (6) in strong form:
 //   u_j -= dt sum_d [ (e1_{j_d}/(w_{j_d} h_d)) Phi_L(right face) - (e0_{j_d}/(w_{j_d} h_d)) Phi_R(left face) ]
 // One degree of freedom e of the context; sw = {dt e0/(w h), dt e1/(w h)} of the context.
@@ -1059,6 +1150,16 @@ cudaError_t launch_riemann_n(const StepArgs& a, const Tables& t, cudaStream_t s)
   long long off = 0;
   for (int d = 0; d < D; ++d) {
     const long long nf = (long long)(a.g.n[d] + 1) * (a.g.ncells / a.g.n[d]);
+    if constexpr (RiemannPack<P, D, N>::USE) {
+      if (!a.fspeed) {
+        constexpr int FPB = 4 * RiemannPack<P, D, N>::FPW;  // faces per block
+        k_riemann_packed<P, D, N><<<(unsigned)((nf + FPB - 1) / FPB), 128, 0, s>>>(a, t, d, off);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        off += nf * (long long)(C::NPHI * C::NF * C::NV);
+        continue;
+      }
+    }
     const long long blocks = (nf + 3) / 4;
     k_riemann<P, D, N><<<(unsigned)blocks, 128, 0, s>>>(a, t, d, off);
     cudaError_t e = cudaGetLastError();

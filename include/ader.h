@@ -56,7 +56,9 @@ typedef enum {
  * predictor): Q = (h, hu, hv, b), flux (h u_d, hu u_d, hv u_d, 0) and the state-dependent
  * non-conservative product g h d(h + b)/dx_d on the momentum of direction d, taken node by node
  * in the predictor and as the path-conservative fluctuation along the straight segment between
- * the face states (3-point rule) at faces. */
+ * the face states (3-point rule) at faces.  Shallow water has no limiter: a state whose depth
+ * h falls to or below zero gives a non-finite wave speed sqrt(g h), which the CFL reduction of
+ * a step with the CFL dt latches as ADER_ENONFINITE. */
 typedef enum { ADER_PDE_ADVECTION = 0, ADER_PDE_EULER = 1, ADER_PDE_ELASTIC = 2,
                ADER_PDE_SWE = 3 } ader_pde;
 

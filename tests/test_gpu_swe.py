@@ -80,3 +80,22 @@ def test_swe_options_beyond_the_kernels_are_rejected():
         with pytest.raises(ader.AderError) as e:
             ader.Context(cfg)
         assert e.value.status == ader.EUNSUPPORTED, kw
+
+
+def test_swe_depth_loss_is_reported():
+    """Shallow water has no limiter: a state whose depth reaches zero or below gives a non-finite
+    wave speed sqrt(g h), latched by the CFL reduction as ADER_ENONFINITE; a wet state afterwards
+    steps normally."""
+    c = Case("swe", 2, 3, (6, 5), bc="periodic")
+    u0 = flow_over_bump(c.X)
+    for h in (0.0, -0.01):
+        bad = u0.copy()
+        bad[7, 1, 2, 0] = h
+        c.set(bad)
+        c.ctx.step()
+        with pytest.raises(ader.AderError) as e:
+            c.ctx.sync()
+        assert e.value.status == ader.ENONFINITE, h
+    c.set(u0)
+    c.ctx.step()
+    c.ctx.sync()

@@ -68,11 +68,6 @@ __device__ __forceinline__ int kmaj_off(int r, int k) {
 __device__ __forceinline__ constexpr int ck_need(int d, int q) {
   return q < 3 ? q : Elastic::sig(q - 3, d);
 }
-// Inverse: the slot q of variable v in direction d, -1 if its derivative is not needed.
-__device__ __forceinline__ constexpr int ck_slot(int d, int v) {
-  return v < 3 ? v
-               : (v == Elastic::sig(0, d) ? 3 : (v == Elastic::sig(1, d) ? 4 : (v == Elastic::sig(2, d) ? 5 : -1)));
-}
 
 // The three variables of direction d whose derivatives no row of B_d reads (their faces are
 // extrapolated in a separate pass): the normal stresses other than sigma_dd and the shear stress
